@@ -1,0 +1,227 @@
+/*
+ * dda.h -- C ABI of the GB300 DDA hot path: the FFT-accelerated product of
+ * the Discrete Dipole Approximation interaction matrix with a vector, the
+ * Krylov solves built on it, the bit-fielded target description and the
+ * cross sections (Mc Donald, Golden & Jennings, "OpenDDA: a novel
+ * high-performance computational framework for the Discrete Dipole
+ * Approximation", arXiv:0908.0863).
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ * Units: Gaussian, lattice spacing d = 1, wavenumber k in units of 1/d.
+ *   The system solved is  sum_l A_jl P_l = E_inc,j  with A_jj = alpha_j^-1
+ *   and, for j != l, r = r_j - r_l,
+ *   A_jl = exp(ikr)/r^3 [ k^2 (r r - r^2 I) + (ikr - 1)/r^2 (3 r r - r^2 I) ]
+ *   (Eq. 1 with the dyadic product of Eq. 2; the SI prefactor k^2/eps0 and
+ *   1/(4 pi) of the paper are absorbed into the unit of P).
+ * Lattice: K x J x P sites along x, y, z; site (i, j, k) has linear index
+ *   s = (k J + j) K + i, x fastest (App. A), and sits at r = (i, j, k).
+ * Occupancy bit field (Sec. 2): uint32 words, site s -> word s >> 5,
+ *   bit s & 31 (least significant first); ceil(KJP / 32) words.
+ * Composition bit field (Sec. 2): b = max(1, ceil(log2 n_materials)) bits
+ *   per field, floor(32 / b) whole fields per uint32 word (none straddles),
+ *   field q = 3 s + axis (axis 0, 1, 2 = x, y, z) at word q / f, bit offset
+ *   (q % f) * b.  NULL when n_materials == 1.
+ * Compressed vectors (Sec. 4, zero storage): [3][N_d] complex, component
+ *   major; entry n of each component belongs to the n-th occupied site in
+ *   increasing s.  DDA_C128 = interleaved (re, im) doubles, DDA_C64 =
+ *   interleaved floats.  Device buffers must be 16-byte aligned.
+ * Streams: every call takes a cudaStream_t as void* (NULL = legacy default
+ *   stream) and is stream ordered; a context serves one stream at a time
+ *   (its scratch is shared by all its calls).
+ * Ownership: the caller owns every buffer it passes; the context owns its
+ *   device state (bit fields, ranks, Green's-tensor spectra, scratch and
+ *   solver workspace), all allocated by dda_init_lattice and released by
+ *   dda_free.  No other call allocates device memory.
+ * Errors: every int-returning call returns a dda_status; on failure
+ *   dda_last_error() gives a message (thread local).  Arguments are
+ *   checked before any work is queued; a failed call leaves outputs
+ *   unspecified and the context usable unless DDA_ERR_CUDA is returned.
+ */
+#ifndef DDA_H_
+#define DDA_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dda_ctx dda_ctx; /* opaque, library owned */
+
+typedef enum {
+    DDA_OK = 0,
+    DDA_ERR_ARG = -1,            /* bad shape, pointer, size or option      */
+    DDA_ERR_CUDA = -2,           /* a CUDA call failed                      */
+    DDA_ERR_OOM = -3,            /* device allocation failed                */
+    DDA_ERR_NOT_CONVERGED = -4,  /* max_iter reached; last iterate returned */
+    DDA_ERR_BREAKDOWN = -5,      /* Krylov breakdown (a zero denominator)   */
+    DDA_ERR_NAN = -6             /* non-finite value met                    */
+} dda_status;
+
+typedef enum { DDA_C128 = 0, DDA_C64 = 1 } dda_dtype;
+typedef enum { DDA_BICG = 0, DDA_BICGSTAB = 1, DDA_QMR = 2 } dda_method;
+typedef enum { DDA_FP64 = 0, DDA_MIXED = 1 } dda_precision;
+typedef enum { DDA_POL_CM = 0, DDA_POL_CMRR = 1, DDA_POL_LDR = 2 } dda_polarizability_rule;
+
+typedef struct {
+    int iterations;           /* Krylov iterations (inner ones summed, mixed)   */
+    int matvecs;              /* products with A in the working precision        */
+    int matvecs_fp64;         /* FP64 products (mixed: true-residual products)   */
+    int refinements;          /* outer refinement steps (mixed), 0 for FP64      */
+    double rel_residual;      /* last recurrence residual / ||E_inc||            */
+    double rel_residual_true; /* ||E_inc - A P|| / ||E_inc|| with an FP64 product */
+    double seconds;           /* wall time of the call                           */
+} dda_solve_info;
+
+/* ---------------------------------------------------------------- target */
+
+/*
+ * Polarisability of each material (host only, no GPU work).  Sec. 1 cites
+ * the prescriptions without formulas; they are, with eps = m^2,
+ *   CM   : a = (3 / 4pi) (eps - 1) / (eps + 2)
+ *   CMRR : a_CM / (1 - (2/3) i k^3 a_CM)                  (Draine 1988)
+ *   LDR  : a_CM / (1 + a_CM [(b1 + m^2 b2 + m^2 b3 S) k^2 - (2/3) i k^3]),
+ *          b1 = -1.8915316, b2 = 0.1648469, b3 = -1.7700004,
+ *          S = sum_a (khat_a e0_a)^2                      (Draine & Goodman 1993)
+ * m: [n][2] (re, im); khat: unit propagation (LDR only, may be NULL
+ * otherwise); e0: [3][2] polarisation (LDR only); alpha_out: [n][3][2], the
+ * same value on all three axes.  Returns DDA_ERR_ARG for n < 1 or an
+ * unknown rule.
+ */
+int dda_polarizability(int n, const double* m, double k, int rule, const double* khat,
+                       const double* e0, double* alpha_out);
+
+/*
+ * Pack a per-site occupancy mask into the occupancy bit field (Sec. 2;
+ * kernel family (d)).  mask: device uint8[n_sites] (nonzero = occupied);
+ * bits: device uint32[ceil(n_sites/32)], fully overwritten (padding bits 0).
+ */
+int dda_pack_occupancy(const uint8_t* mask, int64_t n_sites, uint32_t* bits, void* stream);
+
+/* Inverse of dda_pack_occupancy: bits -> uint8 mask[n_sites] (0/1), device. */
+int dda_unpack_occupancy(const uint32_t* bits, int64_t n_sites, uint8_t* mask, void* stream);
+
+/*
+ * Pack per-site, per-axis material indices into the composition bit field
+ * (Sec. 2).  materials: device uint8[n_sites][3]; bits: device
+ * uint32[ceil(3 n_sites / floor(32/b))].  Indices >= n_materials are
+ * rejected on the device: the call then returns DDA_ERR_ARG.
+ */
+int dda_pack_composition(const uint8_t* materials, int64_t n_sites, int n_materials,
+                         uint32_t* bits, void* stream);
+
+/* Inverse of dda_pack_composition: bits -> uint8 materials[n_sites][3], device. */
+int dda_unpack_composition(const uint32_t* bits, int64_t n_sites, int n_materials,
+                           uint8_t* materials, void* stream);
+
+/*
+ * Build a context for one target and wavenumber (Sec. 2-3, App. A).
+ *   shape:            {K, J, P}, each in [1, 512].
+ *   occupancy_bits:   host or device, layout above.  At least one site occupied.
+ *   composition_bits: host or device, or NULL when n_materials == 1.
+ *   n_materials:      1..256.
+ *   alpha:            host [n_materials][3][2] doubles: polarisability of
+ *                     material q acting on axis c (from dda_polarizability or
+ *                     the caller's own prescription); must be nonzero, finite.
+ *   k:                wavenumber, > 0 and finite.
+ * Allocates all device state, ranks the occupied sites (per-word popcount
+ * and scan), evaluates the six independent Green's-tensor components on
+ * section 1 of the embedding (displacements 0 <= i < K, 0 <= j < J,
+ * 0 <= k < P) and transforms them with the fused Toeplitz-to-circulant
+ * line DFTs of Sec. 3 (x, then y, then z; mirrored halves signed per
+ * Table 1; only L/2 + 1 outputs of each length-L line kept), in FP64, with
+ * a complex64 copy.  L = smallest power of two >= 2n - 1 per axis.
+ * Returns DDA_ERR_ARG (bad shape, pointers, no occupied site, material
+ * index out of range), DDA_ERR_OOM, DDA_ERR_CUDA.  *out is NULL on failure.
+ * The call synchronises the stream before returning.
+ */
+int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occupancy_bits,
+                     const uint32_t* composition_bits, int n_materials, const double* alpha,
+                     double k, void* stream);
+
+/* Release every device resource of the context (NULL is a no-op). */
+void dda_free(dda_ctx* ctx);
+
+/*
+ * Sizes of a context: occupied sites N_d, padded grid {Lx, Ly, Lz} and the
+ * device bytes the context holds.  Any output pointer may be NULL.
+ */
+int dda_query(const dda_ctx* ctx, int64_t* n_dipoles, int32_t padded[3], int64_t* device_bytes);
+
+/*
+ * Compressed index of every site: rank[s] = number of occupied sites before
+ * s (device uint32[KJP]), as the matvec uses it.  Diagnostic entry point
+ * for the bit-exact tests of the occupancy kernels.
+ */
+int dda_site_ranks(const dda_ctx* ctx, uint32_t* rank, void* stream);
+
+/*
+ * Copy the stored half spectrum of the six tensor components, scaled by
+ * 1 / (Lx Ly Lz): device complex [6][Lz/2+1][Ly/2+1][Lx/2+1] of the given
+ * dtype.  Diagnostic entry point (parity of the init step).
+ */
+int dda_tensor_spectrum(const dda_ctx* ctx, void* out, int dtype, void* stream);
+
+/* ------------------------------------------------------------ hot path */
+
+/*
+ * y = A p (Eq. 1) by the pruned FFT algorithm of Sec. 3: expand the
+ * compressed vector (Sec. 4) into the K x J'' x P y-line array and
+ * transform along y (K P lines), transform along x (J'' P lines), then per
+ * z-line forward DFT, the 3 x 3 symmetric spectrum product of Eqs. 6-8
+ * with the signed mirror lookup, and inverse DFT keeping k < P; inverse
+ * along x keeping i < K, inverse along y keeping j < J, add alpha^-1 p and
+ * compress.  p, y: device [3][N_d] complex of the given dtype; p and y may
+ * not overlap.  DDA_C64 runs every step in complex FP32 with the complex64
+ * spectrum.  Returns DDA_ERR_ARG for NULL or host pointers.
+ */
+int dda_matvec(dda_ctx* ctx, const void* p, void* y, int dtype, void* stream);
+
+/*
+ * Incident plane wave at the occupied sites: E_c = e0_c exp(i k khat . r),
+ * r = (i, j, k) (phase origin at site 0).  khat: host unit vector[3];
+ * e0: host [3][2]; einc: device [3][N_d] complex128.
+ */
+int dda_incident_field(dda_ctx* ctx, const double* khat, const double* e0, void* einc, void* stream);
+
+/*
+ * Solve A P = E_inc (Sec. 4) with BiCG, BiCGSTAB or QMR, unpreconditioned.
+ *   einc, p: host or device [3][N_d] complex128.  p is read as the starting
+ *            guess when use_x0 != 0, else the start is 0 (Sec. 6); on return
+ *            it holds the last iterate.
+ *   precision: DDA_FP64 runs everything in FP64.  DDA_MIXED runs an outer
+ *            FP64 iterative refinement: r = E_inc - A P with the FP64
+ *            product, an inner complex64 Krylov solve of A d = r / ||r||
+ *            (complex64 products and vectors, FP64 inner products and
+ *            scalars), P += ||r|| d, until ||r|| <= tol ||E_inc||.
+ *   tol:      relative residual target (> 0); max_iter: cap on Krylov
+ *             iterations (summed over inner solves for DDA_MIXED).
+ *   info:     host, may be NULL.
+ * Stopping rule: ||r||_2 <= tol ||E_inc||_2 on the recurrence residual
+ * (BiCGSTAB also stops half way on ||s||); info->rel_residual_true is then
+ * recomputed with one FP64 product.  Returns DDA_OK, DDA_ERR_NOT_CONVERGED
+ * (max_iter reached, p = last iterate), DDA_ERR_BREAKDOWN, DDA_ERR_NAN,
+ * DDA_ERR_ARG.  Synchronises the stream.
+ */
+int dda_solve(dda_ctx* ctx, const void* einc, void* p, int method, int precision, double tol,
+              int max_iter, int use_x0, dda_solve_info* info, void* stream);
+
+/*
+ * Cross sections with |E0| = 1 (Draine 1988; values only in Table 7):
+ *   C_ext = 4 pi k sum_j Im(E_inc,j^* . P_j)
+ *   C_abs = 4 pi k sum_j sum_c [-Im(alpha^-1_jc) - (2/3) k^3] |P_jc|^2
+ *   C_sca = C_ext - C_abs.
+ * einc, p: host or device [3][N_d] complex128; out: host double[3] =
+ * {C_ext, C_abs, C_sca}.  FP64 reductions in a fixed order (deterministic).
+ * Synchronises the stream.
+ */
+int dda_cross_sections(dda_ctx* ctx, const void* einc, const void* p, double* out, void* stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* dda_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DDA_H_ */

@@ -44,6 +44,10 @@ def lib():
             L.oracle_interaction_tensor.restype = None
             L.oracle_direct_matvec.argtypes = [ctypes.c_int64, ip, dp, ctypes.c_double, dp, dp, ctypes.c_int]
             L.oracle_direct_matvec.restype = None
+            L.oracle_direct_matvec_rows.argtypes = [ctypes.c_int64, ip, dp, ctypes.c_double, dp,
+                                                    ctypes.POINTER(ctypes.c_int64), ctypes.c_int64, dp,
+                                                    ctypes.c_int]
+            L.oracle_direct_matvec_rows.restype = None
             L.oracle_dense_matrix.argtypes = [ctypes.c_int64, ip, dp, ctypes.c_double, dp]
             L.oracle_dense_matrix.restype = None
             L.oracle_csca_double_sum.argtypes = [ctypes.c_int64, ip, ctypes.c_double, dp, ctypes.c_int]

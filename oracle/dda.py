@@ -41,21 +41,23 @@ def pack_occupancy(mask: np.ndarray) -> np.ndarray:
 
     Layout: site s sits in word s // 32 at bit s % 32 (least significant
     first), s = (k J + j) K + i.  Padding bits of the last word are zero.
+    (numpy's packbits with little bit order puts site s at bit s % 8 of
+    byte s // 8; four little-endian bytes make one word.)
     """
     flat = np.asarray(mask).reshape(-1).astype(bool)
     n = flat.size
-    words = np.zeros((n + 31) // 32, dtype=np.uint32)
-    for s in np.nonzero(flat)[0]:
-        words[s >> 5] |= np.uint32(1) << np.uint32(s & 31)
-    return words
+    nbytes = 4 * ((n + 31) // 32)
+    b = np.zeros(nbytes, dtype=np.uint8)
+    packed = np.packbits(flat, bitorder="little")
+    b[:packed.size] = packed
+    return b.view("<u4").astype(np.uint32)
 
 
 def unpack_occupancy(words: np.ndarray, n_sites: int) -> np.ndarray:
-    """Inverse of pack_occupancy: test bit s of the words for every site."""
-    out = np.zeros(n_sites, dtype=np.uint8)
-    for s in range(n_sites):
-        out[s] = (int(words[s >> 5]) >> (s & 31)) & 1
-    return out
+    """Inverse of pack_occupancy: bit s % 32 of word s // 32 for every site."""
+    s = np.arange(n_sites, dtype=np.int64)
+    w = np.asarray(words, dtype=np.uint32).astype(np.int64)
+    return ((w[s >> 5] >> (s & 31)) & 1).astype(np.uint8)
 
 
 def pack_composition(materials: np.ndarray, n_materials: int) -> np.ndarray:
@@ -71,9 +73,10 @@ def pack_composition(materials: np.ndarray, n_materials: int) -> np.ndarray:
     vals = np.asarray(materials).reshape(-1).astype(np.uint64)
     if vals.size and int(vals.max()) >= n_materials:
         raise ValueError("material index out of range")
+    q = np.arange(vals.size, dtype=np.int64)
     words = np.zeros((vals.size + f - 1) // f, dtype=np.uint64)
-    for q in range(vals.size):
-        words[q // f] |= vals[q] << np.uint64((q % f) * b)
+    # fields of one word occupy disjoint bits, so adding them is OR-ing them
+    np.add.at(words, q // f, vals << ((q % f) * b).astype(np.uint64))
     return words.astype(np.uint32)
 
 
@@ -82,10 +85,9 @@ def unpack_composition(words: np.ndarray, n_sites: int, n_materials: int) -> np.
     b = composition_bits(n_materials)
     f = 32 // b
     msk = (1 << b) - 1
-    out = np.zeros(3 * n_sites, dtype=np.int64)
-    for q in range(3 * n_sites):
-        out[q] = (int(words[q // f]) >> ((q % f) * b)) & msk
-    return out.reshape(n_sites, 3)
+    q = np.arange(3 * n_sites, dtype=np.int64)
+    w = np.asarray(words, dtype=np.uint32).astype(np.int64)
+    return ((w[q // f] >> ((q % f) * b)) & msk).reshape(n_sites, 3)
 
 
 def bitfield_bytes(n_sites: int, n_materials: int) -> int:
@@ -215,6 +217,21 @@ def direct_matvec(coords: np.ndarray, ainv: np.ndarray, k: float, p: np.ndarray,
     y = np.empty((3, n), dtype=np.complex128)
     _native.lib().oracle_direct_matvec(n, _ip(c), _dp(a), float(k), _dp(pv), _dp(y), int(nthreads))
     return y
+
+
+def direct_matvec_rows(coords: np.ndarray, ainv: np.ndarray, k: float, p: np.ndarray, rows,
+                       nthreads: int = 0) -> np.ndarray:
+    """(A p) at the given dipoles only, each by its own direct sum; [3][len(rows)]."""
+    n = coords.shape[0]
+    c = np.ascontiguousarray(coords, dtype=np.int32)
+    a = np.ascontiguousarray(ainv, dtype=np.complex128)
+    pv = np.ascontiguousarray(np.asarray(p, dtype=np.complex128).reshape(3, n))
+    rr = np.ascontiguousarray(np.asarray(rows, dtype=np.int64))
+    out = np.empty((3, rr.size), dtype=np.complex128)
+    _native.lib().oracle_direct_matvec_rows(n, _ip(c), _dp(a), float(k), _dp(pv),
+                                            rr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), rr.size,
+                                            _dp(out), int(nthreads))
+    return out
 
 
 def dense_matrix(coords: np.ndarray, ainv: np.ndarray, k: float) -> np.ndarray:

@@ -93,6 +93,53 @@ void oracle_direct_matvec(int64_t n, const int32_t* coords, const double* ainv, 
 }
 
 /*
+ * Selected rows of y = A p: out[c][q] = (A p)_{c, rows[q]} for q < nrows,
+ * out laid out [3][nrows].  The same sum as oracle_direct_matvec, for
+ * checking a few outputs of a large lattice one by one.
+ */
+void oracle_direct_matvec_rows(int64_t n, const int32_t* coords, const double* ainv, double k,
+                               const double* p, const int64_t* rows, int64_t nrows, double* out,
+                               int nthreads) {
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    for (int64_t q = 0; q < nrows; ++q) {
+        const int64_t j = rows[q];
+        double ar[3] = {0, 0, 0}, ai[3] = {0, 0, 0};
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) reduction(+ : ar[:3], ai[:3])
+#endif
+        for (int64_t l = 0; l < n; ++l) {
+            double complex pl[3];
+            for (int c = 0; c < 3; ++c) pl[c] = p[(c * n + l) * 2] + I * p[(c * n + l) * 2 + 1];
+            if (l == j) {
+                for (int c = 0; c < 3; ++c) {
+                    const double complex a = ainv[(j * 3 + c) * 2] + I * ainv[(j * 3 + c) * 2 + 1];
+                    const double complex v = a * pl[c];
+                    ar[c] += creal(v);
+                    ai[c] += cimag(v);
+                }
+                continue;
+            }
+            double complex t[6];
+            interaction_tensor(k, (double)(coords[3 * j] - coords[3 * l]),
+                               (double)(coords[3 * j + 1] - coords[3 * l + 1]),
+                               (double)(coords[3 * j + 2] - coords[3 * l + 2]), t);
+            for (int a = 0; a < 3; ++a) {
+                double complex s = 0.0;
+                for (int b = 0; b < 3; ++b) s += t[comp_of[a][b]] * pl[b];
+                ar[a] += creal(s);
+                ai[a] += cimag(s);
+            }
+        }
+        for (int c = 0; c < 3; ++c) {
+            out[(c * nrows + q) * 2] = ar[c];
+            out[(c * nrows + q) * 2 + 1] = ai[c];
+        }
+    }
+}
+
+/*
  * Dense A (3n x 3n, row-major, complex interleaved), unknown ordering
  * [3][n] to match the vectors: row index a*n + j, column index b*n + l.
  */

@@ -1,0 +1,76 @@
+"""GB300 (sm_103a) library for the DDA hot path of OpenDDA (arXiv:0908.0863).
+
+The FFT-accelerated interaction-matrix product of the Discrete Dipole
+Approximation, the Krylov solves built on it (BiCG, BiCGSTAB, QMR in FP64
+or complex64-inside-FP64 refinement), the bit-fielded target description
+and the cross sections, all as hand-written CUDA kernels behind the C ABI
+of ``include/dda.h``.  This package is the thin Python binding: the names
+are the C entry points; ``Lattice`` only bundles a context handle.
+
+Importing the package loads the CUDA library and raises if it has not been
+built (``__graft_entry__.build()``); there is no CPU fallback.
+"""
+from __future__ import annotations
+
+from ._lib import (  # noqa: F401
+    DDA_BICG, DDA_BICGSTAB, DDA_C64, DDA_C128, DDA_ERR_ARG, DDA_ERR_BREAKDOWN, DDA_ERR_CUDA, DDA_ERR_NAN,
+    DDA_ERR_NOT_CONVERGED, DDA_ERR_OOM, DDA_FP64, DDA_MIXED, DDA_OK, DDA_QMR, EXPORTS, DDAError,
+    dda_cross_sections, dda_free, dda_incident_field, dda_init_lattice, dda_last_error, dda_matvec,
+    dda_pack_composition, dda_pack_occupancy, dda_polarizability, dda_query, dda_site_ranks, dda_solve,
+    dda_tensor_spectrum, dda_unpack_composition, dda_unpack_occupancy, library_path, load,
+)
+
+load()
+
+
+class Lattice:
+    """A context (target + wavenumber) with the entry points as methods.
+
+    occupancy_bits / composition_bits: packed words (numpy on the host or a
+    torch tensor on the device), alpha: (n_materials, 3) complex.
+    """
+
+    def __init__(self, shape, occupancy_bits, alpha, k, composition_bits=None, n_materials=1, stream=None):
+        self.shape = tuple(int(v) for v in shape)
+        self.k = float(k)
+        self.ctx = dda_init_lattice(self.shape, occupancy_bits, composition_bits, n_materials, alpha, k, stream)
+        q = dda_query(self.ctx)
+        self.n_dipoles = q["n_dipoles"]
+        self.padded = q["padded"]
+        self.device_bytes = q["device_bytes"]
+
+    def close(self):
+        if self.ctx:
+            dda_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def matvec(self, p, y, stream=None):
+        dda_matvec(self.ctx, p, y, stream)
+
+    def incident_field(self, khat, e0, einc, stream=None):
+        dda_incident_field(self.ctx, khat, e0, einc, stream)
+
+    def solve(self, einc, p, method="bicgstab", precision="fp64", tol=1e-8, max_iter=1000, use_x0=False,
+              stream=None):
+        return dda_solve(self.ctx, einc, p, method, precision, tol, max_iter, use_x0, stream)
+
+    def cross_sections(self, einc, p, stream=None):
+        return dda_cross_sections(self.ctx, einc, p, stream)
+
+    def site_ranks(self, rank, stream=None):
+        dda_site_ranks(self.ctx, rank, stream)
+
+    def tensor_spectrum(self, out, stream=None):
+        dda_tensor_spectrum(self.ctx, out, stream)

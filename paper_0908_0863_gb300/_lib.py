@@ -1,0 +1,238 @@
+"""ctypes binding of the C ABI in include/dda.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does
+nothing but convert arguments (torch tensors -> device pointers, numpy
+arrays -> host pointers, streams -> cudaStream_t) and turn error codes into
+exceptions.  All computation happens in the CUDA library; if that library
+is missing the import of this module fails instead of falling back.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+DDA_OK = 0
+DDA_ERR_ARG = -1
+DDA_ERR_CUDA = -2
+DDA_ERR_OOM = -3
+DDA_ERR_NOT_CONVERGED = -4
+DDA_ERR_BREAKDOWN = -5
+DDA_ERR_NAN = -6
+DDA_C128 = 0
+DDA_C64 = 1
+DDA_BICG, DDA_BICGSTAB, DDA_QMR = 0, 1, 2
+DDA_FP64, DDA_MIXED = 0, 1
+DDA_POL_CM, DDA_POL_CMRR, DDA_POL_LDR = 0, 1, 2
+
+METHODS = {"bicg": DDA_BICG, "bicgstab": DDA_BICGSTAB, "qmr": DDA_QMR}
+PRECISIONS = {"fp64": DDA_FP64, "mixed": DDA_MIXED}
+RULES = {"cm": DDA_POL_CM, "cmrr": DDA_POL_CMRR, "ldr": DDA_POL_LDR}
+
+# every entry point declared in include/dda.h
+EXPORTS = (
+    "dda_polarizability", "dda_pack_occupancy", "dda_unpack_occupancy", "dda_pack_composition",
+    "dda_unpack_composition", "dda_init_lattice", "dda_free", "dda_query", "dda_site_ranks",
+    "dda_tensor_spectrum", "dda_matvec", "dda_incident_field", "dda_solve", "dda_cross_sections",
+    "dda_last_error",
+)
+
+
+class DDAError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("matvecs", ctypes.c_int), ("matvecs_fp64", ctypes.c_int),
+                ("refinements", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("rel_residual_true", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libdda.so (built by __graft_entry__.build()); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"DDA CUDA library not built ({path}); run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    vp, i64, i32, d = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    L.dda_polarizability.argtypes = [i32, vp, d, i32, vp, vp, vp]
+    L.dda_pack_occupancy.argtypes = [vp, i64, vp, vp]
+    L.dda_unpack_occupancy.argtypes = [vp, i64, vp, vp]
+    L.dda_pack_composition.argtypes = [vp, i64, i32, vp, vp]
+    L.dda_unpack_composition.argtypes = [vp, i64, i32, vp, vp]
+    L.dda_init_lattice.argtypes = [ctypes.POINTER(vp), vp, vp, vp, i32, vp, d, vp]
+    L.dda_free.argtypes = [vp]
+    L.dda_free.restype = None
+    L.dda_query.argtypes = [vp, vp, vp, vp]
+    L.dda_site_ranks.argtypes = [vp, vp, vp]
+    L.dda_tensor_spectrum.argtypes = [vp, vp, i32, vp]
+    L.dda_matvec.argtypes = [vp, vp, vp, i32, vp]
+    L.dda_incident_field.argtypes = [vp, vp, vp, vp, vp]
+    L.dda_solve.argtypes = [vp, vp, vp, i32, i32, d, i32, i32, ctypes.POINTER(SolveInfo), vp]
+    L.dda_cross_sections.argtypes = [vp, vp, vp, vp, vp]
+    L.dda_last_error.argtypes = []
+    L.dda_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("dda_free", "dda_last_error"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(code):
+    if code != DDA_OK:
+        raise DDAError(code, load().dda_last_error().decode())
+    return code
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(x):
+    """Device pointer of a torch tensor, or host pointer of a numpy array."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(x.ctypes.data)
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(x.data_ptr())
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _dtype_code(t):
+    import torch
+    if t.dtype == torch.complex128:
+        return DDA_C128
+    if t.dtype == torch.complex64:
+        return DDA_C64
+    raise TypeError("vectors must be complex128 or complex64")
+
+
+def _c2(v, n):
+    a = np.asarray(v, dtype=np.complex128).reshape(n)
+    return np.ascontiguousarray(np.stack([a.real, a.imag], axis=-1).reshape(-1))
+
+
+# ------------------------------------------------------------ entry points
+
+def dda_polarizability(m, k, rule="cmrr", khat=None, e0=None) -> np.ndarray:
+    """alpha per material and axis, shape (n_materials, 3) complex128."""
+    m = np.atleast_1d(np.asarray(m, dtype=np.complex128))
+    n = m.size
+    out = np.zeros(n * 6)
+    kh = None if khat is None else np.ascontiguousarray(np.asarray(khat, dtype=np.float64))
+    ee = None if e0 is None else _c2(e0, 3)
+    _check(load().dda_polarizability(n, _ptr(_c2(m, n)), float(k), RULES.get(rule, rule),
+                                     _ptr(kh), _ptr(ee), _ptr(out)))
+    return (out[0::2] + 1j * out[1::2]).reshape(n, 3)
+
+
+def dda_pack_occupancy(mask, bits, stream=None):
+    _check(load().dda_pack_occupancy(_ptr(mask), mask.numel(), _ptr(bits), _stream(stream)))
+
+
+def dda_unpack_occupancy(bits, n_sites, mask, stream=None):
+    _check(load().dda_unpack_occupancy(_ptr(bits), int(n_sites), _ptr(mask), _stream(stream)))
+
+
+def dda_pack_composition(materials, n_sites, n_materials, bits, stream=None):
+    _check(load().dda_pack_composition(_ptr(materials), int(n_sites), int(n_materials), _ptr(bits),
+                                       _stream(stream)))
+
+
+def dda_unpack_composition(bits, n_sites, n_materials, materials, stream=None):
+    _check(load().dda_unpack_composition(_ptr(bits), int(n_sites), int(n_materials), _ptr(materials),
+                                         _stream(stream)))
+
+
+def dda_init_lattice(shape, occupancy_bits, composition_bits, n_materials, alpha, k, stream=None):
+    """Returns an opaque context handle (int).  Bit fields: numpy (host) or torch (device)."""
+    ctx = ctypes.c_void_p()
+    shp = np.ascontiguousarray(np.asarray(shape, dtype=np.int32).reshape(3))
+    al = _c2(np.asarray(alpha, dtype=np.complex128).reshape(-1), int(n_materials) * 3)
+    _check(load().dda_init_lattice(ctypes.byref(ctx), _ptr(shp), _ptr(occupancy_bits),
+                                   _ptr(composition_bits), int(n_materials), _ptr(al), float(k),
+                                   _stream(stream)))
+    return ctx.value
+
+
+def dda_free(ctx):
+    load().dda_free(ctypes.c_void_p(ctx))
+
+
+def dda_query(ctx):
+    nd = ctypes.c_int64()
+    pad = (ctypes.c_int32 * 3)()
+    nb = ctypes.c_int64()
+    _check(load().dda_query(ctypes.c_void_p(ctx), ctypes.byref(nd), pad, ctypes.byref(nb)))
+    return {"n_dipoles": nd.value, "padded": tuple(pad), "device_bytes": nb.value}
+
+
+def dda_site_ranks(ctx, rank, stream=None):
+    _check(load().dda_site_ranks(ctypes.c_void_p(ctx), _ptr(rank), _stream(stream)))
+
+
+def dda_tensor_spectrum(ctx, out, stream=None):
+    _check(load().dda_tensor_spectrum(ctypes.c_void_p(ctx), _ptr(out), _dtype_code(out), _stream(stream)))
+
+
+def dda_matvec(ctx, p, y, stream=None):
+    if p.dtype != y.dtype:
+        raise TypeError("p and y must have the same dtype")
+    _check(load().dda_matvec(ctypes.c_void_p(ctx), _ptr(p), _ptr(y), _dtype_code(p), _stream(stream)))
+
+
+def dda_incident_field(ctx, khat, e0, einc, stream=None):
+    kh = np.ascontiguousarray(np.asarray(khat, dtype=np.float64).reshape(3))
+    _check(load().dda_incident_field(ctypes.c_void_p(ctx), _ptr(kh), _ptr(_c2(e0, 3)), _ptr(einc),
+                                     _stream(stream)))
+
+
+def dda_solve(ctx, einc, p, method="bicgstab", precision="fp64", tol=1e-8, max_iter=1000, use_x0=False,
+              stream=None):
+    """Returns (status, info dict); raises only for argument / CUDA errors."""
+    info = SolveInfo()
+    code = load().dda_solve(ctypes.c_void_p(ctx), _ptr(einc), _ptr(p), METHODS.get(method, method),
+                            PRECISIONS.get(precision, precision), float(tol), int(max_iter), int(bool(use_x0)),
+                            ctypes.byref(info), _stream(stream))
+    if code in (DDA_ERR_ARG, DDA_ERR_CUDA, DDA_ERR_OOM):
+        _check(code)
+    return code, info.as_dict()
+
+
+def dda_cross_sections(ctx, einc, p, stream=None):
+    out = np.zeros(3)
+    _check(load().dda_cross_sections(ctypes.c_void_p(ctx), _ptr(einc), _ptr(p), _ptr(out), _stream(stream)))
+    return tuple(float(v) for v in out)
+
+
+def dda_last_error() -> str:
+    return load().dda_last_error().decode()

@@ -1,0 +1,561 @@
+// C ABI of the library (include/dda.h): context set-up, the matvec, the
+// solves with FP64 or mixed-precision iterative refinement, and the
+// observables.  Host code only orchestrates; every step runs in the kernels
+// of matvec.cu, spectrum.cu, target.cu and krylov.cu.
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "krylov.cuh"
+#include "matvec.cuh"
+#include "spectrum.cuh"
+#include "target.cuh"
+
+namespace dda {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+int fail(int status, const std::string& msg) {
+    g_last_error = msg;
+    return status;
+}
+int cuda_fail(cudaError_t e, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? DDA_ERR_OOM : DDA_ERR_CUDA;
+}
+
+static bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// bump allocator over one device allocation
+struct Arena {
+    char* base = nullptr;
+    size_t used = 0, cap = 0;
+    template <typename X> X* take(size_t count) {
+        used = (used + 255) & ~size_t(255);
+        X* p = reinterpret_cast<X*>(base + used);
+        used += count * sizeof(X);
+        return p;
+    }
+};
+
+__global__ void k_clear_tail(uint32_t* occ, int64_t nwords, int64_t nsites) {
+    const int rem = (int)(nsites & 31);
+    if (rem) occ[nwords - 1] &= (1u << rem) - 1u;
+}
+
+}  // namespace dda
+
+using namespace dda;
+
+struct dda_ctx {
+    Geometry g{};
+    double k = 0.0;
+    int device = 0;
+    void* arena0 = nullptr;   // target, spectrum, matvec scratch
+    void* arena1 = nullptr;   // solver vectors
+    int64_t bytes = 0;
+    uint32_t *occ = nullptr, *rank = nullptr, *comp = nullptr;
+    double2* ainv64 = nullptr;
+    float2* ainv32 = nullptr;
+    double2* spec64 = nullptr;
+    float2* spec32 = nullptr;
+    double2* tw64 = nullptr;
+    float2* tw32 = nullptr;
+    void* work = nullptr;
+    double2* xsec = nullptr;
+    double2* x64 = nullptr;   // solution
+    double2* b64 = nullptr;   // right-hand side
+    double2* r64 = nullptr;   // outer residual
+    float2* b32 = nullptr;    // inner right-hand side
+    float2* d32 = nullptr;    // inner solution
+    KrylovWork<double> w64{};
+    KrylovWork<float> w32{};
+    KState* host_state = nullptr;  // pinned, 2 entries
+    MatvecView<double> mv64{};
+    MatvecView<float> mv32{};
+};
+
+namespace {
+
+TargetView target_view(const dda_ctx* c) {
+    TargetView t;
+    t.occ = c->occ;
+    t.rank = c->rank;
+    t.comp = c->comp;
+    t.cbits = c->g.cbits;
+    t.cfields = c->g.cfields;
+    return t;
+}
+
+int check_ctx(const dda_ctx* c) {
+    if (!c) return fail(DDA_ERR_ARG, "null context");
+    return 0;
+}
+
+int check_dev(const void* p, const char* what) {
+    if (!p) return fail(DDA_ERR_ARG, std::string(what) + " is NULL");
+    if (!is_device_ptr(p)) return fail(DDA_ERR_ARG, std::string(what) + " must be a device pointer");
+    if (reinterpret_cast<uintptr_t>(p) % 16) return fail(DDA_ERR_ARG, std::string(what) + " must be 16-byte aligned");
+    return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dda_last_error(void) { return g_last_error.c_str(); }
+
+int dda_polarizability(int n, const double* m, double k, int rule, const double* khat, const double* e0,
+                       double* alpha_out) {
+    if (n < 1 || !m || !alpha_out) return fail(DDA_ERR_ARG, "dda_polarizability: bad arguments");
+    if (rule < DDA_POL_CM || rule > DDA_POL_LDR) return fail(DDA_ERR_ARG, "dda_polarizability: unknown rule");
+    if (rule == DDA_POL_LDR && (!khat || !e0)) return fail(DDA_ERR_ARG, "dda_polarizability: LDR needs khat and e0");
+    if (!(k >= 0.0) || !std::isfinite(k)) return fail(DDA_ERR_ARG, "dda_polarizability: bad k");
+    using cd = std::complex<double>;
+    const double b1 = -1.8915316, b2 = 0.1648469, b3 = -1.7700004;
+    double S = 0.0;
+    if (rule == DDA_POL_LDR) {
+        // S = sum_a (khat_a e_a)^2 with e complex; the real part is used
+        cd s = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            const cd t = khat[a] * cd(e0[2 * a], e0[2 * a + 1]);
+            s += t * t;
+        }
+        S = s.real();
+    }
+    for (int q = 0; q < n; ++q) {
+        const cd mm(m[2 * q], m[2 * q + 1]);
+        const cd eps = mm * mm;
+        const cd acm = 3.0 / (4.0 * M_PI) * (eps - 1.0) / (eps + 2.0);
+        cd a = acm;
+        if (rule == DDA_POL_CMRR) {
+            a = acm / (1.0 - cd(0.0, 2.0 / 3.0) * k * k * k * acm);
+        } else if (rule == DDA_POL_LDR) {
+            const cd corr = (b1 + eps * b2 + eps * b3 * S) * (k * k) - cd(0.0, 2.0 / 3.0) * (k * k * k);
+            a = acm / (1.0 + acm * corr);
+        }
+        for (int c = 0; c < 3; ++c) {
+            alpha_out[(q * 3 + c) * 2] = a.real();
+            alpha_out[(q * 3 + c) * 2 + 1] = a.imag();
+        }
+    }
+    return DDA_OK;
+}
+
+int dda_pack_occupancy(const uint8_t* mask, int64_t n_sites, uint32_t* bits, void* stream) {
+    if (n_sites <= 0) return fail(DDA_ERR_ARG, "dda_pack_occupancy: n_sites must be > 0");
+    if (!mask || !bits || !is_device_ptr(mask) || !is_device_ptr(bits))
+        return fail(DDA_ERR_ARG, "dda_pack_occupancy: mask and bits must be device pointers");
+    return launch_pack_occupancy(mask, n_sites, bits, as_stream(stream));
+}
+
+int dda_unpack_occupancy(const uint32_t* bits, int64_t n_sites, uint8_t* mask, void* stream) {
+    if (n_sites <= 0) return fail(DDA_ERR_ARG, "dda_unpack_occupancy: n_sites must be > 0");
+    if (!mask || !bits || !is_device_ptr(mask) || !is_device_ptr(bits))
+        return fail(DDA_ERR_ARG, "dda_unpack_occupancy: mask and bits must be device pointers");
+    return launch_unpack_occupancy(bits, n_sites, mask, as_stream(stream));
+}
+
+int dda_pack_composition(const uint8_t* materials, int64_t n_sites, int n_materials, uint32_t* bits, void* stream) {
+    if (n_sites <= 0 || n_materials < 1 || n_materials > 256)
+        return fail(DDA_ERR_ARG, "dda_pack_composition: bad sizes");
+    if (!materials || !bits || !is_device_ptr(materials) || !is_device_ptr(bits))
+        return fail(DDA_ERR_ARG, "dda_pack_composition: materials and bits must be device pointers");
+    int bad = 0;
+    if (int rc = launch_pack_composition(materials, n_sites, n_materials, bits, &bad, as_stream(stream))) return rc;
+    if (bad) return fail(DDA_ERR_ARG, "dda_pack_composition: material index >= n_materials");
+    return DDA_OK;
+}
+
+int dda_unpack_composition(const uint32_t* bits, int64_t n_sites, int n_materials, uint8_t* materials, void* stream) {
+    if (n_sites <= 0 || n_materials < 1 || n_materials > 256)
+        return fail(DDA_ERR_ARG, "dda_unpack_composition: bad sizes");
+    if (!materials || !bits || !is_device_ptr(materials) || !is_device_ptr(bits))
+        return fail(DDA_ERR_ARG, "dda_unpack_composition: materials and bits must be device pointers");
+    return launch_unpack_composition(bits, n_sites, n_materials, materials, as_stream(stream));
+}
+
+void dda_free(dda_ctx* c) {
+    if (!c) return;
+    if (c->arena0) cudaFree(c->arena0);
+    if (c->arena1) cudaFree(c->arena1);
+    if (c->host_state) cudaFreeHost(c->host_state);
+    delete c;
+}
+
+int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occupancy_bits,
+                     const uint32_t* composition_bits, int n_materials, const double* alpha, double k,
+                     void* stream) {
+    if (!out) return fail(DDA_ERR_ARG, "dda_init_lattice: out is NULL");
+    *out = nullptr;
+    if (!shape || !occupancy_bits || !alpha) return fail(DDA_ERR_ARG, "dda_init_lattice: NULL argument");
+    for (int a = 0; a < 3; ++a)
+        if (shape[a] < 1 || shape[a] > kMaxEdge)
+            return fail(DDA_ERR_ARG, "dda_init_lattice: each lattice edge must be in [1, 512]");
+    if (n_materials < 1 || n_materials > 256) return fail(DDA_ERR_ARG, "dda_init_lattice: n_materials in [1, 256]");
+    if (n_materials > 1 && !composition_bits)
+        return fail(DDA_ERR_ARG, "dda_init_lattice: composition bits required when n_materials > 1");
+    if (!(k > 0.0) || !std::isfinite(k)) return fail(DDA_ERR_ARG, "dda_init_lattice: k must be finite and > 0");
+    for (int i = 0; i < n_materials * 6; ++i)
+        if (!std::isfinite(alpha[i])) return fail(DDA_ERR_NAN, "dda_init_lattice: non-finite polarisability");
+    for (int i = 0; i < n_materials * 3; ++i)
+        if (alpha[2 * i] == 0.0 && alpha[2 * i + 1] == 0.0)
+            return fail(DDA_ERR_ARG, "dda_init_lattice: zero polarisability");
+    cudaStream_t st = as_stream(stream);
+    dda_ctx* c = new dda_ctx();
+    cudaGetDevice(&c->device);
+    Geometry& g = c->g;
+    g.K = shape[0]; g.J = shape[1]; g.P = shape[2];
+    g.Lx = padded_length(g.K); g.Ly = padded_length(g.J); g.Lz = padded_length(g.P);
+    g.Hx = g.Lx / 2 + 1; g.Hy = g.Ly / 2 + 1; g.Hz = g.Lz / 2 + 1;
+    g.nsites = (int64_t)g.K * g.J * g.P;
+    g.nwords = (g.nsites + 31) / 32;
+    g.nmat = n_materials;
+    g.cbits = dda::composition_bits(n_materials);
+    g.cfields = 32 / g.cbits;
+    c->k = k;
+    const int64_t ncw = n_materials > 1 ? (3 * g.nsites + g.cfields - 1) / g.cfields : 0;
+    const size_t nspec = 6ull * g.Hz * g.Hy * g.Hx;
+    const size_t nwork = 3ull * g.P * g.Ly * ((size_t)g.K + g.Lx);   // Ay + Bxy
+    // ---- arena 0: target, tables, spectrum, matvec scratch
+    Arena a0;
+    {
+        Arena probe;  // sizing pass
+        probe.take<uint32_t>(g.nwords);
+        probe.take<uint32_t>(g.nwords);
+        probe.take<uint32_t>(ncw);
+        probe.take<uint32_t>(rank_scratch_words(g.nwords));
+        probe.take<double2>(3 * (size_t)n_materials);
+        probe.take<float2>(3 * (size_t)n_materials);
+        probe.take<double2>(nspec);
+        probe.take<float2>(nspec);
+        probe.take<double2>(kMaxLine);
+        probe.take<float2>(kMaxLine);
+        probe.take<double2>(nwork);
+        probe.take<double2>(xsec_scratch_elems());
+        probe.take<int>(4);
+        a0.cap = probe.used + 256;
+    }
+    cudaError_t e = cudaMalloc(&c->arena0, a0.cap);
+    if (e != cudaSuccess) { dda_free(c); return cuda_fail(e, "dda_init_lattice: allocation"); }
+    a0.base = static_cast<char*>(c->arena0);
+    c->occ = a0.take<uint32_t>(g.nwords);
+    c->rank = a0.take<uint32_t>(g.nwords);
+    c->comp = ncw ? a0.take<uint32_t>(ncw) : nullptr;
+    uint32_t* rscratch = a0.take<uint32_t>(rank_scratch_words(g.nwords));
+    c->ainv64 = a0.take<double2>(3 * (size_t)n_materials);
+    c->ainv32 = a0.take<float2>(3 * (size_t)n_materials);
+    c->spec64 = a0.take<double2>(nspec);
+    c->spec32 = a0.take<float2>(nspec);
+    c->tw64 = a0.take<double2>(kMaxLine);
+    c->tw32 = a0.take<float2>(kMaxLine);
+    c->work = a0.take<double2>(nwork);
+    c->xsec = a0.take<double2>(xsec_scratch_elems());
+    int* flags = a0.take<int>(4);
+    c->bytes = (int64_t)a0.cap;
+    int rc = 0;
+    auto bail = [&](int code) { dda_free(c); return code; };
+    // ---- target bit fields
+    if (cudaMemcpyAsync(c->occ, occupancy_bits, g.nwords * 4, cudaMemcpyDefault, st) != cudaSuccess)
+        return bail(fail(DDA_ERR_ARG, "dda_init_lattice: cannot read occupancy bits"));
+    k_clear_tail<<<1, 1, 0, st>>>(c->occ, g.nwords, g.nsites);
+    if (ncw) {
+        if (cudaMemcpyAsync(c->comp, composition_bits, ncw * 4, cudaMemcpyDefault, st) != cudaSuccess)
+            return bail(fail(DDA_ERR_ARG, "dda_init_lattice: cannot read composition bits"));
+    }
+    if (cudaMemsetAsync(flags, 0, 4 * sizeof(int), st) != cudaSuccess) return bail(fail(DDA_ERR_CUDA, "memset"));
+    if (ncw && (rc = launch_check_composition(c->comp, g.nsites, n_materials, flags, st))) return bail(rc);
+    uint32_t* total = reinterpret_cast<uint32_t*>(flags + 1);
+    if ((rc = launch_ranks(c->occ, g.nwords, c->rank, rscratch, total, st))) return bail(rc);
+    int hflags[2] = {0, 0};
+    if (cudaMemcpyAsync(hflags, flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return bail(fail(DDA_ERR_CUDA, "dda_init_lattice: rank scan failed"));
+    if (hflags[0]) return bail(fail(DDA_ERR_ARG, "dda_init_lattice: material index >= n_materials"));
+    g.nd = (int64_t)(uint32_t)hflags[1];
+    if (g.nd == 0) return bail(fail(DDA_ERR_ARG, "dda_init_lattice: no occupied site"));
+    // ---- alpha^-1 and twiddle tables (host FP64, a few hundred numbers)
+    {
+        std::vector<double2> ai(3 * n_materials);
+        std::vector<float2> af(3 * n_materials);
+        for (int i = 0; i < 3 * n_materials; ++i) {
+            const std::complex<double> inv = 1.0 / std::complex<double>(alpha[2 * i], alpha[2 * i + 1]);
+            ai[i] = make_double2(inv.real(), inv.imag());
+            af[i] = make_float2((float)inv.real(), (float)inv.imag());
+        }
+        std::vector<double2> t64(kMaxLine);
+        std::vector<float2> t32(kMaxLine);
+        for (int m = 0; m < kMaxLine; ++m) {
+            const double ang = -2.0 * M_PI * (double)m / kMaxLine;
+            t64[m] = make_double2(std::cos(ang), std::sin(ang));
+            t32[m] = make_float2((float)t64[m].x, (float)t64[m].y);
+        }
+        if (cudaMemcpyAsync(c->ainv64, ai.data(), ai.size() * sizeof(double2), cudaMemcpyHostToDevice, st) ||
+            cudaMemcpyAsync(c->ainv32, af.data(), af.size() * sizeof(float2), cudaMemcpyHostToDevice, st) ||
+            cudaMemcpyAsync(c->tw64, t64.data(), kMaxLine * sizeof(double2), cudaMemcpyHostToDevice, st) ||
+            cudaMemcpyAsync(c->tw32, t32.data(), kMaxLine * sizeof(float2), cudaMemcpyHostToDevice, st) ||
+            cudaStreamSynchronize(st))
+            return bail(fail(DDA_ERR_CUDA, "dda_init_lattice: table upload"));
+    }
+    // ---- Green's-tensor spectrum (temporary build buffers)
+    {
+        const size_t ns = spectrum_scratch_elems(g);
+        void* tmp = nullptr;
+        e = cudaMalloc(&tmp, 2 * ns * sizeof(double2));
+        if (e != cudaSuccess) return bail(cuda_fail(e, "dda_init_lattice: spectrum scratch"));
+        double2* s0 = static_cast<double2*>(tmp);
+        rc = build_spectrum(g, k, c->tw64, s0, s0 + ns, c->spec64, c->spec32, st);
+        cudaError_t e2 = cudaStreamSynchronize(st);
+        cudaFree(tmp);
+        if (rc) return bail(rc);
+        if (e2 != cudaSuccess) return bail(cuda_fail(e2, "dda_init_lattice: spectrum build"));
+    }
+    // ---- solver workspace: 13 complex128 + 12 complex64 vectors of 3 N_d
+    {
+        const size_t n = 3 * (size_t)g.nd;
+        Arena probe;
+        for (int i = 0; i < 13; ++i) probe.take<double2>(n);
+        for (int i = 0; i < 12; ++i) probe.take<float2>(n);
+        probe.take<double2>(kVecBlocks * kMaxRed);
+        probe.take<double2>(kVecBlocks * kMaxRed);
+        probe.take<KState>(2);
+        Arena a1;
+        a1.cap = probe.used + 256;
+        e = cudaMalloc(&c->arena1, a1.cap);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "dda_init_lattice: solver workspace"));
+        a1.base = static_cast<char*>(c->arena1);
+        c->x64 = a1.take<double2>(n);
+        c->b64 = a1.take<double2>(n);
+        c->r64 = a1.take<double2>(n);
+        c->w64.n = (int64_t)n;
+        for (int i = 0; i < 10; ++i) c->w64.v[i] = a1.take<double2>(n);
+        c->b32 = a1.take<float2>(n);
+        c->d32 = a1.take<float2>(n);
+        c->w32.n = (int64_t)n;
+        for (int i = 0; i < 10; ++i) c->w32.v[i] = a1.take<float2>(n);
+        c->w64.part = a1.take<double2>(kVecBlocks * kMaxRed);
+        c->w32.part = a1.take<double2>(kVecBlocks * kMaxRed);
+        KState* ks = a1.take<KState>(2);
+        c->w64.st = ks;
+        c->w32.st = ks + 1;
+        c->bytes += (int64_t)a1.cap;
+        e = cudaMallocHost(&c->host_state, 2 * sizeof(KState));
+        if (e != cudaSuccess) return bail(cuda_fail(e, "dda_init_lattice: pinned state"));
+        std::memset(c->host_state, 0, 2 * sizeof(KState));
+    }
+    // ---- matvec views
+    {
+        const TargetView tv = target_view(c);
+        MatvecView<double>& m = c->mv64;
+        m.g = g; m.tv = tv; m.ainv = c->ainv64; m.spec = c->spec64; m.tw = c->tw64;
+        m.Ay = static_cast<double2*>(c->work);
+        m.Bxy = m.Ay + 3ull * g.P * g.Ly * g.K;
+        m.status = nullptr; m.conj = 0;
+        configure_matvec<double>(m);
+        MatvecView<float>& f = c->mv32;
+        f.g = g; f.tv = tv; f.ainv = c->ainv32; f.spec = c->spec32; f.tw = c->tw32;
+        f.Ay = reinterpret_cast<float2*>(c->work);
+        f.Bxy = f.Ay + 3ull * g.P * g.Ly * g.K;
+        f.status = nullptr; f.conj = 0;
+        configure_matvec<float>(f);
+    }
+    *out = c;
+    return DDA_OK;
+}
+
+int dda_query(const dda_ctx* c, int64_t* n_dipoles, int32_t padded[3], int64_t* device_bytes) {
+    if (int rc = check_ctx(c)) return rc;
+    if (n_dipoles) *n_dipoles = c->g.nd;
+    if (padded) { padded[0] = c->g.Lx; padded[1] = c->g.Ly; padded[2] = c->g.Lz; }
+    if (device_bytes) *device_bytes = c->bytes;
+    return DDA_OK;
+}
+
+int dda_site_ranks(const dda_ctx* c, uint32_t* rank, void* stream) {
+    if (int rc = check_ctx(c)) return rc;
+    if (!rank || !is_device_ptr(rank)) return fail(DDA_ERR_ARG, "dda_site_ranks: rank must be a device pointer");
+    return launch_site_ranks(target_view(c), c->g.nsites, rank, as_stream(stream));
+}
+
+int dda_tensor_spectrum(const dda_ctx* c, void* out, int dtype, void* stream) {
+    if (int rc = check_ctx(c)) return rc;
+    if (int rc = check_dev(out, "dda_tensor_spectrum: out")) return rc;
+    const size_t ns = 6ull * c->g.Hz * c->g.Hy * c->g.Hx;
+    if (dtype == DDA_C128) {
+        DDA_CUDA_TRY(cudaMemcpyAsync(out, c->spec64, ns * sizeof(double2), cudaMemcpyDeviceToDevice, as_stream(stream)));
+    } else if (dtype == DDA_C64) {
+        DDA_CUDA_TRY(cudaMemcpyAsync(out, c->spec32, ns * sizeof(float2), cudaMemcpyDeviceToDevice, as_stream(stream)));
+    } else {
+        return fail(DDA_ERR_ARG, "dda_tensor_spectrum: unknown dtype");
+    }
+    return DDA_OK;
+}
+
+int dda_matvec(dda_ctx* c, const void* p, void* y, int dtype, void* stream) {
+    if (int rc = check_ctx(c)) return rc;
+    if (int rc = check_dev(p, "dda_matvec: p")) return rc;
+    if (int rc = check_dev(y, "dda_matvec: y")) return rc;
+    if (p == y) return fail(DDA_ERR_ARG, "dda_matvec: p and y must not overlap");
+    cudaStream_t st = as_stream(stream);
+    if (dtype == DDA_C128) {
+        MatvecView<double> m = c->mv64;
+        return launch_matvec<double>(m, static_cast<const double2*>(p), static_cast<double2*>(y), st);
+    } else if (dtype == DDA_C64) {
+        MatvecView<float> m = c->mv32;
+        return launch_matvec<float>(m, static_cast<const float2*>(p), static_cast<float2*>(y), st);
+    }
+    return fail(DDA_ERR_ARG, "dda_matvec: unknown dtype");
+}
+
+int dda_incident_field(dda_ctx* c, const double* khat, const double* e0, void* einc, void* stream) {
+    if (int rc = check_ctx(c)) return rc;
+    if (!khat || !e0) return fail(DDA_ERR_ARG, "dda_incident_field: NULL khat or e0");
+    if (int rc = check_dev(einc, "dda_incident_field: einc")) return rc;
+    for (int i = 0; i < 3; ++i)
+        if (!std::isfinite(khat[i])) return fail(DDA_ERR_NAN, "dda_incident_field: non-finite khat");
+    return launch_incident(target_view(c), c->g, c->k, khat, e0, static_cast<double2*>(einc), as_stream(stream));
+}
+
+static int map_status(int s) {
+    switch (s) {
+        case ST_CONVERGED: return DDA_OK;
+        case ST_BREAKDOWN: return DDA_ERR_BREAKDOWN;
+        case ST_NAN: return DDA_ERR_NAN;
+        default: return DDA_ERR_NOT_CONVERGED;
+    }
+}
+
+int dda_solve(dda_ctx* c, const void* einc, void* p, int method, int precision, double tol, int max_iter,
+              int use_x0, dda_solve_info* info, void* stream) {
+    const auto t0 = std::chrono::steady_clock::now();
+    if (int rc = check_ctx(c)) return rc;
+    if (!einc || !p) return fail(DDA_ERR_ARG, "dda_solve: NULL einc or p");
+    if (method < DDA_BICG || method > DDA_QMR) return fail(DDA_ERR_ARG, "dda_solve: unknown method");
+    if (precision != DDA_FP64 && precision != DDA_MIXED) return fail(DDA_ERR_ARG, "dda_solve: unknown precision");
+    if (!(tol > 0.0) || !std::isfinite(tol)) return fail(DDA_ERR_ARG, "dda_solve: tol must be finite and > 0");
+    if (max_iter < 1) return fail(DDA_ERR_ARG, "dda_solve: max_iter must be >= 1");
+    cudaStream_t st = as_stream(stream);
+    const int64_t n = 3 * c->g.nd;
+    const size_t bytes = n * sizeof(double2);
+    DDA_CUDA_TRY(cudaMemcpyAsync(c->b64, einc, bytes, cudaMemcpyDefault, st));
+    if (use_x0) DDA_CUDA_TRY(cudaMemcpyAsync(c->x64, p, bytes, cudaMemcpyDefault, st));
+    dda_solve_info inf{};
+    int status = DDA_OK;
+    KState* hs = c->host_state;
+    if (precision == DDA_FP64) {
+        SolveResult r{};
+        if (int rc = krylov_solve<double>(method, c->mv64, c->w64, c->b64, c->x64, use_x0 != 0, tol, max_iter, hs, st, &r))
+            return rc;
+        status = map_status(r.status);
+        inf.iterations = r.iterations;
+        inf.matvecs = r.matvecs;
+        inf.matvecs_fp64 = r.matvecs;
+        inf.rel_residual = std::sqrt(r.rel2);
+        // true residual with one FP64 product
+        MatvecView<double> m = c->mv64;
+        if (int rc = launch_matvec<double>(m, c->x64, c->r64, st)) return rc;
+        if (int rc = residual_from_product(c->b64, c->r64, n, c->w64.part, c->w64.st, st)) return rc;
+        double rn2 = 0.0, bn2 = 0.0;
+        if (int rc = vec_norm2_c128(c->r64, n, c->w64.part, c->w64.st, &rn2, hs, st)) return rc;
+        if (int rc = vec_norm2_c128(c->b64, n, c->w64.part, c->w64.st, &bn2, hs, st)) return rc;
+        inf.matvecs_fp64 += 1;
+        inf.rel_residual_true = bn2 > 0 ? std::sqrt(rn2 / bn2) : 0.0;
+    } else {
+        double bn2 = 0.0, rn2 = 0.0;
+        if (int rc = vec_norm2_c128(c->b64, n, c->w64.part, c->w64.st, &bn2, hs, st)) return rc;
+        if (use_x0) {
+            MatvecView<double> m = c->mv64;
+            if (int rc = launch_matvec<double>(m, c->x64, c->r64, st)) return rc;
+            if (int rc = residual_from_product(c->b64, c->r64, n, c->w64.part, c->w64.st, st)) return rc;
+            inf.matvecs_fp64 += 1;
+        } else {
+            DDA_CUDA_TRY(cudaMemsetAsync(c->x64, 0, bytes, st));
+            DDA_CUDA_TRY(cudaMemcpyAsync(c->r64, c->b64, bytes, cudaMemcpyDeviceToDevice, st));
+        }
+        if (int rc = vec_norm2_c128(c->r64, n, c->w64.part, c->w64.st, &rn2, hs, st)) return rc;
+        if (!std::isfinite(bn2) || !std::isfinite(rn2)) return fail(DDA_ERR_NAN, "dda_solve: non-finite input");
+        status = DDA_ERR_NOT_CONVERGED;
+        int stall = 0;
+        double best = rn2;
+        while (true) {
+            const double rel = bn2 > 0 ? std::sqrt(rn2 / bn2) : 0.0;
+            inf.rel_residual = rel;
+            inf.rel_residual_true = rel;
+            if (rel <= tol) { status = DDA_OK; break; }
+            if (inf.iterations >= max_iter) { status = DDA_ERR_NOT_CONVERGED; break; }
+            // inner target: enough to reach tol from here, but not below what FP32 sustains
+            const double inner_tol = std::min(0.5, std::max(0.3 * tol / rel, 1e-6));
+            const double rnorm = std::sqrt(rn2);
+            if (int rc = scale_to_c64(c->r64, 1.0 / rnorm, c->b32, n, st)) return rc;
+            SolveResult r{};
+            if (int rc = krylov_solve<float>(method, c->mv32, c->w32, c->b32, c->d32, false, inner_tol,
+                                             max_iter - inf.iterations, hs, st, &r))
+                return rc;
+            inf.iterations += r.iterations;
+            inf.matvecs += r.matvecs;
+            if (r.status == ST_NAN) { status = DDA_ERR_NAN; break; }
+            if (int rc = axpy_from_c64(c->x64, rnorm, c->d32, n, st)) return rc;
+            MatvecView<double> m = c->mv64;
+            if (int rc = launch_matvec<double>(m, c->x64, c->r64, st)) return rc;
+            if (int rc = residual_from_product(c->b64, c->r64, n, c->w64.part, c->w64.st, st)) return rc;
+            inf.matvecs_fp64 += 1;
+            inf.refinements += 1;
+            if (int rc = vec_norm2_c128(c->r64, n, c->w64.part, c->w64.st, &rn2, hs, st)) return rc;
+            if (!std::isfinite(rn2)) { status = DDA_ERR_NAN; break; }
+            if (rn2 < 0.25 * best) { best = rn2; stall = 0; }
+            else if (++stall >= 3) {
+                inf.rel_residual = inf.rel_residual_true = std::sqrt(rn2 / bn2);
+                status = r.status == ST_BREAKDOWN ? DDA_ERR_BREAKDOWN : DDA_ERR_NOT_CONVERGED;
+                break;
+            }
+            if (r.status == ST_BREAKDOWN && r.iterations == 0) { status = DDA_ERR_BREAKDOWN; break; }
+        }
+    }
+    DDA_CUDA_TRY(cudaMemcpyAsync(p, c->x64, bytes, cudaMemcpyDefault, st));
+    DDA_CUDA_TRY(cudaStreamSynchronize(st));
+    inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info) *info = inf;
+    if (status == DDA_ERR_NOT_CONVERGED) set_error("dda_solve: not converged within max_iter");
+    else if (status == DDA_ERR_BREAKDOWN) set_error("dda_solve: Krylov breakdown");
+    else if (status == DDA_ERR_NAN) set_error("dda_solve: non-finite value");
+    return status;
+}
+
+int dda_cross_sections(dda_ctx* c, const void* einc, const void* p, double* out, void* stream) {
+    if (int rc = check_ctx(c)) return rc;
+    if (!einc || !p || !out) return fail(DDA_ERR_ARG, "dda_cross_sections: NULL argument");
+    cudaStream_t st = as_stream(stream);
+    const size_t bytes = 3 * c->g.nd * sizeof(double2);
+    const double2* E = static_cast<const double2*>(einc);
+    const double2* P = static_cast<const double2*>(p);
+    if (!is_device_ptr(einc)) {
+        DDA_CUDA_TRY(cudaMemcpyAsync(c->w64.v[0], einc, bytes, cudaMemcpyHostToDevice, st));
+        E = c->w64.v[0];
+    }
+    if (!is_device_ptr(p)) {
+        DDA_CUDA_TRY(cudaMemcpyAsync(c->w64.v[1], p, bytes, cudaMemcpyHostToDevice, st));
+        P = c->w64.v[1];
+    }
+    if (int rc = launch_cross_sections(target_view(c), c->g, c->k, c->ainv64, E, P, c->xsec, st)) return rc;
+    double2 h;
+    DDA_CUDA_TRY(cudaMemcpyAsync(&h, c->xsec + xsec_scratch_elems() - 1, sizeof(double2), cudaMemcpyDeviceToHost, st));
+    DDA_CUDA_TRY(cudaStreamSynchronize(st));
+    const double f = 4.0 * M_PI * c->k;
+    out[0] = f * h.x;
+    out[1] = f * h.y;
+    out[2] = out[0] - out[1];
+    return DDA_OK;
+}
+
+}  // extern "C"

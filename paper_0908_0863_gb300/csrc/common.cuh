@@ -1,0 +1,100 @@
+// Shared device/host helpers of the DDA CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/dda.h"
+
+namespace dda {
+
+// ------------------------------------------------------------ complex types
+template <typename T> struct cpx;
+template <> struct cpx<double> { using t = double2; };
+template <> struct cpx<float> { using t = float2; };
+template <typename T> using C = typename cpx<T>::t;
+
+template <typename T> __host__ __device__ __forceinline__ C<T> mk(T re, T im) { C<T> z; z.x = re; z.y = im; return z; }
+template <typename T> __host__ __device__ __forceinline__ C<T> cadd(C<T> a, C<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
+template <typename T> __host__ __device__ __forceinline__ C<T> csub(C<T> a, C<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+template <typename T> __host__ __device__ __forceinline__ C<T> cmul(C<T> a, C<T> b) {
+    return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename T> __host__ __device__ __forceinline__ C<T> cmulc(C<T> a, C<T> b) {
+    return mk<T>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename T> __host__ __device__ __forceinline__ C<T> cscale(C<T> a, T s) { return mk<T>(a.x * s, a.y * s); }
+// acc += a * b
+template <typename T> __host__ __device__ __forceinline__ C<T> cfma(C<T> a, C<T> b, C<T> acc) {
+    return mk<T>(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
+}
+
+// --------------------------------------------------------------- limits
+constexpr int kMaxLine = 1024;      // longest padded line (lattice edge <= 512)
+constexpr int kMaxEdge = 512;
+
+// ------------------------------------------------------- error reporting
+void set_error(const std::string& msg);
+int fail(int status, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define DDA_CUDA_TRY(expr)                                         \
+    do {                                                           \
+        cudaError_t e__ = (expr);                                  \
+        if (e__ != cudaSuccess) return ::dda::cuda_fail(e__, #expr); \
+    } while (0)
+
+#define DDA_LAUNCH_CHECK(what)                                           \
+    do {                                                                 \
+        cudaError_t e__ = cudaGetLastError();                            \
+        if (e__ != cudaSuccess) return ::dda::cuda_fail(e__, what);      \
+    } while (0)
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// -------------------------------------------------------- lattice geometry
+struct Geometry {
+    int K, J, P;          // lattice edges (x, y, z)
+    int Lx, Ly, Lz;       // padded DFT lengths, powers of two >= 2n - 1
+    int Hx, Hy, Hz;       // stored half-spectrum extents L/2 + 1
+    int64_t nsites;       // K J P
+    int64_t nwords;       // occupancy words
+    int64_t nd;           // occupied sites
+    int nmat;             // materials
+    int cbits;            // composition bits per field
+    int cfields;          // fields per word
+};
+
+inline int padded_length(int n) {
+    int L = 2;
+    while (L < 2 * n - 1) L *= 2;
+    return L;
+}
+inline int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
+
+// device view of the target for the expand / compress kernels
+struct TargetView {
+    const uint32_t* occ;     // occupancy words
+    const uint32_t* rank;    // exclusive prefix count per word
+    const uint32_t* comp;    // composition words or nullptr
+    int cbits, cfields;
+};
+
+__device__ __forceinline__ bool occupied(const TargetView& t, int64_t s) {
+    return (__ldg(t.occ + (s >> 5)) >> (s & 31)) & 1u;
+}
+__device__ __forceinline__ uint32_t site_rank(const TargetView& t, int64_t s) {
+    const uint32_t w = __ldg(t.occ + (s >> 5));
+    return __ldg(t.rank + (s >> 5)) + __popc(w & ((1u << (s & 31)) - 1u));
+}
+__device__ __forceinline__ int material(const TargetView& t, int64_t s, int axis) {
+    if (t.comp == nullptr) return 0;
+    const int64_t q = 3 * s + axis;
+    const uint32_t w = __ldg(t.comp + q / t.cfields);
+    return (w >> ((q % t.cfields) * t.cbits)) & ((1u << t.cbits) - 1u);
+}
+
+}  // namespace dda

@@ -1,0 +1,725 @@
+// Device-resident unpreconditioned Krylov solvers (OpenDDA Sec. 4): BiCG,
+// BiCGSTAB and QMR with coupled two-term recurrences, in the textbook forms
+// of Barrett et al. (1994) written for complex vectors: Hermitian products
+// x^H y in BiCG and BiCGSTAB, bilinear x^T y in QMR's Lanczos process with
+// A^T = A (the DDA matrix is complex symmetric, Sec. 3); A^H v is formed as
+// conj(A conj(v)).  BiCG starts from the shadow residual conj(r0),
+// BiCGSTAB from r0.
+//
+// Every vector update is fused with the inner products that follow it;
+// each block writes its partial sums and a one-block "scalar" kernel adds
+// them in a fixed order (deterministic) and runs the scalar recurrence on
+// the device, so the host never waits inside an iteration.  A status word
+// in device memory stops all later kernels (and the matvec passes) once the
+// solve has converged or broken down.  Vector data may be complex64: the
+// products are then formed in FP32, summed in FP32 over at most eight
+// elements per thread and accumulated in FP64; all scalars are FP64.
+#include <cmath>
+#include <cstring>
+
+#include "krylov.cuh"
+
+namespace dda {
+
+namespace {
+
+// ------------------------------------------------------------- reductions
+template <typename T>
+struct DotAcc {  // FP64 accumulator fed by short FP32 (or FP64) partial sums
+    double2 hi;
+    C<T> lo;
+    int cnt;
+    __device__ __forceinline__ void init() { hi = make_double2(0.0, 0.0); lo = mk<T>(0, 0); cnt = 0; }
+    __device__ __forceinline__ void add(C<T> v) {
+        lo = cadd<T>(lo, v);
+        if (++cnt == 8) flush();
+    }
+    __device__ __forceinline__ void flush() {
+        hi.x += (double)lo.x;
+        hi.y += (double)lo.y;
+        lo = mk<T>(0, 0);
+        cnt = 0;
+    }
+};
+
+template <int NR>
+__device__ __forceinline__ void block_partials(double2 (&a)[NR], double2* __restrict__ part) {
+    __shared__ double2 sm[NR][kVecThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a[r].x += __shfl_down_sync(0xffffffffu, a[r].x, o);
+            a[r].y += __shfl_down_sync(0xffffffffu, a[r].y, o);
+        }
+        if (lane == 0) sm[r][wid] = a[r];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            double2 t = make_double2(0.0, 0.0);
+            for (int w = 0; w < kVecThreads / 32; ++w) { t.x += sm[r][w].x; t.y += sm[r][w].y; }
+            part[blockIdx.x * kMaxRed + r] = t;
+        }
+    }
+}
+
+// all threads of the one-block scalar kernel call this; every thread gets the sums
+template <int NR>
+__device__ __forceinline__ void final_sums(const double2* __restrict__ part, double2 (&out)[NR]) {
+    __shared__ double2 sm[NR][kVecThreads];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        double2 a = make_double2(0.0, 0.0);
+        for (int i = threadIdx.x; i < kVecBlocks; i += blockDim.x) {
+            a.x += part[i * kMaxRed + r].x;
+            a.y += part[i * kMaxRed + r].y;
+        }
+        sm[r][threadIdx.x] = a;
+    }
+    __syncthreads();
+    for (int o = kVecThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                sm[r][threadIdx.x].x += sm[r][threadIdx.x + o].x;
+                sm[r][threadIdx.x].y += sm[r][threadIdx.x + o].y;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) out[r] = sm[r][0];
+}
+
+__device__ __forceinline__ double2 dmul(double2 a, double2 b) { return cmul<double>(a, b); }
+__device__ __forceinline__ double2 ddiv(double2 a, double2 b) {
+    const double d = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+__device__ __forceinline__ bool is_zero(double2 a) { return a.x == 0.0 && a.y == 0.0; }
+__device__ __forceinline__ bool finite2(double2 a) { return isfinite(a.x) && isfinite(a.y); }
+
+template <typename T>
+__device__ __forceinline__ C<T> to_t(double2 a) { return mk<T>((T)a.x, (T)a.y); }
+template <typename T>
+__device__ __forceinline__ C<T> conjg(C<T> a) { return mk<T>(a.x, -a.y); }
+
+#define GRID_LOOP(i, n) \
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+// ---------------------------------------------------------------- common
+// r = b - r (r = A x on entry when has_x0), x = 0 otherwise r = b; rt = r or
+// conj(r).  partials: ||b||^2, ||r||^2, rt^H r
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_init(const C<T>* __restrict__ b, C<T>* __restrict__ x,
+                                                      C<T>* __restrict__ r, C<T>* __restrict__ rt, int64_t n,
+                                                      int has_x0, int conj_rt, double2* __restrict__ part) {
+    DotAcc<T> nb, nr, rr;
+    nb.init(); nr.init(); rr.init();
+    GRID_LOOP(i, n) {
+        const C<T> bi = b[i];
+        C<T> ri;
+        if (has_x0) {
+            ri = csub<T>(bi, r[i]);
+        } else {
+            ri = bi;
+            x[i] = mk<T>(0, 0);
+        }
+        r[i] = ri;
+        const C<T> ti = conj_rt ? conjg<T>(ri) : ri;
+        if (rt) rt[i] = ti;
+        nb.add(mk<T>(bi.x * bi.x + bi.y * bi.y, 0));
+        nr.add(mk<T>(ri.x * ri.x + ri.y * ri.y, 0));
+        rr.add(cmul<T>(conjg<T>(ti), ri));
+    }
+    nb.flush(); nr.flush(); rr.flush();
+    double2 a[3] = {nb.hi, nr.hi, rr.hi};
+    block_partials<3>(a, part);
+}
+
+__global__ void __launch_bounds__(kVecThreads) k_init_scalar(KState* st, const double2* __restrict__ part,
+                                                             double tol, int qmr) {
+    double2 s[3];
+    final_sums<3>(part, s);
+    if (threadIdx.x != 0) return;
+    st->status = ST_RUN;
+    st->iter = 0;
+    st->matvecs = 0;
+    st->bnorm2 = s[0].x;
+    st->tol2 = tol * tol;
+    for (int i = 0; i < S_NSLOTS; ++i) st->s[i] = make_double2(0.0, 0.0);
+    if (!isfinite(s[0].x) || !isfinite(s[1].x)) { st->status = ST_NAN; return; }
+    if (s[0].x == 0.0) { st->rel2 = 0.0; st->status = ST_CONVERGED; return; }
+    st->rel2 = s[1].x / s[0].x;
+    if (st->rel2 <= st->tol2) { st->status = ST_CONVERGED; return; }
+    st->s[S_RHO] = s[2];
+    if (qmr) {
+        st->s[S_RHOQ] = make_double2(sqrt(s[1].x), 0.0);
+        st->s[S_XI] = make_double2(sqrt(s[1].x), 0.0);
+        st->s[S_GAMMA_OLD] = make_double2(1.0, 0.0);
+        st->s[S_ETA] = make_double2(-1.0, 0.0);
+    }
+}
+
+// partial dot products: kind 0 = a^H b, kind 1 = a^T b
+template <typename T, int NR>
+__global__ void __launch_bounds__(kVecThreads) k_dots(const KState* st, const C<T>* __restrict__ a0,
+                                                      const C<T>* __restrict__ b0, int kind0,
+                                                      const C<T>* __restrict__ a1, const C<T>* __restrict__ b1,
+                                                      int kind1, int64_t n, double2* __restrict__ part) {
+    if (st->status != ST_RUN) return;
+    DotAcc<T> d0, d1;
+    d0.init(); d1.init();
+    GRID_LOOP(i, n) {
+        C<T> x0 = a0[i];
+        if (kind0 == 0) x0 = conjg<T>(x0);
+        d0.add(cmul<T>(x0, b0[i]));
+        if (NR > 1) {
+            C<T> x1 = a1[i];
+            if (kind1 == 0) x1 = conjg<T>(x1);
+            d1.add(cmul<T>(x1, b1[i]));
+        }
+    }
+    d0.flush(); d1.flush();
+    if (NR == 1) {
+        double2 a[1] = {d0.hi};
+        block_partials<1>(a, part);
+    } else {
+        double2 a[2] = {d0.hi, d1.hi};
+        block_partials<2>(a, part);
+    }
+}
+
+// ---------------------------------------------------------------- BiCGSTAB
+// p = r (first) or p = r + beta (p - omega v)
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_bcs_p(const KState* st, const C<T>* __restrict__ r,
+                                                       C<T>* __restrict__ p, const C<T>* __restrict__ v,
+                                                       int64_t n, int first) {
+    if (st->status != ST_RUN) return;
+    const C<T> beta = to_t<T>(st->s[S_BETA]), omega = to_t<T>(st->s[S_OMEGA]);
+    GRID_LOOP(i, n) {
+        p[i] = first ? r[i] : cfma<T>(beta, csub<T>(p[i], cmul<T>(omega, v[i])), r[i]);
+    }
+}
+
+// s = r - alpha v; partial ||s||^2
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_bcs_s(const KState* st, const C<T>* __restrict__ r,
+                                                       const C<T>* __restrict__ v, C<T>* __restrict__ s,
+                                                       int64_t n, double2* __restrict__ part) {
+    if (st->status != ST_RUN) return;
+    const C<T> alpha = to_t<T>(st->s[S_ALPHA]);
+    DotAcc<T> ns;
+    ns.init();
+    GRID_LOOP(i, n) {
+        const C<T> si = csub<T>(r[i], cmul<T>(alpha, v[i]));
+        s[i] = si;
+        ns.add(mk<T>(si.x * si.x + si.y * si.y, 0));
+    }
+    ns.flush();
+    double2 a[1] = {ns.hi};
+    block_partials<1>(a, part);
+}
+
+// x += alpha p + omega s; r = s - omega t; partials ||r||^2, rt^H r.
+// After a half-step convergence (status HALF) only x += alpha p.
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_bcs_xr(const KState* st, C<T>* __restrict__ x,
+                                                        const C<T>* __restrict__ p, const C<T>* __restrict__ s,
+                                                        const C<T>* __restrict__ t, C<T>* __restrict__ r,
+                                                        const C<T>* __restrict__ rt, int64_t n,
+                                                        double2* __restrict__ part) {
+    const int status = st->status;
+    if (status != ST_RUN && status != ST_HALF) return;
+    const C<T> alpha = to_t<T>(st->s[S_ALPHA]), omega = to_t<T>(st->s[S_OMEGA]);
+    if (status == ST_HALF) {
+        GRID_LOOP(i, n) x[i] = cfma<T>(alpha, p[i], x[i]);
+        return;
+    }
+    DotAcc<T> nr, rr;
+    nr.init(); rr.init();
+    GRID_LOOP(i, n) {
+        const C<T> si = s[i];
+        x[i] = cfma<T>(omega, si, cfma<T>(alpha, p[i], x[i]));
+        const C<T> ri = csub<T>(si, cmul<T>(omega, t[i]));
+        r[i] = ri;
+        nr.add(mk<T>(ri.x * ri.x + ri.y * ri.y, 0));
+        rr.add(cmul<T>(conjg<T>(rt[i]), ri));
+    }
+    nr.flush(); rr.flush();
+    double2 a[2] = {nr.hi, rr.hi};
+    block_partials<2>(a, part);
+}
+
+// step: 0 = alpha from sigma, 1 = half-step check, 2 = omega, 3 = end of iteration
+__global__ void __launch_bounds__(kVecThreads) k_bcs_scalar(KState* st, const double2* __restrict__ part, int step) {
+    if (step == 3 && st->status == ST_HALF) {
+        if (threadIdx.x == 0) { st->status = ST_CONVERGED; st->iter += 1; st->rel2 = st->s[S_TMP].x; }
+        return;
+    }
+    if (st->status != ST_RUN) return;
+    double2 s[2];
+    final_sums<2>(part, s);
+    if (threadIdx.x != 0) return;
+    if (step == 0) {
+        st->matvecs += 1;
+        const double2 sigma = s[0];
+        if (!finite2(sigma)) { st->status = ST_NAN; return; }
+        if (is_zero(sigma)) { st->status = ST_BREAKDOWN; return; }
+        st->s[S_ALPHA] = ddiv(st->s[S_RHO], sigma);
+    } else if (step == 1) {
+        const double rel2s = s[0].x / st->bnorm2;
+        st->s[S_TMP] = make_double2(rel2s, 0.0);
+        if (!isfinite(rel2s)) { st->status = ST_NAN; return; }
+        if (rel2s <= st->tol2) st->status = ST_HALF;
+    } else if (step == 2) {
+        st->matvecs += 1;
+        const double2 tt = s[0], ts = s[1];
+        if (!finite2(tt) || !finite2(ts)) { st->status = ST_NAN; return; }
+        if (tt.x == 0.0) { st->status = ST_BREAKDOWN; return; }
+        st->s[S_OMEGA] = make_double2(ts.x / tt.x, ts.y / tt.x);
+    } else {
+        st->iter += 1;
+        st->rel2 = s[0].x / st->bnorm2;
+        if (!isfinite(st->rel2)) { st->status = ST_NAN; return; }
+        if (st->rel2 <= st->tol2) { st->status = ST_CONVERGED; return; }
+        const double2 rho_new = s[1];
+        if (is_zero(st->s[S_OMEGA]) || is_zero(rho_new)) { st->status = ST_BREAKDOWN; return; }
+        st->s[S_BETA] = dmul(ddiv(rho_new, st->s[S_RHO]), ddiv(st->s[S_ALPHA], st->s[S_OMEGA]));
+        st->s[S_RHO] = rho_new;
+    }
+}
+
+// -------------------------------------------------------------------- BiCG
+// p = r + beta p, pt = rt + conj(beta) pt (copies on the first step)
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_bicg_p(const KState* st, const C<T>* __restrict__ r,
+                                                        const C<T>* __restrict__ rt, C<T>* __restrict__ p,
+                                                        C<T>* __restrict__ pt, int64_t n, int first) {
+    if (st->status != ST_RUN) return;
+    const C<T> beta = to_t<T>(st->s[S_BETA]);
+    const C<T> cbeta = conjg<T>(beta);
+    GRID_LOOP(i, n) {
+        if (first) {
+            p[i] = r[i];
+            pt[i] = rt[i];
+        } else {
+            p[i] = cfma<T>(beta, p[i], r[i]);
+            pt[i] = cfma<T>(cbeta, pt[i], rt[i]);
+        }
+    }
+}
+
+// x += alpha p; r -= alpha q; rt -= conj(alpha) qt; partials ||r||^2, rt^H r
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_bicg_update(const KState* st, C<T>* __restrict__ x,
+                                                             const C<T>* __restrict__ p, const C<T>* __restrict__ q,
+                                                             const C<T>* __restrict__ qt, C<T>* __restrict__ r,
+                                                             C<T>* __restrict__ rt, int64_t n,
+                                                             double2* __restrict__ part) {
+    if (st->status != ST_RUN) return;
+    const C<T> alpha = to_t<T>(st->s[S_ALPHA]);
+    const C<T> nalpha = mk<T>(-alpha.x, -alpha.y), ncalpha = mk<T>(-alpha.x, alpha.y);
+    DotAcc<T> nr, rr;
+    nr.init(); rr.init();
+    GRID_LOOP(i, n) {
+        x[i] = cfma<T>(alpha, p[i], x[i]);
+        const C<T> ri = cfma<T>(nalpha, q[i], r[i]);
+        const C<T> ti = cfma<T>(ncalpha, qt[i], rt[i]);
+        r[i] = ri;
+        rt[i] = ti;
+        nr.add(mk<T>(ri.x * ri.x + ri.y * ri.y, 0));
+        rr.add(cmul<T>(conjg<T>(ti), ri));
+    }
+    nr.flush(); rr.flush();
+    double2 a[2] = {nr.hi, rr.hi};
+    block_partials<2>(a, part);
+}
+
+// step 0: alpha = rho / (pt^H q); step 1: end of iteration
+__global__ void __launch_bounds__(kVecThreads) k_bicg_scalar(KState* st, const double2* __restrict__ part, int step) {
+    if (st->status != ST_RUN) return;
+    double2 s[2];
+    final_sums<2>(part, s);
+    if (threadIdx.x != 0) return;
+    if (step == 0) {
+        st->matvecs += 2;
+        const double2 sigma = s[0];
+        if (!finite2(sigma)) { st->status = ST_NAN; return; }
+        if (is_zero(sigma)) { st->status = ST_BREAKDOWN; return; }
+        st->s[S_ALPHA] = ddiv(st->s[S_RHO], sigma);
+    } else {
+        st->iter += 1;
+        st->rel2 = s[0].x / st->bnorm2;
+        if (!isfinite(st->rel2)) { st->status = ST_NAN; return; }
+        if (st->rel2 <= st->tol2) { st->status = ST_CONVERGED; return; }
+        const double2 rho_new = s[1];
+        if (is_zero(rho_new)) { st->status = ST_BREAKDOWN; return; }
+        st->s[S_BETA] = ddiv(rho_new, st->s[S_RHO]);
+        st->s[S_RHO] = rho_new;
+    }
+}
+
+// --------------------------------------------------------------------- QMR
+// v = vt / rho, w = wt / xi; partial w^T v
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_qmr_vw(const KState* st, const C<T>* __restrict__ vt,
+                                                        const C<T>* __restrict__ wt, C<T>* __restrict__ v,
+                                                        C<T>* __restrict__ w, int64_t n, double2* __restrict__ part) {
+    if (st->status != ST_RUN) return;
+    const T irho = (T)(1.0 / st->s[S_RHOQ].x), ixi = (T)(1.0 / st->s[S_XI].x);
+    DotAcc<T> d;
+    d.init();
+    GRID_LOOP(i, n) {
+        const C<T> vi = cscale<T>(vt[i], irho), wi = cscale<T>(wt[i], ixi);
+        v[i] = vi;
+        w[i] = wi;
+        d.add(cmul<T>(wi, vi));
+    }
+    d.flush();
+    double2 a[1] = {d.hi};
+    block_partials<1>(a, part);
+}
+
+// p = v - cp p, q = w - cq q (copies on the first step)
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_qmr_pq(const KState* st, const C<T>* __restrict__ v,
+                                                        const C<T>* __restrict__ w, C<T>* __restrict__ p,
+                                                        C<T>* __restrict__ q, int64_t n, int first) {
+    if (st->status != ST_RUN) return;
+    // cp = xi delta / eps, cq = rho delta / eps (stored negated in BETA/OMEGA slots? no: S_TMP pair)
+    const C<T> ncp = to_t<T>(st->s[S_SIGMA]), ncq = to_t<T>(st->s[S_OMEGA]);
+    GRID_LOOP(i, n) {
+        if (first) {
+            p[i] = v[i];
+            q[i] = w[i];
+        } else {
+            p[i] = cfma<T>(ncp, p[i], v[i]);
+            q[i] = cfma<T>(ncq, q[i], w[i]);
+        }
+    }
+}
+
+// vt = pt - beta v; wt = (A q) - beta w; partials ||vt||^2, ||wt||^2
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_qmr_vtwt(const KState* st, const C<T>* __restrict__ pt,
+                                                          const C<T>* __restrict__ v, const C<T>* __restrict__ w,
+                                                          C<T>* __restrict__ vt, C<T>* __restrict__ wt, int64_t n,
+                                                          double2* __restrict__ part) {
+    if (st->status != ST_RUN) return;
+    const C<T> beta = to_t<T>(st->s[S_BETA]);
+    const C<T> nbeta = mk<T>(-beta.x, -beta.y);
+    DotAcc<T> a, b;
+    a.init(); b.init();
+    GRID_LOOP(i, n) {
+        const C<T> vi = cfma<T>(nbeta, v[i], pt[i]);
+        const C<T> wi = cfma<T>(nbeta, w[i], wt[i]);
+        vt[i] = vi;
+        wt[i] = wi;
+        a.add(mk<T>(vi.x * vi.x + vi.y * vi.y, 0));
+        b.add(mk<T>(wi.x * wi.x + wi.y * wi.y, 0));
+    }
+    a.flush(); b.flush();
+    double2 s[2] = {a.hi, b.hi};
+    block_partials<2>(s, part);
+}
+
+// d = eta p + f d; s = eta pt + f s; x += d; r -= s; partial ||r||^2
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_qmr_ds(const KState* st, const C<T>* __restrict__ p,
+                                                        const C<T>* __restrict__ pt, C<T>* __restrict__ d,
+                                                        C<T>* __restrict__ s, C<T>* __restrict__ x,
+                                                        C<T>* __restrict__ r, int64_t n, int first,
+                                                        double2* __restrict__ part) {
+    if (st->status != ST_RUN) return;
+    const C<T> eta = to_t<T>(st->s[S_ETA]);
+    const T f = (T)st->s[S_F].x;
+    DotAcc<T> nr;
+    nr.init();
+    GRID_LOOP(i, n) {
+        C<T> di = cmul<T>(eta, p[i]), si = cmul<T>(eta, pt[i]);
+        if (!first) {
+            di = cadd<T>(di, cscale<T>(d[i], f));
+            si = cadd<T>(si, cscale<T>(s[i], f));
+        }
+        d[i] = di;
+        s[i] = si;
+        x[i] = cadd<T>(x[i], di);
+        const C<T> ri = csub<T>(r[i], si);
+        r[i] = ri;
+        nr.add(mk<T>(ri.x * ri.x + ri.y * ri.y, 0));
+    }
+    nr.flush();
+    double2 a[1] = {nr.hi};
+    block_partials<1>(a, part);
+}
+
+// step 0: delta (+ p/q coefficients); 1: eps, beta; 2: rho, xi, theta,
+// gamma, eta, f; 3: end of iteration
+__global__ void __launch_bounds__(kVecThreads) k_qmr_scalar(KState* st, const double2* __restrict__ part, int step,
+                                                            int first) {
+    if (st->status != ST_RUN) return;
+    double2 s[2];
+    final_sums<2>(part, s);
+    if (threadIdx.x != 0) return;
+    if (step == 0) {
+        const double rho = st->s[S_RHOQ].x, xi = st->s[S_XI].x;
+        if (rho == 0.0 || xi == 0.0) { st->status = ST_BREAKDOWN; return; }
+        const double2 delta = s[0];
+        if (!finite2(delta)) { st->status = ST_NAN; return; }
+        if (is_zero(delta)) { st->status = ST_BREAKDOWN; return; }
+        st->s[S_DELTA] = delta;
+        if (!first) {
+            const double2 q = ddiv(delta, st->s[S_EPS]);
+            st->s[S_SIGMA] = make_double2(-xi * q.x, -xi * q.y);    // -(xi delta / eps)
+            st->s[S_OMEGA] = make_double2(-rho * q.x, -rho * q.y);  // -(rho delta / eps)
+        }
+    } else if (step == 1) {
+        st->matvecs += 1;
+        const double2 eps = s[0];
+        if (!finite2(eps)) { st->status = ST_NAN; return; }
+        if (is_zero(eps)) { st->status = ST_BREAKDOWN; return; }
+        st->s[S_EPS] = eps;
+        const double2 beta = ddiv(eps, st->s[S_DELTA]);
+        if (is_zero(beta)) { st->status = ST_BREAKDOWN; return; }
+        st->s[S_BETA] = beta;
+    } else if (step == 2) {
+        st->matvecs += 1;
+        const double rho_new = sqrt(s[0].x), xi_new = sqrt(s[1].x);
+        const double2 beta = st->s[S_BETA];
+        const double gamma_old = st->s[S_GAMMA_OLD].x;
+        const double theta = rho_new / (gamma_old * hypot(beta.x, beta.y));
+        const double gamma = 1.0 / sqrt(1.0 + theta * theta);
+        if (gamma == 0.0 || !isfinite(theta)) { st->status = ST_BREAKDOWN; return; }
+        // eta = -eta rho gamma^2 / (beta gamma_old^2)
+        const double sc = -st->s[S_RHOQ].x * gamma * gamma / (gamma_old * gamma_old);
+        const double2 e = ddiv(st->s[S_ETA], beta);
+        st->s[S_ETA] = make_double2(sc * e.x, sc * e.y);
+        const double tg = st->s[S_THETA_OLD].x * gamma;
+        st->s[S_F] = make_double2(tg * tg, 0.0);
+        st->s[S_RHO_NEW] = make_double2(rho_new, 0.0);
+        st->s[S_XI_NEW] = make_double2(xi_new, 0.0);
+        st->s[S_TMP] = make_double2(theta, gamma);
+    } else {
+        st->iter += 1;
+        st->rel2 = s[0].x / st->bnorm2;
+        if (!isfinite(st->rel2)) { st->status = ST_NAN; return; }
+        if (st->rel2 <= st->tol2) { st->status = ST_CONVERGED; return; }
+        st->s[S_RHOQ] = st->s[S_RHO_NEW];
+        st->s[S_XI] = st->s[S_XI_NEW];
+        st->s[S_THETA_OLD] = make_double2(st->s[S_TMP].x, 0.0);
+        st->s[S_GAMMA_OLD] = make_double2(st->s[S_TMP].y, 0.0);
+    }
+}
+
+// ------------------------------------------------------ refinement helpers
+__global__ void __launch_bounds__(kVecThreads) k_norm2_c128(const double2* __restrict__ a, int64_t n,
+                                                            double2* __restrict__ part) {
+    DotAcc<double> d;
+    d.init();
+    GRID_LOOP(i, n) d.add(make_double2(a[i].x * a[i].x + a[i].y * a[i].y, 0.0));
+    d.flush();
+    double2 s[1] = {d.hi};
+    block_partials<1>(s, part);
+}
+
+__global__ void __launch_bounds__(kVecThreads) k_resid(const double2* __restrict__ b, double2* __restrict__ r,
+                                                       int64_t n, double2* __restrict__ part) {
+    DotAcc<double> d;
+    d.init();
+    GRID_LOOP(i, n) {
+        const double2 ri = make_double2(b[i].x - r[i].x, b[i].y - r[i].y);
+        r[i] = ri;
+        d.add(make_double2(ri.x * ri.x + ri.y * ri.y, 0.0));
+    }
+    d.flush();
+    double2 s[1] = {d.hi};
+    block_partials<1>(s, part);
+}
+
+__global__ void __launch_bounds__(kVecThreads) k_slot(KState* st, const double2* __restrict__ part, int slot) {
+    double2 s[1];
+    final_sums<1>(part, s);
+    if (threadIdx.x == 0) st->s[slot] = s[0];
+}
+
+__global__ void k_to_c64(const double2* __restrict__ r, double scale, float2* __restrict__ out, int64_t n) {
+    GRID_LOOP(i, n) out[i] = make_float2((float)(r[i].x * scale), (float)(r[i].y * scale));
+}
+
+__global__ void k_axpy_c64(double2* __restrict__ x, double scale, const float2* __restrict__ d, int64_t n) {
+    GRID_LOOP(i, n) {
+        x[i].x += scale * (double)d[i].x;
+        x[i].y += scale * (double)d[i].y;
+    }
+}
+
+__global__ void k_copy(double2* __restrict__ dst, const double2* __restrict__ src, int64_t n) {
+    GRID_LOOP(i, n) dst[i] = src[i];
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- host loops
+template <typename T>
+static int run_matvec(MatvecView<T> mv, const C<T>* p, C<T>* y, int conj, cudaStream_t st) {
+    mv.conj = conj;
+    return launch_matvec<T>(mv, p, y, st);
+}
+
+template <typename T>
+int krylov_solve(int method, MatvecView<T> mv, KrylovWork<T>& ws, const C<T>* b, C<T>* x, bool use_x0,
+                 double tol, int max_iter, KState* hs, cudaStream_t st, SolveResult* res) {
+    const int64_t n = ws.n;
+    const dim3 G(kVecBlocks), B(kVecThreads);
+    double2* part = ws.part;
+    KState* ds = ws.st;
+    mv.status = &ds->status;
+    C<T>** v = ws.v;
+    int rc;
+    // ---- initial residual (status is not yet valid: use a status-free matvec)
+    C<T>* r = v[0];
+    if (use_x0) {
+        MatvecView<T> m0 = mv;
+        m0.status = nullptr;
+        if ((rc = run_matvec<T>(m0, x, r, 0, st))) return rc;
+    }
+    C<T>* rt = (method == DDA_QMR) ? v[1] : v[1];
+    k_init<T><<<G, B, 0, st>>>(b, x, r, rt, n, use_x0 ? 1 : 0, method == DDA_BICG ? 1 : 0, part);
+    DDA_LAUNCH_CHECK("krylov init");
+    k_init_scalar<<<1, B, 0, st>>>(ds, part, tol, method == DDA_QMR ? 1 : 0);
+    DDA_LAUNCH_CHECK("krylov init scalar");
+    if (method == DDA_QMR) {  // vt = r (v[1]), wt = r (v[2])
+        DDA_CUDA_TRY(cudaMemcpyAsync(v[2], r, n * sizeof(C<T>), cudaMemcpyDeviceToDevice, st));
+    }
+    // ---- iterations, polling the status two iterations behind
+    cudaEvent_t ev[2];
+    DDA_CUDA_TRY(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+    DDA_CUDA_TRY(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+    volatile int* hstat = &hs[0].status;
+    KState* hslots = hs;  // hs[0], hs[1]: two pinned status copies
+    int it = 0;
+    bool done = false;
+    rc = 0;
+    while (it < max_iter && !done) {
+        ++it;
+        const int first = it == 1;
+        if (method == DDA_BICGSTAB) {
+            C<T>*p = v[2], *vv = v[3], *s = v[4], *t = v[5];
+            k_bcs_p<T><<<G, B, 0, st>>>(ds, r, p, vv, n, first);
+            if ((rc = run_matvec<T>(mv, p, vv, 0, st))) break;
+            k_dots<T, 1><<<G, B, 0, st>>>(ds, rt, vv, 0, nullptr, nullptr, 0, n, part);
+            k_bcs_scalar<<<1, B, 0, st>>>(ds, part, 0);
+            k_bcs_s<T><<<G, B, 0, st>>>(ds, r, vv, s, n, part);
+            k_bcs_scalar<<<1, B, 0, st>>>(ds, part, 1);
+            if ((rc = run_matvec<T>(mv, s, t, 0, st))) break;
+            k_dots<T, 2><<<G, B, 0, st>>>(ds, t, t, 0, t, s, 0, n, part);
+            k_bcs_scalar<<<1, B, 0, st>>>(ds, part, 2);
+            k_bcs_xr<T><<<G, B, 0, st>>>(ds, x, p, s, t, r, rt, n, part);
+            k_bcs_scalar<<<1, B, 0, st>>>(ds, part, 3);
+        } else if (method == DDA_BICG) {
+            C<T>*p = v[2], *pt = v[3], *q = v[4], *qt = v[5];
+            k_bicg_p<T><<<G, B, 0, st>>>(ds, r, rt, p, pt, n, first);
+            if ((rc = run_matvec<T>(mv, p, q, 0, st))) break;
+            if ((rc = run_matvec<T>(mv, pt, qt, 1, st))) break;
+            k_dots<T, 1><<<G, B, 0, st>>>(ds, pt, q, 0, nullptr, nullptr, 0, n, part);
+            k_bicg_scalar<<<1, B, 0, st>>>(ds, part, 0);
+            k_bicg_update<T><<<G, B, 0, st>>>(ds, x, p, q, qt, r, rt, n, part);
+            k_bicg_scalar<<<1, B, 0, st>>>(ds, part, 1);
+        } else {
+            C<T>*vt = v[1], *wt = v[2], *vv = v[3], *w = v[4], *p = v[5], *q = v[6], *pt = v[7], *d = v[8],
+                *s = v[9];
+            k_qmr_vw<T><<<G, B, 0, st>>>(ds, vt, wt, vv, w, n, part);
+            k_qmr_scalar<<<1, B, 0, st>>>(ds, part, 0, first);
+            k_qmr_pq<T><<<G, B, 0, st>>>(ds, vv, w, p, q, n, first);
+            if ((rc = run_matvec<T>(mv, p, pt, 0, st))) break;
+            k_dots<T, 1><<<G, B, 0, st>>>(ds, q, pt, 1, nullptr, nullptr, 0, n, part);
+            k_qmr_scalar<<<1, B, 0, st>>>(ds, part, 1, first);
+            if ((rc = run_matvec<T>(mv, q, wt, 0, st))) break;   // A^T q = A q
+            k_qmr_vtwt<T><<<G, B, 0, st>>>(ds, pt, vv, w, vt, wt, n, part);
+            k_qmr_scalar<<<1, B, 0, st>>>(ds, part, 2, first);
+            k_qmr_ds<T><<<G, B, 0, st>>>(ds, p, pt, d, s, x, r, n, first, part);
+            k_qmr_scalar<<<1, B, 0, st>>>(ds, part, 3, first);
+        }
+        {
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) { rc = cuda_fail(e, "krylov iteration"); break; }
+        }
+        // copy the status word of this iteration; check the one two behind
+        const int slot = it & 1;
+        if (it >= 3) {
+            cudaError_t e = cudaEventSynchronize(ev[slot]);
+            if (e != cudaSuccess) { rc = cuda_fail(e, "krylov poll"); break; }
+            if (hslots[slot].status != ST_RUN) done = true;
+        }
+        cudaMemcpyAsync(&hslots[slot].status, &ds->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+        cudaEventRecord(ev[slot], st);
+    }
+    (void)hstat;
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (rc) return rc;
+    DDA_CUDA_TRY(cudaMemcpyAsync(&hs[0], ds, sizeof(KState), cudaMemcpyDeviceToHost, st));
+    DDA_CUDA_TRY(cudaStreamSynchronize(st));
+    res->status = hs[0].status;
+    res->iterations = hs[0].iter;
+    res->matvecs = hs[0].matvecs + (use_x0 ? 1 : 0);
+    res->rel2 = hs[0].rel2;
+    return 0;
+}
+
+template int krylov_solve<double>(int, MatvecView<double>, KrylovWork<double>&, const C<double>*, C<double>*,
+                                  bool, double, int, KState*, cudaStream_t, SolveResult*);
+template int krylov_solve<float>(int, MatvecView<float>, KrylovWork<float>&, const C<float>*, C<float>*, bool,
+                                 double, int, KState*, cudaStream_t, SolveResult*);
+
+int vec_norm2_c128(const double2* a, int64_t n, double2* part, KState* st_dev, double* out_host, KState* hs,
+                   cudaStream_t st) {
+    k_norm2_c128<<<kVecBlocks, kVecThreads, 0, st>>>(a, n, part);
+    DDA_LAUNCH_CHECK("norm");
+    k_slot<<<1, kVecThreads, 0, st>>>(st_dev, part, S_TMP);
+    DDA_LAUNCH_CHECK("norm final");
+    DDA_CUDA_TRY(cudaMemcpyAsync(&hs->s[S_TMP], &st_dev->s[S_TMP], sizeof(double2), cudaMemcpyDeviceToHost, st));
+    DDA_CUDA_TRY(cudaStreamSynchronize(st));
+    *out_host = hs->s[S_TMP].x;
+    return 0;
+}
+
+int residual_from_product(const double2* b, double2* r, int64_t n, double2* part, KState* st_dev, cudaStream_t st) {
+    k_resid<<<kVecBlocks, kVecThreads, 0, st>>>(b, r, n, part);
+    DDA_LAUNCH_CHECK("residual");
+    k_slot<<<1, kVecThreads, 0, st>>>(st_dev, part, S_TMP);
+    DDA_LAUNCH_CHECK("residual final");
+    return 0;
+}
+
+int scale_to_c64(const double2* r, double scale, float2* out, int64_t n, cudaStream_t st) {
+    k_to_c64<<<kVecBlocks, kVecThreads, 0, st>>>(r, scale, out, n);
+    DDA_LAUNCH_CHECK("to c64");
+    return 0;
+}
+
+int axpy_from_c64(double2* x, double scale, const float2* d, int64_t n, cudaStream_t st) {
+    k_axpy_c64<<<kVecBlocks, kVecThreads, 0, st>>>(x, scale, d, n);
+    DDA_LAUNCH_CHECK("axpy c64");
+    return 0;
+}
+
+int vec_copy_c128(double2* dst, const double2* src, int64_t n, cudaStream_t st) {
+    k_copy<<<kVecBlocks, kVecThreads, 0, st>>>(dst, src, n);
+    DDA_LAUNCH_CHECK("copy");
+    return 0;
+}
+
+int reduce_into_slot(const double2* part, int nr, KState* st_dev, int slot, cudaStream_t st) {
+    (void)nr;
+    k_slot<<<1, kVecThreads, 0, st>>>(st_dev, part, slot);
+    DDA_LAUNCH_CHECK("slot");
+    return 0;
+}
+
+}  // namespace dda

@@ -1,0 +1,313 @@
+// Bit-fielded target description (OpenDDA Sec. 2) and the per-dipole
+// set-up and observables on it: occupancy / composition packing, the rank
+// (compressed index) of every site for the zero-storage vectors of Sec. 4,
+// the incident field and the cross-section sums.
+#include "target.cuh"
+
+namespace dda {
+
+namespace {
+
+// ------------------------------------------------------------- occupancy
+// one warp packs 32 consecutive sites into one word with a ballot: lane l
+// holds site 32 w + l, which becomes bit l (least significant first)
+__global__ void k_pack_occ(const uint8_t* __restrict__ mask, int64_t n, uint32_t* __restrict__ bits) {
+    const int64_t nwords = (n + 31) >> 5;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < (nwords << 5); s += stride) {
+        const bool on = s < n && mask[s] != 0;
+        const uint32_t word = __ballot_sync(0xffffffffu, on);
+        if ((threadIdx.x & 31) == 0) bits[s >> 5] = word;
+    }
+}
+
+__global__ void k_unpack_occ(const uint32_t* __restrict__ bits, int64_t n, uint8_t* __restrict__ mask) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += stride)
+        mask[s] = (bits[s >> 5] >> (s & 31)) & 1u;
+}
+
+// ----------------------------------------------------------- composition
+__global__ void k_pack_comp(const uint8_t* __restrict__ mats, int64_t nfields, int nmat, int b, int f,
+                            uint32_t* __restrict__ bits, int* __restrict__ bad) {
+    const int64_t nwords = (nfields + f - 1) / f;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t wd = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; wd < nwords; wd += stride) {
+        uint32_t word = 0;
+        for (int t = 0; t < f; ++t) {
+            const int64_t q = wd * f + t;
+            if (q >= nfields) break;
+            const uint32_t v = mats[q];
+            if (v >= (uint32_t)nmat) atomicExch(bad, 1);
+            word |= (v & ((1u << b) - 1u)) << (t * b);
+        }
+        bits[wd] = word;
+    }
+}
+
+__global__ void k_unpack_comp(const uint32_t* __restrict__ bits, int64_t nfields, int b, int f,
+                              uint8_t* __restrict__ mats) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nfields; q += stride)
+        mats[q] = (bits[q / f] >> ((q % f) * b)) & ((1u << b) - 1u);
+}
+
+// range check of a composition field array already packed
+__global__ void k_check_comp(const uint32_t* __restrict__ bits, int64_t nfields, int b, int f, int nmat,
+                             int* __restrict__ bad) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nfields; q += stride) {
+        const uint32_t v = (bits[q / f] >> ((q % f) * b)) & ((1u << b) - 1u);
+        if (v >= (uint32_t)nmat) atomicExch(bad, 1);
+    }
+}
+
+// ------------------------------------------------------------------ ranks
+// three-step exclusive scan of the per-word popcounts:
+//   1) each block scans kScanTile words, writing local prefixes and the block total
+//   2) one block scans the block totals
+//   3) add each block's offset
+constexpr int kScanThreads = 1024;
+constexpr int kScanPerThread = 4;
+constexpr int kScanTile = kScanThreads * kScanPerThread;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
+    __shared__ uint32_t warp_sums[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        uint32_t s = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) warp_sums[lane] = s;
+    }
+    __syncthreads();
+    const uint32_t before = (wid > 0 ? warp_sums[wid - 1] : 0) + x - v;
+    if (total) *total = warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_rank_local(const uint32_t* __restrict__ occ, int64_t nwords,
+                                                             uint32_t* __restrict__ rank, uint32_t* __restrict__ block_sum) {
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPerThread;
+    uint32_t c[kScanPerThread];
+    uint32_t mine = 0;
+#pragma unroll
+    for (int t = 0; t < kScanPerThread; ++t) {
+        c[t] = base + t < nwords ? __popc(occ[base + t]) : 0;
+        mine += c[t];
+    }
+    uint32_t tot;
+    uint32_t run = block_exclusive_scan(mine, &tot);
+#pragma unroll
+    for (int t = 0; t < kScanPerThread; ++t) {
+        if (base + t < nwords) rank[base + t] = run;
+        run += c[t];
+    }
+    if (threadIdx.x == 0) block_sum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_rank_blocks(uint32_t* __restrict__ block_sum, int64_t nblocks,
+                                                              uint32_t* __restrict__ total) {
+    uint32_t carry = 0;
+    for (int64_t b0 = 0; b0 < nblocks; b0 += kScanThreads) {
+        const int64_t b = b0 + threadIdx.x;
+        const uint32_t v = b < nblocks ? block_sum[b] : 0;
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan(v, &tot);
+        if (b < nblocks) block_sum[b] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_rank_add(uint32_t* __restrict__ rank, int64_t nwords, const uint32_t* __restrict__ block_off) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nwords; w += stride)
+        rank[w] += block_off[w / kScanTile];
+}
+
+__global__ void k_site_ranks(TargetView tv, int64_t n, uint32_t* __restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += stride) out[s] = site_rank(tv, s);
+}
+
+// --------------------------------------------------------- incident field
+__global__ void k_incident(TargetView tv, Geometry g, double kw, double kx, double ky, double kz, double2 e0,
+                           double2 e1, double2 e2, double2* __restrict__ E) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < g.nsites; s += stride) {
+        if (!occupied(tv, s)) continue;
+        const int i = (int)(s % g.K), j = (int)((s / g.K) % g.J), k = (int)(s / ((int64_t)g.K * g.J));
+        double sn, cs;
+        sincos(kw * (kx * i + ky * j + kz * k), &sn, &cs);
+        const double2 ph = make_double2(cs, sn);
+        const uint32_t r = site_rank(tv, s);
+        E[r] = cmul<double>(e0, ph);
+        E[g.nd + r] = cmul<double>(e1, ph);
+        E[2 * g.nd + r] = cmul<double>(e2, ph);
+    }
+}
+
+// --------------------------------------------------------- cross sections
+// per block partial sums of Im(E^* P) and [-Im(ainv) - 2/3 k^3] |P|^2 over
+// sites; the final sum over blocks runs in a fixed order on one block
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocks = 1024;
+
+__global__ void __launch_bounds__(kRedThreads) k_xsec_partial(TargetView tv, Geometry g, double k3,
+                                                              const double2* __restrict__ ainv,
+                                                              const double2* __restrict__ E,
+                                                              const double2* __restrict__ P,
+                                                              double2* __restrict__ part) {
+    double ext = 0.0, abs_ = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < g.nsites; s += stride) {
+        if (!occupied(tv, s)) continue;
+        const uint32_t r = site_rank(tv, s);
+        for (int c = 0; c < 3; ++c) {
+            const double2 e = E[c * g.nd + r], p = P[c * g.nd + r];
+            ext += e.x * p.y - e.y * p.x;                       // Im(conj(e) p)
+            const double2 a = ainv[material(tv, s, c) * 3 + c];
+            abs_ += (-a.y - (2.0 / 3.0) * k3) * (p.x * p.x + p.y * p.y);
+        }
+    }
+    __shared__ double se[kRedThreads], sa[kRedThreads];
+    se[threadIdx.x] = ext;
+    sa[threadIdx.x] = abs_;
+    __syncthreads();
+    for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            se[threadIdx.x] += se[threadIdx.x + o];
+            sa[threadIdx.x] += sa[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = make_double2(se[0], sa[0]);
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_xsec_final(const double2* __restrict__ part, int n, double2* out) {
+    __shared__ double se[kRedThreads], sa[kRedThreads];
+    double e = 0.0, a = 0.0;
+    for (int i = threadIdx.x; i < n; i += kRedThreads) {
+        e += part[i].x;
+        a += part[i].y;
+    }
+    se[threadIdx.x] = e;
+    sa[threadIdx.x] = a;
+    __syncthreads();
+    for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            se[threadIdx.x] += se[threadIdx.x + o];
+            sa[threadIdx.x] += sa[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = make_double2(se[0], sa[0]);
+}
+
+inline unsigned grid_for(int64_t n, int threads) {
+    const int64_t b = (n + threads - 1) / threads;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 32));
+}
+
+}  // namespace
+
+int launch_pack_occupancy(const uint8_t* mask, int64_t n, uint32_t* bits, cudaStream_t st) {
+    k_pack_occ<<<grid_for((n + 31) / 32 * 32, 256), 256, 0, st>>>(mask, n, bits);
+    DDA_LAUNCH_CHECK("pack occupancy");
+    return 0;
+}
+
+int launch_unpack_occupancy(const uint32_t* bits, int64_t n, uint8_t* mask, cudaStream_t st) {
+    k_unpack_occ<<<grid_for(n, 256), 256, 0, st>>>(bits, n, mask);
+    DDA_LAUNCH_CHECK("unpack occupancy");
+    return 0;
+}
+
+// out-of-range flag of dda_pack_composition: one word per device, shared by
+// all calls (calls that overlap on the GPU share it)
+__device__ int g_pack_bad;
+
+int launch_pack_composition(const uint8_t* mats, int64_t nsites, int nmat, uint32_t* bits, int* bad_host,
+                            cudaStream_t st) {
+    const int b = composition_bits(nmat), f = 32 / b;
+    const int64_t nf = 3 * nsites;
+    int* bad = nullptr;
+    DDA_CUDA_TRY(cudaGetSymbolAddress(reinterpret_cast<void**>(&bad), g_pack_bad));
+    DDA_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), st));
+    k_pack_comp<<<grid_for((nf + f - 1) / f, 256), 256, 0, st>>>(mats, nf, nmat, b, f, bits, bad);
+    DDA_LAUNCH_CHECK("pack composition");
+    DDA_CUDA_TRY(cudaMemcpyAsync(bad_host, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DDA_CUDA_TRY(cudaStreamSynchronize(st));
+    return 0;
+}
+
+int launch_unpack_composition(const uint32_t* bits, int64_t nsites, int nmat, uint8_t* mats, cudaStream_t st) {
+    const int b = composition_bits(nmat), f = 32 / b;
+    k_unpack_comp<<<grid_for(3 * nsites, 256), 256, 0, st>>>(bits, 3 * nsites, b, f, mats);
+    DDA_LAUNCH_CHECK("unpack composition");
+    return 0;
+}
+
+int launch_check_composition(const uint32_t* bits, int64_t nsites, int nmat, int* bad, cudaStream_t st) {
+    const int b = composition_bits(nmat), f = 32 / b;
+    k_check_comp<<<grid_for(3 * nsites, 256), 256, 0, st>>>(bits, 3 * nsites, b, f, nmat, bad);
+    DDA_LAUNCH_CHECK("check composition");
+    return 0;
+}
+
+size_t rank_scratch_words(int64_t nwords) { return (size_t)((nwords + kScanTile - 1) / kScanTile) + 1; }
+
+int launch_ranks(const uint32_t* occ, int64_t nwords, uint32_t* rank, uint32_t* scratch, uint32_t* total,
+                 cudaStream_t st) {
+    const int64_t nblocks = (nwords + kScanTile - 1) / kScanTile;
+    k_rank_local<<<(unsigned)nblocks, kScanThreads, 0, st>>>(occ, nwords, rank, scratch);
+    DDA_LAUNCH_CHECK("rank local scan");
+    k_rank_blocks<<<1, kScanThreads, 0, st>>>(scratch, nblocks, total);
+    DDA_LAUNCH_CHECK("rank block scan");
+    k_rank_add<<<grid_for(nwords, 256), 256, 0, st>>>(rank, nwords, scratch);
+    DDA_LAUNCH_CHECK("rank offsets");
+    return 0;
+}
+
+int launch_site_ranks(const TargetView& tv, int64_t n, uint32_t* out, cudaStream_t st) {
+    k_site_ranks<<<grid_for(n, 256), 256, 0, st>>>(tv, n, out);
+    DDA_LAUNCH_CHECK("site ranks");
+    return 0;
+}
+
+int launch_incident(const TargetView& tv, const Geometry& g, double k, const double* khat, const double* e0,
+                    double2* E, cudaStream_t st) {
+    k_incident<<<grid_for(g.nsites, 256), 256, 0, st>>>(tv, g, k, khat[0], khat[1], khat[2],
+                                                      make_double2(e0[0], e0[1]), make_double2(e0[2], e0[3]),
+                                                      make_double2(e0[4], e0[5]), E);
+    DDA_LAUNCH_CHECK("incident field");
+    return 0;
+}
+
+size_t xsec_scratch_elems() { return kRedBlocks + 1; }
+
+int launch_cross_sections(const TargetView& tv, const Geometry& g, double k, const double2* ainv,
+                          const double2* E, const double2* P, double2* scratch, cudaStream_t st) {
+    const unsigned blocks = (unsigned)std::min<int64_t>(kRedBlocks, std::max<int64_t>(1, (g.nsites + kRedThreads - 1) / kRedThreads));
+    k_xsec_partial<<<blocks, kRedThreads, 0, st>>>(tv, g, k * k * k, ainv, E, P, scratch);
+    DDA_LAUNCH_CHECK("cross-section partial sums");
+    k_xsec_final<<<1, kRedThreads, 0, st>>>(scratch, (int)blocks, scratch + kRedBlocks);
+    DDA_LAUNCH_CHECK("cross-section final sum");
+    return 0;
+}
+
+}  // namespace dda

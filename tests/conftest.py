@@ -18,3 +18,18 @@ def golden():
     import json
     with open(os.path.join(ROOT, "tests", "golden", "paper_values.json")) as f:
         return json.load(f)
+
+
+def build_library():
+    """Compile the CUDA library (idempotent) without importing the package."""
+    import importlib.util
+    path = os.path.join(ROOT, "paper_0908_0863_gb300", "_build.py")
+    spec = importlib.util.spec_from_file_location("_dda_build", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod.build()
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _built_library():
+    build_library()
