@@ -1,0 +1,428 @@
+#!/usr/bin/env python
+"""Benchmark of the DDA hot path on GB300 (one JSON line on stdout).
+
+Workload: the large single target of the benchmark plan -- a sphere of
+diameter 250 dipoles in a 256^3 lattice (N_d = 8,181,840; padded DFT grid
+512^3), m = 1.33 + 0.05i, |m| k d = 0.5, Clausius-Mossotti polarisability
+with radiative reaction, incidence along a seeded random direction with two
+orthogonal polarisations.
+
+One step = one whole job on that target through the C ABI:
+  pack the occupancy bit field from the device mask (Sec. 2),
+  build the context (ranks, alpha^-1, Green's-tensor spectrum, Sec. 3),
+  for each of the two polarisations: incident field, mixed-precision
+  BiCGSTAB solve to 1e-5 (complex64 FFT products inside FP64 refinement,
+  Sec. 4), cross sections; then free the context.
+value = products with A (FFT matvecs, any precision) per second over the
+whole job, max over ranks; solves/s and the per-precision matvec rates are
+reported beside it.
+
+--impl reference times the oracle (plain FP64 direct sum, O(N_d^2)) on the
+host cores on a bounded sample of the same product: a few hundred rows of
+A p, scaled to whole products per second.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FFT-matvecs/s and solves/s at 256³ lattice, HBM GB/s vs roofline, mixed vs FP64"
+UNIT = "FFT-matvecs/s"
+N_EDGE, DIAM = 256, 250
+M_REFR = 1.33 + 0.05j
+K_WAVE = 0.5 / abs(M_REFR)
+SEED = 20260005
+TOL = 1e-5
+
+
+def workload_name(n, d):
+    return f"sphere D={d} in {n}^3 lattice, m=1.33+0.05i, |m|kd=0.5, CM+RR, 2 polarisations, mixed BiCGSTAB 1e-5"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    import paper_0908_0863_gb300 as dda
+
+    n, D = args.edge, args.diameter
+    mask = synth.sphere(D, box=(n, n, n))
+    shape = (n, n, n)
+    nsites = mask.size
+    mask_dev = torch.from_numpy(mask.reshape(-1)).to(dev)
+    bits = torch.empty((nsites + 31) // 32, dtype=torch.int32, device=dev)
+    alpha = dda.dda_polarizability([M_REFR], K_WAVE, "cmrr")
+    # replicas: each rank solves its own incidence direction (weak scaling)
+    khat = synth.random_direction(SEED + rank)[0]
+    pols = synth.orthogonal_polarisations(khat)
+    stream = torch.cuda.current_stream(dev)
+
+    dda.dda_pack_occupancy(mask_dev, bits)
+    probe = dda.Lattice(shape, bits, alpha, K_WAVE)
+    nd = probe.n_dipoles
+    probe.close()
+    E = torch.empty((3, nd), dtype=torch.complex128, device=dev)
+    P = torch.empty_like(E)
+    stats = {"matvecs": 0, "matvecs_fp64": 0, "iters": 0, "solves": 0, "refinements": 0, "worst_true": 0.0,
+             "status": [], "cx": None}
+    pass_ms = {"c128": [[0, 0.0] for _ in range(5)], "c64": [[0, 0.0] for _ in range(5)]}
+
+    def job(record, host_bits=None, host_P=None):
+        if host_bits is None:
+            dda.dda_pack_occupancy(mask_dev, bits)
+            src = bits
+        else:
+            src = host_bits
+        ctx = dda.dda_init_lattice(shape, src, None, 1, alpha, K_WAVE)
+        try:
+            if record:
+                dda.dda_profile(ctx, True)
+            for e in pols:
+                dda.dda_incident_field(ctx, khat, e, E)
+                status, info = dda.dda_solve(ctx, E, P, args.method, "mixed", args.tol, args.max_iter)
+                cx = dda.dda_cross_sections(ctx, E, P)
+                if host_P is not None:
+                    host_P.copy_(P, non_blocking=True)
+                if record:
+                    stats["matvecs"] += info["matvecs"] + info["matvecs_fp64"]
+                    stats["matvecs_fp64"] += info["matvecs_fp64"]
+                    stats["iters"] += info["iterations"]
+                    stats["refinements"] += info["refinements"]
+                    stats["solves"] += 1
+                    stats["status"].append(status)
+                    stats["worst_true"] = max(stats["worst_true"], info["rel_residual_true"])
+                    stats["cx"] = cx
+            if record:
+                prof = dda.dda_profile_read(ctx)
+                for dt in prof:
+                    for q, (c, ms) in enumerate(prof[dt]):
+                        pass_ms[dt][q][0] += c
+                        pass_ms[dt][q][1] += ms
+        finally:
+            dda.dda_free(ctx)
+        if host_P is not None:
+            torch.cuda.current_stream(dev).synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        job(False)
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    l0 = dda.dda_launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        job(True)
+    ev1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    launches = dda.dda_launch_count() - l0
+    ms = ev0.elapsed_time(ev1)
+    ms_max = ms
+    totals = [stats["matvecs"], stats["solves"]]
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+        tt = torch.tensor(totals, dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+        totals = [float(v) for v in tt.tolist()]
+    value = totals[0] / (ms_max / 1e3)
+    solves_per_s = totals[1] / (ms_max / 1e3)
+
+    # ---- end to end through the public API with host buffers (pinned)
+    host_bits = torch.empty(bits.numel(), dtype=torch.int32).pin_memory()
+    host_bits.copy_(bits.cpu())
+    host_P = torch.empty(P.shape, dtype=P.dtype).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        job(False, host_bits=host_bits.numpy(), host_P=host_P)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    # a job makes the same products as in the timed loop; ranks run replicas
+    per_job_mv = stats["matvecs"] / max(1, args.steps)
+    e2e_value = per_job_mv * args.steps / e2e_s * world
+    h2d = host_bits.numel() * 4
+    d2h = 2 * P.numel() * 16 + 2 * 3 * 8
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64 (complex64 FFT products, FP64 refinement)",
+        "data": "synthetic",
+        "config": {"workload": workload_name(n, D), "lattice": [n, n, n], "padded": [2 * n] * 3, "n_dipoles": nd,
+                   "method": args.method, "precision": "mixed", "tol": args.tol, "polarisations": 2,
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (working set ~15 GB per job)"},
+        "solves_per_s": solves_per_s,
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "job": {"matvecs_per_solve": stats["matvecs"] / max(1, stats["solves"]),
+                "fp64_matvecs_per_solve": stats["matvecs_fp64"] / max(1, stats["solves"]),
+                "iterations_per_solve": stats["iters"] / max(1, stats["solves"]),
+                "refinements_per_solve": stats["refinements"] / max(1, stats["solves"]),
+                "worst_true_rel_residual": stats["worst_true"], "status": sorted(set(stats["status"])),
+                "cross_sections_last": stats["cx"]},
+    }
+    result["passes"] = {dt: [{"launches": c, "ms_avg": (t / c if c else None)} for c, t in pass_ms[dt]]
+                        for dt in pass_ms}
+    if rank == 0 and not args.no_extras:
+        result.update(extras(args, dda, torch, dev, shape, bits, alpha, nd, pass_ms, khat, pols))
+    if rank == 0 and not args.no_cpu:
+        result["cpu_baseline"] = cpu_baseline(args, nd, mask)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def algorithmic_bytes(n, nd, esize):
+    """Bytes each matvec pass must move at least (complex element size esize)."""
+    K = J = P = n
+    Lx = Ly = Lz = 2 * n
+    Hx = Hy = Hz = n + 1
+    V = 3 * nd * esize                      # compressed vector
+    A = 3 * K * Ly * P * esize              # y-transformed volume
+    B = 3 * Lx * Ly * P * esize             # xy-transformed volume
+    T = 6 * Hx * Hy * Hz * esize            # half spectrum
+    return {"P1": V + A, "P2": A + B, "P3": 2 * B + T, "P4": B + A, "P5": A + 2 * V,
+            "matvec_min": 3 * V + 4 * A + T}
+
+
+def extras(args, dda, torch, dev, shape, bits, alpha, nd, pass_ms, khat, pols):
+    """Roofline of the dominant kernel, per-precision matvec rates, FP64 solve."""
+    out = {}
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    peak_note = "of measured" if "hbm_gbs" in peaks else "of fallback"
+    # dominant pass by summed device time inside the timed steps
+    best = None
+    for dt, arr in pass_ms.items():
+        for q, (c, t) in enumerate(arr):
+            if c and (best is None or t > best[3]):
+                best = (dt, q, c, t)
+    if best:
+        dt, q, c, t = best
+        esize = 16 if dt == "c128" else 8
+        ab = algorithmic_bytes(args.edge, nd, esize)[f"P{q + 1}"]
+        avg = t / c
+        achieved = ab / (avg / 1e3) / 1e9
+        out["roofline"] = {"bound": "hbm", "kernel": f"P{q + 1} ({dt})", "achieved": achieved, "peak": hbm,
+                           "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                           "algorithmic_bytes": ab, "avg_ms": avg, "launches": c, "peak_source": peak_note}
+    # separate device-timed matvec loops (outside the timed region)
+    ctx = dda.dda_init_lattice(shape, bits, None, 1, alpha, K_WAVE)
+    try:
+        rates = {}
+        for name, dtype, reps in (("c64", torch.complex64, 20), ("c128", torch.complex128, 3)):
+            p = torch.randn((3, nd), dtype=dtype, device=dev)
+            y = torch.empty_like(p)
+            dda.dda_matvec(ctx, p, y)
+            torch.cuda.synchronize(dev)
+            dda.dda_profile(ctx, True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                dda.dda_matvec(ctx, p, y)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1) / reps
+            prof = dda.dda_profile_read(ctx)[name]
+            dda.dda_profile(ctx, False)
+            ab = algorithmic_bytes(args.edge, nd, 16 if name == "c128" else 8)
+            rates[name] = {"matvecs_per_s": 1e3 / ms, "ms": ms,
+                           "algorithmic_GBps": ab["matvec_min"] / (ms / 1e3) / 1e9,
+                           "five_pass_GBps": sum(ab[f"P{i}"] for i in range(1, 6)) / (ms / 1e3) / 1e9,
+                           "pass_ms": [t / c if c else None for c, t in prof]}
+            del p, y
+        out["fft_matvecs"] = rates
+        if args.fp64_solve:
+            E = torch.empty((3, nd), dtype=torch.complex128, device=dev)
+            P = torch.empty_like(E)
+            dda.dda_incident_field(ctx, khat, pols[0], E)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            status, info = dda.dda_solve(ctx, E, P, args.method, "fp64", args.tol, args.max_iter)
+            dt = time.perf_counter() - t0
+            out["fp64_solve"] = {"seconds": dt, "solves_per_s": 1.0 / dt, "status": status,
+                                 "iterations": info["iterations"], "matvecs": info["matvecs"],
+                                 "rel_residual_true": info["rel_residual_true"],
+                                 "cross_sections": dda.dda_cross_sections(ctx, E, P)}
+    finally:
+        dda.dda_free(ctx)
+    return out
+
+
+# ---------------------------------------------------------- oracle timing
+def oracle_rows_sample(nd, mask, rows_count, threads):
+    """Time the oracle's direct sum on rows_count rows of A p; returns
+    (products per second extrapolated to whole products, seconds, rows)."""
+    import numpy as np
+
+    import synth
+    from oracle import dda as odda
+    coords = odda.coords_of(mask)
+    ainv = np.full((nd, 3), 1.0 / odda.alpha_rr(M_REFR, K_WAVE))
+    p = synth.complex_normal(SEED, (3, nd))
+    rows = synth.rng(SEED + 1).choice(nd, size=rows_count, replace=False)
+    odda.direct_matvec_rows(coords, ainv, K_WAVE, p, rows[:1], nthreads=threads)  # warm
+    t0 = time.perf_counter()
+    odda.direct_matvec_rows(coords, ainv, K_WAVE, p, rows, nthreads=threads)
+    dt = time.perf_counter() - t0
+    return rows_count / nd / dt, dt
+
+
+def cpu_baseline(args, nd, mask):
+    threads = os.cpu_count() or 1
+    rate, dt = oracle_rows_sample(nd, mask, args.cpu_rows, threads)
+    return {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{args.cpu_rows} rows of A p by direct FP64 summation over all {nd} dipoles "
+                      f"({dt:.1f} s), scaled to whole products"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import synth
+    n, D = args.edge, args.diameter
+    mask = synth.sphere(D, box=(n, n, n))
+    nd = int(mask.sum())
+    threads = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle_rows_sample(nd, mask, max(1, args.cpu_rows // 10), threads)
+    t0 = time.perf_counter()
+    rows_done = 0
+    for _ in range(args.steps):
+        oracle_rows_sample(nd, mask, args.cpu_rows, threads)
+        rows_done += args.cpu_rows
+    dt = time.perf_counter() - t0
+    value = rows_done / nd / dt
+    sample = f"{args.cpu_rows} rows of A p per step by direct FP64 summation over all {nd} dipoles, scaled to whole products"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(n, D), "lattice": [n, n, n], "n_dipoles": nd},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--edge", type=int, default=N_EDGE)
+    ap.add_argument("--diameter", type=int, default=DIAM)
+    ap.add_argument("--method", default="bicgstab", choices=["bicg", "bicgstab", "qmr"])
+    ap.add_argument("--tol", type=float, default=TOL)
+    ap.add_argument("--max-iter", type=int, default=4000)
+    ap.add_argument("--cpu-rows", type=int, default=200)
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--fp64-solve", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -218,6 +218,28 @@ int dda_solve(dda_ctx* ctx, const void* einc, void* p, int method, int precision
  */
 int dda_cross_sections(dda_ctx* ctx, const void* einc, const void* p, double* out, void* stream);
 
+/* -------------------------------------------------------------- tracing */
+
+/*
+ * Per-pass timing of the matvec (the paper reports per-component times,
+ * Sec. 6 and Tables 4 and 6).  enable != 0: every later product of this
+ * context (dda_matvec and the products inside dda_solve) records a CUDA
+ * event pair around each of its five passes on the calling stream;
+ * enable == 0 stops and drops what was recorded.
+ */
+int dda_profile(dda_ctx* ctx, int enable);
+
+/*
+ * Wait for the recorded events and return, for dtype d (0 = complex128,
+ * 1 = complex64) and pass q (0..4 = P1..P5 of dda_matvec), the launch
+ * count counts[d*5 + q] and the summed device milliseconds ms[d*5 + q];
+ * the records are then cleared.  counts, ms: host arrays of 10.
+ */
+int dda_profile_read(dda_ctx* ctx, int64_t* counts, double* ms);
+
+/* Kernel launches issued by the library since it was loaded (all threads). */
+int64_t dda_launch_count(void);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* dda_last_error(void);
 

@@ -37,7 +37,7 @@ EXPORTS = (
     "dda_polarizability", "dda_pack_occupancy", "dda_unpack_occupancy", "dda_pack_composition",
     "dda_unpack_composition", "dda_init_lattice", "dda_free", "dda_query", "dda_site_ranks",
     "dda_tensor_spectrum", "dda_matvec", "dda_incident_field", "dda_solve", "dda_cross_sections",
-    "dda_last_error",
+    "dda_profile", "dda_profile_read", "dda_launch_count", "dda_last_error",
 )
 
 
@@ -88,10 +88,14 @@ def load(path: str | None = None):
     L.dda_incident_field.argtypes = [vp, vp, vp, vp, vp]
     L.dda_solve.argtypes = [vp, vp, vp, i32, i32, d, i32, i32, ctypes.POINTER(SolveInfo), vp]
     L.dda_cross_sections.argtypes = [vp, vp, vp, vp, vp]
+    L.dda_profile.argtypes = [vp, i32]
+    L.dda_profile_read.argtypes = [vp, vp, vp]
+    L.dda_launch_count.argtypes = []
+    L.dda_launch_count.restype = ctypes.c_int64
     L.dda_last_error.argtypes = []
     L.dda_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("dda_free", "dda_last_error"):
+        if name not in ("dda_free", "dda_last_error", "dda_launch_count"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -232,6 +236,23 @@ def dda_cross_sections(ctx, einc, p, stream=None):
     out = np.zeros(3)
     _check(load().dda_cross_sections(ctypes.c_void_p(ctx), _ptr(einc), _ptr(p), _ptr(out), _stream(stream)))
     return tuple(float(v) for v in out)
+
+
+def dda_profile(ctx, enable=True):
+    _check(load().dda_profile(ctypes.c_void_p(ctx), int(bool(enable))))
+
+
+def dda_profile_read(ctx):
+    """{'c128'|'c64': [(launches, ms) for P1..P5]} of the recorded passes."""
+    counts = np.zeros(10, dtype=np.int64)
+    ms = np.zeros(10)
+    _check(load().dda_profile_read(ctypes.c_void_p(ctx), _ptr(counts), _ptr(ms)))
+    return {name: [(int(counts[d * 5 + q]), float(ms[d * 5 + q])) for q in range(5)]
+            for d, name in ((0, "c128"), (1, "c64"))}
+
+
+def dda_launch_count() -> int:
+    return int(load().dda_launch_count())
 
 
 def dda_last_error() -> str:

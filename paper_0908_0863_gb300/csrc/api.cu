@@ -2,6 +2,7 @@
 // solves with FP64 or mixed-precision iterative refinement, and the
 // observables.  Host code only orchestrates; every step runs in the kernels
 // of matvec.cu, spectrum.cu, target.cu and krylov.cu.
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <complex>
@@ -17,6 +18,10 @@
 namespace dda {
 
 static thread_local std::string g_last_error;
+static std::atomic<int64_t> g_launches{0};
+
+void note_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 int fail(int status, const std::string& msg) {
@@ -84,6 +89,7 @@ struct dda_ctx {
     KState* host_state = nullptr;  // pinned, 2 entries
     MatvecView<double> mv64{};
     MatvecView<float> mv32{};
+    PassProfiler prof;
 };
 
 namespace {
@@ -361,13 +367,13 @@ int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occu
         m.g = g; m.tv = tv; m.ainv = c->ainv64; m.spec = c->spec64; m.tw = c->tw64;
         m.Ay = static_cast<double2*>(c->work);
         m.Bxy = m.Ay + 3ull * g.P * g.Ly * g.K;
-        m.status = nullptr; m.conj = 0;
+        m.status = nullptr; m.conj = 0; m.prof = &c->prof;
         configure_matvec<double>(m);
         MatvecView<float>& f = c->mv32;
         f.g = g; f.tv = tv; f.ainv = c->ainv32; f.spec = c->spec32; f.tw = c->tw32;
         f.Ay = reinterpret_cast<float2*>(c->work);
         f.Bxy = f.Ay + 3ull * g.P * g.Ly * g.K;
-        f.status = nullptr; f.conj = 0;
+        f.status = nullptr; f.conj = 0; f.prof = &c->prof;
         configure_matvec<float>(f);
     }
     *out = c;
@@ -381,6 +387,26 @@ int dda_query(const dda_ctx* c, int64_t* n_dipoles, int32_t padded[3], int64_t* 
     if (device_bytes) *device_bytes = c->bytes;
     return DDA_OK;
 }
+
+int dda_profile(dda_ctx* c, int enable) {
+    if (int rc = check_ctx(c)) return rc;
+    c->prof.on = enable != 0;
+    if (!enable) {
+        int64_t n[10];
+        double ms[10];
+        c->prof.read(n, ms);
+    }
+    return DDA_OK;
+}
+
+int dda_profile_read(dda_ctx* c, int64_t* counts, double* ms) {
+    if (int rc = check_ctx(c)) return rc;
+    if (!counts || !ms) return fail(DDA_ERR_ARG, "dda_profile_read: NULL output");
+    if (c->prof.read(counts, ms)) return fail(DDA_ERR_CUDA, "dda_profile_read: event wait failed");
+    return DDA_OK;
+}
+
+int64_t dda_launch_count(void) { return launch_count(); }
 
 int dda_site_ranks(const dda_ctx* c, uint32_t* rank, void* stream) {
     if (int rc = check_ctx(c)) return rc;

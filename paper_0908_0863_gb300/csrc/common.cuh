@@ -47,8 +47,12 @@ int cuda_fail(cudaError_t e, const char* what);
         if (e__ != cudaSuccess) return ::dda::cuda_fail(e__, #expr); \
     } while (0)
 
+void note_launches(int64_t n);
+
+// after every kernel launch: count it and turn a launch error into a status
 #define DDA_LAUNCH_CHECK(what)                                           \
     do {                                                                 \
+        ::dda::note_launches(1);                                         \
         cudaError_t e__ = cudaGetLastError();                            \
         if (e__ != cudaSuccess) return ::dda::cuda_fail(e__, what);      \
     } while (0)

@@ -645,6 +645,7 @@ int krylov_solve(int method, MatvecView<T> mv, KrylovWork<T>& ws, const C<T>* b,
             k_qmr_ds<T><<<G, B, 0, st>>>(ds, p, pt, d, s, x, r, n, first, part);
             k_qmr_scalar<<<1, B, 0, st>>>(ds, part, 3, first);
         }
+        note_launches(method == DDA_BICGSTAB ? 8 : method == DDA_BICG ? 5 : 9);
         {
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) { rc = cuda_fail(e, "krylov iteration"); break; }

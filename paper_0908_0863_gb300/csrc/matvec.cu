@@ -229,46 +229,58 @@ int launch_matvec(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t 
     constexpr int V = vals_per_thread<T>();
     const Geometry& g = mv.g;
     const int elt = sizeof(C<T>);
+    const int dt = sizeof(T) == 8 ? 0 : 1;
+    PassProfiler* pf = (mv.prof && mv.prof->on) ? mv.prof : nullptr;
     int rc;
     {   // P1
         const int W = 1 << mv.logW_y;
         const size_t sm = (size_t)g.Ly * (W + 1) * elt;
         if ((rc = set_smem<T>((const void*)k_expand_yfwd<T, V>, sm))) return rc;
         dim3 grid((g.K + W - 1) / W, g.P, 3);
+        if (pf) pf->begin(dt, 0, st);
         k_expand_yfwd<T, V><<<grid, W * g.Ly / V, sm, st>>>(mv, p);
         DDA_LAUNCH_CHECK("P1 expand + y-forward");
+        if (pf) pf->end(st);
     }
     {   // P2
         const int W = 1 << mv.logW_x;
         const size_t sm = (size_t)g.Lx * (W + 1) * elt;
         if ((rc = set_smem<T>((const void*)k_xrows<T, V, false>, sm))) return rc;
         const int64_t rows = 3LL * g.P * g.Ly;
+        if (pf) pf->begin(dt, 1, st);
         k_xrows<T, V, false><<<(unsigned)((rows + W - 1) / W), W * g.Lx / V, sm, st>>>(mv);
         DDA_LAUNCH_CHECK("P2 x-forward");
+        if (pf) pf->end(st);
     }
     {   // P3
         const int W = 1 << mv.logW_z;
         const size_t sm = 3 * (size_t)g.Lz * (W + 1) * elt;
         if ((rc = set_smem<T>((const void*)k_zconv<T, V>, sm))) return rc;
         dim3 grid(g.Lx / W > 0 ? g.Lx / W : 1, g.Ly);
+        if (pf) pf->begin(dt, 2, st);
         k_zconv<T, V><<<grid, W * g.Lz / V, sm, st>>>(mv);
         DDA_LAUNCH_CHECK("P3 z-forward, spectrum product, z-inverse");
+        if (pf) pf->end(st);
     }
     {   // P4
         const int W = 1 << mv.logW_x;
         const size_t sm = (size_t)g.Lx * (W + 1) * elt;
         if ((rc = set_smem<T>((const void*)k_xrows<T, V, true>, sm))) return rc;
         const int64_t rows = 3LL * g.P * g.Ly;
+        if (pf) pf->begin(dt, 3, st);
         k_xrows<T, V, true><<<(unsigned)((rows + W - 1) / W), W * g.Lx / V, sm, st>>>(mv);
         DDA_LAUNCH_CHECK("P4 x-inverse");
+        if (pf) pf->end(st);
     }
     {   // P5
         const int W = 1 << mv.logW_y;
         const size_t sm = (size_t)g.Ly * (W + 1) * elt;
         if ((rc = set_smem<T>((const void*)k_yinv_compress<T, V>, sm))) return rc;
         dim3 grid((g.K + W - 1) / W, g.P, 3);
+        if (pf) pf->begin(dt, 4, st);
         k_yinv_compress<T, V><<<grid, W * g.Ly / V, sm, st>>>(mv, p, y);
         DDA_LAUNCH_CHECK("P5 y-inverse + diagonal + compress");
+        if (pf) pf->end(st);
     }
     return 0;
 }

@@ -2,6 +2,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "profile.cuh"
 
 namespace dda {
 
@@ -19,6 +20,7 @@ struct MatvecView {
     int logW_y, logW_x, logW_z;  // tile widths (lines per CTA) of the passes
     const int* status;  // optional: when *status != 0 every pass returns at once
     int conj;           // 1: compute conj(A conj(p)) = A^H p (A complex symmetric)
+    PassProfiler* prof; // host object; when non-null and on, each pass is timed
 };
 
 template <typename T> void configure_matvec(MatvecView<T>& mv);
