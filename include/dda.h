@@ -158,8 +158,9 @@ int dda_site_ranks(const dda_ctx* ctx, uint32_t* rank, void* stream);
 
 /*
  * Copy the stored half spectrum of the six tensor components, scaled by
- * 1 / (Lx Ly Lz): device complex [6][Lz/2+1][Ly/2+1][Lx/2+1] of the given
- * dtype.  Diagnostic entry point (parity of the init step).
+ * 1 / (Lx Ly Lz): device complex [Lz/2+1][Ly/2+1][Lx/2+1][6] of the given
+ * dtype (components xx, xy, xz, yy, yz, zz innermost).  Diagnostic entry
+ * point (parity of the init step).
  */
 int dda_tensor_spectrum(const dda_ctx* ctx, void* out, int dtype, void* stream);
 

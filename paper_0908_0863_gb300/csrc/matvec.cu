@@ -13,76 +13,92 @@
 // y 3[K x P], x 3[J'' x P], z all K'' x J''; the inverse mirrors them.  The
 // 1/(Lx Ly Lz) normalisation of the inverse DFT is folded into the stored
 // spectrum.
-#include "fft.cuh"
+//
+// Every pass keeps its lines in registers (fft_reg.cuh): points are loaded
+// from global memory straight into the registers of the first DFT stage and
+// stored from the registers of the last, and only the exchanges between
+// stages use shared memory.  Strided lines (y, z) are processed W at a
+// time, W adjacent columns so that each load and store touches W
+// contiguous elements.  P3 parks the first two transformed components of a
+// column in shared memory so that the spectrum product happens in place
+// between the forward and the inverse transforms.
+#include <cstdlib>
+
+#include "fft_reg.cuh"
 #include "matvec.cuh"
 
 namespace dda {
 
 namespace {
 
+__device__ __forceinline__ int lines_threads_log(int logN) { return logN > 3 ? logN - 3 : 0; }
+
 // ---------------------------------------------------------------- P1
-template <typename T, int V>
-__global__ void __launch_bounds__(512) k_expand_yfwd(MatvecView<T> mv, const C<T>* __restrict__ p) {
-    extern __shared__ unsigned char smem_raw[];
-    C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);
+template <typename T>
+__global__ void __launch_bounds__(1024) k_p1(MatvecView<T> mv, const C<T>* __restrict__ p) {
     if (mv.status && *mv.status) return;
+    extern __shared__ unsigned char smem_raw[];
+    C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
     const Geometry& g = mv.g;
-    const int logW = mv.logW_y, W = 1 << logW, ld = W + 1;
-    const int i0 = blockIdx.x * W, kz = blockIdx.y, c = blockIdx.z;
-    const int logN = ilog2_dev(g.Ly), N = g.Ly;
+    const int logW = mv.logW_y, W = 1 << logW;
+    const int logN = ilog2_dev(g.Ly), logT = lines_threads_log(logN);
+    const int nv = g.Ly < 8 ? g.Ly : 8;
+    const int w = threadIdx.x & (W - 1), t = threadIdx.x >> logW;
+    const int i = blockIdx.x * W + w, kz = blockIdx.y, c = blockIdx.z;
     const C<T>* pc = p + (int64_t)c * g.nd;
-    for (int e = threadIdx.x; e < W * N; e += blockDim.x) {
-        const int n = e >> logW, w = e & (W - 1), i = i0 + w;
-        C<T> val = mk<T>(0, 0);
-        if (n < g.J && i < g.K) {
+    C<T> v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const int n = t + (m << logT);
+        v[m] = mk<T>(0, 0);
+        if (m < nv && n < g.J && i < g.K) {
             const int64_t s = ((int64_t)kz * g.J + n) * g.K + i;
             if (occupied(mv.tv, s)) {
-                val = pc[site_rank(mv.tv, s)];
-                if (mv.conj) val.y = -val.y;
+                v[m] = pc[site_rank(mv.tv, s)];
+                if (mv.conj) v[m].y = -v[m].y;
             }
         }
-        buf[n * ld + w] = val;
     }
-    __syncthreads();
-    fft_tile<T, V, false>(buf, ld, logW, logN, mv.tw);
-    C<T>* out = mv.Ay + ((int64_t)c * g.P + kz) * N * g.K;
-    for (int e = threadIdx.x; e < W * N; e += blockDim.x) {
-        const int n = e >> logW, w = e & (W - 1), i = i0 + w;
-        if (i < g.K) out[(int64_t)n * g.K + i] = buf[n * ld + w];
+    fft_regs<T, false>(v, sm, ColLayout{W}, w, t, logN, mv.tw);
+    if (i < g.K) {
+        C<T>* out = mv.Ay + ((int64_t)c * g.P + kz) * g.Ly * g.K + i;
+#pragma unroll
+        for (int m = 0; m < 8; ++m)
+            if (m < nv) out[(int64_t)(t + (m << logT)) * g.K] = v[m];
     }
 }
 
 // ------------------------------------------------------- P2 / P4 (rows)
-// Transforms W rows of length Lx.  Forward: rows of K inputs (Ay) -> Lx
-// outputs (Bxy).  Inverse: rows of Lx inputs (Bxy) -> first K outputs (Ay).
-template <typename T, int V, bool INV>
-__global__ void __launch_bounds__(512) k_xrows(MatvecView<T> mv) {
+// Forward: rows of K inputs (Ay) -> Lx outputs (Bxy).  Inverse: rows of Lx
+// inputs (Bxy) -> first K outputs (Ay).  2^logW_x rows per CTA.
+template <typename T, bool INV>
+__global__ void __launch_bounds__(512) k_rows(MatvecView<T> mv) {
     if (mv.status && *mv.status) return;
     extern __shared__ unsigned char smem_raw[];
-    C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);
+    C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
     const Geometry& g = mv.g;
-    const int logW = mv.logW_x, W = 1 << logW, ld = W + 1;
-    const int N = g.Lx, logN = ilog2_dev(N);
+    const int N = g.Lx, logN = ilog2_dev(N), logT = lines_threads_log(logN);
+    const int nv = N < 8 ? N : 8;
+    const int t = threadIdx.x & ((1 << logT) - 1), wl = threadIdx.x >> logT;
     const int64_t nrows = 3LL * g.P * g.Ly;
-    const int64_t r0 = (int64_t)blockIdx.x * W;
-    const int nin = INV ? N : g.K;
-    const C<T>* src = INV ? mv.Bxy : mv.Ay;
-    C<T>* dst = INV ? mv.Ay : mv.Bxy;
-    const int ldin = INV ? N : g.K, ldout = INV ? g.K : N;
-    const int nout = INV ? g.K : N;
-    for (int e = threadIdx.x; e < W * N; e += blockDim.x) {
-        const int w = e >> logN, n = e & (N - 1);
-        const int64_t row = r0 + w;
-        C<T> val = mk<T>(0, 0);
-        if (n < nin && row < nrows) val = src[row * ldin + n];
-        buf[n * ld + w] = val;
+    const int64_t row = ((int64_t)blockIdx.x << mv.logW_x) + wl;
+    const bool ok = row < nrows;
+    const int nin = INV ? N : g.K, nout = INV ? g.K : N;
+    const C<T>* src = (INV ? mv.Bxy : mv.Ay) + (ok ? row * (INV ? N : g.K) : 0);
+    C<T>* dst = (INV ? mv.Ay : mv.Bxy) + (ok ? row * (INV ? g.K : N) : 0);
+    C<T> v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const int n = t + (m << logT);
+        v[m] = (ok && m < nv && n < nin) ? src[n] : mk<T>(0, 0);
     }
-    __syncthreads();
-    fft_tile<T, V, INV>(buf, ld, logW, logN, mv.tw);
-    for (int e = threadIdx.x; e < W * N; e += blockDim.x) {
-        const int w = e >> logN, n = e & (N - 1);
-        const int64_t row = r0 + w;
-        if (n < nout && row < nrows) dst[row * ldout + n] = buf[n * ld + w];
+    fft_regs<T, INV>(v, sm, RowLayout{row_ld(N)}, wl, t, logN, mv.tw);
+    if (ok) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const int n = t + (m << logT);
+            if (m < nv && n < nout) dst[n] = v[m];
+        }
     }
 }
 
@@ -98,187 +114,257 @@ __device__ __forceinline__ int mirror_flip(int m, int fx, int fy, int fz) {
     }
 }
 
-template <typename T, int V>
-__global__ void __launch_bounds__(512) k_zconv(MatvecView<T> mv) {
+// the six spectrum components of one point (contiguous) with 16-byte loads
+template <typename T>
+__device__ __forceinline__ void load6(const C<T>* __restrict__ p, C<T> (&Y)[6]) {
+    if (sizeof(T) == 4) {
+        const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float4 f = __ldg(q + i);
+            Y[2 * i] = mk<T>(f.x, f.y);
+            Y[2 * i + 1] = mk<T>(f.z, f.w);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) Y[i] = __ldg(p + i);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_p3(MatvecView<T> mv) {
     if (mv.status && *mv.status) return;
     extern __shared__ unsigned char smem_raw[];
-    C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);
+    C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
     const Geometry& g = mv.g;
-    const int logW = mv.logW_z, W = 1 << logW, ld = W + 1;
-    const int N = g.Lz, logN = ilog2_dev(N);
-    const int ix0 = blockIdx.x * W, jy = blockIdx.y;
+    const int logW = mv.logW_z, W = 1 << logW;
+    const int N = g.Lz, logN = ilog2_dev(N), logT = lines_threads_log(logN);
+    const int nv = N < 8 ? N : 8;
+    const int w = threadIdx.x & (W - 1), t = threadIdx.x >> logW;
+    // rows jy and Ly - jy read the same spectrum rows (mirror lookup): visit
+    // them back to back (0, 1, Ly-1, 2, Ly-2, ...) so the second read hits L2
+    const int b = blockIdx.y, q2 = (b + 1) >> 1;
+    const int jy = b == 0 ? 0 : ((b & 1) ? q2 : g.Ly - q2);
+    const int ix = blockIdx.x * W + w;
+    const bool ok = ix < g.Lx;
+    const ColLayout L{W};
+    const int region = col_elems(N, W);
+    C<T>* S0 = sm;
+    C<T>* S1 = sm + region;
+    C<T>* S2 = sm + 2 * region;
     const int64_t plane = (int64_t)g.Ly * g.Lx;   // stride between z planes of Bxy
     const int64_t comp = (int64_t)g.P * plane;    // stride between components
-    const int64_t base = (int64_t)jy * g.Lx + ix0;
-    const int cstride = N * ld;
-    for (int c = 0; c < 3; ++c) {
-        for (int e = threadIdx.x; e < W * N; e += blockDim.x) {
-            const int n = e >> logW, w = e & (W - 1);
-            C<T> val = mk<T>(0, 0);
-            if (n < g.P && ix0 + w < g.Lx) val = mv.Bxy[c * comp + n * plane + base + w];
-            buf[c * cstride + n * ld + w] = val;
-        }
-    }
-    __syncthreads();
-    for (int c = 0; c < 3; ++c) fft_tile<T, V, false>(buf + c * cstride, ld, logW, logN, mv.tw);
-    // spectrum product (Eqs. 6-8) with the mirror lookup of Sec. 3
-    const int my = jy <= g.Ly / 2 ? jy : g.Ly - jy;
-    const int fy = jy > g.Ly / 2;
-    const int64_t sm = (int64_t)g.Hz * g.Hy * g.Hx;
-    for (int e = threadIdx.x; e < W * N; e += blockDim.x) {
-        const int n = e >> logW, w = e & (W - 1);
-        const int ix = ix0 + w;
-        if (ix >= g.Lx) continue;
-        const int mx = ix <= g.Lx / 2 ? ix : g.Lx - ix, fx = ix > g.Lx / 2;
-        const int mz = n <= N / 2 ? n : N - n, fz = n > N / 2;
-        const C<T>* S = mv.spec + ((int64_t)mz * g.Hy + my) * g.Hx + mx;
-        C<T> Y[6];
+    C<T>* col = mv.Bxy + (int64_t)jy * g.Lx + (ok ? ix : 0);
+    C<T> v[8], nxt[8];
 #pragma unroll
-        for (int m = 0; m < 6; ++m) {
-            C<T> t = S[m * sm];
-            if (mirror_flip(m, fx, fy, fz)) { t.x = -t.x; t.y = -t.y; }
-            Y[m] = t;
-        }
-        const int o = n * ld + w;
-        const C<T> X0 = buf[o], X1 = buf[cstride + o], X2 = buf[2 * cstride + o];
-        buf[o] = cfma<T>(Y[2], X2, cfma<T>(Y[1], X1, cmul<T>(Y[0], X0)));
-        buf[cstride + o] = cfma<T>(Y[4], X2, cfma<T>(Y[3], X1, cmul<T>(Y[1], X0)));
-        buf[2 * cstride + o] = cfma<T>(Y[5], X2, cfma<T>(Y[4], X1, cmul<T>(Y[2], X0)));
+    for (int m = 0; m < 8; ++m) {
+        const int n = t + (m << logT);
+        nxt[m] = (ok && m < nv && n < g.P) ? col[n * plane] : mk<T>(0, 0);
     }
-    __syncthreads();
-    for (int c = 0; c < 3; ++c) fft_tile<T, V, true>(buf + c * cstride, ld, logW, logN, mv.tw);
+    // forward z DFTs; X0, X1 parked in S0, S1 at the canonical points.  The
+    // loads of the next component are in flight while this one transforms.
     for (int c = 0; c < 3; ++c) {
-        for (int e = threadIdx.x; e < W * N; e += blockDim.x) {
-            const int n = e >> logW, w = e & (W - 1);
-            if (n < g.P && ix0 + w < g.Lx) mv.Bxy[c * comp + n * plane + base + w] = buf[c * cstride + n * ld + w];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) v[m] = nxt[m];
+        if (c < 2) {
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int n = t + (m << logT);
+                nxt[m] = (ok && m < nv && n < g.P) ? col[(c + 1) * comp + n * plane] : mk<T>(0, 0);
+            }
+        }
+        C<T>* S = c == 0 ? S0 : (c == 1 ? S1 : S2);
+        fft_regs<T, false>(v, S, L, w, t, logN, mv.tw);
+        if (c < 2) {
+#pragma unroll
+            for (int m = 0; m < 8; ++m)
+                if (m < nv) S[L(w, t + (m << logT))] = v[m];
+        }
+    }
+    // spectrum product (Eqs. 6-8) with the signed mirror lookup of Sec. 3
+    {
+        const int my = jy <= g.Ly / 2 ? jy : g.Ly - jy, fy = jy > g.Ly / 2;
+        const int mx = ix <= g.Lx / 2 ? ix : g.Lx - ix, fx = ix > g.Lx / 2;
+        const C<T>* spec = mv.spec + ((int64_t)my * g.Hx + (ok ? mx : 0)) * 6;
+        const int64_t zstep = (int64_t)g.Hy * g.Hx * 6;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            if (m >= nv) break;
+            const int n = t + (m << logT);
+            const int mz = n <= N / 2 ? n : N - n, fz = n > N / 2;
+            const int o = L(w, n);
+            C<T> Y[6];
+            if (ok) {
+                load6<T>(spec + mz * zstep, Y);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 6; ++q) Y[q] = mk<T>(0, 0);
+            }
+#pragma unroll
+            for (int q = 0; q < 6; ++q)
+                if (mirror_flip(q, fx, fy, fz)) { Y[q].x = -Y[q].x; Y[q].y = -Y[q].y; }
+            const C<T> X0 = S0[o], X1 = S1[o], X2 = v[m];
+            S0[o] = cfma<T>(Y[2], X2, cfma<T>(Y[1], X1, cmul<T>(Y[0], X0)));
+            S1[o] = cfma<T>(Y[4], X2, cfma<T>(Y[3], X1, cmul<T>(Y[1], X0)));
+            v[m] = cfma<T>(Y[5], X2, cfma<T>(Y[4], X1, cmul<T>(Y[2], X0)));
+        }
+    }
+    // inverse z DFTs, keeping k < P: component 2 from registers, then 1 and 0
+    for (int c = 2; c >= 0; --c) {
+        C<T>* S = c == 0 ? S0 : (c == 1 ? S1 : S2);
+        if (c < 2) {
+#pragma unroll
+            for (int m = 0; m < 8; ++m)
+                if (m < nv) v[m] = S[L(w, t + (m << logT))];
+            __syncthreads();   // all parked values read before S is reused for exchanges
+        }
+        fft_regs<T, true>(v, S, L, w, t, logN, mv.tw);
+        if (ok) {
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int n = t + (m << logT);
+                if (m < nv && n < g.P) col[c * comp + n * plane] = v[m];
+            }
         }
     }
 }
 
 // ---------------------------------------------------------------- P5
-template <typename T, int V>
-__global__ void __launch_bounds__(512) k_yinv_compress(MatvecView<T> mv, const C<T>* __restrict__ p,
-                                                       C<T>* __restrict__ y) {
+template <typename T>
+__global__ void __launch_bounds__(1024) k_p5(MatvecView<T> mv, const C<T>* __restrict__ p, C<T>* __restrict__ y) {
     if (mv.status && *mv.status) return;
     extern __shared__ unsigned char smem_raw[];
-    C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);
+    C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
     const Geometry& g = mv.g;
-    const int logW = mv.logW_y, W = 1 << logW, ld = W + 1;
-    const int i0 = blockIdx.x * W, kz = blockIdx.y, c = blockIdx.z;
-    const int N = g.Ly, logN = ilog2_dev(N);
-    const C<T>* in = mv.Ay + ((int64_t)c * g.P + kz) * N * g.K;
-    for (int e = threadIdx.x; e < W * N; e += blockDim.x) {
-        const int n = e >> logW, w = e & (W - 1), i = i0 + w;
-        buf[n * ld + w] = i < g.K ? in[(int64_t)n * g.K + i] : mk<T>(0, 0);
+    const int logW = mv.logW_y, W = 1 << logW;
+    const int logN = ilog2_dev(g.Ly), logT = lines_threads_log(logN);
+    const int nv = g.Ly < 8 ? g.Ly : 8;
+    const int w = threadIdx.x & (W - 1), t = threadIdx.x >> logW;
+    const int i = blockIdx.x * W + w, kz = blockIdx.y, c = blockIdx.z;
+    const bool ok = i < g.K;
+    const C<T>* in = mv.Ay + ((int64_t)c * g.P + kz) * g.Ly * g.K + (ok ? i : 0);
+    C<T> v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const int n = t + (m << logT);
+        v[m] = (ok && m < nv) ? in[(int64_t)n * g.K] : mk<T>(0, 0);
     }
-    __syncthreads();
-    fft_tile<T, V, true>(buf, ld, logW, logN, mv.tw);
+    fft_regs<T, true>(v, sm, ColLayout{W}, w, t, logN, mv.tw);
+    if (!ok) return;
     const C<T>* pc = p + (int64_t)c * g.nd;
     C<T>* yc = y + (int64_t)c * g.nd;
-    for (int e = threadIdx.x; e < W * g.J; e += blockDim.x) {
-        const int n = e >> logW, w = e & (W - 1), i = i0 + w;
-        if (i >= g.K) continue;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const int n = t + (m << logT);
+        if (m >= nv || n >= g.J) continue;
         const int64_t s = ((int64_t)kz * g.J + n) * g.K + i;
         if (!occupied(mv.tv, s)) continue;
         const uint32_t r = site_rank(mv.tv, s);
         const C<T> a = mv.ainv[material(mv.tv, s, c) * 3 + c];
         C<T> pv = pc[r];
         if (mv.conj) pv.y = -pv.y;
-        C<T> out = cfma<T>(a, pv, buf[n * ld + w]);
+        C<T> out = cfma<T>(a, pv, v[m]);
         if (mv.conj) out.y = -out.y;
         yc[r] = out;
     }
 }
 
-template <typename T> constexpr int vals_per_thread() { return sizeof(T) == 4 ? 16 : 8; }
+inline int threads_log(int N) { return N > 8 ? ilog2(N) - 3 : 0; }
 
-// pick W (a power of two) for a tile of lines of length N: as wide as the
-// row budget allows while the launch stays within 512 threads
-inline int pick_logW(int N, int V, int want_bytes, int elt, int ncols) {
-    int logW = 0;
-    while ((1 << logW) * elt < want_bytes && (2 << logW) * N / V <= 512) ++logW;
-    while (logW > 0 && (1 << (logW - 1)) >= ncols) --logW;   // no wider than the data
-    while ((1 << logW) * N < V) ++logW;                       // at least one full thread
-    return logW;
+// largest power of two <= n (n >= 1), as its log
+inline int floor_log2(int n) { int l = 0; while ((2 << l) <= n) ++l; return l; }
+
+int env_tile(const char* name, int dflt) {
+    const char* s = std::getenv(name);
+    if (!s || !*s) return dflt;
+    const int v = std::atoi(s);
+    return v > 0 ? floor_log2(v) : dflt;
+}
+
+int set_smem(const void* fn, size_t bytes) {
+    if (bytes > 48 * 1024)
+        DDA_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    return 0;
 }
 
 }  // namespace
 
 template <typename T>
 void configure_matvec(MatvecView<T>& mv) {
-    constexpr int V = vals_per_thread<T>();
+    const Geometry& g = mv.g;
     const int elt = sizeof(C<T>);
-    mv.logW_y = pick_logW(mv.g.Ly, V, 128, elt, mv.g.K);
-    mv.logW_x = pick_logW(mv.g.Lx, V, 128, elt, 1 << 30);
-    mv.logW_z = pick_logW(mv.g.Lz, V, 64, elt, mv.g.Lx);
-    // the z tile holds three components: keep it within the shared-memory budget
-    while (mv.logW_z > 0 && 3 * (size_t)mv.g.Lz * ((1 << mv.logW_z) + 1) * elt > 200 * 1024) --mv.logW_z;
-    while (((1 << mv.logW_z) * mv.g.Lz) < V) ++mv.logW_z;
-}
-
-template <typename T>
-static int set_smem(const void* fn, size_t bytes) {
-    if (bytes > 48 * 1024) {
-        DDA_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-    }
-    return 0;
+    const int ty = threads_log(g.Ly), tz = threads_log(g.Lz), tx = threads_log(g.Lx);
+    // strided passes: W adjacent columns (128-byte rows for y, 64 for z)
+    int wy = floor_log2(128 / elt);
+    while (wy > 0 && (1 << (wy + ty)) > 1024) --wy;
+    while (wy > 0 && (1 << (wy - 1)) >= g.K) --wy;          // no wider than the lattice
+    int wz = floor_log2(64 / elt);
+    while (wz > 0 && (1 << (wz + tz)) > 512) --wz;
+    while (wz > 0 && 3ull * col_elems(g.Lz, 1 << wz) * elt > 200 * 1024) --wz;
+    while (wz > 0 && (1 << (wz - 1)) >= g.Lx) --wz;
+    int wx = 0;                                             // rows per CTA: about 256 threads
+    while ((1 << (wx + 1 + tx)) <= 256) ++wx;
+    // DDA_TILE_Y / DDA_TILE_Z / DDA_ROWS_X override the tile widths (tuning)
+    mv.logW_y = env_tile("DDA_TILE_Y", wy);
+    mv.logW_z = env_tile("DDA_TILE_Z", wz);
+    mv.logW_x = env_tile("DDA_ROWS_X", wx);
+    if ((1 << (mv.logW_y + ty)) > 1024) mv.logW_y = wy;
+    if ((1 << (mv.logW_z + tz)) > 512 || 3ull * col_elems(g.Lz, 1 << mv.logW_z) * elt > 220 * 1024) mv.logW_z = wz;
+    if ((1 << (mv.logW_x + tx)) > 512) mv.logW_x = wx;
 }
 
 template <typename T>
 int launch_matvec(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t st) {
-    constexpr int V = vals_per_thread<T>();
     const Geometry& g = mv.g;
     const int elt = sizeof(C<T>);
     const int dt = sizeof(T) == 8 ? 0 : 1;
     PassProfiler* pf = (mv.prof && mv.prof->on) ? mv.prof : nullptr;
+    const int ty = threads_log(g.Ly), tz = threads_log(g.Lz), tx = threads_log(g.Lx);
     int rc;
     {   // P1
         const int W = 1 << mv.logW_y;
-        const size_t sm = (size_t)g.Ly * (W + 1) * elt;
-        if ((rc = set_smem<T>((const void*)k_expand_yfwd<T, V>, sm))) return rc;
+        const size_t sm = (size_t)col_elems(g.Ly, W) * elt;
+        if ((rc = set_smem((const void*)k_p1<T>, sm))) return rc;
         dim3 grid((g.K + W - 1) / W, g.P, 3);
         if (pf) pf->begin(dt, 0, st);
-        k_expand_yfwd<T, V><<<grid, W * g.Ly / V, sm, st>>>(mv, p);
+        k_p1<T><<<grid, W << ty, sm, st>>>(mv, p);
         DDA_LAUNCH_CHECK("P1 expand + y-forward");
         if (pf) pf->end(st);
     }
+    const int64_t rows = 3LL * g.P * g.Ly;
+    const int R = 1 << mv.logW_x;
+    const size_t smx = (size_t)R * row_ld(g.Lx) * elt;
     {   // P2
-        const int W = 1 << mv.logW_x;
-        const size_t sm = (size_t)g.Lx * (W + 1) * elt;
-        if ((rc = set_smem<T>((const void*)k_xrows<T, V, false>, sm))) return rc;
-        const int64_t rows = 3LL * g.P * g.Ly;
+        if ((rc = set_smem((const void*)k_rows<T, false>, smx))) return rc;
         if (pf) pf->begin(dt, 1, st);
-        k_xrows<T, V, false><<<(unsigned)((rows + W - 1) / W), W * g.Lx / V, sm, st>>>(mv);
+        k_rows<T, false><<<(unsigned)((rows + R - 1) / R), R << tx, smx, st>>>(mv);
         DDA_LAUNCH_CHECK("P2 x-forward");
         if (pf) pf->end(st);
     }
     {   // P3
         const int W = 1 << mv.logW_z;
-        const size_t sm = 3 * (size_t)g.Lz * (W + 1) * elt;
-        if ((rc = set_smem<T>((const void*)k_zconv<T, V>, sm))) return rc;
-        dim3 grid(g.Lx / W > 0 ? g.Lx / W : 1, g.Ly);
+        const size_t sm = 3 * (size_t)col_elems(g.Lz, W) * elt;
+        if ((rc = set_smem((const void*)k_p3<T>, sm))) return rc;
+        dim3 grid((g.Lx + W - 1) / W, g.Ly);
         if (pf) pf->begin(dt, 2, st);
-        k_zconv<T, V><<<grid, W * g.Lz / V, sm, st>>>(mv);
+        k_p3<T><<<grid, W << tz, sm, st>>>(mv);
         DDA_LAUNCH_CHECK("P3 z-forward, spectrum product, z-inverse");
         if (pf) pf->end(st);
     }
     {   // P4
-        const int W = 1 << mv.logW_x;
-        const size_t sm = (size_t)g.Lx * (W + 1) * elt;
-        if ((rc = set_smem<T>((const void*)k_xrows<T, V, true>, sm))) return rc;
-        const int64_t rows = 3LL * g.P * g.Ly;
+        if ((rc = set_smem((const void*)k_rows<T, true>, smx))) return rc;
         if (pf) pf->begin(dt, 3, st);
-        k_xrows<T, V, true><<<(unsigned)((rows + W - 1) / W), W * g.Lx / V, sm, st>>>(mv);
+        k_rows<T, true><<<(unsigned)((rows + R - 1) / R), R << tx, smx, st>>>(mv);
         DDA_LAUNCH_CHECK("P4 x-inverse");
         if (pf) pf->end(st);
     }
     {   // P5
         const int W = 1 << mv.logW_y;
-        const size_t sm = (size_t)g.Ly * (W + 1) * elt;
-        if ((rc = set_smem<T>((const void*)k_yinv_compress<T, V>, sm))) return rc;
+        const size_t sm = (size_t)col_elems(g.Ly, W) * elt;
+        if ((rc = set_smem((const void*)k_p5<T>, sm))) return rc;
         dim3 grid((g.K + W - 1) / W, g.P, 3);
         if (pf) pf->begin(dt, 4, st);
-        k_yinv_compress<T, V><<<grid, W * g.Ly / V, sm, st>>>(mv, p, y);
+        k_p5<T><<<grid, W << ty, sm, st>>>(mv, p, y);
         DDA_LAUNCH_CHECK("P5 y-inverse + diagonal + compress");
         if (pf) pf->end(st);
     }

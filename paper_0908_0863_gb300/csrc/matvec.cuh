@@ -13,7 +13,7 @@ struct MatvecView {
     Geometry g;
     TargetView tv;
     const C<T>* ainv;   // [nmat][3] alpha^-1
-    const C<T>* spec;   // [6][Hz][Hy][Hx], scaled by 1/(Lx Ly Lz)
+    const C<T>* spec;   // [Hz][Hy][Hx][6], scaled by 1/(Lx Ly Lz)
     const C<T>* tw;     // twiddle table, kMaxLine entries
     C<T>* Ay;           // [3][P][Ly][K]
     C<T>* Bxy;          // [3][P][Ly][Lx]

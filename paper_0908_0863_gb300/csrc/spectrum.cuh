@@ -11,7 +11,7 @@ namespace dda {
 size_t spectrum_scratch_elems(const Geometry& g);
 
 // Section-1 tensor values -> fused T-to-c + DFT along x, y, z -> half
-// spectrum [6][Hz][Hy][Hx] scaled by 1/(Lx Ly Lz) (FP64 and complex64).
+// spectrum [Hz][Hy][Hx][6] scaled by 1/(Lx Ly Lz) (FP64 and complex64).
 int build_spectrum(const Geometry& g, double k, const double2* tw, double2* s0, double2* s1,
                    double2* spec64, float2* spec32, cudaStream_t st);
 
