@@ -21,7 +21,8 @@
 // time, W adjacent columns so that each load and store touches W
 // contiguous elements.  P3 parks the first two transformed components of a
 // column in shared memory so that the spectrum product happens in place
-// between the forward and the inverse transforms.
+// between the forward and the inverse transforms.  Each kernel is compiled
+// for every power-of-two line length (LOGN = 1..10) and picked at launch.
 #include <cstdlib>
 
 #include "fft_reg.cuh"
@@ -31,54 +32,53 @@ namespace dda {
 
 namespace {
 
-__device__ __forceinline__ int lines_threads_log(int logN) { return logN > 3 ? logN - 3 : 0; }
+__host__ __device__ constexpr int lines_log(int logN) { return logN > 3 ? logN - 3 : 0; }
+__host__ __device__ constexpr int points(int logN) { return logN < 3 ? (1 << logN) : 8; }
 
 // ---------------------------------------------------------------- P1
-template <typename T>
+template <typename T, int LOGN>
 __global__ void __launch_bounds__(1024) k_p1(MatvecView<T> mv, const C<T>* __restrict__ p) {
     if (mv.status && *mv.status) return;
     extern __shared__ unsigned char smem_raw[];
     C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
+    constexpr int logT = lines_log(LOGN), nv = points(LOGN);
     const Geometry& g = mv.g;
     const int logW = mv.logW_y, W = 1 << logW;
-    const int logN = ilog2_dev(g.Ly), logT = lines_threads_log(logN);
-    const int nv = g.Ly < 8 ? g.Ly : 8;
     const int w = threadIdx.x & (W - 1), t = threadIdx.x >> logW;
     const int i = blockIdx.x * W + w, kz = blockIdx.y, c = blockIdx.z;
     const C<T>* pc = p + (int64_t)c * g.nd;
+    const int64_t s0 = (int64_t)kz * g.J * g.K + i;
     C<T> v[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
         const int n = t + (m << logT);
         v[m] = mk<T>(0, 0);
         if (m < nv && n < g.J && i < g.K) {
-            const int64_t s = ((int64_t)kz * g.J + n) * g.K + i;
+            const int64_t s = s0 + (int64_t)n * g.K;
             if (occupied(mv.tv, s)) {
                 v[m] = pc[site_rank(mv.tv, s)];
                 if (mv.conj) v[m].y = -v[m].y;
             }
         }
     }
-    fft_regs<T, false>(v, sm, ColLayout{W}, w, t, logN, mv.tw);
+    fft_regs<T, false, LOGN>(v, sm, ColLayout{logW}, w, t, mv.tw);
     if (i < g.K) {
-        C<T>* out = mv.Ay + ((int64_t)c * g.P + kz) * g.Ly * g.K + i;
+        C<T>* out = mv.Ay + ((int64_t)c * g.P + kz) * ((int64_t)g.K << LOGN) + i;
 #pragma unroll
-        for (int m = 0; m < 8; ++m)
-            if (m < nv) out[(int64_t)(t + (m << logT)) * g.K] = v[m];
+        for (int m = 0; m < nv; ++m) out[(int64_t)(t + (m << logT)) * g.K] = v[m];
     }
 }
 
 // ------------------------------------------------------- P2 / P4 (rows)
 // Forward: rows of K inputs (Ay) -> Lx outputs (Bxy).  Inverse: rows of Lx
 // inputs (Bxy) -> first K outputs (Ay).  2^logW_x rows per CTA.
-template <typename T, bool INV>
+template <typename T, bool INV, int LOGN>
 __global__ void __launch_bounds__(512) k_rows(MatvecView<T> mv) {
     if (mv.status && *mv.status) return;
     extern __shared__ unsigned char smem_raw[];
     C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
+    constexpr int N = 1 << LOGN, logT = lines_log(LOGN), nv = points(LOGN);
     const Geometry& g = mv.g;
-    const int N = g.Lx, logN = ilog2_dev(N), logT = lines_threads_log(logN);
-    const int nv = N < 8 ? N : 8;
     const int t = threadIdx.x & ((1 << logT) - 1), wl = threadIdx.x >> logT;
     const int64_t nrows = 3LL * g.P * g.Ly;
     const int64_t row = ((int64_t)blockIdx.x << mv.logW_x) + wl;
@@ -92,12 +92,12 @@ __global__ void __launch_bounds__(512) k_rows(MatvecView<T> mv) {
         const int n = t + (m << logT);
         v[m] = (ok && m < nv && n < nin) ? src[n] : mk<T>(0, 0);
     }
-    fft_regs<T, INV>(v, sm, RowLayout{row_ld(N)}, wl, t, logN, mv.tw);
+    fft_regs<T, INV, LOGN>(v, sm, RowLayout<LOGN>{}, wl, t, mv.tw);
     if (ok) {
 #pragma unroll
-        for (int m = 0; m < 8; ++m) {
+        for (int m = 0; m < nv; ++m) {
             const int n = t + (m << logT);
-            if (m < nv && n < nout) dst[n] = v[m];
+            if (n < nout) dst[n] = v[m];
         }
     }
 }
@@ -131,15 +131,14 @@ __device__ __forceinline__ void load6(const C<T>* __restrict__ p, C<T> (&Y)[6]) 
     }
 }
 
-template <typename T>
+template <typename T, int LOGN>
 __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_p3(MatvecView<T> mv) {
     if (mv.status && *mv.status) return;
     extern __shared__ unsigned char smem_raw[];
     C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
+    constexpr int N = 1 << LOGN, logT = lines_log(LOGN), nv = points(LOGN);
     const Geometry& g = mv.g;
     const int logW = mv.logW_z, W = 1 << logW;
-    const int N = g.Lz, logN = ilog2_dev(N), logT = lines_threads_log(logN);
-    const int nv = N < 8 ? N : 8;
     const int w = threadIdx.x & (W - 1), t = threadIdx.x >> logW;
     // rows jy and Ly - jy read the same spectrum rows (mirror lookup): visit
     // them back to back (0, 1, Ly-1, 2, Ly-2, ...) so the second read hits L2
@@ -147,7 +146,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_p3(MatvecView<T
     const int jy = b == 0 ? 0 : ((b & 1) ? q2 : g.Ly - q2);
     const int ix = blockIdx.x * W + w;
     const bool ok = ix < g.Lx;
-    const ColLayout L{W};
+    const ColLayout L{logW};
     const int region = col_elems(N, W);
     C<T>* S0 = sm;
     C<T>* S1 = sm + region;
@@ -155,30 +154,20 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_p3(MatvecView<T
     const int64_t plane = (int64_t)g.Ly * g.Lx;   // stride between z planes of Bxy
     const int64_t comp = (int64_t)g.P * plane;    // stride between components
     C<T>* col = mv.Bxy + (int64_t)jy * g.Lx + (ok ? ix : 0);
-    C<T> v[8], nxt[8];
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-        const int n = t + (m << logT);
-        nxt[m] = (ok && m < nv && n < g.P) ? col[n * plane] : mk<T>(0, 0);
-    }
-    // forward z DFTs; X0, X1 parked in S0, S1 at the canonical points.  The
-    // loads of the next component are in flight while this one transforms.
+    C<T> v[8];
+    // forward z DFTs; X0, X1 parked in S0, S1 at the canonical points
+#pragma unroll 1
     for (int c = 0; c < 3; ++c) {
 #pragma unroll
-        for (int m = 0; m < 8; ++m) v[m] = nxt[m];
-        if (c < 2) {
-#pragma unroll
-            for (int m = 0; m < 8; ++m) {
-                const int n = t + (m << logT);
-                nxt[m] = (ok && m < nv && n < g.P) ? col[(c + 1) * comp + n * plane] : mk<T>(0, 0);
-            }
+        for (int m = 0; m < 8; ++m) {
+            const int n = t + (m << logT);
+            v[m] = (ok && m < nv && n < g.P) ? col[c * comp + n * plane] : mk<T>(0, 0);
         }
-        C<T>* S = c == 0 ? S0 : (c == 1 ? S1 : S2);
-        fft_regs<T, false>(v, S, L, w, t, logN, mv.tw);
+        C<T>* S = sm + c * region;
+        fft_regs<T, false, LOGN>(v, S, L, w, t, mv.tw);
         if (c < 2) {
 #pragma unroll
-            for (int m = 0; m < 8; ++m)
-                if (m < nv) S[L(w, t + (m << logT))] = v[m];
+            for (int m = 0; m < nv; ++m) S[L(w, t + (m << logT))] = v[m];
         }
     }
     // spectrum product (Eqs. 6-8) with the signed mirror lookup of Sec. 3
@@ -188,8 +177,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_p3(MatvecView<T
         const C<T>* spec = mv.spec + ((int64_t)my * g.Hx + (ok ? mx : 0)) * 6;
         const int64_t zstep = (int64_t)g.Hy * g.Hx * 6;
 #pragma unroll
-        for (int m = 0; m < 8; ++m) {
-            if (m >= nv) break;
+        for (int m = 0; m < nv; ++m) {
             const int n = t + (m << logT);
             const int mz = n <= N / 2 ? n : N - n, fz = n > N / 2;
             const int o = L(w, n);
@@ -210,54 +198,55 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_p3(MatvecView<T
         }
     }
     // inverse z DFTs, keeping k < P: component 2 from registers, then 1 and 0
+#pragma unroll 1
     for (int c = 2; c >= 0; --c) {
-        C<T>* S = c == 0 ? S0 : (c == 1 ? S1 : S2);
+        C<T>* S = sm + c * region;
         if (c < 2) {
 #pragma unroll
-            for (int m = 0; m < 8; ++m)
-                if (m < nv) v[m] = S[L(w, t + (m << logT))];
+            for (int m = 0; m < nv; ++m) v[m] = S[L(w, t + (m << logT))];
             __syncthreads();   // all parked values read before S is reused for exchanges
         }
-        fft_regs<T, true>(v, S, L, w, t, logN, mv.tw);
+        fft_regs<T, true, LOGN>(v, S, L, w, t, mv.tw);
         if (ok) {
 #pragma unroll
-            for (int m = 0; m < 8; ++m) {
+            for (int m = 0; m < nv; ++m) {
                 const int n = t + (m << logT);
-                if (m < nv && n < g.P) col[c * comp + n * plane] = v[m];
+                if (n < g.P) col[c * comp + n * plane] = v[m];
             }
         }
     }
+    (void)S1; (void)S2;
 }
 
 // ---------------------------------------------------------------- P5
-template <typename T>
+template <typename T, int LOGN>
 __global__ void __launch_bounds__(1024) k_p5(MatvecView<T> mv, const C<T>* __restrict__ p, C<T>* __restrict__ y) {
     if (mv.status && *mv.status) return;
     extern __shared__ unsigned char smem_raw[];
     C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
+    constexpr int logT = lines_log(LOGN), nv = points(LOGN);
     const Geometry& g = mv.g;
     const int logW = mv.logW_y, W = 1 << logW;
-    const int logN = ilog2_dev(g.Ly), logT = lines_threads_log(logN);
-    const int nv = g.Ly < 8 ? g.Ly : 8;
     const int w = threadIdx.x & (W - 1), t = threadIdx.x >> logW;
     const int i = blockIdx.x * W + w, kz = blockIdx.y, c = blockIdx.z;
     const bool ok = i < g.K;
-    const C<T>* in = mv.Ay + ((int64_t)c * g.P + kz) * g.Ly * g.K + (ok ? i : 0);
+    const C<T>* in = mv.Ay + ((int64_t)c * g.P + kz) * ((int64_t)g.K << LOGN) + (ok ? i : 0);
     C<T> v[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
         const int n = t + (m << logT);
         v[m] = (ok && m < nv) ? in[(int64_t)n * g.K] : mk<T>(0, 0);
     }
-    fft_regs<T, true>(v, sm, ColLayout{W}, w, t, logN, mv.tw);
+    fft_regs<T, true, LOGN>(v, sm, ColLayout{logW}, w, t, mv.tw);
     if (!ok) return;
     const C<T>* pc = p + (int64_t)c * g.nd;
     C<T>* yc = y + (int64_t)c * g.nd;
+    const int64_t s0 = (int64_t)kz * g.J * g.K + i;
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
+    for (int m = 0; m < nv; ++m) {
         const int n = t + (m << logT);
-        if (m >= nv || n >= g.J) continue;
-        const int64_t s = ((int64_t)kz * g.J + n) * g.K + i;
+        if (n >= g.J) continue;
+        const int64_t s = s0 + (int64_t)n * g.K;
         if (!occupied(mv.tv, s)) continue;
         const uint32_t r = site_rank(mv.tv, s);
         const C<T> a = mv.ainv[material(mv.tv, s, c) * 3 + c];
@@ -287,6 +276,83 @@ int set_smem(const void* fn, size_t bytes) {
     return 0;
 }
 
+// ------------------------------------------------- per-length launchers
+template <typename T, int LOGN>
+int launch_p1(const MatvecView<T>& mv, const C<T>* p, cudaStream_t st) {
+    const Geometry& g = mv.g;
+    const int W = 1 << mv.logW_y;
+    const size_t sm = (size_t)col_elems(1 << LOGN, W) * sizeof(C<T>);
+    if (int rc = set_smem((const void*)k_p1<T, LOGN>, sm)) return rc;
+    dim3 grid((g.K + W - 1) / W, g.P, 3);
+    k_p1<T, LOGN><<<grid, W << lines_log(LOGN), sm, st>>>(mv, p);
+    DDA_LAUNCH_CHECK("P1 expand + y-forward");
+    return 0;
+}
+
+template <typename T, bool INV, int LOGN>
+int launch_rows(const MatvecView<T>& mv, cudaStream_t st) {
+    const Geometry& g = mv.g;
+    const int64_t rows = 3LL * g.P * g.Ly;
+    const int R = 1 << mv.logW_x;
+    const size_t sm = (size_t)R * row_ld(1 << LOGN) * sizeof(C<T>);
+    if (int rc = set_smem((const void*)k_rows<T, INV, LOGN>, sm)) return rc;
+    k_rows<T, INV, LOGN><<<(unsigned)((rows + R - 1) / R), R << lines_log(LOGN), sm, st>>>(mv);
+    DDA_LAUNCH_CHECK(INV ? "P4 x-inverse" : "P2 x-forward");
+    return 0;
+}
+
+template <typename T, int LOGN>
+int launch_p3(const MatvecView<T>& mv, cudaStream_t st) {
+    const Geometry& g = mv.g;
+    const int W = 1 << mv.logW_z;
+    const size_t sm = 3 * (size_t)col_elems(1 << LOGN, W) * sizeof(C<T>);
+    if (int rc = set_smem((const void*)k_p3<T, LOGN>, sm)) return rc;
+    dim3 grid((g.Lx + W - 1) / W, g.Ly);
+    k_p3<T, LOGN><<<grid, W << lines_log(LOGN), sm, st>>>(mv);
+    DDA_LAUNCH_CHECK("P3 z-forward, spectrum product, z-inverse");
+    return 0;
+}
+
+template <typename T, int LOGN>
+int launch_p5(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t st) {
+    const Geometry& g = mv.g;
+    const int W = 1 << mv.logW_y;
+    const size_t sm = (size_t)col_elems(1 << LOGN, W) * sizeof(C<T>);
+    if (int rc = set_smem((const void*)k_p5<T, LOGN>, sm)) return rc;
+    dim3 grid((g.K + W - 1) / W, g.P, 3);
+    k_p5<T, LOGN><<<grid, W << lines_log(LOGN), sm, st>>>(mv, p, y);
+    DDA_LAUNCH_CHECK("P5 y-inverse + diagonal + compress");
+    return 0;
+}
+
+#define DDA_LOGN_SWITCH(logN, CALL)                    \
+    switch (logN) {                                    \
+        case 1: { constexpr int LN = 1; return CALL; } \
+        case 2: { constexpr int LN = 2; return CALL; } \
+        case 3: { constexpr int LN = 3; return CALL; } \
+        case 4: { constexpr int LN = 4; return CALL; } \
+        case 5: { constexpr int LN = 5; return CALL; } \
+        case 6: { constexpr int LN = 6; return CALL; } \
+        case 7: { constexpr int LN = 7; return CALL; } \
+        case 8: { constexpr int LN = 8; return CALL; } \
+        case 9: { constexpr int LN = 9; return CALL; } \
+        case 10: { constexpr int LN = 10; return CALL; } \
+        default: return fail(DDA_ERR_ARG, "line length out of range"); \
+    }
+
+template <typename T> int pass1(const MatvecView<T>& mv, const C<T>* p, cudaStream_t st) {
+    DDA_LOGN_SWITCH(ilog2(mv.g.Ly), (launch_p1<T, LN>(mv, p, st)))
+}
+template <typename T, bool INV> int pass_rows(const MatvecView<T>& mv, cudaStream_t st) {
+    DDA_LOGN_SWITCH(ilog2(mv.g.Lx), (launch_rows<T, INV, LN>(mv, st)))
+}
+template <typename T> int pass3(const MatvecView<T>& mv, cudaStream_t st) {
+    DDA_LOGN_SWITCH(ilog2(mv.g.Lz), (launch_p3<T, LN>(mv, st)))
+}
+template <typename T> int pass5(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t st) {
+    DDA_LOGN_SWITCH(ilog2(mv.g.Ly), (launch_p5<T, LN>(mv, p, y, st)))
+}
+
 }  // namespace
 
 template <typename T>
@@ -294,16 +360,16 @@ void configure_matvec(MatvecView<T>& mv) {
     const Geometry& g = mv.g;
     const int elt = sizeof(C<T>);
     const int ty = threads_log(g.Ly), tz = threads_log(g.Lz), tx = threads_log(g.Lx);
-    // strided passes: W adjacent columns (128-byte rows for y, 64 for z)
-    int wy = floor_log2(128 / elt);
+    // strided passes: W adjacent columns (64-byte rows)
+    int wy = floor_log2(64 / elt);
     while (wy > 0 && (1 << (wy + ty)) > 1024) --wy;
     while (wy > 0 && (1 << (wy - 1)) >= g.K) --wy;          // no wider than the lattice
     int wz = floor_log2(64 / elt);
     while (wz > 0 && (1 << (wz + tz)) > 512) --wz;
     while (wz > 0 && 3ull * col_elems(g.Lz, 1 << wz) * elt > 200 * 1024) --wz;
     while (wz > 0 && (1 << (wz - 1)) >= g.Lx) --wz;
-    int wx = 0;                                             // rows per CTA: about 256 threads
-    while ((1 << (wx + 1 + tx)) <= 256) ++wx;
+    int wx = 0;                                             // rows per CTA: about 128 threads
+    while ((1 << (wx + 1 + tx)) <= 128) ++wx;
     // DDA_TILE_Y / DDA_TILE_Z / DDA_ROWS_X override the tile widths (tuning)
     mv.logW_y = env_tile("DDA_TILE_Y", wy);
     mv.logW_z = env_tile("DDA_TILE_Z", wz);
@@ -315,59 +381,20 @@ void configure_matvec(MatvecView<T>& mv) {
 
 template <typename T>
 int launch_matvec(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t st) {
-    const Geometry& g = mv.g;
-    const int elt = sizeof(C<T>);
     const int dt = sizeof(T) == 8 ? 0 : 1;
     PassProfiler* pf = (mv.prof && mv.prof->on) ? mv.prof : nullptr;
-    const int ty = threads_log(g.Ly), tz = threads_log(g.Lz), tx = threads_log(g.Lx);
     int rc;
-    {   // P1
-        const int W = 1 << mv.logW_y;
-        const size_t sm = (size_t)col_elems(g.Ly, W) * elt;
-        if ((rc = set_smem((const void*)k_p1<T>, sm))) return rc;
-        dim3 grid((g.K + W - 1) / W, g.P, 3);
-        if (pf) pf->begin(dt, 0, st);
-        k_p1<T><<<grid, W << ty, sm, st>>>(mv, p);
-        DDA_LAUNCH_CHECK("P1 expand + y-forward");
-        if (pf) pf->end(st);
-    }
-    const int64_t rows = 3LL * g.P * g.Ly;
-    const int R = 1 << mv.logW_x;
-    const size_t smx = (size_t)R * row_ld(g.Lx) * elt;
-    {   // P2
-        if ((rc = set_smem((const void*)k_rows<T, false>, smx))) return rc;
-        if (pf) pf->begin(dt, 1, st);
-        k_rows<T, false><<<(unsigned)((rows + R - 1) / R), R << tx, smx, st>>>(mv);
-        DDA_LAUNCH_CHECK("P2 x-forward");
-        if (pf) pf->end(st);
-    }
-    {   // P3
-        const int W = 1 << mv.logW_z;
-        const size_t sm = 3 * (size_t)col_elems(g.Lz, W) * elt;
-        if ((rc = set_smem((const void*)k_p3<T>, sm))) return rc;
-        dim3 grid((g.Lx + W - 1) / W, g.Ly);
-        if (pf) pf->begin(dt, 2, st);
-        k_p3<T><<<grid, W << tz, sm, st>>>(mv);
-        DDA_LAUNCH_CHECK("P3 z-forward, spectrum product, z-inverse");
-        if (pf) pf->end(st);
-    }
-    {   // P4
-        if ((rc = set_smem((const void*)k_rows<T, true>, smx))) return rc;
-        if (pf) pf->begin(dt, 3, st);
-        k_rows<T, true><<<(unsigned)((rows + R - 1) / R), R << tx, smx, st>>>(mv);
-        DDA_LAUNCH_CHECK("P4 x-inverse");
-        if (pf) pf->end(st);
-    }
-    {   // P5
-        const int W = 1 << mv.logW_y;
-        const size_t sm = (size_t)col_elems(g.Ly, W) * elt;
-        if ((rc = set_smem((const void*)k_p5<T>, sm))) return rc;
-        dim3 grid((g.K + W - 1) / W, g.P, 3);
-        if (pf) pf->begin(dt, 4, st);
-        k_p5<T><<<grid, W << ty, sm, st>>>(mv, p, y);
-        DDA_LAUNCH_CHECK("P5 y-inverse + diagonal + compress");
-        if (pf) pf->end(st);
-    }
+    if (pf) pf->begin(dt, 0, st);
+    if ((rc = pass1<T>(mv, p, st))) return rc;
+    if (pf) { pf->end(st); pf->begin(dt, 1, st); }
+    if ((rc = pass_rows<T, false>(mv, st))) return rc;
+    if (pf) { pf->end(st); pf->begin(dt, 2, st); }
+    if ((rc = pass3<T>(mv, st))) return rc;
+    if (pf) { pf->end(st); pf->begin(dt, 3, st); }
+    if ((rc = pass_rows<T, true>(mv, st))) return rc;
+    if (pf) { pf->end(st); pf->begin(dt, 4, st); }
+    if ((rc = pass5<T>(mv, p, y, st))) return rc;
+    if (pf) pf->end(st);
     return 0;
 }
 
