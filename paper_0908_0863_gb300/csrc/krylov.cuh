@@ -10,6 +10,7 @@ namespace dda {
 enum Slot {
     S_RHO = 0, S_RHO_OLD, S_ALPHA, S_BETA, S_OMEGA, S_SIGMA,  // BiCG / BiCGSTAB
     S_DELTA, S_EPS, S_XI, S_RHOQ, S_GAMMA_OLD, S_THETA_OLD, S_ETA, S_F,  // QMR
+    S_NCP, S_NCQ,                                    // QMR: -(xi delta/eps), -(rho delta/eps)
     S_RHO_NEW, S_XI_NEW, S_TMP, S_NSLOTS
 };
 

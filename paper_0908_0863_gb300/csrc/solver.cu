@@ -25,20 +25,28 @@ namespace {
 
 // ------------------------------------------------------------- reductions
 template <typename T>
-struct DotAcc {  // FP64 accumulator fed by short FP32 (or FP64) partial sums
+struct DotAcc {
+    // Per-thread sum of one inner product.  FP64 data: plain FP64 sum.
+    // FP32 data: compensated (Kahan) FP32 sum, whose error does not grow
+    // with the number of terms, converted to FP64 once at the end; the block
+    // and grid reductions are FP64.  (FP64 adds inside the element loop cost
+    // more than the loads on this GPU and hold back the next loads.)
+    C<T> s, c;
     double2 hi;
-    C<T> lo;
-    int cnt;
-    __device__ __forceinline__ void init() { hi = make_double2(0.0, 0.0); lo = mk<T>(0, 0); cnt = 0; }
+    __device__ __forceinline__ void init() { s = mk<T>(0, 0); c = mk<T>(0, 0); hi = make_double2(0.0, 0.0); }
     __device__ __forceinline__ void add(C<T> v) {
-        lo = cadd<T>(lo, v);
-        if (++cnt == 8) flush();
+        if (sizeof(T) == 8) {
+            s = cadd<T>(s, v);
+        } else {
+            const C<T> y = csub<T>(v, c);
+            const C<T> t = cadd<T>(s, y);
+            c = csub<T>(csub<T>(t, s), y);
+            s = t;
+        }
     }
     __device__ __forceinline__ void flush() {
-        hi.x += (double)lo.x;
-        hi.y += (double)lo.y;
-        lo = mk<T>(0, 0);
-        cnt = 0;
+        hi.x = (double)s.x - (double)c.x;
+        hi.y = (double)s.y - (double)c.y;
     }
 };
 
@@ -106,9 +114,36 @@ template <typename T>
 __device__ __forceinline__ C<T> to_t(double2 a) { return mk<T>((T)a.x, (T)a.y); }
 template <typename T>
 __device__ __forceinline__ C<T> conjg(C<T> a) { return mk<T>(a.x, -a.y); }
+template <typename T>
+__device__ __forceinline__ C<T> norm2c(C<T> a) { return mk<T>(a.x * a.x + a.y * a.y, 0); }
 
-#define GRID_LOOP(i, n) \
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+// Grid-strided loop over n elements, four per thread per step: the loads of
+// all four are issued before any of them is used, so every thread keeps
+// several memory requests in flight.
+constexpr int kUnroll = 4;
+template <typename Load, typename Op>
+__device__ __forceinline__ void vec_loop(int64_t n, Load load, Op op) {
+    const int64_t S = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; base < n; base += kUnroll * S) {
+        decltype(load(base)) v[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int64_t i = base + u * S;
+            if (i < n) v[u] = load(i);
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int64_t i = base + u * S;
+            if (i < n) op(i, v[u]);
+        }
+    }
+}
+
+template <typename T> struct V1 { C<T> a; };
+template <typename T> struct V2 { C<T> a, b; };
+template <typename T> struct V3 { C<T> a, b, c; };
+template <typename T> struct V4 { C<T> a, b, c, d; };
+template <typename T> struct V6 { C<T> a, b, c, d, e, f; };
 
 // ---------------------------------------------------------------- common
 // r = b - r (r = A x on entry when has_x0), x = 0 otherwise r = b; rt = r or
@@ -119,22 +154,17 @@ __global__ void __launch_bounds__(kVecThreads) k_init(const C<T>* __restrict__ b
                                                       int has_x0, int conj_rt, double2* __restrict__ part) {
     DotAcc<T> nb, nr, rr;
     nb.init(); nr.init(); rr.init();
-    GRID_LOOP(i, n) {
-        const C<T> bi = b[i];
-        C<T> ri;
-        if (has_x0) {
-            ri = csub<T>(bi, r[i]);
-        } else {
-            ri = bi;
-            x[i] = mk<T>(0, 0);
-        }
-        r[i] = ri;
-        const C<T> ti = conj_rt ? conjg<T>(ri) : ri;
-        if (rt) rt[i] = ti;
-        nb.add(mk<T>(bi.x * bi.x + bi.y * bi.y, 0));
-        nr.add(mk<T>(ri.x * ri.x + ri.y * ri.y, 0));
-        rr.add(cmul<T>(conjg<T>(ti), ri));
-    }
+    vec_loop(n, [&](int64_t i) { return V2<T>{b[i], has_x0 ? r[i] : mk<T>(0, 0)}; },
+             [&](int64_t i, const V2<T>& q) {
+                 const C<T> ri = has_x0 ? csub<T>(q.a, q.b) : q.a;
+                 if (!has_x0) x[i] = mk<T>(0, 0);
+                 r[i] = ri;
+                 const C<T> ti = conj_rt ? conjg<T>(ri) : ri;
+                 if (rt) rt[i] = ti;
+                 nb.add(norm2c<T>(q.a));
+                 nr.add(norm2c<T>(ri));
+                 rr.add(cmul<T>(conjg<T>(ti), ri));
+             });
     nb.flush(); nr.flush(); rr.flush();
     double2 a[3] = {nb.hi, nr.hi, rr.hi};
     block_partials<3>(a, part);
@@ -165,32 +195,36 @@ __global__ void __launch_bounds__(kVecThreads) k_init_scalar(KState* st, const d
 }
 
 // partial dot products: kind 0 = a^H b, kind 1 = a^T b
-template <typename T, int NR>
-__global__ void __launch_bounds__(kVecThreads) k_dots(const KState* st, const C<T>* __restrict__ a0,
-                                                      const C<T>* __restrict__ b0, int kind0,
-                                                      const C<T>* __restrict__ a1, const C<T>* __restrict__ b1,
-                                                      int kind1, int64_t n, double2* __restrict__ part) {
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_dot1(const KState* st, const C<T>* __restrict__ a0,
+                                                      const C<T>* __restrict__ b0, int kind0, int64_t n,
+                                                      double2* __restrict__ part) {
     if (st->status != ST_RUN) return;
-    DotAcc<T> d0, d1;
-    d0.init(); d1.init();
-    GRID_LOOP(i, n) {
-        C<T> x0 = a0[i];
-        if (kind0 == 0) x0 = conjg<T>(x0);
-        d0.add(cmul<T>(x0, b0[i]));
-        if (NR > 1) {
-            C<T> x1 = a1[i];
-            if (kind1 == 0) x1 = conjg<T>(x1);
-            d1.add(cmul<T>(x1, b1[i]));
-        }
-    }
-    d0.flush(); d1.flush();
-    if (NR == 1) {
-        double2 a[1] = {d0.hi};
-        block_partials<1>(a, part);
-    } else {
-        double2 a[2] = {d0.hi, d1.hi};
-        block_partials<2>(a, part);
-    }
+    DotAcc<T> d0;
+    d0.init();
+    vec_loop(n, [&](int64_t i) { return V2<T>{a0[i], b0[i]}; },
+             [&](int64_t, const V2<T>& q) { d0.add(cmul<T>(kind0 == 0 ? conjg<T>(q.a) : q.a, q.b)); });
+    d0.flush();
+    double2 a[1] = {d0.hi};
+    block_partials<1>(a, part);
+}
+
+// partials t^H t and t^H s (BiCGSTAB's omega)
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_dot_ts(const KState* st, const C<T>* __restrict__ t,
+                                                        const C<T>* __restrict__ s, int64_t n,
+                                                        double2* __restrict__ part) {
+    if (st->status != ST_RUN) return;
+    DotAcc<T> tt, ts;
+    tt.init(); ts.init();
+    vec_loop(n, [&](int64_t i) { return V2<T>{t[i], s[i]}; },
+             [&](int64_t, const V2<T>& q) {
+                 tt.add(norm2c<T>(q.a));
+                 ts.add(cmul<T>(conjg<T>(q.a), q.b));
+             });
+    tt.flush(); ts.flush();
+    double2 a[2] = {tt.hi, ts.hi};
+    block_partials<2>(a, part);
 }
 
 // ---------------------------------------------------------------- BiCGSTAB
@@ -201,8 +235,11 @@ __global__ void __launch_bounds__(kVecThreads) k_bcs_p(const KState* st, const C
                                                        int64_t n, int first) {
     if (st->status != ST_RUN) return;
     const C<T> beta = to_t<T>(st->s[S_BETA]), omega = to_t<T>(st->s[S_OMEGA]);
-    GRID_LOOP(i, n) {
-        p[i] = first ? r[i] : cfma<T>(beta, csub<T>(p[i], cmul<T>(omega, v[i])), r[i]);
+    if (first) {
+        vec_loop(n, [&](int64_t i) { return V1<T>{r[i]}; }, [&](int64_t i, const V1<T>& q) { p[i] = q.a; });
+    } else {
+        vec_loop(n, [&](int64_t i) { return V3<T>{r[i], p[i], v[i]}; },
+                 [&](int64_t i, const V3<T>& q) { p[i] = cfma<T>(beta, csub<T>(q.b, cmul<T>(omega, q.c)), q.a); });
     }
 }
 
@@ -215,11 +252,12 @@ __global__ void __launch_bounds__(kVecThreads) k_bcs_s(const KState* st, const C
     const C<T> alpha = to_t<T>(st->s[S_ALPHA]);
     DotAcc<T> ns;
     ns.init();
-    GRID_LOOP(i, n) {
-        const C<T> si = csub<T>(r[i], cmul<T>(alpha, v[i]));
-        s[i] = si;
-        ns.add(mk<T>(si.x * si.x + si.y * si.y, 0));
-    }
+    vec_loop(n, [&](int64_t i) { return V2<T>{r[i], v[i]}; },
+             [&](int64_t i, const V2<T>& q) {
+                 const C<T> si = csub<T>(q.a, cmul<T>(alpha, q.b));
+                 s[i] = si;
+                 ns.add(norm2c<T>(si));
+             });
     ns.flush();
     double2 a[1] = {ns.hi};
     block_partials<1>(a, part);
@@ -237,19 +275,20 @@ __global__ void __launch_bounds__(kVecThreads) k_bcs_xr(const KState* st, C<T>* 
     if (status != ST_RUN && status != ST_HALF) return;
     const C<T> alpha = to_t<T>(st->s[S_ALPHA]), omega = to_t<T>(st->s[S_OMEGA]);
     if (status == ST_HALF) {
-        GRID_LOOP(i, n) x[i] = cfma<T>(alpha, p[i], x[i]);
+        vec_loop(n, [&](int64_t i) { return V2<T>{x[i], p[i]}; },
+                 [&](int64_t i, const V2<T>& q) { x[i] = cfma<T>(alpha, q.b, q.a); });
         return;
     }
     DotAcc<T> nr, rr;
     nr.init(); rr.init();
-    GRID_LOOP(i, n) {
-        const C<T> si = s[i];
-        x[i] = cfma<T>(omega, si, cfma<T>(alpha, p[i], x[i]));
-        const C<T> ri = csub<T>(si, cmul<T>(omega, t[i]));
-        r[i] = ri;
-        nr.add(mk<T>(ri.x * ri.x + ri.y * ri.y, 0));
-        rr.add(cmul<T>(conjg<T>(rt[i]), ri));
-    }
+    vec_loop(n, [&](int64_t i) { return V6<T>{x[i], p[i], s[i], t[i], rt[i], mk<T>(0, 0)}; },
+             [&](int64_t i, const V6<T>& q) {
+                 x[i] = cfma<T>(omega, q.c, cfma<T>(alpha, q.b, q.a));
+                 const C<T> ri = csub<T>(q.c, cmul<T>(omega, q.d));
+                 r[i] = ri;
+                 nr.add(norm2c<T>(ri));
+                 rr.add(cmul<T>(conjg<T>(q.e), ri));
+             });
     nr.flush(); rr.flush();
     double2 a[2] = {nr.hi, rr.hi};
     block_partials<2>(a, part);
@@ -303,14 +342,15 @@ __global__ void __launch_bounds__(kVecThreads) k_bicg_p(const KState* st, const 
     if (st->status != ST_RUN) return;
     const C<T> beta = to_t<T>(st->s[S_BETA]);
     const C<T> cbeta = conjg<T>(beta);
-    GRID_LOOP(i, n) {
-        if (first) {
-            p[i] = r[i];
-            pt[i] = rt[i];
-        } else {
-            p[i] = cfma<T>(beta, p[i], r[i]);
-            pt[i] = cfma<T>(cbeta, pt[i], rt[i]);
-        }
+    if (first) {
+        vec_loop(n, [&](int64_t i) { return V2<T>{r[i], rt[i]}; },
+                 [&](int64_t i, const V2<T>& q) { p[i] = q.a; pt[i] = q.b; });
+    } else {
+        vec_loop(n, [&](int64_t i) { return V4<T>{r[i], rt[i], p[i], pt[i]}; },
+                 [&](int64_t i, const V4<T>& q) {
+                     p[i] = cfma<T>(beta, q.c, q.a);
+                     pt[i] = cfma<T>(cbeta, q.d, q.b);
+                 });
     }
 }
 
@@ -326,15 +366,16 @@ __global__ void __launch_bounds__(kVecThreads) k_bicg_update(const KState* st, C
     const C<T> nalpha = mk<T>(-alpha.x, -alpha.y), ncalpha = mk<T>(-alpha.x, alpha.y);
     DotAcc<T> nr, rr;
     nr.init(); rr.init();
-    GRID_LOOP(i, n) {
-        x[i] = cfma<T>(alpha, p[i], x[i]);
-        const C<T> ri = cfma<T>(nalpha, q[i], r[i]);
-        const C<T> ti = cfma<T>(ncalpha, qt[i], rt[i]);
-        r[i] = ri;
-        rt[i] = ti;
-        nr.add(mk<T>(ri.x * ri.x + ri.y * ri.y, 0));
-        rr.add(cmul<T>(conjg<T>(ti), ri));
-    }
+    vec_loop(n, [&](int64_t i) { return V6<T>{x[i], p[i], q[i], qt[i], r[i], rt[i]}; },
+             [&](int64_t i, const V6<T>& u) {
+                 x[i] = cfma<T>(alpha, u.b, u.a);
+                 const C<T> ri = cfma<T>(nalpha, u.c, u.e);
+                 const C<T> ti = cfma<T>(ncalpha, u.d, u.f);
+                 r[i] = ri;
+                 rt[i] = ti;
+                 nr.add(norm2c<T>(ri));
+                 rr.add(cmul<T>(conjg<T>(ti), ri));
+             });
     nr.flush(); rr.flush();
     double2 a[2] = {nr.hi, rr.hi};
     block_partials<2>(a, part);
@@ -374,12 +415,13 @@ __global__ void __launch_bounds__(kVecThreads) k_qmr_vw(const KState* st, const 
     const T irho = (T)(1.0 / st->s[S_RHOQ].x), ixi = (T)(1.0 / st->s[S_XI].x);
     DotAcc<T> d;
     d.init();
-    GRID_LOOP(i, n) {
-        const C<T> vi = cscale<T>(vt[i], irho), wi = cscale<T>(wt[i], ixi);
-        v[i] = vi;
-        w[i] = wi;
-        d.add(cmul<T>(wi, vi));
-    }
+    vec_loop(n, [&](int64_t i) { return V2<T>{vt[i], wt[i]}; },
+             [&](int64_t i, const V2<T>& q) {
+                 const C<T> vi = cscale<T>(q.a, irho), wi = cscale<T>(q.b, ixi);
+                 v[i] = vi;
+                 w[i] = wi;
+                 d.add(cmul<T>(wi, vi));
+             });
     d.flush();
     double2 a[1] = {d.hi};
     block_partials<1>(a, part);
@@ -391,16 +433,16 @@ __global__ void __launch_bounds__(kVecThreads) k_qmr_pq(const KState* st, const 
                                                         const C<T>* __restrict__ w, C<T>* __restrict__ p,
                                                         C<T>* __restrict__ q, int64_t n, int first) {
     if (st->status != ST_RUN) return;
-    // cp = xi delta / eps, cq = rho delta / eps (stored negated in BETA/OMEGA slots? no: S_TMP pair)
-    const C<T> ncp = to_t<T>(st->s[S_SIGMA]), ncq = to_t<T>(st->s[S_OMEGA]);
-    GRID_LOOP(i, n) {
-        if (first) {
-            p[i] = v[i];
-            q[i] = w[i];
-        } else {
-            p[i] = cfma<T>(ncp, p[i], v[i]);
-            q[i] = cfma<T>(ncq, q[i], w[i]);
-        }
+    const C<T> ncp = to_t<T>(st->s[S_NCP]), ncq = to_t<T>(st->s[S_NCQ]);
+    if (first) {
+        vec_loop(n, [&](int64_t i) { return V2<T>{v[i], w[i]}; },
+                 [&](int64_t i, const V2<T>& u) { p[i] = u.a; q[i] = u.b; });
+    } else {
+        vec_loop(n, [&](int64_t i) { return V4<T>{v[i], w[i], p[i], q[i]}; },
+                 [&](int64_t i, const V4<T>& u) {
+                     p[i] = cfma<T>(ncp, u.c, u.a);
+                     q[i] = cfma<T>(ncq, u.d, u.b);
+                 });
     }
 }
 
@@ -415,14 +457,15 @@ __global__ void __launch_bounds__(kVecThreads) k_qmr_vtwt(const KState* st, cons
     const C<T> nbeta = mk<T>(-beta.x, -beta.y);
     DotAcc<T> a, b;
     a.init(); b.init();
-    GRID_LOOP(i, n) {
-        const C<T> vi = cfma<T>(nbeta, v[i], pt[i]);
-        const C<T> wi = cfma<T>(nbeta, w[i], wt[i]);
-        vt[i] = vi;
-        wt[i] = wi;
-        a.add(mk<T>(vi.x * vi.x + vi.y * vi.y, 0));
-        b.add(mk<T>(wi.x * wi.x + wi.y * wi.y, 0));
-    }
+    vec_loop(n, [&](int64_t i) { return V4<T>{pt[i], v[i], w[i], wt[i]}; },
+             [&](int64_t i, const V4<T>& u) {
+                 const C<T> vi = cfma<T>(nbeta, u.b, u.a);
+                 const C<T> wi = cfma<T>(nbeta, u.c, u.d);
+                 vt[i] = vi;
+                 wt[i] = wi;
+                 a.add(norm2c<T>(vi));
+                 b.add(norm2c<T>(wi));
+             });
     a.flush(); b.flush();
     double2 s[2] = {a.hi, b.hi};
     block_partials<2>(s, part);
@@ -437,22 +480,23 @@ __global__ void __launch_bounds__(kVecThreads) k_qmr_ds(const KState* st, const 
                                                         double2* __restrict__ part) {
     if (st->status != ST_RUN) return;
     const C<T> eta = to_t<T>(st->s[S_ETA]);
-    const T f = (T)st->s[S_F].x;
+    const T f = first ? (T)0 : (T)st->s[S_F].x;
     DotAcc<T> nr;
     nr.init();
-    GRID_LOOP(i, n) {
-        C<T> di = cmul<T>(eta, p[i]), si = cmul<T>(eta, pt[i]);
-        if (!first) {
-            di = cadd<T>(di, cscale<T>(d[i], f));
-            si = cadd<T>(si, cscale<T>(s[i], f));
-        }
-        d[i] = di;
-        s[i] = si;
-        x[i] = cadd<T>(x[i], di);
-        const C<T> ri = csub<T>(r[i], si);
-        r[i] = ri;
-        nr.add(mk<T>(ri.x * ri.x + ri.y * ri.y, 0));
-    }
+    vec_loop(n,
+             [&](int64_t i) {
+                 return V6<T>{p[i], pt[i], first ? mk<T>(0, 0) : d[i], first ? mk<T>(0, 0) : s[i], x[i], r[i]};
+             },
+             [&](int64_t i, const V6<T>& u) {
+                 const C<T> di = cadd<T>(cmul<T>(eta, u.a), cscale<T>(u.c, f));
+                 const C<T> si = cadd<T>(cmul<T>(eta, u.b), cscale<T>(u.d, f));
+                 d[i] = di;
+                 s[i] = si;
+                 x[i] = cadd<T>(u.e, di);
+                 const C<T> ri = csub<T>(u.f, si);
+                 r[i] = ri;
+                 nr.add(norm2c<T>(ri));
+             });
     nr.flush();
     double2 a[1] = {nr.hi};
     block_partials<1>(a, part);
@@ -475,8 +519,8 @@ __global__ void __launch_bounds__(kVecThreads) k_qmr_scalar(KState* st, const do
         st->s[S_DELTA] = delta;
         if (!first) {
             const double2 q = ddiv(delta, st->s[S_EPS]);
-            st->s[S_SIGMA] = make_double2(-xi * q.x, -xi * q.y);    // -(xi delta / eps)
-            st->s[S_OMEGA] = make_double2(-rho * q.x, -rho * q.y);  // -(rho delta / eps)
+            st->s[S_NCP] = make_double2(-xi * q.x, -xi * q.y);    // -(xi delta / eps)
+            st->s[S_NCQ] = make_double2(-rho * q.x, -rho * q.y);  // -(rho delta / eps)
         }
     } else if (step == 1) {
         st->matvecs += 1;
@@ -521,7 +565,8 @@ __global__ void __launch_bounds__(kVecThreads) k_norm2_c128(const double2* __res
                                                             double2* __restrict__ part) {
     DotAcc<double> d;
     d.init();
-    GRID_LOOP(i, n) d.add(make_double2(a[i].x * a[i].x + a[i].y * a[i].y, 0.0));
+    vec_loop(n, [&](int64_t i) { return V1<double>{a[i]}; },
+             [&](int64_t, const V1<double>& q) { d.add(norm2c<double>(q.a)); });
     d.flush();
     double2 s[1] = {d.hi};
     block_partials<1>(s, part);
@@ -531,11 +576,12 @@ __global__ void __launch_bounds__(kVecThreads) k_resid(const double2* __restrict
                                                        int64_t n, double2* __restrict__ part) {
     DotAcc<double> d;
     d.init();
-    GRID_LOOP(i, n) {
-        const double2 ri = make_double2(b[i].x - r[i].x, b[i].y - r[i].y);
-        r[i] = ri;
-        d.add(make_double2(ri.x * ri.x + ri.y * ri.y, 0.0));
-    }
+    vec_loop(n, [&](int64_t i) { return V2<double>{b[i], r[i]}; },
+             [&](int64_t i, const V2<double>& q) {
+                 const double2 ri = csub<double>(q.a, q.b);
+                 r[i] = ri;
+                 d.add(norm2c<double>(ri));
+             });
     d.flush();
     double2 s[1] = {d.hi};
     block_partials<1>(s, part);
@@ -547,19 +593,26 @@ __global__ void __launch_bounds__(kVecThreads) k_slot(KState* st, const double2*
     if (threadIdx.x == 0) st->s[slot] = s[0];
 }
 
-__global__ void k_to_c64(const double2* __restrict__ r, double scale, float2* __restrict__ out, int64_t n) {
-    GRID_LOOP(i, n) out[i] = make_float2((float)(r[i].x * scale), (float)(r[i].y * scale));
+__global__ void __launch_bounds__(kVecThreads) k_to_c64(const double2* __restrict__ r, double scale,
+                                                        float2* __restrict__ out, int64_t n) {
+    vec_loop(n, [&](int64_t i) { return V1<double>{r[i]}; },
+             [&](int64_t i, const V1<double>& q) {
+                 out[i] = make_float2((float)(q.a.x * scale), (float)(q.a.y * scale));
+             });
 }
 
-__global__ void k_axpy_c64(double2* __restrict__ x, double scale, const float2* __restrict__ d, int64_t n) {
-    GRID_LOOP(i, n) {
-        x[i].x += scale * (double)d[i].x;
-        x[i].y += scale * (double)d[i].y;
-    }
+__global__ void __launch_bounds__(kVecThreads) k_axpy_c64(double2* __restrict__ x, double scale,
+                                                          const float2* __restrict__ d, int64_t n) {
+    vec_loop(n, [&](int64_t i) { return V1<double>{make_double2((double)d[i].x, (double)d[i].y)}; },
+             [&](int64_t i, const V1<double>& q) {
+                 x[i].x += scale * q.a.x;
+                 x[i].y += scale * q.a.y;
+             });
 }
 
-__global__ void k_copy(double2* __restrict__ dst, const double2* __restrict__ src, int64_t n) {
-    GRID_LOOP(i, n) dst[i] = src[i];
+__global__ void __launch_bounds__(kVecThreads) k_copy(double2* __restrict__ dst, const double2* __restrict__ src,
+                                                      int64_t n) {
+    vec_loop(n, [&](int64_t i) { return V1<double>{src[i]}; }, [&](int64_t i, const V1<double>& q) { dst[i] = q.a; });
 }
 
 }  // namespace
@@ -588,7 +641,7 @@ int krylov_solve(int method, MatvecView<T> mv, KrylovWork<T>& ws, const C<T>* b,
         m0.status = nullptr;
         if ((rc = run_matvec<T>(m0, x, r, 0, st))) return rc;
     }
-    C<T>* rt = (method == DDA_QMR) ? v[1] : v[1];
+    C<T>* rt = v[1];  // shadow residual (BiCG, BiCGSTAB) or vt (QMR)
     k_init<T><<<G, B, 0, st>>>(b, x, r, rt, n, use_x0 ? 1 : 0, method == DDA_BICG ? 1 : 0, part);
     DDA_LAUNCH_CHECK("krylov init");
     k_init_scalar<<<1, B, 0, st>>>(ds, part, tol, method == DDA_QMR ? 1 : 0);
@@ -612,12 +665,12 @@ int krylov_solve(int method, MatvecView<T> mv, KrylovWork<T>& ws, const C<T>* b,
             C<T>*p = v[2], *vv = v[3], *s = v[4], *t = v[5];
             k_bcs_p<T><<<G, B, 0, st>>>(ds, r, p, vv, n, first);
             if ((rc = run_matvec<T>(mv, p, vv, 0, st))) break;
-            k_dots<T, 1><<<G, B, 0, st>>>(ds, rt, vv, 0, nullptr, nullptr, 0, n, part);
+            k_dot1<T><<<G, B, 0, st>>>(ds, rt, vv, 0, n, part);
             k_bcs_scalar<<<1, B, 0, st>>>(ds, part, 0);
             k_bcs_s<T><<<G, B, 0, st>>>(ds, r, vv, s, n, part);
             k_bcs_scalar<<<1, B, 0, st>>>(ds, part, 1);
             if ((rc = run_matvec<T>(mv, s, t, 0, st))) break;
-            k_dots<T, 2><<<G, B, 0, st>>>(ds, t, t, 0, t, s, 0, n, part);
+            k_dot_ts<T><<<G, B, 0, st>>>(ds, t, s, n, part);
             k_bcs_scalar<<<1, B, 0, st>>>(ds, part, 2);
             k_bcs_xr<T><<<G, B, 0, st>>>(ds, x, p, s, t, r, rt, n, part);
             k_bcs_scalar<<<1, B, 0, st>>>(ds, part, 3);
@@ -626,7 +679,7 @@ int krylov_solve(int method, MatvecView<T> mv, KrylovWork<T>& ws, const C<T>* b,
             k_bicg_p<T><<<G, B, 0, st>>>(ds, r, rt, p, pt, n, first);
             if ((rc = run_matvec<T>(mv, p, q, 0, st))) break;
             if ((rc = run_matvec<T>(mv, pt, qt, 1, st))) break;
-            k_dots<T, 1><<<G, B, 0, st>>>(ds, pt, q, 0, nullptr, nullptr, 0, n, part);
+            k_dot1<T><<<G, B, 0, st>>>(ds, pt, q, 0, n, part);
             k_bicg_scalar<<<1, B, 0, st>>>(ds, part, 0);
             k_bicg_update<T><<<G, B, 0, st>>>(ds, x, p, q, qt, r, rt, n, part);
             k_bicg_scalar<<<1, B, 0, st>>>(ds, part, 1);
@@ -637,7 +690,7 @@ int krylov_solve(int method, MatvecView<T> mv, KrylovWork<T>& ws, const C<T>* b,
             k_qmr_scalar<<<1, B, 0, st>>>(ds, part, 0, first);
             k_qmr_pq<T><<<G, B, 0, st>>>(ds, vv, w, p, q, n, first);
             if ((rc = run_matvec<T>(mv, p, pt, 0, st))) break;
-            k_dots<T, 1><<<G, B, 0, st>>>(ds, q, pt, 1, nullptr, nullptr, 0, n, part);
+            k_dot1<T><<<G, B, 0, st>>>(ds, q, pt, 1, n, part);
             k_qmr_scalar<<<1, B, 0, st>>>(ds, part, 1, first);
             if ((rc = run_matvec<T>(mv, q, wt, 0, st))) break;   // A^T q = A q
             k_qmr_vtwt<T><<<G, B, 0, st>>>(ds, pt, vv, w, vt, wt, n, part);
