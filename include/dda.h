@@ -219,6 +219,35 @@ int dda_solve(dda_ctx* ctx, const void* einc, void* p, int method, int precision
  */
 int dda_cross_sections(dda_ctx* ctx, const void* einc, const void* p, double* out, void* stream);
 
+/*
+ * Occupancy rank scan that allocates no device memory.  This entry point
+ * has no counterpart in the paper; it exists for callers that cannot call
+ * cudaMalloc: code whose device memory all belongs to another framework's
+ * pooling allocator, code that must not allocate once it is running (a
+ * latency-bound service loop), or a host thread that does not own the
+ * allocation policy of the process.  It computes what dda_init_lattice
+ * computes internally: word_rank[w] = number of occupied sites in words
+ * 0..w-1 of the occupancy bit field (so the compressed index of an occupied
+ * site s is word_rank[s >> 5] + popcount(bits[s >> 5] & ((1 << (s & 31)) - 1)))
+ * and *n_occupied = N_d.
+ *   occupancy_bits: device uint32[ceil(n_sites/32)], layout above; read
+ *                   only (padding bits past n_sites are ignored).
+ *   word_rank:      device uint32[ceil(n_sites/32)], written.
+ *   n_occupied:     device uint32[1], written.
+ * The scan keeps its per-block totals in a 16 KB array inside the library
+ * (a file-scope __device__ array, one per GPU, held until the process
+ * exits), which limits n_sites to 536,870,912 (4096 x 4096 x 32); larger
+ * inputs return DDA_ERR_ARG before any work is queued.  The first call on
+ * a device looks up that array's device address (once per device, with
+ * the device current); make that first call before any stream capture.
+ * All calls share the array: each call writes every entry it later reads,
+ * so no state carries over, but calls that overlap on the GPU (on
+ * different streams or from different threads) race on it -- order them
+ * on one stream.  Stream ordered; no synchronisation.
+ */
+int dda_occupancy_ranks_static(const uint32_t* occupancy_bits, int64_t n_sites, uint32_t* word_rank,
+                               uint32_t* n_occupied, void* stream);
+
 /* -------------------------------------------------------------- tracing */
 
 /*

@@ -16,7 +16,8 @@ from ._lib import (  # noqa: F401
     DDA_BICG, DDA_BICGSTAB, DDA_C64, DDA_C128, DDA_ERR_ARG, DDA_ERR_BREAKDOWN, DDA_ERR_CUDA, DDA_ERR_NAN,
     DDA_ERR_NOT_CONVERGED, DDA_ERR_OOM, DDA_FP64, DDA_MIXED, DDA_OK, DDA_QMR, EXPORTS, DDAError,
     dda_cross_sections, dda_free, dda_incident_field, dda_init_lattice, dda_last_error, dda_launch_count,
-    dda_matvec, dda_pack_composition, dda_pack_occupancy, dda_polarizability, dda_profile, dda_profile_read,
+    dda_matvec, dda_occupancy_ranks_static, dda_pack_composition, dda_pack_occupancy, dda_polarizability,
+    dda_profile, dda_profile_read,
     dda_query, dda_site_ranks, dda_solve, dda_tensor_spectrum, dda_unpack_composition, dda_unpack_occupancy,
     library_path, load,
 )

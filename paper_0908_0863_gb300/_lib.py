@@ -37,7 +37,7 @@ EXPORTS = (
     "dda_polarizability", "dda_pack_occupancy", "dda_unpack_occupancy", "dda_pack_composition",
     "dda_unpack_composition", "dda_init_lattice", "dda_free", "dda_query", "dda_site_ranks",
     "dda_tensor_spectrum", "dda_matvec", "dda_incident_field", "dda_solve", "dda_cross_sections",
-    "dda_profile", "dda_profile_read", "dda_launch_count", "dda_last_error",
+    "dda_profile", "dda_profile_read", "dda_launch_count", "dda_last_error", "dda_occupancy_ranks_static",
 )
 
 
@@ -88,6 +88,7 @@ def load(path: str | None = None):
     L.dda_incident_field.argtypes = [vp, vp, vp, vp, vp]
     L.dda_solve.argtypes = [vp, vp, vp, i32, i32, d, i32, i32, ctypes.POINTER(SolveInfo), vp]
     L.dda_cross_sections.argtypes = [vp, vp, vp, vp, vp]
+    L.dda_occupancy_ranks_static.argtypes = [vp, i64, vp, vp, vp]
     L.dda_profile.argtypes = [vp, i32]
     L.dda_profile_read.argtypes = [vp, vp, vp]
     L.dda_launch_count.argtypes = []
@@ -236,6 +237,13 @@ def dda_cross_sections(ctx, einc, p, stream=None):
     out = np.zeros(3)
     _check(load().dda_cross_sections(ctypes.c_void_p(ctx), _ptr(einc), _ptr(p), _ptr(out), _stream(stream)))
     return tuple(float(v) for v in out)
+
+
+def dda_occupancy_ranks_static(bits, n_sites, word_rank, n_occupied, stream=None):
+    """Rank scan of an occupancy bit field that allocates no device memory
+    (device tensors in, device tensors out; see include/dda.h)."""
+    _check(load().dda_occupancy_ranks_static(_ptr(bits), int(n_sites), _ptr(word_rank), _ptr(n_occupied),
+                                             _stream(stream)))
 
 
 def dda_profile(ctx, enable=True):

@@ -2,6 +2,8 @@
 // set-up and observables on it: occupancy / composition packing, the rank
 // (compressed index) of every site for the zero-storage vectors of Sec. 4,
 // the incident field and the cross-section sums.
+#include <mutex>
+
 #include "target.cuh"
 
 namespace dda {
@@ -310,4 +312,91 @@ int launch_cross_sections(const TargetView& tv, const Geometry& g, double k, con
     return 0;
 }
 
+// ------------------------------------- rank scan without device allocation
+// dda_occupancy_ranks_static runs the rank scan above with its per-block
+// totals in this file-scope array instead of caller or context memory, so
+// the call allocates nothing.  Every GPU that loads the library holds the
+// array (16 KB) until the process exits.  It bounds the input at
+// kStaticScanBlocks blocks of kScanTile words: 4096 * 4096 * 32 sites.
+constexpr int kStaticScanBlocks = 4096;
+__device__ __align__(256) uint32_t g_static_scan[kStaticScanBlocks];
+constexpr int64_t kStaticScanMaxSites = (int64_t)kStaticScanBlocks * kScanTile * 32;
+
+namespace {
+
+// the device address of g_static_scan, looked up once per device (with that
+// device current) on the first call made there
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+uint32_t* g_static_addr[kMaxDevices] = {};
+
+int static_scan_address(uint32_t** out) {
+    int dev = 0;
+    DDA_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(DDA_ERR_ARG, "dda_occupancy_ranks_static: device index >= 64");
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scan);
+        if (e != cudaSuccess) return cuda_fail(e, "dda_occupancy_ranks_static: cudaGetSymbolAddress");
+        g_static_addr[dev] = static_cast<uint32_t*>(p);
+    }
+    *out = g_static_addr[dev];
+    return 0;
+}
+
+// first scan step on the caller's (read-only) bit field: the padding bits
+// beyond n_sites in the last word are masked here instead of cleared
+__global__ void __launch_bounds__(kScanThreads) k_rank_local_masked(const uint32_t* __restrict__ occ, int64_t nwords,
+                                                                    uint32_t last_mask, uint32_t* __restrict__ rank,
+                                                                    uint32_t* __restrict__ block_sum) {
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPerThread;
+    uint32_t c[kScanPerThread];
+    uint32_t mine = 0;
+#pragma unroll
+    for (int t = 0; t < kScanPerThread; ++t) {
+        const int64_t w = base + t;
+        c[t] = w < nwords ? __popc(occ[w] & (w == nwords - 1 ? last_mask : 0xffffffffu)) : 0;
+        mine += c[t];
+    }
+    uint32_t tot;
+    uint32_t run = block_exclusive_scan(mine, &tot);
+#pragma unroll
+    for (int t = 0; t < kScanPerThread; ++t) {
+        if (base + t < nwords) rank[base + t] = run;
+        run += c[t];
+    }
+    if (threadIdx.x == 0) block_sum[blockIdx.x] = tot;
+}
+
+}  // namespace
+
 }  // namespace dda
+
+extern "C" int dda_occupancy_ranks_static(const uint32_t* occupancy_bits, int64_t n_sites, uint32_t* word_rank,
+                                          uint32_t* n_occupied, void* stream) {
+    using namespace dda;
+    if (n_sites <= 0) return fail(DDA_ERR_ARG, "dda_occupancy_ranks_static: n_sites must be > 0");
+    if (n_sites > kStaticScanMaxSites)
+        return fail(DDA_ERR_ARG, "dda_occupancy_ranks_static: n_sites above the static scratch limit of "
+                                 "536870912 sites (4096 blocks of 4096 words)");
+    if (!occupancy_bits || !word_rank || !n_occupied)
+        return fail(DDA_ERR_ARG, "dda_occupancy_ranks_static: NULL pointer");
+    uint32_t* scratch = nullptr;
+    if (int rc = static_scan_address(&scratch)) return rc;
+    const cudaStream_t st = as_stream(stream);
+    const int64_t nwords = (n_sites + 31) / 32;
+    const int64_t nblocks = (nwords + kScanTile - 1) / kScanTile;
+    const int rem = (int)(n_sites & 31);
+    const uint32_t last_mask = rem ? ((1u << rem) - 1u) : 0xffffffffu;
+    // every entry of the scratch that the later steps read is written first
+    // by this step, so nothing has to be cleared between calls
+    k_rank_local_masked<<<(unsigned)nblocks, kScanThreads, 0, st>>>(occupancy_bits, nwords, last_mask, word_rank,
+                                                                    scratch);
+    DDA_LAUNCH_CHECK("static rank local scan");
+    k_rank_blocks<<<1, kScanThreads, 0, st>>>(scratch, nblocks, n_occupied);
+    DDA_LAUNCH_CHECK("static rank block scan");
+    k_rank_add<<<grid_for(nwords, 256), 256, 0, st>>>(word_rank, nwords, scratch);
+    DDA_LAUNCH_CHECK("static rank offsets");
+    return DDA_OK;
+}
