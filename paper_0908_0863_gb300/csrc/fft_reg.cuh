@@ -13,6 +13,16 @@
 // The length is a template parameter, so every stride, stage count and
 // twiddle step is a compile-time constant.
 //
+// A thread may carry NL lines at once (the three polarisation components of
+// a z column): they share the twiddles, the addresses and the barriers of
+// every exchange, line l using the shared-memory region sm + l * region.
+//
+// Pruning (the zero-padding of Sec. 3): the matvec's forward transforms see
+// only the first half of each line nonzero (n < L/2 holds every input, since
+// L >= 2n - 1 for n lattice points), and its inverse transforms keep only the
+// first half of the outputs.  HALF_IN skips the work on the known zeros in
+// the first stage; HALF_OUT computes only outputs m < 4 in the last stage.
+//
 // Shared-memory addresses come from a layout functor (line w, point p):
 // RowLayout keeps each line contiguous (lines of the lattice that are
 // contiguous in memory, threads t-fastest); ColLayout keeps point-major
@@ -55,96 +65,187 @@ __device__ __forceinline__ C<T> twiddle(const C<T>* __restrict__ tw, int idx) {
     return t;
 }
 
-// v[1..7] *= w^r with w = exp(-+ 2 pi i k / (8 Ns)), k = index of the butterfly
-template <typename T, bool INV, int LOGNS>
-__device__ __forceinline__ void twiddle8(C<T> (&v)[8], int k, const C<T>* __restrict__ tw) {
-    constexpr int step = 10 - LOGNS - 3;
-    if (sizeof(T) == 4) {
-        const C<T> w1 = twiddle<T, INV>(tw, k << step);
-        const C<T> w2 = cmul<T>(w1, w1), w3 = cmul<T>(w2, w1), w4 = cmul<T>(w2, w2);
-        const C<T> w5 = cmul<T>(w4, w1), w6 = cmul<T>(w3, w3), w7 = cmul<T>(w4, w3);
-        v[1] = cmul<T>(v[1], w1); v[2] = cmul<T>(v[2], w2); v[3] = cmul<T>(v[3], w3);
-        v[4] = cmul<T>(v[4], w4); v[5] = cmul<T>(v[5], w5); v[6] = cmul<T>(v[6], w6);
-        v[7] = cmul<T>(v[7], w7);
+// radix-8 DFT with inputs 4..7 known to be zero: the first layer of dft8
+// degenerates to copies
+template <typename T, bool INV>
+__device__ __forceinline__ void dft8_half_in(C<T>* v) {
+    const T h = (T)0.70710678118654752440;
+    C<T> a[4] = {v[0], v[1], v[2], v[3]};
+    C<T> b[4] = {v[0], v[1], v[2], v[3]};
+    if (INV) {
+        b[1] = mk<T>((b[1].x - b[1].y) * h, (b[1].x + b[1].y) * h);
+        b[3] = mk<T>((-b[3].x - b[3].y) * h, (b[3].x - b[3].y) * h);
     } else {
+        b[1] = mk<T>((b[1].x + b[1].y) * h, (b[1].y - b[1].x) * h);
+        b[3] = mk<T>((b[3].y - b[3].x) * h, (-b[3].x - b[3].y) * h);
+    }
+    b[2] = rot90<T, INV>(b[2]);
+    dft4<T, INV>(a);
+    dft4<T, INV>(b);
 #pragma unroll
-        for (int r = 1; r < 8; ++r) v[r] = cmul<T>(v[r], twiddle<T, INV>(tw, (r * k) << step));
+    for (int r = 0; r < 4; ++r) {
+        v[2 * r] = a[r];
+        v[2 * r + 1] = b[r];
     }
 }
 
+// radix-8 DFT computing only outputs 0..3 (outputs 4..7 left unspecified)
+template <typename T, bool INV>
+__device__ __forceinline__ void dft8_half_out(C<T>* v) {
+    const T h = (T)0.70710678118654752440;
+    C<T> a[4], b[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        a[r] = cadd<T>(v[r], v[r + 4]);
+        b[r] = csub<T>(v[r], v[r + 4]);
+    }
+    if (INV) {
+        b[1] = mk<T>((b[1].x - b[1].y) * h, (b[1].x + b[1].y) * h);
+        b[3] = mk<T>((-b[3].x - b[3].y) * h, (b[3].x - b[3].y) * h);
+    } else {
+        b[1] = mk<T>((b[1].x + b[1].y) * h, (b[1].y - b[1].x) * h);
+        b[3] = mk<T>((b[3].y - b[3].x) * h, (-b[3].x - b[3].y) * h);
+    }
+    b[2] = rot90<T, INV>(b[2]);
+    // outputs 0, 2 from the even radix-4 (its outputs 0, 1), 1, 3 from the odd
+    const C<T> ca0 = cadd<T>(a[0], a[2]), ca2 = csub<T>(a[0], a[2]);
+    const C<T> ca1 = cadd<T>(a[1], a[3]), ca3 = rot90<T, INV>(csub<T>(a[1], a[3]));
+    const C<T> cb0 = cadd<T>(b[0], b[2]), cb2 = csub<T>(b[0], b[2]);
+    const C<T> cb1 = cadd<T>(b[1], b[3]), cb3 = rot90<T, INV>(csub<T>(b[1], b[3]));
+    v[0] = cadd<T>(ca0, ca1);
+    v[2] = cadd<T>(ca2, ca3);
+    v[1] = cadd<T>(cb0, cb1);
+    v[3] = cadd<T>(cb2, cb3);
+}
+
+// v[1..7] *= w^r with w = exp(-+ 2 pi i k / (8 Ns)) for each of NL lines
+template <typename T, bool INV, int LOGNS, int NL>
+__device__ __forceinline__ void twiddle8(C<T> (&v)[NL][8], int k, const C<T>* __restrict__ tw) {
+    constexpr int step = 10 - LOGNS - 3;
+    C<T> w[8];
+    if (sizeof(T) == 4) {
+        // FP32: one table load, the other six twiddles as its powers
+        // (relative error a few ulp, far below the FP32 transform's own)
+        w[1] = twiddle<T, INV>(tw, k << step);
+        w[2] = cmul<T>(w[1], w[1]); w[3] = cmul<T>(w[2], w[1]); w[4] = cmul<T>(w[2], w[2]);
+        w[5] = cmul<T>(w[4], w[1]); w[6] = cmul<T>(w[3], w[3]); w[7] = cmul<T>(w[4], w[3]);
+    } else {
+#pragma unroll
+        for (int r = 1; r < 8; ++r) w[r] = twiddle<T, INV>(tw, (r * k) << step);
+    }
+#pragma unroll
+    for (int l = 0; l < NL; ++l)
+#pragma unroll
+        for (int r = 1; r < 8; ++r) v[l][r] = cmul<T>(v[l][r], w[r]);
+}
+
 // read back the canonical points after an exchange
-template <typename T, int LOGN, class Layout>
-__device__ __forceinline__ void read_canonical(C<T> (&v)[8], const C<T>* __restrict__ sm, const Layout& L, int w,
-                                               int t) {
+template <typename T, int LOGN, int NL, class Layout>
+__device__ __forceinline__ void read_canonical(C<T> (&v)[NL][8], const C<T>* __restrict__ sm, int region,
+                                               const Layout& L, int w, int t) {
     constexpr int Tn = 1 << (LOGN - 3);
 #pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = sm[L(w, t + m * Tn)];
+    for (int m = 0; m < 8; ++m) {
+        const int o = L(w, t + m * Tn);
+#pragma unroll
+        for (int l = 0; l < NL; ++l) v[l][m] = sm[l * region + o];
+    }
 }
 
 // radix-8 stages from Ns = 2^LOGNS on; the last one leaves the outputs on
 // the canonical points
-template <typename T, bool INV, int LOGN, int LOGNS, class Layout>
+template <typename T, bool INV, int LOGN, int LOGNS, int NL, bool HALF_OUT, class Layout>
 struct Radix8Stages {
-    __device__ __forceinline__ static void run(C<T> (&v)[8], C<T>* __restrict__ sm, const Layout& L, int w, int t,
-                                               const C<T>* __restrict__ tw) {
+    __device__ __forceinline__ static void run(C<T> (&v)[NL][8], C<T>* __restrict__ sm, int region,
+                                               const Layout& L, int w, int t, const C<T>* __restrict__ tw) {
         constexpr int Ns = 1 << LOGNS;
         const int k = t & (Ns - 1);
-        twiddle8<T, INV, LOGNS>(v, k, tw);
-        dft8<T, INV>(v);
+        twiddle8<T, INV, LOGNS, NL>(v, k, tw);
         if constexpr (LOGNS + 3 < LOGN) {
+#pragma unroll
+            for (int l = 0; l < NL; ++l) dft8<T, INV>(v[l]);
             const int base = ((t >> LOGNS) << (LOGNS + 3)) + k;
 #pragma unroll
-            for (int r = 0; r < 8; ++r) sm[L(w, base + r * Ns)] = v[r];
+            for (int r = 0; r < 8; ++r) {
+                const int o = L(w, base + r * Ns);
+#pragma unroll
+                for (int l = 0; l < NL; ++l) sm[l * region + o] = v[l][r];
+            }
             __syncthreads();
-            read_canonical<T, LOGN>(v, sm, L, w, t);
+            read_canonical<T, LOGN, NL>(v, sm, region, L, w, t);
             __syncthreads();
-            Radix8Stages<T, INV, LOGN, LOGNS + 3, Layout>::run(v, sm, L, w, t, tw);
+            Radix8Stages<T, INV, LOGN, LOGNS + 3, NL, HALF_OUT, Layout>::run(v, sm, region, L, w, t, tw);
+        } else {
+#pragma unroll
+            for (int l = 0; l < NL; ++l) {
+                if (HALF_OUT) dft8_half_out<T, INV>(v[l]);
+                else dft8<T, INV>(v[l]);
+            }
         }
     }
 };
 
-// In-place DFT of one line held as v[m] = x[t + T m].  All threads of the
-// CTA must call it together (it synchronises when it exchanges).
-template <typename T, bool INV, int LOGN, class Layout>
-__device__ __forceinline__ void fft_regs(C<T> (&v)[8], C<T>* __restrict__ sm, const Layout& L, int w, int t,
-                                         const C<T>* __restrict__ tw) {
+// In-place DFT of NL lines held as v[l][m] = x_l[t + T m].  All threads of
+// the CTA must call it together (it synchronises when it exchanges).
+// HALF_IN: inputs m >= 4 are zero.  HALF_OUT: only outputs m < 4 are needed.
+template <typename T, bool INV, int LOGN, int NL, bool HALF_IN, bool HALF_OUT, class Layout>
+__device__ __forceinline__ void fft_lines(C<T> (&v)[NL][8], C<T>* __restrict__ sm, int region, const Layout& L,
+                                          int w, int t, const C<T>* __restrict__ tw) {
     if constexpr (LOGN <= 3) {  // a single stage: one thread holds the whole line
-        if constexpr (LOGN == 1) dft2<T, INV>(v);
-        else if constexpr (LOGN == 2) dft4<T, INV>(v);
-        else dft8<T, INV>(v);
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            if constexpr (LOGN == 1) dft2<T, INV>(v[l]);
+            else if constexpr (LOGN == 2) dft4<T, INV>(v[l]);
+            else dft8<T, INV>(v[l]);
+        }
     } else {
         constexpr int Tn = 1 << (LOGN - 3);
         constexpr int first = LOGN % 3;
         // first stage (Ns = 1, no twiddles): outputs of butterfly j, point r
         // go to j R + r
-        if constexpr (first == 1) {
-            // butterflies j = t + q T (q < 4) read x[j + 4T r] = v[q + 4r]
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                C<T> b[2] = {v[q], v[q + 4]};
-                dft2<T, INV>(b);
-                sm[L(w, (t + q * Tn) * 2)] = b[0];
-                sm[L(w, (t + q * Tn) * 2 + 1)] = b[1];
+        for (int l = 0; l < NL; ++l) {
+            C<T>* S = sm + l * region;
+            if constexpr (first == 1) {
+                // butterflies j = t + q T (q < 4) read x[j + 4T r] = v[q + 4r]
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    C<T> b[2] = {v[l][q], HALF_IN ? v[l][q] : v[l][q + 4]};
+                    if (!HALF_IN) dft2<T, INV>(b);
+                    S[L(w, (t + q * Tn) * 2)] = b[0];
+                    S[L(w, (t + q * Tn) * 2 + 1)] = b[1];
+                }
+            } else if constexpr (first == 2) {
+                // butterflies j = t + q T (q < 2) read x[j + 2T r] = v[q + 2r]
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    C<T> b[4] = {v[l][q], v[l][q + 2], HALF_IN ? mk<T>(0, 0) : v[l][q + 4],
+                                 HALF_IN ? mk<T>(0, 0) : v[l][q + 6]};
+                    dft4<T, INV>(b);
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) S[L(w, (t + q * Tn) * 4 + r)] = b[r];
+                }
+            } else {
+                if (HALF_IN) dft8_half_in<T, INV>(v[l]);
+                else dft8<T, INV>(v[l]);
+#pragma unroll
+                for (int r = 0; r < 8; ++r) S[L(w, t * 8 + r)] = v[l][r];
             }
-        } else if constexpr (first == 2) {
-            // butterflies j = t + q T (q < 2) read x[j + 2T r] = v[q + 2r]
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                C<T> b[4] = {v[q], v[q + 2], v[q + 4], v[q + 6]};
-                dft4<T, INV>(b);
-#pragma unroll
-                for (int r = 0; r < 4; ++r) sm[L(w, (t + q * Tn) * 4 + r)] = b[r];
-            }
-        } else {
-            dft8<T, INV>(v);
-#pragma unroll
-            for (int r = 0; r < 8; ++r) sm[L(w, t * 8 + r)] = v[r];
         }
         __syncthreads();
-        read_canonical<T, LOGN>(v, sm, L, w, t);
+        read_canonical<T, LOGN, NL>(v, sm, region, L, w, t);
         __syncthreads();
-        Radix8Stages<T, INV, LOGN, (first == 0 ? 3 : first), Layout>::run(v, sm, L, w, t, tw);
+        Radix8Stages<T, INV, LOGN, (first == 0 ? 3 : first), NL, HALF_OUT, Layout>::run(v, sm, region, L, w, t,
+                                                                                        tw);
     }
+}
+
+// one line: v[m] = x[t + T m]
+template <typename T, bool INV, int LOGN, bool HALF_IN, bool HALF_OUT, class Layout>
+__device__ __forceinline__ void fft_regs(C<T> (&v)[8], C<T>* __restrict__ sm, const Layout& L, int w, int t,
+                                         const C<T>* __restrict__ tw) {
+    C<T>(&vv)[1][8] = *reinterpret_cast<C<T>(*)[1][8]>(&v);
+    fft_lines<T, INV, LOGN, 1, HALF_IN, HALF_OUT>(vv, sm, 0, L, w, t, tw);
 }
 
 }  // namespace dda

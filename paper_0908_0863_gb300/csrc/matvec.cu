@@ -12,17 +12,19 @@
 // The line counts are the paper's pruned ones (Sec. 3, Table 2): forward
 // y 3[K x P], x 3[J'' x P], z all K'' x J''; the inverse mirrors them.  The
 // 1/(Lx Ly Lz) normalisation of the inverse DFT is folded into the stored
-// spectrum.
+// spectrum.  Within each line, forward transforms skip the work on the
+// zero half of their input and inverse transforms compute only the half of
+// the output that is kept.
 //
 // Every pass keeps its lines in registers (fft_reg.cuh): points are loaded
 // from global memory straight into the registers of the first DFT stage and
 // stored from the registers of the last, and only the exchanges between
 // stages use shared memory.  Strided lines (y, z) are processed W at a
 // time, W adjacent columns so that each load and store touches W
-// contiguous elements.  P3 parks the first two transformed components of a
-// column in shared memory so that the spectrum product happens in place
-// between the forward and the inverse transforms.  Each kernel is compiled
-// for every power-of-two line length (LOGN = 1..10) and picked at launch.
+// contiguous elements.  In P3 each thread carries the same column of all
+// three components, so the spectrum product happens in registers between
+// the forward and the inverse transforms.  Each kernel is compiled for every
+// power-of-two line length (LOGN = 1..10) and picked at launch.
 #include <cstdlib>
 
 #include "fft_reg.cuh"
@@ -34,6 +36,9 @@ namespace {
 
 __host__ __device__ constexpr int lines_log(int logN) { return logN > 3 ? logN - 3 : 0; }
 __host__ __device__ constexpr int points(int logN) { return logN < 3 ? (1 << logN) : 8; }
+// P3 keeps 3 x 8 complex values per thread: 512 threads fit the register
+// file for complex64, 256 for complex128
+template <typename T> __host__ __device__ constexpr int p3_max_threads() { return sizeof(T) == 4 ? 512 : 256; }
 
 // ---------------------------------------------------------------- P1
 template <typename T, int LOGN>
@@ -61,7 +66,7 @@ __global__ void __launch_bounds__(1024) k_p1(MatvecView<T> mv, const C<T>* __res
             }
         }
     }
-    fft_regs<T, false, LOGN>(v, sm, ColLayout{logW}, w, t, mv.tw);
+    fft_regs<T, false, LOGN, true, false>(v, sm, ColLayout{logW}, w, t, mv.tw);
     if (i < g.K) {
         C<T>* out = mv.Ay + ((int64_t)c * g.P + kz) * ((int64_t)g.K << LOGN) + i;
 #pragma unroll
@@ -92,7 +97,7 @@ __global__ void __launch_bounds__(512) k_rows(MatvecView<T> mv) {
         const int n = t + (m << logT);
         v[m] = (ok && m < nv && n < nin) ? src[n] : mk<T>(0, 0);
     }
-    fft_regs<T, INV, LOGN>(v, sm, RowLayout<LOGN>{}, wl, t, mv.tw);
+    fft_regs<T, INV, LOGN, !INV, INV>(v, sm, RowLayout<LOGN>{}, wl, t, mv.tw);
     if (ok) {
 #pragma unroll
         for (int m = 0; m < nv; ++m) {
@@ -132,7 +137,7 @@ __device__ __forceinline__ void load6(const C<T>* __restrict__ p, C<T> (&Y)[6]) 
 }
 
 template <typename T, int LOGN>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_p3(MatvecView<T> mv) {
+__global__ void __launch_bounds__(p3_max_threads<T>(), 1) k_p3(MatvecView<T> mv) {
     if (mv.status && *mv.status) return;
     extern __shared__ unsigned char smem_raw[];
     C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
@@ -148,28 +153,18 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_p3(MatvecView<T
     const bool ok = ix < g.Lx;
     const ColLayout L{logW};
     const int region = col_elems(N, W);
-    C<T>* S0 = sm;
-    C<T>* S1 = sm + region;
-    C<T>* S2 = sm + 2 * region;
     const int64_t plane = (int64_t)g.Ly * g.Lx;   // stride between z planes of Bxy
     const int64_t comp = (int64_t)g.P * plane;    // stride between components
     C<T>* col = mv.Bxy + (int64_t)jy * g.Lx + (ok ? ix : 0);
-    C<T> v[8];
-    // forward z DFTs; X0, X1 parked in S0, S1 at the canonical points
-#pragma unroll 1
-    for (int c = 0; c < 3; ++c) {
+    C<T> v[3][8];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
             const int n = t + (m << logT);
-            v[m] = (ok && m < nv && n < g.P) ? col[c * comp + n * plane] : mk<T>(0, 0);
+            v[c][m] = (ok && m < nv && n < g.P) ? col[c * comp + n * plane] : mk<T>(0, 0);
         }
-        C<T>* S = sm + c * region;
-        fft_regs<T, false, LOGN>(v, S, L, w, t, mv.tw);
-        if (c < 2) {
-#pragma unroll
-            for (int m = 0; m < nv; ++m) S[L(w, t + (m << logT))] = v[m];
-        }
-    }
+    fft_lines<T, false, LOGN, 3, true, false>(v, sm, region, L, w, t, mv.tw);
     // spectrum product (Eqs. 6-8) with the signed mirror lookup of Sec. 3
     {
         const int my = jy <= g.Ly / 2 ? jy : g.Ly - jy, fy = jy > g.Ly / 2;
@@ -180,7 +175,6 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_p3(MatvecView<T
         for (int m = 0; m < nv; ++m) {
             const int n = t + (m << logT);
             const int mz = n <= N / 2 ? n : N - n, fz = n > N / 2;
-            const int o = L(w, n);
             C<T> Y[6];
             if (ok) {
                 load6<T>(spec + mz * zstep, Y);
@@ -191,31 +185,22 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_p3(MatvecView<T
 #pragma unroll
             for (int q = 0; q < 6; ++q)
                 if (mirror_flip(q, fx, fy, fz)) { Y[q].x = -Y[q].x; Y[q].y = -Y[q].y; }
-            const C<T> X0 = S0[o], X1 = S1[o], X2 = v[m];
-            S0[o] = cfma<T>(Y[2], X2, cfma<T>(Y[1], X1, cmul<T>(Y[0], X0)));
-            S1[o] = cfma<T>(Y[4], X2, cfma<T>(Y[3], X1, cmul<T>(Y[1], X0)));
-            v[m] = cfma<T>(Y[5], X2, cfma<T>(Y[4], X1, cmul<T>(Y[2], X0)));
+            const C<T> X0 = v[0][m], X1 = v[1][m], X2 = v[2][m];
+            v[0][m] = cfma<T>(Y[2], X2, cfma<T>(Y[1], X1, cmul<T>(Y[0], X0)));
+            v[1][m] = cfma<T>(Y[4], X2, cfma<T>(Y[3], X1, cmul<T>(Y[1], X0)));
+            v[2][m] = cfma<T>(Y[5], X2, cfma<T>(Y[4], X1, cmul<T>(Y[2], X0)));
         }
     }
-    // inverse z DFTs, keeping k < P: component 2 from registers, then 1 and 0
-#pragma unroll 1
-    for (int c = 2; c >= 0; --c) {
-        C<T>* S = sm + c * region;
-        if (c < 2) {
+    fft_lines<T, true, LOGN, 3, false, true>(v, sm, region, L, w, t, mv.tw);
+    if (ok) {
 #pragma unroll
-            for (int m = 0; m < nv; ++m) v[m] = S[L(w, t + (m << logT))];
-            __syncthreads();   // all parked values read before S is reused for exchanges
-        }
-        fft_regs<T, true, LOGN>(v, S, L, w, t, mv.tw);
-        if (ok) {
+        for (int c = 0; c < 3; ++c)
 #pragma unroll
             for (int m = 0; m < nv; ++m) {
                 const int n = t + (m << logT);
-                if (n < g.P) col[c * comp + n * plane] = v[m];
+                if (n < g.P) col[c * comp + n * plane] = v[c][m];
             }
-        }
     }
-    (void)S1; (void)S2;
 }
 
 // ---------------------------------------------------------------- P5
@@ -237,7 +222,7 @@ __global__ void __launch_bounds__(1024) k_p5(MatvecView<T> mv, const C<T>* __res
         const int n = t + (m << logT);
         v[m] = (ok && m < nv) ? in[(int64_t)n * g.K] : mk<T>(0, 0);
     }
-    fft_regs<T, true, LOGN>(v, sm, ColLayout{logW}, w, t, mv.tw);
+    fft_regs<T, true, LOGN, false, true>(v, sm, ColLayout{logW}, w, t, mv.tw);
     if (!ok) return;
     const C<T>* pc = p + (int64_t)c * g.nd;
     C<T>* yc = y + (int64_t)c * g.nd;
@@ -365,7 +350,7 @@ void configure_matvec(MatvecView<T>& mv) {
     while (wy > 0 && (1 << (wy + ty)) > 1024) --wy;
     while (wy > 0 && (1 << (wy - 1)) >= g.K) --wy;          // no wider than the lattice
     int wz = floor_log2(64 / elt);
-    while (wz > 0 && (1 << (wz + tz)) > 512) --wz;
+    while (wz > 0 && (1 << (wz + tz)) > p3_max_threads<T>()) --wz;
     while (wz > 0 && 3ull * col_elems(g.Lz, 1 << wz) * elt > 200 * 1024) --wz;
     while (wz > 0 && (1 << (wz - 1)) >= g.Lx) --wz;
     int wx = 0;                                             // rows per CTA: about 128 threads
@@ -375,7 +360,8 @@ void configure_matvec(MatvecView<T>& mv) {
     mv.logW_z = env_tile("DDA_TILE_Z", wz);
     mv.logW_x = env_tile("DDA_ROWS_X", wx);
     if ((1 << (mv.logW_y + ty)) > 1024) mv.logW_y = wy;
-    if ((1 << (mv.logW_z + tz)) > 512 || 3ull * col_elems(g.Lz, 1 << mv.logW_z) * elt > 220 * 1024) mv.logW_z = wz;
+    if ((1 << (mv.logW_z + tz)) > p3_max_threads<T>() || 3ull * col_elems(g.Lz, 1 << mv.logW_z) * elt > 220 * 1024)
+        mv.logW_z = wz;
     if ((1 << (mv.logW_x + tx)) > 512) mv.logW_x = wx;
 }
 
