@@ -102,6 +102,27 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ------------------------------------------------------------ replicas
+def replica_incidence(rank):
+    """Replicas (weak scaling): rank r solves its own seeded incidence
+    direction with its two orthogonal polarisations; no data is exchanged."""
+    import synth
+    khat = synth.random_direction(SEED + rank)[0]
+    return khat, synth.orthogonal_polarisations(khat)
+
+
+def reduce_over_ranks(dist, ms, totals, device):
+    """Whole-job figures: the slowest rank's time and the sum of the work."""
+    if dist is None:
+        return ms, [float(v) for v in totals]
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tt = torch.tensor([float(v) for v in totals], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+    return float(t.item()), [float(v) for v in tt.tolist()]
+
+
 # --------------------------------------------------------------- our arm
 def run_ours(args):
     import numpy as np
@@ -128,9 +149,7 @@ def run_ours(args):
     mask_dev = torch.from_numpy(mask.reshape(-1)).to(dev)
     bits = torch.empty((nsites + 31) // 32, dtype=torch.int32, device=dev)
     alpha = dda.dda_polarizability([M_REFR], K_WAVE, "cmrr")
-    # replicas: each rank solves its own incidence direction (weak scaling)
-    khat = synth.random_direction(SEED + rank)[0]
-    pols = synth.orthogonal_polarisations(khat)
+    khat, pols = replica_incidence(rank)
     stream = torch.cuda.current_stream(dev)
 
     dda.dda_pack_occupancy(mask_dev, bits)
@@ -201,15 +220,7 @@ def run_ours(args):
     clocks = sampler.stop()
     launches = dda.dda_launch_count() - l0
     ms = ev0.elapsed_time(ev1)
-    ms_max = ms
-    totals = [stats["matvecs"], stats["solves"]]
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-        tt = torch.tensor(totals, dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-        totals = [float(v) for v in tt.tolist()]
+    ms_max, totals = reduce_over_ranks(dist, ms, [stats["matvecs"], stats["solves"]], dev)
     value = totals[0] / (ms_max / 1e3)
     solves_per_s = totals[1] / (ms_max / 1e3)
 
