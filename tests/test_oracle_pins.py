@@ -376,3 +376,48 @@ def test_oracle_build_is_idempotent():
     p1 = oracle.build()
     p2 = oracle.build()
     assert p1 == p2
+
+
+# ---------------------------------------------------------------- adjoint
+
+@pytest.mark.parametrize("rule", ["cm", "cmrr", "ldr"])
+def test_alpha_inverse_derivative_against_differences(rule):
+    from oracle import adjoint
+    k, kh, e0 = 0.5, (0.6, 0.0, 0.8), (0.8, 0.0, -0.6)
+    for eps in (1.7689 + 0.0266j, 4.0 + 2.0j):
+        h = 1e-6
+        fd = (adjoint.alpha_inverse(eps + h, k, rule, kh, e0) - adjoint.alpha_inverse(eps - h, k, rule, kh, e0)) / (2 * h)
+        fdi = (adjoint.alpha_inverse(eps + 1j * h, k, rule, kh, e0)
+               - adjoint.alpha_inverse(eps - 1j * h, k, rule, kh, e0)) / (2j * h)
+        d = adjoint.alpha_inverse_derivative(eps, k, rule, kh, e0)
+        assert abs(fd - d) < 1e-7 * abs(d) and abs(fdi - d) < 1e-7 * abs(d)   # holomorphic in eps
+
+
+@pytest.mark.parametrize("which", ["abs", "ext"])
+def test_adjoint_gradient_against_central_differences(which):
+    # brute force: perturb one dipole's permittivity, re-solve densely
+    from oracle import adjoint
+    g = synth.rng(11)
+    mask = synth.sphere(6, box=(6, 5, 6))
+    c = dda.coords_of(mask)
+    n = c.shape[0]
+    k, rule = 0.45, "cmrr"
+    eps = np.where(g.random(n) < 0.3, (2.0 + 0.5j) ** 2, (1.33 + 0.01j) ** 2)
+    E = dda.incident_field(c, k, [0, 0, 1], [1, 0, 0])
+    ainv = np.array([[adjoint.alpha_inverse(e, k, rule)] * 3 for e in eps])
+    dainv = np.array([[adjoint.alpha_inverse_derivative(e, k, rule)] * 3 for e in eps])
+    fn = adjoint.abs_gradient_dense if which == "abs" else adjoint.ext_gradient_dense
+    grad, _ = fn(c, ainv, dainv, k, E)
+    pick = 1 if which == "abs" else 0
+    h = 1e-6
+    for j in g.choice(n, size=6, replace=False):
+        num = []
+        for step in (h, 1j * h):
+            ep, em = eps.copy(), eps.copy()
+            ep[j] += step
+            em[j] -= step
+            cp = adjoint.cross_sections_for_eps(c, ep, k, E, rule)[pick]
+            cm = adjoint.cross_sections_for_eps(c, em, k, E, rule)[pick]
+            num.append((cp - cm) / (2 * h))
+        fd = num[0] + 1j * num[1]
+        assert abs(fd - grad[j]) <= 1e-6 * np.abs(grad).max()
