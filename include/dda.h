@@ -60,7 +60,10 @@ typedef enum {
 } dda_status;
 
 typedef enum { DDA_C128 = 0, DDA_C64 = 1 } dda_dtype;
-typedef enum { DDA_BICG = 0, DDA_BICGSTAB = 1, DDA_QMR = 2 } dda_method;
+/* Krylov schemes of Sec. 4: BiCG (two products per iteration), BiCGSTAB,
+ * QMR with coupled two-term recurrences (two products), and BiCG for
+ * complex-symmetric systems ("BiCG_sym", one product per iteration). */
+typedef enum { DDA_BICG = 0, DDA_BICGSTAB = 1, DDA_QMR = 2, DDA_BICG_SYM = 3 } dda_method;
 typedef enum { DDA_FP64 = 0, DDA_MIXED = 1 } dda_precision;
 typedef enum { DDA_POL_CM = 0, DDA_POL_CMRR = 1, DDA_POL_LDR = 2 } dda_polarizability_rule;
 
@@ -269,6 +272,51 @@ int dda_profile_read(dda_ctx* ctx, int64_t* counts, double* ms);
 
 /* Kernel launches issued by the library since it was loaded (all threads). */
 int64_t dda_launch_count(void);
+
+/* ------------------------------------------- observables and gradients */
+
+/*
+ * C_sca as the exact pair sum of the power the dipoles radiate (Draine
+ * 1988; the paper prints only the values, Table 7), independent of C_ext
+ * and C_abs: C_sca = 4 pi k sum_j [(2/3) k^3 |P_j|^2 + P_j^H sum_{l!=j}
+ * Im(G_jl) P_l], with G = diag(alpha^-1) - A the dipole field tensor.  For
+ * an exact solution C_ext = C_abs + C_sca (optical theorem).  Computed with
+ * two FP64 products, A P and A^H P.  p: host or device [3][N_d] complex128;
+ * out: host double[1].  Synchronises the stream.
+ */
+int dda_scattering_cross_section(dda_ctx* ctx, const void* p, double* out, void* stream);
+
+/*
+ * d(alpha^-1)/d eps for each material, eps = m^2, for the prescriptions of
+ * dda_polarizability (host only): -4 pi/(eps - 1)^2 for CM and CMRR, plus
+ * (b2 + b3 S) k^2 for LDR.  Same arguments and output layout as
+ * dda_polarizability ([n][3][2]); DDA_ERR_ARG for m = 1.
+ */
+int dda_polarizability_derivative(int n, const double* m, double k, int rule, const double* khat,
+                                  const double* e0, double* dalpha_inv_out);
+
+/*
+ * Gradient of C_ext (which = 0) or C_abs (which = 1) with respect to the
+ * complex permittivity eps_j of every dipole, g_j = dC/dRe(eps_j) +
+ * i dC/dIm(eps_j), the three axes of a dipole sharing eps_j.  Adjoint
+ * method: one extra solve with the same matrix (A^T = A, Sec. 3), of
+ * A mu = W conj(P) (C_abs, W = -Im(alpha^-1) - (2/3) k^3) or A mu = conj(E)
+ * (C_ext), then per dipole S = sum_c mu_c a'_c P_c and
+ *   C_abs: g = 4 pi k (sum_c -|P_c|^2 Im a'_c - 2 Re S) + i 4 pi k (sum_c -|P_c|^2 Re a'_c + 2 Im S)
+ *   C_ext: g = 4 pi k (-Im S) + i 4 pi k (-Re S)
+ * with a' from dalpha_inv.  Only P is needed from the forward solve; no
+ * Krylov iterate is stored.
+ *   einc: host or device [3][N_d] complex128 (read for which = 0 only).
+ *   p: host or device [3][N_d] complex128, the solution of A P = E_inc.
+ *   dalpha_inv: host [n_materials][3][2] (dda_polarizability_derivative).
+ *   method, precision, tol, max_iter: of the adjoint solve (dda_solve).
+ *   grad: host or device [N_d] complex128, compressed order.
+ *   info: host, may be NULL (the adjoint solve's).
+ * Returns the adjoint solve's status (DDA_OK, DDA_ERR_NOT_CONVERGED, ...);
+ * grad is written in every case but DDA_ERR_ARG / DDA_ERR_CUDA / DDA_ERR_OOM.
+ */
+int dda_gradient(dda_ctx* ctx, int which, const void* einc, const void* p, const double* dalpha_inv, int method,
+                 int precision, double tol, int max_iter, void* grad, dda_solve_info* info, void* stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* dda_last_error(void);

@@ -13,9 +13,10 @@ built (``__graft_entry__.build()``); there is no CPU fallback.
 from __future__ import annotations
 
 from ._lib import (  # noqa: F401
-    DDA_BICG, DDA_BICGSTAB, DDA_C64, DDA_C128, DDA_ERR_ARG, DDA_ERR_BREAKDOWN, DDA_ERR_CUDA, DDA_ERR_NAN,
-    DDA_ERR_NOT_CONVERGED, DDA_ERR_OOM, DDA_FP64, DDA_MIXED, DDA_OK, DDA_QMR, EXPORTS, DDAError,
-    dda_cross_sections, dda_free, dda_incident_field, dda_init_lattice, dda_last_error, dda_launch_count,
+    DDA_BICG, DDA_BICG_SYM, DDA_BICGSTAB, DDA_C64, DDA_C128, DDA_ERR_ARG, DDA_ERR_BREAKDOWN, DDA_ERR_CUDA,
+    DDA_ERR_NAN, DDA_ERR_NOT_CONVERGED, DDA_ERR_OOM, DDA_FP64, DDA_MIXED, DDA_OK, DDA_QMR, EXPORTS, DDAError,
+    dda_cross_sections, dda_free, dda_gradient, dda_incident_field, dda_init_lattice, dda_last_error,
+    dda_launch_count, dda_polarizability_derivative, dda_scattering_cross_section,
     dda_matvec, dda_occupancy_ranks_static, dda_pack_composition, dda_pack_occupancy, dda_polarizability,
     dda_profile, dda_profile_read,
     dda_query, dda_site_ranks, dda_solve, dda_tensor_spectrum, dda_unpack_composition, dda_unpack_occupancy,
@@ -70,6 +71,13 @@ class Lattice:
 
     def cross_sections(self, einc, p, stream=None):
         return dda_cross_sections(self.ctx, einc, p, stream)
+
+    def scattering_cross_section(self, p, stream=None):
+        return dda_scattering_cross_section(self.ctx, p, stream)
+
+    def gradient(self, which, einc, p, dalpha_inv, grad, method="bicgstab", precision="fp64", tol=1e-8,
+                 max_iter=1000, stream=None):
+        return dda_gradient(self.ctx, which, einc, p, dalpha_inv, grad, method, precision, tol, max_iter, stream)
 
     def site_ranks(self, rank, stream=None):
         dda_site_ranks(self.ctx, rank, stream)

@@ -24,11 +24,11 @@ DDA_ERR_BREAKDOWN = -5
 DDA_ERR_NAN = -6
 DDA_C128 = 0
 DDA_C64 = 1
-DDA_BICG, DDA_BICGSTAB, DDA_QMR = 0, 1, 2
+DDA_BICG, DDA_BICGSTAB, DDA_QMR, DDA_BICG_SYM = 0, 1, 2, 3
 DDA_FP64, DDA_MIXED = 0, 1
 DDA_POL_CM, DDA_POL_CMRR, DDA_POL_LDR = 0, 1, 2
 
-METHODS = {"bicg": DDA_BICG, "bicgstab": DDA_BICGSTAB, "qmr": DDA_QMR}
+METHODS = {"bicg": DDA_BICG, "bicgstab": DDA_BICGSTAB, "qmr": DDA_QMR, "bicg_sym": DDA_BICG_SYM}
 PRECISIONS = {"fp64": DDA_FP64, "mixed": DDA_MIXED}
 RULES = {"cm": DDA_POL_CM, "cmrr": DDA_POL_CMRR, "ldr": DDA_POL_LDR}
 
@@ -38,6 +38,7 @@ EXPORTS = (
     "dda_unpack_composition", "dda_init_lattice", "dda_free", "dda_query", "dda_site_ranks",
     "dda_tensor_spectrum", "dda_matvec", "dda_incident_field", "dda_solve", "dda_cross_sections",
     "dda_profile", "dda_profile_read", "dda_launch_count", "dda_last_error", "dda_occupancy_ranks_static",
+    "dda_scattering_cross_section", "dda_polarizability_derivative", "dda_gradient",
 )
 
 
@@ -89,6 +90,9 @@ def load(path: str | None = None):
     L.dda_solve.argtypes = [vp, vp, vp, i32, i32, d, i32, i32, ctypes.POINTER(SolveInfo), vp]
     L.dda_cross_sections.argtypes = [vp, vp, vp, vp, vp]
     L.dda_occupancy_ranks_static.argtypes = [vp, i64, vp, vp, vp]
+    L.dda_scattering_cross_section.argtypes = [vp, vp, vp, vp]
+    L.dda_polarizability_derivative.argtypes = [i32, vp, d, i32, vp, vp, vp]
+    L.dda_gradient.argtypes = [vp, i32, vp, vp, vp, i32, i32, d, i32, vp, ctypes.POINTER(SolveInfo), vp]
     L.dda_profile.argtypes = [vp, i32]
     L.dda_profile_read.argtypes = [vp, vp, vp]
     L.dda_launch_count.argtypes = []
@@ -237,6 +241,38 @@ def dda_cross_sections(ctx, einc, p, stream=None):
     out = np.zeros(3)
     _check(load().dda_cross_sections(ctypes.c_void_p(ctx), _ptr(einc), _ptr(p), _ptr(out), _stream(stream)))
     return tuple(float(v) for v in out)
+
+
+def dda_scattering_cross_section(ctx, p, stream=None) -> float:
+    out = np.zeros(1)
+    _check(load().dda_scattering_cross_section(ctypes.c_void_p(ctx), _ptr(p), _ptr(out), _stream(stream)))
+    return float(out[0])
+
+
+def dda_polarizability_derivative(m, k, rule="cmrr", khat=None, e0=None) -> np.ndarray:
+    """d(1/alpha)/d eps per material and axis, shape (n_materials, 3) complex128."""
+    m = np.atleast_1d(np.asarray(m, dtype=np.complex128))
+    n = m.size
+    out = np.zeros(n * 6)
+    kh = None if khat is None else np.ascontiguousarray(np.asarray(khat, dtype=np.float64))
+    ee = None if e0 is None else _c2(e0, 3)
+    _check(load().dda_polarizability_derivative(n, _ptr(_c2(m, n)), float(k), RULES.get(rule, rule),
+                                                _ptr(kh), _ptr(ee), _ptr(out)))
+    return (out[0::2] + 1j * out[1::2]).reshape(n, 3)
+
+
+def dda_gradient(ctx, which, einc, p, dalpha_inv, grad, method="bicgstab", precision="fp64", tol=1e-8,
+                 max_iter=1000, stream=None):
+    """Per-dipole d C / d eps (which: 'ext' or 'abs'); returns (status, info)."""
+    w = {"ext": 0, "abs": 1}.get(which, which)
+    da = _c2(np.asarray(dalpha_inv, dtype=np.complex128).reshape(-1), np.asarray(dalpha_inv).size)
+    info = SolveInfo()
+    code = load().dda_gradient(ctypes.c_void_p(ctx), int(w), _ptr(einc), _ptr(p), _ptr(da),
+                               METHODS.get(method, method), PRECISIONS.get(precision, precision), float(tol),
+                               int(max_iter), _ptr(grad), ctypes.byref(info), _stream(stream))
+    if code in (DDA_ERR_ARG, DDA_ERR_CUDA, DDA_ERR_OOM, DDA_ERR_NAN):
+        _check(code)
+    return code, info.as_dict()
 
 
 def dda_occupancy_ranks_static(bits, n_sites, word_rank, n_occupied, stream=None):

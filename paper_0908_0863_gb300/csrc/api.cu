@@ -1,7 +1,8 @@
 // C ABI of the library (include/dda.h): context set-up, the matvec, the
 // solves with FP64 or mixed-precision iterative refinement, and the
-// observables.  Host code only orchestrates; every step runs in the kernels
-// of matvec.cu, spectrum.cu, target.cu and krylov.cu.
+// observables and their permittivity gradients.  Host code only
+// orchestrates; every step runs in the kernels of matvec.cu, spectrum.cu,
+// target.cu and solver.cu.
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -82,6 +83,8 @@ struct dda_ctx {
     double2* x64 = nullptr;   // solution
     double2* b64 = nullptr;   // right-hand side
     double2* r64 = nullptr;   // outer residual
+    double2* aux[3] = {};     // adjoint / C_sca work vectors (P, right-hand side, mu)
+    double2* dainv64 = nullptr;  // d(alpha^-1)/d eps table of the last gradient call
     float2* b32 = nullptr;    // inner right-hand side
     float2* d32 = nullptr;    // inner solution
     KrylovWork<double> w64{};
@@ -243,6 +246,7 @@ int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occu
         probe.take<uint32_t>(ncw);
         probe.take<uint32_t>(rank_scratch_words(g.nwords));
         probe.take<double2>(3 * (size_t)n_materials);
+        probe.take<double2>(3 * (size_t)n_materials);
         probe.take<float2>(3 * (size_t)n_materials);
         probe.take<double2>(nspec);
         probe.take<float2>(nspec);
@@ -262,6 +266,7 @@ int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occu
     uint32_t* rscratch = a0.take<uint32_t>(rank_scratch_words(g.nwords));
     c->ainv64 = a0.take<double2>(3 * (size_t)n_materials);
     c->ainv32 = a0.take<float2>(3 * (size_t)n_materials);
+    c->dainv64 = a0.take<double2>(3 * (size_t)n_materials);
     c->spec64 = a0.take<double2>(nspec);
     c->spec32 = a0.take<float2>(nspec);
     c->tw64 = a0.take<double2>(kMaxLine);
@@ -327,11 +332,11 @@ int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occu
         if (rc) return bail(rc);
         if (e2 != cudaSuccess) return bail(cuda_fail(e2, "dda_init_lattice: spectrum build"));
     }
-    // ---- solver workspace: 13 complex128 + 12 complex64 vectors of 3 N_d
+    // ---- solver workspace: 16 complex128 + 12 complex64 vectors of 3 N_d
     {
         const size_t n = 3 * (size_t)g.nd;
         Arena probe;
-        for (int i = 0; i < 13; ++i) probe.take<double2>(n);
+        for (int i = 0; i < 16; ++i) probe.take<double2>(n);
         for (int i = 0; i < 12; ++i) probe.take<float2>(n);
         probe.take<double2>(kVecBlocks * kMaxRed);
         probe.take<double2>(kVecBlocks * kMaxRed);
@@ -344,6 +349,7 @@ int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occu
         c->x64 = a1.take<double2>(n);
         c->b64 = a1.take<double2>(n);
         c->r64 = a1.take<double2>(n);
+        for (int i = 0; i < 3; ++i) c->aux[i] = a1.take<double2>(n);
         c->w64.n = (int64_t)n;
         for (int i = 0; i < 10; ++i) c->w64.v[i] = a1.take<double2>(n);
         c->b32 = a1.take<float2>(n);
@@ -467,7 +473,7 @@ int dda_solve(dda_ctx* c, const void* einc, void* p, int method, int precision, 
     const auto t0 = std::chrono::steady_clock::now();
     if (int rc = check_ctx(c)) return rc;
     if (!einc || !p) return fail(DDA_ERR_ARG, "dda_solve: NULL einc or p");
-    if (method < DDA_BICG || method > DDA_QMR) return fail(DDA_ERR_ARG, "dda_solve: unknown method");
+    if (method < DDA_BICG || method > DDA_BICG_SYM) return fail(DDA_ERR_ARG, "dda_solve: unknown method");
     if (precision != DDA_FP64 && precision != DDA_MIXED) return fail(DDA_ERR_ARG, "dda_solve: unknown precision");
     if (!(tol > 0.0) || !std::isfinite(tol)) return fail(DDA_ERR_ARG, "dda_solve: tol must be finite and > 0");
     if (max_iter < 1) return fail(DDA_ERR_ARG, "dda_solve: max_iter must be >= 1");
@@ -555,6 +561,90 @@ int dda_solve(dda_ctx* c, const void* einc, void* p, int method, int precision, 
     if (status == DDA_ERR_NOT_CONVERGED) set_error("dda_solve: not converged within max_iter");
     else if (status == DDA_ERR_BREAKDOWN) set_error("dda_solve: Krylov breakdown");
     else if (status == DDA_ERR_NAN) set_error("dda_solve: non-finite value");
+    return status;
+}
+
+int dda_polarizability_derivative(int n, const double* m, double k, int rule, const double* khat, const double* e0,
+                                  double* out) {
+    if (n < 1 || !m || !out) return fail(DDA_ERR_ARG, "dda_polarizability_derivative: bad arguments");
+    if (rule < DDA_POL_CM || rule > DDA_POL_LDR)
+        return fail(DDA_ERR_ARG, "dda_polarizability_derivative: unknown rule");
+    if (rule == DDA_POL_LDR && (!khat || !e0))
+        return fail(DDA_ERR_ARG, "dda_polarizability_derivative: LDR needs khat and e0");
+    using cd = std::complex<double>;
+    double S = 0.0;
+    if (rule == DDA_POL_LDR) {
+        cd s = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            const cd t = khat[a] * cd(e0[2 * a], e0[2 * a + 1]);
+            s += t * t;
+        }
+        S = s.real();
+    }
+    const double b2 = 0.1648469, b3 = -1.7700004;
+    for (int q = 0; q < n; ++q) {
+        const cd mm(m[2 * q], m[2 * q + 1]);
+        const cd eps = mm * mm;
+        if (eps == cd(1.0, 0.0)) return fail(DDA_ERR_ARG, "dda_polarizability_derivative: m = 1 (no polarisability)");
+        // 1/alpha_CM = (4 pi/3)(eps + 2)/(eps - 1): derivative -4 pi/(eps - 1)^2;
+        // radiative reaction adds a constant; LDR adds (b1 + eps b2 + eps b3 S) k^2
+        cd d = -4.0 * M_PI / ((eps - 1.0) * (eps - 1.0));
+        if (rule == DDA_POL_LDR) d += (b2 + b3 * S) * k * k;
+        for (int c = 0; c < 3; ++c) {
+            out[(q * 3 + c) * 2] = d.real();
+            out[(q * 3 + c) * 2 + 1] = d.imag();
+        }
+    }
+    return DDA_OK;
+}
+
+int dda_scattering_cross_section(dda_ctx* c, const void* p, double* out, void* stream) {
+    if (int rc = check_ctx(c)) return rc;
+    if (!p || !out) return fail(DDA_ERR_ARG, "dda_scattering_cross_section: NULL argument");
+    cudaStream_t st = as_stream(stream);
+    const size_t bytes = 3 * c->g.nd * sizeof(double2);
+    double2* P = c->aux[0];
+    DDA_CUDA_TRY(cudaMemcpyAsync(P, p, bytes, cudaMemcpyDefault, st));
+    MatvecView<double> m = c->mv64;
+    m.status = nullptr;
+    m.conj = 0;
+    if (int rc = launch_matvec<double>(m, P, c->aux[1], st)) return rc;        // A P
+    m.conj = 1;
+    if (int rc = launch_matvec<double>(m, P, c->aux[2], st)) return rc;        // A^H P
+    if (int rc = launch_csca(target_view(c), c->g, c->k, c->ainv64, P, c->aux[1], c->aux[2], c->xsec, st)) return rc;
+    double2 h;
+    DDA_CUDA_TRY(cudaMemcpyAsync(&h, c->xsec + xsec_scratch_elems() - 1, sizeof(double2), cudaMemcpyDeviceToHost, st));
+    DDA_CUDA_TRY(cudaStreamSynchronize(st));
+    *out = 4.0 * M_PI * c->k * h.x;
+    return DDA_OK;
+}
+
+int dda_gradient(dda_ctx* c, int which, const void* einc, const void* p, const double* dalpha_inv, int method,
+                 int precision, double tol, int max_iter, void* grad, dda_solve_info* info, void* stream) {
+    if (int rc = check_ctx(c)) return rc;
+    if (which != 0 && which != 1) return fail(DDA_ERR_ARG, "dda_gradient: which must be 0 (C_ext) or 1 (C_abs)");
+    if (!p || !grad || !dalpha_inv || (which == 0 && !einc)) return fail(DDA_ERR_ARG, "dda_gradient: NULL argument");
+    for (int i = 0; i < 6 * c->g.nmat; ++i)
+        if (!std::isfinite(dalpha_inv[i])) return fail(DDA_ERR_NAN, "dda_gradient: non-finite derivative table");
+    cudaStream_t st = as_stream(stream);
+    const int64_t nd = c->g.nd;
+    const size_t bytes = 3 * nd * sizeof(double2);
+    double2 *P = c->aux[0], *rhs = c->aux[1], *mu = c->aux[2];
+    DDA_CUDA_TRY(cudaMemcpyAsync(P, p, bytes, cudaMemcpyDefault, st));
+    if (which == 0) DDA_CUDA_TRY(cudaMemcpyAsync(rhs, einc, bytes, cudaMemcpyDefault, st));
+    DDA_CUDA_TRY(cudaMemcpyAsync(c->dainv64, dalpha_inv, 3 * c->g.nmat * sizeof(double2), cudaMemcpyHostToDevice, st));
+    // adjoint right-hand side (in place for C_ext: conj(E))
+    if (int rc = launch_adjoint_rhs(target_view(c), c->g, c->k, which, c->ainv64, rhs, P, rhs, st)) return rc;
+    // one extra solve with A^T = A (the adjoint of a complex-symmetric system)
+    dda_solve_info inf{};
+    const int status = dda_solve(c, rhs, mu, method, precision, tol, max_iter, 0, &inf, stream);
+    if (info) *info = inf;
+    if (status == DDA_ERR_ARG || status == DDA_ERR_CUDA || status == DDA_ERR_OOM) return status;
+    const bool dev_out = is_device_ptr(grad);
+    double2* g = dev_out ? static_cast<double2*>(grad) : rhs;
+    if (int rc = launch_gradient(target_view(c), c->g, c->k, which, c->dainv64, P, mu, g, st)) return rc;
+    if (!dev_out) DDA_CUDA_TRY(cudaMemcpyAsync(grad, g, nd * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    DDA_CUDA_TRY(cudaStreamSynchronize(st));
     return status;
 }
 

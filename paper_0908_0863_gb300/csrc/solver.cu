@@ -381,14 +381,41 @@ __global__ void __launch_bounds__(kVecThreads) k_bicg_update(const KState* st, C
     block_partials<2>(a, part);
 }
 
-// step 0: alpha = rho / (pt^H q); step 1: end of iteration
-__global__ void __launch_bounds__(kVecThreads) k_bicg_scalar(KState* st, const double2* __restrict__ part, int step) {
+// BiCG for complex-symmetric A (Freund 1992; the paper's BiCG_sym, Sec. 4):
+// x += alpha p; r -= alpha q; partials ||r||^2 and the bilinear r^T r
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_cocg_update(const KState* st, C<T>* __restrict__ x,
+                                                             const C<T>* __restrict__ p, const C<T>* __restrict__ q,
+                                                             C<T>* __restrict__ r, int64_t n,
+                                                             double2* __restrict__ part) {
+    if (st->status != ST_RUN) return;
+    const C<T> alpha = to_t<T>(st->s[S_ALPHA]);
+    const C<T> nalpha = mk<T>(-alpha.x, -alpha.y);
+    DotAcc<T> nr, rr;
+    nr.init(); rr.init();
+    vec_loop(n, [&](int64_t i) { return V4<T>{x[i], p[i], q[i], r[i]}; },
+             [&](int64_t i, const V4<T>& u) {
+                 x[i] = cfma<T>(alpha, u.b, u.a);
+                 const C<T> ri = cfma<T>(nalpha, u.c, u.d);
+                 r[i] = ri;
+                 nr.add(norm2c<T>(ri));
+                 rr.add(cmul<T>(ri, ri));
+             });
+    nr.flush(); rr.flush();
+    double2 a[2] = {nr.hi, rr.hi};
+    block_partials<2>(a, part);
+}
+
+// step 0: alpha = rho / sigma (sigma = pt^H q for BiCG, p^T q for BiCG_sym);
+// step 1: end of iteration.  mv: products per iteration (2 or 1)
+__global__ void __launch_bounds__(kVecThreads) k_bicg_scalar(KState* st, const double2* __restrict__ part, int step,
+                                                             int mv) {
     if (st->status != ST_RUN) return;
     double2 s[2];
     final_sums<2>(part, s);
     if (threadIdx.x != 0) return;
     if (step == 0) {
-        st->matvecs += 2;
+        st->matvecs += mv;
         const double2 sigma = s[0];
         if (!finite2(sigma)) { st->status = ST_NAN; return; }
         if (is_zero(sigma)) { st->status = ST_BREAKDOWN; return; }
@@ -642,7 +669,9 @@ int krylov_solve(int method, MatvecView<T> mv, KrylovWork<T>& ws, const C<T>* b,
         if ((rc = run_matvec<T>(m0, x, r, 0, st))) return rc;
     }
     C<T>* rt = v[1];  // shadow residual (BiCG, BiCGSTAB) or vt (QMR)
-    k_init<T><<<G, B, 0, st>>>(b, x, r, rt, n, use_x0 ? 1 : 0, method == DDA_BICG ? 1 : 0, part);
+    // BiCG: shadow conj(r0); BiCG_sym: rho = r^T r = conj(r)^H r, the same start
+    const int conj_rt = (method == DDA_BICG || method == DDA_BICG_SYM) ? 1 : 0;
+    k_init<T><<<G, B, 0, st>>>(b, x, r, rt, n, use_x0 ? 1 : 0, conj_rt, part);
     DDA_LAUNCH_CHECK("krylov init");
     k_init_scalar<<<1, B, 0, st>>>(ds, part, tol, method == DDA_QMR ? 1 : 0);
     DDA_LAUNCH_CHECK("krylov init scalar");
@@ -680,9 +709,18 @@ int krylov_solve(int method, MatvecView<T> mv, KrylovWork<T>& ws, const C<T>* b,
             if ((rc = run_matvec<T>(mv, p, q, 0, st))) break;
             if ((rc = run_matvec<T>(mv, pt, qt, 1, st))) break;
             k_dot1<T><<<G, B, 0, st>>>(ds, pt, q, 0, n, part);
-            k_bicg_scalar<<<1, B, 0, st>>>(ds, part, 0);
+            k_bicg_scalar<<<1, B, 0, st>>>(ds, part, 0, 2);
             k_bicg_update<T><<<G, B, 0, st>>>(ds, x, p, q, qt, r, rt, n, part);
-            k_bicg_scalar<<<1, B, 0, st>>>(ds, part, 1);
+            k_bicg_scalar<<<1, B, 0, st>>>(ds, part, 1, 2);
+        } else if (method == DDA_BICG_SYM) {
+            // p = r + beta p (k_bcs_p with omega = 0), q = A p
+            C<T>*p = v[2], *q = v[3];
+            k_bcs_p<T><<<G, B, 0, st>>>(ds, r, p, p, n, first);
+            if ((rc = run_matvec<T>(mv, p, q, 0, st))) break;
+            k_dot1<T><<<G, B, 0, st>>>(ds, p, q, 1, n, part);
+            k_bicg_scalar<<<1, B, 0, st>>>(ds, part, 0, 1);
+            k_cocg_update<T><<<G, B, 0, st>>>(ds, x, p, q, r, n, part);
+            k_bicg_scalar<<<1, B, 0, st>>>(ds, part, 1, 1);
         } else {
             C<T>*vt = v[1], *wt = v[2], *vv = v[3], *w = v[4], *p = v[5], *q = v[6], *pt = v[7], *d = v[8],
                 *s = v[9];
@@ -698,7 +736,7 @@ int krylov_solve(int method, MatvecView<T> mv, KrylovWork<T>& ws, const C<T>* b,
             k_qmr_ds<T><<<G, B, 0, st>>>(ds, p, pt, d, s, x, r, n, first, part);
             k_qmr_scalar<<<1, B, 0, st>>>(ds, part, 3, first);
         }
-        note_launches(method == DDA_BICGSTAB ? 8 : method == DDA_BICG ? 5 : 9);
+        note_launches(method == DDA_BICGSTAB ? 8 : method == DDA_QMR ? 9 : 5);
         {
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) { rc = cuda_fail(e, "krylov iteration"); break; }

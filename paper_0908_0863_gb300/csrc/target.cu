@@ -220,6 +220,102 @@ __global__ void __launch_bounds__(kRedThreads) k_xsec_final(const double2* __res
     if (threadIdx.x == 0) *out = make_double2(se[0], sa[0]);
 }
 
+// C_sca as the exact pair sum of the radiated power,
+//   C_sca = 4 pi k sum_j [ (2/3) k^3 |P_j|^2 + P_j^H sum_{l != j} Im(G_jl) P_l ],
+// G = diag(alpha^-1) - A being the dipole field tensor.  With A complex
+// symmetric, Im(G) P = Im(alpha^-1) P - (A P - A^H P) / (2i), so the sum
+// needs the two products A P and A^H P and this per-site reduction.
+__global__ void __launch_bounds__(kRedThreads) k_csca_partial(TargetView tv, Geometry g, double k3,
+                                                              const double2* __restrict__ ainv,
+                                                              const double2* __restrict__ P,
+                                                              const double2* __restrict__ AP,
+                                                              const double2* __restrict__ AhP,
+                                                              double2* __restrict__ part) {
+    double acc = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < g.nsites; s += stride) {
+        if (!occupied(tv, s)) continue;
+        const uint32_t r = site_rank(tv, s);
+        for (int c = 0; c < 3; ++c) {
+            const int64_t i = c * g.nd + r;
+            const double2 p = P[i];
+            const double2 a = ainv[material(tv, s, c) * 3 + c];
+            const double2 d = make_double2(AP[i].x - AhP[i].x, AP[i].y - AhP[i].y);
+            // (A P - A^H P) / (2i) = (d.y - i d.x) / 2
+            const double2 q = make_double2(0.5 * d.y, -0.5 * d.x);
+            const double re = p.x * q.x + p.y * q.y;   // Re(conj(p) q)
+            acc += ((2.0 / 3.0) * k3 + a.y) * (p.x * p.x + p.y * p.y) - re;
+        }
+    }
+    __shared__ double sa[kRedThreads];
+    sa[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sa[threadIdx.x] += sa[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = make_double2(sa[0], 0.0);
+}
+
+// right-hand side of the adjoint solve A mu = b (A complex symmetric):
+//   C_abs: b_c = w_c conj(P_c), w_c = -Im(alpha^-1_c) - (2/3) k^3;   C_ext: b = conj(E)
+__global__ void k_adjoint_rhs(TargetView tv, Geometry g, double k3, int which, const double2* __restrict__ ainv,
+                              const double2* __restrict__ E, const double2* __restrict__ P,
+                              double2* __restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < g.nsites; s += stride) {
+        if (!occupied(tv, s)) continue;
+        const uint32_t r = site_rank(tv, s);
+        for (int c = 0; c < 3; ++c) {
+            const int64_t i = c * g.nd + r;
+            if (which == 1) {
+                const double w = -ainv[material(tv, s, c) * 3 + c].y - (2.0 / 3.0) * k3;
+                out[i] = make_double2(w * P[i].x, -w * P[i].y);
+            } else {
+                out[i] = make_double2(E[i].x, -E[i].y);
+            }
+        }
+    }
+}
+
+// per-dipole gradient g_j = dC/dRe(eps_j) + i dC/dIm(eps_j) from P and the
+// adjoint solution mu, with a'_jc = d(alpha^-1_jc)/d eps (the three axes of
+// a dipole share eps_j):
+//   S = sum_c mu_c a'_c P_c
+//   C_abs: 4 pi k ( sum_c -|P_c|^2 Im a'_c - 2 Re S ,  sum_c -|P_c|^2 Re a'_c + 2 Im S )
+//   C_ext: 4 pi k ( -Im S , -Re S )
+__global__ void k_gradient(TargetView tv, Geometry g, double k, int which, const double2* __restrict__ dainv,
+                           const double2* __restrict__ P, const double2* __restrict__ mu,
+                           double2* __restrict__ grad) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const double f = 4.0 * 3.14159265358979323846 * k;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < g.nsites; s += stride) {
+        if (!occupied(tv, s)) continue;
+        const uint32_t r = site_rank(tv, s);
+        double2 S = make_double2(0.0, 0.0);
+        double dx = 0.0, dy = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            const int64_t i = c * g.nd + r;
+            const double2 p = P[i], u = mu[i];
+            const double2 d = dainv[material(tv, s, c) * 3 + c];
+            const double2 t = cmul<double>(cmul<double>(u, d), p);
+            S.x += t.x;
+            S.y += t.y;
+            const double ap = p.x * p.x + p.y * p.y;
+            dx -= ap * d.y;
+            dy -= ap * d.x;
+        }
+        if (which == 1) {
+            dx -= 2.0 * S.x;
+            dy += 2.0 * S.y;
+        } else {
+            dx = -S.y;
+            dy = -S.x;
+        }
+        grad[r] = make_double2(f * dx, f * dy);
+    }
+}
+
 inline unsigned grid_for(int64_t n, int threads) {
     const int64_t b = (n + threads - 1) / threads;
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 32));
@@ -309,6 +405,31 @@ int launch_cross_sections(const TargetView& tv, const Geometry& g, double k, con
     DDA_LAUNCH_CHECK("cross-section partial sums");
     k_xsec_final<<<1, kRedThreads, 0, st>>>(scratch, (int)blocks, scratch + kRedBlocks);
     DDA_LAUNCH_CHECK("cross-section final sum");
+    return 0;
+}
+
+int launch_csca(const TargetView& tv, const Geometry& g, double k, const double2* ainv, const double2* P,
+                const double2* AP, const double2* AhP, double2* scratch, cudaStream_t st) {
+    const unsigned blocks =
+        (unsigned)std::min<int64_t>(kRedBlocks, std::max<int64_t>(1, (g.nsites + kRedThreads - 1) / kRedThreads));
+    k_csca_partial<<<blocks, kRedThreads, 0, st>>>(tv, g, k * k * k, ainv, P, AP, AhP, scratch);
+    DDA_LAUNCH_CHECK("C_sca partial sums");
+    k_xsec_final<<<1, kRedThreads, 0, st>>>(scratch, (int)blocks, scratch + kRedBlocks);
+    DDA_LAUNCH_CHECK("C_sca final sum");
+    return 0;
+}
+
+int launch_adjoint_rhs(const TargetView& tv, const Geometry& g, double k, int which, const double2* ainv,
+                       const double2* E, const double2* P, double2* out, cudaStream_t st) {
+    k_adjoint_rhs<<<grid_for(g.nsites, 256), 256, 0, st>>>(tv, g, k * k * k, which, ainv, E, P, out);
+    DDA_LAUNCH_CHECK("adjoint right-hand side");
+    return 0;
+}
+
+int launch_gradient(const TargetView& tv, const Geometry& g, double k, int which, const double2* dainv,
+                    const double2* P, const double2* mu, double2* grad, cudaStream_t st) {
+    k_gradient<<<grid_for(g.nsites, 256), 256, 0, st>>>(tv, g, k, which, dainv, P, mu, grad);
+    DDA_LAUNCH_CHECK("permittivity gradient");
     return 0;
 }
 

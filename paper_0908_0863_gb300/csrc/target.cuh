@@ -36,4 +36,14 @@ size_t xsec_scratch_elems();
 int launch_cross_sections(const TargetView& tv, const Geometry& g, double k, const double2* ainv,
                           const double2* E, const double2* P, double2* scratch, cudaStream_t st);
 
+// C_sca by the exact pair sum from P, A P and A^H P; the sum lands in
+// scratch[xsec_scratch_elems()-1].x (without the 4 pi k factor)
+int launch_csca(const TargetView& tv, const Geometry& g, double k, const double2* ainv, const double2* P,
+                const double2* AP, const double2* AhP, double2* scratch, cudaStream_t st);
+// which: 0 = C_ext, 1 = C_abs
+int launch_adjoint_rhs(const TargetView& tv, const Geometry& g, double k, int which, const double2* ainv,
+                       const double2* E, const double2* P, double2* out, cudaStream_t st);
+int launch_gradient(const TargetView& tv, const Geometry& g, double k, int which, const double2* dainv,
+                    const double2* P, const double2* mu, double2* grad, cudaStream_t st);
+
 }  // namespace dda
