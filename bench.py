@@ -27,6 +27,7 @@ import argparse
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -285,6 +286,37 @@ def algorithmic_bytes(n, nd, esize):
             "matvec_min": 3 * V + 4 * A + T}
 
 
+def kernel_sources_hash():
+    """First 16 hex digits of the SHA-256 of the matvec kernel sources."""
+    import hashlib
+    h = hashlib.sha256()
+    for rel in ("paper_0908_0863_gb300/csrc/matvec.cu", "paper_0908_0863_gb300/csrc/fft_reg.cuh"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel):
+    """DRAM bytes per launch of `kernel` at the bench size, from the ncu
+    summaries under profiles/ ("traffic-bench:" lines), or None when no
+    summary covers it or the kernel sources changed since the capture."""
+    pdir = os.path.join(ROOT, "profiles")
+    try:
+        names = sorted(os.listdir(pdir))
+    except OSError:
+        return None
+    want = kernel_sources_hash()
+    pat = re.compile(r"traffic-bench: kernel=(.+?) bytes=(\d+) sources=([0-9a-f]+)")
+    for name in names:
+        if not name.endswith(".md"):
+            continue
+        with open(os.path.join(pdir, name)) as f:
+            for m in pat.finditer(f.read()):
+                if m.group(1) == kernel and m.group(3) == want:
+                    return {"bytes": int(m.group(2)), "source": f"profiles/{name}"}
+    return None
+
+
 def extras(args, dda, torch, dev, shape, bits, alpha, nd, pass_ms, khat, pols):
     """Roofline of the dominant kernel, per-precision matvec rates, FP64 solve."""
     out = {}
@@ -308,8 +340,12 @@ def extras(args, dda, torch, dev, shape, bits, alpha, nd, pass_ms, khat, pols):
         ab = algorithmic_bytes(args.edge, nd, esize)[f"P{q + 1}"]
         avg = t / c
         achieved = ab / (avg / 1e3) / 1e9
-        out["roofline"] = {"bound": "hbm", "kernel": f"P{q + 1} ({dt})", "achieved": achieved, "peak": hbm,
-                           "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+        kernel = f"P{q + 1} ({dt})"
+        traffic = measured_traffic(kernel) if args.edge == N_EDGE else None
+        out["roofline"] = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": hbm,
+                           "unit": "GB/s", "frac": achieved / hbm,
+                           "traffic": traffic["bytes"] if traffic else None,
+                           "traffic_source": traffic["source"] if traffic else None,
                            "algorithmic_bytes": ab, "avg_ms": avg, "launches": c, "peak_source": peak_note}
     # separate device-timed matvec loops (outside the timed region)
     ctx = dda.dda_init_lattice(shape, bits, None, 1, alpha, K_WAVE)
