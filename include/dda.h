@@ -29,10 +29,17 @@
  * Streams: every call takes a cudaStream_t as void* (NULL = legacy default
  *   stream) and is stream ordered; a context serves one stream at a time
  *   (its scratch is shared by all its calls).
+ * Batches: the *_batch entry points take nb right-hand sides that share the
+ *   context's spectrum, stored back to back: [nb][3][N_d].  One launch of
+ *   each matvec pass covers the whole batch (the batch extension of the
+ *   paper's plan reuse, Sec. 5).
  * Ownership: the caller owns every buffer it passes; the context owns its
  *   device state (bit fields, ranks, Green's-tensor spectra, scratch and
- *   solver workspace), all allocated by dda_init_lattice and released by
- *   dda_free.  No other call allocates device memory.
+ *   solver workspace), allocated by dda_init_lattice (workspace for one
+ *   right-hand side in both precisions) and released by dda_free.  The
+ *   workspace grows, once, when a call first needs more right-hand sides
+ *   (or the first batch in a precision) than it holds; dda_reserve makes
+ *   that allocation ahead of time.  No other call allocates device memory.
  * Errors: every int-returning call returns a dda_status; on failure
  *   dda_last_error() gives a message (thread local).  Arguments are
  *   checked before any work is queued; a failed call leaves outputs
@@ -183,6 +190,26 @@ int dda_tensor_spectrum(const dda_ctx* ctx, void* out, int dtype, void* stream);
 int dda_matvec(dda_ctx* ctx, const void* p, void* y, int dtype, void* stream);
 
 /*
+ * y_b = A p_b for nb right-hand sides (1 <= nb <= 4096) at once: p, y are
+ * device [nb][3][N_d] complex of the given dtype and may not overlap.  Every
+ * pass of dda_matvec runs once over the batch (in chunks when the work
+ * space holds fewer complex128 slots than nb), reading the shared spectrum
+ * once per tile for all right-hand sides.  Results equal nb calls of
+ * dda_matvec bit for bit.  May grow the workspace (see Ownership).
+ */
+int dda_matvec_batch(dda_ctx* ctx, int nb, const void* p, void* y, int dtype, void* stream);
+
+/*
+ * Grow the solve workspace to hold nb right-hand sides (1 <= nb <= 4096)
+ * for solves of the given precision, so that later calls with up to nb
+ * right-hand sides allocate nothing.  Per right-hand side it holds 3
+ * complex128 vectors of 3 N_d, one complex64 matvec work slot (2 for the
+ * first) and 10 complex128 (DDA_FP64) or 12 complex64 (DDA_MIXED) Krylov
+ * vectors; dda_query reports the total.  DDA_ERR_OOM when it does not fit.
+ */
+int dda_reserve(dda_ctx* ctx, int nb, int precision);
+
+/*
  * Incident plane wave at the occupied sites: E_c = e0_c exp(i k khat . r),
  * r = (i, j, k) (phase origin at site 0).  khat: host unit vector[3];
  * e0: host [3][2]; einc: device [3][N_d] complex128.
@@ -212,6 +239,25 @@ int dda_solve(dda_ctx* ctx, const void* einc, void* p, int method, int precision
               int max_iter, int use_x0, dda_solve_info* info, void* stream);
 
 /*
+ * dda_solve for nb right-hand sides with the same matrix (incidence
+ * directions and polarisations of one target), solved in lock step: every
+ * Krylov kernel and matvec pass covers all of them, each right-hand side
+ * keeps its own scalars, stopping test and iteration count, and one that
+ * has finished is skipped by all later kernels.  Iterations after the first
+ * of each Krylov solve are replayed from a CUDA graph (unless dda_profile
+ * is on).  In the mixed form each right-hand side has its own refinement
+ * steps and inner tolerances.
+ *   einc, p: host or device [nb][3][N_d] complex128 (as in dda_solve).
+ *   info: host dda_solve_info[nb] or NULL; status: host int[nb] or NULL,
+ *         each right-hand side's dda_status.
+ * Returns DDA_ERR_ARG / CUDA / OOM for a failed call, else the most severe
+ * per-right-hand-side status (NAN, then BREAKDOWN, then NOT_CONVERGED).
+ * May grow the workspace (see Ownership).
+ */
+int dda_solve_batch(dda_ctx* ctx, int nb, const void* einc, void* p, int method, int precision, double tol,
+                    int max_iter, int use_x0, dda_solve_info* info, int* status, void* stream);
+
+/*
  * Cross sections with |E0| = 1 (Draine 1988; values only in Table 7):
  *   C_ext = 4 pi k sum_j Im(E_inc,j^* . P_j)
  *   C_abs = 4 pi k sum_j sum_c [-Im(alpha^-1_jc) - (2/3) k^3] |P_jc|^2
@@ -221,6 +267,10 @@ int dda_solve(dda_ctx* ctx, const void* einc, void* p, int method, int precision
  * Synchronises the stream.
  */
 int dda_cross_sections(dda_ctx* ctx, const void* einc, const void* p, double* out, void* stream);
+
+/* dda_cross_sections for nb right-hand sides: einc, p host or device
+ * [nb][3][N_d] complex128, out host double[nb][3]. */
+int dda_cross_sections_batch(dda_ctx* ctx, int nb, const void* einc, const void* p, double* out, void* stream);
 
 /*
  * Occupancy rank scan that allocates no device memory.  This entry point

@@ -15,7 +15,8 @@ from __future__ import annotations
 from ._lib import (  # noqa: F401
     DDA_BICG, DDA_BICG_SYM, DDA_BICGSTAB, DDA_C64, DDA_C128, DDA_ERR_ARG, DDA_ERR_BREAKDOWN, DDA_ERR_CUDA,
     DDA_ERR_NAN, DDA_ERR_NOT_CONVERGED, DDA_ERR_OOM, DDA_FP64, DDA_MIXED, DDA_OK, DDA_QMR, EXPORTS, DDAError,
-    dda_cross_sections, dda_free, dda_gradient, dda_incident_field, dda_init_lattice, dda_last_error,
+    dda_cross_sections, dda_cross_sections_batch, dda_free, dda_gradient, dda_incident_field, dda_init_lattice,
+    dda_last_error, dda_matvec_batch, dda_reserve, dda_solve_batch,
     dda_launch_count, dda_polarizability_derivative, dda_scattering_cross_section,
     dda_matvec, dda_occupancy_ranks_static, dda_pack_composition, dda_pack_occupancy, dda_polarizability,
     dda_profile, dda_profile_read,
@@ -61,6 +62,19 @@ class Lattice:
 
     def matvec(self, p, y, stream=None):
         dda_matvec(self.ctx, p, y, stream)
+
+    def matvec_batch(self, p, y, stream=None):
+        dda_matvec_batch(self.ctx, p, y, stream)
+
+    def reserve(self, nb, precision="mixed"):
+        dda_reserve(self.ctx, nb, precision)
+
+    def solve_batch(self, einc, p, method="bicgstab", precision="fp64", tol=1e-8, max_iter=1000, use_x0=False,
+                    stream=None):
+        return dda_solve_batch(self.ctx, einc, p, method, precision, tol, max_iter, use_x0, stream)
+
+    def cross_sections_batch(self, einc, p, stream=None):
+        return dda_cross_sections_batch(self.ctx, einc, p, stream)
 
     def incident_field(self, khat, e0, einc, stream=None):
         dda_incident_field(self.ctx, khat, e0, einc, stream)

@@ -39,6 +39,7 @@ EXPORTS = (
     "dda_tensor_spectrum", "dda_matvec", "dda_incident_field", "dda_solve", "dda_cross_sections",
     "dda_profile", "dda_profile_read", "dda_launch_count", "dda_last_error", "dda_occupancy_ranks_static",
     "dda_scattering_cross_section", "dda_polarizability_derivative", "dda_gradient",
+    "dda_matvec_batch", "dda_reserve", "dda_solve_batch", "dda_cross_sections_batch",
 )
 
 
@@ -89,6 +90,10 @@ def load(path: str | None = None):
     L.dda_incident_field.argtypes = [vp, vp, vp, vp, vp]
     L.dda_solve.argtypes = [vp, vp, vp, i32, i32, d, i32, i32, ctypes.POINTER(SolveInfo), vp]
     L.dda_cross_sections.argtypes = [vp, vp, vp, vp, vp]
+    L.dda_matvec_batch.argtypes = [vp, i32, vp, vp, i32, vp]
+    L.dda_reserve.argtypes = [vp, i32, i32]
+    L.dda_solve_batch.argtypes = [vp, i32, vp, vp, i32, i32, d, i32, i32, vp, vp, vp]
+    L.dda_cross_sections_batch.argtypes = [vp, i32, vp, vp, vp, vp]
     L.dda_occupancy_ranks_static.argtypes = [vp, i64, vp, vp, vp]
     L.dda_scattering_cross_section.argtypes = [vp, vp, vp, vp]
     L.dda_polarizability_derivative.argtypes = [i32, vp, d, i32, vp, vp, vp]
@@ -219,6 +224,18 @@ def dda_matvec(ctx, p, y, stream=None):
     _check(load().dda_matvec(ctypes.c_void_p(ctx), _ptr(p), _ptr(y), _dtype_code(p), _stream(stream)))
 
 
+def dda_matvec_batch(ctx, p, y, stream=None):
+    """y[b] = A p[b] for p, y of shape (nb, 3, N_d) (device, same complex dtype)."""
+    if p.dtype != y.dtype or p.shape != y.shape:
+        raise TypeError("p and y must have the same dtype and shape")
+    _check(load().dda_matvec_batch(ctypes.c_void_p(ctx), int(p.shape[0]), _ptr(p), _ptr(y), _dtype_code(p),
+                                   _stream(stream)))
+
+
+def dda_reserve(ctx, nb, precision="mixed"):
+    _check(load().dda_reserve(ctypes.c_void_p(ctx), int(nb), PRECISIONS.get(precision, precision)))
+
+
 def dda_incident_field(ctx, khat, e0, einc, stream=None):
     kh = np.ascontiguousarray(np.asarray(khat, dtype=np.float64).reshape(3))
     _check(load().dda_incident_field(ctypes.c_void_p(ctx), _ptr(kh), _ptr(_c2(e0, 3)), _ptr(einc),
@@ -235,6 +252,32 @@ def dda_solve(ctx, einc, p, method="bicgstab", precision="fp64", tol=1e-8, max_i
     if code in (DDA_ERR_ARG, DDA_ERR_CUDA, DDA_ERR_OOM):
         _check(code)
     return code, info.as_dict()
+
+
+def dda_solve_batch(ctx, einc, p, method="bicgstab", precision="fp64", tol=1e-8, max_iter=1000, use_x0=False,
+                    stream=None):
+    """Solves for einc, p of shape (nb, 3, N_d) complex128 (host numpy or
+    device torch).  Returns (status, [per-RHS status], [per-RHS info dict]);
+    raises only for argument / CUDA / allocation errors."""
+    nb = int(einc.shape[0])
+    infos = (SolveInfo * nb)()
+    stats = np.zeros(nb, dtype=np.int32)
+    code = load().dda_solve_batch(ctypes.c_void_p(ctx), nb, _ptr(einc), _ptr(p), METHODS.get(method, method),
+                                  PRECISIONS.get(precision, precision), float(tol), int(max_iter),
+                                  int(bool(use_x0)), ctypes.cast(infos, ctypes.c_void_p), _ptr(stats),
+                                  _stream(stream))
+    if code in (DDA_ERR_ARG, DDA_ERR_CUDA, DDA_ERR_OOM):
+        _check(code)
+    return code, [int(v) for v in stats], [infos[b].as_dict() for b in range(nb)]
+
+
+def dda_cross_sections_batch(ctx, einc, p, stream=None) -> np.ndarray:
+    """(nb, 3) array of (C_ext, C_abs, C_sca) for einc, p of shape (nb, 3, N_d)."""
+    nb = int(einc.shape[0])
+    out = np.zeros(3 * nb)
+    _check(load().dda_cross_sections_batch(ctypes.c_void_p(ctx), nb, _ptr(einc), _ptr(p), _ptr(out),
+                                           _stream(stream)))
+    return out.reshape(nb, 3)
 
 
 def dda_cross_sections(ctx, einc, p, stream=None):

@@ -1,8 +1,8 @@
 // C ABI of the library (include/dda.h): context set-up, the matvec, the
-// solves with FP64 or mixed-precision iterative refinement, and the
-// observables and their permittivity gradients.  Host code only
-// orchestrates; every step runs in the kernels of matvec.cu, spectrum.cu,
-// target.cu and solver.cu.
+// solves with FP64 or mixed-precision iterative refinement (single and
+// batched right-hand sides), and the observables and their permittivity
+// gradients.  Host code only orchestrates; every step runs in the kernels
+// of matvec.cu, spectrum.cu, target.cu and solver.cu.
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -20,8 +20,14 @@ namespace dda {
 
 static thread_local std::string g_last_error;
 static std::atomic<int64_t> g_launches{0};
+static thread_local int64_t* t_capture_sink = nullptr;
 
-void note_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+// launches recorded into a CUDA graph are counted when the graph runs
+void note_launches(int64_t n) {
+    if (t_capture_sink) *t_capture_sink += n;
+    else g_launches.fetch_add(n, std::memory_order_relaxed);
+}
+void capture_launches_into(int64_t* sink) { t_capture_sink = sink; }
 int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 void set_error(const std::string& msg) { g_last_error = msg; }
@@ -64,13 +70,46 @@ __global__ void k_clear_tail(uint32_t* occ, int64_t nwords, int64_t nsites) {
 
 using namespace dda;
 
+// Solve workspace for `cap` right-hand sides of n = 3 N_d elements, in four
+// groups that grow independently on demand (a larger batch, or the first
+// batch in a precision): core vectors and per-RHS state, matvec work
+// slots, FP64 Krylov vectors, complex64 Krylov vectors.
+struct Space {
+    int64_t n = 0;
+    // core
+    int cap_core = 0;
+    void* mem_core = nullptr;
+    void* pinned = nullptr;
+    double2 *x64 = nullptr, *b64 = nullptr, *r64 = nullptr;   // [cap][n]
+    RhsCtl* ctl = nullptr;        // device [cap]
+    RhsCtl* hctl = nullptr;       // pinned [cap]
+    KState *st64 = nullptr, *st32 = nullptr;     // device [cap]
+    double2 *part64 = nullptr, *part32 = nullptr;
+    KState* host = nullptr;       // pinned [cap]
+    int* host_status = nullptr;   // pinned [2][cap]
+    size_t bytes_core = 0;
+    // matvec work: slots32 complex64 slots, or slots64 complex128 ones, in the same bytes
+    int cap_work = 0;
+    void* work = nullptr;
+    int slots32 = 0, slots64 = 0;
+    size_t bytes_work = 0;
+    // Krylov vectors
+    int cap64 = 0, cap32 = 0;
+    void *mem64 = nullptr, *mem32 = nullptr;
+    double2* v64[10] = {};
+    float2* v32[10] = {};
+    float2 *b32 = nullptr, *d32 = nullptr;   // inner right-hand side and solution
+    size_t bytes64 = 0, bytes32 = 0;
+    cudaStream_t capture = nullptr;   // graph capture stream
+};
+
 struct dda_ctx {
     Geometry g{};
     double k = 0.0;
     int device = 0;
-    void* arena0 = nullptr;   // target, spectrum, matvec scratch
-    void* arena1 = nullptr;   // solver vectors
-    int64_t bytes = 0;
+    void* arena0 = nullptr;   // target, tables, spectrum
+    void* arena1 = nullptr;   // adjoint / C_sca vectors
+    int64_t bytes_fixed = 0;
     uint32_t *occ = nullptr, *rank = nullptr, *comp = nullptr;
     double2* ainv64 = nullptr;
     float2* ainv32 = nullptr;
@@ -78,19 +117,11 @@ struct dda_ctx {
     float2* spec32 = nullptr;
     double2* tw64 = nullptr;
     float2* tw32 = nullptr;
-    void* work = nullptr;
     double2* xsec = nullptr;
-    double2* x64 = nullptr;   // solution
-    double2* b64 = nullptr;   // right-hand side
-    double2* r64 = nullptr;   // outer residual
     double2* aux[3] = {};     // adjoint / C_sca work vectors (P, right-hand side, mu)
     double2* dainv64 = nullptr;  // d(alpha^-1)/d eps table of the last gradient call
-    float2* b32 = nullptr;    // inner right-hand side
-    float2* d32 = nullptr;    // inner solution
-    KrylovWork<double> w64{};
-    KrylovWork<float> w32{};
-    KState* host_state = nullptr;  // pinned, 2 entries
-    MatvecView<double> mv64{};
+    Space sp;
+    MatvecView<double> mv64{};   // geometry, tables and tiles; work set per call
     MatvecView<float> mv32{};
     PassProfiler prof;
 };
@@ -117,6 +148,185 @@ int check_dev(const void* p, const char* what) {
     if (!is_device_ptr(p)) return fail(DDA_ERR_ARG, std::string(what) + " must be a device pointer");
     if (reinterpret_cast<uintptr_t>(p) % 16) return fail(DDA_ERR_ARG, std::string(what) + " must be 16-byte aligned");
     return 0;
+}
+
+constexpr int kMaxBatch = 4096;
+
+// elements of one matvec work slot (Ay + Bxy)
+size_t work_elems(const Geometry& g) { return 3ull * g.P * g.Ly * ((size_t)g.K + g.Lx); }
+
+int ensure_core(Space& sp, int nb) {
+    if (sp.cap_core >= nb) return 0;
+    if (sp.mem_core) { cudaFree(sp.mem_core); sp.mem_core = nullptr; }
+    if (sp.pinned) { cudaFreeHost(sp.pinned); sp.pinned = nullptr; }
+    sp.cap_core = 0;
+    sp.bytes_core = 0;
+    const size_t n = (size_t)sp.n, npart = (size_t)(kVecBlocks + nb) * kMaxRed;
+    Arena probe;
+    for (int i = 0; i < 3; ++i) probe.take<double2>(nb * n);
+    probe.take<RhsCtl>(nb);
+    probe.take<KState>(nb);
+    probe.take<KState>(nb);
+    probe.take<double2>(npart);
+    probe.take<double2>(npart);
+    Arena a;
+    a.cap = probe.used + 256;
+    cudaError_t e = cudaMalloc(&sp.mem_core, a.cap);
+    if (e != cudaSuccess) { sp.mem_core = nullptr; return cuda_fail(e, "solve workspace"); }
+    a.base = static_cast<char*>(sp.mem_core);
+    sp.x64 = a.take<double2>(nb * n);
+    sp.b64 = a.take<double2>(nb * n);
+    sp.r64 = a.take<double2>(nb * n);
+    sp.ctl = a.take<RhsCtl>(nb);
+    sp.st64 = a.take<KState>(nb);
+    sp.st32 = a.take<KState>(nb);
+    sp.part64 = a.take<double2>(npart);
+    sp.part32 = a.take<double2>(npart);
+    const size_t hbytes = nb * (sizeof(RhsCtl) + sizeof(KState) + 2 * sizeof(int)) + 64;
+    e = cudaMallocHost(&sp.pinned, hbytes);
+    if (e != cudaSuccess) {
+        cudaFree(sp.mem_core);
+        sp.mem_core = nullptr;
+        sp.pinned = nullptr;
+        return cuda_fail(e, "pinned solver state");
+    }
+    std::memset(sp.pinned, 0, hbytes);
+    char* h = static_cast<char*>(sp.pinned);
+    sp.host = reinterpret_cast<KState*>(h);
+    sp.hctl = reinterpret_cast<RhsCtl*>(h + nb * sizeof(KState));
+    sp.host_status = reinterpret_cast<int*>(h + nb * (sizeof(KState) + sizeof(RhsCtl)));
+    sp.cap_core = nb;
+    sp.bytes_core = a.cap;
+    return 0;
+}
+
+// work for nb complex64 slots; the complex128 products use the same bytes
+// (at least one complex128 slot)
+int ensure_work(Space& sp, const Geometry& g, int nb) {
+    if (sp.cap_work >= nb) return 0;
+    if (sp.work) { cudaFree(sp.work); sp.work = nullptr; }
+    sp.cap_work = 0;
+    sp.bytes_work = 0;
+    const size_t w32 = work_elems(g) * sizeof(float2), w64 = work_elems(g) * sizeof(double2);
+    const size_t bytes = std::max((size_t)nb * w32, w64);
+    cudaError_t e = cudaMalloc(&sp.work, bytes);
+    if (e != cudaSuccess) { sp.work = nullptr; return cuda_fail(e, "matvec work"); }
+    sp.cap_work = nb;
+    sp.slots32 = nb;
+    sp.slots64 = (int)std::max<size_t>(1, std::min<size_t>((size_t)nb, bytes / w64));
+    sp.bytes_work = bytes;
+    return 0;
+}
+
+int ensure_v64(Space& sp, int nb) {
+    if (sp.cap64 >= nb) return 0;
+    if (sp.mem64) { cudaFree(sp.mem64); sp.mem64 = nullptr; }
+    sp.cap64 = 0;
+    sp.bytes64 = 0;
+    const size_t n = (size_t)sp.n;
+    Arena probe;
+    for (int i = 0; i < 10; ++i) probe.take<double2>(nb * n);
+    Arena a;
+    a.cap = probe.used + 256;
+    cudaError_t e = cudaMalloc(&sp.mem64, a.cap);
+    if (e != cudaSuccess) { sp.mem64 = nullptr; return cuda_fail(e, "FP64 Krylov vectors"); }
+    a.base = static_cast<char*>(sp.mem64);
+    for (int i = 0; i < 10; ++i) sp.v64[i] = a.take<double2>(nb * n);
+    sp.cap64 = nb;
+    sp.bytes64 = a.cap;
+    return 0;
+}
+
+int ensure_v32(Space& sp, int nb) {
+    if (sp.cap32 >= nb) return 0;
+    if (sp.mem32) { cudaFree(sp.mem32); sp.mem32 = nullptr; }
+    sp.cap32 = 0;
+    sp.bytes32 = 0;
+    const size_t n = (size_t)sp.n;
+    Arena probe;
+    for (int i = 0; i < 12; ++i) probe.take<float2>(nb * n);
+    Arena a;
+    a.cap = probe.used + 256;
+    cudaError_t e = cudaMalloc(&sp.mem32, a.cap);
+    if (e != cudaSuccess) { sp.mem32 = nullptr; return cuda_fail(e, "complex64 Krylov vectors"); }
+    a.base = static_cast<char*>(sp.mem32);
+    for (int i = 0; i < 10; ++i) sp.v32[i] = a.take<float2>(nb * n);
+    sp.b32 = a.take<float2>(nb * n);
+    sp.d32 = a.take<float2>(nb * n);
+    sp.cap32 = nb;
+    sp.bytes32 = a.cap;
+    return 0;
+}
+
+void free_space(Space& sp) {
+    if (sp.mem_core) cudaFree(sp.mem_core);
+    if (sp.pinned) cudaFreeHost(sp.pinned);
+    if (sp.work) cudaFree(sp.work);
+    if (sp.mem64) cudaFree(sp.mem64);
+    if (sp.mem32) cudaFree(sp.mem32);
+    if (sp.capture) cudaStreamDestroy(sp.capture);
+    sp = Space{};
+}
+
+// everything a solve of nb right-hand sides in this precision needs
+int reserve(dda_ctx* c, int nb, int precision) {
+    if (int rc = ensure_core(c->sp, nb)) return rc;
+    if (int rc = ensure_work(c->sp, c->g, nb)) return rc;
+    return precision == DDA_FP64 ? ensure_v64(c->sp, nb) : ensure_v32(c->sp, nb);
+}
+
+// matvec views over the workspace's work slots
+MatvecView<double> view64(const dda_ctx* c, int nb) {
+    MatvecView<double> m = c->mv64;
+    m.slots = c->sp.slots64;
+    m.Ay = static_cast<double2*>(c->sp.work);
+    m.Bxy = m.Ay + (size_t)m.slots * 3ull * c->g.P * c->g.Ly * c->g.K;
+    m.nb = nb;
+    m.vstride = 3 * c->g.nd;
+    m.status = nullptr;
+    m.conj = 0;
+    return m;
+}
+MatvecView<float> view32(const dda_ctx* c, int nb) {
+    MatvecView<float> m = c->mv32;
+    m.slots = c->sp.slots32;
+    m.Ay = static_cast<float2*>(c->sp.work);
+    m.Bxy = m.Ay + (size_t)m.slots * 3ull * c->g.P * c->g.Ly * c->g.K;
+    m.nb = nb;
+    m.vstride = 3 * c->g.nd;
+    m.status = nullptr;
+    m.conj = 0;
+    return m;
+}
+
+KrylovWork<double> work64(const dda_ctx* c, int nb) {
+    KrylovWork<double> w;
+    w.n = c->sp.n;
+    w.nb = nb;
+    for (int i = 0; i < 10; ++i) w.v[i] = c->sp.v64[i];
+    w.part = c->sp.part64;
+    w.st = c->sp.st64;
+    w.host = c->sp.host;
+    w.host_status = c->sp.host_status;
+    w.capture = c->sp.capture;
+    return w;
+}
+KrylovWork<float> work32(const dda_ctx* c, int nb) {
+    KrylovWork<float> w;
+    w.n = c->sp.n;
+    w.nb = nb;
+    for (int i = 0; i < 10; ++i) w.v[i] = c->sp.v32[i];
+    w.part = c->sp.part32;
+    w.st = c->sp.st32;
+    w.host = c->sp.host;
+    w.host_status = c->sp.host_status;
+    w.capture = c->sp.capture;
+    return w;
+}
+
+int64_t context_bytes(const dda_ctx* c) {
+    const Space& s = c->sp;
+    return c->bytes_fixed + (int64_t)(s.bytes_core + s.bytes_work + s.bytes64 + s.bytes32);
 }
 
 }  // namespace
@@ -199,7 +409,7 @@ void dda_free(dda_ctx* c) {
     if (!c) return;
     if (c->arena0) cudaFree(c->arena0);
     if (c->arena1) cudaFree(c->arena1);
-    if (c->host_state) cudaFreeHost(c->host_state);
+    free_space(c->sp);
     delete c;
 }
 
@@ -236,8 +446,7 @@ int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occu
     c->k = k;
     const int64_t ncw = n_materials > 1 ? (3 * g.nsites + g.cfields - 1) / g.cfields : 0;
     const size_t nspec = 6ull * g.Hz * g.Hy * g.Hx;
-    const size_t nwork = 3ull * g.P * g.Ly * ((size_t)g.K + g.Lx);   // Ay + Bxy
-    // ---- arena 0: target, tables, spectrum, matvec scratch
+    // ---- arena 0: target, tables, spectrum
     Arena a0;
     {
         Arena probe;  // sizing pass
@@ -252,7 +461,6 @@ int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occu
         probe.take<float2>(nspec);
         probe.take<double2>(kMaxLine);
         probe.take<float2>(kMaxLine);
-        probe.take<double2>(nwork);
         probe.take<double2>(xsec_scratch_elems());
         probe.take<int>(4);
         a0.cap = probe.used + 256;
@@ -271,10 +479,9 @@ int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occu
     c->spec32 = a0.take<float2>(nspec);
     c->tw64 = a0.take<double2>(kMaxLine);
     c->tw32 = a0.take<float2>(kMaxLine);
-    c->work = a0.take<double2>(nwork);
     c->xsec = a0.take<double2>(xsec_scratch_elems());
     int* flags = a0.take<int>(4);
-    c->bytes = (int64_t)a0.cap;
+    c->bytes_fixed = (int64_t)a0.cap;
     int rc = 0;
     auto bail = [&](int code) { dda_free(c); return code; };
     // ---- target bit fields
@@ -332,53 +539,36 @@ int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occu
         if (rc) return bail(rc);
         if (e2 != cudaSuccess) return bail(cuda_fail(e2, "dda_init_lattice: spectrum build"));
     }
-    // ---- solver workspace: 16 complex128 + 12 complex64 vectors of 3 N_d
+    // ---- adjoint / C_sca vectors, and the solve workspace for one
+    // right-hand side in both precisions (3 + 3 + 10 complex128 and 12
+    // complex64 vectors of 3 N_d, one matvec work slot)
     {
         const size_t n = 3 * (size_t)g.nd;
         Arena probe;
-        for (int i = 0; i < 16; ++i) probe.take<double2>(n);
-        for (int i = 0; i < 12; ++i) probe.take<float2>(n);
-        probe.take<double2>(kVecBlocks * kMaxRed);
-        probe.take<double2>(kVecBlocks * kMaxRed);
-        probe.take<KState>(2);
+        for (int i = 0; i < 3; ++i) probe.take<double2>(n);
         Arena a1;
         a1.cap = probe.used + 256;
         e = cudaMalloc(&c->arena1, a1.cap);
-        if (e != cudaSuccess) return bail(cuda_fail(e, "dda_init_lattice: solver workspace"));
+        if (e != cudaSuccess) return bail(cuda_fail(e, "dda_init_lattice: adjoint vectors"));
         a1.base = static_cast<char*>(c->arena1);
-        c->x64 = a1.take<double2>(n);
-        c->b64 = a1.take<double2>(n);
-        c->r64 = a1.take<double2>(n);
         for (int i = 0; i < 3; ++i) c->aux[i] = a1.take<double2>(n);
-        c->w64.n = (int64_t)n;
-        for (int i = 0; i < 10; ++i) c->w64.v[i] = a1.take<double2>(n);
-        c->b32 = a1.take<float2>(n);
-        c->d32 = a1.take<float2>(n);
-        c->w32.n = (int64_t)n;
-        for (int i = 0; i < 10; ++i) c->w32.v[i] = a1.take<float2>(n);
-        c->w64.part = a1.take<double2>(kVecBlocks * kMaxRed);
-        c->w32.part = a1.take<double2>(kVecBlocks * kMaxRed);
-        KState* ks = a1.take<KState>(2);
-        c->w64.st = ks;
-        c->w32.st = ks + 1;
-        c->bytes += (int64_t)a1.cap;
-        e = cudaMallocHost(&c->host_state, 2 * sizeof(KState));
-        if (e != cudaSuccess) return bail(cuda_fail(e, "dda_init_lattice: pinned state"));
-        std::memset(c->host_state, 0, 2 * sizeof(KState));
+        c->bytes_fixed += (int64_t)a1.cap;
+        c->sp.n = (int64_t)n;
+        if ((rc = ensure_core(c->sp, 1)) || (rc = ensure_work(c->sp, g, 1)) || (rc = ensure_v64(c->sp, 1)) ||
+            (rc = ensure_v32(c->sp, 1)))
+            return bail(rc);
+        e = cudaStreamCreateWithFlags(&c->sp.capture, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "dda_init_lattice: capture stream"));
     }
-    // ---- matvec views
+    // ---- matvec views (the work arrays are taken per call from the workspace)
     {
         const TargetView tv = target_view(c);
         MatvecView<double>& m = c->mv64;
         m.g = g; m.tv = tv; m.ainv = c->ainv64; m.spec = c->spec64; m.tw = c->tw64;
-        m.Ay = static_cast<double2*>(c->work);
-        m.Bxy = m.Ay + 3ull * g.P * g.Ly * g.K;
         m.status = nullptr; m.conj = 0; m.prof = &c->prof;
         configure_matvec<double>(m);
         MatvecView<float>& f = c->mv32;
         f.g = g; f.tv = tv; f.ainv = c->ainv32; f.spec = c->spec32; f.tw = c->tw32;
-        f.Ay = reinterpret_cast<float2*>(c->work);
-        f.Bxy = f.Ay + 3ull * g.P * g.Ly * g.K;
         f.status = nullptr; f.conj = 0; f.prof = &c->prof;
         configure_matvec<float>(f);
     }
@@ -390,7 +580,7 @@ int dda_query(const dda_ctx* c, int64_t* n_dipoles, int32_t padded[3], int64_t* 
     if (int rc = check_ctx(c)) return rc;
     if (n_dipoles) *n_dipoles = c->g.nd;
     if (padded) { padded[0] = c->g.Lx; padded[1] = c->g.Ly; padded[2] = c->g.Lz; }
-    if (device_bytes) *device_bytes = c->bytes;
+    if (device_bytes) *device_bytes = context_bytes(c);
     return DDA_OK;
 }
 
@@ -434,20 +624,32 @@ int dda_tensor_spectrum(const dda_ctx* c, void* out, int dtype, void* stream) {
     return DDA_OK;
 }
 
-int dda_matvec(dda_ctx* c, const void* p, void* y, int dtype, void* stream) {
+int dda_matvec_batch(dda_ctx* c, int nb, const void* p, void* y, int dtype, void* stream) {
     if (int rc = check_ctx(c)) return rc;
+    if (nb < 1 || nb > kMaxBatch) return fail(DDA_ERR_ARG, "dda_matvec: nb must be in [1, 4096]");
     if (int rc = check_dev(p, "dda_matvec: p")) return rc;
     if (int rc = check_dev(y, "dda_matvec: y")) return rc;
-    if (p == y) return fail(DDA_ERR_ARG, "dda_matvec: p and y must not overlap");
+    const size_t esize = dtype == DDA_C128 ? sizeof(double2) : sizeof(float2);
+    const char *pb = static_cast<const char*>(p), *yb = static_cast<const char*>(y);
+    const size_t span = (size_t)nb * 3 * c->g.nd * esize;
+    if (pb < yb + span && yb < pb + span) return fail(DDA_ERR_ARG, "dda_matvec: p and y must not overlap");
+    if (dtype != DDA_C128 && dtype != DDA_C64) return fail(DDA_ERR_ARG, "dda_matvec: unknown dtype");
+    if (int rc = ensure_work(c->sp, c->g, nb)) return rc;
     cudaStream_t st = as_stream(stream);
-    if (dtype == DDA_C128) {
-        MatvecView<double> m = c->mv64;
-        return launch_matvec<double>(m, static_cast<const double2*>(p), static_cast<double2*>(y), st);
-    } else if (dtype == DDA_C64) {
-        MatvecView<float> m = c->mv32;
-        return launch_matvec<float>(m, static_cast<const float2*>(p), static_cast<float2*>(y), st);
-    }
-    return fail(DDA_ERR_ARG, "dda_matvec: unknown dtype");
+    if (dtype == DDA_C128)
+        return launch_matvec<double>(view64(c, nb), static_cast<const double2*>(p), static_cast<double2*>(y), st);
+    return launch_matvec<float>(view32(c, nb), static_cast<const float2*>(p), static_cast<float2*>(y), st);
+}
+
+int dda_matvec(dda_ctx* c, const void* p, void* y, int dtype, void* stream) {
+    return dda_matvec_batch(c, 1, p, y, dtype, stream);
+}
+
+int dda_reserve(dda_ctx* c, int nb, int precision) {
+    if (int rc = check_ctx(c)) return rc;
+    if (nb < 1 || nb > kMaxBatch) return fail(DDA_ERR_ARG, "dda_reserve: nb must be in [1, 4096]");
+    if (precision != DDA_FP64 && precision != DDA_MIXED) return fail(DDA_ERR_ARG, "dda_reserve: unknown precision");
+    return reserve(c, nb, precision);
 }
 
 int dda_incident_field(dda_ctx* c, const double* khat, const double* e0, void* einc, void* stream) {
@@ -468,100 +670,193 @@ static int map_status(int s) {
     }
 }
 
-int dda_solve(dda_ctx* c, const void* einc, void* p, int method, int precision, double tol, int max_iter,
-              int use_x0, dda_solve_info* info, void* stream) {
-    const auto t0 = std::chrono::steady_clock::now();
+// the batch's return value: the most severe per-RHS status
+static int worst_status(const int* st, int nb) {
+    int w = DDA_OK;
+    for (int b = 0; b < nb; ++b) {
+        if (st[b] == DDA_ERR_NAN) return DDA_ERR_NAN;
+        if (st[b] == DDA_ERR_BREAKDOWN) w = DDA_ERR_BREAKDOWN;
+        else if (st[b] == DDA_ERR_NOT_CONVERGED && w == DDA_OK) w = DDA_ERR_NOT_CONVERGED;
+    }
+    return w;
+}
+
+// Solves of nb right-hand sides in lock step (vectors [nb][3 N_d]); per-RHS
+// results into inf[] and stat[].  Returns a non-solver error (ARG, CUDA,
+// OOM) or 0.
+static int solve_batch(dda_ctx* c, int nb, const void* einc, void* p, int method, int precision, double tol,
+                       int max_iter, int use_x0, dda_solve_info* inf, int* stat, cudaStream_t st) {
+    if (int rc = reserve(c, nb, precision)) return rc;
+    Space& sp = c->sp;
+    const int64_t n = sp.n;
+    const size_t bytes = (size_t)nb * n * sizeof(double2);
+    DDA_CUDA_TRY(cudaMemcpyAsync(sp.b64, einc, bytes, cudaMemcpyDefault, st));
+    if (use_x0) DDA_CUDA_TRY(cudaMemcpyAsync(sp.x64, p, bytes, cudaMemcpyDefault, st));
+    for (int b = 0; b < nb; ++b) { inf[b] = dda_solve_info{}; stat[b] = DDA_ERR_NOT_CONVERGED; }
+    std::vector<SolveResult> res(nb);
+    std::vector<double> bn2(nb), rn2(nb);
+    if (precision == DDA_FP64) {
+        KrylovWork<double> w = work64(c, nb);
+        if (int rc = krylov_solve<double>(method, view64(c, nb), w, sp.b64, sp.x64, use_x0 != 0, nullptr, tol,
+                                          max_iter, st, res.data()))
+            return rc;
+        // true residuals with one FP64 product per right-hand side
+        if (int rc = launch_matvec<double>(view64(c, nb), sp.x64, sp.r64, st)) return rc;
+        if (int rc = residual_from_product(sp.b64, sp.r64, n, nb, nullptr, sp.part64, sp.st64, st)) return rc;
+        if (int rc = read_tmp_slots(sp.st64, nb, sp.host, rn2.data(), st)) return rc;
+        if (int rc = vec_norm2_c128(sp.b64, n, nb, sp.part64, sp.st64, st)) return rc;
+        if (int rc = read_tmp_slots(sp.st64, nb, sp.host, bn2.data(), st)) return rc;
+        for (int b = 0; b < nb; ++b) {
+            stat[b] = map_status(res[b].status);
+            inf[b].iterations = res[b].iterations;
+            inf[b].matvecs = res[b].matvecs;
+            inf[b].matvecs_fp64 = res[b].matvecs + 1;
+            inf[b].rel_residual = std::sqrt(res[b].rel2);
+            inf[b].rel_residual_true = bn2[b] > 0 ? std::sqrt(rn2[b] / bn2[b]) : 0.0;
+        }
+    } else {
+        if (int rc = vec_norm2_c128(sp.b64, n, nb, sp.part64, sp.st64, st)) return rc;
+        if (int rc = read_tmp_slots(sp.st64, nb, sp.host, bn2.data(), st)) return rc;
+        if (use_x0) {
+            if (int rc = launch_matvec<double>(view64(c, nb), sp.x64, sp.r64, st)) return rc;
+            if (int rc = residual_from_product(sp.b64, sp.r64, n, nb, nullptr, sp.part64, sp.st64, st)) return rc;
+            if (int rc = read_tmp_slots(sp.st64, nb, sp.host, rn2.data(), st)) return rc;
+            for (int b = 0; b < nb; ++b) inf[b].matvecs_fp64 += 1;
+        } else {
+            DDA_CUDA_TRY(cudaMemsetAsync(sp.x64, 0, bytes, st));
+            DDA_CUDA_TRY(cudaMemcpyAsync(sp.r64, sp.b64, bytes, cudaMemcpyDeviceToDevice, st));
+            rn2 = bn2;
+        }
+        std::vector<char> active(nb, 1);
+        std::vector<int> stall(nb, 0);
+        std::vector<double> best(nb);
+        for (int b = 0; b < nb; ++b) {
+            best[b] = rn2[b];
+            if (!std::isfinite(bn2[b]) || !std::isfinite(rn2[b])) { stat[b] = DDA_ERR_NAN; active[b] = 0; }
+        }
+        RhsCtl* hc = sp.hctl;
+        KrylovWork<float> w = work32(c, nb);
+        MatvecView<double> m64 = view64(c, nb);
+        m64.status = &sp.ctl[0].skip;   // the residual product skips finished right-hand sides
+        m64.status_stride = kCtlInts;
+        while (true) {
+            bool any = false;
+            for (int b = 0; b < nb; ++b) {
+                if (!active[b]) continue;
+                const double rel = bn2[b] > 0 ? std::sqrt(rn2[b] / bn2[b]) : 0.0;
+                inf[b].rel_residual = inf[b].rel_residual_true = rel;
+                if (rel <= tol) { stat[b] = DDA_OK; active[b] = 0; }
+                else if (inf[b].iterations >= max_iter) { stat[b] = DDA_ERR_NOT_CONVERGED; active[b] = 0; }
+                else any = true;
+            }
+            if (!any) break;
+            for (int b = 0; b < nb; ++b) {
+                if (active[b]) {
+                    const double rel = std::sqrt(rn2[b] / bn2[b]);
+                    // inner target: enough to reach tol from here, not below what FP32 sustains
+                    hc[b].tol = std::min(0.5, std::max(0.3 * tol / rel, 1e-6));
+                    hc[b].scale = 1.0 / std::sqrt(rn2[b]);
+                    hc[b].mult = std::sqrt(rn2[b]);
+                    hc[b].maxit = max_iter - inf[b].iterations;
+                    hc[b].skip = 0;
+                } else {
+                    hc[b] = RhsCtl{0.0, 0.0, 0.0, 0, 1};
+                }
+            }
+            DDA_CUDA_TRY(cudaMemcpyAsync(sp.ctl, hc, nb * sizeof(RhsCtl), cudaMemcpyHostToDevice, st));
+            if (int rc = scale_to_c64(sp.r64, sp.ctl, sp.b32, n, nb, st)) return rc;
+            if (int rc = krylov_solve<float>(method, view32(c, nb), w, sp.b32, sp.d32, false, sp.ctl, 0.0, 0, st,
+                                             res.data()))
+                return rc;
+            // krylov_solve synchronised the stream: the controls may be rewritten
+            bool changed = false;
+            for (int b = 0; b < nb; ++b) {
+                if (!active[b]) continue;
+                inf[b].iterations += res[b].iterations;
+                inf[b].matvecs += res[b].matvecs;
+                if (res[b].status == ST_NAN) {
+                    stat[b] = DDA_ERR_NAN;
+                    active[b] = 0;
+                    hc[b] = RhsCtl{0.0, 0.0, 0.0, 0, 1};
+                    changed = true;
+                }
+            }
+            if (changed)
+                DDA_CUDA_TRY(cudaMemcpyAsync(sp.ctl, hc, nb * sizeof(RhsCtl), cudaMemcpyHostToDevice, st));
+            if (int rc = axpy_from_c64(sp.x64, sp.ctl, sp.d32, n, nb, st)) return rc;
+            if (int rc = launch_matvec<double>(m64, sp.x64, sp.r64, st)) return rc;
+            if (int rc = residual_from_product(sp.b64, sp.r64, n, nb, sp.ctl, sp.part64, sp.st64, st)) return rc;
+            std::vector<double> rnew(nb);
+            if (int rc = read_tmp_slots(sp.st64, nb, sp.host, rnew.data(), st)) return rc;
+            for (int b = 0; b < nb; ++b) {
+                if (!active[b]) continue;
+                inf[b].matvecs_fp64 += 1;
+                inf[b].refinements += 1;
+                rn2[b] = rnew[b];
+                if (!std::isfinite(rn2[b])) { stat[b] = DDA_ERR_NAN; active[b] = 0; continue; }
+                if (rn2[b] < 0.25 * best[b]) {
+                    best[b] = rn2[b];
+                    stall[b] = 0;
+                } else if (++stall[b] >= 3) {
+                    inf[b].rel_residual = inf[b].rel_residual_true = std::sqrt(rn2[b] / bn2[b]);
+                    stat[b] = res[b].status == ST_BREAKDOWN ? DDA_ERR_BREAKDOWN : DDA_ERR_NOT_CONVERGED;
+                    active[b] = 0;
+                    continue;
+                }
+                if (res[b].status == ST_BREAKDOWN && res[b].iterations == 0) {
+                    inf[b].rel_residual = inf[b].rel_residual_true = std::sqrt(rn2[b] / bn2[b]);
+                    stat[b] = DDA_ERR_BREAKDOWN;
+                    active[b] = 0;
+                }
+            }
+        }
+    }
+    DDA_CUDA_TRY(cudaMemcpyAsync(p, sp.x64, bytes, cudaMemcpyDefault, st));
+    DDA_CUDA_TRY(cudaStreamSynchronize(st));
+    return 0;
+}
+
+static int check_solve_args(const dda_ctx* c, int nb, const void* einc, const void* p, int method, int precision,
+                            double tol, int max_iter) {
     if (int rc = check_ctx(c)) return rc;
+    if (nb < 1 || nb > kMaxBatch) return fail(DDA_ERR_ARG, "dda_solve: nb must be in [1, 4096]");
     if (!einc || !p) return fail(DDA_ERR_ARG, "dda_solve: NULL einc or p");
     if (method < DDA_BICG || method > DDA_BICG_SYM) return fail(DDA_ERR_ARG, "dda_solve: unknown method");
     if (precision != DDA_FP64 && precision != DDA_MIXED) return fail(DDA_ERR_ARG, "dda_solve: unknown precision");
     if (!(tol > 0.0) || !std::isfinite(tol)) return fail(DDA_ERR_ARG, "dda_solve: tol must be finite and > 0");
     if (max_iter < 1) return fail(DDA_ERR_ARG, "dda_solve: max_iter must be >= 1");
-    cudaStream_t st = as_stream(stream);
-    const int64_t n = 3 * c->g.nd;
-    const size_t bytes = n * sizeof(double2);
-    DDA_CUDA_TRY(cudaMemcpyAsync(c->b64, einc, bytes, cudaMemcpyDefault, st));
-    if (use_x0) DDA_CUDA_TRY(cudaMemcpyAsync(c->x64, p, bytes, cudaMemcpyDefault, st));
-    dda_solve_info inf{};
-    int status = DDA_OK;
-    KState* hs = c->host_state;
-    if (precision == DDA_FP64) {
-        SolveResult r{};
-        if (int rc = krylov_solve<double>(method, c->mv64, c->w64, c->b64, c->x64, use_x0 != 0, tol, max_iter, hs, st, &r))
-            return rc;
-        status = map_status(r.status);
-        inf.iterations = r.iterations;
-        inf.matvecs = r.matvecs;
-        inf.matvecs_fp64 = r.matvecs;
-        inf.rel_residual = std::sqrt(r.rel2);
-        // true residual with one FP64 product
-        MatvecView<double> m = c->mv64;
-        if (int rc = launch_matvec<double>(m, c->x64, c->r64, st)) return rc;
-        if (int rc = residual_from_product(c->b64, c->r64, n, c->w64.part, c->w64.st, st)) return rc;
-        double rn2 = 0.0, bn2 = 0.0;
-        if (int rc = vec_norm2_c128(c->r64, n, c->w64.part, c->w64.st, &rn2, hs, st)) return rc;
-        if (int rc = vec_norm2_c128(c->b64, n, c->w64.part, c->w64.st, &bn2, hs, st)) return rc;
-        inf.matvecs_fp64 += 1;
-        inf.rel_residual_true = bn2 > 0 ? std::sqrt(rn2 / bn2) : 0.0;
-    } else {
-        double bn2 = 0.0, rn2 = 0.0;
-        if (int rc = vec_norm2_c128(c->b64, n, c->w64.part, c->w64.st, &bn2, hs, st)) return rc;
-        if (use_x0) {
-            MatvecView<double> m = c->mv64;
-            if (int rc = launch_matvec<double>(m, c->x64, c->r64, st)) return rc;
-            if (int rc = residual_from_product(c->b64, c->r64, n, c->w64.part, c->w64.st, st)) return rc;
-            inf.matvecs_fp64 += 1;
-        } else {
-            DDA_CUDA_TRY(cudaMemsetAsync(c->x64, 0, bytes, st));
-            DDA_CUDA_TRY(cudaMemcpyAsync(c->r64, c->b64, bytes, cudaMemcpyDeviceToDevice, st));
-        }
-        if (int rc = vec_norm2_c128(c->r64, n, c->w64.part, c->w64.st, &rn2, hs, st)) return rc;
-        if (!std::isfinite(bn2) || !std::isfinite(rn2)) return fail(DDA_ERR_NAN, "dda_solve: non-finite input");
-        status = DDA_ERR_NOT_CONVERGED;
-        int stall = 0;
-        double best = rn2;
-        while (true) {
-            const double rel = bn2 > 0 ? std::sqrt(rn2 / bn2) : 0.0;
-            inf.rel_residual = rel;
-            inf.rel_residual_true = rel;
-            if (rel <= tol) { status = DDA_OK; break; }
-            if (inf.iterations >= max_iter) { status = DDA_ERR_NOT_CONVERGED; break; }
-            // inner target: enough to reach tol from here, but not below what FP32 sustains
-            const double inner_tol = std::min(0.5, std::max(0.3 * tol / rel, 1e-6));
-            const double rnorm = std::sqrt(rn2);
-            if (int rc = scale_to_c64(c->r64, 1.0 / rnorm, c->b32, n, st)) return rc;
-            SolveResult r{};
-            if (int rc = krylov_solve<float>(method, c->mv32, c->w32, c->b32, c->d32, false, inner_tol,
-                                             max_iter - inf.iterations, hs, st, &r))
-                return rc;
-            inf.iterations += r.iterations;
-            inf.matvecs += r.matvecs;
-            if (r.status == ST_NAN) { status = DDA_ERR_NAN; break; }
-            if (int rc = axpy_from_c64(c->x64, rnorm, c->d32, n, st)) return rc;
-            MatvecView<double> m = c->mv64;
-            if (int rc = launch_matvec<double>(m, c->x64, c->r64, st)) return rc;
-            if (int rc = residual_from_product(c->b64, c->r64, n, c->w64.part, c->w64.st, st)) return rc;
-            inf.matvecs_fp64 += 1;
-            inf.refinements += 1;
-            if (int rc = vec_norm2_c128(c->r64, n, c->w64.part, c->w64.st, &rn2, hs, st)) return rc;
-            if (!std::isfinite(rn2)) { status = DDA_ERR_NAN; break; }
-            if (rn2 < 0.25 * best) { best = rn2; stall = 0; }
-            else if (++stall >= 3) {
-                inf.rel_residual = inf.rel_residual_true = std::sqrt(rn2 / bn2);
-                status = r.status == ST_BREAKDOWN ? DDA_ERR_BREAKDOWN : DDA_ERR_NOT_CONVERGED;
-                break;
-            }
-            if (r.status == ST_BREAKDOWN && r.iterations == 0) { status = DDA_ERR_BREAKDOWN; break; }
-        }
-    }
-    DDA_CUDA_TRY(cudaMemcpyAsync(p, c->x64, bytes, cudaMemcpyDefault, st));
-    DDA_CUDA_TRY(cudaStreamSynchronize(st));
-    inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    if (info) *info = inf;
+    return 0;
+}
+
+static void report(int status) {
     if (status == DDA_ERR_NOT_CONVERGED) set_error("dda_solve: not converged within max_iter");
     else if (status == DDA_ERR_BREAKDOWN) set_error("dda_solve: Krylov breakdown");
     else if (status == DDA_ERR_NAN) set_error("dda_solve: non-finite value");
-    return status;
+}
+
+int dda_solve_batch(dda_ctx* c, int nb, const void* einc, void* p, int method, int precision, double tol,
+                    int max_iter, int use_x0, dda_solve_info* info, int* status, void* stream) {
+    const auto t0 = std::chrono::steady_clock::now();
+    if (int rc = check_solve_args(c, nb, einc, p, method, precision, tol, max_iter)) return rc;
+    std::vector<dda_solve_info> inf(nb);
+    std::vector<int> stat(nb);
+    if (int rc = solve_batch(c, nb, einc, p, method, precision, tol, max_iter, use_x0, inf.data(), stat.data(),
+                             as_stream(stream)))
+        return rc;
+    const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (int b = 0; b < nb; ++b) {
+        inf[b].seconds = sec;
+        if (info) info[b] = inf[b];
+        if (status) status[b] = stat[b];
+    }
+    const int w = worst_status(stat.data(), nb);
+    report(w);
+    return w;
+}
+
+int dda_solve(dda_ctx* c, const void* einc, void* p, int method, int precision, double tol, int max_iter,
+              int use_x0, dda_solve_info* info, void* stream) {
+    return dda_solve_batch(c, 1, einc, p, method, precision, tol, max_iter, use_x0, info, nullptr, stream);
 }
 
 int dda_polarizability_derivative(int n, const double* m, double k, int rule, const double* khat, const double* e0,
@@ -605,9 +900,7 @@ int dda_scattering_cross_section(dda_ctx* c, const void* p, double* out, void* s
     const size_t bytes = 3 * c->g.nd * sizeof(double2);
     double2* P = c->aux[0];
     DDA_CUDA_TRY(cudaMemcpyAsync(P, p, bytes, cudaMemcpyDefault, st));
-    MatvecView<double> m = c->mv64;
-    m.status = nullptr;
-    m.conj = 0;
+    MatvecView<double> m = view64(c, 1);
     if (int rc = launch_matvec<double>(m, P, c->aux[1], st)) return rc;        // A P
     m.conj = 1;
     if (int rc = launch_matvec<double>(m, P, c->aux[2], st)) return rc;        // A^H P
@@ -648,30 +941,46 @@ int dda_gradient(dda_ctx* c, int which, const void* einc, const void* p, const d
     return status;
 }
 
-int dda_cross_sections(dda_ctx* c, const void* einc, const void* p, double* out, void* stream) {
+int dda_cross_sections_batch(dda_ctx* c, int nb, const void* einc, const void* p, double* out, void* stream) {
     if (int rc = check_ctx(c)) return rc;
+    if (nb < 1 || nb > kMaxBatch) return fail(DDA_ERR_ARG, "dda_cross_sections: nb must be in [1, 4096]");
     if (!einc || !p || !out) return fail(DDA_ERR_ARG, "dda_cross_sections: NULL argument");
     cudaStream_t st = as_stream(stream);
-    const size_t bytes = 3 * c->g.nd * sizeof(double2);
+    const int64_t n = 3 * c->g.nd;
+    const size_t bytes = (size_t)nb * n * sizeof(double2);
     const double2* E = static_cast<const double2*>(einc);
     const double2* P = static_cast<const double2*>(p);
+    if (!is_device_ptr(einc) || !is_device_ptr(p))
+        if (int rc = ensure_core(c->sp, nb)) return rc;
     if (!is_device_ptr(einc)) {
-        DDA_CUDA_TRY(cudaMemcpyAsync(c->w64.v[0], einc, bytes, cudaMemcpyHostToDevice, st));
-        E = c->w64.v[0];
+        DDA_CUDA_TRY(cudaMemcpyAsync(c->sp.b64, einc, bytes, cudaMemcpyHostToDevice, st));
+        E = c->sp.b64;
     }
     if (!is_device_ptr(p)) {
-        DDA_CUDA_TRY(cudaMemcpyAsync(c->w64.v[1], p, bytes, cudaMemcpyHostToDevice, st));
-        P = c->w64.v[1];
+        DDA_CUDA_TRY(cudaMemcpyAsync(c->sp.r64, p, bytes, cudaMemcpyHostToDevice, st));
+        P = c->sp.r64;
     }
-    if (int rc = launch_cross_sections(target_view(c), c->g, c->k, c->ainv64, E, P, c->xsec, st)) return rc;
-    double2 h;
-    DDA_CUDA_TRY(cudaMemcpyAsync(&h, c->xsec + xsec_scratch_elems() - 1, sizeof(double2), cudaMemcpyDeviceToHost, st));
+    // one reduction per right-hand side; each result is copied out before
+    // the next one reuses the scratch (stream order)
+    double2* h = reinterpret_cast<double2*>(c->sp.host);   // pinned, >= nb double2
+    for (int b = 0; b < nb; ++b) {
+        if (int rc = launch_cross_sections(target_view(c), c->g, c->k, c->ainv64, E + b * n, P + b * n, c->xsec, st))
+            return rc;
+        DDA_CUDA_TRY(cudaMemcpyAsync(h + b, c->xsec + xsec_scratch_elems() - 1, sizeof(double2),
+                                     cudaMemcpyDeviceToHost, st));
+    }
     DDA_CUDA_TRY(cudaStreamSynchronize(st));
     const double f = 4.0 * M_PI * c->k;
-    out[0] = f * h.x;
-    out[1] = f * h.y;
-    out[2] = out[0] - out[1];
+    for (int b = 0; b < nb; ++b) {
+        out[3 * b] = f * h[b].x;
+        out[3 * b + 1] = f * h[b].y;
+        out[3 * b + 2] = out[3 * b] - out[3 * b + 1];
+    }
     return DDA_OK;
+}
+
+int dda_cross_sections(dda_ctx* c, const void* einc, const void* p, double* out, void* stream) {
+    return dda_cross_sections_batch(c, 1, einc, p, out, stream);
 }
 
 }  // extern "C"

@@ -16,6 +16,13 @@
 // zero half of their input and inverse transforms compute only the half of
 // the output that is kept.
 //
+// Batches: one launch of each pass covers up to `slots` right-hand sides
+// that share the context's spectrum (vectors [nb][3][N_d], work arrays one
+// per slot); a right-hand side whose solver status is no longer "running"
+// is skipped block by block.  In P3 the slot index is the fastest-varying
+// block index, so the CTAs of all right-hand sides that read one spectrum
+// tile run back to back and the tile is fetched from HBM once.
+//
 // Every pass keeps its lines in registers (fft_reg.cuh): points are loaded
 // from global memory straight into the registers of the first DFT stage and
 // stored from the registers of the last, and only the exchanges between
@@ -25,6 +32,7 @@
 // three components, so the spectrum product happens in registers between
 // the forward and the inverse transforms.  Each kernel is compiled for every
 // power-of-two line length (LOGN = 1..10) and picked at launch.
+#include <atomic>
 #include <cstdlib>
 
 #include "fft_reg.cuh"
@@ -40,18 +48,24 @@ __host__ __device__ constexpr int points(int logN) { return logN < 3 ? (1 << log
 // file for complex64, 256 for complex128
 template <typename T> __host__ __device__ constexpr int p3_max_threads() { return sizeof(T) == 4 ? 512 : 256; }
 
+// elements of one slot of the work arrays
+__host__ __device__ __forceinline__ int64_t ay_elems(const Geometry& g) { return 3LL * g.P * g.Ly * g.K; }
+__host__ __device__ __forceinline__ int64_t bxy_elems(const Geometry& g) { return 3LL * g.P * g.Ly * g.Lx; }
+
 // ---------------------------------------------------------------- P1
 template <typename T, int LOGN>
 __global__ void __launch_bounds__(1024) k_p1(MatvecView<T> mv, const C<T>* __restrict__ p) {
-    if (mv.status && *mv.status) return;
+    const int c = blockIdx.z % 3, j = blockIdx.z / 3;      // component, batch slot
+    const int b = mv.b0 + j;
+    if (rhs_done(mv, b)) return;
     extern __shared__ unsigned char smem_raw[];
     C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
     constexpr int logT = lines_log(LOGN), nv = points(LOGN);
     const Geometry& g = mv.g;
     const int logW = mv.logW_y, W = 1 << logW;
     const int w = threadIdx.x & (W - 1), t = threadIdx.x >> logW;
-    const int i = blockIdx.x * W + w, kz = blockIdx.y, c = blockIdx.z;
-    const C<T>* pc = p + (int64_t)c * g.nd;
+    const int i = blockIdx.x * W + w, kz = blockIdx.y;
+    const C<T>* pc = p + (int64_t)b * mv.vstride + (int64_t)c * g.nd;
     const int64_t s0 = (int64_t)kz * g.J * g.K + i;
     C<T> v[8];
 #pragma unroll
@@ -68,7 +82,7 @@ __global__ void __launch_bounds__(1024) k_p1(MatvecView<T> mv, const C<T>* __res
     }
     fft_regs<T, false, LOGN, true, false>(v, sm, ColLayout{logW}, w, t, mv.tw);
     if (i < g.K) {
-        C<T>* out = mv.Ay + ((int64_t)c * g.P + kz) * ((int64_t)g.K << LOGN) + i;
+        C<T>* out = mv.Ay + j * ay_elems(g) + ((int64_t)c * g.P + kz) * ((int64_t)g.K << LOGN) + i;
 #pragma unroll
         for (int m = 0; m < nv; ++m) out[(int64_t)(t + (m << logT)) * g.K] = v[m];
     }
@@ -79,15 +93,15 @@ __global__ void __launch_bounds__(1024) k_p1(MatvecView<T> mv, const C<T>* __res
 // inputs (Bxy) -> first K outputs (Ay).  2^logW_x rows per CTA.
 template <typename T, bool INV, int LOGN>
 __global__ void __launch_bounds__(512) k_rows(MatvecView<T> mv) {
-    if (mv.status && *mv.status) return;
     extern __shared__ unsigned char smem_raw[];
     C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
     constexpr int N = 1 << LOGN, logT = lines_log(LOGN), nv = points(LOGN);
     const Geometry& g = mv.g;
     const int t = threadIdx.x & ((1 << logT) - 1), wl = threadIdx.x >> logT;
-    const int64_t nrows = 3LL * g.P * g.Ly;
+    // rows of consecutive slots are contiguous: row r belongs to slot r / rows1
+    const int64_t rows1 = 3LL * g.P * g.Ly, nrows = rows1 * mv.nb;
     const int64_t row = ((int64_t)blockIdx.x << mv.logW_x) + wl;
-    const bool ok = row < nrows;
+    const bool ok = row < nrows && !rhs_done(mv, mv.b0 + (int)(row / rows1));
     const int nin = INV ? N : g.K, nout = INV ? g.K : N;
     const C<T>* src = (INV ? mv.Bxy : mv.Ay) + (ok ? row * (INV ? N : g.K) : 0);
     C<T>* dst = (INV ? mv.Ay : mv.Bxy) + (ok ? row * (INV ? g.K : N) : 0);
@@ -138,7 +152,8 @@ __device__ __forceinline__ void load6(const C<T>* __restrict__ p, C<T> (&Y)[6]) 
 
 template <typename T, int LOGN>
 __global__ void __launch_bounds__(p3_max_threads<T>(), 1) k_p3(MatvecView<T> mv) {
-    if (mv.status && *mv.status) return;
+    const int j = blockIdx.x % mv.nb, xt = blockIdx.x / mv.nb;   // batch slot, column tile
+    if (rhs_done(mv, mv.b0 + j)) return;
     extern __shared__ unsigned char smem_raw[];
     C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
     constexpr int N = 1 << LOGN, logT = lines_log(LOGN), nv = points(LOGN);
@@ -149,13 +164,13 @@ __global__ void __launch_bounds__(p3_max_threads<T>(), 1) k_p3(MatvecView<T> mv)
     // them back to back (0, 1, Ly-1, 2, Ly-2, ...) so the second read hits L2
     const int b = blockIdx.y, q2 = (b + 1) >> 1;
     const int jy = b == 0 ? 0 : ((b & 1) ? q2 : g.Ly - q2);
-    const int ix = blockIdx.x * W + w;
+    const int ix = xt * W + w;
     const bool ok = ix < g.Lx;
     const ColLayout L{logW};
     const int region = col_elems(N, W);
     const int64_t plane = (int64_t)g.Ly * g.Lx;   // stride between z planes of Bxy
     const int64_t comp = (int64_t)g.P * plane;    // stride between components
-    C<T>* col = mv.Bxy + (int64_t)jy * g.Lx + (ok ? ix : 0);
+    C<T>* col = mv.Bxy + j * bxy_elems(g) + (int64_t)jy * g.Lx + (ok ? ix : 0);
     C<T> v[3][8];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
@@ -206,16 +221,18 @@ __global__ void __launch_bounds__(p3_max_threads<T>(), 1) k_p3(MatvecView<T> mv)
 // ---------------------------------------------------------------- P5
 template <typename T, int LOGN>
 __global__ void __launch_bounds__(1024) k_p5(MatvecView<T> mv, const C<T>* __restrict__ p, C<T>* __restrict__ y) {
-    if (mv.status && *mv.status) return;
+    const int c = blockIdx.z % 3, j = blockIdx.z / 3;      // component, batch slot
+    const int b = mv.b0 + j;
+    if (rhs_done(mv, b)) return;
     extern __shared__ unsigned char smem_raw[];
     C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
     constexpr int logT = lines_log(LOGN), nv = points(LOGN);
     const Geometry& g = mv.g;
     const int logW = mv.logW_y, W = 1 << logW;
     const int w = threadIdx.x & (W - 1), t = threadIdx.x >> logW;
-    const int i = blockIdx.x * W + w, kz = blockIdx.y, c = blockIdx.z;
+    const int i = blockIdx.x * W + w, kz = blockIdx.y;
     const bool ok = i < g.K;
-    const C<T>* in = mv.Ay + ((int64_t)c * g.P + kz) * ((int64_t)g.K << LOGN) + (ok ? i : 0);
+    const C<T>* in = mv.Ay + j * ay_elems(g) + ((int64_t)c * g.P + kz) * ((int64_t)g.K << LOGN) + (ok ? i : 0);
     C<T> v[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
@@ -224,8 +241,8 @@ __global__ void __launch_bounds__(1024) k_p5(MatvecView<T> mv, const C<T>* __res
     }
     fft_regs<T, true, LOGN, false, true>(v, sm, ColLayout{logW}, w, t, mv.tw);
     if (!ok) return;
-    const C<T>* pc = p + (int64_t)c * g.nd;
-    C<T>* yc = y + (int64_t)c * g.nd;
+    const C<T>* pc = p + (int64_t)b * mv.vstride + (int64_t)c * g.nd;
+    C<T>* yc = y + (int64_t)b * mv.vstride + (int64_t)c * g.nd;
     const int64_t s0 = (int64_t)kz * g.J * g.K + i;
 #pragma unroll
     for (int m = 0; m < nv; ++m) {
@@ -255,9 +272,15 @@ int env_tile(const char* name, int dflt) {
     return v > 0 ? floor_log2(v) : dflt;
 }
 
-int set_smem(const void* fn, size_t bytes) {
-    if (bytes > 48 * 1024)
-        DDA_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+// Raises a kernel's dynamic shared-memory limit once per kernel and size
+// (`done` is the launcher's own record), so that launches recorded into a
+// CUDA graph make no attribute calls.
+int set_smem(const void* fn, size_t bytes, std::atomic<size_t>& done) {
+    if (bytes <= 48 * 1024 || bytes <= done.load(std::memory_order_relaxed)) return 0;
+    DDA_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    size_t cur = done.load(std::memory_order_relaxed);
+    while (cur < bytes && !done.compare_exchange_weak(cur, bytes)) {
+    }
     return 0;
 }
 
@@ -267,8 +290,9 @@ int launch_p1(const MatvecView<T>& mv, const C<T>* p, cudaStream_t st) {
     const Geometry& g = mv.g;
     const int W = 1 << mv.logW_y;
     const size_t sm = (size_t)col_elems(1 << LOGN, W) * sizeof(C<T>);
-    if (int rc = set_smem((const void*)k_p1<T, LOGN>, sm)) return rc;
-    dim3 grid((g.K + W - 1) / W, g.P, 3);
+    static std::atomic<size_t> smem_set{0};
+    if (int rc = set_smem((const void*)k_p1<T, LOGN>, sm, smem_set)) return rc;
+    dim3 grid((g.K + W - 1) / W, g.P, 3 * mv.nb);
     k_p1<T, LOGN><<<grid, W << lines_log(LOGN), sm, st>>>(mv, p);
     DDA_LAUNCH_CHECK("P1 expand + y-forward");
     return 0;
@@ -277,10 +301,11 @@ int launch_p1(const MatvecView<T>& mv, const C<T>* p, cudaStream_t st) {
 template <typename T, bool INV, int LOGN>
 int launch_rows(const MatvecView<T>& mv, cudaStream_t st) {
     const Geometry& g = mv.g;
-    const int64_t rows = 3LL * g.P * g.Ly;
+    const int64_t rows = 3LL * g.P * g.Ly * mv.nb;
     const int R = 1 << mv.logW_x;
     const size_t sm = (size_t)R * row_ld(1 << LOGN) * sizeof(C<T>);
-    if (int rc = set_smem((const void*)k_rows<T, INV, LOGN>, sm)) return rc;
+    static std::atomic<size_t> smem_set{0};
+    if (int rc = set_smem((const void*)k_rows<T, INV, LOGN>, sm, smem_set)) return rc;
     k_rows<T, INV, LOGN><<<(unsigned)((rows + R - 1) / R), R << lines_log(LOGN), sm, st>>>(mv);
     DDA_LAUNCH_CHECK(INV ? "P4 x-inverse" : "P2 x-forward");
     return 0;
@@ -291,8 +316,9 @@ int launch_p3(const MatvecView<T>& mv, cudaStream_t st) {
     const Geometry& g = mv.g;
     const int W = 1 << mv.logW_z;
     const size_t sm = 3 * (size_t)col_elems(1 << LOGN, W) * sizeof(C<T>);
-    if (int rc = set_smem((const void*)k_p3<T, LOGN>, sm)) return rc;
-    dim3 grid((g.Lx + W - 1) / W, g.Ly);
+    static std::atomic<size_t> smem_set{0};
+    if (int rc = set_smem((const void*)k_p3<T, LOGN>, sm, smem_set)) return rc;
+    dim3 grid((g.Lx + W - 1) / W * mv.nb, g.Ly);
     k_p3<T, LOGN><<<grid, W << lines_log(LOGN), sm, st>>>(mv);
     DDA_LAUNCH_CHECK("P3 z-forward, spectrum product, z-inverse");
     return 0;
@@ -303,8 +329,9 @@ int launch_p5(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t st) 
     const Geometry& g = mv.g;
     const int W = 1 << mv.logW_y;
     const size_t sm = (size_t)col_elems(1 << LOGN, W) * sizeof(C<T>);
-    if (int rc = set_smem((const void*)k_p5<T, LOGN>, sm)) return rc;
-    dim3 grid((g.K + W - 1) / W, g.P, 3);
+    static std::atomic<size_t> smem_set{0};
+    if (int rc = set_smem((const void*)k_p5<T, LOGN>, sm, smem_set)) return rc;
+    dim3 grid((g.K + W - 1) / W, g.P, 3 * mv.nb);
     k_p5<T, LOGN><<<grid, W << lines_log(LOGN), sm, st>>>(mv, p, y);
     DDA_LAUNCH_CHECK("P5 y-inverse + diagonal + compress");
     return 0;
@@ -366,7 +393,7 @@ void configure_matvec(MatvecView<T>& mv) {
 }
 
 template <typename T>
-int launch_matvec(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t st) {
+static int launch_chunk(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t st) {
     const int dt = sizeof(T) == 8 ? 0 : 1;
     PassProfiler* pf = (mv.prof && mv.prof->on) ? mv.prof : nullptr;
     int rc;
@@ -381,6 +408,18 @@ int launch_matvec(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t 
     if (pf) { pf->end(st); pf->begin(dt, 4, st); }
     if ((rc = pass5<T>(mv, p, y, st))) return rc;
     if (pf) pf->end(st);
+    return 0;
+}
+
+template <typename T>
+int launch_matvec(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t st) {
+    if (mv.nb < 1 || mv.slots < 1) return fail(DDA_ERR_ARG, "matvec: empty batch");
+    for (int b0 = 0; b0 < mv.nb; b0 += mv.slots) {
+        MatvecView<T> m = mv;
+        m.b0 = b0;
+        m.nb = mv.nb - b0 < mv.slots ? mv.nb - b0 : mv.slots;
+        if (int rc = launch_chunk<T>(m, p, y, st)) return rc;
+    }
     return 0;
 }
 

@@ -15,13 +15,29 @@ struct MatvecView {
     const C<T>* ainv;   // [nmat][3] alpha^-1
     const C<T>* spec;   // [Hz][Hy][Hx][6], scaled by 1/(Lx Ly Lz)
     const C<T>* tw;     // twiddle table, kMaxLine entries
-    C<T>* Ay;           // [3][P][Ly][K]
-    C<T>* Bxy;          // [3][P][Ly][Lx]
+    C<T>* Ay;           // [slots][3][P][Ly][K]
+    C<T>* Bxy;          // [slots][3][P][Ly][Lx]
     int logW_y, logW_x, logW_z;  // tile widths (lines per CTA) of the passes
-    const int* status;  // optional: when *status != 0 every pass returns at once
+    const int* status;  // optional: right-hand side b is skipped while
+                        // status[b * status_stride] != 0
+    int status_stride;  // ints between the status words of consecutive RHS
     int conj;           // 1: compute conj(A conj(p)) = A^H p (A complex symmetric)
     PassProfiler* prof; // host object; when non-null and on, each pass is timed
+    // Batches: p and y hold nb right-hand sides of vstride elements each
+    // ([nb][3][N_d]); the work arrays hold `slots` of them.  launch_matvec
+    // runs the batch in chunks of at most `slots`; inside a launch, RHS
+    // b0 + j uses work slot j.
+    int nb = 1;
+    int slots = 1;
+    int b0 = 0;
+    int64_t vstride = 0;
 };
+
+// status of right-hand side b (true: skip it)
+template <typename T>
+__device__ __forceinline__ bool rhs_done(const MatvecView<T>& mv, int b) {
+    return mv.status && mv.status[(int64_t)b * mv.status_stride] != 0;
+}
 
 template <typename T> void configure_matvec(MatvecView<T>& mv);
 template <typename T> int launch_matvec(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t st);

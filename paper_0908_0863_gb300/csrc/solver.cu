@@ -1,19 +1,25 @@
 // Device-resident unpreconditioned Krylov solvers (OpenDDA Sec. 4): BiCG,
-// BiCGSTAB and QMR with coupled two-term recurrences, in the textbook forms
-// of Barrett et al. (1994) written for complex vectors: Hermitian products
-// x^H y in BiCG and BiCGSTAB, bilinear x^T y in QMR's Lanczos process with
-// A^T = A (the DDA matrix is complex symmetric, Sec. 3); A^H v is formed as
-// conj(A conj(v)).  BiCG starts from the shadow residual conj(r0),
-// BiCGSTAB from r0.
+// BiCG_sym, BiCGSTAB and QMR with coupled two-term recurrences, in the
+// textbook forms of Barrett et al. (1994) written for complex vectors:
+// Hermitian products x^H y in BiCG and BiCGSTAB, bilinear x^T y in BiCG_sym
+// and in QMR's Lanczos process with A^T = A (the DDA matrix is complex
+// symmetric, Sec. 3); A^H v is formed as conj(A conj(v)).  BiCG starts from
+// the shadow residual conj(r0), BiCGSTAB from r0.
+//
+// A solve runs a batch of right-hand sides with the same matrix in lock
+// step: every vector kernel covers all of them (blockIdx.y selects the
+// right-hand side), every scalar kernel runs one block per right-hand side,
+// and each matvec launch transforms the whole batch against the one shared
+// spectrum.  Each right-hand side has its own scalars and status word; once
+// it has converged, broken down or used its iterations, all later kernels
+// and the matvec passes skip its blocks.
 //
 // Every vector update is fused with the inner products that follow it;
-// each block writes its partial sums and a one-block "scalar" kernel adds
-// them in a fixed order (deterministic) and runs the scalar recurrence on
-// the device, so the host never waits inside an iteration.  A status word
-// in device memory stops all later kernels (and the matvec passes) once the
-// solve has converged or broken down.  Vector data may be complex64: the
-// products are then formed in FP32, summed in FP32 over at most eight
-// elements per thread and accumulated in FP64; all scalars are FP64.
+// each block writes its partial sums and the scalar kernel adds them in a
+// fixed order (deterministic) and runs the scalar recurrence on the
+// device, so the host never waits inside an iteration.  Vector data may be
+// complex64: the products are then formed in FP32, summed per thread with
+// compensation and accumulated in FP64; all scalars are FP64.
 #include <cmath>
 #include <cstring>
 
@@ -50,6 +56,7 @@ struct DotAcc {
     }
 };
 
+// partial sums of this block into part (already offset to its right-hand side)
 template <int NR>
 __device__ __forceinline__ void block_partials(double2 (&a)[NR], double2* __restrict__ part) {
     __shared__ double2 sm[NR][kVecThreads / 32];
@@ -74,14 +81,15 @@ __device__ __forceinline__ void block_partials(double2 (&a)[NR], double2* __rest
     }
 }
 
-// all threads of the one-block scalar kernel call this; every thread gets the sums
+// all threads of a scalar block call this; every thread gets the sums of
+// the nparts partials of its right-hand side
 template <int NR>
-__device__ __forceinline__ void final_sums(const double2* __restrict__ part, double2 (&out)[NR]) {
+__device__ __forceinline__ void final_sums(const double2* __restrict__ part, int nparts, double2 (&out)[NR]) {
     __shared__ double2 sm[NR][kVecThreads];
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
         double2 a = make_double2(0.0, 0.0);
-        for (int i = threadIdx.x; i < kVecBlocks; i += blockDim.x) {
+        for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
             a.x += part[i * kMaxRed + r].x;
             a.y += part[i * kMaxRed + r].y;
         }
@@ -117,22 +125,29 @@ __device__ __forceinline__ C<T> conjg(C<T> a) { return mk<T>(a.x, -a.y); }
 template <typename T>
 __device__ __forceinline__ C<T> norm2c(C<T> a) { return mk<T>(a.x * a.x + a.y * a.y, 0); }
 
-// Grid-strided loop over n elements, four per thread per step: the loads of
-// all four are issued before any of them is used, so every thread keeps
-// several memory requests in flight.
-constexpr int kUnroll = 4;
+// ---- batch addressing: vector kernels run a (blocks per RHS, nb) grid,
+// scalar kernels an (nb) grid
+template <typename P>
+__device__ __forceinline__ P* rhs_vec(P* p, int64_t n) { return p + (int64_t)blockIdx.y * n; }
+__device__ __forceinline__ double2* rhs_part(double2* part) {
+    return part + (int64_t)blockIdx.y * gridDim.x * kMaxRed;
+}
+
+// Grid-strided loop over the n elements of this block's right-hand side,
+// kVecUnroll per thread per step: the loads of all of them are issued
+// before any is used, so every thread keeps several requests in flight.
 template <typename Load, typename Op>
 __device__ __forceinline__ void vec_loop(int64_t n, Load load, Op op) {
     const int64_t S = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; base < n; base += kUnroll * S) {
-        decltype(load(base)) v[kUnroll];
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; base < n; base += kVecUnroll * S) {
+        decltype(load(base)) v[kVecUnroll];
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
+        for (int u = 0; u < kVecUnroll; ++u) {
             const int64_t i = base + u * S;
             if (i < n) v[u] = load(i);
         }
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
+        for (int u = 0; u < kVecUnroll; ++u) {
             const int64_t i = base + u * S;
             if (i < n) op(i, v[u]);
         }
@@ -152,6 +167,9 @@ template <typename T>
 __global__ void __launch_bounds__(kVecThreads) k_init(const C<T>* __restrict__ b, C<T>* __restrict__ x,
                                                       C<T>* __restrict__ r, C<T>* __restrict__ rt, int64_t n,
                                                       int has_x0, int conj_rt, double2* __restrict__ part) {
+    b = rhs_vec(b, n); x = rhs_vec(x, n); r = rhs_vec(r, n);
+    if (rt) rt = rhs_vec(rt, n);
+    part = rhs_part(part);
     DotAcc<T> nb, nr, rr;
     nb.init(); nr.init(); rr.init();
     vec_loop(n, [&](int64_t i) { return V2<T>{b[i], has_x0 ? r[i] : mk<T>(0, 0)}; },
@@ -170,21 +188,32 @@ __global__ void __launch_bounds__(kVecThreads) k_init(const C<T>* __restrict__ b
     block_partials<3>(a, part);
 }
 
+// ctl: per right-hand side tolerance and cap (device) or null for tol and
+// max_iter; a tolerance <= 0 marks a right-hand side that this solve leaves
+// alone
 __global__ void __launch_bounds__(kVecThreads) k_init_scalar(KState* st, const double2* __restrict__ part,
-                                                             double tol, int qmr) {
+                                                             int nparts, const RhsCtl* __restrict__ ctl,
+                                                             double tol, int max_iter, int qmr) {
+    st += blockIdx.x;
+    part += (int64_t)blockIdx.x * nparts * kMaxRed;
     double2 s[3];
-    final_sums<3>(part, s);
+    final_sums<3>(part, nparts, s);
     if (threadIdx.x != 0) return;
-    st->status = ST_RUN;
+    const double tl = ctl ? ctl[blockIdx.x].tol : tol;
+    const int maxit = ctl ? ctl[blockIdx.x].maxit : max_iter;
     st->iter = 0;
     st->matvecs = 0;
+    st->maxit = maxit;
     st->bnorm2 = s[0].x;
-    st->tol2 = tol * tol;
+    st->tol2 = tl * tl;
     for (int i = 0; i < S_NSLOTS; ++i) st->s[i] = make_double2(0.0, 0.0);
+    st->status = ST_RUN;
+    if (!(tl > 0.0)) { st->rel2 = 0.0; st->status = ST_CONVERGED; return; }
     if (!isfinite(s[0].x) || !isfinite(s[1].x)) { st->status = ST_NAN; return; }
     if (s[0].x == 0.0) { st->rel2 = 0.0; st->status = ST_CONVERGED; return; }
     st->rel2 = s[1].x / s[0].x;
     if (st->rel2 <= st->tol2) { st->status = ST_CONVERGED; return; }
+    if (maxit < 1) { st->status = ST_MAXIT; return; }
     st->s[S_RHO] = s[2];
     if (qmr) {
         st->s[S_RHOQ] = make_double2(sqrt(s[1].x), 0.0);
@@ -194,12 +223,24 @@ __global__ void __launch_bounds__(kVecThreads) k_init_scalar(KState* st, const d
     }
 }
 
+// end of an iteration: convergence or the iteration cap (true: stop here)
+__device__ __forceinline__ bool end_of_iteration(KState* st, double rel2) {
+    st->iter += 1;
+    st->rel2 = rel2;
+    if (!isfinite(rel2)) { st->status = ST_NAN; return true; }
+    if (rel2 <= st->tol2) { st->status = ST_CONVERGED; return true; }
+    if (st->iter >= st->maxit) { st->status = ST_MAXIT; return true; }
+    return false;
+}
+
 // partial dot products: kind 0 = a^H b, kind 1 = a^T b
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads) k_dot1(const KState* st, const C<T>* __restrict__ a0,
                                                       const C<T>* __restrict__ b0, int kind0, int64_t n,
                                                       double2* __restrict__ part) {
+    st += blockIdx.y;
     if (st->status != ST_RUN) return;
+    a0 = rhs_vec(a0, n); b0 = rhs_vec(b0, n); part = rhs_part(part);
     DotAcc<T> d0;
     d0.init();
     vec_loop(n, [&](int64_t i) { return V2<T>{a0[i], b0[i]}; },
@@ -214,7 +255,9 @@ template <typename T>
 __global__ void __launch_bounds__(kVecThreads) k_dot_ts(const KState* st, const C<T>* __restrict__ t,
                                                         const C<T>* __restrict__ s, int64_t n,
                                                         double2* __restrict__ part) {
+    st += blockIdx.y;
     if (st->status != ST_RUN) return;
+    t = rhs_vec(t, n); s = rhs_vec(s, n); part = rhs_part(part);
     DotAcc<T> tt, ts;
     tt.init(); ts.init();
     vec_loop(n, [&](int64_t i) { return V2<T>{t[i], s[i]}; },
@@ -233,7 +276,9 @@ template <typename T>
 __global__ void __launch_bounds__(kVecThreads) k_bcs_p(const KState* st, const C<T>* __restrict__ r,
                                                        C<T>* __restrict__ p, const C<T>* __restrict__ v,
                                                        int64_t n, int first) {
+    st += blockIdx.y;
     if (st->status != ST_RUN) return;
+    r = rhs_vec(r, n); p = rhs_vec(p, n); v = rhs_vec(v, n);
     const C<T> beta = to_t<T>(st->s[S_BETA]), omega = to_t<T>(st->s[S_OMEGA]);
     if (first) {
         vec_loop(n, [&](int64_t i) { return V1<T>{r[i]}; }, [&](int64_t i, const V1<T>& q) { p[i] = q.a; });
@@ -248,7 +293,9 @@ template <typename T>
 __global__ void __launch_bounds__(kVecThreads) k_bcs_s(const KState* st, const C<T>* __restrict__ r,
                                                        const C<T>* __restrict__ v, C<T>* __restrict__ s,
                                                        int64_t n, double2* __restrict__ part) {
+    st += blockIdx.y;
     if (st->status != ST_RUN) return;
+    r = rhs_vec(r, n); v = rhs_vec(v, n); s = rhs_vec(s, n); part = rhs_part(part);
     const C<T> alpha = to_t<T>(st->s[S_ALPHA]);
     DotAcc<T> ns;
     ns.init();
@@ -271,8 +318,11 @@ __global__ void __launch_bounds__(kVecThreads) k_bcs_xr(const KState* st, C<T>* 
                                                         const C<T>* __restrict__ t, C<T>* __restrict__ r,
                                                         const C<T>* __restrict__ rt, int64_t n,
                                                         double2* __restrict__ part) {
+    st += blockIdx.y;
     const int status = st->status;
     if (status != ST_RUN && status != ST_HALF) return;
+    x = rhs_vec(x, n); p = rhs_vec(p, n); s = rhs_vec(s, n); t = rhs_vec(t, n);
+    r = rhs_vec(r, n); rt = rhs_vec(rt, n); part = rhs_part(part);
     const C<T> alpha = to_t<T>(st->s[S_ALPHA]), omega = to_t<T>(st->s[S_OMEGA]);
     if (status == ST_HALF) {
         vec_loop(n, [&](int64_t i) { return V2<T>{x[i], p[i]}; },
@@ -295,14 +345,17 @@ __global__ void __launch_bounds__(kVecThreads) k_bcs_xr(const KState* st, C<T>* 
 }
 
 // step: 0 = alpha from sigma, 1 = half-step check, 2 = omega, 3 = end of iteration
-__global__ void __launch_bounds__(kVecThreads) k_bcs_scalar(KState* st, const double2* __restrict__ part, int step) {
+__global__ void __launch_bounds__(kVecThreads) k_bcs_scalar(KState* st, const double2* __restrict__ part,
+                                                            int nparts, int step) {
+    st += blockIdx.x;
+    part += (int64_t)blockIdx.x * nparts * kMaxRed;
     if (step == 3 && st->status == ST_HALF) {
         if (threadIdx.x == 0) { st->status = ST_CONVERGED; st->iter += 1; st->rel2 = st->s[S_TMP].x; }
         return;
     }
     if (st->status != ST_RUN) return;
     double2 s[2];
-    final_sums<2>(part, s);
+    final_sums<2>(part, nparts, s);
     if (threadIdx.x != 0) return;
     if (step == 0) {
         st->matvecs += 1;
@@ -322,10 +375,7 @@ __global__ void __launch_bounds__(kVecThreads) k_bcs_scalar(KState* st, const do
         if (tt.x == 0.0) { st->status = ST_BREAKDOWN; return; }
         st->s[S_OMEGA] = make_double2(ts.x / tt.x, ts.y / tt.x);
     } else {
-        st->iter += 1;
-        st->rel2 = s[0].x / st->bnorm2;
-        if (!isfinite(st->rel2)) { st->status = ST_NAN; return; }
-        if (st->rel2 <= st->tol2) { st->status = ST_CONVERGED; return; }
+        if (end_of_iteration(st, s[0].x / st->bnorm2)) return;
         const double2 rho_new = s[1];
         if (is_zero(st->s[S_OMEGA]) || is_zero(rho_new)) { st->status = ST_BREAKDOWN; return; }
         st->s[S_BETA] = dmul(ddiv(rho_new, st->s[S_RHO]), ddiv(st->s[S_ALPHA], st->s[S_OMEGA]));
@@ -339,7 +389,9 @@ template <typename T>
 __global__ void __launch_bounds__(kVecThreads) k_bicg_p(const KState* st, const C<T>* __restrict__ r,
                                                         const C<T>* __restrict__ rt, C<T>* __restrict__ p,
                                                         C<T>* __restrict__ pt, int64_t n, int first) {
+    st += blockIdx.y;
     if (st->status != ST_RUN) return;
+    r = rhs_vec(r, n); rt = rhs_vec(rt, n); p = rhs_vec(p, n); pt = rhs_vec(pt, n);
     const C<T> beta = to_t<T>(st->s[S_BETA]);
     const C<T> cbeta = conjg<T>(beta);
     if (first) {
@@ -361,7 +413,10 @@ __global__ void __launch_bounds__(kVecThreads) k_bicg_update(const KState* st, C
                                                              const C<T>* __restrict__ qt, C<T>* __restrict__ r,
                                                              C<T>* __restrict__ rt, int64_t n,
                                                              double2* __restrict__ part) {
+    st += blockIdx.y;
     if (st->status != ST_RUN) return;
+    x = rhs_vec(x, n); p = rhs_vec(p, n); q = rhs_vec(q, n); qt = rhs_vec(qt, n);
+    r = rhs_vec(r, n); rt = rhs_vec(rt, n); part = rhs_part(part);
     const C<T> alpha = to_t<T>(st->s[S_ALPHA]);
     const C<T> nalpha = mk<T>(-alpha.x, -alpha.y), ncalpha = mk<T>(-alpha.x, alpha.y);
     DotAcc<T> nr, rr;
@@ -388,7 +443,9 @@ __global__ void __launch_bounds__(kVecThreads) k_cocg_update(const KState* st, C
                                                              const C<T>* __restrict__ p, const C<T>* __restrict__ q,
                                                              C<T>* __restrict__ r, int64_t n,
                                                              double2* __restrict__ part) {
+    st += blockIdx.y;
     if (st->status != ST_RUN) return;
+    x = rhs_vec(x, n); p = rhs_vec(p, n); q = rhs_vec(q, n); r = rhs_vec(r, n); part = rhs_part(part);
     const C<T> alpha = to_t<T>(st->s[S_ALPHA]);
     const C<T> nalpha = mk<T>(-alpha.x, -alpha.y);
     DotAcc<T> nr, rr;
@@ -408,11 +465,13 @@ __global__ void __launch_bounds__(kVecThreads) k_cocg_update(const KState* st, C
 
 // step 0: alpha = rho / sigma (sigma = pt^H q for BiCG, p^T q for BiCG_sym);
 // step 1: end of iteration.  mv: products per iteration (2 or 1)
-__global__ void __launch_bounds__(kVecThreads) k_bicg_scalar(KState* st, const double2* __restrict__ part, int step,
-                                                             int mv) {
+__global__ void __launch_bounds__(kVecThreads) k_bicg_scalar(KState* st, const double2* __restrict__ part,
+                                                             int nparts, int step, int mv) {
+    st += blockIdx.x;
+    part += (int64_t)blockIdx.x * nparts * kMaxRed;
     if (st->status != ST_RUN) return;
     double2 s[2];
-    final_sums<2>(part, s);
+    final_sums<2>(part, nparts, s);
     if (threadIdx.x != 0) return;
     if (step == 0) {
         st->matvecs += mv;
@@ -421,10 +480,7 @@ __global__ void __launch_bounds__(kVecThreads) k_bicg_scalar(KState* st, const d
         if (is_zero(sigma)) { st->status = ST_BREAKDOWN; return; }
         st->s[S_ALPHA] = ddiv(st->s[S_RHO], sigma);
     } else {
-        st->iter += 1;
-        st->rel2 = s[0].x / st->bnorm2;
-        if (!isfinite(st->rel2)) { st->status = ST_NAN; return; }
-        if (st->rel2 <= st->tol2) { st->status = ST_CONVERGED; return; }
+        if (end_of_iteration(st, s[0].x / st->bnorm2)) return;
         const double2 rho_new = s[1];
         if (is_zero(rho_new)) { st->status = ST_BREAKDOWN; return; }
         st->s[S_BETA] = ddiv(rho_new, st->s[S_RHO]);
@@ -438,7 +494,9 @@ template <typename T>
 __global__ void __launch_bounds__(kVecThreads) k_qmr_vw(const KState* st, const C<T>* __restrict__ vt,
                                                         const C<T>* __restrict__ wt, C<T>* __restrict__ v,
                                                         C<T>* __restrict__ w, int64_t n, double2* __restrict__ part) {
+    st += blockIdx.y;
     if (st->status != ST_RUN) return;
+    vt = rhs_vec(vt, n); wt = rhs_vec(wt, n); v = rhs_vec(v, n); w = rhs_vec(w, n); part = rhs_part(part);
     const T irho = (T)(1.0 / st->s[S_RHOQ].x), ixi = (T)(1.0 / st->s[S_XI].x);
     DotAcc<T> d;
     d.init();
@@ -459,7 +517,9 @@ template <typename T>
 __global__ void __launch_bounds__(kVecThreads) k_qmr_pq(const KState* st, const C<T>* __restrict__ v,
                                                         const C<T>* __restrict__ w, C<T>* __restrict__ p,
                                                         C<T>* __restrict__ q, int64_t n, int first) {
+    st += blockIdx.y;
     if (st->status != ST_RUN) return;
+    v = rhs_vec(v, n); w = rhs_vec(w, n); p = rhs_vec(p, n); q = rhs_vec(q, n);
     const C<T> ncp = to_t<T>(st->s[S_NCP]), ncq = to_t<T>(st->s[S_NCQ]);
     if (first) {
         vec_loop(n, [&](int64_t i) { return V2<T>{v[i], w[i]}; },
@@ -479,7 +539,10 @@ __global__ void __launch_bounds__(kVecThreads) k_qmr_vtwt(const KState* st, cons
                                                           const C<T>* __restrict__ v, const C<T>* __restrict__ w,
                                                           C<T>* __restrict__ vt, C<T>* __restrict__ wt, int64_t n,
                                                           double2* __restrict__ part) {
+    st += blockIdx.y;
     if (st->status != ST_RUN) return;
+    pt = rhs_vec(pt, n); v = rhs_vec(v, n); w = rhs_vec(w, n); vt = rhs_vec(vt, n); wt = rhs_vec(wt, n);
+    part = rhs_part(part);
     const C<T> beta = to_t<T>(st->s[S_BETA]);
     const C<T> nbeta = mk<T>(-beta.x, -beta.y);
     DotAcc<T> a, b;
@@ -505,7 +568,10 @@ __global__ void __launch_bounds__(kVecThreads) k_qmr_ds(const KState* st, const 
                                                         C<T>* __restrict__ s, C<T>* __restrict__ x,
                                                         C<T>* __restrict__ r, int64_t n, int first,
                                                         double2* __restrict__ part) {
+    st += blockIdx.y;
     if (st->status != ST_RUN) return;
+    p = rhs_vec(p, n); pt = rhs_vec(pt, n); d = rhs_vec(d, n); s = rhs_vec(s, n);
+    x = rhs_vec(x, n); r = rhs_vec(r, n); part = rhs_part(part);
     const C<T> eta = to_t<T>(st->s[S_ETA]);
     const T f = first ? (T)0 : (T)st->s[S_F].x;
     DotAcc<T> nr;
@@ -531,11 +597,13 @@ __global__ void __launch_bounds__(kVecThreads) k_qmr_ds(const KState* st, const 
 
 // step 0: delta (+ p/q coefficients); 1: eps, beta; 2: rho, xi, theta,
 // gamma, eta, f; 3: end of iteration
-__global__ void __launch_bounds__(kVecThreads) k_qmr_scalar(KState* st, const double2* __restrict__ part, int step,
-                                                            int first) {
+__global__ void __launch_bounds__(kVecThreads) k_qmr_scalar(KState* st, const double2* __restrict__ part,
+                                                            int nparts, int step, int first) {
+    st += blockIdx.x;
+    part += (int64_t)blockIdx.x * nparts * kMaxRed;
     if (st->status != ST_RUN) return;
     double2 s[2];
-    final_sums<2>(part, s);
+    final_sums<2>(part, nparts, s);
     if (threadIdx.x != 0) return;
     if (step == 0) {
         const double rho = st->s[S_RHOQ].x, xi = st->s[S_XI].x;
@@ -576,10 +644,7 @@ __global__ void __launch_bounds__(kVecThreads) k_qmr_scalar(KState* st, const do
         st->s[S_XI_NEW] = make_double2(xi_new, 0.0);
         st->s[S_TMP] = make_double2(theta, gamma);
     } else {
-        st->iter += 1;
-        st->rel2 = s[0].x / st->bnorm2;
-        if (!isfinite(st->rel2)) { st->status = ST_NAN; return; }
-        if (st->rel2 <= st->tol2) { st->status = ST_CONVERGED; return; }
+        if (end_of_iteration(st, s[0].x / st->bnorm2)) return;
         st->s[S_RHOQ] = st->s[S_RHO_NEW];
         st->s[S_XI] = st->s[S_XI_NEW];
         st->s[S_THETA_OLD] = make_double2(st->s[S_TMP].x, 0.0);
@@ -590,6 +655,7 @@ __global__ void __launch_bounds__(kVecThreads) k_qmr_scalar(KState* st, const do
 // ------------------------------------------------------ refinement helpers
 __global__ void __launch_bounds__(kVecThreads) k_norm2_c128(const double2* __restrict__ a, int64_t n,
                                                             double2* __restrict__ part) {
+    a = rhs_vec(a, n); part = rhs_part(part);
     DotAcc<double> d;
     d.init();
     vec_loop(n, [&](int64_t i) { return V1<double>{a[i]}; },
@@ -600,7 +666,10 @@ __global__ void __launch_bounds__(kVecThreads) k_norm2_c128(const double2* __res
 }
 
 __global__ void __launch_bounds__(kVecThreads) k_resid(const double2* __restrict__ b, double2* __restrict__ r,
-                                                       int64_t n, double2* __restrict__ part) {
+                                                       int64_t n, const RhsCtl* __restrict__ ctl,
+                                                       double2* __restrict__ part) {
+    if (ctl && ctl[blockIdx.y].skip) return;
+    b = rhs_vec(b, n); r = rhs_vec(r, n); part = rhs_part(part);
     DotAcc<double> d;
     d.init();
     vec_loop(n, [&](int64_t i) { return V2<double>{b[i], r[i]}; },
@@ -614,32 +683,38 @@ __global__ void __launch_bounds__(kVecThreads) k_resid(const double2* __restrict
     block_partials<1>(s, part);
 }
 
-__global__ void __launch_bounds__(kVecThreads) k_slot(KState* st, const double2* __restrict__ part, int slot) {
+// sum of the partials of each right-hand side into st[b].s[slot]
+__global__ void __launch_bounds__(kVecThreads) k_slot(KState* st, const double2* __restrict__ part, int nparts,
+                                                      int slot, const RhsCtl* __restrict__ ctl) {
+    if (ctl && ctl[blockIdx.x].skip) return;
+    st += blockIdx.x;
+    part += (int64_t)blockIdx.x * nparts * kMaxRed;
     double2 s[1];
-    final_sums<1>(part, s);
+    final_sums<1>(part, nparts, s);
     if (threadIdx.x == 0) st->s[slot] = s[0];
 }
 
-__global__ void __launch_bounds__(kVecThreads) k_to_c64(const double2* __restrict__ r, double scale,
+__global__ void __launch_bounds__(kVecThreads) k_to_c64(const double2* __restrict__ r,
+                                                        const RhsCtl* __restrict__ ctl,
                                                         float2* __restrict__ out, int64_t n) {
+    const double sc = ctl[blockIdx.y].scale;
+    r = rhs_vec(r, n); out = rhs_vec(out, n);
     vec_loop(n, [&](int64_t i) { return V1<double>{r[i]}; },
              [&](int64_t i, const V1<double>& q) {
-                 out[i] = make_float2((float)(q.a.x * scale), (float)(q.a.y * scale));
+                 out[i] = make_float2((float)(q.a.x * sc), (float)(q.a.y * sc));
              });
 }
 
-__global__ void __launch_bounds__(kVecThreads) k_axpy_c64(double2* __restrict__ x, double scale,
+__global__ void __launch_bounds__(kVecThreads) k_axpy_c64(double2* __restrict__ x, const RhsCtl* __restrict__ ctl,
                                                           const float2* __restrict__ d, int64_t n) {
+    const double sc = ctl[blockIdx.y].mult;
+    if (sc == 0.0) return;
+    x = rhs_vec(x, n); d = rhs_vec(d, n);
     vec_loop(n, [&](int64_t i) { return V1<double>{make_double2((double)d[i].x, (double)d[i].y)}; },
              [&](int64_t i, const V1<double>& q) {
-                 x[i].x += scale * q.a.x;
-                 x[i].y += scale * q.a.y;
+                 x[i].x += sc * q.a.x;
+                 x[i].y += sc * q.a.y;
              });
-}
-
-__global__ void __launch_bounds__(kVecThreads) k_copy(double2* __restrict__ dst, const double2* __restrict__ src,
-                                                      int64_t n) {
-    vec_loop(n, [&](int64_t i) { return V1<double>{src[i]}; }, [&](int64_t i, const V1<double>& q) { dst[i] = q.a; });
 }
 
 }  // namespace
@@ -651,14 +726,112 @@ static int run_matvec(MatvecView<T> mv, const C<T>* p, C<T>* y, int conj, cudaSt
     return launch_matvec<T>(mv, p, y, st);
 }
 
+// the kernels of one iteration (first: the first iteration's variants)
 template <typename T>
-int krylov_solve(int method, MatvecView<T> mv, KrylovWork<T>& ws, const C<T>* b, C<T>* x, bool use_x0,
-                 double tol, int max_iter, KState* hs, cudaStream_t st, SolveResult* res) {
+static int enqueue_iteration(int method, const MatvecView<T>& mv, KrylovWork<T>& ws, C<T>* x, int first,
+                             cudaStream_t st) {
     const int64_t n = ws.n;
-    const dim3 G(kVecBlocks), B(kVecThreads);
+    const int nb = ws.nb, gx = vec_blocks(n, nb);
+    const dim3 G(gx, nb), B(kVecThreads);
     double2* part = ws.part;
     KState* ds = ws.st;
-    mv.status = &ds->status;
+    C<T>** v = ws.v;
+    C<T>*r = v[0], *rt = v[1];
+    int rc;
+    int64_t k = 0;
+    if (method == DDA_BICGSTAB) {
+        C<T>*p = v[2], *vv = v[3], *s = v[4], *t = v[5];
+        k_bcs_p<T><<<G, B, 0, st>>>(ds, r, p, vv, n, first);
+        if ((rc = run_matvec<T>(mv, p, vv, 0, st))) return rc;
+        k_dot1<T><<<G, B, 0, st>>>(ds, rt, vv, 0, n, part);
+        k_bcs_scalar<<<nb, B, 0, st>>>(ds, part, gx, 0);
+        k_bcs_s<T><<<G, B, 0, st>>>(ds, r, vv, s, n, part);
+        k_bcs_scalar<<<nb, B, 0, st>>>(ds, part, gx, 1);
+        if ((rc = run_matvec<T>(mv, s, t, 0, st))) return rc;
+        k_dot_ts<T><<<G, B, 0, st>>>(ds, t, s, n, part);
+        k_bcs_scalar<<<nb, B, 0, st>>>(ds, part, gx, 2);
+        k_bcs_xr<T><<<G, B, 0, st>>>(ds, x, p, s, t, r, rt, n, part);
+        k_bcs_scalar<<<nb, B, 0, st>>>(ds, part, gx, 3);
+        k = 9;
+    } else if (method == DDA_BICG) {
+        C<T>*p = v[2], *pt = v[3], *q = v[4], *qt = v[5];
+        k_bicg_p<T><<<G, B, 0, st>>>(ds, r, rt, p, pt, n, first);
+        if ((rc = run_matvec<T>(mv, p, q, 0, st))) return rc;
+        if ((rc = run_matvec<T>(mv, pt, qt, 1, st))) return rc;
+        k_dot1<T><<<G, B, 0, st>>>(ds, pt, q, 0, n, part);
+        k_bicg_scalar<<<nb, B, 0, st>>>(ds, part, gx, 0, 2);
+        k_bicg_update<T><<<G, B, 0, st>>>(ds, x, p, q, qt, r, rt, n, part);
+        k_bicg_scalar<<<nb, B, 0, st>>>(ds, part, gx, 1, 2);
+        k = 5;
+    } else if (method == DDA_BICG_SYM) {
+        // p = r + beta p (k_bcs_p with omega = 0), q = A p
+        C<T>*p = v[2], *q = v[3];
+        k_bcs_p<T><<<G, B, 0, st>>>(ds, r, p, p, n, first);
+        if ((rc = run_matvec<T>(mv, p, q, 0, st))) return rc;
+        k_dot1<T><<<G, B, 0, st>>>(ds, p, q, 1, n, part);
+        k_bicg_scalar<<<nb, B, 0, st>>>(ds, part, gx, 0, 1);
+        k_cocg_update<T><<<G, B, 0, st>>>(ds, x, p, q, r, n, part);
+        k_bicg_scalar<<<nb, B, 0, st>>>(ds, part, gx, 1, 1);
+        k = 5;
+    } else {
+        C<T>*vt = v[1], *wt = v[2], *vv = v[3], *w = v[4], *p = v[5], *q = v[6], *pt = v[7], *d = v[8],
+            *s = v[9];
+        k_qmr_vw<T><<<G, B, 0, st>>>(ds, vt, wt, vv, w, n, part);
+        k_qmr_scalar<<<nb, B, 0, st>>>(ds, part, gx, 0, first);
+        k_qmr_pq<T><<<G, B, 0, st>>>(ds, vv, w, p, q, n, first);
+        if ((rc = run_matvec<T>(mv, p, pt, 0, st))) return rc;
+        k_dot1<T><<<G, B, 0, st>>>(ds, q, pt, 1, n, part);
+        k_qmr_scalar<<<nb, B, 0, st>>>(ds, part, gx, 1, first);
+        if ((rc = run_matvec<T>(mv, q, wt, 0, st))) return rc;   // A^T q = A q
+        k_qmr_vtwt<T><<<G, B, 0, st>>>(ds, pt, vv, w, vt, wt, n, part);
+        k_qmr_scalar<<<nb, B, 0, st>>>(ds, part, gx, 2, first);
+        k_qmr_ds<T><<<G, B, 0, st>>>(ds, p, pt, d, s, x, r, n, first, part);
+        k_qmr_scalar<<<nb, B, 0, st>>>(ds, part, gx, 3, first);
+        k = 9;
+    }
+    note_launches(k);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "krylov iteration");
+    return 0;
+}
+
+// records one steady iteration into an executable graph; false: capture
+// was not possible (the iteration then runs with plain launches)
+template <typename T>
+static bool capture_iteration(int method, const MatvecView<T>& mv, KrylovWork<T>& ws, C<T>* x,
+                              cudaGraphExec_t* exec, int64_t* kernels) {
+    if (!ws.capture) return false;
+    if (cudaStreamBeginCapture(ws.capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    int64_t sink = 0;
+    capture_launches_into(&sink);
+    const int rc = enqueue_iteration<T>(method, mv, ws, x, 0, ws.capture);
+    capture_launches_into(nullptr);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(ws.capture, &graph);
+    bool ok = rc == 0 && e == cudaSuccess && graph != nullptr;
+    if (ok && cudaGraphInstantiate(exec, graph, 0) != cudaSuccess) ok = false;
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) {
+        cudaGetLastError();
+        set_error("");
+        return false;
+    }
+    *kernels = sink;
+    return true;
+}
+
+template <typename T>
+int krylov_solve(int method, MatvecView<T> mv, KrylovWork<T>& ws, const C<T>* b, C<T>* x, bool use_x0,
+                 const RhsCtl* ctl, double tol, int max_iter, cudaStream_t st, SolveResult* res) {
+    const int64_t n = ws.n;
+    const int nb = ws.nb, gx = vec_blocks(n, nb);
+    mv.nb = nb;
+    mv.vstride = n;
+    mv.status = &ws.st->status;
+    mv.status_stride = kStateInts;
     C<T>** v = ws.v;
     int rc;
     // ---- initial residual (status is not yet valid: use a status-free matvec)
@@ -671,146 +844,122 @@ int krylov_solve(int method, MatvecView<T> mv, KrylovWork<T>& ws, const C<T>* b,
     C<T>* rt = v[1];  // shadow residual (BiCG, BiCGSTAB) or vt (QMR)
     // BiCG: shadow conj(r0); BiCG_sym: rho = r^T r = conj(r)^H r, the same start
     const int conj_rt = (method == DDA_BICG || method == DDA_BICG_SYM) ? 1 : 0;
-    k_init<T><<<G, B, 0, st>>>(b, x, r, rt, n, use_x0 ? 1 : 0, conj_rt, part);
+    k_init<T><<<dim3(gx, nb), kVecThreads, 0, st>>>(b, x, r, rt, n, use_x0 ? 1 : 0, conj_rt, ws.part);
     DDA_LAUNCH_CHECK("krylov init");
-    k_init_scalar<<<1, B, 0, st>>>(ds, part, tol, method == DDA_QMR ? 1 : 0);
+    k_init_scalar<<<nb, kVecThreads, 0, st>>>(ws.st, ws.part, gx, ctl, tol, max_iter,
+                                              method == DDA_QMR ? 1 : 0);
     DDA_LAUNCH_CHECK("krylov init scalar");
     if (method == DDA_QMR) {  // vt = r (v[1]), wt = r (v[2])
-        DDA_CUDA_TRY(cudaMemcpyAsync(v[2], r, n * sizeof(C<T>), cudaMemcpyDeviceToDevice, st));
+        DDA_CUDA_TRY(cudaMemcpyAsync(v[2], r, nb * n * sizeof(C<T>), cudaMemcpyDeviceToDevice, st));
     }
-    // ---- iterations, polling the status two iterations behind
+    // ---- iterations, polling the status words two iterations behind
     cudaEvent_t ev[2];
     DDA_CUDA_TRY(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
     DDA_CUDA_TRY(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
-    volatile int* hstat = &hs[0].status;
-    KState* hslots = hs;  // hs[0], hs[1]: two pinned status copies
+    const bool graphs = ws.capture && !(mv.prof && mv.prof->on);
+    cudaGraphExec_t exec = nullptr;
+    int64_t graph_kernels = 0;
+    bool have_graph = false;
     int it = 0;
     bool done = false;
     rc = 0;
-    while (it < max_iter && !done) {
-        ++it;
-        const int first = it == 1;
-        if (method == DDA_BICGSTAB) {
-            C<T>*p = v[2], *vv = v[3], *s = v[4], *t = v[5];
-            k_bcs_p<T><<<G, B, 0, st>>>(ds, r, p, vv, n, first);
-            if ((rc = run_matvec<T>(mv, p, vv, 0, st))) break;
-            k_dot1<T><<<G, B, 0, st>>>(ds, rt, vv, 0, n, part);
-            k_bcs_scalar<<<1, B, 0, st>>>(ds, part, 0);
-            k_bcs_s<T><<<G, B, 0, st>>>(ds, r, vv, s, n, part);
-            k_bcs_scalar<<<1, B, 0, st>>>(ds, part, 1);
-            if ((rc = run_matvec<T>(mv, s, t, 0, st))) break;
-            k_dot_ts<T><<<G, B, 0, st>>>(ds, t, s, n, part);
-            k_bcs_scalar<<<1, B, 0, st>>>(ds, part, 2);
-            k_bcs_xr<T><<<G, B, 0, st>>>(ds, x, p, s, t, r, rt, n, part);
-            k_bcs_scalar<<<1, B, 0, st>>>(ds, part, 3);
-        } else if (method == DDA_BICG) {
-            C<T>*p = v[2], *pt = v[3], *q = v[4], *qt = v[5];
-            k_bicg_p<T><<<G, B, 0, st>>>(ds, r, rt, p, pt, n, first);
-            if ((rc = run_matvec<T>(mv, p, q, 0, st))) break;
-            if ((rc = run_matvec<T>(mv, pt, qt, 1, st))) break;
-            k_dot1<T><<<G, B, 0, st>>>(ds, pt, q, 0, n, part);
-            k_bicg_scalar<<<1, B, 0, st>>>(ds, part, 0, 2);
-            k_bicg_update<T><<<G, B, 0, st>>>(ds, x, p, q, qt, r, rt, n, part);
-            k_bicg_scalar<<<1, B, 0, st>>>(ds, part, 1, 2);
-        } else if (method == DDA_BICG_SYM) {
-            // p = r + beta p (k_bcs_p with omega = 0), q = A p
-            C<T>*p = v[2], *q = v[3];
-            k_bcs_p<T><<<G, B, 0, st>>>(ds, r, p, p, n, first);
-            if ((rc = run_matvec<T>(mv, p, q, 0, st))) break;
-            k_dot1<T><<<G, B, 0, st>>>(ds, p, q, 1, n, part);
-            k_bicg_scalar<<<1, B, 0, st>>>(ds, part, 0, 1);
-            k_cocg_update<T><<<G, B, 0, st>>>(ds, x, p, q, r, n, part);
-            k_bicg_scalar<<<1, B, 0, st>>>(ds, part, 1, 1);
-        } else {
-            C<T>*vt = v[1], *wt = v[2], *vv = v[3], *w = v[4], *p = v[5], *q = v[6], *pt = v[7], *d = v[8],
-                *s = v[9];
-            k_qmr_vw<T><<<G, B, 0, st>>>(ds, vt, wt, vv, w, n, part);
-            k_qmr_scalar<<<1, B, 0, st>>>(ds, part, 0, first);
-            k_qmr_pq<T><<<G, B, 0, st>>>(ds, vv, w, p, q, n, first);
-            if ((rc = run_matvec<T>(mv, p, pt, 0, st))) break;
-            k_dot1<T><<<G, B, 0, st>>>(ds, q, pt, 1, n, part);
-            k_qmr_scalar<<<1, B, 0, st>>>(ds, part, 1, first);
-            if ((rc = run_matvec<T>(mv, q, wt, 0, st))) break;   // A^T q = A q
-            k_qmr_vtwt<T><<<G, B, 0, st>>>(ds, pt, vv, w, vt, wt, n, part);
-            k_qmr_scalar<<<1, B, 0, st>>>(ds, part, 2, first);
-            k_qmr_ds<T><<<G, B, 0, st>>>(ds, p, pt, d, s, x, r, n, first, part);
-            k_qmr_scalar<<<1, B, 0, st>>>(ds, part, 3, first);
-        }
-        note_launches(method == DDA_BICGSTAB ? 8 : method == DDA_QMR ? 9 : 5);
-        {
-            cudaError_t e = cudaGetLastError();
-            if (e != cudaSuccess) { rc = cuda_fail(e, "krylov iteration"); break; }
-        }
-        // copy the status word of this iteration; check the one two behind
-        const int slot = it & 1;
-        if (it >= 3) {
-            cudaError_t e = cudaEventSynchronize(ev[slot]);
-            if (e != cudaSuccess) { rc = cuda_fail(e, "krylov poll"); break; }
-            if (hslots[slot].status != ST_RUN) done = true;
-        }
-        cudaMemcpyAsync(&hslots[slot].status, &ds->status, sizeof(int), cudaMemcpyDeviceToHost, st);
-        cudaEventRecord(ev[slot], st);
+    // every right-hand side stops on the device after its iteration cap; the
+    // two extra rounds cover the polling lag
+    int cap = max_iter;
+    if (ctl) {
+        // caps live on the device: bound the host loop by the largest one
+        RhsCtl* hc = reinterpret_cast<RhsCtl*>(ws.host);   // pinned, nb * sizeof(KState) >= nb * sizeof(RhsCtl)
+        DDA_CUDA_TRY(cudaMemcpyAsync(hc, ctl, nb * sizeof(RhsCtl), cudaMemcpyDeviceToHost, st));
+        DDA_CUDA_TRY(cudaStreamSynchronize(st));
+        cap = 0;
+        for (int q = 0; q < nb; ++q) cap = hc[q].maxit > cap ? hc[q].maxit : cap;
     }
-    (void)hstat;
+    while (it < cap + 2 && !done) {
+        ++it;
+        if (it == 1) {
+            rc = enqueue_iteration<T>(method, mv, ws, x, 1, st);
+        } else {
+            if (it == 2 && graphs) have_graph = capture_iteration<T>(method, mv, ws, x, &exec, &graph_kernels);
+            if (have_graph) {
+                const cudaError_t e = cudaGraphLaunch(exec, st);
+                if (e != cudaSuccess) rc = cuda_fail(e, "krylov graph launch");
+                else note_launches(graph_kernels);
+            } else {
+                rc = enqueue_iteration<T>(method, mv, ws, x, 0, st);
+            }
+        }
+        if (rc) break;
+        // copy the status words of this iteration; check the ones two behind
+        const int slot = it & 1;
+        int* hst = ws.host_status + slot * nb;
+        if (it >= 3) {
+            const cudaError_t e = cudaEventSynchronize(ev[slot]);
+            if (e != cudaSuccess) { rc = cuda_fail(e, "krylov poll"); break; }
+            done = true;
+            for (int q = 0; q < nb; ++q)
+                if (hst[q] == ST_RUN) { done = false; break; }
+        }
+        cudaError_t e = cudaMemcpy2DAsync(hst, sizeof(int), &ws.st->status, sizeof(KState), sizeof(int), nb,
+                                          cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[slot], st);
+        if (e != cudaSuccess) { rc = cuda_fail(e, "krylov status copy"); break; }
+    }
+    if (exec) cudaGraphExecDestroy(exec);
     cudaEventDestroy(ev[0]);
     cudaEventDestroy(ev[1]);
     if (rc) return rc;
-    DDA_CUDA_TRY(cudaMemcpyAsync(&hs[0], ds, sizeof(KState), cudaMemcpyDeviceToHost, st));
+    DDA_CUDA_TRY(cudaMemcpyAsync(ws.host, ws.st, nb * sizeof(KState), cudaMemcpyDeviceToHost, st));
     DDA_CUDA_TRY(cudaStreamSynchronize(st));
-    res->status = hs[0].status;
-    res->iterations = hs[0].iter;
-    res->matvecs = hs[0].matvecs + (use_x0 ? 1 : 0);
-    res->rel2 = hs[0].rel2;
+    for (int q = 0; q < nb; ++q) {
+        res[q].status = ws.host[q].status;
+        res[q].iterations = ws.host[q].iter;
+        res[q].matvecs = ws.host[q].matvecs + (use_x0 ? 1 : 0);
+        res[q].rel2 = ws.host[q].rel2;
+    }
     return 0;
 }
 
 template int krylov_solve<double>(int, MatvecView<double>, KrylovWork<double>&, const C<double>*, C<double>*,
-                                  bool, double, int, KState*, cudaStream_t, SolveResult*);
+                                  bool, const RhsCtl*, double, int, cudaStream_t, SolveResult*);
 template int krylov_solve<float>(int, MatvecView<float>, KrylovWork<float>&, const C<float>*, C<float>*, bool,
-                                 double, int, KState*, cudaStream_t, SolveResult*);
+                                 const RhsCtl*, double, int, cudaStream_t, SolveResult*);
 
-int vec_norm2_c128(const double2* a, int64_t n, double2* part, KState* st_dev, double* out_host, KState* hs,
-                   cudaStream_t st) {
-    k_norm2_c128<<<kVecBlocks, kVecThreads, 0, st>>>(a, n, part);
-    DDA_LAUNCH_CHECK("norm");
-    k_slot<<<1, kVecThreads, 0, st>>>(st_dev, part, S_TMP);
-    DDA_LAUNCH_CHECK("norm final");
-    DDA_CUDA_TRY(cudaMemcpyAsync(&hs->s[S_TMP], &st_dev->s[S_TMP], sizeof(double2), cudaMemcpyDeviceToHost, st));
-    DDA_CUDA_TRY(cudaStreamSynchronize(st));
-    *out_host = hs->s[S_TMP].x;
-    return 0;
-}
-
-int residual_from_product(const double2* b, double2* r, int64_t n, double2* part, KState* st_dev, cudaStream_t st) {
-    k_resid<<<kVecBlocks, kVecThreads, 0, st>>>(b, r, n, part);
+int residual_from_product(const double2* b, double2* r, int64_t n, int nb, const RhsCtl* ctl, double2* part,
+                          KState* st_dev, cudaStream_t st) {
+    const int gx = vec_blocks(n, nb);
+    k_resid<<<dim3(gx, nb), kVecThreads, 0, st>>>(b, r, n, ctl, part);
     DDA_LAUNCH_CHECK("residual");
-    k_slot<<<1, kVecThreads, 0, st>>>(st_dev, part, S_TMP);
+    k_slot<<<nb, kVecThreads, 0, st>>>(st_dev, part, gx, S_TMP, ctl);
     DDA_LAUNCH_CHECK("residual final");
     return 0;
 }
 
-int scale_to_c64(const double2* r, double scale, float2* out, int64_t n, cudaStream_t st) {
-    k_to_c64<<<kVecBlocks, kVecThreads, 0, st>>>(r, scale, out, n);
+int vec_norm2_c128(const double2* a, int64_t n, int nb, double2* part, KState* st_dev, cudaStream_t st) {
+    const int gx = vec_blocks(n, nb);
+    k_norm2_c128<<<dim3(gx, nb), kVecThreads, 0, st>>>(a, n, part);
+    DDA_LAUNCH_CHECK("norm");
+    k_slot<<<nb, kVecThreads, 0, st>>>(st_dev, part, gx, S_TMP, nullptr);
+    DDA_LAUNCH_CHECK("norm final");
+    return 0;
+}
+
+int read_tmp_slots(const KState* st_dev, int nb, KState* host, double* out, cudaStream_t st) {
+    DDA_CUDA_TRY(cudaMemcpy2DAsync(&host[0].s[S_TMP], sizeof(KState), &st_dev[0].s[S_TMP], sizeof(KState),
+                                   sizeof(double2), nb, cudaMemcpyDeviceToHost, st));
+    DDA_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int q = 0; q < nb; ++q) out[q] = host[q].s[S_TMP].x;
+    return 0;
+}
+
+int scale_to_c64(const double2* r, const RhsCtl* ctl, float2* out, int64_t n, int nb, cudaStream_t st) {
+    k_to_c64<<<dim3(vec_blocks(n, nb), nb), kVecThreads, 0, st>>>(r, ctl, out, n);
     DDA_LAUNCH_CHECK("to c64");
     return 0;
 }
 
-int axpy_from_c64(double2* x, double scale, const float2* d, int64_t n, cudaStream_t st) {
-    k_axpy_c64<<<kVecBlocks, kVecThreads, 0, st>>>(x, scale, d, n);
+int axpy_from_c64(double2* x, const RhsCtl* ctl, const float2* d, int64_t n, int nb, cudaStream_t st) {
+    k_axpy_c64<<<dim3(vec_blocks(n, nb), nb), kVecThreads, 0, st>>>(x, ctl, d, n);
     DDA_LAUNCH_CHECK("axpy c64");
-    return 0;
-}
-
-int vec_copy_c128(double2* dst, const double2* src, int64_t n, cudaStream_t st) {
-    k_copy<<<kVecBlocks, kVecThreads, 0, st>>>(dst, src, n);
-    DDA_LAUNCH_CHECK("copy");
-    return 0;
-}
-
-int reduce_into_slot(const double2* part, int nr, KState* st_dev, int slot, cudaStream_t st) {
-    (void)nr;
-    k_slot<<<1, kVecThreads, 0, st>>>(st_dev, part, slot);
-    DDA_LAUNCH_CHECK("slot");
     return 0;
 }
 
