@@ -156,6 +156,10 @@ def run_ours(args):
     dda.dda_pack_occupancy(mask_dev, bits)
     probe = dda.Lattice(shape, bits, alpha, K_WAVE)
     nd = probe.n_dipoles
+    # tile widths tuned once per process (untimed); every later context of
+    # this shape starts with them
+    tuned = {dt: {"pass_ms": probe.autotune(dt, nb=1, reps=3), "tiles": probe.tiles(dt)}
+             for dt in ("c64", "c128")} if args.autotune else None
     probe.close()
     E = torch.empty((3, nd), dtype=torch.complex128, device=dev)
     P = torch.empty_like(E)
@@ -263,6 +267,8 @@ def run_ours(args):
     }
     result["passes"] = {dt: [{"launches": c, "ms_avg": (t / c if c else None)} for c, t in pass_ms[dt]]
                         for dt in pass_ms}
+    if tuned:
+        result["autotune"] = tuned
     if rank == 0 and not args.no_extras:
         result.update(extras(args, dda, torch, dev, shape, bits, alpha, nd, pass_ms, khat, pols))
     if rank == 0 and not args.no_cpu:
@@ -385,9 +391,184 @@ def extras(args, dda, torch, dev, shape, bits, alpha, nd, pass_ms, khat, pols):
                                  "iterations": info["iterations"], "matvecs": info["matvecs"],
                                  "rel_residual_true": info["rel_residual_true"],
                                  "cross_sections": dda.dda_cross_sections(ctx, E, P)}
+            del E, P
+        if args.qmr_solve:
+            out["qmr_mixed_solve"] = timed_single_solve(dda, torch, dev, ctx, nd, khat, pols[0], "qmr", args)
+        if args.batch > 0:
+            out["batch"] = timed_batch(dda, torch, dev, ctx, nd, args)
     finally:
         dda.dda_free(ctx)
     return out
+
+
+def timed_single_solve(dda, torch, dev, ctx, nd, khat, e0, method, args):
+    """One mixed-precision solve of the bench target with another method."""
+    E = torch.empty((3, nd), dtype=torch.complex128, device=dev)
+    P = torch.empty_like(E)
+    dda.dda_incident_field(ctx, khat, e0, E)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    status, info = dda.dda_solve(ctx, E, P, method, "mixed", args.tol, args.max_iter)
+    dt = time.perf_counter() - t0
+    return {"method": method, "seconds": dt, "solves_per_s": 1.0 / dt, "status": status,
+            "iterations": info["iterations"], "matvecs": info["matvecs"], "matvecs_fp64": info["matvecs_fp64"],
+            "rel_residual_true": info["rel_residual_true"]}
+
+
+def timed_batch(dda, torch, dev, ctx, nd, args):
+    """args.batch incidence directions (first polarisation of each) solved
+    together in one batched mixed-precision solve sharing the spectrum."""
+    import synth
+    nbt = args.batch
+    dirs = synth.random_direction(SEED + 1000, nbt)
+    E = torch.empty((nbt, 3, nd), dtype=torch.complex128, device=dev)
+    for b, kh in enumerate(dirs):
+        dda.dda_incident_field(ctx, kh, synth.orthogonal_polarisations(kh)[0], E[b])
+    P = torch.zeros_like(E)
+    dda.dda_reserve(ctx, nbt, "mixed")
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize(dev)
+    l0 = dda.dda_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    status, stats, infos = dda.dda_solve_batch(ctx, E, P, args.method, "mixed", args.tol, args.max_iter)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    launches = dda.dda_launch_count() - l0
+    cx = dda.dda_cross_sections_batch(ctx, E, P)
+    mv = sum(i["matvecs"] + i["matvecs_fp64"] for i in infos)
+    return {"rhs": nbt, "what": f"{nbt} seeded incidence directions, first polarisation each, "
+                                "one dda_solve_batch call (mixed, shared spectrum)",
+            "seconds": ms / 1e3, "solves_per_s": nbt / (ms / 1e3), "matvecs_per_s": mv / (ms / 1e3),
+            "iterations": [i["iterations"] for i in infos], "refinements": [i["refinements"] for i in infos],
+            "worst_true_rel_residual": max(i["rel_residual_true"] for i in infos),
+            "status": sorted(set(stats)), "gpu_launches": int(launches),
+            "device_bytes": dda.dda_query(ctx)["device_bytes"],
+            "c_ext_range": [float(cx[:, 0].min()), float(cx[:, 0].max())]}
+
+
+# ------------------------------------------------------------ aggregates
+AGG_MONOMERS = (20, 45, 70, 95, 120, 145, 170, 200)
+AGG_REFR = 1.6 + 0.05j
+AGG_SEED = 20260003
+
+
+def run_aggregates(args):
+    """Batching workload: 8 seeded ballistic aggregates of touching spheres
+    (monomer diameter 8, 20-200 monomers, uneven lattices), each solved for
+    64 seeded incidence directions x 2 polarisations in one batched
+    mixed-precision call sharing that aggregate's spectrum; per-orientation
+    C_ext and C_abs.  value = solves per second over the whole job."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_0908_0863_gb300 as dda
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    k = 0.5 / abs(AGG_REFR)
+    alpha = dda.dda_polarizability([AGG_REFR], k, "cmrr")
+    ndir = args.agg_directions
+    targets = []
+    for i, nm in enumerate(AGG_MONOMERS[:args.agg_count]):
+        mask, _ = synth.ballistic_aggregate(AGG_SEED + nm, nm, mono_diameter=8)
+        dirs = synth.random_direction(AGG_SEED + 1000 + i, ndir)
+        pairs = []
+        for kh in dirs:
+            e1, e2 = synth.orthogonal_polarisations(kh)
+            pairs += [(kh, e1), (kh, e2)]
+        targets.append((nm, mask, pairs))
+
+    def solve_target(nm, mask, pairs, detail):
+        P_, J_, K_ = mask.shape
+        m_dev = torch.from_numpy(np.ascontiguousarray(mask).reshape(-1)).to(dev)
+        bits = torch.empty((mask.size + 31) // 32, dtype=torch.int32, device=dev)
+        dda.dda_pack_occupancy(m_dev, bits)
+        ctx = dda.dda_init_lattice((K_, J_, P_), bits, None, 1, alpha, k)
+        try:
+            nd = dda.dda_query(ctx)["n_dipoles"]
+            nb = len(pairs)
+            E = torch.empty((nb, 3, nd), dtype=torch.complex128, device=dev)
+            for b, (kh, e) in enumerate(pairs):
+                dda.dda_incident_field(ctx, kh, e, E[b])
+            P = torch.zeros_like(E)
+            status, stats, infos = dda.dda_solve_batch(ctx, E, P, args.method, "mixed", args.tol, args.max_iter)
+            cx = dda.dda_cross_sections_batch(ctx, E, P)
+            if detail is not None:
+                q = dda.dda_query(ctx)
+                detail.append({"monomers": nm, "lattice": [K_, J_, P_], "padded": list(q["padded"]),
+                               "n_dipoles": nd, "rhs": nb, "status": sorted(set(stats)),
+                               "iterations_mean": float(np.mean([i["iterations"] for i in infos])),
+                               "matvecs": int(sum(i["matvecs"] + i["matvecs_fp64"] for i in infos)),
+                               "worst_true_rel_residual": max(i["rel_residual_true"] for i in infos),
+                               "q_ext_mean": float(np.mean(cx[:, 0])) / (np.pi * (3 * nd / (4 * np.pi)) ** (2 / 3)),
+                               "tiles_c64": list(dda.dda_tiles(ctx, "c64")),
+                               "device_bytes": q["device_bytes"]})
+            return sum(i["matvecs"] + i["matvecs_fp64"] for i in infos), len(pairs)
+        finally:
+            dda.dda_free(ctx)
+
+    tiles = {}
+    if args.autotune:
+        # tile widths per aggregate shape, tuned once before the timed region
+        for nm, mask, _ in targets:
+            P_, J_, K_ = mask.shape
+            m_dev = torch.from_numpy(np.ascontiguousarray(mask).reshape(-1)).to(dev)
+            bits = torch.empty((mask.size + 31) // 32, dtype=torch.int32, device=dev)
+            dda.dda_pack_occupancy(m_dev, bits)
+            ctx = dda.dda_init_lattice((K_, J_, P_), bits, None, 1, alpha, k)
+            try:
+                dda.dda_autotune(ctx, "c64", nb=8, reps=2)
+                tiles[nm] = dda.dda_tiles(ctx, "c64")
+            finally:
+                dda.dda_free(ctx)
+    # warm-up: the smallest aggregate with a few right-hand sides
+    for _ in range(args.warmup):
+        solve_target(targets[0][0], targets[0][1], targets[0][2][:4], None)
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(0)
+    sampler.start()
+    l0 = dda.dda_launch_count()
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    detail = []
+    mv = solves = 0
+    e0.record(stream)
+    for _ in range(args.steps):
+        for nm, mask, pairs in targets:
+            a, b = solve_target(nm, mask, pairs, detail if len(detail) < len(targets) else None)
+            mv += a
+            solves += b
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    launches = dda.dda_launch_count() - l0
+    # the same solves one right-hand side per call, on a sample of 8
+    nm, mask, pairs = targets[-1]
+    t0 = time.perf_counter()
+    solve_target(nm, mask, pairs[:8], None)
+    t_batched8 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for pr in pairs[:8]:
+        solve_target(nm, mask, [pr], None)
+    t_single8 = time.perf_counter() - t0
+    print(json.dumps({
+        "metric": "batched mixed-precision solves/s: 8 ballistic aggregates x 64 orientations x 2 polarisations",
+        "value": solves / (ms / 1e3), "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64+f64 (complex64 FFT products, FP64 refinement)", "data": "synthetic",
+        "config": {"workload": f"{len(targets)} ballistic aggregates ({', '.join(str(t[0]) for t in targets)} "
+                               f"monomers of diameter 8), m=1.6+0.05i, |m|kd=0.5, CM+RR, {ndir} directions x 2 "
+                               f"polarisations each, mixed {args.method} {args.tol:g}",
+                   "parallelism": "single", "batch": "one dda_solve_batch per aggregate (all its orientations)"},
+        "matvecs_per_s": mv / (ms / 1e3), "clocks": clocks, "gpu_launches": int(launches),
+        "aggregates": detail,
+        "batched_vs_single_8rhs_largest": {"batched_s": t_batched8, "single_calls_s": t_single8,
+                                           "speedup": t_single8 / t_batched8},
+    }), flush=True)
 
 
 # ---------------------------------------------------------- oracle timing
@@ -462,11 +643,21 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--fp64-solve", action="store_true")
+    ap.add_argument("--qmr-solve", action="store_true", help="also time one mixed QMR solve")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the default tile widths instead of tuning them before the warm-up")
+    ap.add_argument("--batch", type=int, default=16, help="right-hand sides of the batched-solve extra (0: skip)")
+    ap.add_argument("--workload", default="sphere256", choices=["sphere256", "aggregates"],
+                    help="sphere256: the headline metric; aggregates: the batched orientation-averaging workload")
+    ap.add_argument("--agg-count", type=int, default=len(AGG_MONOMERS))
+    ap.add_argument("--agg-directions", type=int, default=64)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "aggregates":
+        run_aggregates(args)
     else:
         run_ours(args)
 

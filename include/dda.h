@@ -200,6 +200,32 @@ int dda_matvec(dda_ctx* ctx, const void* p, void* y, int dtype, void* stream);
 int dda_matvec_batch(dda_ctx* ctx, int nb, const void* p, void* y, int dtype, void* stream);
 
 /*
+ * Tile widths of the matvec passes, as log2 of the lines one CTA
+ * transforms: tiles[0] for P1/P5 (y lines), tiles[1] for P3 (z columns),
+ * tiles[2] for P2/P4 (x rows), for dtype DDA_C128 or DDA_C64.  tiles_in
+ * (host int[3], may be NULL) sets them after checking the launch limits
+ * (threads per block, shared memory; DDA_ERR_ARG when exceeded); tiles_out
+ * (host int[3], may be NULL) receives the current ones.  The widths only
+ * regroup lines between CTAs: every line's arithmetic, and so every result
+ * bit, is the same for all valid widths.
+ */
+int dda_tiles(dda_ctx* ctx, int dtype, int* tiles_out, const int* tiles_in);
+
+/*
+ * Autotune the tile widths of dtype on this context: starting from the
+ * current widths, try up to two steps either way for P3, then P1/P5, then
+ * P2/P4, timing `reps` batched products of nb right-hand sides per
+ * candidate with CUDA events (after one untimed product), and keep the
+ * fastest.  The choice is set on the context and remembered for the
+ * process: contexts created later with the same lattice shape start with
+ * it.  pass_ms (host double[5], may be NULL) receives the per-pass
+ * milliseconds of the chosen widths.  Allocates (and frees) two scratch
+ * vectors of nb right-hand sides; may grow the workspace to nb slots.
+ * Synchronises the stream.
+ */
+int dda_autotune(dda_ctx* ctx, int dtype, int nb, int reps, double* pass_ms, void* stream);
+
+/*
  * Grow the solve workspace to hold nb right-hand sides (1 <= nb <= 4096)
  * for solves of the given precision, so that later calls with up to nb
  * right-hand sides allocate nothing.  Per right-hand side it holds 3

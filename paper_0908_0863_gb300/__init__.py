@@ -16,7 +16,7 @@ from ._lib import (  # noqa: F401
     DDA_BICG, DDA_BICG_SYM, DDA_BICGSTAB, DDA_C64, DDA_C128, DDA_ERR_ARG, DDA_ERR_BREAKDOWN, DDA_ERR_CUDA,
     DDA_ERR_NAN, DDA_ERR_NOT_CONVERGED, DDA_ERR_OOM, DDA_FP64, DDA_MIXED, DDA_OK, DDA_QMR, EXPORTS, DDAError,
     dda_cross_sections, dda_cross_sections_batch, dda_free, dda_gradient, dda_incident_field, dda_init_lattice,
-    dda_last_error, dda_matvec_batch, dda_reserve, dda_solve_batch,
+    dda_last_error, dda_matvec_batch, dda_reserve, dda_solve_batch, dda_tiles, dda_autotune,
     dda_launch_count, dda_polarizability_derivative, dda_scattering_cross_section,
     dda_matvec, dda_occupancy_ranks_static, dda_pack_composition, dda_pack_occupancy, dda_polarizability,
     dda_profile, dda_profile_read,
@@ -65,6 +65,12 @@ class Lattice:
 
     def matvec_batch(self, p, y, stream=None):
         dda_matvec_batch(self.ctx, p, y, stream)
+
+    def tiles(self, dtype="c64", tiles=None):
+        return dda_tiles(self.ctx, dtype, tiles)
+
+    def autotune(self, dtype="c64", nb=1, reps=3, stream=None):
+        return dda_autotune(self.ctx, dtype, nb, reps, stream)
 
     def reserve(self, nb, precision="mixed"):
         dda_reserve(self.ctx, nb, precision)

@@ -57,7 +57,7 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
             raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stderr}")
         return r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1, len(srcs)))) as ex:
         logs = list(ex.map(compile_one, zip(srcs, objs)))
     if verbose:
         for l in logs:

@@ -39,7 +39,8 @@ EXPORTS = (
     "dda_tensor_spectrum", "dda_matvec", "dda_incident_field", "dda_solve", "dda_cross_sections",
     "dda_profile", "dda_profile_read", "dda_launch_count", "dda_last_error", "dda_occupancy_ranks_static",
     "dda_scattering_cross_section", "dda_polarizability_derivative", "dda_gradient",
-    "dda_matvec_batch", "dda_reserve", "dda_solve_batch", "dda_cross_sections_batch",
+    "dda_matvec_batch", "dda_reserve", "dda_solve_batch", "dda_cross_sections_batch", "dda_tiles",
+    "dda_autotune",
 )
 
 
@@ -92,6 +93,8 @@ def load(path: str | None = None):
     L.dda_cross_sections.argtypes = [vp, vp, vp, vp, vp]
     L.dda_matvec_batch.argtypes = [vp, i32, vp, vp, i32, vp]
     L.dda_reserve.argtypes = [vp, i32, i32]
+    L.dda_tiles.argtypes = [vp, i32, vp, vp]
+    L.dda_autotune.argtypes = [vp, i32, i32, i32, vp, vp]
     L.dda_solve_batch.argtypes = [vp, i32, vp, vp, i32, i32, d, i32, i32, vp, vp, vp]
     L.dda_cross_sections_batch.argtypes = [vp, i32, vp, vp, vp, vp]
     L.dda_occupancy_ranks_static.argtypes = [vp, i64, vp, vp, vp]
@@ -230,6 +233,26 @@ def dda_matvec_batch(ctx, p, y, stream=None):
         raise TypeError("p and y must have the same dtype and shape")
     _check(load().dda_matvec_batch(ctypes.c_void_p(ctx), int(p.shape[0]), _ptr(p), _ptr(y), _dtype_code(p),
                                    _stream(stream)))
+
+
+def _dtype_name(dtype):
+    return {"c128": DDA_C128, "c64": DDA_C64}.get(dtype, dtype)
+
+
+def dda_tiles(ctx, dtype="c64", tiles=None):
+    """Current tile widths (log2 lines per CTA of P1/P5, P3, P2/P4); sets them first when given."""
+    out = np.zeros(3, dtype=np.int32)
+    tin = None if tiles is None else np.ascontiguousarray(np.asarray(tiles, dtype=np.int32).reshape(3))
+    _check(load().dda_tiles(ctypes.c_void_p(ctx), _dtype_name(dtype), _ptr(out), _ptr(tin)))
+    return tuple(int(v) for v in out)
+
+
+def dda_autotune(ctx, dtype="c64", nb=1, reps=3, stream=None):
+    """Tune the tile widths; returns the per-pass milliseconds of the choice."""
+    ms = np.zeros(5)
+    _check(load().dda_autotune(ctypes.c_void_p(ctx), _dtype_name(dtype), int(nb), int(reps), _ptr(ms),
+                               _stream(stream)))
+    return [float(v) for v in ms]
 
 
 def dda_reserve(ctx, nb, precision="mixed"):

@@ -3,11 +3,15 @@
 // batched right-hand sides), and the observables and their permittivity
 // gradients.  Host code only orchestrates; every step runs in the kernels
 // of matvec.cu, spectrum.cu, target.cu and solver.cu.
+#include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -324,6 +328,20 @@ KrylovWork<float> work32(const dda_ctx* c, int nb) {
     return w;
 }
 
+// Tile widths chosen by dda_autotune, per lattice shape and dtype, for the
+// whole process: later contexts of the same shape start with them.
+std::mutex g_tiles_mu;
+std::map<std::array<int, 4>, std::array<int, 3>> g_tiles;
+
+std::array<int, 4> tile_key(const Geometry& g, int dtype) { return {g.K, g.J, g.P, dtype}; }
+
+template <typename T>
+void apply_tiles(MatvecView<T>& m, const std::array<int, 3>& t) {
+    m.logW_y = t[0];
+    m.logW_z = t[1];
+    m.logW_x = t[2];
+}
+
 int64_t context_bytes(const dda_ctx* c) {
     const Space& s = c->sp;
     return c->bytes_fixed + (int64_t)(s.bytes_core + s.bytes_work + s.bytes64 + s.bytes32);
@@ -571,6 +589,11 @@ int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occu
         f.g = g; f.tv = tv; f.ainv = c->ainv32; f.spec = c->spec32; f.tw = c->tw32;
         f.status = nullptr; f.conj = 0; f.prof = &c->prof;
         configure_matvec<float>(f);
+        std::lock_guard<std::mutex> lock(g_tiles_mu);
+        auto it = g_tiles.find(tile_key(g, DDA_C128));
+        if (it != g_tiles.end()) apply_tiles(m, it->second);
+        it = g_tiles.find(tile_key(g, DDA_C64));
+        if (it != g_tiles.end()) apply_tiles(f, it->second);
     }
     *out = c;
     return DDA_OK;
@@ -643,6 +666,110 @@ int dda_matvec_batch(dda_ctx* c, int nb, const void* p, void* y, int dtype, void
 
 int dda_matvec(dda_ctx* c, const void* p, void* y, int dtype, void* stream) {
     return dda_matvec_batch(c, 1, p, y, dtype, stream);
+}
+
+int dda_tiles(dda_ctx* c, int dtype, int* tiles_out, const int* tiles_in) {
+    if (int rc = check_ctx(c)) return rc;
+    if (dtype != DDA_C128 && dtype != DDA_C64) return fail(DDA_ERR_ARG, "dda_tiles: unknown dtype");
+    if (tiles_in) {
+        const bool ok = dtype == DDA_C128 ? tiles_ok<double>(c->g, tiles_in[0], tiles_in[1], tiles_in[2])
+                                          : tiles_ok<float>(c->g, tiles_in[0], tiles_in[1], tiles_in[2]);
+        if (!ok) return fail(DDA_ERR_ARG, "dda_tiles: tile widths exceed the launch limits");
+        const std::array<int, 3> t{tiles_in[0], tiles_in[1], tiles_in[2]};
+        if (dtype == DDA_C128) apply_tiles(c->mv64, t);
+        else apply_tiles(c->mv32, t);
+    }
+    if (tiles_out) {
+        if (dtype == DDA_C128) { tiles_out[0] = c->mv64.logW_y; tiles_out[1] = c->mv64.logW_z; tiles_out[2] = c->mv64.logW_x; }
+        else { tiles_out[0] = c->mv32.logW_y; tiles_out[1] = c->mv32.logW_z; tiles_out[2] = c->mv32.logW_x; }
+    }
+    return DDA_OK;
+}
+
+int dda_autotune(dda_ctx* c, int dtype, int nb, int reps, double* pass_ms, void* stream) {
+    if (int rc = check_ctx(c)) return rc;
+    if (dtype != DDA_C128 && dtype != DDA_C64) return fail(DDA_ERR_ARG, "dda_autotune: unknown dtype");
+    if (nb < 1 || nb > kMaxBatch || reps < 1 || reps > 1000) return fail(DDA_ERR_ARG, "dda_autotune: bad nb or reps");
+    if (int rc = ensure_work(c->sp, c->g, nb)) return rc;
+    cudaStream_t st = as_stream(stream);
+    const size_t esize = dtype == DDA_C128 ? sizeof(double2) : sizeof(float2);
+    const size_t bytes = (size_t)nb * 3 * c->g.nd * esize;
+    void* buf = nullptr;
+    cudaError_t e = cudaMalloc(&buf, 2 * bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "dda_autotune: scratch vectors");
+    // finite, nonzero data (every byte 0x3f) so the timed arithmetic is ordinary
+    e = cudaMemsetAsync(buf, 0x3f, 2 * bytes, st);
+    const bool was_on = c->prof.on;
+    int64_t cnt[10];
+    double ms[10];
+    c->prof.read(cnt, ms);   // drop older records
+    c->prof.on = true;
+    const int d = dtype == DDA_C128 ? 0 : 1;
+    auto current = [&]() {
+        return dtype == DDA_C128 ? std::array<int, 3>{c->mv64.logW_y, c->mv64.logW_z, c->mv64.logW_x}
+                                 : std::array<int, 3>{c->mv32.logW_y, c->mv32.logW_z, c->mv32.logW_x};
+    };
+    auto set = [&](const std::array<int, 3>& t) {
+        if (dtype == DDA_C128) apply_tiles(c->mv64, t);
+        else apply_tiles(c->mv32, t);
+    };
+    auto valid = [&](const std::array<int, 3>& t) {
+        return dtype == DDA_C128 ? tiles_ok<double>(c->g, t[0], t[1], t[2]) : tiles_ok<float>(c->g, t[0], t[1], t[2]);
+    };
+    // one warm product, then reps timed ones; per-pass average milliseconds
+    auto time_tiles = [&](double (&out)[5]) -> int {
+        for (int r = 0; r <= reps; ++r) {
+            if (r == 1) c->prof.read(cnt, ms);
+            int rc = dtype == DDA_C128
+                         ? launch_matvec<double>(view64(c, nb), static_cast<const double2*>(buf),
+                                                 reinterpret_cast<double2*>(static_cast<char*>(buf) + bytes), st)
+                         : launch_matvec<float>(view32(c, nb), static_cast<const float2*>(buf),
+                                                reinterpret_cast<float2*>(static_cast<char*>(buf) + bytes), st);
+            if (rc) return rc;
+        }
+        if (c->prof.read(cnt, ms)) return fail(DDA_ERR_CUDA, "dda_autotune: event wait failed");
+        for (int q = 0; q < 5; ++q) out[q] = cnt[d * 5 + q] ? ms[d * 5 + q] / reps : 0.0;
+        return 0;
+    };
+    int rc = e == cudaSuccess ? 0 : cuda_fail(e, "dda_autotune: fill");
+    double best_ms[5] = {};
+    if (!rc) rc = time_tiles(best_ms);
+    // one coordinate at a time: P3's width (index 1), then P1/P5's (0), then P2/P4's (2)
+    const int order[3] = {1, 0, 2};
+    for (int oi = 0; oi < 3 && !rc; ++oi) {
+        const int a = order[oi];
+        std::array<int, 3> best = current();
+        auto cost = [&](const double (&m)[5]) {
+            return a == 1 ? m[2] : a == 0 ? m[0] + m[4] : m[1] + m[3];
+        };
+        double best_cost = cost(best_ms);
+        const int center = best[a];
+        for (int v = std::max(0, center - 2); v <= center + 2 && !rc; ++v) {
+            if (v == center) continue;
+            std::array<int, 3> t = best;
+            t[a] = v;
+            if (!valid(t)) continue;
+            set(t);
+            double m[5];
+            rc = time_tiles(m);
+            if (!rc && cost(m) < best_cost) {
+                best_cost = cost(m);
+                best = t;
+                std::copy(m, m + 5, best_ms);
+            }
+        }
+        set(best);
+    }
+    c->prof.on = was_on;
+    cudaStreamSynchronize(st);
+    cudaFree(buf);
+    if (rc) return rc;
+    {
+        std::lock_guard<std::mutex> lock(g_tiles_mu);
+        g_tiles[tile_key(c->g, dtype)] = current();
+    }
+    if (pass_ms) std::copy(best_ms, best_ms + 5, pass_ms);
+    return DDA_OK;
 }
 
 int dda_reserve(dda_ctx* c, int nb, int precision) {

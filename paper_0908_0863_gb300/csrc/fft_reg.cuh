@@ -53,10 +53,16 @@ struct ColLayout {
     int logW;  // 2^logW lines per tile; one pad row after every 8 points
     __device__ __forceinline__ int operator()(int w, int p) const { return ((p + (p >> 3)) << logW) + w; }
 };
+// the same layout with the tile width fixed at compile time, so that every
+// exchange address folds into a constant offset from the thread's base
+template <int LOGW>
+struct ColLayoutT {
+    __device__ __forceinline__ int operator()(int w, int p) const { return ((p + (p >> 3)) << LOGW) + w; }
+};
 
-__host__ __device__ inline int row_ld(int N) { return N + N / 16 + 1; }
+__host__ __device__ constexpr int row_ld(int N) { return N + N / 16 + 1; }
 // elements of a ColLayout tile of W lines of N points
-__host__ __device__ inline int col_elems(int N, int W) { return (N + N / 8) * W; }
+__host__ __device__ constexpr int col_elems(int N, int W) { return (N + N / 8) * W; }
 
 template <typename T, bool INV>
 __device__ __forceinline__ C<T> twiddle(const C<T>* __restrict__ tw, int idx) {

@@ -39,7 +39,11 @@ __device__ __forceinline__ bool rhs_done(const MatvecView<T>& mv, int b) {
     return mv.status && mv.status[(int64_t)b * mv.status_stride] != 0;
 }
 
+// default tile widths for the view's geometry
 template <typename T> void configure_matvec(MatvecView<T>& mv);
+// whether tile widths (log2 of lines per CTA of P1/P5, P3 and P2/P4) fit the
+// launch limits (threads per block, shared memory) for this geometry
+template <typename T> bool tiles_ok(const Geometry& g, int logW_y, int logW_z, int logW_x);
 template <typename T> int launch_matvec(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t st);
 
 }  // namespace dda

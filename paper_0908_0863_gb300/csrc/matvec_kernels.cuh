@@ -1,0 +1,376 @@
+// Kernels and per-length launchers of the pruned FFT matrix-vector product
+// y = A p of the DDA (OpenDDA Sec. 3).  Each of the translation units
+// mv_p1.cu, mv_p3_*.cu, mv_p5.cu and mv_rows.cu instantiates one pass for
+// every line length (and tile width) and exposes its dispatcher; matvec.cu
+// sequences the passes.
+//
+// Five stream-ordered passes over device arrays (x fastest everywhere):
+//   P1  expand + y-forward   compressed p -> Ay[3][P][Ly][K]   (K*P lines per component)
+//   P2  x-forward            Ay -> Bxy[3][P][Ly][Lx]           (Ly*P lines, K nonzero inputs)
+//   P3  z conv               per (ix, jy): z-forward of the 3 components (P nonzero
+//                            inputs), the 3x3 spectrum product of Eqs. 6-8 with the
+//                            signed mirror lookup, z-inverse keeping k < P, in place
+//   P4  x-inverse            Bxy -> Ay, keeping i < K
+//   P5  y-inverse + compress Ay -> y, keeping j < J, y = alpha^-1 p + conv for
+//                            occupied sites (Sec. 4 zero storage)
+// The line counts are the paper's pruned ones (Sec. 3, Table 2): forward
+// y 3[K x P], x 3[J'' x P], z all K'' x J''; the inverse mirrors them.  The
+// 1/(Lx Ly Lz) normalisation of the inverse DFT is folded into the stored
+// spectrum.  Within each line, forward transforms skip the work on the
+// zero half of their input and inverse transforms compute only the half of
+// the output that is kept.
+//
+// Batches: one launch of each pass covers up to `slots` right-hand sides
+// that share the context's spectrum (vectors [nb][3][N_d], work arrays one
+// per slot); a right-hand side whose solver status is no longer "running"
+// is skipped block by block.  The slot is a grid coordinate of its own (no
+// index division in the kernels); in P3 it is the fastest-varying one, so
+// the CTAs of all right-hand sides that read one spectrum tile run back to
+// back and the tile is fetched from HBM once.
+//
+// Every pass keeps its lines in registers (fft_reg.cuh): points are loaded
+// from global memory straight into the registers of the first DFT stage and
+// stored from the registers of the last, and only the exchanges between
+// stages use shared memory.  Strided lines (y, z) are processed W at a
+// time, W adjacent columns so that each load and store touches W
+// contiguous elements.  In P3 each thread carries the same column of all
+// three components, so the spectrum product happens in registers between
+// the forward and the inverse transforms.  Each kernel is compiled for every
+// power-of-two line length (LOGN = 1..10) and, for the strided passes, every
+// tile width (LOGW = 0..4 lines per CTA, log2), and picked at launch, so all
+// shared-memory addresses are compile-time offsets.
+#pragma once
+
+#include <atomic>
+
+#include "fft_reg.cuh"
+#include "matvec.cuh"
+
+namespace dda {
+
+
+__host__ __device__ constexpr int lines_log(int logN) { return logN > 3 ? logN - 3 : 0; }
+__host__ __device__ constexpr int points(int logN) { return logN < 3 ? (1 << logN) : 8; }
+// P3 keeps 3 x 8 complex values per thread: 512 threads fit the register
+// file for complex64, 256 for complex128
+template <typename T> __host__ __device__ constexpr int p3_max_threads() { return sizeof(T) == 4 ? 512 : 256; }
+
+// elements of one slot of the work arrays
+__host__ __device__ __forceinline__ int64_t ay_elems(const Geometry& g) { return 3LL * g.P * g.Ly * g.K; }
+__host__ __device__ __forceinline__ int64_t bxy_elems(const Geometry& g) { return 3LL * g.P * g.Ly * g.Lx; }
+
+// ---------------------------------------------------------------- P1
+template <typename T, int LOGN, int LOGW>
+__global__ void __launch_bounds__(1024) k_p1(MatvecView<T> mv, const C<T>* __restrict__ p) {
+    const int c = blockIdx.z % 3, j = blockIdx.z / 3;      // component, batch slot
+    const int b = mv.b0 + j;
+    if (rhs_done(mv, b)) return;
+    extern __shared__ unsigned char smem_raw[];
+    C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
+    constexpr int logT = lines_log(LOGN), nv = points(LOGN);
+    const Geometry& g = mv.g;
+    constexpr int logW = LOGW, W = 1 << LOGW;
+    const int w = threadIdx.x & (W - 1), t = threadIdx.x >> logW;
+    const int i = blockIdx.x * W + w, kz = blockIdx.y;
+    const C<T>* pc = p + (int64_t)b * mv.vstride + (int64_t)c * g.nd;
+    const int64_t s0 = (int64_t)kz * g.J * g.K + i;
+    C<T> v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const int n = t + (m << logT);
+        v[m] = mk<T>(0, 0);
+        if (m < nv && n < g.J && i < g.K) {
+            const int64_t s = s0 + (int64_t)n * g.K;
+            if (occupied(mv.tv, s)) {
+                v[m] = pc[site_rank(mv.tv, s)];
+                if (mv.conj) v[m].y = -v[m].y;
+            }
+        }
+    }
+    fft_regs<T, false, LOGN, true, false>(v, sm, ColLayoutT<LOGW>{}, w, t, mv.tw);
+    if (i < g.K) {
+        C<T>* out = mv.Ay + j * ay_elems(g) + ((int64_t)c * g.P + kz) * ((int64_t)g.K << LOGN) + i;
+#pragma unroll
+        for (int m = 0; m < nv; ++m) out[(int64_t)(t + (m << logT)) * g.K] = v[m];
+    }
+}
+
+// ------------------------------------------------------- P2 / P4 (rows)
+// Forward: rows of K inputs (Ay) -> Lx outputs (Bxy).  Inverse: rows of Lx
+// inputs (Bxy) -> first K outputs (Ay).  2^logW_x rows per CTA.
+template <typename T, bool INV, int LOGN>
+__global__ void __launch_bounds__(512) k_rows(MatvecView<T> mv) {
+    const int j = blockIdx.y;                               // batch slot
+    if (rhs_done(mv, mv.b0 + j)) return;
+    extern __shared__ unsigned char smem_raw[];
+    C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
+    constexpr int N = 1 << LOGN, logT = lines_log(LOGN), nv = points(LOGN);
+    const Geometry& g = mv.g;
+    const int t = threadIdx.x & ((1 << logT) - 1), wl = threadIdx.x >> logT;
+    const int64_t nrows = 3LL * g.P * g.Ly;
+    const int64_t row = ((int64_t)blockIdx.x << mv.logW_x) + wl;
+    const bool ok = row < nrows;
+    const int nin = INV ? N : g.K, nout = INV ? g.K : N;
+    const C<T>* src = (INV ? mv.Bxy + j * bxy_elems(g) : mv.Ay + j * ay_elems(g)) + (ok ? row * (INV ? N : g.K) : 0);
+    C<T>* dst = (INV ? mv.Ay + j * ay_elems(g) : mv.Bxy + j * bxy_elems(g)) + (ok ? row * (INV ? g.K : N) : 0);
+    C<T> v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const int n = t + (m << logT);
+        v[m] = (ok && m < nv && n < nin) ? src[n] : mk<T>(0, 0);
+    }
+    fft_regs<T, INV, LOGN, !INV, INV>(v, sm, RowLayout<LOGN>{}, wl, t, mv.tw);
+    if (ok) {
+#pragma unroll
+        for (int m = 0; m < nv; ++m) {
+            const int n = t + (m << logT);
+            if (n < nout) dst[n] = v[m];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- P3
+// Signs of the mirrored half for component m (xx, xy, xz, yy, yz, zz):
+// Table 1 per axis, multiplied over the mirrored axes.
+__device__ __forceinline__ int mirror_flip(int m, int fx, int fy, int fz) {
+    switch (m) {
+        case 1: return fx ^ fy;   // xy
+        case 2: return fx ^ fz;   // xz
+        case 4: return fy ^ fz;   // yz
+        default: return 0;        // xx, yy, zz
+    }
+}
+
+// the six spectrum components of one point (contiguous) with 16-byte loads
+template <typename T>
+__device__ __forceinline__ void load6(const C<T>* __restrict__ p, C<T> (&Y)[6]) {
+    if (sizeof(T) == 4) {
+        const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float4 f = __ldg(q + i);
+            Y[2 * i] = mk<T>(f.x, f.y);
+            Y[2 * i + 1] = mk<T>(f.z, f.w);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) Y[i] = __ldg(p + i);
+    }
+}
+
+template <typename T, int LOGN, int LOGW>
+__global__ void __launch_bounds__(p3_max_threads<T>(), 1) k_p3(MatvecView<T> mv) {
+    const int j = blockIdx.x, xt = blockIdx.y;                  // batch slot, column tile
+    if (rhs_done(mv, mv.b0 + j)) return;
+    extern __shared__ unsigned char smem_raw[];
+    C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
+    constexpr int N = 1 << LOGN, logT = lines_log(LOGN), nv = points(LOGN);
+    const Geometry& g = mv.g;
+    constexpr int logW = LOGW, W = 1 << LOGW;
+    const int w = threadIdx.x & (W - 1), t = threadIdx.x >> logW;
+    // rows jy and Ly - jy read the same spectrum rows (mirror lookup): visit
+    // them back to back (0, 1, Ly-1, 2, Ly-2, ...) so the second read hits L2
+    const int b = blockIdx.z, q2 = (b + 1) >> 1;
+    const int jy = b == 0 ? 0 : ((b & 1) ? q2 : g.Ly - q2);
+    const int ix = xt * W + w;
+    const bool ok = ix < g.Lx;
+    const ColLayoutT<LOGW> L{};
+    constexpr int region = col_elems(N, W);
+    const int64_t plane = (int64_t)g.Ly * g.Lx;   // stride between z planes of Bxy
+    const int64_t comp = (int64_t)g.P * plane;    // stride between components
+    C<T>* col = mv.Bxy + j * bxy_elems(g) + (int64_t)jy * g.Lx + (ok ? ix : 0);
+    C<T> v[3][8];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const int n = t + (m << logT);
+            v[c][m] = (ok && m < nv && n < g.P) ? col[c * comp + n * plane] : mk<T>(0, 0);
+        }
+    fft_lines<T, false, LOGN, 3, true, false>(v, sm, region, L, w, t, mv.tw);
+    // spectrum product (Eqs. 6-8) with the signed mirror lookup of Sec. 3
+    {
+        const int my = jy <= g.Ly / 2 ? jy : g.Ly - jy, fy = jy > g.Ly / 2;
+        const int mx = ix <= g.Lx / 2 ? ix : g.Lx - ix, fx = ix > g.Lx / 2;
+        const C<T>* spec = mv.spec + ((int64_t)my * g.Hx + (ok ? mx : 0)) * 6;
+        const int64_t zstep = (int64_t)g.Hy * g.Hx * 6;
+#pragma unroll
+        for (int m = 0; m < nv; ++m) {
+            const int n = t + (m << logT);
+            const int mz = n <= N / 2 ? n : N - n, fz = n > N / 2;
+            C<T> Y[6];
+            if (ok) {
+                load6<T>(spec + mz * zstep, Y);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 6; ++q) Y[q] = mk<T>(0, 0);
+            }
+#pragma unroll
+            for (int q = 0; q < 6; ++q)
+                if (mirror_flip(q, fx, fy, fz)) { Y[q].x = -Y[q].x; Y[q].y = -Y[q].y; }
+            const C<T> X0 = v[0][m], X1 = v[1][m], X2 = v[2][m];
+            v[0][m] = cfma<T>(Y[2], X2, cfma<T>(Y[1], X1, cmul<T>(Y[0], X0)));
+            v[1][m] = cfma<T>(Y[4], X2, cfma<T>(Y[3], X1, cmul<T>(Y[1], X0)));
+            v[2][m] = cfma<T>(Y[5], X2, cfma<T>(Y[4], X1, cmul<T>(Y[2], X0)));
+        }
+    }
+    fft_lines<T, true, LOGN, 3, false, true>(v, sm, region, L, w, t, mv.tw);
+    if (ok) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int m = 0; m < nv; ++m) {
+                const int n = t + (m << logT);
+                if (n < g.P) col[c * comp + n * plane] = v[c][m];
+            }
+    }
+}
+
+// ---------------------------------------------------------------- P5
+template <typename T, int LOGN, int LOGW>
+__global__ void __launch_bounds__(1024) k_p5(MatvecView<T> mv, const C<T>* __restrict__ p, C<T>* __restrict__ y) {
+    const int c = blockIdx.z % 3, j = blockIdx.z / 3;      // component, batch slot
+    const int b = mv.b0 + j;
+    if (rhs_done(mv, b)) return;
+    extern __shared__ unsigned char smem_raw[];
+    C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
+    constexpr int logT = lines_log(LOGN), nv = points(LOGN);
+    const Geometry& g = mv.g;
+    constexpr int logW = LOGW, W = 1 << LOGW;
+    const int w = threadIdx.x & (W - 1), t = threadIdx.x >> logW;
+    const int i = blockIdx.x * W + w, kz = blockIdx.y;
+    const bool ok = i < g.K;
+    const C<T>* in = mv.Ay + j * ay_elems(g) + ((int64_t)c * g.P + kz) * ((int64_t)g.K << LOGN) + (ok ? i : 0);
+    C<T> v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const int n = t + (m << logT);
+        v[m] = (ok && m < nv) ? in[(int64_t)n * g.K] : mk<T>(0, 0);
+    }
+    fft_regs<T, true, LOGN, false, true>(v, sm, ColLayoutT<LOGW>{}, w, t, mv.tw);
+    if (!ok) return;
+    const C<T>* pc = p + (int64_t)b * mv.vstride + (int64_t)c * g.nd;
+    C<T>* yc = y + (int64_t)b * mv.vstride + (int64_t)c * g.nd;
+    const int64_t s0 = (int64_t)kz * g.J * g.K + i;
+#pragma unroll
+    for (int m = 0; m < nv; ++m) {
+        const int n = t + (m << logT);
+        if (n >= g.J) continue;
+        const int64_t s = s0 + (int64_t)n * g.K;
+        if (!occupied(mv.tv, s)) continue;
+        const uint32_t r = site_rank(mv.tv, s);
+        const C<T> a = mv.ainv[material(mv.tv, s, c) * 3 + c];
+        C<T> pv = pc[r];
+        if (mv.conj) pv.y = -pv.y;
+        C<T> out = cfma<T>(a, pv, v[m]);
+        if (mv.conj) out.y = -out.y;
+        yc[r] = out;
+    }
+}
+
+inline int threads_log(int N) { return N > 8 ? ilog2(N) - 3 : 0; }
+
+// largest power of two <= n (n >= 1), as its log
+inline int floor_log2(int n) { int l = 0; while ((2 << l) <= n) ++l; return l; }
+
+// Raises a kernel's dynamic shared-memory limit once per kernel and size
+// (`done` is the launcher's own record), so that launches recorded into a
+// CUDA graph make no attribute calls.
+inline int set_smem(const void* fn, size_t bytes, std::atomic<size_t>& done) {
+    if (bytes <= 48 * 1024 || bytes <= done.load(std::memory_order_relaxed)) return 0;
+    DDA_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    size_t cur = done.load(std::memory_order_relaxed);
+    while (cur < bytes && !done.compare_exchange_weak(cur, bytes)) {
+    }
+    return 0;
+}
+
+// ------------------------------------------------- per-length launchers
+template <typename T, int LOGN, int LOGW>
+int launch_p1(const MatvecView<T>& mv, const C<T>* p, cudaStream_t st) {
+    const Geometry& g = mv.g;
+    constexpr int W = 1 << LOGW;
+    const size_t sm = (size_t)col_elems(1 << LOGN, W) * sizeof(C<T>);
+    static std::atomic<size_t> smem_set{0};
+    if (int rc = set_smem((const void*)k_p1<T, LOGN, LOGW>, sm, smem_set)) return rc;
+    dim3 grid((g.K + W - 1) / W, g.P, 3 * mv.nb);
+    k_p1<T, LOGN, LOGW><<<grid, W << lines_log(LOGN), sm, st>>>(mv, p);
+    DDA_LAUNCH_CHECK("P1 expand + y-forward");
+    return 0;
+}
+
+template <typename T, bool INV, int LOGN>
+int launch_rows(const MatvecView<T>& mv, cudaStream_t st) {
+    const Geometry& g = mv.g;
+    const int64_t rows = 3LL * g.P * g.Ly;
+    const int R = 1 << mv.logW_x;
+    const size_t sm = (size_t)R * row_ld(1 << LOGN) * sizeof(C<T>);
+    static std::atomic<size_t> smem_set{0};
+    if (int rc = set_smem((const void*)k_rows<T, INV, LOGN>, sm, smem_set)) return rc;
+    const dim3 grid((unsigned)((rows + R - 1) / R), mv.nb);
+    k_rows<T, INV, LOGN><<<grid, R << lines_log(LOGN), sm, st>>>(mv);
+    DDA_LAUNCH_CHECK(INV ? "P4 x-inverse" : "P2 x-forward");
+    return 0;
+}
+
+template <typename T, int LOGN, int LOGW>
+int launch_p3(const MatvecView<T>& mv, cudaStream_t st) {
+    const Geometry& g = mv.g;
+    constexpr int W = 1 << LOGW;
+    const size_t sm = 3 * (size_t)col_elems(1 << LOGN, W) * sizeof(C<T>);
+    static std::atomic<size_t> smem_set{0};
+    if (int rc = set_smem((const void*)k_p3<T, LOGN, LOGW>, sm, smem_set)) return rc;
+    dim3 grid(mv.nb, (g.Lx + W - 1) / W, g.Ly);
+    k_p3<T, LOGN, LOGW><<<grid, W << lines_log(LOGN), sm, st>>>(mv);
+    DDA_LAUNCH_CHECK("P3 z-forward, spectrum product, z-inverse");
+    return 0;
+}
+
+template <typename T, int LOGN, int LOGW>
+int launch_p5(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t st) {
+    const Geometry& g = mv.g;
+    constexpr int W = 1 << LOGW;
+    const size_t sm = (size_t)col_elems(1 << LOGN, W) * sizeof(C<T>);
+    static std::atomic<size_t> smem_set{0};
+    if (int rc = set_smem((const void*)k_p5<T, LOGN, LOGW>, sm, smem_set)) return rc;
+    dim3 grid((g.K + W - 1) / W, g.P, 3 * mv.nb);
+    k_p5<T, LOGN, LOGW><<<grid, W << lines_log(LOGN), sm, st>>>(mv, p, y);
+    DDA_LAUNCH_CHECK("P5 y-inverse + diagonal + compress");
+    return 0;
+}
+
+#define DDA_LOGN_SWITCH(logN, CALL)                    \
+    switch (logN) {                                    \
+        case 1: { constexpr int LN = 1; return CALL; } \
+        case 2: { constexpr int LN = 2; return CALL; } \
+        case 3: { constexpr int LN = 3; return CALL; } \
+        case 4: { constexpr int LN = 4; return CALL; } \
+        case 5: { constexpr int LN = 5; return CALL; } \
+        case 6: { constexpr int LN = 6; return CALL; } \
+        case 7: { constexpr int LN = 7; return CALL; } \
+        case 8: { constexpr int LN = 8; return CALL; } \
+        case 9: { constexpr int LN = 9; return CALL; } \
+        case 10: { constexpr int LN = 10; return CALL; } \
+        default: return fail(DDA_ERR_ARG, "line length out of range"); \
+    }
+
+#define DDA_LOGW_SWITCH(logW, CALL)                    \
+    switch (logW) {                                    \
+        case 0: { constexpr int LW = 0; return CALL; } \
+        case 1: { constexpr int LW = 1; return CALL; } \
+        case 2: { constexpr int LW = 2; return CALL; } \
+        case 3: { constexpr int LW = 3; return CALL; } \
+        case 4: { constexpr int LW = 4; return CALL; } \
+        default: return fail(DDA_ERR_ARG, "tile width out of range"); \
+    }
+
+// widest tile (log2 lines per CTA) the strided passes are compiled for
+constexpr int kMaxLogW = 4;
+
+// per-pass dispatchers (one translation unit each)
+template <typename T> int pass1(const MatvecView<T>& mv, const C<T>* p, cudaStream_t st);
+template <typename T, bool INV> int pass_rows(const MatvecView<T>& mv, cudaStream_t st);
+template <typename T> int pass3(const MatvecView<T>& mv, cudaStream_t st);
+template <typename T> int pass5(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t st);
+
+}  // namespace dda

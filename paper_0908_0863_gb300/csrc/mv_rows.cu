@@ -1,0 +1,16 @@
+// Instantiations of the matvec pass P2 and P4 (x-forward, x-inverse) for every line
+// length and tile width, and its dispatcher.
+#include "matvec_kernels.cuh"
+
+namespace dda {
+
+template <typename T, bool INV> int pass_rows(const MatvecView<T>& mv, cudaStream_t st) {
+    DDA_LOGN_SWITCH(ilog2(mv.g.Lx), (launch_rows<T, INV, LN>(mv, st)))
+}
+
+template int pass_rows<double, false>(const MatvecView<double>&, cudaStream_t);
+template int pass_rows<double, true>(const MatvecView<double>&, cudaStream_t);
+template int pass_rows<float, false>(const MatvecView<float>&, cudaStream_t);
+template int pass_rows<float, true>(const MatvecView<float>&, cudaStream_t);
+
+}  // namespace dda

@@ -276,3 +276,57 @@ def test_aggregate_200_monomers_sampled_rows(dda):
     # optical theorem with the independent pair-sum C_sca, to the solve's accuracy
     for q, b in enumerate((0, 5)):
         assert abs((cx[b, 0] - cx[b, 1]) / csca[q] - 1) < 1e-3
+
+
+# --------------------------------------------------------------- tiles
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_tile_widths_do_not_change_results(dda, dtype):
+    case = random_case((21, 13, 9), seed=41, fill=0.6)
+    tdt = torch.complex128 if dtype == "c128" else torch.complex64
+    p = torch.from_numpy(synth.complex_normal(42, (2, 3, case.nd))).to(DEV).to(tdt)
+    with case.lattice() as lat:
+        base = lat.tiles(dtype)
+        y0 = torch.empty_like(p)
+        lat.matvec_batch(p, y0)
+        tried = 0
+        for d in ((-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1), (1, 1, 1)):
+            t = tuple(b + e for b, e in zip(base, d))
+            try:
+                lat.tiles(dtype, t)
+            except dda.DDAError as err:
+                assert err.code == dda.DDA_ERR_ARG
+                continue
+            assert lat.tiles(dtype) == t
+            y1 = torch.empty_like(p)
+            lat.matvec_batch(p, y1)
+            assert torch.equal(y0, y1), t
+            tried += 1
+        assert tried >= 4
+        lat.tiles(dtype, base)
+
+
+def test_tile_limits_rejected(dda):
+    case = random_case((9, 9, 9), seed=43, fill=0.8)
+    with case.lattice() as lat:
+        base = lat.tiles("c64")
+        with pytest.raises(dda.DDAError) as e:
+            lat.tiles("c64", (base[0], 12, base[2]))     # 4096 columns x 4 threads per CTA
+        assert e.value.code == dda.DDA_ERR_ARG
+        assert lat.tiles("c64") == base
+
+
+def test_autotune_keeps_results_and_is_remembered(dda):
+    case = Case(synth.sphere(40), [1.33 + 0.05j], 0.5 / abs(1.33 + 0.05j))
+    p = torch.from_numpy(synth.complex_normal(44, (2, 3, case.nd))).to(DEV).to(torch.complex64)
+    with case.lattice() as lat:
+        y0 = torch.empty_like(p)
+        lat.matvec_batch(p, y0)
+        ms = lat.autotune("c64", nb=2, reps=2)
+        assert len(ms) == 5 and all(m > 0 for m in ms)
+        chosen = lat.tiles("c64")
+        y1 = torch.empty_like(p)
+        lat.matvec_batch(p, y1)
+        assert torch.equal(y0, y1)
+    with case.lattice() as lat2:
+        assert lat2.tiles("c64") == chosen
