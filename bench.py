@@ -292,11 +292,15 @@ def algorithmic_bytes(n, nd, esize):
             "matvec_min": 3 * V + 4 * A + T}
 
 
+KERNEL_SOURCES = ("matvec_kernels.cuh", "fft_reg.cuh", "fft.cuh", "matvec.cuh", "common.cuh")
+
+
 def kernel_sources_hash():
-    """First 16 hex digits of the SHA-256 of the matvec kernel sources."""
+    """First 16 hex digits of the SHA-256 of the matvec kernel sources
+    (csrc/ + KERNEL_SOURCES, concatenated in that order)."""
     import hashlib
     h = hashlib.sha256()
-    for rel in ("paper_0908_0863_gb300/csrc/matvec.cu", "paper_0908_0863_gb300/csrc/fft_reg.cuh"):
+    for rel in (f"paper_0908_0863_gb300/csrc/{f}" for f in KERNEL_SOURCES):
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

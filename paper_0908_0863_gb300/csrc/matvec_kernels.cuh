@@ -55,13 +55,19 @@ __host__ __device__ constexpr int points(int logN) { return logN < 3 ? (1 << log
 // file for complex64, 256 for complex128
 template <typename T> __host__ __device__ constexpr int p3_max_threads() { return sizeof(T) == 4 ? 512 : 256; }
 
+// P1 and P5 keep the eight points, their gather indices and (P5) the
+// gathered entries of p in registers: at most 512 threads per CTA leave
+// room for them (P5 is held to two such CTAs per SM, which measured faster
+// than one with no register cap)
+constexpr int kYThreads = 512;
+
 // elements of one slot of the work arrays
 __host__ __device__ __forceinline__ int64_t ay_elems(const Geometry& g) { return 3LL * g.P * g.Ly * g.K; }
 __host__ __device__ __forceinline__ int64_t bxy_elems(const Geometry& g) { return 3LL * g.P * g.Ly * g.Lx; }
 
 // ---------------------------------------------------------------- P1
 template <typename T, int LOGN, int LOGW>
-__global__ void __launch_bounds__(1024) k_p1(MatvecView<T> mv, const C<T>* __restrict__ p) {
+__global__ void __launch_bounds__(kYThreads) k_p1(MatvecView<T> mv, const C<T>* __restrict__ p) {
     const int c = blockIdx.z % 3, j = blockIdx.z / 3;      // component, batch slot
     const int b = mv.b0 + j;
     if (rhs_done(mv, b)) return;
@@ -74,17 +80,27 @@ __global__ void __launch_bounds__(1024) k_p1(MatvecView<T> mv, const C<T>* __res
     const int i = blockIdx.x * W + w, kz = blockIdx.y;
     const C<T>* pc = p + (int64_t)b * mv.vstride + (int64_t)c * g.nd;
     const int64_t s0 = (int64_t)kz * g.J * g.K + i;
+    // the gather as two rounds of independent loads: first the occupancy and
+    // rank words of all eight sites, then the eight occupied entries of p
+    uint32_t word[8], rbase[8];
+    const bool inx = i < g.K;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const int n = t + (m << logT);
+        const bool in = inx && m < nv && n < g.J;
+        const int64_t q = (s0 + (int64_t)n * g.K) >> 5;
+        word[m] = in ? __ldg(mv.tv.occ + q) : 0u;
+        rbase[m] = in ? __ldg(mv.tv.rank + q) : 0u;
+    }
     C<T> v[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
         const int n = t + (m << logT);
+        const uint32_t bit = (uint32_t)((s0 + (int64_t)n * g.K) & 31);
         v[m] = mk<T>(0, 0);
-        if (m < nv && n < g.J && i < g.K) {
-            const int64_t s = s0 + (int64_t)n * g.K;
-            if (occupied(mv.tv, s)) {
-                v[m] = pc[site_rank(mv.tv, s)];
-                if (mv.conj) v[m].y = -v[m].y;
-            }
+        if ((word[m] >> bit) & 1u) {
+            v[m] = pc[rbase[m] + __popc(word[m] & ((1u << bit) - 1u))];
+            if (mv.conj) v[m].y = -v[m].y;
         }
     }
     fft_regs<T, false, LOGN, true, false>(v, sm, ColLayoutT<LOGW>{}, w, t, mv.tw);
@@ -228,7 +244,7 @@ __global__ void __launch_bounds__(p3_max_threads<T>(), 1) k_p3(MatvecView<T> mv)
 
 // ---------------------------------------------------------------- P5
 template <typename T, int LOGN, int LOGW>
-__global__ void __launch_bounds__(1024) k_p5(MatvecView<T> mv, const C<T>* __restrict__ p, C<T>* __restrict__ y) {
+__global__ void __launch_bounds__(kYThreads, 2) k_p5(MatvecView<T> mv, const C<T>* __restrict__ p, C<T>* __restrict__ y) {
     const int c = blockIdx.z % 3, j = blockIdx.z / 3;      // component, batch slot
     const int b = mv.b0 + j;
     if (rhs_done(mv, b)) return;
@@ -252,19 +268,36 @@ __global__ void __launch_bounds__(1024) k_p5(MatvecView<T> mv, const C<T>* __res
     const C<T>* pc = p + (int64_t)b * mv.vstride + (int64_t)c * g.nd;
     C<T>* yc = y + (int64_t)b * mv.vstride + (int64_t)c * g.nd;
     const int64_t s0 = (int64_t)kz * g.J * g.K + i;
+    // the scatter in rounds of independent loads: occupancy and rank words,
+    // then the entries of p (and alpha^-1), then the stores of y
+    uint32_t word[8], rbase[8];
 #pragma unroll
-    for (int m = 0; m < nv; ++m) {
+    for (int m = 0; m < 8; ++m) {
         const int n = t + (m << logT);
-        if (n >= g.J) continue;
-        const int64_t s = s0 + (int64_t)n * g.K;
-        if (!occupied(mv.tv, s)) continue;
-        const uint32_t r = site_rank(mv.tv, s);
+        const bool in = m < nv && n < g.J;
+        const int64_t q = (s0 + (int64_t)n * g.K) >> 5;
+        word[m] = in ? __ldg(mv.tv.occ + q) : 0u;
+        rbase[m] = in ? __ldg(mv.tv.rank + q) : 0u;
+    }
+    C<T> pv[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const int n = t + (m << logT);
+        const uint32_t bit = (uint32_t)((s0 + (int64_t)n * g.K) & 31);
+        rbase[m] += __popc(word[m] & ((1u << bit) - 1u));   // the site's rank
+        word[m] = (word[m] >> bit) & 1u;                    // occupied?
+        if (word[m]) pv[m] = pc[rbase[m]];
+    }
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        if (!word[m]) continue;
+        const int64_t s = s0 + (int64_t)(t + (m << logT)) * g.K;
         const C<T> a = mv.ainv[material(mv.tv, s, c) * 3 + c];
-        C<T> pv = pc[r];
-        if (mv.conj) pv.y = -pv.y;
-        C<T> out = cfma<T>(a, pv, v[m]);
+        C<T> q = pv[m];
+        if (mv.conj) q.y = -q.y;
+        C<T> out = cfma<T>(a, q, v[m]);
         if (mv.conj) out.y = -out.y;
-        yc[r] = out;
+        yc[rbase[m]] = out;
     }
 }
 
