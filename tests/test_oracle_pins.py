@@ -285,7 +285,7 @@ def test_optical_theorem_and_far_field():
     assert abs(ce - ca - cs) < 1e-12 * ce
 
 
-@pytest.mark.parametrize("name", ["bicg", "bicg_sym", "bicgstab", "qmr"])
+@pytest.mark.parametrize("name", ["bicg", "bicg_sym", "bicgstab", "qmr", "cg", "cgs", "tfqmr", "qmr_sym"])
 def test_solvers_match_lu(name):
     k = 0.45
     c, ainv, E, A, P = _solved(synth.sphere(6), k, 1.33 + 0.01j)
@@ -305,6 +305,95 @@ def test_bicg_equals_bicg_sym_iterates():
         x2, i2 = solvers.bicg_sym(lambda v: A @ v, E.reshape(-1), tol=0, max_iter=it)
         assert np.abs(x1 - x2).max() <= 1e-12 * np.abs(x1).max()
         assert i1["matvecs"] == 2 * i2["matvecs"]
+
+
+def test_cg_and_qmr_sym_follow_their_symmetric_twins():
+    # with the bilinear form, CG is BiCG_sym step for step; QMR_sym's single
+    # Lanczos sequence reproduces QMR's (w_n = v_n) with half the products
+    k = 0.45
+    c, ainv, E, A, P = _solved(synth.sphere(5), k, 1.33 + 0.01j)
+    op = lambda v: A @ v
+    for it in (2, 5, 9):
+        x1, i1 = solvers.bicg_sym(op, E.reshape(-1), tol=0, max_iter=it)
+        x2, i2 = solvers.cg(op, E.reshape(-1), tol=0, max_iter=it)
+        assert np.abs(x1 - x2).max() <= 1e-12 * np.abs(x1).max()
+        assert i1["matvecs"] == i2["matvecs"] == it
+        y1, j1 = solvers.qmr(op, E.reshape(-1), tol=0, max_iter=it)
+        y2, j2 = solvers.qmr_sym(op, E.reshape(-1), tol=0, max_iter=it)
+        assert np.abs(y1 - y2).max() <= 1e-11 * np.abs(y1).max()
+        assert j1["matvecs"] == 2 * j2["matvecs"]
+
+
+def test_tfqmr_bound_covers_true_residual():
+    # the quasi-residual bound tau sqrt(m+1) is an upper bound of ||r_m||,
+    # so the stopping test never stops early
+    k = 0.45
+    c, ainv, E, A, P = _solved(synth.sphere(6), k, 1.33 + 0.05j)
+    b = E.reshape(-1)
+    for tol in (1e-3, 1e-6, 1e-9):
+        x, info = solvers.tfqmr(lambda v: A @ v, b, tol=tol, max_iter=500)
+        assert info["converged"]
+        true = np.linalg.norm(b - A @ x) / np.linalg.norm(b)
+        assert true <= info["rel_residual"] * (1 + 1e-9) and true <= tol
+
+
+def test_cgs_is_bicg_squared():
+    # CGS's residual polynomial is the square of BiCG's: after n steps with the
+    # same shadow vector, r_CGS = phi_n(A)^2 r0 where r_BiCG = phi_n(A) r0
+    k = 0.45
+    c, ainv, E, A, P = _solved(synth.sphere(4), k, 1.33 + 0.01j)
+    b = E.reshape(-1)
+    # BiCG with shadow r0 (not conj(r0)): run the recurrence by hand for phi_n
+    n = 3
+    r = b.copy(); rt = b.copy(); p = pt = None; rho_old = None
+    alphas, betas = [], []
+    for it in range(n):
+        rho = np.vdot(rt, r)
+        if it == 0:
+            p, pt = r.copy(), rt.copy()
+        else:
+            beta = rho / rho_old; betas.append(beta)
+            p = r + beta * p; pt = rt + np.conj(beta) * pt
+        q = A @ p
+        alpha = rho / np.vdot(pt, q); alphas.append(alpha)
+        r = r - alpha * q
+        rt = rt - np.conj(alpha) * (np.conj(A @ np.conj(pt)))
+        rho_old = rho
+    # phi_n(A) applied twice to r0, via the coupled recurrences phi, psi
+    def apply_phi(v):
+        ph, ps = v.copy(), v.copy()
+        for it in range(n):
+            if it > 0:
+                ps = ph + betas[it - 1] * ps
+            ph = ph - alphas[it] * (A @ ps)
+        return ph
+    target = apply_phi(apply_phi(b))
+    x, info = solvers.cgs(lambda v: A @ v, b, tol=0, max_iter=n)
+    assert np.abs((b - A @ x) - target).max() <= 1e-10 * np.abs(target).max()
+
+
+def test_jacobi_scaling():
+    # one material: diag(A) is a multiple of I, so the scaled system has the
+    # same Krylov spaces and the same iterates; two materials: still the LU
+    # solution
+    k = 0.45
+    c, ainv, E, A, P = _solved(synth.sphere(6), k, 1.33 + 0.05j)
+    b = E.reshape(-1)
+    op = lambda v: A @ v
+    for name in ("bicgstab", "qmr_sym", "tfqmr"):
+        x1, i1 = solvers.SOLVERS[name](op, b, tol=0, max_iter=6)
+        x2, i2 = solvers.jacobi(solvers.SOLVERS[name], np.diag(A))(op, b, tol=0, max_iter=6)
+        assert np.abs(x1 - x2).max() <= 1e-10 * np.abs(x1).max(), name
+    mask = synth.sphere(6)
+    mats = synth.bernoulli_materials(7, mask, 0.4)
+    c2, ainv2 = _setup(mask, k, materials=mats, refr=[1.33 + 0.05j, 2.0 + 0.5j])
+    A2 = dda.dense_matrix(c2, ainv2, k)
+    b2 = dda.incident_field(c2, k, [0, 0, 1], [1, 0, 0]).reshape(-1)
+    P2 = np.linalg.solve(A2, b2)
+    for name in ("bicg_sym", "bicgstab", "qmr_sym", "tfqmr", "cgs"):
+        x, info = solvers.jacobi(solvers.SOLVERS[name], np.diag(A2))(lambda v: A2 @ v, b2, tol=1e-12, max_iter=800)
+        assert info["converged"], name
+        assert np.abs(x - P2).max() <= 1e-9 * np.abs(P2).max(), name
 
 
 def test_solver_reports_non_convergence():
