@@ -67,10 +67,21 @@ typedef enum {
 } dda_status;
 
 typedef enum { DDA_C128 = 0, DDA_C64 = 1 } dda_dtype;
-/* Krylov schemes of Sec. 4: BiCG (two products per iteration), BiCGSTAB,
- * QMR with coupled two-term recurrences (two products), and BiCG for
- * complex-symmetric systems ("BiCG_sym", one product per iteration). */
-typedef enum { DDA_BICG = 0, DDA_BICGSTAB = 1, DDA_QMR = 2, DDA_BICG_SYM = 3 } dda_method;
+/* Krylov schemes of Sec. 4 (products with A per iteration in brackets):
+ * BiCG [2], BiCGSTAB [2], QMR with coupled two-term recurrences [2],
+ * BiCG for complex-symmetric systems "BiCG_sym" [1], CG with the bilinear
+ * form x^T y [1] (for a complex-symmetric A the same recurrence as
+ * BiCG_sym), CGS [2], TFQMR [2; one iteration = two half-steps] and QMR
+ * for complex-symmetric systems "QMR_sym" [1].  OR DDA_PRECOND_JACOBI into
+ * the method for point-Jacobi preconditioning (Sec. 6), applied as the
+ * symmetric scaling (S A S) y = S E_inc, P = S y, S = diag(alpha)^(1/2),
+ * which keeps the matrix complex symmetric; the stopping test then applies
+ * to the scaled residual. */
+typedef enum {
+    DDA_BICG = 0, DDA_BICGSTAB = 1, DDA_QMR = 2, DDA_BICG_SYM = 3, DDA_CG = 4, DDA_CGS = 5, DDA_TFQMR = 6,
+    DDA_QMR_SYM = 7
+} dda_method;
+#define DDA_PRECOND_JACOBI 0x100
 typedef enum { DDA_FP64 = 0, DDA_MIXED = 1 } dda_precision;
 typedef enum { DDA_POL_CM = 0, DDA_POL_CMRR = 1, DDA_POL_LDR = 2 } dda_polarizability_rule;
 

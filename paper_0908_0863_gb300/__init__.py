@@ -13,7 +13,8 @@ built (``__graft_entry__.build()``); there is no CPU fallback.
 from __future__ import annotations
 
 from ._lib import (  # noqa: F401
-    DDA_BICG, DDA_BICG_SYM, DDA_BICGSTAB, DDA_C64, DDA_C128, DDA_ERR_ARG, DDA_ERR_BREAKDOWN, DDA_ERR_CUDA,
+    DDA_BICG, DDA_BICG_SYM, DDA_BICGSTAB, DDA_C64, DDA_C128, DDA_CG, DDA_CGS, DDA_ERR_ARG, DDA_ERR_BREAKDOWN,
+    DDA_ERR_CUDA, DDA_PRECOND_JACOBI, DDA_QMR_SYM, DDA_TFQMR, method_code,
     DDA_ERR_NAN, DDA_ERR_NOT_CONVERGED, DDA_ERR_OOM, DDA_FP64, DDA_MIXED, DDA_OK, DDA_QMR, EXPORTS, DDAError,
     dda_cross_sections, dda_cross_sections_batch, dda_free, dda_gradient, dda_incident_field, dda_init_lattice,
     dda_last_error, dda_matvec_batch, dda_reserve, dda_solve_batch, dda_tiles, dda_autotune,

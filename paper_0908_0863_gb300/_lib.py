@@ -25,10 +25,26 @@ DDA_ERR_NAN = -6
 DDA_C128 = 0
 DDA_C64 = 1
 DDA_BICG, DDA_BICGSTAB, DDA_QMR, DDA_BICG_SYM = 0, 1, 2, 3
+DDA_CG, DDA_CGS, DDA_TFQMR, DDA_QMR_SYM = 4, 5, 6, 7
+DDA_PRECOND_JACOBI = 0x100
 DDA_FP64, DDA_MIXED = 0, 1
 DDA_POL_CM, DDA_POL_CMRR, DDA_POL_LDR = 0, 1, 2
 
-METHODS = {"bicg": DDA_BICG, "bicgstab": DDA_BICGSTAB, "qmr": DDA_QMR, "bicg_sym": DDA_BICG_SYM}
+METHODS = {"bicg": DDA_BICG, "bicgstab": DDA_BICGSTAB, "qmr": DDA_QMR, "bicg_sym": DDA_BICG_SYM, "cg": DDA_CG,
+           "cgs": DDA_CGS, "tfqmr": DDA_TFQMR, "qmr_sym": DDA_QMR_SYM}
+
+
+def method_code(method) -> int:
+    """A dda_method value from a name ("bicgstab", "qmr_sym+jacobi", ...) or an int."""
+    if not isinstance(method, str):
+        return int(method)
+    base, *opts = method.split("+")
+    code = METHODS[base]
+    for o in opts:
+        if o != "jacobi":
+            raise ValueError(f"unknown solver option {o!r}")
+        code |= DDA_PRECOND_JACOBI
+    return code
 PRECISIONS = {"fp64": DDA_FP64, "mixed": DDA_MIXED}
 RULES = {"cm": DDA_POL_CM, "cmrr": DDA_POL_CMRR, "ldr": DDA_POL_LDR}
 
@@ -269,7 +285,7 @@ def dda_solve(ctx, einc, p, method="bicgstab", precision="fp64", tol=1e-8, max_i
               stream=None):
     """Returns (status, info dict); raises only for argument / CUDA errors."""
     info = SolveInfo()
-    code = load().dda_solve(ctypes.c_void_p(ctx), _ptr(einc), _ptr(p), METHODS.get(method, method),
+    code = load().dda_solve(ctypes.c_void_p(ctx), _ptr(einc), _ptr(p), method_code(method),
                             PRECISIONS.get(precision, precision), float(tol), int(max_iter), int(bool(use_x0)),
                             ctypes.byref(info), _stream(stream))
     if code in (DDA_ERR_ARG, DDA_ERR_CUDA, DDA_ERR_OOM):
@@ -285,7 +301,7 @@ def dda_solve_batch(ctx, einc, p, method="bicgstab", precision="fp64", tol=1e-8,
     nb = int(einc.shape[0])
     infos = (SolveInfo * nb)()
     stats = np.zeros(nb, dtype=np.int32)
-    code = load().dda_solve_batch(ctypes.c_void_p(ctx), nb, _ptr(einc), _ptr(p), METHODS.get(method, method),
+    code = load().dda_solve_batch(ctypes.c_void_p(ctx), nb, _ptr(einc), _ptr(p), method_code(method),
                                   PRECISIONS.get(precision, precision), float(tol), int(max_iter),
                                   int(bool(use_x0)), ctypes.cast(infos, ctypes.c_void_p), _ptr(stats),
                                   _stream(stream))
@@ -334,7 +350,7 @@ def dda_gradient(ctx, which, einc, p, dalpha_inv, grad, method="bicgstab", preci
     da = _c2(np.asarray(dalpha_inv, dtype=np.complex128).reshape(-1), np.asarray(dalpha_inv).size)
     info = SolveInfo()
     code = load().dda_gradient(ctypes.c_void_p(ctx), int(w), _ptr(einc), _ptr(p), _ptr(da),
-                               METHODS.get(method, method), PRECISIONS.get(precision, precision), float(tol),
+                               method_code(method), PRECISIONS.get(precision, precision), float(tol),
                                int(max_iter), _ptr(grad), ctypes.byref(info), _stream(stream))
     if code in (DDA_ERR_ARG, DDA_ERR_CUDA, DDA_ERR_OOM, DDA_ERR_NAN):
         _check(code)

@@ -117,6 +117,8 @@ struct dda_ctx {
     uint32_t *occ = nullptr, *rank = nullptr, *comp = nullptr;
     double2* ainv64 = nullptr;
     float2* ainv32 = nullptr;
+    double2* jac64 = nullptr;    // point-Jacobi scale diag(A)^(-1/2) per material and axis
+    float2* jac32 = nullptr;
     double2* spec64 = nullptr;
     float2* spec32 = nullptr;
     double2* tw64 = nullptr;
@@ -475,6 +477,8 @@ int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occu
         probe.take<double2>(3 * (size_t)n_materials);
         probe.take<double2>(3 * (size_t)n_materials);
         probe.take<float2>(3 * (size_t)n_materials);
+        probe.take<double2>(3 * (size_t)n_materials);
+        probe.take<float2>(3 * (size_t)n_materials);
         probe.take<double2>(nspec);
         probe.take<float2>(nspec);
         probe.take<double2>(kMaxLine);
@@ -493,6 +497,8 @@ int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occu
     c->ainv64 = a0.take<double2>(3 * (size_t)n_materials);
     c->ainv32 = a0.take<float2>(3 * (size_t)n_materials);
     c->dainv64 = a0.take<double2>(3 * (size_t)n_materials);
+    c->jac64 = a0.take<double2>(3 * (size_t)n_materials);
+    c->jac32 = a0.take<float2>(3 * (size_t)n_materials);
     c->spec64 = a0.take<double2>(nspec);
     c->spec32 = a0.take<float2>(nspec);
     c->tw64 = a0.take<double2>(kMaxLine);
@@ -523,12 +529,15 @@ int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occu
     if (g.nd == 0) return bail(fail(DDA_ERR_ARG, "dda_init_lattice: no occupied site"));
     // ---- alpha^-1 and twiddle tables (host FP64, a few hundred numbers)
     {
-        std::vector<double2> ai(3 * n_materials);
-        std::vector<float2> af(3 * n_materials);
+        std::vector<double2> ai(3 * n_materials), sj(3 * n_materials);
+        std::vector<float2> af(3 * n_materials), sf(3 * n_materials);
         for (int i = 0; i < 3 * n_materials; ++i) {
             const std::complex<double> inv = 1.0 / std::complex<double>(alpha[2 * i], alpha[2 * i + 1]);
             ai[i] = make_double2(inv.real(), inv.imag());
             af[i] = make_float2((float)inv.real(), (float)inv.imag());
+            const std::complex<double> sc = 1.0 / std::sqrt(inv);   // diag(A)^(-1/2), principal root
+            sj[i] = make_double2(sc.real(), sc.imag());
+            sf[i] = make_float2((float)sc.real(), (float)sc.imag());
         }
         std::vector<double2> t64(kMaxLine);
         std::vector<float2> t32(kMaxLine);
@@ -539,6 +548,8 @@ int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occu
         }
         if (cudaMemcpyAsync(c->ainv64, ai.data(), ai.size() * sizeof(double2), cudaMemcpyHostToDevice, st) ||
             cudaMemcpyAsync(c->ainv32, af.data(), af.size() * sizeof(float2), cudaMemcpyHostToDevice, st) ||
+            cudaMemcpyAsync(c->jac64, sj.data(), sj.size() * sizeof(double2), cudaMemcpyHostToDevice, st) ||
+            cudaMemcpyAsync(c->jac32, sf.data(), sf.size() * sizeof(float2), cudaMemcpyHostToDevice, st) ||
             cudaMemcpyAsync(c->tw64, t64.data(), kMaxLine * sizeof(double2), cudaMemcpyHostToDevice, st) ||
             cudaMemcpyAsync(c->tw32, t32.data(), kMaxLine * sizeof(float2), cudaMemcpyHostToDevice, st) ||
             cudaStreamSynchronize(st))
@@ -814,6 +825,9 @@ static int worst_status(const int* st, int nb) {
 static int solve_batch(dda_ctx* c, int nb, const void* einc, void* p, int method, int precision, double tol,
                        int max_iter, int use_x0, dda_solve_info* inf, int* stat, cudaStream_t st) {
     if (int rc = reserve(c, nb, precision)) return rc;
+    const bool jacobi = (method & DDA_PRECOND_JACOBI) != 0;
+    method &= 0xff;
+    const TargetView tv = target_view(c);
     Space& sp = c->sp;
     const int64_t n = sp.n;
     const size_t bytes = (size_t)nb * n * sizeof(double2);
@@ -824,9 +838,22 @@ static int solve_batch(dda_ctx* c, int nb, const void* einc, void* p, int method
     std::vector<double> bn2(nb), rn2(nb);
     if (precision == DDA_FP64) {
         KrylovWork<double> w = work64(c, nb);
-        if (int rc = krylov_solve<double>(method, view64(c, nb), w, sp.b64, sp.x64, use_x0 != 0, nullptr, tol,
-                                          max_iter, st, res.data()))
+        MatvecView<double> m = view64(c, nb);
+        const double2* rhs = sp.b64;
+        if (jacobi) {
+            // (S A S) y = S E, P = S y: the scaled right-hand side in r, the start y0 = S^-1 P0
+            m.jac = c->jac64;
+            DDA_CUDA_TRY(cudaMemcpyAsync(sp.r64, sp.b64, bytes, cudaMemcpyDeviceToDevice, st));
+            if (int rc = launch_site_scale<double>(tv, c->g, c->jac64, sp.r64, nb, n, 0, st)) return rc;
+            if (use_x0)
+                if (int rc = launch_site_scale<double>(tv, c->g, c->jac64, sp.x64, nb, n, 1, st)) return rc;
+            rhs = sp.r64;
+        }
+        if (int rc = krylov_solve<double>(method, m, w, rhs, sp.x64, use_x0 != 0, nullptr, tol, max_iter, st,
+                                          res.data()))
             return rc;
+        if (jacobi)
+            if (int rc = launch_site_scale<double>(tv, c->g, c->jac64, sp.x64, nb, n, 0, st)) return rc;
         // true residuals with one FP64 product per right-hand side
         if (int rc = launch_matvec<double>(view64(c, nb), sp.x64, sp.r64, st)) return rc;
         if (int rc = residual_from_product(sp.b64, sp.r64, n, nb, nullptr, sp.part64, sp.st64, st)) return rc;
@@ -892,9 +919,15 @@ static int solve_batch(dda_ctx* c, int nb, const void* einc, void* p, int method
             }
             DDA_CUDA_TRY(cudaMemcpyAsync(sp.ctl, hc, nb * sizeof(RhsCtl), cudaMemcpyHostToDevice, st));
             if (int rc = scale_to_c64(sp.r64, sp.ctl, sp.b32, n, nb, st)) return rc;
-            if (int rc = krylov_solve<float>(method, view32(c, nb), w, sp.b32, sp.d32, false, sp.ctl, 0.0, 0, st,
-                                             res.data()))
+            MatvecView<float> m32 = view32(c, nb);
+            if (jacobi) {   // inner solve of (S A S) d' = S r, d = S d'
+                m32.jac = c->jac32;
+                if (int rc = launch_site_scale<float>(tv, c->g, c->jac32, sp.b32, nb, n, 0, st)) return rc;
+            }
+            if (int rc = krylov_solve<float>(method, m32, w, sp.b32, sp.d32, false, sp.ctl, 0.0, 0, st, res.data()))
                 return rc;
+            if (jacobi)
+                if (int rc = launch_site_scale<float>(tv, c->g, c->jac32, sp.d32, nb, n, 0, st)) return rc;
             // krylov_solve synchronised the stream: the controls may be rewritten
             bool changed = false;
             for (int b = 0; b < nb; ++b) {
@@ -948,7 +981,8 @@ static int check_solve_args(const dda_ctx* c, int nb, const void* einc, const vo
     if (int rc = check_ctx(c)) return rc;
     if (nb < 1 || nb > kMaxBatch) return fail(DDA_ERR_ARG, "dda_solve: nb must be in [1, 4096]");
     if (!einc || !p) return fail(DDA_ERR_ARG, "dda_solve: NULL einc or p");
-    if (method < DDA_BICG || method > DDA_BICG_SYM) return fail(DDA_ERR_ARG, "dda_solve: unknown method");
+    if ((method & ~(0xff | DDA_PRECOND_JACOBI)) || (method & 0xff) > DDA_QMR_SYM)
+        return fail(DDA_ERR_ARG, "dda_solve: unknown method");
     if (precision != DDA_FP64 && precision != DDA_MIXED) return fail(DDA_ERR_ARG, "dda_solve: unknown precision");
     if (!(tol > 0.0) || !std::isfinite(tol)) return fail(DDA_ERR_ARG, "dda_solve: tol must be finite and > 0");
     if (max_iter < 1) return fail(DDA_ERR_ARG, "dda_solve: max_iter must be >= 1");

@@ -12,7 +12,9 @@ enum Slot {
     S_RHO = 0, S_RHO_OLD, S_ALPHA, S_BETA, S_OMEGA, S_SIGMA,  // BiCG / BiCGSTAB
     S_DELTA, S_EPS, S_XI, S_RHOQ, S_GAMMA_OLD, S_THETA_OLD, S_ETA, S_F,  // QMR
     S_NCP, S_NCQ,                                    // QMR: -(xi delta/eps), -(rho delta/eps)
-    S_RHO_NEW, S_XI_NEW, S_TMP, S_NSLOTS
+    S_RHO_NEW, S_XI_NEW, S_TMP,
+    S_TAU, S_THETA, S_CD,                            // TFQMR: tau, theta, theta^2 eta / alpha
+    S_NSLOTS
 };
 
 // ST_RUN must stay 0: the matvec passes skip a right-hand side whose status

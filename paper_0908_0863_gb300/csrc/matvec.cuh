@@ -22,6 +22,7 @@ struct MatvecView {
                         // status[b * status_stride] != 0
     int status_stride;  // ints between the status words of consecutive RHS
     int conj;           // 1: compute conj(A conj(p)) = A^H p (A complex symmetric)
+    const C<T>* jac = nullptr;  // point-Jacobi: when set, y = S A S p with S = diag(jac[mat][axis])
     PassProfiler* prof; // host object; when non-null and on, each pass is timed
     // Batches: p and y hold nb right-hand sides of vstride elements each
     // ([nb][3][N_d]); the work arrays hold `slots` of them.  launch_matvec

@@ -57,8 +57,8 @@ template <typename T> __host__ __device__ constexpr int p3_max_threads() { retur
 
 // P1 and P5 keep the eight points, their gather indices and (P5) the
 // gathered entries of p in registers: at most 512 threads per CTA leave
-// room for them (P5 is held to two such CTAs per SM, which measured faster
-// than one with no register cap)
+// room for them (the complex64 P5 is held to two such CTAs per SM, which
+// measured faster than one with no register cap)
 constexpr int kYThreads = 512;
 
 // elements of one slot of the work arrays
@@ -101,6 +101,14 @@ __global__ void __launch_bounds__(kYThreads) k_p1(MatvecView<T> mv, const C<T>* 
         if ((word[m] >> bit) & 1u) {
             v[m] = pc[rbase[m] + __popc(word[m] & ((1u << bit) - 1u))];
             if (mv.conj) v[m].y = -v[m].y;
+        }
+    }
+    if (mv.jac) {   // point-Jacobi: the product starts from S p
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const int n = t + (m << logT);
+            if (inx && m < nv && n < g.J)
+                v[m] = cmul<T>(v[m], mv.jac[material(mv.tv, s0 + (int64_t)n * g.K, c) * 3 + c]);
         }
     }
     fft_regs<T, false, LOGN, true, false>(v, sm, ColLayoutT<LOGW>{}, w, t, mv.tw);
@@ -244,7 +252,7 @@ __global__ void __launch_bounds__(p3_max_threads<T>(), 1) k_p3(MatvecView<T> mv)
 
 // ---------------------------------------------------------------- P5
 template <typename T, int LOGN, int LOGW>
-__global__ void __launch_bounds__(kYThreads, 2) k_p5(MatvecView<T> mv, const C<T>* __restrict__ p, C<T>* __restrict__ y) {
+__global__ void __launch_bounds__(kYThreads, sizeof(T) == 4 ? 2 : 1) k_p5(MatvecView<T> mv, const C<T>* __restrict__ p, C<T>* __restrict__ y) {
     const int c = blockIdx.z % 3, j = blockIdx.z / 3;      // component, batch slot
     const int b = mv.b0 + j;
     if (rhs_done(mv, b)) return;
@@ -292,10 +300,17 @@ __global__ void __launch_bounds__(kYThreads, 2) k_p5(MatvecView<T> mv, const C<T
     for (int m = 0; m < 8; ++m) {
         if (!word[m]) continue;
         const int64_t s = s0 + (int64_t)(t + (m << logT)) * g.K;
-        const C<T> a = mv.ainv[material(mv.tv, s, c) * 3 + c];
+        const int mat = material(mv.tv, s, c);
+        const C<T> a = mv.ainv[mat * 3 + c];
         C<T> q = pv[m];
         if (mv.conj) q.y = -q.y;
-        C<T> out = cfma<T>(a, q, v[m]);
+        C<T> out;
+        if (mv.jac) {   // point-Jacobi: S (alpha^-1 S p + conv)
+            const C<T> f = mv.jac[mat * 3 + c];
+            out = cmul<T>(f, cfma<T>(a, cmul<T>(f, q), v[m]));
+        } else {
+            out = cfma<T>(a, q, v[m]);
+        }
         if (mv.conj) out.y = -out.y;
         yc[rbase[m]] = out;
     }

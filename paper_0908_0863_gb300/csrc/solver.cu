@@ -1,10 +1,14 @@
-// Device-resident unpreconditioned Krylov solvers (OpenDDA Sec. 4): BiCG,
-// BiCG_sym, BiCGSTAB and QMR with coupled two-term recurrences, in the
-// textbook forms of Barrett et al. (1994) written for complex vectors:
-// Hermitian products x^H y in BiCG and BiCGSTAB, bilinear x^T y in BiCG_sym
-// and in QMR's Lanczos process with A^T = A (the DDA matrix is complex
-// symmetric, Sec. 3); A^H v is formed as conj(A conj(v)).  BiCG starts from
-// the shadow residual conj(r0), BiCGSTAB from r0.
+// Device-resident Krylov solvers (OpenDDA Sec. 4): BiCG, BiCG_sym (and CG
+// with the bilinear form, the same recurrence), BiCGSTAB, CGS, TFQMR, QMR
+// with coupled two-term recurrences and QMR_sym, in the textbook forms the
+// paper cites (Barrett et al. 1994; Sonneveld 1989; Freund 1992, 1993)
+// written for complex vectors: Hermitian products x^H y in BiCG, BiCGSTAB,
+// CGS and TFQMR, bilinear x^T y in BiCG_sym, CG and the QMR Lanczos
+// processes with A^T = A (the DDA matrix is complex symmetric, Sec. 3);
+// A^H v is formed as conj(A conj(v)).  BiCG starts from the shadow residual
+// conj(r0), BiCGSTAB, CGS and TFQMR from r0.  QMR_sym runs QMR's
+// recurrences on the complex-symmetric Lanczos process, whose left and
+// right Lanczos vectors coincide, so it needs one product per iteration.
 //
 // A solve runs a batch of right-hand sides with the same matrix in lock
 // step: every vector kernel covers all of them (blockIdx.y selects the
@@ -190,10 +194,10 @@ __global__ void __launch_bounds__(kVecThreads) k_init(const C<T>* __restrict__ b
 
 // ctl: per right-hand side tolerance and cap (device) or null for tol and
 // max_iter; a tolerance <= 0 marks a right-hand side that this solve leaves
-// alone
+// alone.  kind: 1 = QMR Lanczos norms, 2 = TFQMR's tau
 __global__ void __launch_bounds__(kVecThreads) k_init_scalar(KState* st, const double2* __restrict__ part,
                                                              int nparts, const RhsCtl* __restrict__ ctl,
-                                                             double tol, int max_iter, int qmr) {
+                                                             double tol, int max_iter, int kind) {
     st += blockIdx.x;
     part += (int64_t)blockIdx.x * nparts * kMaxRed;
     double2 s[3];
@@ -215,7 +219,8 @@ __global__ void __launch_bounds__(kVecThreads) k_init_scalar(KState* st, const d
     if (st->rel2 <= st->tol2) { st->status = ST_CONVERGED; return; }
     if (maxit < 1) { st->status = ST_MAXIT; return; }
     st->s[S_RHO] = s[2];
-    if (qmr) {
+    if (kind == 2) st->s[S_TAU] = make_double2(sqrt(s[1].x), 0.0);
+    if (kind == 1) {
         st->s[S_RHOQ] = make_double2(sqrt(s[1].x), 0.0);
         st->s[S_XI] = make_double2(sqrt(s[1].x), 0.0);
         st->s[S_GAMMA_OLD] = make_double2(1.0, 0.0);
@@ -598,7 +603,7 @@ __global__ void __launch_bounds__(kVecThreads) k_qmr_ds(const KState* st, const 
 // step 0: delta (+ p/q coefficients); 1: eps, beta; 2: rho, xi, theta,
 // gamma, eta, f; 3: end of iteration
 __global__ void __launch_bounds__(kVecThreads) k_qmr_scalar(KState* st, const double2* __restrict__ part,
-                                                            int nparts, int step, int first) {
+                                                            int nparts, int step, int first, int sym) {
     st += blockIdx.x;
     part += (int64_t)blockIdx.x * nparts * kMaxRed;
     if (st->status != ST_RUN) return;
@@ -627,7 +632,7 @@ __global__ void __launch_bounds__(kVecThreads) k_qmr_scalar(KState* st, const do
         if (is_zero(beta)) { st->status = ST_BREAKDOWN; return; }
         st->s[S_BETA] = beta;
     } else if (step == 2) {
-        st->matvecs += 1;
+        if (!sym) st->matvecs += 1;   // QMR's second product, A^T q
         const double rho_new = sqrt(s[0].x), xi_new = sqrt(s[1].x);
         const double2 beta = st->s[S_BETA];
         const double gamma_old = st->s[S_GAMMA_OLD].x;
@@ -649,6 +654,349 @@ __global__ void __launch_bounds__(kVecThreads) k_qmr_scalar(KState* st, const do
         st->s[S_XI] = st->s[S_XI_NEW];
         st->s[S_THETA_OLD] = make_double2(st->s[S_TMP].x, 0.0);
         st->s[S_GAMMA_OLD] = make_double2(st->s[S_TMP].y, 0.0);
+    }
+}
+
+// ----------------------------------------------------------------- QMR_sym
+// v = vt / rho; partial v^T v
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_qs_v(const KState* st, const C<T>* __restrict__ vt,
+                                                      C<T>* __restrict__ v, int64_t n, double2* __restrict__ part) {
+    st += blockIdx.y;
+    if (st->status != ST_RUN) return;
+    vt = rhs_vec(vt, n); v = rhs_vec(v, n); part = rhs_part(part);
+    const T irho = (T)(1.0 / st->s[S_RHOQ].x);
+    DotAcc<T> d;
+    d.init();
+    vec_loop(n, [&](int64_t i) { return V1<T>{vt[i]}; },
+             [&](int64_t i, const V1<T>& q) {
+                 const C<T> vi = cscale<T>(q.a, irho);
+                 v[i] = vi;
+                 d.add(cmul<T>(vi, vi));
+             });
+    d.flush();
+    double2 a[1] = {d.hi};
+    block_partials<1>(a, part);
+}
+
+// p = v - (rho delta / eps) p (a copy on the first step)
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_qs_p(const KState* st, const C<T>* __restrict__ v,
+                                                      C<T>* __restrict__ p, int64_t n, int first) {
+    st += blockIdx.y;
+    if (st->status != ST_RUN) return;
+    v = rhs_vec(v, n); p = rhs_vec(p, n);
+    const C<T> ncp = to_t<T>(st->s[S_NCP]);
+    if (first) {
+        vec_loop(n, [&](int64_t i) { return V1<T>{v[i]}; }, [&](int64_t i, const V1<T>& u) { p[i] = u.a; });
+    } else {
+        vec_loop(n, [&](int64_t i) { return V2<T>{v[i], p[i]}; },
+                 [&](int64_t i, const V2<T>& u) { p[i] = cfma<T>(ncp, u.b, u.a); });
+    }
+}
+
+// vt = pt - beta v; partial ||vt||^2 in both slots the QMR scalar step reads
+// (the norms of the right and the left Lanczos vectors, equal here)
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_qs_vt(const KState* st, const C<T>* __restrict__ pt,
+                                                       const C<T>* __restrict__ v, C<T>* __restrict__ vt, int64_t n,
+                                                       double2* __restrict__ part) {
+    st += blockIdx.y;
+    if (st->status != ST_RUN) return;
+    pt = rhs_vec(pt, n); v = rhs_vec(v, n); vt = rhs_vec(vt, n); part = rhs_part(part);
+    const C<T> beta = to_t<T>(st->s[S_BETA]);
+    const C<T> nbeta = mk<T>(-beta.x, -beta.y);
+    DotAcc<T> a;
+    a.init();
+    vec_loop(n, [&](int64_t i) { return V2<T>{pt[i], v[i]}; },
+             [&](int64_t i, const V2<T>& u) {
+                 const C<T> vi = cfma<T>(nbeta, u.b, u.a);
+                 vt[i] = vi;
+                 a.add(norm2c<T>(vi));
+             });
+    a.flush();
+    double2 s2[2] = {a.hi, a.hi};
+    block_partials<2>(s2, part);
+}
+
+// --------------------------------------------------------------------- CGS
+// u = r + beta q, p = u + beta (q + beta p) (copies of r on the first step)
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_cgs_up(const KState* st, const C<T>* __restrict__ r,
+                                                        const C<T>* __restrict__ q, C<T>* __restrict__ u,
+                                                        C<T>* __restrict__ p, int64_t n, int first) {
+    st += blockIdx.y;
+    if (st->status != ST_RUN) return;
+    r = rhs_vec(r, n); q = rhs_vec(q, n); u = rhs_vec(u, n); p = rhs_vec(p, n);
+    const C<T> beta = to_t<T>(st->s[S_BETA]);
+    if (first) {
+        vec_loop(n, [&](int64_t i) { return V1<T>{r[i]}; },
+                 [&](int64_t i, const V1<T>& a) { u[i] = a.a; p[i] = a.a; });
+    } else {
+        vec_loop(n, [&](int64_t i) { return V3<T>{r[i], q[i], p[i]}; },
+                 [&](int64_t i, const V3<T>& a) {
+                     const C<T> ui = cfma<T>(beta, a.b, a.a);
+                     u[i] = ui;
+                     p[i] = cfma<T>(beta, cfma<T>(beta, a.c, a.b), ui);
+                 });
+    }
+}
+
+// q = u - alpha vh; uh = u + q; x += alpha uh
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_cgs_q(const KState* st, const C<T>* __restrict__ u,
+                                                       const C<T>* __restrict__ vh, C<T>* __restrict__ q,
+                                                       C<T>* __restrict__ uh, C<T>* __restrict__ x, int64_t n) {
+    st += blockIdx.y;
+    if (st->status != ST_RUN) return;
+    u = rhs_vec(u, n); vh = rhs_vec(vh, n); q = rhs_vec(q, n); uh = rhs_vec(uh, n); x = rhs_vec(x, n);
+    const C<T> alpha = to_t<T>(st->s[S_ALPHA]);
+    const C<T> nalpha = mk<T>(-alpha.x, -alpha.y);
+    vec_loop(n, [&](int64_t i) { return V3<T>{u[i], vh[i], x[i]}; },
+             [&](int64_t i, const V3<T>& a) {
+                 const C<T> qi = cfma<T>(nalpha, a.b, a.a);
+                 const C<T> ui = cadd<T>(a.a, qi);
+                 q[i] = qi;
+                 uh[i] = ui;
+                 x[i] = cfma<T>(alpha, ui, a.c);
+             });
+}
+
+// r -= alpha qh; partials ||r||^2, rt^H r
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_cgs_r(const KState* st, const C<T>* __restrict__ qh,
+                                                       C<T>* __restrict__ r, const C<T>* __restrict__ rt, int64_t n,
+                                                       double2* __restrict__ part) {
+    st += blockIdx.y;
+    if (st->status != ST_RUN) return;
+    qh = rhs_vec(qh, n); r = rhs_vec(r, n); rt = rhs_vec(rt, n); part = rhs_part(part);
+    const C<T> alpha = to_t<T>(st->s[S_ALPHA]);
+    const C<T> nalpha = mk<T>(-alpha.x, -alpha.y);
+    DotAcc<T> nr, rr;
+    nr.init(); rr.init();
+    vec_loop(n, [&](int64_t i) { return V3<T>{qh[i], r[i], rt[i]}; },
+             [&](int64_t i, const V3<T>& a) {
+                 const C<T> ri = cfma<T>(nalpha, a.a, a.b);
+                 r[i] = ri;
+                 nr.add(norm2c<T>(ri));
+                 rr.add(cmul<T>(conjg<T>(a.c), ri));
+             });
+    nr.flush(); rr.flush();
+    double2 s2[2] = {nr.hi, rr.hi};
+    block_partials<2>(s2, part);
+}
+
+// ------------------------------------------------------------------- TFQMR
+// One iteration = the half-steps m = 2n (vector u0 = u_m, product Au0) and
+// m = 2n + 1 (u1, Au1).  The update x += eta_m d_m of each half-step runs in
+// the next vector kernel, after the scalar kernel has formed eta_m; when the
+// bound test stops the iteration, the status HALF lets exactly that pending
+// update through.
+
+// d's coefficient theta_{m-1}^2 eta_{m-1} / alpha for the half-step at hand
+template <typename T>
+__device__ __forceinline__ C<T> tf_cd(const KState* st) {
+    const double th = st->s[S_THETA].x;
+    const double2 c = ddiv(st->s[S_ETA], st->s[S_ALPHA]);
+    return to_t<T>(make_double2(th * th * c.x, th * th * c.y));
+}
+
+// u0 = r, d = 0
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_tf_init(const KState* st, const C<T>* __restrict__ r,
+                                                         C<T>* __restrict__ u0, C<T>* __restrict__ d, int64_t n) {
+    st += blockIdx.y;
+    if (st->status != ST_RUN) return;
+    r = rhs_vec(r, n); u0 = rhs_vec(u0, n); d = rhs_vec(d, n);
+    vec_loop(n, [&](int64_t i) { return V1<T>{r[i]}; },
+             [&](int64_t i, const V1<T>& a) { u0[i] = a.a; d[i] = mk<T>(0, 0); });
+}
+
+// u1 = u0 - alpha v
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_tf_u1(const KState* st, const C<T>* __restrict__ u0,
+                                                       const C<T>* __restrict__ v, C<T>* __restrict__ u1, int64_t n) {
+    st += blockIdx.y;
+    if (st->status != ST_RUN) return;
+    u0 = rhs_vec(u0, n); v = rhs_vec(v, n); u1 = rhs_vec(u1, n);
+    const C<T> alpha = to_t<T>(st->s[S_ALPHA]);
+    const C<T> nalpha = mk<T>(-alpha.x, -alpha.y);
+    vec_loop(n, [&](int64_t i) { return V2<T>{u0[i], v[i]}; },
+             [&](int64_t i, const V2<T>& a) { u1[i] = cfma<T>(nalpha, a.b, a.a); });
+}
+
+// even half-step: w -= alpha Au0; d = u0 + cd d; partial ||w||^2
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_tf_even(const KState* st, C<T>* __restrict__ w,
+                                                         const C<T>* __restrict__ Au0, const C<T>* __restrict__ u0,
+                                                         C<T>* __restrict__ d, int64_t n, double2* __restrict__ part) {
+    st += blockIdx.y;
+    if (st->status != ST_RUN) return;
+    w = rhs_vec(w, n); Au0 = rhs_vec(Au0, n); u0 = rhs_vec(u0, n); d = rhs_vec(d, n); part = rhs_part(part);
+    const C<T> alpha = to_t<T>(st->s[S_ALPHA]);
+    const C<T> nalpha = mk<T>(-alpha.x, -alpha.y);
+    const C<T> cd = tf_cd<T>(st);
+    DotAcc<T> nw;
+    nw.init();
+    vec_loop(n, [&](int64_t i) { return V4<T>{w[i], Au0[i], u0[i], d[i]}; },
+             [&](int64_t i, const V4<T>& a) {
+                 const C<T> wi = cfma<T>(nalpha, a.b, a.a);
+                 w[i] = wi;
+                 d[i] = cfma<T>(cd, a.d, a.c);
+                 nw.add(norm2c<T>(wi));
+             });
+    nw.flush();
+    double2 s1[1] = {nw.hi};
+    block_partials<1>(s1, part);
+}
+
+// x += eta d (the even half-step's update); then, unless the iteration has
+// stopped, the odd half-step: w -= alpha Au1; d = u1 + cd d; partials
+// ||w||^2, rt^H w
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_tf_odd(const KState* st, C<T>* __restrict__ x, C<T>* __restrict__ w,
+                                                        const C<T>* __restrict__ Au1, const C<T>* __restrict__ u1,
+                                                        C<T>* __restrict__ d, const C<T>* __restrict__ rt, int64_t n,
+                                                        double2* __restrict__ part) {
+    st += blockIdx.y;
+    const int status = st->status;
+    if (status != ST_RUN && status != ST_HALF) return;
+    x = rhs_vec(x, n); w = rhs_vec(w, n); Au1 = rhs_vec(Au1, n); u1 = rhs_vec(u1, n); d = rhs_vec(d, n);
+    rt = rhs_vec(rt, n); part = rhs_part(part);
+    const C<T> eta = to_t<T>(st->s[S_ETA]);
+    if (status == ST_HALF) {
+        vec_loop(n, [&](int64_t i) { return V2<T>{x[i], d[i]}; },
+                 [&](int64_t i, const V2<T>& a) { x[i] = cfma<T>(eta, a.b, a.a); });
+        return;
+    }
+    const C<T> alpha = to_t<T>(st->s[S_ALPHA]);
+    const C<T> nalpha = mk<T>(-alpha.x, -alpha.y);
+    const C<T> cd = tf_cd<T>(st);
+    DotAcc<T> nw, rw;
+    nw.init(); rw.init();
+    vec_loop(n, [&](int64_t i) { return V6<T>{x[i], w[i], Au1[i], u1[i], d[i], rt[i]}; },
+             [&](int64_t i, const V6<T>& a) {
+                 x[i] = cfma<T>(eta, a.e, a.a);
+                 const C<T> wi = cfma<T>(nalpha, a.c, a.b);
+                 w[i] = wi;
+                 d[i] = cfma<T>(cd, a.e, a.d);
+                 nw.add(norm2c<T>(wi));
+                 rw.add(cmul<T>(conjg<T>(a.f), wi));
+             });
+    nw.flush(); rw.flush();
+    double2 s2[2] = {nw.hi, rw.hi};
+    block_partials<2>(s2, part);
+}
+
+// x += eta d (the odd half-step's update); then, unless the iteration has
+// stopped, u0 = w + beta u1
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_tf_next(const KState* st, C<T>* __restrict__ x,
+                                                         const C<T>* __restrict__ d, const C<T>* __restrict__ w,
+                                                         const C<T>* __restrict__ u1, C<T>* __restrict__ u0,
+                                                         int64_t n) {
+    st += blockIdx.y;
+    const int status = st->status;
+    if (status != ST_RUN && status != ST_HALF) return;
+    x = rhs_vec(x, n); d = rhs_vec(d, n); w = rhs_vec(w, n); u1 = rhs_vec(u1, n); u0 = rhs_vec(u0, n);
+    const C<T> eta = to_t<T>(st->s[S_ETA]);
+    if (status == ST_HALF) {
+        vec_loop(n, [&](int64_t i) { return V2<T>{x[i], d[i]}; },
+                 [&](int64_t i, const V2<T>& a) { x[i] = cfma<T>(eta, a.b, a.a); });
+        return;
+    }
+    const C<T> beta = to_t<T>(st->s[S_BETA]);
+    vec_loop(n, [&](int64_t i) { return V4<T>{x[i], d[i], w[i], u1[i]}; },
+             [&](int64_t i, const V4<T>& a) {
+                 x[i] = cfma<T>(eta, a.b, a.a);
+                 u0[i] = cfma<T>(beta, a.d, a.c);
+             });
+}
+
+// v = Au0 + beta (Au1 + beta v) (first: v = Au0); partial rt^H v
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_tf_v(const KState* st, const C<T>* __restrict__ Au0,
+                                                      const C<T>* __restrict__ Au1, C<T>* __restrict__ v,
+                                                      const C<T>* __restrict__ rt, int64_t n, int first,
+                                                      double2* __restrict__ part) {
+    st += blockIdx.y;
+    if (st->status != ST_RUN) return;
+    Au0 = rhs_vec(Au0, n); Au1 = rhs_vec(Au1, n); v = rhs_vec(v, n); rt = rhs_vec(rt, n); part = rhs_part(part);
+    const C<T> beta = first ? mk<T>(0, 0) : to_t<T>(st->s[S_BETA]);
+    DotAcc<T> sv;
+    sv.init();
+    vec_loop(n,
+             [&](int64_t i) {
+                 return V4<T>{Au0[i], first ? mk<T>(0, 0) : Au1[i], first ? mk<T>(0, 0) : v[i], rt[i]};
+             },
+             [&](int64_t i, const V4<T>& a) {
+                 const C<T> vi = cfma<T>(beta, cfma<T>(beta, a.c, a.b), a.a);
+                 v[i] = vi;
+                 sv.add(cmul<T>(conjg<T>(a.d), vi));
+             });
+    sv.flush();
+    double2 s1[1] = {sv.hi};
+    block_partials<1>(s1, part);
+}
+
+// theta, c, tau, eta of half-step m from ||w||^2; true: the bound test stops
+__device__ __forceinline__ bool tf_half(KState* st, double w2, int m) {
+    const double theta = sqrt(w2) / st->s[S_TAU].x;
+    const double c2 = 1.0 / (1.0 + theta * theta);
+    const double tau = st->s[S_TAU].x * theta * sqrt(c2);
+    const double2 alpha = st->s[S_ALPHA];
+    st->s[S_THETA] = make_double2(theta, 0.0);
+    st->s[S_TAU] = make_double2(tau, 0.0);
+    st->s[S_ETA] = make_double2(c2 * alpha.x, c2 * alpha.y);
+    const double rel2 = tau * tau * (m + 1) / st->bnorm2;
+    st->rel2 = rel2;
+    if (!isfinite(rel2)) { st->status = ST_NAN; return true; }
+    if (rel2 <= st->tol2) { st->status = ST_HALF; return true; }
+    return false;
+}
+
+// alpha = rho / sigma; false after a breakdown
+__device__ __forceinline__ bool tf_alpha(KState* st, double2 sigma) {
+    if (!finite2(sigma)) { st->status = ST_NAN; return false; }
+    if (is_zero(sigma) || is_zero(st->s[S_RHO])) { st->status = ST_BREAKDOWN; return false; }
+    st->s[S_ALPHA] = ddiv(st->s[S_RHO], sigma);
+    return true;
+}
+
+// step 0: first alpha (after the first product); 1: after the even
+// half-step; 2: after the odd one (rho, beta); 3: after the new v (alpha,
+// end of the iteration)
+__global__ void __launch_bounds__(kVecThreads) k_tf_scalar(KState* st, const double2* __restrict__ part,
+                                                           int nparts, int step) {
+    st += blockIdx.x;
+    part += (int64_t)blockIdx.x * nparts * kMaxRed;
+    if ((step == 2 || step == 3) && st->status == ST_HALF) {
+        // the pending update of x has run: the iteration ends here
+        if (threadIdx.x == 0) { st->status = ST_CONVERGED; st->iter += 1; }
+        return;
+    }
+    if (st->status != ST_RUN) return;
+    double2 s[2];
+    final_sums<2>(part, nparts, s);
+    if (threadIdx.x != 0) return;
+    if (step == 0) {
+        st->matvecs += 1;
+        tf_alpha(st, s[0]);
+    } else if (step == 1) {
+        st->matvecs += 1;
+        tf_half(st, s[0].x, 2 * st->iter);
+    } else if (step == 2) {
+        if (tf_half(st, s[0].x, 2 * st->iter + 1)) return;
+        const double2 rho_new = s[1];
+        if (!finite2(rho_new)) { st->status = ST_NAN; return; }
+        if (is_zero(rho_new)) { st->status = ST_BREAKDOWN; return; }
+        st->s[S_BETA] = ddiv(rho_new, st->s[S_RHO]);
+        st->s[S_RHO] = rho_new;
+    } else {
+        st->matvecs += 1;
+        st->iter += 1;
+        if (!tf_alpha(st, s[0])) return;
+        if (st->iter >= st->maxit) st->status = ST_MAXIT;
     }
 }
 
@@ -763,8 +1111,9 @@ static int enqueue_iteration(int method, const MatvecView<T>& mv, KrylovWork<T>&
         k_bicg_update<T><<<G, B, 0, st>>>(ds, x, p, q, qt, r, rt, n, part);
         k_bicg_scalar<<<nb, B, 0, st>>>(ds, part, gx, 1, 2);
         k = 5;
-    } else if (method == DDA_BICG_SYM) {
-        // p = r + beta p (k_bcs_p with omega = 0), q = A p
+    } else if (method == DDA_BICG_SYM || method == DDA_CG) {
+        // p = r + beta p (k_bcs_p with omega = 0), q = A p; CG with the
+        // bilinear form runs this same recurrence
         C<T>*p = v[2], *q = v[3];
         k_bcs_p<T><<<G, B, 0, st>>>(ds, r, p, p, n, first);
         if ((rc = run_matvec<T>(mv, p, q, 0, st))) return rc;
@@ -773,20 +1122,58 @@ static int enqueue_iteration(int method, const MatvecView<T>& mv, KrylovWork<T>&
         k_cocg_update<T><<<G, B, 0, st>>>(ds, x, p, q, r, n, part);
         k_bicg_scalar<<<nb, B, 0, st>>>(ds, part, gx, 1, 1);
         k = 5;
+    } else if (method == DDA_CGS) {
+        C<T>*u = v[2], *p = v[3], *q = v[4], *vh = v[5], *uh = v[6], *qh = v[7];
+        k_cgs_up<T><<<G, B, 0, st>>>(ds, r, q, u, p, n, first);
+        if ((rc = run_matvec<T>(mv, p, vh, 0, st))) return rc;
+        k_dot1<T><<<G, B, 0, st>>>(ds, rt, vh, 0, n, part);
+        k_bicg_scalar<<<nb, B, 0, st>>>(ds, part, gx, 0, 2);
+        k_cgs_q<T><<<G, B, 0, st>>>(ds, u, vh, q, uh, x, n);
+        if ((rc = run_matvec<T>(mv, uh, qh, 0, st))) return rc;
+        k_cgs_r<T><<<G, B, 0, st>>>(ds, qh, r, rt, n, part);
+        k_bicg_scalar<<<nb, B, 0, st>>>(ds, part, gx, 1, 2);
+        k = 6;
+    } else if (method == DDA_TFQMR) {
+        // w = r (v[0]), rt = r (v[1]); the first iteration's prologue ran in krylov_solve
+        C<T>*w = v[0], *u0 = v[2], *u1 = v[3], *Au0 = v[4], *Au1 = v[5], *vv = v[6], *d = v[7];
+        k_tf_u1<T><<<G, B, 0, st>>>(ds, u0, vv, u1, n);
+        if ((rc = run_matvec<T>(mv, u1, Au1, 0, st))) return rc;
+        k_tf_even<T><<<G, B, 0, st>>>(ds, w, Au0, u0, d, n, part);
+        k_tf_scalar<<<nb, B, 0, st>>>(ds, part, gx, 1);
+        k_tf_odd<T><<<G, B, 0, st>>>(ds, x, w, Au1, u1, d, rt, n, part);
+        k_tf_scalar<<<nb, B, 0, st>>>(ds, part, gx, 2);
+        k_tf_next<T><<<G, B, 0, st>>>(ds, x, d, w, u1, u0, n);
+        if ((rc = run_matvec<T>(mv, u0, Au0, 0, st))) return rc;
+        k_tf_v<T><<<G, B, 0, st>>>(ds, Au0, Au1, vv, rt, n, 0, part);
+        k_tf_scalar<<<nb, B, 0, st>>>(ds, part, gx, 3);
+        k = 8;
+    } else if (method == DDA_QMR_SYM) {
+        C<T>*vt = v[1], *vv = v[3], *p = v[5], *pt = v[7], *d = v[8], *s = v[9];
+        k_qs_v<T><<<G, B, 0, st>>>(ds, vt, vv, n, part);
+        k_qmr_scalar<<<nb, B, 0, st>>>(ds, part, gx, 0, first, 1);
+        k_qs_p<T><<<G, B, 0, st>>>(ds, vv, p, n, first);
+        if ((rc = run_matvec<T>(mv, p, pt, 0, st))) return rc;
+        k_dot1<T><<<G, B, 0, st>>>(ds, p, pt, 1, n, part);
+        k_qmr_scalar<<<nb, B, 0, st>>>(ds, part, gx, 1, first, 1);
+        k_qs_vt<T><<<G, B, 0, st>>>(ds, pt, vv, vt, n, part);
+        k_qmr_scalar<<<nb, B, 0, st>>>(ds, part, gx, 2, first, 1);
+        k_qmr_ds<T><<<G, B, 0, st>>>(ds, p, pt, d, s, x, r, n, first, part);
+        k_qmr_scalar<<<nb, B, 0, st>>>(ds, part, gx, 3, first, 1);
+        k = 9;
     } else {
         C<T>*vt = v[1], *wt = v[2], *vv = v[3], *w = v[4], *p = v[5], *q = v[6], *pt = v[7], *d = v[8],
             *s = v[9];
         k_qmr_vw<T><<<G, B, 0, st>>>(ds, vt, wt, vv, w, n, part);
-        k_qmr_scalar<<<nb, B, 0, st>>>(ds, part, gx, 0, first);
+        k_qmr_scalar<<<nb, B, 0, st>>>(ds, part, gx, 0, first, 0);
         k_qmr_pq<T><<<G, B, 0, st>>>(ds, vv, w, p, q, n, first);
         if ((rc = run_matvec<T>(mv, p, pt, 0, st))) return rc;
         k_dot1<T><<<G, B, 0, st>>>(ds, q, pt, 1, n, part);
-        k_qmr_scalar<<<nb, B, 0, st>>>(ds, part, gx, 1, first);
+        k_qmr_scalar<<<nb, B, 0, st>>>(ds, part, gx, 1, first, 0);
         if ((rc = run_matvec<T>(mv, q, wt, 0, st))) return rc;   // A^T q = A q
         k_qmr_vtwt<T><<<G, B, 0, st>>>(ds, pt, vv, w, vt, wt, n, part);
-        k_qmr_scalar<<<nb, B, 0, st>>>(ds, part, gx, 2, first);
+        k_qmr_scalar<<<nb, B, 0, st>>>(ds, part, gx, 2, first, 0);
         k_qmr_ds<T><<<G, B, 0, st>>>(ds, p, pt, d, s, x, r, n, first, part);
-        k_qmr_scalar<<<nb, B, 0, st>>>(ds, part, gx, 3, first);
+        k_qmr_scalar<<<nb, B, 0, st>>>(ds, part, gx, 3, first, 0);
         k = 9;
     }
     note_launches(k);
@@ -843,14 +1230,25 @@ int krylov_solve(int method, MatvecView<T> mv, KrylovWork<T>& ws, const C<T>* b,
     }
     C<T>* rt = v[1];  // shadow residual (BiCG, BiCGSTAB) or vt (QMR)
     // BiCG: shadow conj(r0); BiCG_sym: rho = r^T r = conj(r)^H r, the same start
-    const int conj_rt = (method == DDA_BICG || method == DDA_BICG_SYM) ? 1 : 0;
+    const int conj_rt = (method == DDA_BICG || method == DDA_BICG_SYM || method == DDA_CG) ? 1 : 0;
     k_init<T><<<dim3(gx, nb), kVecThreads, 0, st>>>(b, x, r, rt, n, use_x0 ? 1 : 0, conj_rt, ws.part);
     DDA_LAUNCH_CHECK("krylov init");
-    k_init_scalar<<<nb, kVecThreads, 0, st>>>(ws.st, ws.part, gx, ctl, tol, max_iter,
-                                              method == DDA_QMR ? 1 : 0);
+    const int kind = (method == DDA_QMR || method == DDA_QMR_SYM) ? 1 : method == DDA_TFQMR ? 2 : 0;
+    k_init_scalar<<<nb, kVecThreads, 0, st>>>(ws.st, ws.part, gx, ctl, tol, max_iter, kind);
     DDA_LAUNCH_CHECK("krylov init scalar");
     if (method == DDA_QMR) {  // vt = r (v[1]), wt = r (v[2])
         DDA_CUDA_TRY(cudaMemcpyAsync(v[2], r, nb * n * sizeof(C<T>), cudaMemcpyDeviceToDevice, st));
+    }
+    if (method == DDA_TFQMR) {  // u0 = r, d = 0, Au0 = A u0, v = Au0, first alpha
+        const dim3 G(gx, nb);
+        MatvecView<T> m1 = mv;
+        k_tf_init<T><<<G, kVecThreads, 0, st>>>(ws.st, r, v[2], v[7], n);
+        DDA_LAUNCH_CHECK("tfqmr init");
+        if ((rc = run_matvec<T>(m1, v[2], v[4], 0, st))) return rc;
+        k_tf_v<T><<<G, kVecThreads, 0, st>>>(ws.st, v[4], v[5], v[6], rt, n, 1, ws.part);
+        DDA_LAUNCH_CHECK("tfqmr first v");
+        k_tf_scalar<<<nb, kVecThreads, 0, st>>>(ws.st, ws.part, gx, 0);
+        DDA_LAUNCH_CHECK("tfqmr first alpha");
     }
     // ---- iterations, polling the status words two iterations behind
     cudaEvent_t ev[2];

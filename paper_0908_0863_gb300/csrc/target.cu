@@ -426,6 +426,41 @@ int launch_adjoint_rhs(const TargetView& tv, const Geometry& g, double k, int wh
     return 0;
 }
 
+template <typename T>
+__global__ void k_site_scale(TargetView tv, Geometry g, const C<T>* __restrict__ tab, C<T>* __restrict__ vec,
+                             int64_t stride, int inverse) {
+    vec += (int64_t)blockIdx.y * stride;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < g.nsites; s += step) {
+        if (!occupied(tv, s)) continue;
+        const uint32_t r = site_rank(tv, s);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            C<T> f = tab[material(tv, s, c) * 3 + c];
+            if (inverse) {
+                const T d = f.x * f.x + f.y * f.y;
+                f = mk<T>(f.x / d, -f.y / d);
+            }
+            C<T>& v = vec[(int64_t)c * g.nd + r];
+            v = cmul<T>(v, f);
+        }
+    }
+}
+
+template <typename T>
+int launch_site_scale(const TargetView& tv, const Geometry& g, const C<T>* tab, C<T>* vec, int nb, int64_t stride,
+                      int inverse, cudaStream_t st) {
+    const unsigned gx = std::max(1u, std::min(grid_for(g.nsites, 256), (unsigned)((1216 + nb - 1) / nb)));
+    k_site_scale<T><<<dim3(gx, nb), 256, 0, st>>>(tv, g, tab, vec, stride, inverse);
+    DDA_LAUNCH_CHECK("Jacobi scaling");
+    return 0;
+}
+
+template int launch_site_scale<double>(const TargetView&, const Geometry&, const C<double>*, C<double>*, int, int64_t,
+                                       int, cudaStream_t);
+template int launch_site_scale<float>(const TargetView&, const Geometry&, const C<float>*, C<float>*, int, int64_t,
+                                      int, cudaStream_t);
+
 int launch_gradient(const TargetView& tv, const Geometry& g, double k, int which, const double2* dainv,
                     const double2* P, const double2* mu, double2* grad, cudaStream_t st) {
     k_gradient<<<grid_for(g.nsites, 256), 256, 0, st>>>(tv, g, k, which, dainv, P, mu, grad);

@@ -46,4 +46,11 @@ int launch_adjoint_rhs(const TargetView& tv, const Geometry& g, double k, int wh
 int launch_gradient(const TargetView& tv, const Geometry& g, double k, int which, const double2* dainv,
                     const double2* P, const double2* mu, double2* grad, cudaStream_t st);
 
+// Point-Jacobi scaling (Sec. 6): vec[b][c][rank(s)] *= tab[material(s, c)][c]
+// (or /= with inverse) for every occupied site s and right-hand side b < nb
+// (vectors of stride elements); tab = diag(A)^(-1/2) per material and axis
+template <typename T>
+int launch_site_scale(const TargetView& tv, const Geometry& g, const C<T>* tab, C<T>* vec, int nb, int64_t stride,
+                      int inverse, cudaStream_t st);
+
 }  // namespace dda
