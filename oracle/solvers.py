@@ -5,7 +5,8 @@ the paper cites for it, written for complex vectors:
 
 * BiCG, BiCGSTAB, QMR: Barrett et al. (1994); CGS: Sonneveld (1989);
   TFQMR: Freund (1993); BiCG_sym and QMR_sym: Freund (1992), the
-  complex-symmetric forms; CG: Hestenes & Stiefel (1952).
+  complex-symmetric forms; CG: Hestenes & Stiefel (1952); RBiCGSTAB as
+  BiCGSTAB(ell): Sleijpen & Fokkema (1993).
 * Hermitian inner products x^H y where the real template has x^T y (BiCG,
   BiCGSTAB, CGS, TFQMR, all with the shadow vector r0 or conj(r0)),
   bilinear products x^T y where the method relies on A = A^T (BiCG_sym,
@@ -418,6 +419,83 @@ def qmr_sym(A, b, tol=1e-8, max_iter=1000, x0=None):
     return x, _info(max_iter, mv, False, False, rel)
 
 
+def bicgstab_l(A, b, tol=1e-8, max_iter=1000, x0=None, ell=2):
+    """BiCGSTAB(ell) (Sleijpen & Fokkema 1993), the paper's restarted,
+    stabilised BiCG "RBiCGSTAB" with ell = its number of starting vectors:
+    each iteration ("cycle") runs ell BiCG steps that build r_j = A^j r and
+    u_j = A^j u, then replaces the residual by the minimal-residual
+    combination r_0 - sum_j gamma_j r_j (modified Gram-Schmidt on r_1..r_ell)
+    and updates x, u alike.  Shadow vector r0, Hermitian products; 2 ell
+    products per iteration.  Stopping test at the end of each cycle."""
+    x = np.zeros_like(b) if x0 is None else x0.copy()
+    r = b - A(x) if x0 is not None else b.copy()
+    mv = 1 if x0 is not None else 0
+    nb = _norm(b)
+    rel = _norm(r) / nb
+    if rel <= tol:
+        return x, _info(0, mv, True, False, rel)
+    rt = r.copy()
+    u = np.zeros_like(b)
+    rho0, alpha, omega = 1.0 + 0j, 0.0 + 0j, 1.0 + 0j
+    for it in range(1, max_iter + 1):
+        rh = [r] + [None] * ell
+        uh = [u] + [None] * ell
+        rho0 = -omega * rho0
+        for j in range(ell):                         # BiCG part
+            rho1 = np.vdot(rt, rh[j])
+            if rho0 == 0:
+                return x, _info(it, mv, False, True, rel)
+            beta = alpha * rho1 / rho0
+            rho0 = rho1
+            for i in range(j + 1):
+                uh[i] = rh[i] - beta * uh[i]
+            uh[j + 1] = A(uh[j])
+            mv += 1
+            gam = np.vdot(rt, uh[j + 1])
+            if gam == 0:
+                return x, _info(it, mv, False, True, rel)
+            alpha = rho0 / gam
+            for i in range(j + 1):
+                rh[i] = rh[i] - alpha * uh[i + 1]
+            rh[j + 1] = A(rh[j])
+            mv += 1
+            x = x + alpha * uh[0]
+        # minimal-residual part (modified Gram-Schmidt)
+        tau = np.zeros((ell + 1, ell + 1), dtype=complex)
+        sigma = np.zeros(ell + 1)
+        gp = np.zeros(ell + 1, dtype=complex)
+        for j in range(1, ell + 1):
+            for i in range(1, j):
+                tau[i, j] = np.vdot(rh[i], rh[j]) / sigma[i]
+                rh[j] = rh[j] - tau[i, j] * rh[i]
+            sigma[j] = np.real(np.vdot(rh[j], rh[j]))
+            if sigma[j] == 0:
+                return x, _info(it, mv, False, True, rel)
+            gp[j] = np.vdot(rh[j], rh[0]) / sigma[j]
+        g = np.zeros(ell + 1, dtype=complex)
+        g[ell] = gp[ell]
+        omega = g[ell]
+        for j in range(ell - 1, 0, -1):
+            g[j] = gp[j] - sum(tau[j, i] * g[i] for i in range(j + 1, ell + 1))
+        gpp = np.zeros(ell + 1, dtype=complex)
+        for j in range(1, ell):
+            gpp[j] = g[j + 1] + sum(tau[j, i] * g[i + 1] for i in range(j + 1, ell))
+        x = x + g[1] * rh[0]
+        rh[0] = rh[0] - gp[ell] * rh[ell]
+        uh[0] = uh[0] - g[ell] * uh[ell]
+        for j in range(1, ell):
+            uh[0] = uh[0] - g[j] * uh[j]
+            x = x + gpp[j] * rh[j]
+            rh[0] = rh[0] - gp[j] * rh[j]
+        r, u = rh[0], uh[0]
+        rel = _norm(r) / nb
+        if rel <= tol:
+            return x, _info(it, mv, True, False, rel)
+        if omega == 0:
+            return x, _info(it, mv, False, True, rel)
+    return x, _info(max_iter, mv, False, False, rel)
+
+
 def jacobi(solver, diag):
     """Point-Jacobi (diagonal) preconditioning of `solver`, applied as the
     symmetric scaling S A S y = S b, x = S y, S = diag^(-1/2) (principal
@@ -432,4 +510,7 @@ def jacobi(solver, diag):
 
 
 SOLVERS = {"bicg": bicg, "bicgstab": bicgstab, "qmr": qmr, "bicg_sym": bicg_sym, "cg": cg, "cgs": cgs,
-           "tfqmr": tfqmr, "qmr_sym": qmr_sym}
+           "tfqmr": tfqmr, "qmr_sym": qmr_sym,
+           "rbicgstab1": lambda *a, **k: bicgstab_l(*a, ell=1, **k),
+           "rbicgstab2": lambda *a, **k: bicgstab_l(*a, ell=2, **k),
+           "rbicgstab3": lambda *a, **k: bicgstab_l(*a, ell=3, **k)}

@@ -285,7 +285,8 @@ def test_optical_theorem_and_far_field():
     assert abs(ce - ca - cs) < 1e-12 * ce
 
 
-@pytest.mark.parametrize("name", ["bicg", "bicg_sym", "bicgstab", "qmr", "cg", "cgs", "tfqmr", "qmr_sym"])
+@pytest.mark.parametrize("name", ["bicg", "bicg_sym", "bicgstab", "qmr", "cg", "cgs", "tfqmr", "qmr_sym",
+                                  "rbicgstab1", "rbicgstab2", "rbicgstab3"])
 def test_solvers_match_lu(name):
     k = 0.45
     c, ainv, E, A, P = _solved(synth.sphere(6), k, 1.33 + 0.01j)
@@ -322,6 +323,23 @@ def test_cg_and_qmr_sym_follow_their_symmetric_twins():
         y2, j2 = solvers.qmr_sym(op, E.reshape(-1), tol=0, max_iter=it)
         assert np.abs(y1 - y2).max() <= 1e-11 * np.abs(y1).max()
         assert j1["matvecs"] == 2 * j2["matvecs"]
+
+
+def test_bicgstab_l_with_one_is_bicgstab():
+    # BiCGSTAB(1) is BiCGSTAB (Sleijpen & Fokkema 1993): same iterates when
+    # neither stops early; BiCGSTAB(ell) for ell = 2, 3 builds the same
+    # Krylov space with 2 ell products per cycle
+    k = 0.45
+    c, ainv, E, A, P = _solved(synth.sphere(5), k, 1.33 + 0.05j)
+    b = E.reshape(-1)
+    for it in (1, 3, 6):
+        x1, i1 = solvers.bicgstab_l(lambda v: A @ v, b, tol=0, max_iter=it, ell=1)
+        x2, i2 = solvers.bicgstab(lambda v: A @ v, b, tol=0, max_iter=it)
+        assert np.abs(x1 - x2).max() <= 1e-12 * np.abs(x2).max()
+        assert i1["matvecs"] == i2["matvecs"] == 2 * it
+    for ell in (2, 3):
+        x, info = solvers.bicgstab_l(lambda v: A @ v, b, tol=0, max_iter=2, ell=ell)
+        assert info["matvecs"] == 4 * ell
 
 
 def test_tfqmr_bound_covers_true_residual():
