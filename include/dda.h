@@ -71,15 +71,18 @@ typedef enum { DDA_C128 = 0, DDA_C64 = 1 } dda_dtype;
  * BiCG [2], BiCGSTAB [2], QMR with coupled two-term recurrences [2],
  * BiCG for complex-symmetric systems "BiCG_sym" [1], CG with the bilinear
  * form x^T y [1] (for a complex-symmetric A the same recurrence as
- * BiCG_sym), CGS [2], TFQMR [2; one iteration = two half-steps] and QMR
- * for complex-symmetric systems "QMR_sym" [1].  OR DDA_PRECOND_JACOBI into
+ * BiCG_sym), CGS [2], TFQMR [2; one iteration = two half-steps], QMR for
+ * complex-symmetric systems "QMR_sym" [1] and the restarted, stabilised BiCG
+ * "RBiCGSTAB" as BiCGSTAB(l), l = 1, 2, 3 [2 l; one iteration = one cycle of
+ * l BiCG steps and a degree-l minimal-residual polynomial, with the stopping
+ * test at the end of a cycle].  OR DDA_PRECOND_JACOBI into
  * the method for point-Jacobi preconditioning (Sec. 6), applied as the
  * symmetric scaling (S A S) y = S E_inc, P = S y, S = diag(alpha)^(1/2),
  * which keeps the matrix complex symmetric; the stopping test then applies
  * to the scaled residual. */
 typedef enum {
     DDA_BICG = 0, DDA_BICGSTAB = 1, DDA_QMR = 2, DDA_BICG_SYM = 3, DDA_CG = 4, DDA_CGS = 5, DDA_TFQMR = 6,
-    DDA_QMR_SYM = 7
+    DDA_QMR_SYM = 7, DDA_RBICGSTAB1 = 8, DDA_RBICGSTAB2 = 9, DDA_RBICGSTAB3 = 10
 } dda_method;
 #define DDA_PRECOND_JACOBI 0x100
 typedef enum { DDA_FP64 = 0, DDA_MIXED = 1 } dda_precision;

@@ -26,12 +26,14 @@ DDA_C128 = 0
 DDA_C64 = 1
 DDA_BICG, DDA_BICGSTAB, DDA_QMR, DDA_BICG_SYM = 0, 1, 2, 3
 DDA_CG, DDA_CGS, DDA_TFQMR, DDA_QMR_SYM = 4, 5, 6, 7
+DDA_RBICGSTAB1, DDA_RBICGSTAB2, DDA_RBICGSTAB3 = 8, 9, 10
 DDA_PRECOND_JACOBI = 0x100
 DDA_FP64, DDA_MIXED = 0, 1
 DDA_POL_CM, DDA_POL_CMRR, DDA_POL_LDR = 0, 1, 2
 
 METHODS = {"bicg": DDA_BICG, "bicgstab": DDA_BICGSTAB, "qmr": DDA_QMR, "bicg_sym": DDA_BICG_SYM, "cg": DDA_CG,
-           "cgs": DDA_CGS, "tfqmr": DDA_TFQMR, "qmr_sym": DDA_QMR_SYM}
+           "cgs": DDA_CGS, "tfqmr": DDA_TFQMR, "qmr_sym": DDA_QMR_SYM, "rbicgstab1": DDA_RBICGSTAB1,
+           "rbicgstab2": DDA_RBICGSTAB2, "rbicgstab3": DDA_RBICGSTAB3}
 
 
 def method_code(method) -> int:

@@ -981,7 +981,7 @@ static int check_solve_args(const dda_ctx* c, int nb, const void* einc, const vo
     if (int rc = check_ctx(c)) return rc;
     if (nb < 1 || nb > kMaxBatch) return fail(DDA_ERR_ARG, "dda_solve: nb must be in [1, 4096]");
     if (!einc || !p) return fail(DDA_ERR_ARG, "dda_solve: NULL einc or p");
-    if ((method & ~(0xff | DDA_PRECOND_JACOBI)) || (method & 0xff) > DDA_QMR_SYM)
+    if ((method & ~(0xff | DDA_PRECOND_JACOBI)) || (method & 0xff) > DDA_RBICGSTAB3)
         return fail(DDA_ERR_ARG, "dda_solve: unknown method");
     if (precision != DDA_FP64 && precision != DDA_MIXED) return fail(DDA_ERR_ARG, "dda_solve: unknown precision");
     if (!(tol > 0.0) || !std::isfinite(tol)) return fail(DDA_ERR_ARG, "dda_solve: tol must be finite and > 0");

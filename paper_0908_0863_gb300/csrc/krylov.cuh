@@ -14,6 +14,7 @@ enum Slot {
     S_NCP, S_NCQ,                                    // QMR: -(xi delta/eps), -(rho delta/eps)
     S_RHO_NEW, S_XI_NEW, S_TMP,
     S_TAU, S_THETA, S_CD,                            // TFQMR: tau, theta, theta^2 eta / alpha
+    S_G1, S_G2, S_G3,                                // BiCGSTAB(ell): minimal-residual coefficients
     S_NSLOTS
 };
 
@@ -49,7 +50,7 @@ constexpr int kCtlInts = (int)(sizeof(RhsCtl) / sizeof(int));
 constexpr int kVecBlocks = 152 * 4;   // blocks of one vector kernel over the whole batch
 constexpr int kVecThreads = 256;
 constexpr int kVecUnroll = 4;         // elements per thread per grid step
-constexpr int kMaxRed = 4;
+constexpr int kMaxRed = 10;         // partial sums per block (BiCGSTAB(3)'s Gram entries: 9)
 
 // blocks per right-hand side of the vector kernels: enough to cover n with
 // one grid step, at most kVecBlocks in total over the batch, at least one

@@ -163,6 +163,7 @@ template <typename T> struct V2 { C<T> a, b; };
 template <typename T> struct V3 { C<T> a, b, c; };
 template <typename T> struct V4 { C<T> a, b, c, d; };
 template <typename T> struct V6 { C<T> a, b, c, d, e, f; };
+template <typename T, int K> struct VN { C<T> v[K]; };
 
 // ---------------------------------------------------------------- common
 // r = b - r (r = A x on entry when has_x0), x = 0 otherwise r = b; rt = r or
@@ -220,6 +221,10 @@ __global__ void __launch_bounds__(kVecThreads) k_init_scalar(KState* st, const d
     if (maxit < 1) { st->status = ST_MAXIT; return; }
     st->s[S_RHO] = s[2];
     if (kind == 2) st->s[S_TAU] = make_double2(sqrt(s[1].x), 0.0);
+    if (kind == 3) {   // BiCGSTAB(ell): rho0 = 1, alpha = 0, omega = 1, the first cycle starts from -omega rho0
+        st->s[S_RHO_OLD] = make_double2(-1.0, 0.0);
+        st->s[S_OMEGA] = make_double2(1.0, 0.0);
+    }
     if (kind == 1) {
         st->s[S_RHOQ] = make_double2(sqrt(s[1].x), 0.0);
         st->s[S_XI] = make_double2(sqrt(s[1].x), 0.0);
@@ -1000,6 +1005,235 @@ __global__ void __launch_bounds__(kVecThreads) k_tf_scalar(KState* st, const dou
     }
 }
 
+// ------------------------------------------------------------ BiCGSTAB(l)
+// One iteration is a cycle of l BiCG steps building r_j = A^j r and
+// u_j = A^j u (j <= l), then the minimal-residual step: the gamma_j that
+// minimise ||r_0 - sum_j gamma_j r_j|| come from the l x l Gram system of
+// r_1..r_l (solved in FP64 on the device; the same minimiser as the
+// modified Gram-Schmidt of Sleijpen & Fokkema 1993), and
+// x += sum gamma_j r_(j-1), r_0 -= sum gamma_j r_j, u_0 -= sum gamma_j u_j.
+template <typename T>
+struct BLVecs {
+    C<T>* r[4];
+    C<T>* u[4];
+};
+
+// u_i = r_i - beta u_i, i < CNT
+template <typename T, int CNT>
+__global__ void __launch_bounds__(kVecThreads) k_bl_u(const KState* st, BLVecs<T> w, int64_t n) {
+    st += blockIdx.y;
+    if (st->status != ST_RUN) return;
+    const C<T>* r[CNT];
+    C<T>* u[CNT];
+#pragma unroll
+    for (int i = 0; i < CNT; ++i) { r[i] = rhs_vec(w.r[i], n); u[i] = rhs_vec(w.u[i], n); }
+    const C<T> beta = to_t<T>(st->s[S_BETA]);
+    const C<T> nbeta = mk<T>(-beta.x, -beta.y);
+    vec_loop(n,
+             [&](int64_t k) {
+                 VN<T, 2 * CNT> a;
+#pragma unroll
+                 for (int i = 0; i < CNT; ++i) { a.v[i] = r[i][k]; a.v[CNT + i] = u[i][k]; }
+                 return a;
+             },
+             [&](int64_t k, const VN<T, 2 * CNT>& a) {
+#pragma unroll
+                 for (int i = 0; i < CNT; ++i) u[i][k] = cfma<T>(nbeta, a.v[CNT + i], a.v[i]);
+             });
+}
+
+// r_i -= alpha u_(i+1), i < CNT; x += alpha u_0
+template <typename T, int CNT>
+__global__ void __launch_bounds__(kVecThreads) k_bl_r(const KState* st, BLVecs<T> w, C<T>* __restrict__ x,
+                                                      int64_t n) {
+    st += blockIdx.y;
+    if (st->status != ST_RUN) return;
+    C<T>* r[CNT];
+    const C<T>* u[CNT + 1];
+#pragma unroll
+    for (int i = 0; i < CNT; ++i) r[i] = rhs_vec(w.r[i], n);
+#pragma unroll
+    for (int i = 0; i <= CNT; ++i) u[i] = rhs_vec(w.u[i], n);
+    x = rhs_vec(x, n);
+    const C<T> alpha = to_t<T>(st->s[S_ALPHA]);
+    const C<T> nalpha = mk<T>(-alpha.x, -alpha.y);
+    vec_loop(n,
+             [&](int64_t k) {
+                 VN<T, 2 * CNT + 2> a;
+#pragma unroll
+                 for (int i = 0; i < CNT; ++i) a.v[i] = r[i][k];
+#pragma unroll
+                 for (int i = 0; i <= CNT; ++i) a.v[CNT + i] = u[i][k];
+                 a.v[2 * CNT + 1] = x[k];
+                 return a;
+             },
+             [&](int64_t k, const VN<T, 2 * CNT + 2>& a) {
+#pragma unroll
+                 for (int i = 0; i < CNT; ++i) r[i][k] = cfma<T>(nalpha, a.v[CNT + i + 1], a.v[i]);
+                 x[k] = cfma<T>(alpha, a.v[CNT], a.v[2 * CNT + 1]);
+             });
+}
+
+// Gram entries of the minimal-residual step: c_i = r_i^H r_0 (i = 1..L),
+// then G_ij = r_i^H r_j for 1 <= i <= j <= L, in that order
+template <typename T, int L>
+__global__ void __launch_bounds__(kVecThreads) k_bl_gram(const KState* st, BLVecs<T> w, int64_t n,
+                                                         double2* __restrict__ part) {
+    st += blockIdx.y;
+    if (st->status != ST_RUN) return;
+    constexpr int NR = L + L * (L + 1) / 2;
+    const C<T>* r[L + 1];
+#pragma unroll
+    for (int i = 0; i <= L; ++i) r[i] = rhs_vec(w.r[i], n);
+    part = rhs_part(part);
+    DotAcc<T> acc[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) acc[q].init();
+    vec_loop(n,
+             [&](int64_t k) {
+                 VN<T, L + 1> a;
+#pragma unroll
+                 for (int i = 0; i <= L; ++i) a.v[i] = r[i][k];
+                 return a;
+             },
+             [&](int64_t, const VN<T, L + 1>& a) {
+                 int q = 0;
+#pragma unroll
+                 for (int i = 1; i <= L; ++i) acc[q++].add(cmul<T>(conjg<T>(a.v[i]), a.v[0]));
+#pragma unroll
+                 for (int i = 1; i <= L; ++i)
+#pragma unroll
+                     for (int j = i; j <= L; ++j) acc[q++].add(cmul<T>(conjg<T>(a.v[i]), a.v[j]));
+             });
+    double2 out[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) { acc[q].flush(); out[q] = acc[q].hi; }
+    block_partials<NR>(out, part);
+}
+
+// x += sum_j gamma_j r_(j-1); r_0 -= sum_j gamma_j r_j; u_0 -= sum_j gamma_j u_j;
+// partials ||r_0||^2, rt^H r_0
+template <typename T, int L>
+__global__ void __launch_bounds__(kVecThreads) k_bl_fin(const KState* st, BLVecs<T> w, C<T>* __restrict__ x,
+                                                        const C<T>* __restrict__ rt, int64_t n,
+                                                        double2* __restrict__ part) {
+    st += blockIdx.y;
+    if (st->status != ST_RUN) return;
+    C<T>* r[L + 1];
+    C<T>* u[L + 1];
+#pragma unroll
+    for (int i = 0; i <= L; ++i) { r[i] = rhs_vec(w.r[i], n); u[i] = rhs_vec(w.u[i], n); }
+    x = rhs_vec(x, n); rt = rhs_vec(rt, n); part = rhs_part(part);
+    C<T> g[L + 1];
+#pragma unroll
+    for (int j = 1; j <= L; ++j) g[j] = to_t<T>(st->s[S_G1 + j - 1]);
+    DotAcc<T> nr, rr;
+    nr.init(); rr.init();
+    vec_loop(n,
+             [&](int64_t k) {
+                 VN<T, 2 * L + 4> a;
+#pragma unroll
+                 for (int i = 0; i <= L; ++i) { a.v[i] = r[i][k]; a.v[L + 1 + i] = u[i][k]; }
+                 a.v[2 * L + 2] = x[k];
+                 a.v[2 * L + 3] = rt[k];
+                 return a;
+             },
+             [&](int64_t k, const VN<T, 2 * L + 4>& a) {
+                 C<T> xi = a.v[2 * L + 2], ri = a.v[0], ui = a.v[L + 1];
+#pragma unroll
+                 for (int j = 1; j <= L; ++j) {
+                     xi = cfma<T>(g[j], a.v[j - 1], xi);
+                     ri = csub<T>(ri, cmul<T>(g[j], a.v[j]));
+                     ui = csub<T>(ui, cmul<T>(g[j], a.v[L + 1 + j]));
+                 }
+                 x[k] = xi;
+                 r[0][k] = ri;
+                 u[0][k] = ui;
+                 nr.add(norm2c<T>(ri));
+                 rr.add(cmul<T>(conjg<T>(a.v[2 * L + 3]), ri));
+             });
+    nr.flush(); rr.flush();
+    double2 s2[2] = {nr.hi, rr.hi};
+    block_partials<2>(s2, part);
+}
+
+// solves the Hermitian L x L system G g = c (G_ij for i <= j given, row i
+// of the upper triangle first) by Gaussian elimination with partial
+// pivoting; false when singular
+__device__ bool bl_solve(int L, const double2* __restrict__ gram, double2* g) {
+    double2 M[3][4];
+    int q = L;
+    for (int i = 0; i < L; ++i) M[i][L] = gram[i];
+    for (int i = 0; i < L; ++i)
+        for (int j = i; j < L; ++j) {
+            const double2 v = gram[q++];
+            M[i][j] = v;
+            M[j][i] = make_double2(v.x, -v.y);
+        }
+    for (int c = 0; c < L; ++c) {
+        int piv = c;
+        for (int i = c + 1; i < L; ++i)
+            if (hypot(M[i][c].x, M[i][c].y) > hypot(M[piv][c].x, M[piv][c].y)) piv = i;
+        if (is_zero(M[piv][c])) return false;
+        if (piv != c)
+            for (int j = 0; j <= L; ++j) { const double2 t = M[c][j]; M[c][j] = M[piv][j]; M[piv][j] = t; }
+        for (int i = c + 1; i < L; ++i) {
+            const double2 f = ddiv(M[i][c], M[c][c]);
+            for (int j = c; j <= L; ++j) {
+                const double2 t = dmul(f, M[c][j]);
+                M[i][j] = make_double2(M[i][j].x - t.x, M[i][j].y - t.y);
+            }
+        }
+    }
+    for (int i = L - 1; i >= 0; --i) {
+        double2 acc = M[i][L];
+        for (int j = i + 1; j < L; ++j) {
+            const double2 t = dmul(M[i][j], g[j]);
+            acc = make_double2(acc.x - t.x, acc.y - t.y);
+        }
+        g[i] = ddiv(acc, M[i][i]);
+        if (!finite2(g[i])) return false;
+    }
+    return true;
+}
+
+// step 0: beta (rho1 from the dot of step j > 0, or carried over for j = 0);
+// 1: alpha; 2: the minimal-residual coefficients; 3: end of the cycle
+__global__ void __launch_bounds__(kVecThreads) k_bl_scalar(KState* st, const double2* __restrict__ part,
+                                                           int nparts, int step, int j, int ell) {
+    st += blockIdx.x;
+    part += (int64_t)blockIdx.x * nparts * kMaxRed;
+    if (st->status != ST_RUN) return;
+    double2 s[9];
+    final_sums<9>(part, nparts, s);
+    if (threadIdx.x != 0) return;
+    if (step == 0) {
+        const double2 rho1 = j == 0 ? st->s[S_RHO] : s[0];
+        const double2 rho0 = st->s[S_RHO_OLD];
+        if (!finite2(rho1)) { st->status = ST_NAN; return; }
+        if (is_zero(rho0)) { st->status = ST_BREAKDOWN; return; }
+        st->s[S_BETA] = dmul(st->s[S_ALPHA], ddiv(rho1, rho0));
+        st->s[S_RHO_OLD] = rho1;
+    } else if (step == 1) {
+        const double2 gam = s[0];
+        if (!finite2(gam)) { st->status = ST_NAN; return; }
+        if (is_zero(gam)) { st->status = ST_BREAKDOWN; return; }
+        st->s[S_ALPHA] = ddiv(st->s[S_RHO_OLD], gam);
+    } else if (step == 2) {
+        st->matvecs += 2 * ell;
+        double2 g[3];
+        if (!bl_solve(ell, s, g)) { st->status = ST_BREAKDOWN; return; }
+        for (int q = 0; q < ell; ++q) st->s[S_G1 + q] = g[q];
+        st->s[S_OMEGA] = g[ell - 1];
+    } else {
+        if (end_of_iteration(st, s[0].x / st->bnorm2)) return;
+        const double2 om = st->s[S_OMEGA];
+        if (is_zero(om)) { st->status = ST_BREAKDOWN; return; }
+        st->s[S_RHO] = s[1];                                     // rho1 of the next cycle's first step
+        st->s[S_RHO_OLD] = dmul(make_double2(-om.x, -om.y), st->s[S_RHO_OLD]);
+    }
+}
+
 // ------------------------------------------------------ refinement helpers
 __global__ void __launch_bounds__(kVecThreads) k_norm2_c128(const double2* __restrict__ a, int64_t n,
                                                             double2* __restrict__ part) {
@@ -1147,6 +1381,36 @@ static int enqueue_iteration(int method, const MatvecView<T>& mv, KrylovWork<T>&
         k_tf_v<T><<<G, B, 0, st>>>(ds, Au0, Au1, vv, rt, n, 0, part);
         k_tf_scalar<<<nb, B, 0, st>>>(ds, part, gx, 3);
         k = 8;
+    } else if (method >= DDA_RBICGSTAB1 && method <= DDA_RBICGSTAB3) {
+        const int ell = method - DDA_RBICGSTAB1 + 1;
+        BLVecs<T> w{{v[0], v[2], v[3], v[4]}, {v[5], v[6], v[7], v[8]}};
+        for (int j = 0; j < ell; ++j) {
+            if (j > 0) {
+                k_dot1<T><<<G, B, 0, st>>>(ds, rt, w.r[j], 0, n, part);
+                ++k;
+            }
+            k_bl_scalar<<<nb, B, 0, st>>>(ds, part, gx, 0, j, ell);
+            if (j == 0) k_bl_u<T, 1><<<G, B, 0, st>>>(ds, w, n);
+            else if (j == 1) k_bl_u<T, 2><<<G, B, 0, st>>>(ds, w, n);
+            else k_bl_u<T, 3><<<G, B, 0, st>>>(ds, w, n);
+            if ((rc = run_matvec<T>(mv, w.u[j], w.u[j + 1], 0, st))) return rc;
+            k_dot1<T><<<G, B, 0, st>>>(ds, rt, w.u[j + 1], 0, n, part);
+            k_bl_scalar<<<nb, B, 0, st>>>(ds, part, gx, 1, j, ell);
+            if (j == 0) k_bl_r<T, 1><<<G, B, 0, st>>>(ds, w, x, n);
+            else if (j == 1) k_bl_r<T, 2><<<G, B, 0, st>>>(ds, w, x, n);
+            else k_bl_r<T, 3><<<G, B, 0, st>>>(ds, w, x, n);
+            if ((rc = run_matvec<T>(mv, w.r[j], w.r[j + 1], 0, st))) return rc;
+            k += 5;
+        }
+        if (ell == 1) k_bl_gram<T, 1><<<G, B, 0, st>>>(ds, w, n, part);
+        else if (ell == 2) k_bl_gram<T, 2><<<G, B, 0, st>>>(ds, w, n, part);
+        else k_bl_gram<T, 3><<<G, B, 0, st>>>(ds, w, n, part);
+        k_bl_scalar<<<nb, B, 0, st>>>(ds, part, gx, 2, 0, ell);
+        if (ell == 1) k_bl_fin<T, 1><<<G, B, 0, st>>>(ds, w, x, rt, n, part);
+        else if (ell == 2) k_bl_fin<T, 2><<<G, B, 0, st>>>(ds, w, x, rt, n, part);
+        else k_bl_fin<T, 3><<<G, B, 0, st>>>(ds, w, x, rt, n, part);
+        k_bl_scalar<<<nb, B, 0, st>>>(ds, part, gx, 3, 0, ell);
+        k += 4;
     } else if (method == DDA_QMR_SYM) {
         C<T>*vt = v[1], *vv = v[3], *p = v[5], *pt = v[7], *d = v[8], *s = v[9];
         k_qs_v<T><<<G, B, 0, st>>>(ds, vt, vv, n, part);
@@ -1233,11 +1497,15 @@ int krylov_solve(int method, MatvecView<T> mv, KrylovWork<T>& ws, const C<T>* b,
     const int conj_rt = (method == DDA_BICG || method == DDA_BICG_SYM || method == DDA_CG) ? 1 : 0;
     k_init<T><<<dim3(gx, nb), kVecThreads, 0, st>>>(b, x, r, rt, n, use_x0 ? 1 : 0, conj_rt, ws.part);
     DDA_LAUNCH_CHECK("krylov init");
-    const int kind = (method == DDA_QMR || method == DDA_QMR_SYM) ? 1 : method == DDA_TFQMR ? 2 : 0;
+    const bool bl = method >= DDA_RBICGSTAB1 && method <= DDA_RBICGSTAB3;
+    const int kind = (method == DDA_QMR || method == DDA_QMR_SYM) ? 1 : method == DDA_TFQMR ? 2 : bl ? 3 : 0;
     k_init_scalar<<<nb, kVecThreads, 0, st>>>(ws.st, ws.part, gx, ctl, tol, max_iter, kind);
     DDA_LAUNCH_CHECK("krylov init scalar");
     if (method == DDA_QMR) {  // vt = r (v[1]), wt = r (v[2])
         DDA_CUDA_TRY(cudaMemcpyAsync(v[2], r, nb * n * sizeof(C<T>), cudaMemcpyDeviceToDevice, st));
+    }
+    if (bl) {  // u_0 = 0
+        DDA_CUDA_TRY(cudaMemsetAsync(v[5], 0, nb * n * sizeof(C<T>), st));
     }
     if (method == DDA_TFQMR) {  // u0 = r, d = 0, Au0 = A u0, v = Au0, first alpha
         const dim3 G(gx, nb);

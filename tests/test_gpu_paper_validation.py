@@ -73,9 +73,10 @@ def test_table3_iteration_counts(dda, golden):
     """The paper's solver benchmark (Sec. 6, Table 3): SPHERE 200^3, x =
     0.98948, m = 1.63631 + 0.372i, point-Jacobi, tol 1e-10, x0 = 0.  The
     paper does not state its stopping test; with ours (recurrence residual
-    <= tol ||E||, TFQMR's quasi-residual bound) every scheme stops within
-    two iterations of the printed count, and BiCGSTAB, CGS and TFQMR on it.
-    The polarisability is LDR (the reading Table 7 pins)."""
+    <= tol ||E||, TFQMR's quasi-residual bound, BiCGSTAB(l) at the end of a
+    cycle) every scheme stops within two iterations of the printed count,
+    and BiCGSTAB, CGS, TFQMR and BiCGSTAB(3) on it.  The polarisability is
+    LDR (the reading Table 7 pins)."""
     t = golden["table3_iterations"]
     n = t["n"]
     m = complex(t["m_re"], t["m_im"])
@@ -96,5 +97,5 @@ def test_table3_iteration_counts(dda, golden):
     print("Table 3 iterations (ours / paper):", {m: (got[m], t["iterations"][m]) for m in got})
     for method, ni in t["iterations"].items():
         assert abs(got[method] - ni) <= 2, (method, got[method], ni)
-    for method in ("bicgstab", "cgs", "tfqmr"):
+    for method in ("bicgstab", "cgs", "tfqmr", "rbicgstab3"):
         assert got[method] == t["iterations"][method]

@@ -1,4 +1,4 @@
-"""GPU parity of CG, CGS, TFQMR and QMR_sym and of point-Jacobi
+"""GPU parity of CG, CGS, TFQMR, QMR_sym and BiCGSTAB(l) and of point-Jacobi
 preconditioning against the FP64 oracle, through the C ABI.
 
 Targets: the 16^3 sphere of the single-solve tests (config 1, one
@@ -18,7 +18,7 @@ from _cases import Case, config1_case
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 DEV = "cuda"
-NEW = ["cg", "cgs", "tfqmr", "qmr_sym"]
+NEW = ["cg", "cgs", "tfqmr", "qmr_sym", "rbicgstab1", "rbicgstab2", "rbicgstab3"]
 
 
 @pytest.fixture(scope="module")
@@ -79,7 +79,7 @@ def test_new_solvers_follow_oracle_iterates(dda, c1, method):
     assert np.abs(Pg.reshape(-1) - x).max() <= 1e-6 * np.abs(x).max()
 
 
-@pytest.mark.parametrize("method", ["bicgstab", "qmr_sym", "tfqmr"])
+@pytest.mark.parametrize("method", ["bicgstab", "qmr_sym", "tfqmr", "rbicgstab2"])
 def test_new_solvers_mixed(dda, c1, method):
     case, A, E, P = c1
     status, info, Pg, cx = _gpu_solve(case, E, method, "mixed", 1e-6)
@@ -89,7 +89,7 @@ def test_new_solvers_mixed(dda, c1, method):
     assert abs(cx[0] / ce - 1) < 1e-5 and abs(cx[1] / ca - 1) < 1e-5
 
 
-@pytest.mark.parametrize("method", ["bicg_sym", "bicgstab", "qmr_sym", "tfqmr", "cgs"])
+@pytest.mark.parametrize("method", ["bicg_sym", "bicgstab", "qmr_sym", "tfqmr", "cgs", "rbicgstab3"])
 def test_jacobi_two_materials(dda, incl, method):
     case, A, E, P = incl
     status, info, Pg, cx = _gpu_solve(case, E, method + "+jacobi", "fp64", 1e-12)
@@ -124,7 +124,7 @@ def test_jacobi_single_material_is_a_scaling(dda, c1):
     assert np.abs(P0 - P1).max() <= 1e-9 * np.abs(P0).max()
 
 
-@pytest.mark.parametrize("method", ["cg", "cgs", "tfqmr", "qmr_sym"])
+@pytest.mark.parametrize("method", ["cg", "cgs", "tfqmr", "qmr_sym", "rbicgstab2"])
 def test_new_solvers_batched(dda, c1, method):
     case, A, E, P = c1
     pairs = []
