@@ -292,14 +292,22 @@ def algorithmic_bytes(n, nd, esize):
             "matvec_min": 3 * V + 4 * A + T}
 
 
-KERNEL_SOURCES = ("matvec_kernels.cuh", "fft_reg.cuh", "fft.cuh", "matvec.cuh", "common.cuh")
+# what the P3 traffic figure depends on: the P3 section of the kernel header
+# (from its P3 banner to the P5 banner) and the headers it includes
+KERNEL_SOURCES = ("fft_reg.cuh", "fft.cuh", "matvec.cuh", "common.cuh")
+P3_SECTION = ("// ---------------------------------------------------------------- P3",
+              "// ---------------------------------------------------------------- P5")
 
 
 def kernel_sources_hash():
-    """First 16 hex digits of the SHA-256 of the matvec kernel sources
-    (csrc/ + KERNEL_SOURCES, concatenated in that order)."""
+    """First 16 hex digits of the SHA-256 of the z-pass kernel source: the P3
+    section of csrc/matvec_kernels.cuh followed by KERNEL_SOURCES."""
     import hashlib
     h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_0908_0863_gb300/csrc/matvec_kernels.cuh")) as f:
+        text = f.read()
+    a, b = text.index(P3_SECTION[0]), text.index(P3_SECTION[1])
+    h.update(text[a:b].encode())
     for rel in (f"paper_0908_0863_gb300/csrc/{f}" for f in KERNEL_SOURCES):
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
