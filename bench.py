@@ -406,6 +406,9 @@ def extras(args, dda, torch, dev, shape, bits, alpha, nd, pass_ms, khat, pols):
             del E, P
         if args.qmr_solve:
             out["qmr_mixed_solve"] = timed_single_solve(dda, torch, dev, ctx, nd, khat, pols[0], "qmr", args)
+        for meth in [m for m in args.also_methods.split(",") if m]:
+            out.setdefault("other_methods", {})[meth] = timed_single_solve(dda, torch, dev, ctx, nd, khat, pols[0],
+                                                                           meth, args)
         if args.batch > 0:
             out["batch"] = timed_batch(dda, torch, dev, ctx, nd, args)
     finally:
@@ -648,7 +651,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--edge", type=int, default=N_EDGE)
     ap.add_argument("--diameter", type=int, default=DIAM)
-    ap.add_argument("--method", default="bicgstab", choices=["bicg", "bicgstab", "qmr"])
+    ap.add_argument("--method", default="bicgstab")
     ap.add_argument("--tol", type=float, default=TOL)
     ap.add_argument("--max-iter", type=int, default=4000)
     ap.add_argument("--cpu-rows", type=int, default=200)
@@ -656,6 +659,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--fp64-solve", action="store_true")
     ap.add_argument("--qmr-solve", action="store_true", help="also time one mixed QMR solve")
+    ap.add_argument("--also-methods", default="", help="comma-separated methods to time one mixed solve each")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the default tile widths instead of tuning them before the warm-up")
     ap.add_argument("--batch", type=int, default=16, help="right-hand sides of the batched-solve extra (0: skip)")
