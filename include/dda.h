@@ -214,21 +214,25 @@ int dda_matvec(dda_ctx* ctx, const void* p, void* y, int dtype, void* stream);
 int dda_matvec_batch(dda_ctx* ctx, int nb, const void* p, void* y, int dtype, void* stream);
 
 /*
- * Tile widths of the matvec passes, as log2 of the lines one CTA
- * transforms: tiles[0] for P1/P5 (y lines), tiles[1] for P3 (z columns),
- * tiles[2] for P2/P4 (x rows), for dtype DDA_C128 or DDA_C64.  tiles_in
- * (host int[3], may be NULL) sets them after checking the launch limits
- * (threads per block, shared memory; DDA_ERR_ARG when exceeded); tiles_out
- * (host int[3], may be NULL) receives the current ones.  The widths only
+ * Tile settings of the matvec passes for dtype DDA_C128 or DDA_C64, as host
+ * int[4]: tiles[0], [1], [2] = log2 of the lines one CTA transforms in
+ * P1/P5 (y lines), P3 (z columns) and P2/P4 (x rows); tiles[3] = the z
+ * pass schedule, 0 = one CTA per tile of columns, 1 = persistent CTAs that
+ * stage the next tile's input columns in shared memory (cp.async) while
+ * transforming the current one (whole tiles and 16-byte stage rows only).
+ * tiles_in (may be NULL) sets them after checking the launch limits
+ * (threads per block, shared memory; DDA_ERR_ARG when exceeded);
+ * tiles_out (may be NULL) receives the current ones.  The settings only
  * regroup lines between CTAs: every line's arithmetic, and so every result
- * bit, is the same for all valid widths.
+ * bit, is the same for all valid settings.
  */
 int dda_tiles(dda_ctx* ctx, int dtype, int* tiles_out, const int* tiles_in);
 
 /*
- * Autotune the tile widths of dtype on this context: starting from the
- * current widths, try up to two steps either way for P3, then P1/P5, then
- * P2/P4, timing `reps` batched products of nb right-hand sides per
+ * Autotune the tile settings of dtype on this context: starting from the
+ * current ones, try up to two width steps either way for P3, then both z
+ * pass schedules, then up to two steps for P1/P5 and for P2/P4, timing
+ * `reps` batched products of nb right-hand sides per
  * candidate with CUDA events (after one untimed product), and keep the
  * fastest.  The choice is set on the context and remembered for the
  * process: contexts created later with the same lattice shape start with

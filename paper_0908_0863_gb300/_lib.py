@@ -258,9 +258,16 @@ def _dtype_name(dtype):
 
 
 def dda_tiles(ctx, dtype="c64", tiles=None):
-    """Current tile widths (log2 lines per CTA of P1/P5, P3, P2/P4); sets them first when given."""
-    out = np.zeros(3, dtype=np.int32)
-    tin = None if tiles is None else np.ascontiguousarray(np.asarray(tiles, dtype=np.int32).reshape(3))
+    """Current tile settings (log2 lines per CTA of P1/P5, P3, P2/P4, and the
+    z pass schedule 0/1); sets them first when given (3 widths keep the
+    schedule)."""
+    out = np.zeros(4, dtype=np.int32)
+    tin = None
+    if tiles is not None:
+        tiles = list(tiles)
+        if len(tiles) == 3:
+            tiles.append(dda_tiles(ctx, dtype)[3])
+        tin = np.ascontiguousarray(np.asarray(tiles, dtype=np.int32).reshape(4))
     _check(load().dda_tiles(ctypes.c_void_p(ctx), _dtype_name(dtype), _ptr(out), _ptr(tin)))
     return tuple(int(v) for v in out)
 

@@ -333,15 +333,16 @@ KrylovWork<float> work32(const dda_ctx* c, int nb) {
 // Tile widths chosen by dda_autotune, per lattice shape and dtype, for the
 // whole process: later contexts of the same shape start with them.
 std::mutex g_tiles_mu;
-std::map<std::array<int, 4>, std::array<int, 3>> g_tiles;
+std::map<std::array<int, 4>, std::array<int, 4>> g_tiles;
 
 std::array<int, 4> tile_key(const Geometry& g, int dtype) { return {g.K, g.J, g.P, dtype}; }
 
 template <typename T>
-void apply_tiles(MatvecView<T>& m, const std::array<int, 3>& t) {
+void apply_tiles(MatvecView<T>& m, const std::array<int, 4>& t) {
     m.logW_y = t[0];
     m.logW_z = t[1];
     m.logW_x = t[2];
+    m.p3_sched = t[3];
 }
 
 int64_t context_bytes(const dda_ctx* c) {
@@ -683,16 +684,22 @@ int dda_tiles(dda_ctx* c, int dtype, int* tiles_out, const int* tiles_in) {
     if (int rc = check_ctx(c)) return rc;
     if (dtype != DDA_C128 && dtype != DDA_C64) return fail(DDA_ERR_ARG, "dda_tiles: unknown dtype");
     if (tiles_in) {
-        const bool ok = dtype == DDA_C128 ? tiles_ok<double>(c->g, tiles_in[0], tiles_in[1], tiles_in[2])
-                                          : tiles_ok<float>(c->g, tiles_in[0], tiles_in[1], tiles_in[2]);
-        if (!ok) return fail(DDA_ERR_ARG, "dda_tiles: tile widths exceed the launch limits");
-        const std::array<int, 3> t{tiles_in[0], tiles_in[1], tiles_in[2]};
+        const bool ok =
+            dtype == DDA_C128 ? tiles_ok<double>(c->g, tiles_in[0], tiles_in[1], tiles_in[2], tiles_in[3])
+                              : tiles_ok<float>(c->g, tiles_in[0], tiles_in[1], tiles_in[2], tiles_in[3]);
+        if (!ok) return fail(DDA_ERR_ARG, "dda_tiles: tile widths or schedule not launchable for this lattice");
+        const std::array<int, 4> t{tiles_in[0], tiles_in[1], tiles_in[2], tiles_in[3]};
         if (dtype == DDA_C128) apply_tiles(c->mv64, t);
         else apply_tiles(c->mv32, t);
     }
     if (tiles_out) {
-        if (dtype == DDA_C128) { tiles_out[0] = c->mv64.logW_y; tiles_out[1] = c->mv64.logW_z; tiles_out[2] = c->mv64.logW_x; }
-        else { tiles_out[0] = c->mv32.logW_y; tiles_out[1] = c->mv32.logW_z; tiles_out[2] = c->mv32.logW_x; }
+        if (dtype == DDA_C128) {
+            tiles_out[0] = c->mv64.logW_y; tiles_out[1] = c->mv64.logW_z; tiles_out[2] = c->mv64.logW_x;
+            tiles_out[3] = c->mv64.p3_sched;
+        } else {
+            tiles_out[0] = c->mv32.logW_y; tiles_out[1] = c->mv32.logW_z; tiles_out[2] = c->mv32.logW_x;
+            tiles_out[3] = c->mv32.p3_sched;
+        }
     }
     return DDA_OK;
 }
@@ -717,15 +724,17 @@ int dda_autotune(dda_ctx* c, int dtype, int nb, int reps, double* pass_ms, void*
     c->prof.on = true;
     const int d = dtype == DDA_C128 ? 0 : 1;
     auto current = [&]() {
-        return dtype == DDA_C128 ? std::array<int, 3>{c->mv64.logW_y, c->mv64.logW_z, c->mv64.logW_x}
-                                 : std::array<int, 3>{c->mv32.logW_y, c->mv32.logW_z, c->mv32.logW_x};
+        return dtype == DDA_C128
+                   ? std::array<int, 4>{c->mv64.logW_y, c->mv64.logW_z, c->mv64.logW_x, c->mv64.p3_sched}
+                   : std::array<int, 4>{c->mv32.logW_y, c->mv32.logW_z, c->mv32.logW_x, c->mv32.p3_sched};
     };
-    auto set = [&](const std::array<int, 3>& t) {
+    auto set = [&](const std::array<int, 4>& t) {
         if (dtype == DDA_C128) apply_tiles(c->mv64, t);
         else apply_tiles(c->mv32, t);
     };
-    auto valid = [&](const std::array<int, 3>& t) {
-        return dtype == DDA_C128 ? tiles_ok<double>(c->g, t[0], t[1], t[2]) : tiles_ok<float>(c->g, t[0], t[1], t[2]);
+    auto valid = [&](const std::array<int, 4>& t) {
+        return dtype == DDA_C128 ? tiles_ok<double>(c->g, t[0], t[1], t[2], t[3])
+                                 : tiles_ok<float>(c->g, t[0], t[1], t[2], t[3]);
     };
     // one warm product, then reps timed ones; per-pass average milliseconds
     auto time_tiles = [&](double (&out)[5]) -> int {
@@ -745,19 +754,21 @@ int dda_autotune(dda_ctx* c, int dtype, int nb, int reps, double* pass_ms, void*
     int rc = e == cudaSuccess ? 0 : cuda_fail(e, "dda_autotune: fill");
     double best_ms[5] = {};
     if (!rc) rc = time_tiles(best_ms);
-    // one coordinate at a time: P3's width (index 1), then P1/P5's (0), then P2/P4's (2)
-    const int order[3] = {1, 0, 2};
-    for (int oi = 0; oi < 3 && !rc; ++oi) {
+    // one coordinate at a time: P3's width (index 1), P3's schedule (3),
+    // P1/P5's width (0), then P2/P4's (2)
+    const int order[4] = {1, 3, 0, 2};
+    for (int oi = 0; oi < 4 && !rc; ++oi) {
         const int a = order[oi];
-        std::array<int, 3> best = current();
+        std::array<int, 4> best = current();
         auto cost = [&](const double (&m)[5]) {
-            return a == 1 ? m[2] : a == 0 ? m[0] + m[4] : m[1] + m[3];
+            return (a == 1 || a == 3) ? m[2] : a == 0 ? m[0] + m[4] : m[1] + m[3];
         };
         double best_cost = cost(best_ms);
         const int center = best[a];
-        for (int v = std::max(0, center - 2); v <= center + 2 && !rc; ++v) {
+        const int lo = a == 3 ? 0 : std::max(0, center - 2), hi = a == 3 ? 1 : center + 2;
+        for (int v = lo; v <= hi && !rc; ++v) {
             if (v == center) continue;
-            std::array<int, 3> t = best;
+            std::array<int, 4> t = best;
             t[a] = v;
             if (!valid(t)) continue;
             set(t);

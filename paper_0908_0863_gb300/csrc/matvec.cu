@@ -6,7 +6,9 @@
 namespace dda {
 
 template <typename T>
-bool tiles_ok(const Geometry& g, int logW_y, int logW_z, int logW_x) {
+bool tiles_ok(const Geometry& g, int logW_y, int logW_z, int logW_x, int p3_sched) {
+    if (p3_sched != 0 && p3_sched != 1) return false;
+    if (p3_sched == 1 && (logW_z < 0 || logW_z > kMaxLogW || !p3_persistent_ok<T>(g, logW_z))) return false;
     const int elt = sizeof(C<T>);
     const int ty = threads_log(g.Ly), tz = threads_log(g.Lz), tx = threads_log(g.Lx);
     if (logW_y < 0 || logW_z < 0 || logW_x < 0) return false;
@@ -70,8 +72,8 @@ int launch_matvec(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t 
 
 template void configure_matvec<double>(MatvecView<double>&);
 template void configure_matvec<float>(MatvecView<float>&);
-template bool tiles_ok<double>(const Geometry&, int, int, int);
-template bool tiles_ok<float>(const Geometry&, int, int, int);
+template bool tiles_ok<double>(const Geometry&, int, int, int, int);
+template bool tiles_ok<float>(const Geometry&, int, int, int, int);
 template int launch_matvec<double>(const MatvecView<double>&, const C<double>*, C<double>*, cudaStream_t);
 template int launch_matvec<float>(const MatvecView<float>&, const C<float>*, C<float>*, cudaStream_t);
 

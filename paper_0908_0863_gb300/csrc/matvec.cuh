@@ -18,6 +18,7 @@ struct MatvecView {
     C<T>* Ay;           // [slots][3][P][Ly][K]
     C<T>* Bxy;          // [slots][3][P][Ly][Lx]
     int logW_y, logW_x, logW_z;  // tile widths (lines per CTA) of the passes
+    int p3_sched = 0;   // z pass: 0 = one CTA per tile, 1 = persistent CTAs with staged inputs
     const int* status;  // optional: right-hand side b is skipped while
                         // status[b * status_stride] != 0
     int status_stride;  // ints between the status words of consecutive RHS
@@ -44,7 +45,7 @@ __device__ __forceinline__ bool rhs_done(const MatvecView<T>& mv, int b) {
 template <typename T> void configure_matvec(MatvecView<T>& mv);
 // whether tile widths (log2 of lines per CTA of P1/P5, P3 and P2/P4) fit the
 // launch limits (threads per block, shared memory) for this geometry
-template <typename T> bool tiles_ok(const Geometry& g, int logW_y, int logW_z, int logW_x);
+template <typename T> bool tiles_ok(const Geometry& g, int logW_y, int logW_z, int logW_x, int p3_sched = 0);
 template <typename T> int launch_matvec(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t st);
 
 }  // namespace dda

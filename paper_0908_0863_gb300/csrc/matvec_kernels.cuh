@@ -41,6 +41,7 @@
 // shared-memory addresses are compile-time offsets.
 #pragma once
 
+#include <algorithm>
 #include <atomic>
 
 #include "fft_reg.cuh"
@@ -182,20 +183,24 @@ __device__ __forceinline__ void load6(const C<T>* __restrict__ p, C<T> (&Y)[6]) 
     }
 }
 
+// row jy of the b-th tile row: rows jy and Ly - jy read the same spectrum
+// rows (mirror lookup), so they are visited back to back (0, 1, Ly-1, 2,
+// Ly-2, ...) and the second read hits L2
+__device__ __forceinline__ int p3_row(int b, int Ly) {
+    const int q2 = (b + 1) >> 1;
+    return b == 0 ? 0 : ((b & 1) ? q2 : Ly - q2);
+}
+
+// One tile of W columns (x = xt W + w, row jy, batch slot j) whose inputs v
+// (the P nonzero z points of the three components, canonical order) are
+// loaded: forward z DFTs, the spectrum product of Eqs. 6-8 with the signed
+// mirror lookup of Sec. 3, inverse z DFTs, and the store of k < P.
 template <typename T, int LOGN, int LOGW>
-__global__ void __launch_bounds__(p3_max_threads<T>(), 1) k_p3(MatvecView<T> mv) {
-    const int j = blockIdx.x, xt = blockIdx.y;                  // batch slot, column tile
-    if (rhs_done(mv, mv.b0 + j)) return;
-    extern __shared__ unsigned char smem_raw[];
-    C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
+__device__ __forceinline__ void p3_tile(const MatvecView<T>& mv, C<T>* sm, int j, int xt, int jy, C<T> (&v)[3][8]) {
     constexpr int N = 1 << LOGN, logT = lines_log(LOGN), nv = points(LOGN);
     const Geometry& g = mv.g;
     constexpr int logW = LOGW, W = 1 << LOGW;
     const int w = threadIdx.x & (W - 1), t = threadIdx.x >> logW;
-    // rows jy and Ly - jy read the same spectrum rows (mirror lookup): visit
-    // them back to back (0, 1, Ly-1, 2, Ly-2, ...) so the second read hits L2
-    const int b = blockIdx.z, q2 = (b + 1) >> 1;
-    const int jy = b == 0 ? 0 : ((b & 1) ? q2 : g.Ly - q2);
     const int ix = xt * W + w;
     const bool ok = ix < g.Lx;
     const ColLayoutT<LOGW> L{};
@@ -203,16 +208,7 @@ __global__ void __launch_bounds__(p3_max_threads<T>(), 1) k_p3(MatvecView<T> mv)
     const int64_t plane = (int64_t)g.Ly * g.Lx;   // stride between z planes of Bxy
     const int64_t comp = (int64_t)g.P * plane;    // stride between components
     C<T>* col = mv.Bxy + j * bxy_elems(g) + (int64_t)jy * g.Lx + (ok ? ix : 0);
-    C<T> v[3][8];
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int m = 0; m < 8; ++m) {
-            const int n = t + (m << logT);
-            v[c][m] = (ok && m < nv && n < g.P) ? col[c * comp + n * plane] : mk<T>(0, 0);
-        }
     fft_lines<T, false, LOGN, 3, true, false>(v, sm, region, L, w, t, mv.tw);
-    // spectrum product (Eqs. 6-8) with the signed mirror lookup of Sec. 3
     {
         const int my = jy <= g.Ly / 2 ? jy : g.Ly - jy, fy = jy > g.Ly / 2;
         const int mx = ix <= g.Lx / 2 ? ix : g.Lx - ix, fx = ix > g.Lx / 2;
@@ -247,6 +243,99 @@ __global__ void __launch_bounds__(p3_max_threads<T>(), 1) k_p3(MatvecView<T> mv)
                 const int n = t + (m << logT);
                 if (n < g.P) col[c * comp + n * plane] = v[c][m];
             }
+    }
+}
+
+// one CTA per tile, inputs loaded from global memory
+template <typename T, int LOGN, int LOGW>
+__global__ void __launch_bounds__(p3_max_threads<T>(), 1) k_p3(MatvecView<T> mv) {
+    const int j = blockIdx.x, xt = blockIdx.y;                  // batch slot, column tile
+    if (rhs_done(mv, mv.b0 + j)) return;
+    extern __shared__ unsigned char smem_raw[];
+    C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
+    constexpr int logT = lines_log(LOGN), nv = points(LOGN);
+    const Geometry& g = mv.g;
+    constexpr int W = 1 << LOGW;
+    const int w = threadIdx.x & (W - 1), t = threadIdx.x >> LOGW;
+    const int jy = p3_row(blockIdx.z, g.Ly);
+    const int ix = xt * W + w;
+    const bool ok = ix < g.Lx;
+    const int64_t plane = (int64_t)g.Ly * g.Lx, comp = (int64_t)g.P * plane;
+    const C<T>* col = mv.Bxy + j * bxy_elems(g) + (int64_t)jy * g.Lx + (ok ? ix : 0);
+    C<T> v[3][8];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const int n = t + (m << logT);
+            v[c][m] = (ok && m < nv && n < g.P) ? col[c * comp + n * plane] : mk<T>(0, 0);
+        }
+    p3_tile<T, LOGN, LOGW>(mv, sm, j, xt, jy, v);
+}
+
+// Persistent schedule: each CTA walks the tiles q = blockIdx.x, + gridDim.x,
+// ... in the order of the per-tile grid (batch slot fastest, then column
+// tile, then row), and while it transforms tile q the next one's input
+// columns are already on their way into a shared-memory stage with cp.async
+// (16-byte copies, no registers held), so the column loads of a tile no
+// longer stall the SM.  Tiles must be whole (W <= Lx) and a stage row must
+// be whole 16-byte copies (W * sizeof(C<T>) a multiple of 16).
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <typename T, int LOGN, int LOGW>
+__global__ void __launch_bounds__(p3_max_threads<T>(), 1) k_p3p(MatvecView<T> mv, int stage_off) {
+    extern __shared__ unsigned char smem_raw[];
+    C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
+    C<T>* stage = sm + stage_off;                                  // [3][P][W]
+    constexpr int logT = lines_log(LOGN), nv = points(LOGN);
+    const Geometry& g = mv.g;
+    constexpr int W = 1 << LOGW;
+    constexpr int per16 = 16 / (int)sizeof(C<T>), chunks = W / per16;   // 16-byte copies per stage row
+    if constexpr (chunks == 0) {
+        return;   // never launched: the host only picks this schedule for whole 16-byte stage rows
+    } else {
+    const int w = threadIdx.x & (W - 1), t = threadIdx.x >> LOGW;
+    const int ntx = g.Lx / W;
+    const int ntiles = mv.nb * ntx * g.Ly;
+    const int64_t plane = (int64_t)g.Ly * g.Lx, comp = (int64_t)g.P * plane;
+    const int rows = 3 * g.P;
+    auto issue = [&](int q) {
+        const int j = q % mv.nb, xt = (q / mv.nb) % ntx, jy = p3_row(q / (mv.nb * ntx), g.Ly);
+        if (rhs_done(mv, mv.b0 + j)) return;
+        const C<T>* base = mv.Bxy + j * bxy_elems(g) + (int64_t)jy * g.Lx + xt * W;
+        for (int e = threadIdx.x; e < rows * chunks; e += blockDim.x) {
+            const int row = e / chunks, ch = e - row * chunks;
+            const int c = row / g.P, n = row - c * g.P;
+            cp_async16(stage + row * W + ch * per16, base + c * comp + (int64_t)n * plane + ch * per16);
+        }
+    };
+    int q = blockIdx.x;
+    if (q < ntiles) issue(q);
+    cp_async_commit();
+    for (; q < ntiles; q += gridDim.x) {
+        const int j = q % mv.nb, xt = (q / mv.nb) % ntx, jy = p3_row(q / (mv.nb * ntx), g.Ly);
+        const bool skip = rhs_done(mv, mv.b0 + j);             // the same for the whole CTA
+        cp_async_wait_all();
+        __syncthreads();
+        C<T> v[3][8];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int n = t + (m << logT);
+                v[c][m] = (!skip && m < nv && n < g.P) ? stage[(c * g.P + n) * W + w] : mk<T>(0, 0);
+            }
+        __syncthreads();                                         // the stage is free again
+        if (q + (int)gridDim.x < ntiles) issue(q + gridDim.x);
+        cp_async_commit();
+        if (!skip) p3_tile<T, LOGN, LOGW>(mv, sm, j, xt, jy, v);
+    }
+    cp_async_wait_all();
     }
 }
 
@@ -361,15 +450,57 @@ int launch_rows(const MatvecView<T>& mv, cudaStream_t st) {
     return 0;
 }
 
+// the persistent z pass applies: whole tiles, whole 16-byte stage copies,
+// stage and exchange buffers within the shared-memory budget
+template <typename T>
+inline bool p3_persistent_ok(const Geometry& g, int logW) {
+    const int W = 1 << logW;
+    if (W > g.Lx || (W * (int)sizeof(C<T>)) % 16) return false;
+    const size_t stage_off = (3 * (size_t)col_elems(g.Lz, W) + 1) & ~size_t(1);
+    return (stage_off + 3ull * g.P * W) * sizeof(C<T>) <= 220 * 1024;
+}
+
+inline int sm_count() {
+    static std::atomic<int> n{0};
+    int v = n.load(std::memory_order_relaxed);
+    if (!v) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) v = 1;
+        n.store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
+
 template <typename T, int LOGN, int LOGW>
 int launch_p3(const MatvecView<T>& mv, cudaStream_t st) {
     const Geometry& g = mv.g;
     constexpr int W = 1 << LOGW;
+    const int threads = W << lines_log(LOGN);
+    if (mv.p3_sched == 1 && p3_persistent_ok<T>(g, LOGW)) {
+        const int stage_off = (int)((3 * (size_t)col_elems(1 << LOGN, W) + 1) & ~size_t(1));
+        const size_t sm = ((size_t)stage_off + 3ull * g.P * W) * sizeof(C<T>);
+        static std::atomic<size_t> smem_set{0};
+        if (int rc = set_smem((const void*)k_p3p<T, LOGN, LOGW>, sm, smem_set)) return rc;
+        static std::atomic<int> per_sm{0};
+        int bps = per_sm.load(std::memory_order_relaxed);
+        if (!bps) {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_p3p<T, LOGN, LOGW>, threads, sm) != cudaSuccess ||
+                bps < 1)
+                bps = 1;
+            per_sm.store(bps, std::memory_order_relaxed);
+        }
+        const int64_t ntiles = (int64_t)mv.nb * (g.Lx / W) * g.Ly;
+        const int grid = (int)std::min<int64_t>(ntiles, (int64_t)sm_count() * bps);
+        k_p3p<T, LOGN, LOGW><<<grid, threads, sm, st>>>(mv, stage_off);
+        DDA_LAUNCH_CHECK("P3 z-forward, spectrum product, z-inverse (persistent)");
+        return 0;
+    }
     const size_t sm = 3 * (size_t)col_elems(1 << LOGN, W) * sizeof(C<T>);
     static std::atomic<size_t> smem_set{0};
     if (int rc = set_smem((const void*)k_p3<T, LOGN, LOGW>, sm, smem_set)) return rc;
     dim3 grid(mv.nb, (g.Lx + W - 1) / W, g.Ly);
-    k_p3<T, LOGN, LOGW><<<grid, W << lines_log(LOGN), sm, st>>>(mv);
+    k_p3<T, LOGN, LOGW><<<grid, threads, sm, st>>>(mv);
     DDA_LAUNCH_CHECK("P3 z-forward, spectrum product, z-inverse");
     return 0;
 }

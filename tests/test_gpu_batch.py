@@ -287,10 +287,12 @@ def test_tile_widths_do_not_change_results(dda, dtype):
     p = torch.from_numpy(synth.complex_normal(42, (2, 3, case.nd))).to(DEV).to(tdt)
     with case.lattice() as lat:
         base = lat.tiles(dtype)
+        assert len(base) == 4 and base[3] == 0
         y0 = torch.empty_like(p)
         lat.matvec_batch(p, y0)
         tried = 0
-        for d in ((-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1), (1, 1, 1)):
+        for d in ((-1, 0, 0, 0), (1, 0, 0, 0), (0, -1, 0, 0), (0, 1, 0, 0), (0, 0, -1, 0), (0, 0, 1, 0),
+                  (1, 1, 1, 0), (0, 0, 0, 1), (0, -1, 0, 1)):
             t = tuple(b + e for b, e in zip(base, d))
             try:
                 lat.tiles(dtype, t)
@@ -302,8 +304,30 @@ def test_tile_widths_do_not_change_results(dda, dtype):
             lat.matvec_batch(p, y1)
             assert torch.equal(y0, y1), t
             tried += 1
-        assert tried >= 4
+        assert tried >= 5
         lat.tiles(dtype, base)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_persistent_z_pass_in_batched_solves(dda, dtype):
+    # the staged persistent z pass gives the same bits as the per-tile grid,
+    # also while right-hand sides drop out of a batched solve one by one
+    case = Case(synth.sphere(24), [1.33 + 0.05j], 0.5 / abs(1.33 + 0.05j))
+    pairs = _pairs(20260071, 3)
+    precision = "fp64" if dtype == "c128" else "mixed"
+    out = []
+    with case.lattice() as lat:
+        E = _einc(lat, case.nd, pairs)
+        base = lat.tiles(dtype)
+        for sched in (0, 1):
+            lat.tiles(dtype, (base[0], base[1], base[2], sched))
+            P = torch.zeros_like(E)
+            status, stats, infos = lat.solve_batch(E, P, "bicgstab", precision, tol=1e-9, max_iter=2000)
+            assert status == dda.DDA_OK, stats
+            out.append((P.clone(), [i["iterations"] for i in infos]))
+        lat.tiles(dtype, base)
+    assert torch.equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
 
 
 def test_tile_limits_rejected(dda):
@@ -311,7 +335,7 @@ def test_tile_limits_rejected(dda):
     with case.lattice() as lat:
         base = lat.tiles("c64")
         with pytest.raises(dda.DDAError) as e:
-            lat.tiles("c64", (base[0], 12, base[2]))     # 4096 columns x 4 threads per CTA
+            lat.tiles("c64", (base[0], 12, base[2], 0))     # 4096 columns x 4 threads per CTA
         assert e.value.code == dda.DDA_ERR_ARG
         assert lat.tiles("c64") == base
 
