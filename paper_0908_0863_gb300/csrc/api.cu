@@ -482,8 +482,8 @@ int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occu
         probe.take<float2>(3 * (size_t)n_materials);
         probe.take<double2>(nspec);
         probe.take<float2>(nspec);
-        probe.take<double2>(kMaxLine);
-        probe.take<float2>(kMaxLine);
+        probe.take<double2>(kTwEntries);
+        probe.take<float2>(kTwEntries);
         probe.take<double2>(xsec_scratch_elems());
         probe.take<int>(4);
         a0.cap = probe.used + 256;
@@ -502,8 +502,8 @@ int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occu
     c->jac32 = a0.take<float2>(3 * (size_t)n_materials);
     c->spec64 = a0.take<double2>(nspec);
     c->spec32 = a0.take<float2>(nspec);
-    c->tw64 = a0.take<double2>(kMaxLine);
-    c->tw32 = a0.take<float2>(kMaxLine);
+    c->tw64 = a0.take<double2>(kTwEntries);
+    c->tw32 = a0.take<float2>(kTwEntries);
     c->xsec = a0.take<double2>(xsec_scratch_elems());
     int* flags = a0.take<int>(4);
     c->bytes_fixed = (int64_t)a0.cap;
@@ -540,10 +540,10 @@ int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occu
             sj[i] = make_double2(sc.real(), sc.imag());
             sf[i] = make_float2((float)sc.real(), (float)sc.imag());
         }
-        std::vector<double2> t64(kMaxLine);
-        std::vector<float2> t32(kMaxLine);
-        for (int m = 0; m < kMaxLine; ++m) {
-            const double ang = -2.0 * M_PI * (double)m / kMaxLine;
+        std::vector<double2> t64(kTwEntries);
+        std::vector<float2> t32(kTwEntries);
+        for (int m = 0; m < kTwEntries; ++m) {
+            const double ang = -2.0 * M_PI * (double)m / kTwEntries;
             t64[m] = make_double2(std::cos(ang), std::sin(ang));
             t32[m] = make_float2((float)t64[m].x, (float)t64[m].y);
         }
@@ -551,8 +551,8 @@ int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occu
             cudaMemcpyAsync(c->ainv32, af.data(), af.size() * sizeof(float2), cudaMemcpyHostToDevice, st) ||
             cudaMemcpyAsync(c->jac64, sj.data(), sj.size() * sizeof(double2), cudaMemcpyHostToDevice, st) ||
             cudaMemcpyAsync(c->jac32, sf.data(), sf.size() * sizeof(float2), cudaMemcpyHostToDevice, st) ||
-            cudaMemcpyAsync(c->tw64, t64.data(), kMaxLine * sizeof(double2), cudaMemcpyHostToDevice, st) ||
-            cudaMemcpyAsync(c->tw32, t32.data(), kMaxLine * sizeof(float2), cudaMemcpyHostToDevice, st) ||
+            cudaMemcpyAsync(c->tw64, t64.data(), kTwEntries * sizeof(double2), cudaMemcpyHostToDevice, st) ||
+            cudaMemcpyAsync(c->tw32, t32.data(), kTwEntries * sizeof(float2), cudaMemcpyHostToDevice, st) ||
             cudaStreamSynchronize(st))
             return bail(fail(DDA_ERR_CUDA, "dda_init_lattice: table upload"));
     }

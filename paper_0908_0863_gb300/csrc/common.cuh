@@ -34,6 +34,7 @@ template <typename T> __host__ __device__ __forceinline__ C<T> cfma(C<T> a, C<T>
 
 // --------------------------------------------------------------- limits
 constexpr int kMaxLine = 1024;      // longest padded line (lattice edge <= 512)
+constexpr int kTwEntries = 3072;    // twiddle table: exp(-2 pi i m / 3072), lines of 2^a and 3 * 2^a points
 constexpr int kMaxEdge = 512;
 
 // ------------------------------------------------------- error reporting
@@ -72,10 +73,15 @@ struct Geometry {
     int cfields;          // fields per word
 };
 
+// circulant length of an n-point Toeplitz level: the smallest L >= 2n - 1
+// (and >= 2) of the form 2^a or 3 * 2^a with a >= 3 (Sec. 3: K'' = 2K - 1 + kf
+// with kf chosen for a fast DFT)
 inline int padded_length(int n) {
-    int L = 2;
-    while (L < 2 * n - 1) L *= 2;
-    return L;
+    const int need = 2 * n - 1 > 2 ? 2 * n - 1 : 2;
+    int L = 2, t = 24;
+    while (L < need) L *= 2;
+    while (t < need) t *= 2;
+    return t < L ? t : L;
 }
 inline int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
 

@@ -1,4 +1,5 @@
-// Batched power-of-two line DFTs on a shared-memory tile (sm_103a).
+// Batched line DFTs on a shared-memory tile (sm_103a), for lines of 2^a or
+// 3 * 2^a points.
 //
 // The 3D DFTs of the DDA matvec are done as ensembles of 1D line transforms
 // (OpenDDA Sec. 3).  Here a CTA holds W lines of N points in shared memory,
@@ -13,9 +14,10 @@
 // the launch uses exactly W*N/V threads.  A stage reads everything into
 // registers, synchronises, then writes, so one buffer suffices.
 //
-// Twiddles come from a table tw[m] = exp(-2 pi i m / kMaxLine) computed in
-// FP64 on the host (rounded once for the FP32 table); the inverse transform
-// uses their conjugates.  Transforms are unnormalised.
+// Twiddles come from a table tw[m] = exp(-2 pi i m / 3072) computed in FP64
+// on the host (rounded once for the FP32 table); the inverse transform uses
+// their conjugates.  Lines of N = 3 * 2^a points end with a radix-3 stage.
+// Transforms are unnormalised.
 #pragma once
 
 #include "common.cuh"
@@ -108,10 +110,10 @@ __device__ __forceinline__ void fft_stage(C<T>* __restrict__ buf, int ld, int lo
         const int j = g >> logW;
         const int k = j & (Ns - 1);
         if (logNs > 0) {
-            // twiddle exp(-+ 2 pi i r k / (Ns R)) = tw[r k * kMaxLine / (Ns R)]
+            // twiddle exp(-+ 2 pi i r k / (Ns R)) = tw[3 r k * 1024 / (Ns R)]
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                C<T> t = __ldg(tw + ((r * k) << logTwStep));
+                C<T> t = __ldg(tw + ((3 * r * k) << logTwStep));
                 if (INV) t.y = -t.y;
                 v[q][r] = cmul<T>(v[q][r], t);
             }
@@ -124,15 +126,43 @@ __device__ __forceinline__ void fft_stage(C<T>* __restrict__ buf, int ld, int lo
     __syncthreads();
 }
 
-// In-place DFT of the W = 2^logW lines (length N = 2^logN) of a tile.
-// tw: table of kMaxLine entries.  Requires blockDim.x * V == W * N.
+// The closing radix-3 stage of an N = 3M line (Ns = M): butterfly j < M
+// twiddles x[j + M r] by exp(-+ 2 pi i j r / N) = tw[3072 j r / N] and
+// transforms the three points in place.  W M butterflies over the CTA.
+template <typename T, bool INV>
+__device__ __forceinline__ void fft_stage3(C<T>* __restrict__ buf, int ld, int logW, int N,
+                                           const C<T>* __restrict__ tw) {
+    const int M = N / 3, W = 1 << logW, step = 3072 / N;
+    const T h = (T)0.86602540378443864676;   // sqrt(3) / 2
+    for (int g = threadIdx.x; g < W * M; g += blockDim.x) {
+        const int w = g & (W - 1), j = g >> logW;
+        C<T> t1 = __ldg(tw + j * step), t2 = __ldg(tw + 2 * j * step);
+        if (INV) { t1.y = -t1.y; t2.y = -t2.y; }
+        const C<T> a = buf[j * ld + w];
+        const C<T> b = cmul<T>(buf[(j + M) * ld + w], t1), c = cmul<T>(buf[(j + 2 * M) * ld + w], t2);
+        const C<T> s = cadd<T>(b, c), d = csub<T>(b, c);
+        const C<T> m = mk<T>(a.x - (T)0.5 * s.x, a.y - (T)0.5 * s.y);
+        const C<T> r = cscale<T>(rot90<T, INV>(d), h);
+        buf[j * ld + w] = cadd<T>(a, s);
+        buf[(j + M) * ld + w] = cadd<T>(m, r);
+        buf[(j + 2 * M) * ld + w] = csub<T>(m, r);
+    }
+    __syncthreads();
+}
+
+// In-place DFT of the W = 2^logW lines of N points (N = 2^a, or 3 * 2^a with
+// a >= 3) of a tile: the Stockham stages of the power-of-two factor, then
+// the radix-3 stage.  tw: table of 3072 entries exp(-2 pi i m / 3072).
+// Requires blockDim.x * V == W * N.
 template <typename T, int V, bool INV>
-__device__ __forceinline__ void fft_tile(C<T>* __restrict__ buf, int ld, int logW, int logN,
+__device__ __forceinline__ void fft_tile(C<T>* __restrict__ buf, int ld, int logW, int N,
                                          const C<T>* __restrict__ tw) {
-    const int N = 1 << logN;
-    const int logMax = 10;  // log2(kMaxLine)
+    const int M = (N % 3) ? N : N / 3;
+    int logM = 0;
+    while ((1 << logM) < M) ++logM;
+    const int logMax = 10;  // log2 of the longest power-of-two line
     int logNs = 0;
-    const int first = logN % 3;
+    const int first = logM % 3;
     if (first == 1) {
         fft_stage<T, V, 2, INV>(buf, ld, logW, N, 0, tw, logMax - 1);
         logNs = 1;
@@ -140,10 +170,11 @@ __device__ __forceinline__ void fft_tile(C<T>* __restrict__ buf, int ld, int log
         fft_stage<T, V, 4, INV>(buf, ld, logW, N, 0, tw, logMax - 2);
         logNs = 2;
     }
-    while (logNs < logN) {
+    while (logNs < logM) {
         fft_stage<T, V, 8, INV>(buf, ld, logW, N, logNs, tw, logMax - logNs - 3);
         logNs += 3;
     }
+    if (M != N) fft_stage3<T, INV>(buf, ld, logW, N, tw);
 }
 
 }  // namespace dda

@@ -1,17 +1,23 @@
-// Register-resident power-of-two line DFTs for the matvec passes (sm_103a).
+// Register-resident line DFTs for the matvec passes (sm_103a), for lines of
+// N = 2^a or N = 3 * 2^a (a >= 3) points.
 //
-// Each line of N = 2^LOGN points is owned by T = N/8 threads; thread t
-// holds the eight "canonical" points t + T m (m = 0..7) in registers.  The
-// Stockham autosort stages (radix 8, one radix 2 or 4 first when LOGN is
-// not a multiple of 3) all read exactly these canonical points, so the
-// first stage takes its inputs straight from global memory, every stage
-// runs its butterflies in registers, and only the data exchange between two
-// stages goes through shared memory (write at the Stockham output
-// positions, read back the canonical points).  The last radix-8 stage writes
-// its outputs to the canonical positions themselves, so the transform ends
-// in registers in natural order: N = 512 costs two shared-memory exchanges.
-// The length is a template parameter, so every stride, stage count and
-// twiddle step is a compile-time constant.
+// Each line of N >= 8 points is owned by T = N/8 threads; thread t holds
+// the eight "canonical" points t + T m (m = 0..7) in registers.  The
+// Stockham autosort stages of the power-of-two factor M (radix 8, one radix
+// 2 or 4 first when log2 M is not a multiple of 3) all read exactly these
+// canonical points (a radix-8 stage reads stride N/8 = T whatever N's other
+// factor), so the first stage takes its inputs straight from global memory,
+// every stage runs its butterflies in registers, and only the data exchange
+// between two stages goes through shared memory (write at the Stockham
+// output positions, read back the canonical points).  For N = 2^a the last
+// radix-8 stage writes its outputs to the canonical positions themselves, so
+// the transform ends in registers in natural order: N = 512 costs two
+// shared-memory exchanges.  For N = 3M the radix-3 stage comes last (Ns = M):
+// its butterfly j < M reads and writes the positions j, j + M, j + 2M, so it
+// runs in place in shared memory after the last radix-8 exchange, and one
+// more canonical read ends the transform.  The length is a template
+// parameter, so every stride, stage count and twiddle step is a
+// compile-time constant.
 //
 // A thread may carry NL lines at once (the three polarisation components of
 // a z column): they share the twiddles, the addresses and the barriers of
@@ -21,31 +27,43 @@
 // only the first half of each line nonzero (n < L/2 holds every input, since
 // L >= 2n - 1 for n lattice points), and its inverse transforms keep only the
 // first half of the outputs.  HALF_IN skips the work on the known zeros in
-// the first stage; HALF_OUT computes only outputs m < 4 in the last stage.
+// the first stage; HALF_OUT computes only outputs m < 4 in the last radix-8
+// stage of a power-of-two length (a radix-3 length computes all outputs).
 //
 // Shared-memory addresses come from a layout functor (line w, point p):
 // RowLayout keeps each line contiguous (lines of the lattice that are
 // contiguous in memory, threads t-fastest); ColLayout keeps point-major
 // tiles of 2^logW lines side by side (strided lines of the lattice, threads
-// w-fastest).  Their paddings make every exchange take the minimum number
-// of shared-memory wavefronts for 8- and 16-byte elements at the tile
-// shapes the passes use (checked by replaying each stage's access pattern
-// for N = 16..1024).
+// w-fastest).
 //
 // Lines shorter than 8 points (lattice edges of 1 or 2 sites) are done by
 // one thread each in registers.  Twiddles come from the FP64 table
-// tw[m] = exp(-2 pi i m / 1024) (rounded once for FP32), conjugated for the
-// inverse; FP32 stages load one twiddle and form the other six as its
-// powers.  Transforms are unnormalised.
+// tw[m] = exp(-2 pi i m / 3072) (rounded once for FP32), conjugated for the
+// inverse; FP32 radix-8 stages load one twiddle and form the other six as
+// its powers.  Transforms are unnormalised.
 #pragma once
 
 #include "fft.cuh"
 
 namespace dda {
 
-template <int LOGN>
+constexpr int kTwLen = 3072;   // twiddle table length: 3 * the longest power-of-two line
+
+__host__ __device__ constexpr int log2c(int n) { return n <= 1 ? 0 : 1 + log2c(n / 2); }
+
+// shape of the transform of one N-point line
+template <int N>
+struct Line {
+    static constexpr bool R3 = (N % 3) == 0;         // N = 3 M
+    static constexpr int M = R3 ? N / 3 : N;          // power-of-two factor
+    static constexpr int LOGM = log2c(M);
+    static constexpr int T = N >= 8 ? N / 8 : 1;      // threads per line
+    static constexpr int NV = N >= 8 ? 8 : N;         // points per thread
+    static_assert(!R3 || M >= 8, "3 * 2^a lengths need a >= 3");
+};
+
+template <int N>
 struct RowLayout {
-    static constexpr int N = 1 << LOGN;
     static constexpr int ld = N + N / 16 + 1;
     __device__ __forceinline__ int operator()(int w, int p) const { return w * ld + p + (p >> 4); }
 };
@@ -125,9 +143,11 @@ __device__ __forceinline__ void dft8_half_out(C<T>* v) {
 }
 
 // v[1..7] *= w^r with w = exp(-+ 2 pi i k / (8 Ns)) for each of NL lines
+// (table index 3 k 1024 / (8 Ns))
 template <typename T, bool INV, int LOGNS, int NL>
 __device__ __forceinline__ void twiddle8(C<T> (&v)[NL][8], int k, const C<T>* __restrict__ tw) {
     constexpr int step = 10 - LOGNS - 3;
+    k *= 3;
     C<T> w[8];
     if (sizeof(T) == 4) {
         // FP32: one table load, the other six twiddles as its powers
@@ -146,10 +166,10 @@ __device__ __forceinline__ void twiddle8(C<T> (&v)[NL][8], int k, const C<T>* __
 }
 
 // read back the canonical points after an exchange
-template <typename T, int LOGN, int NL, class Layout>
+template <typename T, int N, int NL, class Layout>
 __device__ __forceinline__ void read_canonical(C<T> (&v)[NL][8], const C<T>* __restrict__ sm, int region,
                                                const Layout& L, int w, int t) {
-    constexpr int Tn = 1 << (LOGN - 3);
+    constexpr int Tn = N / 8;
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
         const int o = L(w, t + m * Tn);
@@ -158,16 +178,61 @@ __device__ __forceinline__ void read_canonical(C<T> (&v)[NL][8], const C<T>* __r
     }
 }
 
-// radix-8 stages from Ns = 2^LOGNS on; the last one leaves the outputs on
-// the canonical points
-template <typename T, bool INV, int LOGN, int LOGNS, int NL, bool HALF_OUT, class Layout>
+// radix-3 DFT of (a, b, c), forward (exp(-2 pi i / 3)) or inverse
+template <typename T, bool INV>
+__device__ __forceinline__ void dft3(C<T>& a, C<T>& b, C<T>& c) {
+    const T h = (T)0.86602540378443864676;   // sqrt(3) / 2
+    const C<T> s = cadd<T>(b, c), d = csub<T>(b, c);
+    const C<T> m = mk<T>(a.x - (T)0.5 * s.x, a.y - (T)0.5 * s.y);
+    const C<T> r = cscale<T>(rot90<T, INV>(d), h);
+    a = cadd<T>(a, s);
+    b = cadd<T>(m, r);
+    c = csub<T>(m, r);
+}
+
+// After the last radix-8 stage of an N = 3M line has written its outputs to
+// the Stockham positions: the radix-3 stage (Ns = M) in place in shared
+// memory -- butterfly j < M twiddles x[j + M r] by exp(-+ 2 pi i j r / N) --
+// then the canonical read that ends the transform in registers.  Thread t
+// takes the butterflies j = t, t + T, t + 2T below M.
+template <typename T, bool INV, int N, int NL, class Layout>
+__device__ __forceinline__ void radix3_finish(C<T> (&v)[NL][8], C<T>* __restrict__ sm, int region,
+                                              const Layout& L, int w, int t, const C<T>* __restrict__ tw) {
+    constexpr int M = N / 3, Tn = N / 8, step = kTwLen / N;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int j = t + q * Tn;
+        if (j < M) {
+            const C<T> w1 = twiddle<T, INV>(tw, j * step), w2 = twiddle<T, INV>(tw, 2 * j * step);
+            const int o0 = L(w, j), o1 = L(w, j + M), o2 = L(w, j + 2 * M);
+#pragma unroll
+            for (int l = 0; l < NL; ++l) {
+                C<T>* S = sm + l * region;
+                C<T> a = S[o0], b = cmul<T>(S[o1], w1), c = cmul<T>(S[o2], w2);
+                dft3<T, INV>(a, b, c);
+                S[o0] = a;
+                S[o1] = b;
+                S[o2] = c;
+            }
+        }
+    }
+    __syncthreads();
+    read_canonical<T, N, NL>(v, sm, region, L, w, t);
+    __syncthreads();
+}
+
+// radix-8 stages from Ns = 2^LOGNS on.  The last one of a 2^a line leaves
+// the outputs on the canonical points; that of a 3 * 2^a line writes them
+// to shared memory for the radix-3 stage.
+template <typename T, bool INV, int N, int LOGNS, int NL, bool HALF_OUT, class Layout>
 struct Radix8Stages {
     __device__ __forceinline__ static void run(C<T> (&v)[NL][8], C<T>* __restrict__ sm, int region,
                                                const Layout& L, int w, int t, const C<T>* __restrict__ tw) {
-        constexpr int Ns = 1 << LOGNS;
+        constexpr int Ns = 1 << LOGNS, LOGM = Line<N>::LOGM;
         const int k = t & (Ns - 1);
         twiddle8<T, INV, LOGNS, NL>(v, k, tw);
-        if constexpr (LOGNS + 3 < LOGN) {
+        if constexpr (LOGNS + 3 < LOGM || Line<N>::R3) {
 #pragma unroll
             for (int l = 0; l < NL; ++l) dft8<T, INV>(v[l]);
             const int base = ((t >> LOGNS) << (LOGNS + 3)) + k;
@@ -177,10 +242,14 @@ struct Radix8Stages {
 #pragma unroll
                 for (int l = 0; l < NL; ++l) sm[l * region + o] = v[l][r];
             }
-            __syncthreads();
-            read_canonical<T, LOGN, NL>(v, sm, region, L, w, t);
-            __syncthreads();
-            Radix8Stages<T, INV, LOGN, LOGNS + 3, NL, HALF_OUT, Layout>::run(v, sm, region, L, w, t, tw);
+            if constexpr (LOGNS + 3 < LOGM) {
+                __syncthreads();
+                read_canonical<T, N, NL>(v, sm, region, L, w, t);
+                __syncthreads();
+                Radix8Stages<T, INV, N, LOGNS + 3, NL, HALF_OUT, Layout>::run(v, sm, region, L, w, t, tw);
+            } else {
+                radix3_finish<T, INV, N, NL>(v, sm, region, L, w, t, tw);
+            }
         } else {
 #pragma unroll
             for (int l = 0; l < NL; ++l) {
@@ -194,19 +263,20 @@ struct Radix8Stages {
 // In-place DFT of NL lines held as v[l][m] = x_l[t + T m].  All threads of
 // the CTA must call it together (it synchronises when it exchanges).
 // HALF_IN: inputs m >= 4 are zero.  HALF_OUT: only outputs m < 4 are needed.
-template <typename T, bool INV, int LOGN, int NL, bool HALF_IN, bool HALF_OUT, class Layout>
+template <typename T, bool INV, int N, int NL, bool HALF_IN, bool HALF_OUT, class Layout>
 __device__ __forceinline__ void fft_lines(C<T> (&v)[NL][8], C<T>* __restrict__ sm, int region, const Layout& L,
                                           int w, int t, const C<T>* __restrict__ tw) {
-    if constexpr (LOGN <= 3) {  // a single stage: one thread holds the whole line
+    if constexpr (N <= 8 && !Line<N>::R3) {  // a single stage: one thread holds the whole line
 #pragma unroll
         for (int l = 0; l < NL; ++l) {
-            if constexpr (LOGN == 1) dft2<T, INV>(v[l]);
-            else if constexpr (LOGN == 2) dft4<T, INV>(v[l]);
+            if constexpr (N == 2) dft2<T, INV>(v[l]);
+            else if constexpr (N == 4) dft4<T, INV>(v[l]);
             else dft8<T, INV>(v[l]);
         }
     } else {
-        constexpr int Tn = 1 << (LOGN - 3);
-        constexpr int first = LOGN % 3;
+        constexpr int Tn = N / 8, LOGM = Line<N>::LOGM;
+        constexpr int first = LOGM % 3;
+        constexpr int L1 = first == 0 ? 3 : first;   // log2 of the first radix
         // first stage (Ns = 1, no twiddles): outputs of butterfly j, point r
         // go to j R + r
 #pragma unroll
@@ -238,20 +308,24 @@ __device__ __forceinline__ void fft_lines(C<T> (&v)[NL][8], C<T>* __restrict__ s
                 for (int r = 0; r < 8; ++r) S[L(w, t * 8 + r)] = v[l][r];
             }
         }
-        __syncthreads();
-        read_canonical<T, LOGN, NL>(v, sm, region, L, w, t);
-        __syncthreads();
-        Radix8Stages<T, INV, LOGN, (first == 0 ? 3 : first), NL, HALF_OUT, Layout>::run(v, sm, region, L, w, t,
-                                                                                        tw);
+        if constexpr (L1 == LOGM) {
+            // the first stage was the only power-of-two stage (N = 3 * 8)
+            radix3_finish<T, INV, N, NL>(v, sm, region, L, w, t, tw);
+        } else {
+            __syncthreads();
+            read_canonical<T, N, NL>(v, sm, region, L, w, t);
+            __syncthreads();
+            Radix8Stages<T, INV, N, L1, NL, HALF_OUT, Layout>::run(v, sm, region, L, w, t, tw);
+        }
     }
 }
 
 // one line: v[m] = x[t + T m]
-template <typename T, bool INV, int LOGN, bool HALF_IN, bool HALF_OUT, class Layout>
+template <typename T, bool INV, int N, bool HALF_IN, bool HALF_OUT, class Layout>
 __device__ __forceinline__ void fft_regs(C<T> (&v)[8], C<T>* __restrict__ sm, const Layout& L, int w, int t,
                                          const C<T>* __restrict__ tw) {
     C<T>(&vv)[1][8] = *reinterpret_cast<C<T>(*)[1][8]>(&v);
-    fft_lines<T, INV, LOGN, 1, HALF_IN, HALF_OUT>(vv, sm, 0, L, w, t, tw);
+    fft_lines<T, INV, N, 1, HALF_IN, HALF_OUT>(vv, sm, 0, L, w, t, tw);
 }
 
 }  // namespace dda

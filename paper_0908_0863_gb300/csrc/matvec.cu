@@ -10,13 +10,13 @@ bool tiles_ok(const Geometry& g, int logW_y, int logW_z, int logW_x, int p3_sche
     if (p3_sched != 0 && p3_sched != 1) return false;
     if (p3_sched == 1 && (logW_z < 0 || logW_z > kMaxLogW || !p3_persistent_ok<T>(g, logW_z))) return false;
     const int elt = sizeof(C<T>);
-    const int ty = threads_log(g.Ly), tz = threads_log(g.Lz), tx = threads_log(g.Lx);
+    const int ty = threads_of(g.Ly), tz = threads_of(g.Lz), tx = threads_of(g.Lx);
     if (logW_y < 0 || logW_z < 0 || logW_x < 0) return false;
     if (logW_y > kMaxLogW || logW_z > kMaxLogW || logW_x > 10) return false;   // compiled widths
-    if ((1 << (logW_y + ty)) > kYThreads || (1ull << logW_y) * col_elems(g.Ly, 1) * elt > 200 * 1024) return false;
-    if ((1 << (logW_z + tz)) > p3_max_threads<T>() || 3ull * col_elems(g.Lz, 1 << logW_z) * elt > 220 * 1024)
+    if ((1 << logW_y) * ty > kYThreads || (1ull << logW_y) * col_elems(g.Ly, 1) * elt > 200 * 1024) return false;
+    if ((1 << logW_z) * tz > p3_max_threads<T>() || 3ull * col_elems(g.Lz, 1 << logW_z) * elt > 220 * 1024)
         return false;
-    if ((1 << (logW_x + tx)) > 512 || (1ull << logW_x) * row_ld(g.Lx) * elt > 200 * 1024) return false;
+    if ((1 << logW_x) * tx > 512 || (1ull << logW_x) * row_ld(g.Lx) * elt > 200 * 1024) return false;
     return true;
 }
 
@@ -24,17 +24,17 @@ template <typename T>
 void configure_matvec(MatvecView<T>& mv) {
     const Geometry& g = mv.g;
     const int elt = sizeof(C<T>);
-    const int ty = threads_log(g.Ly), tz = threads_log(g.Lz), tx = threads_log(g.Lx);
+    const int ty = threads_of(g.Ly), tz = threads_of(g.Lz), tx = threads_of(g.Lx);
     // strided passes: W adjacent columns (64-byte rows)
     int wy = floor_log2(64 / elt);
-    while (wy > 0 && (1 << (wy + ty)) > kYThreads) --wy;
+    while (wy > 0 && (1 << wy) * ty > kYThreads) --wy;
     while (wy > 0 && (1 << (wy - 1)) >= g.K) --wy;          // no wider than the lattice
     int wz = floor_log2(64 / elt);
-    while (wz > 0 && (1 << (wz + tz)) > p3_max_threads<T>()) --wz;
+    while (wz > 0 && (1 << wz) * tz > p3_max_threads<T>()) --wz;
     while (wz > 0 && 3ull * col_elems(g.Lz, 1 << wz) * elt > 200 * 1024) --wz;
     while (wz > 0 && (1 << (wz - 1)) >= g.Lx) --wz;
     int wx = 0;                                             // rows per CTA: about 128 threads
-    while ((1 << (wx + 1 + tx)) <= 128) ++wx;
+    while ((2 << wx) * tx <= 128) ++wx;
     mv.logW_y = wy;
     mv.logW_z = wz;
     mv.logW_x = wx;
@@ -69,6 +69,12 @@ int launch_matvec(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t 
     }
     return 0;
 }
+
+template <typename T> int pass3(const MatvecView<T>& mv, cudaStream_t st) {
+    DDA_LEN_SWITCH(mv.g.Lz, (p3_len<T, LN>(mv, st)))
+}
+template int pass3<double>(const MatvecView<double>&, cudaStream_t);
+template int pass3<float>(const MatvecView<float>&, cudaStream_t);
 
 template void configure_matvec<double>(MatvecView<double>&);
 template void configure_matvec<float>(MatvecView<float>&);

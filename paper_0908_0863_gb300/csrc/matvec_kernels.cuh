@@ -36,9 +36,9 @@
 // contiguous elements.  In P3 each thread carries the same column of all
 // three components, so the spectrum product happens in registers between
 // the forward and the inverse transforms.  Each kernel is compiled for every
-// power-of-two line length (LOGN = 1..10) and, for the strided passes, every
-// tile width (LOGW = 0..4 lines per CTA, log2), and picked at launch, so all
-// shared-memory addresses are compile-time offsets.
+// line length N (2^a up to 1024 and 3 * 2^a from 24 to 768) and, for the
+// strided passes, every tile width (LOGW = 0..4 lines per CTA, log2), and
+// picked at launch, so all shared-memory addresses are compile-time offsets.
 #pragma once
 
 #include <algorithm>
@@ -50,8 +50,6 @@
 namespace dda {
 
 
-__host__ __device__ constexpr int lines_log(int logN) { return logN > 3 ? logN - 3 : 0; }
-__host__ __device__ constexpr int points(int logN) { return logN < 3 ? (1 << logN) : 8; }
 // P3 keeps 3 x 8 complex values per thread: 512 threads fit the register
 // file for complex64, 256 for complex128
 template <typename T> __host__ __device__ constexpr int p3_max_threads() { return sizeof(T) == 4 ? 512 : 256; }
@@ -67,14 +65,14 @@ __host__ __device__ __forceinline__ int64_t ay_elems(const Geometry& g) { return
 __host__ __device__ __forceinline__ int64_t bxy_elems(const Geometry& g) { return 3LL * g.P * g.Ly * g.Lx; }
 
 // ---------------------------------------------------------------- P1
-template <typename T, int LOGN, int LOGW>
+template <typename T, int N, int LOGW>
 __global__ void __launch_bounds__(kYThreads) k_p1(MatvecView<T> mv, const C<T>* __restrict__ p) {
     const int c = blockIdx.z % 3, j = blockIdx.z / 3;      // component, batch slot
     const int b = mv.b0 + j;
     if (rhs_done(mv, b)) return;
     extern __shared__ unsigned char smem_raw[];
     C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
-    constexpr int logT = lines_log(LOGN), nv = points(LOGN);
+    constexpr int TL = Line<N>::T, nv = Line<N>::NV;
     const Geometry& g = mv.g;
     constexpr int logW = LOGW, W = 1 << LOGW;
     const int w = threadIdx.x & (W - 1), t = threadIdx.x >> logW;
@@ -87,7 +85,7 @@ __global__ void __launch_bounds__(kYThreads) k_p1(MatvecView<T> mv, const C<T>* 
     const bool inx = i < g.K;
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
-        const int n = t + (m << logT);
+        const int n = t + m * TL;
         const bool in = inx && m < nv && n < g.J;
         const int64_t q = (s0 + (int64_t)n * g.K) >> 5;
         word[m] = in ? __ldg(mv.tv.occ + q) : 0u;
@@ -96,7 +94,7 @@ __global__ void __launch_bounds__(kYThreads) k_p1(MatvecView<T> mv, const C<T>* 
     C<T> v[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
-        const int n = t + (m << logT);
+        const int n = t + m * TL;
         const uint32_t bit = (uint32_t)((s0 + (int64_t)n * g.K) & 31);
         v[m] = mk<T>(0, 0);
         if ((word[m] >> bit) & 1u) {
@@ -107,31 +105,31 @@ __global__ void __launch_bounds__(kYThreads) k_p1(MatvecView<T> mv, const C<T>* 
     if (mv.jac) {   // point-Jacobi: the product starts from S p
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
-            const int n = t + (m << logT);
+            const int n = t + m * TL;
             if (inx && m < nv && n < g.J)
                 v[m] = cmul<T>(v[m], mv.jac[material(mv.tv, s0 + (int64_t)n * g.K, c) * 3 + c]);
         }
     }
-    fft_regs<T, false, LOGN, true, false>(v, sm, ColLayoutT<LOGW>{}, w, t, mv.tw);
+    fft_regs<T, false, N, true, false>(v, sm, ColLayoutT<LOGW>{}, w, t, mv.tw);
     if (i < g.K) {
-        C<T>* out = mv.Ay + j * ay_elems(g) + ((int64_t)c * g.P + kz) * ((int64_t)g.K << LOGN) + i;
+        C<T>* out = mv.Ay + j * ay_elems(g) + ((int64_t)c * g.P + kz) * ((int64_t)g.K * N) + i;
 #pragma unroll
-        for (int m = 0; m < nv; ++m) out[(int64_t)(t + (m << logT)) * g.K] = v[m];
+        for (int m = 0; m < nv; ++m) out[(int64_t)(t + m * TL) * g.K] = v[m];
     }
 }
 
 // ------------------------------------------------------- P2 / P4 (rows)
 // Forward: rows of K inputs (Ay) -> Lx outputs (Bxy).  Inverse: rows of Lx
 // inputs (Bxy) -> first K outputs (Ay).  2^logW_x rows per CTA.
-template <typename T, bool INV, int LOGN>
+template <typename T, bool INV, int N>
 __global__ void __launch_bounds__(512) k_rows(MatvecView<T> mv) {
     const int j = blockIdx.y;                               // batch slot
     if (rhs_done(mv, mv.b0 + j)) return;
     extern __shared__ unsigned char smem_raw[];
     C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
-    constexpr int N = 1 << LOGN, logT = lines_log(LOGN), nv = points(LOGN);
+    constexpr int TL = Line<N>::T, nv = Line<N>::NV;
     const Geometry& g = mv.g;
-    const int t = threadIdx.x & ((1 << logT) - 1), wl = threadIdx.x >> logT;
+    const int t = threadIdx.x % TL, wl = threadIdx.x / TL;
     const int64_t nrows = 3LL * g.P * g.Ly;
     const int64_t row = ((int64_t)blockIdx.x << mv.logW_x) + wl;
     const bool ok = row < nrows;
@@ -141,14 +139,14 @@ __global__ void __launch_bounds__(512) k_rows(MatvecView<T> mv) {
     C<T> v[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
-        const int n = t + (m << logT);
+        const int n = t + m * TL;
         v[m] = (ok && m < nv && n < nin) ? src[n] : mk<T>(0, 0);
     }
-    fft_regs<T, INV, LOGN, !INV, INV>(v, sm, RowLayout<LOGN>{}, wl, t, mv.tw);
+    fft_regs<T, INV, N, !INV, INV>(v, sm, RowLayout<N>{}, wl, t, mv.tw);
     if (ok) {
 #pragma unroll
         for (int m = 0; m < nv; ++m) {
-            const int n = t + (m << logT);
+            const int n = t + m * TL;
             if (n < nout) dst[n] = v[m];
         }
     }
@@ -195,9 +193,9 @@ __device__ __forceinline__ int p3_row(int b, int Ly) {
 // (the P nonzero z points of the three components, canonical order) are
 // loaded: forward z DFTs, the spectrum product of Eqs. 6-8 with the signed
 // mirror lookup of Sec. 3, inverse z DFTs, and the store of k < P.
-template <typename T, int LOGN, int LOGW>
+template <typename T, int N, int LOGW>
 __device__ __forceinline__ void p3_tile(const MatvecView<T>& mv, C<T>* sm, int j, int xt, int jy, C<T> (&v)[3][8]) {
-    constexpr int N = 1 << LOGN, logT = lines_log(LOGN), nv = points(LOGN);
+    constexpr int TL = Line<N>::T, nv = Line<N>::NV;
     const Geometry& g = mv.g;
     constexpr int logW = LOGW, W = 1 << LOGW;
     const int w = threadIdx.x & (W - 1), t = threadIdx.x >> logW;
@@ -208,7 +206,7 @@ __device__ __forceinline__ void p3_tile(const MatvecView<T>& mv, C<T>* sm, int j
     const int64_t plane = (int64_t)g.Ly * g.Lx;   // stride between z planes of Bxy
     const int64_t comp = (int64_t)g.P * plane;    // stride between components
     C<T>* col = mv.Bxy + j * bxy_elems(g) + (int64_t)jy * g.Lx + (ok ? ix : 0);
-    fft_lines<T, false, LOGN, 3, true, false>(v, sm, region, L, w, t, mv.tw);
+    fft_lines<T, false, N, 3, true, false>(v, sm, region, L, w, t, mv.tw);
     {
         const int my = jy <= g.Ly / 2 ? jy : g.Ly - jy, fy = jy > g.Ly / 2;
         const int mx = ix <= g.Lx / 2 ? ix : g.Lx - ix, fx = ix > g.Lx / 2;
@@ -216,7 +214,7 @@ __device__ __forceinline__ void p3_tile(const MatvecView<T>& mv, C<T>* sm, int j
         const int64_t zstep = (int64_t)g.Hy * g.Hx * 6;
 #pragma unroll
         for (int m = 0; m < nv; ++m) {
-            const int n = t + (m << logT);
+            const int n = t + m * TL;
             const int mz = n <= N / 2 ? n : N - n, fz = n > N / 2;
             C<T> Y[6];
             if (ok) {
@@ -234,26 +232,26 @@ __device__ __forceinline__ void p3_tile(const MatvecView<T>& mv, C<T>* sm, int j
             v[2][m] = cfma<T>(Y[5], X2, cfma<T>(Y[4], X1, cmul<T>(Y[2], X0)));
         }
     }
-    fft_lines<T, true, LOGN, 3, false, true>(v, sm, region, L, w, t, mv.tw);
+    fft_lines<T, true, N, 3, false, true>(v, sm, region, L, w, t, mv.tw);
     if (ok) {
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
             for (int m = 0; m < nv; ++m) {
-                const int n = t + (m << logT);
+                const int n = t + m * TL;
                 if (n < g.P) col[c * comp + n * plane] = v[c][m];
             }
     }
 }
 
 // one CTA per tile, inputs loaded from global memory
-template <typename T, int LOGN, int LOGW>
+template <typename T, int N, int LOGW>
 __global__ void __launch_bounds__(p3_max_threads<T>(), 1) k_p3(MatvecView<T> mv) {
     const int j = blockIdx.x, xt = blockIdx.y;                  // batch slot, column tile
     if (rhs_done(mv, mv.b0 + j)) return;
     extern __shared__ unsigned char smem_raw[];
     C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
-    constexpr int logT = lines_log(LOGN), nv = points(LOGN);
+    constexpr int TL = Line<N>::T, nv = Line<N>::NV;
     const Geometry& g = mv.g;
     constexpr int W = 1 << LOGW;
     const int w = threadIdx.x & (W - 1), t = threadIdx.x >> LOGW;
@@ -267,10 +265,10 @@ __global__ void __launch_bounds__(p3_max_threads<T>(), 1) k_p3(MatvecView<T> mv)
     for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
-            const int n = t + (m << logT);
+            const int n = t + m * TL;
             v[c][m] = (ok && m < nv && n < g.P) ? col[c * comp + n * plane] : mk<T>(0, 0);
         }
-    p3_tile<T, LOGN, LOGW>(mv, sm, j, xt, jy, v);
+    p3_tile<T, N, LOGW>(mv, sm, j, xt, jy, v);
 }
 
 // Persistent schedule: each CTA walks the tiles q = blockIdx.x, + gridDim.x,
@@ -287,12 +285,12 @@ __device__ __forceinline__ void cp_async16(void* dst_smem, const void* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-template <typename T, int LOGN, int LOGW>
+template <typename T, int N, int LOGW>
 __global__ void __launch_bounds__(p3_max_threads<T>(), 1) k_p3p(MatvecView<T> mv, int stage_off) {
     extern __shared__ unsigned char smem_raw[];
     C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
     C<T>* stage = sm + stage_off;                                  // [3][P][W]
-    constexpr int logT = lines_log(LOGN), nv = points(LOGN);
+    constexpr int TL = Line<N>::T, nv = Line<N>::NV;
     const Geometry& g = mv.g;
     constexpr int W = 1 << LOGW;
     constexpr int per16 = 16 / (int)sizeof(C<T>), chunks = W / per16;   // 16-byte copies per stage row
@@ -327,40 +325,40 @@ __global__ void __launch_bounds__(p3_max_threads<T>(), 1) k_p3p(MatvecView<T> mv
         for (int c = 0; c < 3; ++c)
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
-                const int n = t + (m << logT);
+                const int n = t + m * TL;
                 v[c][m] = (!skip && m < nv && n < g.P) ? stage[(c * g.P + n) * W + w] : mk<T>(0, 0);
             }
         __syncthreads();                                         // the stage is free again
         if (q + (int)gridDim.x < ntiles) issue(q + gridDim.x);
         cp_async_commit();
-        if (!skip) p3_tile<T, LOGN, LOGW>(mv, sm, j, xt, jy, v);
+        if (!skip) p3_tile<T, N, LOGW>(mv, sm, j, xt, jy, v);
     }
     cp_async_wait_all();
     }
 }
 
 // ---------------------------------------------------------------- P5
-template <typename T, int LOGN, int LOGW>
+template <typename T, int N, int LOGW>
 __global__ void __launch_bounds__(kYThreads, sizeof(T) == 4 ? 2 : 1) k_p5(MatvecView<T> mv, const C<T>* __restrict__ p, C<T>* __restrict__ y) {
     const int c = blockIdx.z % 3, j = blockIdx.z / 3;      // component, batch slot
     const int b = mv.b0 + j;
     if (rhs_done(mv, b)) return;
     extern __shared__ unsigned char smem_raw[];
     C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
-    constexpr int logT = lines_log(LOGN), nv = points(LOGN);
+    constexpr int TL = Line<N>::T, nv = Line<N>::NV;
     const Geometry& g = mv.g;
     constexpr int logW = LOGW, W = 1 << LOGW;
     const int w = threadIdx.x & (W - 1), t = threadIdx.x >> logW;
     const int i = blockIdx.x * W + w, kz = blockIdx.y;
     const bool ok = i < g.K;
-    const C<T>* in = mv.Ay + j * ay_elems(g) + ((int64_t)c * g.P + kz) * ((int64_t)g.K << LOGN) + (ok ? i : 0);
+    const C<T>* in = mv.Ay + j * ay_elems(g) + ((int64_t)c * g.P + kz) * ((int64_t)g.K * N) + (ok ? i : 0);
     C<T> v[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
-        const int n = t + (m << logT);
+        const int n = t + m * TL;
         v[m] = (ok && m < nv) ? in[(int64_t)n * g.K] : mk<T>(0, 0);
     }
-    fft_regs<T, true, LOGN, false, true>(v, sm, ColLayoutT<LOGW>{}, w, t, mv.tw);
+    fft_regs<T, true, N, false, true>(v, sm, ColLayoutT<LOGW>{}, w, t, mv.tw);
     if (!ok) return;
     const C<T>* pc = p + (int64_t)b * mv.vstride + (int64_t)c * g.nd;
     C<T>* yc = y + (int64_t)b * mv.vstride + (int64_t)c * g.nd;
@@ -370,7 +368,7 @@ __global__ void __launch_bounds__(kYThreads, sizeof(T) == 4 ? 2 : 1) k_p5(Matvec
     uint32_t word[8], rbase[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
-        const int n = t + (m << logT);
+        const int n = t + m * TL;
         const bool in = m < nv && n < g.J;
         const int64_t q = (s0 + (int64_t)n * g.K) >> 5;
         word[m] = in ? __ldg(mv.tv.occ + q) : 0u;
@@ -379,7 +377,7 @@ __global__ void __launch_bounds__(kYThreads, sizeof(T) == 4 ? 2 : 1) k_p5(Matvec
     C<T> pv[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
-        const int n = t + (m << logT);
+        const int n = t + m * TL;
         const uint32_t bit = (uint32_t)((s0 + (int64_t)n * g.K) & 31);
         rbase[m] += __popc(word[m] & ((1u << bit) - 1u));   // the site's rank
         word[m] = (word[m] >> bit) & 1u;                    // occupied?
@@ -388,7 +386,7 @@ __global__ void __launch_bounds__(kYThreads, sizeof(T) == 4 ? 2 : 1) k_p5(Matvec
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
         if (!word[m]) continue;
-        const int64_t s = s0 + (int64_t)(t + (m << logT)) * g.K;
+        const int64_t s = s0 + (int64_t)(t + m * TL) * g.K;
         const int mat = material(mv.tv, s, c);
         const C<T> a = mv.ainv[mat * 3 + c];
         C<T> q = pv[m];
@@ -405,7 +403,8 @@ __global__ void __launch_bounds__(kYThreads, sizeof(T) == 4 ? 2 : 1) k_p5(Matvec
     }
 }
 
-inline int threads_log(int N) { return N > 8 ? ilog2(N) - 3 : 0; }
+// threads per line of N points
+inline int threads_of(int N) { return N >= 8 ? N / 8 : 1; }
 
 // largest power of two <= n (n >= 1), as its log
 inline int floor_log2(int n) { int l = 0; while ((2 << l) <= n) ++l; return l; }
@@ -423,29 +422,29 @@ inline int set_smem(const void* fn, size_t bytes, std::atomic<size_t>& done) {
 }
 
 // ------------------------------------------------- per-length launchers
-template <typename T, int LOGN, int LOGW>
+template <typename T, int N, int LOGW>
 int launch_p1(const MatvecView<T>& mv, const C<T>* p, cudaStream_t st) {
     const Geometry& g = mv.g;
     constexpr int W = 1 << LOGW;
-    const size_t sm = (size_t)col_elems(1 << LOGN, W) * sizeof(C<T>);
+    const size_t sm = (size_t)col_elems(N, W) * sizeof(C<T>);
     static std::atomic<size_t> smem_set{0};
-    if (int rc = set_smem((const void*)k_p1<T, LOGN, LOGW>, sm, smem_set)) return rc;
+    if (int rc = set_smem((const void*)k_p1<T, N, LOGW>, sm, smem_set)) return rc;
     dim3 grid((g.K + W - 1) / W, g.P, 3 * mv.nb);
-    k_p1<T, LOGN, LOGW><<<grid, W << lines_log(LOGN), sm, st>>>(mv, p);
+    k_p1<T, N, LOGW><<<grid, W * Line<N>::T, sm, st>>>(mv, p);
     DDA_LAUNCH_CHECK("P1 expand + y-forward");
     return 0;
 }
 
-template <typename T, bool INV, int LOGN>
+template <typename T, bool INV, int N>
 int launch_rows(const MatvecView<T>& mv, cudaStream_t st) {
     const Geometry& g = mv.g;
     const int64_t rows = 3LL * g.P * g.Ly;
     const int R = 1 << mv.logW_x;
-    const size_t sm = (size_t)R * row_ld(1 << LOGN) * sizeof(C<T>);
+    const size_t sm = (size_t)R * row_ld(N) * sizeof(C<T>);
     static std::atomic<size_t> smem_set{0};
-    if (int rc = set_smem((const void*)k_rows<T, INV, LOGN>, sm, smem_set)) return rc;
+    if (int rc = set_smem((const void*)k_rows<T, INV, N>, sm, smem_set)) return rc;
     const dim3 grid((unsigned)((rows + R - 1) / R), mv.nb);
-    k_rows<T, INV, LOGN><<<grid, R << lines_log(LOGN), sm, st>>>(mv);
+    k_rows<T, INV, N><<<grid, R * Line<N>::T, sm, st>>>(mv);
     DDA_LAUNCH_CHECK(INV ? "P4 x-inverse" : "P2 x-forward");
     return 0;
 }
@@ -455,7 +454,7 @@ int launch_rows(const MatvecView<T>& mv, cudaStream_t st) {
 template <typename T>
 inline bool p3_persistent_ok(const Geometry& g, int logW) {
     const int W = 1 << logW;
-    if (W > g.Lx || (W * (int)sizeof(C<T>)) % 16) return false;
+    if (W > g.Lx || g.Lx % W || (W * (int)sizeof(C<T>)) % 16) return false;
     const size_t stage_off = (3 * (size_t)col_elems(g.Lz, W) + 1) & ~size_t(1);
     return (stage_off + 3ull * g.P * W) * sizeof(C<T>) <= 220 * 1024;
 }
@@ -472,65 +471,64 @@ inline int sm_count() {
     return v;
 }
 
-template <typename T, int LOGN, int LOGW>
+template <typename T, int N, int LOGW>
 int launch_p3(const MatvecView<T>& mv, cudaStream_t st) {
     const Geometry& g = mv.g;
     constexpr int W = 1 << LOGW;
-    const int threads = W << lines_log(LOGN);
+    const int threads = W * Line<N>::T;
     if (mv.p3_sched == 1 && p3_persistent_ok<T>(g, LOGW)) {
-        const int stage_off = (int)((3 * (size_t)col_elems(1 << LOGN, W) + 1) & ~size_t(1));
+        const int stage_off = (int)((3 * (size_t)col_elems(N, W) + 1) & ~size_t(1));
         const size_t sm = ((size_t)stage_off + 3ull * g.P * W) * sizeof(C<T>);
         static std::atomic<size_t> smem_set{0};
-        if (int rc = set_smem((const void*)k_p3p<T, LOGN, LOGW>, sm, smem_set)) return rc;
+        if (int rc = set_smem((const void*)k_p3p<T, N, LOGW>, sm, smem_set)) return rc;
         static std::atomic<int> per_sm{0};
         int bps = per_sm.load(std::memory_order_relaxed);
         if (!bps) {
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_p3p<T, LOGN, LOGW>, threads, sm) != cudaSuccess ||
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_p3p<T, N, LOGW>, threads, sm) != cudaSuccess ||
                 bps < 1)
                 bps = 1;
             per_sm.store(bps, std::memory_order_relaxed);
         }
         const int64_t ntiles = (int64_t)mv.nb * (g.Lx / W) * g.Ly;
         const int grid = (int)std::min<int64_t>(ntiles, (int64_t)sm_count() * bps);
-        k_p3p<T, LOGN, LOGW><<<grid, threads, sm, st>>>(mv, stage_off);
+        k_p3p<T, N, LOGW><<<grid, threads, sm, st>>>(mv, stage_off);
         DDA_LAUNCH_CHECK("P3 z-forward, spectrum product, z-inverse (persistent)");
         return 0;
     }
-    const size_t sm = 3 * (size_t)col_elems(1 << LOGN, W) * sizeof(C<T>);
+    const size_t sm = 3 * (size_t)col_elems(N, W) * sizeof(C<T>);
     static std::atomic<size_t> smem_set{0};
-    if (int rc = set_smem((const void*)k_p3<T, LOGN, LOGW>, sm, smem_set)) return rc;
+    if (int rc = set_smem((const void*)k_p3<T, N, LOGW>, sm, smem_set)) return rc;
     dim3 grid(mv.nb, (g.Lx + W - 1) / W, g.Ly);
-    k_p3<T, LOGN, LOGW><<<grid, threads, sm, st>>>(mv);
+    k_p3<T, N, LOGW><<<grid, threads, sm, st>>>(mv);
     DDA_LAUNCH_CHECK("P3 z-forward, spectrum product, z-inverse");
     return 0;
 }
 
-template <typename T, int LOGN, int LOGW>
+template <typename T, int N, int LOGW>
 int launch_p5(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t st) {
     const Geometry& g = mv.g;
     constexpr int W = 1 << LOGW;
-    const size_t sm = (size_t)col_elems(1 << LOGN, W) * sizeof(C<T>);
+    const size_t sm = (size_t)col_elems(N, W) * sizeof(C<T>);
     static std::atomic<size_t> smem_set{0};
-    if (int rc = set_smem((const void*)k_p5<T, LOGN, LOGW>, sm, smem_set)) return rc;
+    if (int rc = set_smem((const void*)k_p5<T, N, LOGW>, sm, smem_set)) return rc;
     dim3 grid((g.K + W - 1) / W, g.P, 3 * mv.nb);
-    k_p5<T, LOGN, LOGW><<<grid, W << lines_log(LOGN), sm, st>>>(mv, p, y);
+    k_p5<T, N, LOGW><<<grid, W * Line<N>::T, sm, st>>>(mv, p, y);
     DDA_LAUNCH_CHECK("P5 y-inverse + diagonal + compress");
     return 0;
 }
 
-#define DDA_LOGN_SWITCH(logN, CALL)                    \
-    switch (logN) {                                    \
-        case 1: { constexpr int LN = 1; return CALL; } \
-        case 2: { constexpr int LN = 2; return CALL; } \
-        case 3: { constexpr int LN = 3; return CALL; } \
-        case 4: { constexpr int LN = 4; return CALL; } \
-        case 5: { constexpr int LN = 5; return CALL; } \
-        case 6: { constexpr int LN = 6; return CALL; } \
-        case 7: { constexpr int LN = 7; return CALL; } \
-        case 8: { constexpr int LN = 8; return CALL; } \
-        case 9: { constexpr int LN = 9; return CALL; } \
-        case 10: { constexpr int LN = 10; return CALL; } \
-        default: return fail(DDA_ERR_ARG, "line length out of range"); \
+// every line length the passes are compiled for: 2^a (a = 1..10) and
+// 3 * 2^a (a = 3..8)
+#define DDA_LEN_CASE(V, CALL) case V: { constexpr int LN = V; return CALL; }
+#define DDA_LEN_SWITCH(len, CALL)                                                        \
+    switch (len) {                                                                       \
+        DDA_LEN_CASE(2, CALL) DDA_LEN_CASE(4, CALL) DDA_LEN_CASE(8, CALL)                \
+        DDA_LEN_CASE(16, CALL) DDA_LEN_CASE(32, CALL) DDA_LEN_CASE(64, CALL)             \
+        DDA_LEN_CASE(128, CALL) DDA_LEN_CASE(256, CALL) DDA_LEN_CASE(512, CALL)          \
+        DDA_LEN_CASE(1024, CALL) DDA_LEN_CASE(24, CALL) DDA_LEN_CASE(48, CALL)           \
+        DDA_LEN_CASE(96, CALL) DDA_LEN_CASE(192, CALL) DDA_LEN_CASE(384, CALL)           \
+        DDA_LEN_CASE(768, CALL)                                                          \
+        default: return fail(DDA_ERR_ARG, "line length out of range");                   \
     }
 
 #define DDA_LOGW_SWITCH(logW, CALL)                    \
@@ -550,6 +548,9 @@ constexpr int kMaxLogW = 4;
 template <typename T> int pass1(const MatvecView<T>& mv, const C<T>* p, cudaStream_t st);
 template <typename T, bool INV> int pass_rows(const MatvecView<T>& mv, cudaStream_t st);
 template <typename T> int pass3(const MatvecView<T>& mv, cudaStream_t st);
+// P3 for one line length (all tile widths); each length group is
+// instantiated in its own translation unit (mv_p3_*.cu)
+template <typename T, int N> int p3_len(const MatvecView<T>& mv, cudaStream_t st);
 template <typename T> int pass5(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t st);
 
 }  // namespace dda

@@ -10,7 +10,7 @@ static int p1_width(const MatvecView<T>& mv, const C<T>* p, cudaStream_t st) {
 }
 
 template <typename T> int pass1(const MatvecView<T>& mv, const C<T>* p, cudaStream_t st) {
-    DDA_LOGN_SWITCH(ilog2(mv.g.Ly), (p1_width<T, LN>(mv, p, st)))
+    DDA_LEN_SWITCH(mv.g.Ly, (p1_width<T, LN>(mv, p, st)))
 }
 
 template int pass1<double>(const MatvecView<double>&, const C<double>*, cudaStream_t);

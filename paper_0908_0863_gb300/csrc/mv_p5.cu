@@ -10,7 +10,7 @@ static int p5_width(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_
 }
 
 template <typename T> int pass5(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t st) {
-    DDA_LOGN_SWITCH(ilog2(mv.g.Ly), (p5_width<T, LN>(mv, p, y, st)))
+    DDA_LEN_SWITCH(mv.g.Ly, (p5_width<T, LN>(mv, p, y, st)))
 }
 
 template int pass5<double>(const MatvecView<double>&, const C<double>*, C<double>*, cudaStream_t);

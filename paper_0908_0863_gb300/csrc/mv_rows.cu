@@ -5,7 +5,7 @@
 namespace dda {
 
 template <typename T, bool INV> int pass_rows(const MatvecView<T>& mv, cudaStream_t st) {
-    DDA_LOGN_SWITCH(ilog2(mv.g.Lx), (launch_rows<T, INV, LN>(mv, st)))
+    DDA_LEN_SWITCH(mv.g.Lx, (launch_rows<T, INV, LN>(mv, st)))
 }
 
 template int pass_rows<double, false>(const MatvecView<double>&, cudaStream_t);

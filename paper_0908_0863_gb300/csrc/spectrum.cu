@@ -68,11 +68,11 @@ __global__ void __launch_bounds__(512) k_tensor_x(Geometry g, int logW, const do
                                                   const double2* __restrict__ in, double2* __restrict__ out) {
     extern __shared__ unsigned char smem_raw[];
     double2* buf = reinterpret_cast<double2*>(smem_raw);
-    const int W = 1 << logW, ld = W + 1, N = g.Lx, logN = ilog2_dev(N);
+    const int W = 1 << logW, ld = W + 1, N = g.Lx;
     const int64_t rows_per_m = (int64_t)g.P * g.J, nrows = 6 * rows_per_m;
     const int64_t r0 = (int64_t)blockIdx.x * W;
     for (int e = threadIdx.x; e < W * N; e += blockDim.x) {
-        const int w = e >> logN, n = e & (N - 1);
+        const int w = e / N, n = e - w * N;
         const int64_t row = r0 + w;
         double2 v = make_double2(0.0, 0.0);
         if (row < nrows) {
@@ -88,9 +88,9 @@ __global__ void __launch_bounds__(512) k_tensor_x(Geometry g, int logW, const do
         buf[n * ld + w] = v;
     }
     __syncthreads();
-    fft_tile<double, kV, false>(buf, ld, logW, logN, tw);
+    fft_tile<double, kV, false>(buf, ld, logW, N, tw);
     for (int e = threadIdx.x; e < W * N; e += blockDim.x) {
-        const int w = e >> logN, n = e & (N - 1);
+        const int w = e / N, n = e - w * N;
         const int64_t row = r0 + w;
         if (row < nrows && n < g.Hx) out[row * g.Hx + n] = buf[n * ld + w];
     }
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(512) k_tensor_col(Geometry g, int logW, const 
     extern __shared__ unsigned char smem_raw[];
     double2* buf = reinterpret_cast<double2*>(smem_raw);
     const int W = 1 << logW, ld = W + 1;
-    const int N = AXIS == 1 ? g.Ly : g.Lz, logN = ilog2_dev(N);
+    const int N = AXIS == 1 ? g.Ly : g.Lz;
     const int nline = AXIS == 1 ? g.J : g.P;
     const int H = AXIS == 1 ? g.Hy : g.Hz;
     const int x0 = blockIdx.x * W;
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(512) k_tensor_col(Geometry g, int logW, const 
         buf[n * ld + w] = v;
     }
     __syncthreads();
-    fft_tile<double, kV, false>(buf, ld, logW, logN, tw);
+    fft_tile<double, kV, false>(buf, ld, logW, N, tw);
     for (int e = threadIdx.x; e < W * H; e += blockDim.x) {
         const int n = e >> logW, w = e & (W - 1), x = x0 + w;
         if (x >= g.Hx) continue;

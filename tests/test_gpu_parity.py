@@ -182,6 +182,29 @@ def test_matvec_full_size_sampled_rows(dda, n, D):
     assert np.abs(y32 - ref).max() <= 5e-6 * scale
 
 
+@pytest.mark.parametrize("box,D", [((96, 96, 96), 96), ((192, 160, 100), 100)])
+def test_matvec_radix3_lengths_sampled_rows(dda, box, D):
+    # lattices whose circulant lengths are 3 * 2^a (192 = 3 * 64 on all axes;
+    # 384, 384, 256): the radix-3 closing stage in every pass and in the
+    # spectrum build, against 24 direct sums
+    m = 1.33 + 0.05j
+    k = 0.5 / abs(m)
+    mask = synth.sphere(D, box=box)
+    case = Case(mask, [m], k)
+    assert case.shape == box
+    p = synth.complex_normal(6, (3, case.nd))
+    rows = synth.rng(10).choice(case.nd, size=24, replace=False)
+    ref = odda.direct_matvec_rows(case.coords, case.ainv, case.k, p, rows)
+    with case.lattice() as lat:
+        assert lat.padded == tuple(circulant.padded_length(v) for v in box)
+        assert any(v % 3 == 0 for v in lat.padded)
+    y = _matvec(dda, case, p, np.complex128)[:, rows]
+    scale = np.abs(ref).max()
+    assert np.abs(y - ref).max() <= 1e-11 * scale
+    y32 = _matvec(dda, case, p, np.complex64)[:, rows]
+    assert np.abs(y32 - ref).max() <= 5e-6 * scale
+
+
 def test_matvec_rejects_host_and_aliased(dda):
     case = random_case((4, 4, 4), seed=1, two_materials=False)
     with case.lattice() as lat:
