@@ -32,16 +32,17 @@ AXES = ((0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2))
 
 def padded_length(n: int) -> int:
     """Circulant length of an n-point Toeplitz level: the smallest L >= 2n - 1
-    (and >= 2) of the form 2^a or 3 * 2^a with a >= 3, the paper's
-    K'' = 2K - 1 + kf with kf chosen for a fast DFT (Sec. 3, App. A)."""
+    (and >= 2) of the form 2^a, 3 * 2^a or 5 * 2^a (a >= 3 for the last two),
+    the paper's K'' = 2K - 1 + kf with kf chosen for a fast DFT (Sec. 3,
+    App. A)."""
     need = max(2, 2 * n - 1)
-    L = 2
-    while L < need:
-        L *= 2
-    t = 24
-    while t < need:
-        t *= 2
-    return min(L, t)
+    best = None
+    for start in (2, 24, 40):
+        L = start
+        while L < need:
+            L *= 2
+        best = L if best is None else min(best, L)
+    return best
 
 
 def mirror_signs() -> np.ndarray:

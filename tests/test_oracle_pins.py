@@ -178,7 +178,7 @@ def test_direct_equals_dense():
 
 @pytest.mark.parametrize("shape,hollow", [((1, 1, 1), False), ((2, 3, 5), False), ((5, 4, 3), True),
                                           ((8, 8, 8), False), ((7, 3, 6), True), ((12, 5, 4), False),
-                                          ((12, 24, 9), True), ((13, 12, 24), False)])
+                                          ((12, 24, 9), True), ((13, 12, 24), False), ((20, 7, 17), True)])
 def test_fft_matvec_equals_direct_sum(shape, hollow):
     # App. A standard algorithm (circulant embedding + Eqs. 6-8) == definition
     K, J, P = shape
@@ -214,10 +214,10 @@ def test_half_spectrum_and_mirror_lookup(shape):
 
 
 def test_padded_lengths():
-    # K'' = 2K - 1 + kf: the smallest 2^a or 3 * 2^a (a >= 3) >= 2K - 1
-    ns = (1, 2, 5, 12, 13, 16, 24, 48, 96, 100, 128, 138, 193, 256, 512)
-    assert [circulant.padded_length(n) for n in ns] == [2, 4, 16, 24, 32, 32, 48, 96, 192, 256, 256, 384, 512,
-                                                        512, 1024]
+    # K'' = 2K - 1 + kf: the smallest 2^a, 3 * 2^a or 5 * 2^a (a >= 3) >= 2K - 1
+    ns = (1, 2, 5, 12, 13, 16, 20, 24, 48, 74, 96, 100, 128, 138, 160, 193, 256, 300, 512)
+    assert [circulant.padded_length(n) for n in ns] == [2, 4, 16, 24, 32, 32, 40, 48, 96, 160, 192, 256, 256,
+                                                        320, 320, 512, 512, 640, 1024]
 
 
 # ---------------------------------------------------------- polarisability
