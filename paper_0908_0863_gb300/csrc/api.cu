@@ -543,7 +543,8 @@ int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occu
         std::vector<double2> t64(kTwEntries);
         std::vector<float2> t32(kTwEntries);
         for (int m = 0; m < kTwEntries; ++m) {
-            const double ang = -2.0 * M_PI * (double)m / kTwEntries;
+            // exp(-2 pi i m / 3072) for m < 3072, then exp(-2 pi i m' / 5120)
+            const double ang = m < 3072 ? -2.0 * M_PI * (double)m / 3072.0 : -2.0 * M_PI * (double)(m - 3072) / 5120.0;
             t64[m] = make_double2(std::cos(ang), std::sin(ang));
             t32[m] = make_float2((float)t64[m].x, (float)t64[m].y);
         }

@@ -34,7 +34,7 @@ template <typename T> __host__ __device__ __forceinline__ C<T> cfma(C<T> a, C<T>
 
 // --------------------------------------------------------------- limits
 constexpr int kMaxLine = 1024;      // longest padded line (lattice edge <= 512)
-constexpr int kTwEntries = 3072;    // twiddle table: exp(-2 pi i m / 3072), lines of 2^a and 3 * 2^a points
+constexpr int kTwEntries = 3072 + 5120;   // twiddle tables exp(-2 pi i m / 3072) and exp(-2 pi i m / 5120)
 constexpr int kMaxEdge = 512;
 
 // ------------------------------------------------------- error reporting
@@ -74,14 +74,17 @@ struct Geometry {
 };
 
 // circulant length of an n-point Toeplitz level: the smallest L >= 2n - 1
-// (and >= 2) of the form 2^a or 3 * 2^a with a >= 3 (Sec. 3: K'' = 2K - 1 + kf
-// with kf chosen for a fast DFT)
+// (and >= 2) of the form 2^a, 3 * 2^a or 5 * 2^a (a >= 3 for the last two;
+// Sec. 3: K'' = 2K - 1 + kf with kf chosen for a fast DFT)
 inline int padded_length(int n) {
     const int need = 2 * n - 1 > 2 ? 2 * n - 1 : 2;
-    int L = 2, t = 24;
-    while (L < need) L *= 2;
-    while (t < need) t *= 2;
-    return t < L ? t : L;
+    int best = 0;
+    for (int start : {2, 24, 40}) {
+        int L = start;
+        while (L < need) L *= 2;
+        if (!best || L < best) best = L;
+    }
+    return best;
 }
 inline int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
 

@@ -1,5 +1,5 @@
-// Batched line DFTs on a shared-memory tile (sm_103a), for lines of 2^a or
-// 3 * 2^a points.
+// Batched line DFTs on a shared-memory tile (sm_103a), for lines of 2^a,
+// 3 * 2^a or 5 * 2^a points.
 //
 // The 3D DFTs of the DDA matvec are done as ensembles of 1D line transforms
 // (OpenDDA Sec. 3).  Here a CTA holds W lines of N points in shared memory,
@@ -14,10 +14,11 @@
 // the launch uses exactly W*N/V threads.  A stage reads everything into
 // registers, synchronises, then writes, so one buffer suffices.
 //
-// Twiddles come from a table tw[m] = exp(-2 pi i m / 3072) computed in FP64
-// on the host (rounded once for the FP32 table); the inverse transform uses
-// their conjugates.  Lines of N = 3 * 2^a points end with a radix-3 stage.
-// Transforms are unnormalised.
+// Twiddles come from the tables exp(-2 pi i m / 3072) and, after it,
+// exp(-2 pi i m / 5120), computed in FP64 on the host (rounded once for
+// FP32); the inverse transform uses their conjugates.  Lines of 3 * 2^a and
+// 5 * 2^a points end with a radix-3 or radix-5 stage.  Transforms are
+// unnormalised.
 #pragma once
 
 #include "common.cuh"
@@ -126,38 +127,64 @@ __device__ __forceinline__ void fft_stage(C<T>* __restrict__ buf, int ld, int lo
     __syncthreads();
 }
 
-// The closing radix-3 stage of an N = 3M line (Ns = M): butterfly j < M
-// twiddles x[j + M r] by exp(-+ 2 pi i j r / N) = tw[3072 j r / N] and
-// transforms the three points in place.  W M butterflies over the CTA.
-template <typename T, bool INV>
-__device__ __forceinline__ void fft_stage3(C<T>* __restrict__ buf, int ld, int logW, int N,
-                                           const C<T>* __restrict__ tw) {
-    const int M = N / 3, W = 1 << logW, step = 3072 / N;
-    const T h = (T)0.86602540378443864676;   // sqrt(3) / 2
+// The closing stage of an N = R M line (R = 3 or 5, Ns = M): butterfly j < M
+// twiddles x[j + M r] by exp(-+ 2 pi i j r / N) and transforms the R points
+// in place.  Twiddles: tw[3072 j r / N] for R = 3, tw[3072 + 5120 j r / N]
+// for R = 5.  W M butterflies over the CTA.
+template <typename T, int R, bool INV>
+__device__ __forceinline__ void fft_stage_odd(C<T>* __restrict__ buf, int ld, int logW, int N,
+                                              const C<T>* __restrict__ tw) {
+    const int M = N / R, W = 1 << logW;
+    const int off = R == 3 ? 0 : 3072, step = (R == 3 ? 3072 : 5120) / N;
     for (int g = threadIdx.x; g < W * M; g += blockDim.x) {
         const int w = g & (W - 1), j = g >> logW;
-        C<T> t1 = __ldg(tw + j * step), t2 = __ldg(tw + 2 * j * step);
-        if (INV) { t1.y = -t1.y; t2.y = -t2.y; }
-        const C<T> a = buf[j * ld + w];
-        const C<T> b = cmul<T>(buf[(j + M) * ld + w], t1), c = cmul<T>(buf[(j + 2 * M) * ld + w], t2);
-        const C<T> s = cadd<T>(b, c), d = csub<T>(b, c);
-        const C<T> m = mk<T>(a.x - (T)0.5 * s.x, a.y - (T)0.5 * s.y);
-        const C<T> r = cscale<T>(rot90<T, INV>(d), h);
-        buf[j * ld + w] = cadd<T>(a, s);
-        buf[(j + M) * ld + w] = cadd<T>(m, r);
-        buf[(j + 2 * M) * ld + w] = csub<T>(m, r);
+        C<T> x[R];
+        x[0] = buf[j * ld + w];
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+            C<T> t = __ldg(tw + off + j * r * step);
+            if (INV) t.y = -t.y;
+            x[r] = cmul<T>(buf[(j + r * M) * ld + w], t);
+        }
+        if constexpr (R == 3) {
+            const T h = (T)0.86602540378443864676;   // sqrt(3) / 2
+            const C<T> s = cadd<T>(x[1], x[2]), d = csub<T>(x[1], x[2]);
+            const C<T> m = mk<T>(x[0].x - (T)0.5 * s.x, x[0].y - (T)0.5 * s.y);
+            const C<T> rr = cscale<T>(rot90<T, INV>(d), h);
+            x[0] = cadd<T>(x[0], s);
+            x[1] = cadd<T>(m, rr);
+            x[2] = csub<T>(m, rr);
+        } else {
+            const T c1 = (T)0.30901699437494742410, c2 = (T)-0.80901699437494742410;
+            const T s1 = (T)0.95105651629515357212, s2 = (T)0.58778525229247312917;
+            const C<T> a1 = cadd<T>(x[1], x[4]), b1 = csub<T>(x[1], x[4]);
+            const C<T> a2 = cadd<T>(x[2], x[3]), b2 = csub<T>(x[2], x[3]);
+            const C<T> t1 = mk<T>(x[0].x + c1 * a1.x + c2 * a2.x, x[0].y + c1 * a1.y + c2 * a2.y);
+            const C<T> t2 = mk<T>(x[0].x + c2 * a1.x + c1 * a2.x, x[0].y + c2 * a1.y + c1 * a2.y);
+            const C<T> u1 = rot90<T, INV>(mk<T>(s1 * b1.x + s2 * b2.x, s1 * b1.y + s2 * b2.y));
+            const C<T> u2 = rot90<T, INV>(mk<T>(s2 * b1.x - s1 * b2.x, s2 * b1.y - s1 * b2.y));
+            x[0] = cadd<T>(x[0], cadd<T>(a1, a2));
+            x[1] = cadd<T>(t1, u1);
+            x[4] = csub<T>(t1, u1);
+            x[2] = cadd<T>(t2, u2);
+            x[3] = csub<T>(t2, u2);
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[(j + r * M) * ld + w] = x[r];
     }
     __syncthreads();
 }
 
-// In-place DFT of the W = 2^logW lines of N points (N = 2^a, or 3 * 2^a with
-// a >= 3) of a tile: the Stockham stages of the power-of-two factor, then
-// the radix-3 stage.  tw: table of 3072 entries exp(-2 pi i m / 3072).
-// Requires blockDim.x * V == W * N.
+// In-place DFT of the W = 2^logW lines of N points (N = 2^a, or 3 * 2^a or
+// 5 * 2^a with a >= 3) of a tile: the Stockham stages of the power-of-two
+// factor, then the closing radix-3 or radix-5 stage.  tw: the tables
+// exp(-2 pi i m / 3072) (3072 entries) and exp(-2 pi i m / 5120) (5120
+// entries, after the first).  Requires blockDim.x * V == W * N.
 template <typename T, int V, bool INV>
 __device__ __forceinline__ void fft_tile(C<T>* __restrict__ buf, int ld, int logW, int N,
                                          const C<T>* __restrict__ tw) {
-    const int M = (N % 3) ? N : N / 3;
+    const int R = (N % 3) == 0 ? 3 : (N % 5) == 0 ? 5 : 1;
+    const int M = N / R;
     int logM = 0;
     while ((1 << logM) < M) ++logM;
     const int logMax = 10;  // log2 of the longest power-of-two line
@@ -174,7 +201,8 @@ __device__ __forceinline__ void fft_tile(C<T>* __restrict__ buf, int ld, int log
         fft_stage<T, V, 8, INV>(buf, ld, logW, N, logNs, tw, logMax - logNs - 3);
         logNs += 3;
     }
-    if (M != N) fft_stage3<T, INV>(buf, ld, logW, N, tw);
+    if (R == 3) fft_stage_odd<T, 3, INV>(buf, ld, logW, N, tw);
+    else if (R == 5) fft_stage_odd<T, 5, INV>(buf, ld, logW, N, tw);
 }
 
 }  // namespace dda

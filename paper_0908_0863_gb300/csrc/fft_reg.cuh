@@ -1,5 +1,5 @@
 // Register-resident line DFTs for the matvec passes (sm_103a), for lines of
-// N = 2^a or N = 3 * 2^a (a >= 3) points.
+// N = 2^a, 3 * 2^a or 5 * 2^a (a >= 3) points.
 //
 // Each line of N >= 8 points is owned by T = N/8 threads; thread t holds
 // the eight "canonical" points t + T m (m = 0..7) in registers.  The
@@ -12,10 +12,10 @@
 // output positions, read back the canonical points).  For N = 2^a the last
 // radix-8 stage writes its outputs to the canonical positions themselves, so
 // the transform ends in registers in natural order: N = 512 costs two
-// shared-memory exchanges.  For N = 3M the radix-3 stage comes last (Ns = M):
-// its butterfly j < M reads and writes the positions j, j + M, j + 2M, so it
-// runs in place in shared memory after the last radix-8 exchange, and one
-// more canonical read ends the transform.  The length is a template
+// shared-memory exchanges.  For N = R M (R = 3 or 5) the radix-R stage comes
+// last (Ns = M): its butterfly j < M reads and writes the positions j + M r,
+// r < R, so it runs in place in shared memory after the last radix-8
+// exchange, and one more canonical read ends the transform.  The length is a template
 // parameter, so every stride, stage count and twiddle step is a
 // compile-time constant.
 //
@@ -28,7 +28,8 @@
 // L >= 2n - 1 for n lattice points), and its inverse transforms keep only the
 // first half of the outputs.  HALF_IN skips the work on the known zeros in
 // the first stage; HALF_OUT computes only outputs m < 4 in the last radix-8
-// stage of a power-of-two length (a radix-3 length computes all outputs).
+// stage of a power-of-two length (a 3 * 2^a or 5 * 2^a length computes all
+// outputs).
 //
 // Shared-memory addresses come from a layout functor (line w, point p):
 // RowLayout keeps each line contiguous (lines of the lattice that are
@@ -38,28 +39,31 @@
 //
 // Lines shorter than 8 points (lattice edges of 1 or 2 sites) are done by
 // one thread each in registers.  Twiddles come from the FP64 table
-// tw[m] = exp(-2 pi i m / 3072) (rounded once for FP32), conjugated for the
-// inverse; FP32 radix-8 stages load one twiddle and form the other six as
-// its powers.  Transforms are unnormalised.
+// tw[m] = exp(-2 pi i m / 3072), m < 3072, followed by
+// tw[3072 + m] = exp(-2 pi i m / 5120), m < 5120 (rounded once for FP32),
+// conjugated for the inverse; FP32 radix-8 stages load one twiddle and form
+// the other six as its powers.  Transforms are unnormalised.
 #pragma once
 
 #include "fft.cuh"
 
 namespace dda {
 
-constexpr int kTwLen = 3072;   // twiddle table length: 3 * the longest power-of-two line
+constexpr int kTwLen = 3072;   // first twiddle table: 3 * the longest power-of-two line
+constexpr int kTw5Len = 5120;  // second one (lines of 5 * 2^a points), stored after the first
 
 __host__ __device__ constexpr int log2c(int n) { return n <= 1 ? 0 : 1 + log2c(n / 2); }
 
 // shape of the transform of one N-point line
 template <int N>
 struct Line {
-    static constexpr bool R3 = (N % 3) == 0;         // N = 3 M
-    static constexpr int M = R3 ? N / 3 : N;          // power-of-two factor
+    static constexpr int R = (N % 3) == 0 ? 3 : (N % 5) == 0 ? 5 : 1;   // closing radix (1: none)
+    static constexpr bool ODD = R != 1;                                 // N = R M
+    static constexpr int M = N / R;                   // power-of-two factor
     static constexpr int LOGM = log2c(M);
     static constexpr int T = N >= 8 ? N / 8 : 1;      // threads per line
     static constexpr int NV = N >= 8 ? 8 : N;         // points per thread
-    static_assert(!R3 || M >= 8, "3 * 2^a lengths need a >= 3");
+    static_assert(!ODD || M >= 8, "3 * 2^a and 5 * 2^a lengths need a >= 3");
 };
 
 template <int N>
@@ -190,30 +194,61 @@ __device__ __forceinline__ void dft3(C<T>& a, C<T>& b, C<T>& c) {
     c = csub<T>(m, r);
 }
 
-// After the last radix-8 stage of an N = 3M line has written its outputs to
-// the Stockham positions: the radix-3 stage (Ns = M) in place in shared
-// memory -- butterfly j < M twiddles x[j + M r] by exp(-+ 2 pi i j r / N) --
-// then the canonical read that ends the transform in registers.  Thread t
-// takes the butterflies j = t, t + T, t + 2T below M.
+// radix-5 DFT of x[0..4] in place, forward (exp(-2 pi i / 5)) or inverse
+template <typename T, bool INV>
+__device__ __forceinline__ void dft5(C<T> (&x)[5]) {
+    const T c1 = (T)0.30901699437494742410, c2 = (T)-0.80901699437494742410;   // cos(2 pi/5), cos(4 pi/5)
+    const T s1 = (T)0.95105651629515357212, s2 = (T)0.58778525229247312917;    // sin(2 pi/5), sin(4 pi/5)
+    const C<T> a1 = cadd<T>(x[1], x[4]), b1 = csub<T>(x[1], x[4]);
+    const C<T> a2 = cadd<T>(x[2], x[3]), b2 = csub<T>(x[2], x[3]);
+    const C<T> t1 = mk<T>(x[0].x + c1 * a1.x + c2 * a2.x, x[0].y + c1 * a1.y + c2 * a2.y);
+    const C<T> t2 = mk<T>(x[0].x + c2 * a1.x + c1 * a2.x, x[0].y + c2 * a1.y + c1 * a2.y);
+    const C<T> u1 = rot90<T, INV>(mk<T>(s1 * b1.x + s2 * b2.x, s1 * b1.y + s2 * b2.y));
+    const C<T> u2 = rot90<T, INV>(mk<T>(s2 * b1.x - s1 * b2.x, s2 * b1.y - s1 * b2.y));
+    x[0] = cadd<T>(x[0], cadd<T>(a1, a2));
+    x[1] = cadd<T>(t1, u1);
+    x[4] = csub<T>(t1, u1);
+    x[2] = cadd<T>(t2, u2);
+    x[3] = csub<T>(t2, u2);
+}
+
+// After the last radix-8 stage of an N = R M line (R = 3 or 5) has written
+// its outputs to the Stockham positions: the radix-R stage (Ns = M) in
+// place in shared memory -- butterfly j < M twiddles x[j + M r] by
+// exp(-+ 2 pi i j r / N) -- then the canonical read that ends the transform
+// in registers.  Thread t takes the butterflies j = t, t + T, ... below M.
 template <typename T, bool INV, int N, int NL, class Layout>
-__device__ __forceinline__ void radix3_finish(C<T> (&v)[NL][8], C<T>* __restrict__ sm, int region,
-                                              const Layout& L, int w, int t, const C<T>* __restrict__ tw) {
-    constexpr int M = N / 3, Tn = N / 8, step = kTwLen / N;
+__device__ __forceinline__ void odd_finish(C<T> (&v)[NL][8], C<T>* __restrict__ sm, int region,
+                                           const Layout& L, int w, int t, const C<T>* __restrict__ tw) {
+    constexpr int R = Line<N>::R, M = N / R, Tn = N / 8;
+    constexpr int off = R == 3 ? 0 : kTwLen, step = (R == 3 ? kTwLen : kTw5Len) / N;
+    constexpr int nq = (M + Tn - 1) / Tn;   // butterflies per thread (3 for R = 3, 2 for R = 5)
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
+    for (int q = 0; q < nq; ++q) {
         const int j = t + q * Tn;
         if (j < M) {
-            const C<T> w1 = twiddle<T, INV>(tw, j * step), w2 = twiddle<T, INV>(tw, 2 * j * step);
-            const int o0 = L(w, j), o1 = L(w, j + M), o2 = L(w, j + 2 * M);
+            C<T> wr[R];
+            int o[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                wr[r] = twiddle<T, INV>(tw, off + j * r * step);
+                o[r] = L(w, j + r * M);
+            }
 #pragma unroll
             for (int l = 0; l < NL; ++l) {
                 C<T>* S = sm + l * region;
-                C<T> a = S[o0], b = cmul<T>(S[o1], w1), c = cmul<T>(S[o2], w2);
-                dft3<T, INV>(a, b, c);
-                S[o0] = a;
-                S[o1] = b;
-                S[o2] = c;
+                C<T> x[R];
+                x[0] = S[o[0]];
+#pragma unroll
+                for (int r = 1; r < R; ++r) x[r] = cmul<T>(S[o[r]], wr[r]);
+                if constexpr (R == 3) {
+                    dft3<T, INV>(x[0], x[1], x[2]);
+                } else {
+                    dft5<T, INV>(x);
+                }
+#pragma unroll
+                for (int r = 0; r < R; ++r) S[o[r]] = x[r];
             }
         }
     }
@@ -223,8 +258,8 @@ __device__ __forceinline__ void radix3_finish(C<T> (&v)[NL][8], C<T>* __restrict
 }
 
 // radix-8 stages from Ns = 2^LOGNS on.  The last one of a 2^a line leaves
-// the outputs on the canonical points; that of a 3 * 2^a line writes them
-// to shared memory for the radix-3 stage.
+// the outputs on the canonical points; that of a 3 * 2^a or 5 * 2^a line
+// writes them to shared memory for the closing radix-3 or radix-5 stage.
 template <typename T, bool INV, int N, int LOGNS, int NL, bool HALF_OUT, class Layout>
 struct Radix8Stages {
     __device__ __forceinline__ static void run(C<T> (&v)[NL][8], C<T>* __restrict__ sm, int region,
@@ -232,7 +267,7 @@ struct Radix8Stages {
         constexpr int Ns = 1 << LOGNS, LOGM = Line<N>::LOGM;
         const int k = t & (Ns - 1);
         twiddle8<T, INV, LOGNS, NL>(v, k, tw);
-        if constexpr (LOGNS + 3 < LOGM || Line<N>::R3) {
+        if constexpr (LOGNS + 3 < LOGM || Line<N>::ODD) {
 #pragma unroll
             for (int l = 0; l < NL; ++l) dft8<T, INV>(v[l]);
             const int base = ((t >> LOGNS) << (LOGNS + 3)) + k;
@@ -248,7 +283,7 @@ struct Radix8Stages {
                 __syncthreads();
                 Radix8Stages<T, INV, N, LOGNS + 3, NL, HALF_OUT, Layout>::run(v, sm, region, L, w, t, tw);
             } else {
-                radix3_finish<T, INV, N, NL>(v, sm, region, L, w, t, tw);
+                odd_finish<T, INV, N, NL>(v, sm, region, L, w, t, tw);
             }
         } else {
 #pragma unroll
@@ -266,7 +301,7 @@ struct Radix8Stages {
 template <typename T, bool INV, int N, int NL, bool HALF_IN, bool HALF_OUT, class Layout>
 __device__ __forceinline__ void fft_lines(C<T> (&v)[NL][8], C<T>* __restrict__ sm, int region, const Layout& L,
                                           int w, int t, const C<T>* __restrict__ tw) {
-    if constexpr (N <= 8 && !Line<N>::R3) {  // a single stage: one thread holds the whole line
+    if constexpr (N <= 8 && !Line<N>::ODD) {  // a single stage: one thread holds the whole line
 #pragma unroll
         for (int l = 0; l < NL; ++l) {
             if constexpr (N == 2) dft2<T, INV>(v[l]);
@@ -309,8 +344,8 @@ __device__ __forceinline__ void fft_lines(C<T> (&v)[NL][8], C<T>* __restrict__ s
             }
         }
         if constexpr (L1 == LOGM) {
-            // the first stage was the only power-of-two stage (N = 3 * 8)
-            radix3_finish<T, INV, N, NL>(v, sm, region, L, w, t, tw);
+            // the first stage was the only power-of-two stage (N = 3 * 8, 5 * 8)
+            odd_finish<T, INV, N, NL>(v, sm, region, L, w, t, tw);
         } else {
             __syncthreads();
             read_canonical<T, N, NL>(v, sm, region, L, w, t);

@@ -14,7 +14,7 @@ struct MatvecView {
     TargetView tv;
     const C<T>* ainv;   // [nmat][3] alpha^-1
     const C<T>* spec;   // [Hz][Hy][Hx][6], scaled by 1/(Lx Ly Lz)
-    const C<T>* tw;     // twiddle table exp(-2 pi i m / 3072), kTwEntries entries
+    const C<T>* tw;     // twiddle tables exp(-2 pi i m / 3072) then exp(-2 pi i m / 5120)
     C<T>* Ay;           // [slots][3][P][Ly][K]
     C<T>* Bxy;          // [slots][3][P][Ly][Lx]
     int logW_y, logW_x, logW_z;  // tile widths (lines per CTA) of the passes

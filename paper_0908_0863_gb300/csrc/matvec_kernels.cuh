@@ -36,7 +36,8 @@
 // contiguous elements.  In P3 each thread carries the same column of all
 // three components, so the spectrum product happens in registers between
 // the forward and the inverse transforms.  Each kernel is compiled for every
-// line length N (2^a up to 1024 and 3 * 2^a from 24 to 768) and, for the
+// line length N (2^a up to 1024, 3 * 2^a from 24 to 768, 5 * 2^a from 40
+// to 640) and, for the
 // strided passes, every tile width (LOGW = 0..4 lines per CTA, log2), and
 // picked at launch, so all shared-memory addresses are compile-time offsets.
 #pragma once
@@ -517,8 +518,8 @@ int launch_p5(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t st) 
     return 0;
 }
 
-// every line length the passes are compiled for: 2^a (a = 1..10) and
-// 3 * 2^a (a = 3..8)
+// every line length the passes are compiled for: 2^a (a = 1..10), 3 * 2^a
+// (a = 3..8) and 5 * 2^a (a = 3..7)
 #define DDA_LEN_CASE(V, CALL) case V: { constexpr int LN = V; return CALL; }
 #define DDA_LEN_SWITCH(len, CALL)                                                        \
     switch (len) {                                                                       \
@@ -527,7 +528,8 @@ int launch_p5(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t st) 
         DDA_LEN_CASE(128, CALL) DDA_LEN_CASE(256, CALL) DDA_LEN_CASE(512, CALL)          \
         DDA_LEN_CASE(1024, CALL) DDA_LEN_CASE(24, CALL) DDA_LEN_CASE(48, CALL)           \
         DDA_LEN_CASE(96, CALL) DDA_LEN_CASE(192, CALL) DDA_LEN_CASE(384, CALL)           \
-        DDA_LEN_CASE(768, CALL)                                                          \
+        DDA_LEN_CASE(768, CALL) DDA_LEN_CASE(40, CALL) DDA_LEN_CASE(80, CALL)            \
+        DDA_LEN_CASE(160, CALL) DDA_LEN_CASE(320, CALL) DDA_LEN_CASE(640, CALL)          \
         default: return fail(DDA_ERR_ARG, "line length out of range");                   \
     }
 

@@ -1,4 +1,4 @@
-// Instantiations of the matvec pass P1 (expand + y-forward) for every line
+// Instantiations (complex FP64) of the matvec pass P1 (expand + y-forward) for every line
 // length and tile width, and its dispatcher.
 #include "matvec_kernels.cuh"
 
@@ -14,6 +14,5 @@ template <typename T> int pass1(const MatvecView<T>& mv, const C<T>* p, cudaStre
 }
 
 template int pass1<double>(const MatvecView<double>&, const C<double>*, cudaStream_t);
-template int pass1<float>(const MatvecView<float>&, const C<float>*, cudaStream_t);
 
 }  // namespace dda

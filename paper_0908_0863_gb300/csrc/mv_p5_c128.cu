@@ -1,4 +1,4 @@
-// Instantiations of the matvec pass P5 (y-inverse + diagonal + compress) for every line
+// Instantiations (complex FP64) of the matvec pass P5 (y-inverse + diagonal + compress) for every line
 // length and tile width, and its dispatcher.
 #include "matvec_kernels.cuh"
 
@@ -14,6 +14,5 @@ template <typename T> int pass5(const MatvecView<T>& mv, const C<T>* p, C<T>* y,
 }
 
 template int pass5<double>(const MatvecView<double>&, const C<double>*, C<double>*, cudaStream_t);
-template int pass5<float>(const MatvecView<float>&, const C<float>*, C<float>*, cudaStream_t);
 
 }  // namespace dda

@@ -87,7 +87,7 @@ def test_site_ranks_bit_exact(dda, shape):
 
 # ------------------------------------------------------------ tensor spectrum
 
-@pytest.mark.parametrize("shape", [(1, 1, 1), (4, 4, 4), (3, 5, 2), (9, 4, 5), (16, 8, 12)])
+@pytest.mark.parametrize("shape", [(1, 1, 1), (4, 4, 4), (3, 5, 2), (9, 4, 5), (16, 8, 12), (20, 10, 40)])
 def test_tensor_spectrum_matches_oracle(dda, shape):
     K, J, P = shape
     k = 0.7
@@ -183,10 +183,10 @@ def test_matvec_full_size_sampled_rows(dda, n, D):
 
 
 @pytest.mark.parametrize("box,D", [((96, 96, 96), 96), ((192, 160, 100), 100)])
-def test_matvec_radix3_lengths_sampled_rows(dda, box, D):
-    # lattices whose circulant lengths are 3 * 2^a (192 = 3 * 64 on all axes;
-    # 384, 384, 256): the radix-3 closing stage in every pass and in the
-    # spectrum build, against 24 direct sums
+def test_matvec_odd_radix_lengths_sampled_rows(dda, box, D):
+    # lattices whose circulant lengths are 3 * 2^a or 5 * 2^a (192 = 3 * 64 on
+    # all axes; 384, 320, 256): the radix-3 and radix-5 closing stages in
+    # every pass and in the spectrum build, against 24 direct sums
     m = 1.33 + 0.05j
     k = 0.5 / abs(m)
     mask = synth.sphere(D, box=box)
@@ -197,7 +197,7 @@ def test_matvec_radix3_lengths_sampled_rows(dda, box, D):
     ref = odda.direct_matvec_rows(case.coords, case.ainv, case.k, p, rows)
     with case.lattice() as lat:
         assert lat.padded == tuple(circulant.padded_length(v) for v in box)
-        assert any(v % 3 == 0 for v in lat.padded)
+        assert any(v % 3 == 0 or v % 5 == 0 for v in lat.padded)
     y = _matvec(dda, case, p, np.complex128)[:, rows]
     scale = np.abs(ref).max()
     assert np.abs(y - ref).max() <= 1e-11 * scale
