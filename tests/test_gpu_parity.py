@@ -205,6 +205,23 @@ def test_matvec_odd_radix_lengths_sampled_rows(dda, box, D):
     assert np.abs(y32 - ref).max() <= 5e-6 * scale
 
 
+@pytest.mark.parametrize("box", [(512, 6, 5), (5, 512, 6), (6, 5, 512)])
+def test_matvec_longest_lines(dda, box):
+    # a 512-site edge (the largest the library takes) gives 1024-point lines:
+    # along x through P2/P4, along y through P1/P5, along z through P3, with
+    # the other two axes short and ragged; every output against the direct sum
+    case = random_case(box, seed=sum(box), fill=0.5)
+    with case.lattice() as lat:
+        assert max(lat.padded) == 1024
+    p = synth.complex_normal(11, (3, case.nd))
+    rows = synth.rng(12).choice(case.nd, size=64, replace=False)
+    ref = odda.direct_matvec_rows(case.coords, case.ainv, case.k, p, rows)
+    y = _matvec(dda, case, p, np.complex128)[:, rows]
+    assert np.abs(y - ref).max() <= 1e-11 * np.abs(ref).max()
+    y32 = _matvec(dda, case, p, np.complex64)[:, rows]
+    assert np.abs(y32 - ref).max() <= 5e-6 * np.abs(ref).max()
+
+
 def test_matvec_rejects_host_and_aliased(dda):
     case = random_case((4, 4, 4), seed=1, two_materials=False)
     with case.lattice() as lat:
