@@ -39,7 +39,8 @@
  *   right-hand side in both precisions) and released by dda_free.  The
  *   workspace grows, once, when a call first needs more right-hand sides
  *   (or the first batch in a precision) than it holds; dda_reserve makes
- *   that allocation ahead of time.  No other call allocates device memory.
+ *   that allocation ahead of time.  Apart from that growth and the scratch
+ *   dda_autotune takes and frees, no call allocates device memory.
  * Errors: every int-returning call returns a dda_status; on failure
  *   dda_last_error() gives a message (thread local).  Arguments are
  *   checked before any work is queued; a failed call leaves outputs
@@ -155,7 +156,9 @@ int dda_unpack_composition(const uint32_t* bits, int64_t n_sites, int n_material
  * 0 <= k < P) and transforms them with the fused Toeplitz-to-circulant
  * line DFTs of Sec. 3 (x, then y, then z; mirrored halves signed per
  * Table 1; only L/2 + 1 outputs of each length-L line kept), in FP64, with
- * a complex64 copy.  L = smallest power of two >= 2n - 1 per axis.
+ * a complex64 copy.  L per axis = the smallest length >= 2n - 1 of the form
+ * 2^a, 3 * 2^a or 5 * 2^a (a >= 3 for the last two): the paper's
+ * K'' = 2K - 1 + kf with kf chosen for a fast DFT; dda_query reports it.
  * Returns DDA_ERR_ARG (bad shape, pointers, no occupied site, material
  * index out of range), DDA_ERR_OOM, DDA_ERR_CUDA.  *out is NULL on failure.
  * The call synchronises the stream before returning.
