@@ -270,7 +270,7 @@ def run_ours(args):
     if tuned:
         result["autotune"] = tuned
     if rank == 0 and not args.no_extras:
-        result.update(extras(args, dda, torch, dev, shape, bits, alpha, nd, pass_ms, khat, pols))
+        result.update(extras(args, dda, torch, dev, shape, bits, alpha, nd, pass_ms, khat, pols, mask))
     if rank == 0 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(args, nd, mask)
     if rank == 0:
@@ -335,7 +335,7 @@ def measured_traffic(kernel):
     return None
 
 
-def extras(args, dda, torch, dev, shape, bits, alpha, nd, pass_ms, khat, pols):
+def extras(args, dda, torch, dev, shape, bits, alpha, nd, pass_ms, khat, pols, mask):
     """Roofline of the dominant kernel, per-precision matvec rates, FP64 solve."""
     out = {}
     peaks = {}
@@ -411,6 +411,8 @@ def extras(args, dda, torch, dev, shape, bits, alpha, nd, pass_ms, khat, pols):
                                                                            meth, args)
         if args.batch > 0:
             out["batch"] = timed_batch(dda, torch, dev, ctx, nd, args)
+        if args.unpruned:
+            out["unpruned_cufft"] = timed_unpruned(dda, torch, dev, ctx, mask, alpha, nd)
     finally:
         dda.dda_free(ctx)
     return out
@@ -461,6 +463,111 @@ def timed_batch(dda, torch, dev, ctx, nd, args):
             "status": sorted(set(stats)), "gpu_launches": int(launches),
             "device_bytes": dda.dda_query(ctx)["device_bytes"],
             "c_ext_range": [float(cx[:, 0].min()), float(cx[:, 0].max())]}
+
+
+# --------------------------------------------- unpruned cuFFT comparison
+class UnprunedFFT:
+    """Same-GPU comparison arm: the product y = A p done with unpruned 3-D
+    FFTs (cuFFT, through torch.fft) on the whole zero-padded grid
+    2K x 2J x 2P -- three forward transforms of the padded components, the
+    6-component spectrum product of Eqs. 6-8 at every frequency, three
+    inverse transforms, then the diagonal alpha^-1 p (Sec. 3).  Nothing is
+    pruned: every transform runs over all lines of all three axes.  It builds
+    its own spectrum from the interaction tensor, so it also checks the
+    library's product independently.  Timed beside the library's path, never
+    used by it.
+
+    mask: bool [P][J][K] occupancy (x fastest); ainv: complex alpha^-1 per
+    occupied site and axis, shape [3][N_d] or broadcastable to it."""
+
+    def __init__(self, torch, dev, mask, ainv, k, cdtype):
+        import numpy as np
+        self.torch = torch
+        P, J, K = mask.shape
+        self.L = (2 * P, 2 * J, 2 * K)
+        self.cdtype = cdtype
+        z, y, x = np.nonzero(mask)     # C order = x-fastest site order
+        L0, L1, L2 = self.L
+        self.idx = torch.from_numpy((z * L1 + y) * L2 + x).to(dev)
+        self.ainv = torch.as_tensor(ainv, dtype=cdtype, device=dev)
+        self.Y = self._spectrum(torch, dev, (P, J, K), k)
+        self.X = torch.zeros((3,) + self.L, dtype=cdtype, device=dev)
+        self.Q = torch.empty_like(self.X)
+
+    def _spectrum(self, torch, dev, n, k):
+        """DFT of t = -G on the padded grid: displacement i for i < n,
+        i - 2n for i > n, zero at i = n (the extension element) and at r = 0."""
+        f64 = torch.float64
+        axes = []
+        for na, La in zip(n, self.L):
+            i = torch.arange(La, dtype=f64, device=dev)
+            d = torch.where(i < na, i, i - La)
+            axes.append((d, i == na))
+        (z, zn), (y, yn), (x, xn) = axes
+        z, y, x = z.view(-1, 1, 1), y.view(1, -1, 1), x.view(1, 1, -1)
+        r2 = z * z + y * y + x * x
+        dead = (r2 == 0) | zn.view(-1, 1, 1) | yn.view(1, -1, 1) | xn.view(1, 1, -1)
+        r2 = torch.where(dead, torch.ones_like(r2), r2)
+        r = torch.sqrt(r2)
+        ikr = torch.complex(torch.zeros_like(r), k * r)
+        e = torch.exp(ikr) / (r2 * r)
+        # G_ab = a delta_ab + b x_a x_b, t = -G
+        a = -(e * (k * k * r2 - 1.0 + ikr))
+        b = -(e * ((3.0 - 3.0 * ikr) / r2 - k * k))
+        a = torch.where(dead, torch.zeros_like(a), a)
+        b = torch.where(dead, torch.zeros_like(b), b)
+        del r, ikr, e
+        comp = {"x": x, "y": y, "z": z}
+        Y = []
+        for m in ("xx", "xy", "xz", "yy", "yz", "zz"):
+            t = b * (comp[m[0]] * comp[m[1]])
+            if m[0] == m[1]:
+                t = t + a
+            Y.append(torch.fft.fftn(t.to(self.cdtype), dim=(0, 1, 2)))
+            del t
+        return Y
+
+    def matvec(self, p):
+        torch = self.torch
+        X, Q, Y = self.X, self.Q, self.Y
+        X.zero_()
+        X.view(3, -1)[:, self.idx] = p
+        F = torch.fft.fftn(X, dim=(1, 2, 3))
+        for a, row in enumerate(((0, 1, 2), (1, 3, 4), (2, 4, 5))):
+            torch.mul(Y[row[0]], F[0], out=Q[a])
+            Q[a].addcmul_(Y[row[1]], F[1])
+            Q[a].addcmul_(Y[row[2]], F[2])
+        del F
+        q = torch.fft.ifftn(Q, dim=(1, 2, 3))
+        return self.ainv * p + q.view(3, -1)[:, self.idx]
+
+
+def timed_unpruned(dda, torch, dev, ctx, mask, alpha, nd):
+    """ms per product of the unpruned cuFFT arm against the library's
+    product on the same random p, with their relative difference."""
+    out = {}
+    ainv = torch.full((3, 1), 1.0 / complex(alpha[0, 0]), dtype=torch.complex128)
+    for name, dtype, reps in (("c64", torch.complex64, 5), ("c128", torch.complex128, 2)):
+        arm = UnprunedFFT(torch, dev, mask, ainv, K_WAVE, dtype)
+        p = torch.randn((3, nd), dtype=dtype, device=dev)
+        y = torch.empty_like(p)
+        dda.dda_matvec(ctx, p, y)
+        z = arm.matvec(p)
+        torch.cuda.synchronize(dev)
+        diff = float((z - y).norm() / y.norm())
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            arm.matvec(p)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"ms": ms, "matvecs_per_s": 1e3 / ms, "rel_diff_vs_library": diff}
+        del arm, p, y, z
+        torch.cuda.empty_cache()
+    out["what"] = ("unpruned 3-D cuFFT (torch.fft) on the whole padded grid: 3 forward + 6-component "
+                   "spectrum product + 3 inverse, scatter/gather and diagonal included; not the product path")
+    return out
 
 
 # ------------------------------------------------------------ aggregates
@@ -662,6 +769,8 @@ def main():
     ap.add_argument("--also-methods", default="", help="comma-separated methods to time one mixed solve each")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the default tile widths instead of tuning them before the warm-up")
+    ap.add_argument("--no-unpruned", dest="unpruned", action="store_false",
+                    help="skip the unpruned cuFFT comparison extra")
     ap.add_argument("--batch", type=int, default=16, help="right-hand sides of the batched-solve extra (0: skip)")
     ap.add_argument("--workload", default="sphere256", choices=["sphere256", "aggregates"],
                     help="sphere256: the headline metric; aggregates: the batched orientation-averaging workload")

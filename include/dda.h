@@ -233,8 +233,9 @@ int dda_tiles(dda_ctx* ctx, int dtype, int* tiles_out, const int* tiles_in);
 
 /*
  * Autotune the tile settings of dtype on this context: starting from the
- * current ones, try up to two width steps either way for P3, then both z
- * pass schedules, then up to two steps for P1/P5 and for P2/P4, timing
+ * current ones, try every z pass schedule with P3 widths up to two steps
+ * either way of the current one, then up to two width steps for P1/P5 and
+ * for P2/P4, timing
  * `reps` batched products of nb right-hand sides per
  * candidate with CUDA events (after one untimed product), and keep the
  * fastest.  The choice is set on the context and remembered for the

@@ -755,23 +755,21 @@ int dda_autotune(dda_ctx* c, int dtype, int nb, int reps, double* pass_ms, void*
     int rc = e == cudaSuccess ? 0 : cuda_fail(e, "dda_autotune: fill");
     double best_ms[5] = {};
     if (!rc) rc = time_tiles(best_ms);
-    // one coordinate at a time: P3's width (index 1), P3's schedule (3),
-    // P1/P5's width (0), then P2/P4's (2)
-    const int order[4] = {1, 3, 0, 2};
-    for (int oi = 0; oi < 4 && !rc; ++oi) {
-        const int a = order[oi];
+    // P3's width (index 1) and schedule (3) together, then P1/P5's width
+    // (0), then P2/P4's (2)
+    for (int a : {1, 0, 2}) {
+        if (rc) break;
         std::array<int, 4> best = current();
-        auto cost = [&](const double (&m)[5]) {
-            return (a == 1 || a == 3) ? m[2] : a == 0 ? m[0] + m[4] : m[1] + m[3];
-        };
+        auto cost = [&](const double (&m)[5]) { return a == 1 ? m[2] : a == 0 ? m[0] + m[4] : m[1] + m[3]; };
         double best_cost = cost(best_ms);
-        const int center = best[a];
-        const int lo = a == 3 ? 0 : std::max(0, center - 2), hi = a == 3 ? 1 : center + 2;
-        for (int v = lo; v <= hi && !rc; ++v) {
-            if (v == center) continue;
-            std::array<int, 4> t = best;
-            t[a] = v;
-            if (!valid(t)) continue;
+        const std::array<int, 4> start = best;
+        const int center = start[a];
+        for (int cand = 0; cand < 5 * kP3Schedules && !rc; ++cand) {
+            std::array<int, 4> t = start;
+            t[a] = center - 2 + cand % 5;
+            if (a == 1) t[3] = cand / 5;
+            else if (cand >= 5) break;
+            if (t == start || t[a] < 0 || !valid(t)) continue;
             set(t);
             double m[5];
             rc = time_tiles(m);

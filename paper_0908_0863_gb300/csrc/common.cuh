@@ -33,7 +33,6 @@ template <typename T> __host__ __device__ __forceinline__ C<T> cfma(C<T> a, C<T>
 }
 
 // --------------------------------------------------------------- limits
-constexpr int kMaxLine = 1024;      // longest padded line (lattice edge <= 512)
 constexpr int kTwEntries = 3072 + 5120;   // twiddle tables exp(-2 pi i m / 3072) and exp(-2 pi i m / 5120)
 constexpr int kMaxEdge = 512;
 

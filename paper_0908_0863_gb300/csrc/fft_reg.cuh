@@ -33,7 +33,7 @@
 //
 // Shared-memory addresses come from a layout functor (line w, point p):
 // RowLayout keeps each line contiguous (lines of the lattice that are
-// contiguous in memory, threads t-fastest); ColLayout keeps point-major
+// contiguous in memory, threads t-fastest); ColLayoutT keeps point-major
 // tiles of 2^logW lines side by side (strided lines of the lattice, threads
 // w-fastest).
 //
@@ -71,19 +71,16 @@ struct RowLayout {
     static constexpr int ld = N + N / 16 + 1;
     __device__ __forceinline__ int operator()(int w, int p) const { return w * ld + p + (p >> 4); }
 };
-struct ColLayout {
-    int logW;  // 2^logW lines per tile; one pad row after every 8 points
-    __device__ __forceinline__ int operator()(int w, int p) const { return ((p + (p >> 3)) << logW) + w; }
-};
-// the same layout with the tile width fixed at compile time, so that every
-// exchange address folds into a constant offset from the thread's base
+// 2^LOGW lines per tile, one pad row after every 8 points; the width is a
+// compile-time constant, so every exchange address folds into a constant
+// offset from the thread's base
 template <int LOGW>
 struct ColLayoutT {
     __device__ __forceinline__ int operator()(int w, int p) const { return ((p + (p >> 3)) << LOGW) + w; }
 };
 
 __host__ __device__ constexpr int row_ld(int N) { return N + N / 16 + 1; }
-// elements of a ColLayout tile of W lines of N points
+// elements of a ColLayoutT tile of W lines of N points
 __host__ __device__ constexpr int col_elems(int N, int W) { return (N + N / 8) * W; }
 
 template <typename T, bool INV>

@@ -7,7 +7,7 @@ namespace dda {
 
 template <typename T>
 bool tiles_ok(const Geometry& g, int logW_y, int logW_z, int logW_x, int p3_sched) {
-    if (p3_sched != 0 && p3_sched != 1) return false;
+    if (p3_sched < 0 || p3_sched >= kP3Schedules) return false;
     if (p3_sched == 1 && (logW_z < 0 || logW_z > kMaxLogW || !p3_persistent_ok<T>(g, logW_z))) return false;
     const int elt = sizeof(C<T>);
     const int ty = threads_of(g.Ly), tz = threads_of(g.Lz), tx = threads_of(g.Lx);

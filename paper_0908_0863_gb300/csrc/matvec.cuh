@@ -6,7 +6,7 @@
 
 namespace dda {
 
-__device__ __forceinline__ int ilog2_dev(int n) { return 31 - __clz(n); }
+constexpr int kP3Schedules = 2;   // z pass schedules (MatvecView::p3_sched)
 
 template <typename T>
 struct MatvecView {

@@ -190,6 +190,30 @@ __device__ __forceinline__ int p3_row(int b, int Ly) {
     return b == 0 ? 0 : ((b & 1) ? q2 : Ly - q2);
 }
 
+// the spectrum product of Eqs. 6-8 at z point n of the column whose mirrored
+// spectrum row starts at spec (flips fx, fy of the x and y mirrors): one
+// 48-byte load of the six components, the Table-1 signs, then
+// (X0, X1, X2) <- Y (X0, X1, X2)
+template <typename T, int N>
+__device__ __forceinline__ void p3_product(const C<T>* __restrict__ spec, int64_t zstep, bool ok, int fx, int fy,
+                                           int n, C<T>& X0, C<T>& X1, C<T>& X2) {
+    const int mz = n <= N / 2 ? n : N - n, fz = n > N / 2;
+    C<T> Y[6];
+    if (ok) {
+        load6<T>(spec + mz * zstep, Y);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) Y[q] = mk<T>(0, 0);
+    }
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+        if (mirror_flip(q, fx, fy, fz)) { Y[q].x = -Y[q].x; Y[q].y = -Y[q].y; }
+    const C<T> a = X0, b = X1, c = X2;
+    X0 = cfma<T>(Y[2], c, cfma<T>(Y[1], b, cmul<T>(Y[0], a)));
+    X1 = cfma<T>(Y[4], c, cfma<T>(Y[3], b, cmul<T>(Y[1], a)));
+    X2 = cfma<T>(Y[5], c, cfma<T>(Y[4], b, cmul<T>(Y[2], a)));
+}
+
 // One tile of W columns (x = xt W + w, row jy, batch slot j) whose inputs v
 // (the P nonzero z points of the three components, canonical order) are
 // loaded: forward z DFTs, the spectrum product of Eqs. 6-8 with the signed
@@ -214,24 +238,8 @@ __device__ __forceinline__ void p3_tile(const MatvecView<T>& mv, C<T>* sm, int j
         const C<T>* spec = mv.spec + ((int64_t)my * g.Hx + (ok ? mx : 0)) * 6;
         const int64_t zstep = (int64_t)g.Hy * g.Hx * 6;
 #pragma unroll
-        for (int m = 0; m < nv; ++m) {
-            const int n = t + m * TL;
-            const int mz = n <= N / 2 ? n : N - n, fz = n > N / 2;
-            C<T> Y[6];
-            if (ok) {
-                load6<T>(spec + mz * zstep, Y);
-            } else {
-#pragma unroll
-                for (int q = 0; q < 6; ++q) Y[q] = mk<T>(0, 0);
-            }
-#pragma unroll
-            for (int q = 0; q < 6; ++q)
-                if (mirror_flip(q, fx, fy, fz)) { Y[q].x = -Y[q].x; Y[q].y = -Y[q].y; }
-            const C<T> X0 = v[0][m], X1 = v[1][m], X2 = v[2][m];
-            v[0][m] = cfma<T>(Y[2], X2, cfma<T>(Y[1], X1, cmul<T>(Y[0], X0)));
-            v[1][m] = cfma<T>(Y[4], X2, cfma<T>(Y[3], X1, cmul<T>(Y[1], X0)));
-            v[2][m] = cfma<T>(Y[5], X2, cfma<T>(Y[4], X1, cmul<T>(Y[2], X0)));
-        }
+        for (int m = 0; m < nv; ++m)
+            p3_product<T, N>(spec, zstep, ok, fx, fy, t + m * TL, v[0][m], v[1][m], v[2][m]);
     }
     fft_lines<T, true, N, 3, false, true>(v, sm, region, L, w, t, mv.tw);
     if (ok) {

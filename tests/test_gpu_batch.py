@@ -281,8 +281,10 @@ def test_aggregate_200_monomers_sampled_rows(dda):
 # --------------------------------------------------------------- tiles
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
-def test_tile_widths_do_not_change_results(dda, dtype):
-    case = random_case((21, 13, 9), seed=41, fill=0.6)
+@pytest.mark.parametrize("shape", [(21, 13, 9), (40, 20, 64)])
+def test_tile_widths_do_not_change_results(dda, dtype, shape):
+    # padded z lines of 24 (3 * 2^3) and 128 points
+    case = random_case(shape, seed=41, fill=0.6)
     tdt = torch.complex128 if dtype == "c128" else torch.complex64
     p = torch.from_numpy(synth.complex_normal(42, (2, 3, case.nd))).to(DEV).to(tdt)
     with case.lattice() as lat:
@@ -326,7 +328,8 @@ def test_persistent_z_pass_in_batched_solves(dda, dtype):
             assert status == dda.DDA_OK, stats
             out.append((P.clone(), [i["iterations"] for i in infos]))
         lat.tiles(dtype, base)
-    assert torch.equal(out[0][0], out[1][0])
+    for other in out[1:]:
+        assert torch.equal(out[0][0], other[0])
     assert out[0][1] == out[1][1]
 
 
@@ -337,6 +340,11 @@ def test_tile_limits_rejected(dda):
         with pytest.raises(dda.DDAError) as e:
             lat.tiles("c64", (base[0], 12, base[2], 0))     # 4096 columns x 4 threads per CTA
         assert e.value.code == dda.DDA_ERR_ARG
+        assert lat.tiles("c64") == base
+        for sched in (-1, 2):                                  # no such schedule
+            with pytest.raises(dda.DDAError) as e:
+                lat.tiles("c64", (base[0], base[1], base[2], sched))
+            assert e.value.code == dda.DDA_ERR_ARG
         assert lat.tiles("c64") == base
 
 
