@@ -47,6 +47,7 @@
 
 #include "fft_reg.cuh"
 #include "matvec.cuh"
+#include "mbarrier.cuh"
 
 namespace dda {
 
@@ -166,6 +167,24 @@ __device__ __forceinline__ int mirror_flip(int m, int fx, int fy, int fz) {
 }
 
 // the six spectrum components of one point (contiguous) with 16-byte loads
+// from shared memory
+template <typename T>
+__device__ __forceinline__ void load6_shared(const C<T>* p, C<T> (&Y)[6]) {
+    if (sizeof(T) == 4) {
+        const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float4 f = q[i];
+            Y[2 * i] = mk<T>(f.x, f.y);
+            Y[2 * i + 1] = mk<T>(f.z, f.w);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) Y[i] = p[i];
+    }
+}
+
+// the same from global memory (read-only path)
 template <typename T>
 __device__ __forceinline__ void load6(const C<T>* __restrict__ p, C<T> (&Y)[6]) {
     if (sizeof(T) == 4) {
@@ -191,16 +210,18 @@ __device__ __forceinline__ int p3_row(int b, int Ly) {
 }
 
 // the spectrum product of Eqs. 6-8 at z point n of the column whose mirrored
-// spectrum row starts at spec (flips fx, fy of the x and y mirrors): one
+// spectrum row starts at spec (flips fx, fy of the x and y mirrors; entry mz
+// at spec + mz zstep, in global memory or, SHARED, in a staged copy): one
 // 48-byte load of the six components, the Table-1 signs, then
 // (X0, X1, X2) <- Y (X0, X1, X2)
-template <typename T, int N>
+template <typename T, int N, bool SHARED = false>
 __device__ __forceinline__ void p3_product(const C<T>* __restrict__ spec, int64_t zstep, bool ok, int fx, int fy,
                                            int n, C<T>& X0, C<T>& X1, C<T>& X2) {
     const int mz = n <= N / 2 ? n : N - n, fz = n > N / 2;
     C<T> Y[6];
     if (ok) {
-        load6<T>(spec + mz * zstep, Y);
+        if constexpr (SHARED) load6_shared<T>(spec + mz * zstep, Y);
+        else load6<T>(spec + mz * zstep, Y);
     } else {
 #pragma unroll
         for (int q = 0; q < 6; ++q) Y[q] = mk<T>(0, 0);
@@ -278,6 +299,100 @@ __global__ void __launch_bounds__(p3_max_threads<T>(), 1) k_p3(MatvecView<T> mv)
             v[c][m] = (ok && m < nv && n < g.P) ? col[c * comp + n * plane] : mk<T>(0, 0);
         }
     p3_tile<T, N, LOGW>(mv, sm, j, xt, jy, v);
+}
+
+// Staged schedule: per tile, warp 0 first issues one bulk copy per z entry
+// mz <= N/2 of the tile's spectrum rows -- the x mirrors lo..hi of its
+// columns at the row's y mirror, (hi - lo + 1) x 48 contiguous bytes -- into
+// a shared stage; the copies run while the tile loads its columns and does
+// the forward z DFTs.  The product of Eqs. 6-8 then reads the stage instead
+// of global memory, and each spectrum entry crosses L2 once per tile
+// instead of once per point (points n and N - n share one).  If the copies
+// never complete (a wait gives up), the tile's output is zeros and the error
+// word is set for the host.
+template <typename T, int N, int LOGW>
+__host__ __device__ constexpr size_t p3_staged_smem() {
+    return (3 * (size_t)col_elems(N, 1 << LOGW) + (size_t)(N / 2 + 1) * (1 << LOGW) * 6) * sizeof(C<T>) + 16;
+}
+// compiled for complex64 lines of 64 points or more
+template <typename T, int N>
+__host__ __device__ constexpr bool p3_staged_compiled() {
+    return sizeof(T) == 4 && N >= 64;
+}
+
+template <typename T, int N, int LOGW>
+__global__ void __launch_bounds__(p3_max_threads<T>(), 1) k_p3b(MatvecView<T> mv) {
+    const int j = blockIdx.x, xt = blockIdx.y;                  // batch slot, column tile
+    if (rhs_done(mv, mv.b0 + j)) return;                        // the same for the whole CTA
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
+    constexpr int TL = Line<N>::T, nv = Line<N>::NV;
+    constexpr int W = 1 << LOGW, HZ = N / 2 + 1, region = col_elems(N, W);
+    C<T>* stage = sm + 3 * region;                                // [HZ][W][6]
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(stage + (size_t)HZ * W * 6);
+    const Geometry& g = mv.g;
+    const int w = threadIdx.x & (W - 1), t = threadIdx.x >> LOGW;
+    const int jy = p3_row(blockIdx.z, g.Ly);
+    const int ix = xt * W + w;
+    const bool ok = ix < g.Lx;
+    const int my = jy <= g.Ly / 2 ? jy : g.Ly - jy, fy = jy > g.Ly / 2;
+    const int mx = ix <= g.Lx / 2 ? ix : g.Lx - ix, fx = ix > g.Lx / 2;
+    // x mirrors of the tile's columns: one contiguous range of at most W
+    int lo = g.Lx, hi = -1;
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+        const int i = xt * W + q;
+        if (i < g.Lx) {
+            const int m = i <= g.Lx / 2 ? i : g.Lx - i;
+            lo = m < lo ? m : lo;
+            hi = m > hi ? m : hi;
+        }
+    }
+    const unsigned row = (unsigned)(hi - lo + 1) * 6u * (unsigned)sizeof(C<T>);
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_arrive_expect(bar, row * HZ);   // posted before any copy is issued
+    }
+    __syncthreads();
+    // the first min(32, blockDim.x) threads issue the HZ row copies
+    constexpr int issuers = W * TL < 32 ? W * TL : 32;
+    if (threadIdx.x < issuers) {
+        const C<T>* src = mv.spec + ((int64_t)my * g.Hx + lo) * 6;
+        const int64_t zstep = (int64_t)g.Hy * g.Hx * 6;
+        for (int mz = threadIdx.x; mz < HZ; mz += issuers)
+            bulk_to_shared(stage + mz * W * 6, src + mz * zstep, row, bar);
+    }
+    const int64_t plane = (int64_t)g.Ly * g.Lx, comp = (int64_t)g.P * plane;
+    C<T>* col = mv.Bxy + j * bxy_elems(g) + (int64_t)jy * g.Lx + (ok ? ix : 0);
+    C<T> v[3][8];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const int n = t + m * TL;
+            v[c][m] = (ok && m < nv && n < g.P) ? col[c * comp + n * plane] : mk<T>(0, 0);
+        }
+    const ColLayoutT<LOGW> L{};
+    fft_lines<T, false, N, 3, true, false>(v, sm, region, L, w, t, mv.tw);
+    const bool ready = mbar_wait(bar, 0);
+    if (!ready && mv.err) atomicOr(mv.err, 1);
+    {
+        const C<T>* spec = stage + (ok ? mx - lo : 0) * 6;
+#pragma unroll
+        for (int m = 0; m < nv; ++m)
+            p3_product<T, N, true>(spec, W * 6, ok && ready, fx, fy, t + m * TL, v[0][m], v[1][m], v[2][m]);
+    }
+    fft_lines<T, true, N, 3, false, true>(v, sm, region, L, w, t, mv.tw);
+    if (ok) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int m = 0; m < nv; ++m) {
+                const int n = t + m * TL;
+                if (n < g.P) col[c * comp + n * plane] = v[c][m];
+            }
+    }
+    if (!ready) mbar_wait(bar, 0);   // copies still in flight land before the CTA's shared memory is released
 }
 
 // Persistent schedule: each CTA walks the tiles q = blockIdx.x, + gridDim.x,
@@ -504,10 +619,21 @@ int launch_p3(const MatvecView<T>& mv, cudaStream_t st) {
         DDA_LAUNCH_CHECK("P3 z-forward, spectrum product, z-inverse (persistent)");
         return 0;
     }
+    dim3 grid(mv.nb, (g.Lx + W - 1) / W, g.Ly);
+    if constexpr (p3_staged_compiled<T, N>()) {
+        if (mv.p3_sched == 2) {
+            constexpr size_t sm = p3_staged_smem<T, N, LOGW>();
+            if (sm > kMaxSmem) return fail(DDA_ERR_ARG, "P3 staged schedule: shared memory exceeded");
+            static std::atomic<size_t> smem_set{0};
+            if (int rc = set_smem((const void*)k_p3b<T, N, LOGW>, sm, smem_set)) return rc;
+            k_p3b<T, N, LOGW><<<grid, threads, sm, st>>>(mv);
+            DDA_LAUNCH_CHECK("P3 z-forward, spectrum product, z-inverse (staged spectrum)");
+            return 0;
+        }
+    }
     const size_t sm = 3 * (size_t)col_elems(N, W) * sizeof(C<T>);
     static std::atomic<size_t> smem_set{0};
     if (int rc = set_smem((const void*)k_p3<T, N, LOGW>, sm, smem_set)) return rc;
-    dim3 grid(mv.nb, (g.Lx + W - 1) / W, g.Ly);
     k_p3<T, N, LOGW><<<grid, threads, sm, st>>>(mv);
     DDA_LAUNCH_CHECK("P3 z-forward, spectrum product, z-inverse");
     return 0;
