@@ -294,7 +294,7 @@ def algorithmic_bytes(n, nd, esize):
 
 # what the P3 traffic figure depends on: the P3 section of the kernel header
 # (from its P3 banner to the P5 banner) and the headers it includes
-KERNEL_SOURCES = ("fft_reg.cuh", "fft.cuh", "matvec.cuh", "common.cuh", "mbarrier.cuh")
+KERNEL_SOURCES = ("fft_reg.cuh", "fft.cuh", "matvec.cuh", "common.cuh")
 P3_SECTION = ("// ---------------------------------------------------------------- P3",
               "// ---------------------------------------------------------------- P5")
 

@@ -222,10 +222,7 @@ int dda_matvec_batch(dda_ctx* ctx, int nb, const void* p, void* y, int dtype, vo
  * P1/P5 (y lines), P3 (z columns) and P2/P4 (x rows); tiles[3] = the z
  * pass schedule, 0 = one CTA per tile of columns, 1 = persistent CTAs that
  * stage the next tile's input columns in shared memory (cp.async) while
- * transforming the current one (whole tiles and 16-byte stage rows only),
- * 2 = one CTA per tile whose spectrum rows are staged in shared memory by
- * bulk asynchronous copies during its forward transforms (DDA_C64, z lines
- * of 64 points or more, stage and exchange buffers within 227 KB).
+ * transforming the current one (whole tiles and 16-byte stage rows only).
  * tiles_in (may be NULL) sets them after checking the launch limits
  * (threads per block, shared memory; DDA_ERR_ARG when exceeded);
  * tiles_out (may be NULL) receives the current ones.  The settings only
@@ -249,22 +246,6 @@ int dda_tiles(dda_ctx* ctx, int dtype, int* tiles_out, const int* tiles_in);
  * Synchronises the stream.
  */
 int dda_autotune(dda_ctx* ctx, int dtype, int nb, int reps, double* pass_ms, void* stream);
-
-/*
- * Device-side waits.  Kernels that wait for their own asynchronous copies
- * (the staged z pass, tiles[3] = 2) give up after a bounded number of tries
- * (about a second) instead of spinning on; they then write zeros for their
- * tile and set a device error word.  The next synchronising call on the
- * context -- dda_solve, dda_solve_batch, dda_gradient,
- * dda_cross_sections(_batch), dda_autotune -- returns DDA_ERR_CUDA for it and
- * clears the word; the context stays usable.  This call checks the word on
- * demand (synchronising the stream) and clears it: DDA_OK, or DDA_ERR_CUDA
- * when a wait gave up since the last check.  probe = 1 first runs one
- * thread block whose wait has nothing to wait for, so that the give-up path
- * itself is exercised: the call then takes about a second and returns
- * DDA_ERR_CUDA.
- */
-int dda_device_wait_status(dda_ctx* ctx, int probe, void* stream);
 
 /*
  * Grow the solve workspace to hold nb right-hand sides (1 <= nb <= 4096)

@@ -17,7 +17,7 @@ from ._lib import (  # noqa: F401
     DDA_ERR_CUDA, DDA_PRECOND_JACOBI, DDA_QMR_SYM, DDA_TFQMR, method_code,
     DDA_ERR_NAN, DDA_ERR_NOT_CONVERGED, DDA_ERR_OOM, DDA_FP64, DDA_MIXED, DDA_OK, DDA_QMR, EXPORTS, DDAError,
     dda_cross_sections, dda_cross_sections_batch, dda_free, dda_gradient, dda_incident_field, dda_init_lattice,
-    dda_last_error, dda_matvec_batch, dda_reserve, dda_solve_batch, dda_tiles, dda_autotune, dda_device_wait_status,
+    dda_last_error, dda_matvec_batch, dda_reserve, dda_solve_batch, dda_tiles, dda_autotune,
     dda_launch_count, dda_polarizability_derivative, dda_scattering_cross_section,
     dda_matvec, dda_occupancy_ranks_static, dda_pack_composition, dda_pack_occupancy, dda_polarizability,
     dda_profile, dda_profile_read,
@@ -69,9 +69,6 @@ class Lattice:
 
     def tiles(self, dtype="c64", tiles=None):
         return dda_tiles(self.ctx, dtype, tiles)
-
-    def device_wait_status(self, probe=False, stream=None):
-        return dda_device_wait_status(self.ctx, probe, stream)
 
     def autotune(self, dtype="c64", nb=1, reps=3, stream=None):
         return dda_autotune(self.ctx, dtype, nb, reps, stream)

@@ -58,7 +58,7 @@ EXPORTS = (
     "dda_profile", "dda_profile_read", "dda_launch_count", "dda_last_error", "dda_occupancy_ranks_static",
     "dda_scattering_cross_section", "dda_polarizability_derivative", "dda_gradient",
     "dda_matvec_batch", "dda_reserve", "dda_solve_batch", "dda_cross_sections_batch", "dda_tiles",
-    "dda_autotune", "dda_device_wait_status",
+    "dda_autotune",
 )
 
 
@@ -121,7 +121,6 @@ def load(path: str | None = None):
     L.dda_gradient.argtypes = [vp, i32, vp, vp, vp, i32, i32, d, i32, vp, ctypes.POINTER(SolveInfo), vp]
     L.dda_profile.argtypes = [vp, i32]
     L.dda_profile_read.argtypes = [vp, vp, vp]
-    L.dda_device_wait_status.argtypes = [vp, i32, vp]
     L.dda_launch_count.argtypes = []
     L.dda_launch_count.restype = ctypes.c_int64
     L.dda_last_error.argtypes = []
@@ -260,7 +259,7 @@ def _dtype_name(dtype):
 
 def dda_tiles(ctx, dtype="c64", tiles=None):
     """Current tile settings (log2 lines per CTA of P1/P5, P3, P2/P4, and the
-    z pass schedule 0/1/2); sets them first when given (3 widths keep the
+    z pass schedule 0/1); sets them first when given (3 widths keep the
     schedule)."""
     out = np.zeros(4, dtype=np.int32)
     tin = None
@@ -385,12 +384,6 @@ def dda_profile_read(ctx):
     _check(load().dda_profile_read(ctypes.c_void_p(ctx), _ptr(counts), _ptr(ms)))
     return {name: [(int(counts[d * 5 + q]), float(ms[d * 5 + q])) for q in range(5)]
             for d, name in ((0, "c128"), (1, "c64"))}
-
-
-def dda_device_wait_status(ctx, probe=False, stream=None):
-    """Raise DDAError (DDA_ERR_CUDA) when a device-side wait gave up since
-    the last check; probe=True first makes one wait give up on purpose."""
-    _check(load().dda_device_wait_status(ctypes.c_void_p(ctx), int(bool(probe)), _stream(stream)))
 
 
 def dda_launch_count() -> int:

@@ -126,7 +126,6 @@ struct dda_ctx {
     double2* xsec = nullptr;
     double2* aux[3] = {};     // adjoint / C_sca work vectors (P, right-hand side, mu)
     double2* dainv64 = nullptr;  // d(alpha^-1)/d eps table of the last gradient call
-    int* dev_err = nullptr;      // device word set by a kernel whose bounded wait gave up
     Space sp;
     MatvecView<double> mv64{};   // geometry, tables and tiles; work set per call
     MatvecView<float> mv32{};
@@ -148,19 +147,6 @@ TargetView target_view(const dda_ctx* c) {
 int check_ctx(const dda_ctx* c) {
     if (!c) return fail(DDA_ERR_ARG, "null context");
     return 0;
-}
-
-// Reports (and clears) the device error word at a point where the stream is
-// synchronised: a kernel whose bounded wait gave up has left invalid
-// results in the products enqueued since the last check.
-int check_device_wait(dda_ctx* c, cudaStream_t st) {
-    int h = 0;
-    DDA_CUDA_TRY(cudaMemcpyAsync(&h, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    DDA_CUDA_TRY(cudaStreamSynchronize(st));
-    if (!h) return 0;
-    DDA_CUDA_TRY(cudaMemsetAsync(c->dev_err, 0, sizeof(int), st));
-    return fail(DDA_ERR_CUDA, "a device-side wait gave up (staged copies did not complete): the products enqueued "
-                              "since the last check are invalid");
 }
 
 int check_dev(const void* p, const char* what) {
@@ -519,8 +505,7 @@ int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occu
     c->tw64 = a0.take<double2>(kTwEntries);
     c->tw32 = a0.take<float2>(kTwEntries);
     c->xsec = a0.take<double2>(xsec_scratch_elems());
-    int* flags = a0.take<int>(4);   // [0] composition check, [1] site count, [2] device wait error
-    c->dev_err = flags + 2;
+    int* flags = a0.take<int>(4);
     c->bytes_fixed = (int64_t)a0.cap;
     int rc = 0;
     auto bail = [&](int code) { dda_free(c); return code; };
@@ -611,11 +596,11 @@ int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occu
         const TargetView tv = target_view(c);
         MatvecView<double>& m = c->mv64;
         m.g = g; m.tv = tv; m.ainv = c->ainv64; m.spec = c->spec64; m.tw = c->tw64;
-        m.status = nullptr; m.conj = 0; m.prof = &c->prof; m.err = c->dev_err;
+        m.status = nullptr; m.conj = 0; m.prof = &c->prof;
         configure_matvec<double>(m);
         MatvecView<float>& f = c->mv32;
         f.g = g; f.tv = tv; f.ainv = c->ainv32; f.spec = c->spec32; f.tw = c->tw32;
-        f.status = nullptr; f.conj = 0; f.prof = &c->prof; f.err = c->dev_err;
+        f.status = nullptr; f.conj = 0; f.prof = &c->prof;
         configure_matvec<float>(f);
         std::lock_guard<std::mutex> lock(g_tiles_mu);
         auto it = g_tiles.find(tile_key(g, DDA_C128));
@@ -800,22 +785,12 @@ int dda_autotune(dda_ctx* c, int dtype, int nb, int reps, double* pass_ms, void*
     cudaStreamSynchronize(st);
     cudaFree(buf);
     if (rc) return rc;
-    if ((rc = check_device_wait(c, st))) return rc;
     {
         std::lock_guard<std::mutex> lock(g_tiles_mu);
         g_tiles[tile_key(c->g, dtype)] = current();
     }
     if (pass_ms) std::copy(best_ms, best_ms + 5, pass_ms);
     return DDA_OK;
-}
-
-int dda_device_wait_status(dda_ctx* c, int probe, void* stream) {
-    if (int rc = check_ctx(c)) return rc;
-    if (probe != 0 && probe != 1) return fail(DDA_ERR_ARG, "dda_device_wait_status: probe must be 0 or 1");
-    cudaStream_t st = as_stream(stream);
-    if (probe)
-        if (int rc = launch_wait_probe(c->dev_err, st)) return rc;
-    return check_device_wait(c, st);
 }
 
 int dda_reserve(dda_ctx* c, int nb, int precision) {
@@ -1039,7 +1014,6 @@ int dda_solve_batch(dda_ctx* c, int nb, const void* einc, void* p, int method, i
     if (int rc = solve_batch(c, nb, einc, p, method, precision, tol, max_iter, use_x0, inf.data(), stat.data(),
                              as_stream(stream)))
         return rc;
-    if (int rc = check_device_wait(c, as_stream(stream))) return rc;
     const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     for (int b = 0; b < nb; ++b) {
         inf[b].seconds = sec;
@@ -1135,7 +1109,6 @@ int dda_gradient(dda_ctx* c, int which, const void* einc, const void* p, const d
     if (int rc = launch_gradient(target_view(c), c->g, c->k, which, c->dainv64, P, mu, g, st)) return rc;
     if (!dev_out) DDA_CUDA_TRY(cudaMemcpyAsync(grad, g, nd * sizeof(double2), cudaMemcpyDeviceToHost, st));
     DDA_CUDA_TRY(cudaStreamSynchronize(st));
-    if (int rc = check_device_wait(c, st)) return rc;
     return status;
 }
 
@@ -1168,7 +1141,6 @@ int dda_cross_sections_batch(dda_ctx* c, int nb, const void* einc, const void* p
                                      cudaMemcpyDeviceToHost, st));
     }
     DDA_CUDA_TRY(cudaStreamSynchronize(st));
-    if (int rc = check_device_wait(c, st)) return rc;
     const double f = 4.0 * M_PI * c->k;
     for (int b = 0; b < nb; ++b) {
         out[3 * b] = f * h[b].x;

@@ -8,12 +8,6 @@ namespace dda {
 template <typename T>
 bool tiles_ok(const Geometry& g, int logW_y, int logW_z, int logW_x, int p3_sched) {
     if (p3_sched < 0 || p3_sched >= kP3Schedules) return false;
-    if (p3_sched == 2) {   // staged spectrum: complex64, lines of 64+ points, stage within the opt-in limit
-        if (sizeof(T) != 4 || g.Lz < 64 || logW_z < 0 || logW_z > kMaxLogW) return false;
-        const size_t W = (size_t)1 << logW_z;
-        if ((3 * (size_t)col_elems(g.Lz, (int)W) + (size_t)(g.Lz / 2 + 1) * W * 6) * sizeof(C<T>) + 16 > kMaxSmem)
-            return false;
-    }
     if (p3_sched == 1 && (logW_z < 0 || logW_z > kMaxLogW || !p3_persistent_ok<T>(g, logW_z))) return false;
     const int elt = sizeof(C<T>);
     const int ty = threads_of(g.Ly), tz = threads_of(g.Lz), tx = threads_of(g.Lx);
@@ -73,24 +67,6 @@ int launch_matvec(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t 
         m.nb = mv.nb - b0 < mv.slots ? mv.nb - b0 : mv.slots;
         if (int rc = launch_chunk<T>(m, p, y, st)) return rc;
     }
-    return 0;
-}
-
-// one CTA whose wait has nothing to wait for (16 expected bytes that no copy
-// delivers): every thread's bounded wait gives up and the error word is set
-__global__ void k_wait_probe(int* err) {
-    __shared__ unsigned long long bar;
-    if (threadIdx.x == 0) {
-        mbar_init(&bar, 1);
-        mbar_arrive_expect(&bar, 16);
-    }
-    __syncthreads();
-    if (!mbar_wait(&bar, 0) && threadIdx.x == 0) atomicOr(err, 1);
-}
-
-int launch_wait_probe(int* err, cudaStream_t st) {
-    k_wait_probe<<<1, 32, 0, st>>>(err);
-    DDA_LAUNCH_CHECK("device wait probe");
     return 0;
 }
 

@@ -6,8 +6,7 @@
 
 namespace dda {
 
-constexpr int kP3Schedules = 3;   // z pass schedules (MatvecView::p3_sched)
-constexpr size_t kMaxSmem = 227 * 1024;   // dynamic shared memory one CTA may opt in to
+constexpr int kP3Schedules = 2;   // z pass schedules (MatvecView::p3_sched)
 
 template <typename T>
 struct MatvecView {
@@ -19,9 +18,7 @@ struct MatvecView {
     C<T>* Ay;           // [slots][3][P][Ly][K]
     C<T>* Bxy;          // [slots][3][P][Ly][Lx]
     int logW_y, logW_x, logW_z;  // tile widths (lines per CTA) of the passes
-    int p3_sched = 0;   // z pass: 0 = one CTA per tile, 1 = persistent CTAs with staged inputs,
-                        // 2 = one CTA per tile with its spectrum rows staged by bulk copies
-    int* err = nullptr; // device word: bit 0 is set when a kernel's bounded wait gave up
+    int p3_sched = 0;   // z pass: 0 = one CTA per tile, 1 = persistent CTAs with staged inputs
     const int* status;  // optional: right-hand side b is skipped while
                         // status[b * status_stride] != 0
     int status_stride;  // ints between the status words of consecutive RHS
@@ -50,7 +47,5 @@ template <typename T> void configure_matvec(MatvecView<T>& mv);
 // launch limits (threads per block, shared memory) for this geometry
 template <typename T> bool tiles_ok(const Geometry& g, int logW_y, int logW_z, int logW_x, int p3_sched = 0);
 template <typename T> int launch_matvec(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t st);
-// one CTA whose bounded wait is made to give up (sets *err)
-int launch_wait_probe(int* err, cudaStream_t st);
 
 }  // namespace dda

@@ -47,7 +47,6 @@
 
 #include "fft_reg.cuh"
 #include "matvec.cuh"
-#include "mbarrier.cuh"
 
 namespace dda {
 
@@ -66,6 +65,14 @@ constexpr int kYThreads = 512;
 __host__ __device__ __forceinline__ int64_t ay_elems(const Geometry& g) { return 3LL * g.P * g.Ly * g.K; }
 __host__ __device__ __forceinline__ int64_t bxy_elems(const Geometry& g) { return 3LL * g.P * g.Ly * g.Lx; }
 
+// points t + T m of a y line (T = N/8 threads, m < 8) that can hold
+// lattice sites: m < 4, since J <= N/2 (N >= 2J - 1 and N even); lines of
+// fewer than 8 points have all their points in one thread
+template <int N>
+__host__ __device__ constexpr int p15_sites() {
+    return N >= 8 ? 4 : (N / 2 > 0 ? N / 2 : 1);
+}
+
 // ---------------------------------------------------------------- P1
 template <typename T, int N, int LOGW>
 __global__ void __launch_bounds__(kYThreads) k_p1(MatvecView<T> mv, const C<T>* __restrict__ p) {
@@ -82,23 +89,26 @@ __global__ void __launch_bounds__(kYThreads) k_p1(MatvecView<T> mv, const C<T>* 
     const C<T>* pc = p + (int64_t)b * mv.vstride + (int64_t)c * g.nd;
     const int64_t s0 = (int64_t)kz * g.J * g.K + i;
     // the gather as two rounds of independent loads: first the occupancy and
-    // rank words of all eight sites, then the eight occupied entries of p
-    uint32_t word[8], rbase[8];
+    // rank words of the thread's sites, then their occupied entries of p.
+    // Only the first half of the points can hold sites (J <= N/2).
+    constexpr int nh = p15_sites<N>();
+    uint32_t word[nh], rbase[nh];
     const bool inx = i < g.K;
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
+    for (int m = 0; m < nh; ++m) {
         const int n = t + m * TL;
-        const bool in = inx && m < nv && n < g.J;
+        const bool in = inx && n < g.J;
         const int64_t q = (s0 + (int64_t)n * g.K) >> 5;
         word[m] = in ? __ldg(mv.tv.occ + q) : 0u;
         rbase[m] = in ? __ldg(mv.tv.rank + q) : 0u;
     }
     C<T> v[8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
+    for (int m = 0; m < 8; ++m) v[m] = mk<T>(0, 0);
+#pragma unroll
+    for (int m = 0; m < nh; ++m) {
         const int n = t + m * TL;
         const uint32_t bit = (uint32_t)((s0 + (int64_t)n * g.K) & 31);
-        v[m] = mk<T>(0, 0);
         if ((word[m] >> bit) & 1u) {
             v[m] = pc[rbase[m] + __popc(word[m] & ((1u << bit) - 1u))];
             if (mv.conj) v[m].y = -v[m].y;
@@ -106,9 +116,9 @@ __global__ void __launch_bounds__(kYThreads) k_p1(MatvecView<T> mv, const C<T>* 
     }
     if (mv.jac) {   // point-Jacobi: the product starts from S p
 #pragma unroll
-        for (int m = 0; m < 8; ++m) {
+        for (int m = 0; m < nh; ++m) {
             const int n = t + m * TL;
-            if (inx && m < nv && n < g.J)
+            if (inx && n < g.J)
                 v[m] = cmul<T>(v[m], mv.jac[material(mv.tv, s0 + (int64_t)n * g.K, c) * 3 + c]);
         }
     }
@@ -167,24 +177,6 @@ __device__ __forceinline__ int mirror_flip(int m, int fx, int fy, int fz) {
 }
 
 // the six spectrum components of one point (contiguous) with 16-byte loads
-// from shared memory
-template <typename T>
-__device__ __forceinline__ void load6_shared(const C<T>* p, C<T> (&Y)[6]) {
-    if (sizeof(T) == 4) {
-        const float4* q = reinterpret_cast<const float4*>(p);
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const float4 f = q[i];
-            Y[2 * i] = mk<T>(f.x, f.y);
-            Y[2 * i + 1] = mk<T>(f.z, f.w);
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < 6; ++i) Y[i] = p[i];
-    }
-}
-
-// the same from global memory (read-only path)
 template <typename T>
 __device__ __forceinline__ void load6(const C<T>* __restrict__ p, C<T> (&Y)[6]) {
     if (sizeof(T) == 4) {
@@ -210,18 +202,16 @@ __device__ __forceinline__ int p3_row(int b, int Ly) {
 }
 
 // the spectrum product of Eqs. 6-8 at z point n of the column whose mirrored
-// spectrum row starts at spec (flips fx, fy of the x and y mirrors; entry mz
-// at spec + mz zstep, in global memory or, SHARED, in a staged copy): one
+// spectrum row starts at spec (flips fx, fy of the x and y mirrors): one
 // 48-byte load of the six components, the Table-1 signs, then
 // (X0, X1, X2) <- Y (X0, X1, X2)
-template <typename T, int N, bool SHARED = false>
+template <typename T, int N>
 __device__ __forceinline__ void p3_product(const C<T>* __restrict__ spec, int64_t zstep, bool ok, int fx, int fy,
                                            int n, C<T>& X0, C<T>& X1, C<T>& X2) {
     const int mz = n <= N / 2 ? n : N - n, fz = n > N / 2;
     C<T> Y[6];
     if (ok) {
-        if constexpr (SHARED) load6_shared<T>(spec + mz * zstep, Y);
-        else load6<T>(spec + mz * zstep, Y);
+        load6<T>(spec + mz * zstep, Y);
     } else {
 #pragma unroll
         for (int q = 0; q < 6; ++q) Y[q] = mk<T>(0, 0);
@@ -299,100 +289,6 @@ __global__ void __launch_bounds__(p3_max_threads<T>(), 1) k_p3(MatvecView<T> mv)
             v[c][m] = (ok && m < nv && n < g.P) ? col[c * comp + n * plane] : mk<T>(0, 0);
         }
     p3_tile<T, N, LOGW>(mv, sm, j, xt, jy, v);
-}
-
-// Staged schedule: per tile, warp 0 first issues one bulk copy per z entry
-// mz <= N/2 of the tile's spectrum rows -- the x mirrors lo..hi of its
-// columns at the row's y mirror, (hi - lo + 1) x 48 contiguous bytes -- into
-// a shared stage; the copies run while the tile loads its columns and does
-// the forward z DFTs.  The product of Eqs. 6-8 then reads the stage instead
-// of global memory, and each spectrum entry crosses L2 once per tile
-// instead of once per point (points n and N - n share one).  If the copies
-// never complete (a wait gives up), the tile's output is zeros and the error
-// word is set for the host.
-template <typename T, int N, int LOGW>
-__host__ __device__ constexpr size_t p3_staged_smem() {
-    return (3 * (size_t)col_elems(N, 1 << LOGW) + (size_t)(N / 2 + 1) * (1 << LOGW) * 6) * sizeof(C<T>) + 16;
-}
-// compiled for complex64 lines of 64 points or more
-template <typename T, int N>
-__host__ __device__ constexpr bool p3_staged_compiled() {
-    return sizeof(T) == 4 && N >= 64;
-}
-
-template <typename T, int N, int LOGW>
-__global__ void __launch_bounds__(p3_max_threads<T>(), 1) k_p3b(MatvecView<T> mv) {
-    const int j = blockIdx.x, xt = blockIdx.y;                  // batch slot, column tile
-    if (rhs_done(mv, mv.b0 + j)) return;                        // the same for the whole CTA
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
-    constexpr int TL = Line<N>::T, nv = Line<N>::NV;
-    constexpr int W = 1 << LOGW, HZ = N / 2 + 1, region = col_elems(N, W);
-    C<T>* stage = sm + 3 * region;                                // [HZ][W][6]
-    unsigned long long* bar = reinterpret_cast<unsigned long long*>(stage + (size_t)HZ * W * 6);
-    const Geometry& g = mv.g;
-    const int w = threadIdx.x & (W - 1), t = threadIdx.x >> LOGW;
-    const int jy = p3_row(blockIdx.z, g.Ly);
-    const int ix = xt * W + w;
-    const bool ok = ix < g.Lx;
-    const int my = jy <= g.Ly / 2 ? jy : g.Ly - jy, fy = jy > g.Ly / 2;
-    const int mx = ix <= g.Lx / 2 ? ix : g.Lx - ix, fx = ix > g.Lx / 2;
-    // x mirrors of the tile's columns: one contiguous range of at most W
-    int lo = g.Lx, hi = -1;
-#pragma unroll
-    for (int q = 0; q < W; ++q) {
-        const int i = xt * W + q;
-        if (i < g.Lx) {
-            const int m = i <= g.Lx / 2 ? i : g.Lx - i;
-            lo = m < lo ? m : lo;
-            hi = m > hi ? m : hi;
-        }
-    }
-    const unsigned row = (unsigned)(hi - lo + 1) * 6u * (unsigned)sizeof(C<T>);
-    if (threadIdx.x == 0) {
-        mbar_init(bar, 1);
-        mbar_arrive_expect(bar, row * HZ);   // posted before any copy is issued
-    }
-    __syncthreads();
-    // the first min(32, blockDim.x) threads issue the HZ row copies
-    constexpr int issuers = W * TL < 32 ? W * TL : 32;
-    if (threadIdx.x < issuers) {
-        const C<T>* src = mv.spec + ((int64_t)my * g.Hx + lo) * 6;
-        const int64_t zstep = (int64_t)g.Hy * g.Hx * 6;
-        for (int mz = threadIdx.x; mz < HZ; mz += issuers)
-            bulk_to_shared(stage + mz * W * 6, src + mz * zstep, row, bar);
-    }
-    const int64_t plane = (int64_t)g.Ly * g.Lx, comp = (int64_t)g.P * plane;
-    C<T>* col = mv.Bxy + j * bxy_elems(g) + (int64_t)jy * g.Lx + (ok ? ix : 0);
-    C<T> v[3][8];
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int m = 0; m < 8; ++m) {
-            const int n = t + m * TL;
-            v[c][m] = (ok && m < nv && n < g.P) ? col[c * comp + n * plane] : mk<T>(0, 0);
-        }
-    const ColLayoutT<LOGW> L{};
-    fft_lines<T, false, N, 3, true, false>(v, sm, region, L, w, t, mv.tw);
-    const bool ready = mbar_wait(bar, 0);
-    if (!ready && mv.err) atomicOr(mv.err, 1);
-    {
-        const C<T>* spec = stage + (ok ? mx - lo : 0) * 6;
-#pragma unroll
-        for (int m = 0; m < nv; ++m)
-            p3_product<T, N, true>(spec, W * 6, ok && ready, fx, fy, t + m * TL, v[0][m], v[1][m], v[2][m]);
-    }
-    fft_lines<T, true, N, 3, false, true>(v, sm, region, L, w, t, mv.tw);
-    if (ok) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int m = 0; m < nv; ++m) {
-                const int n = t + m * TL;
-                if (n < g.P) col[c * comp + n * plane] = v[c][m];
-            }
-    }
-    if (!ready) mbar_wait(bar, 0);   // copies still in flight land before the CTA's shared memory is released
 }
 
 // Persistent schedule: each CTA walks the tiles q = blockIdx.x, + gridDim.x,
@@ -482,33 +378,35 @@ __global__ void __launch_bounds__(kYThreads, sizeof(T) == 4 ? 2 : 1) k_p5(Matvec
         const int n = t + m * TL;
         v[m] = (ok && m < nv) ? in[(int64_t)n * g.K] : mk<T>(0, 0);
     }
-    fft_regs<T, true, N, false, true>(v, sm, ColLayoutT<LOGW>{}, w, t, mv.tw);
-    if (!ok) return;
+    // the gather of the thread's sites (first half of the points, J <= N/2)
+    // goes out before the transform, which does not depend on it: occupancy
+    // and rank words, then the occupied entries of p
     const C<T>* pc = p + (int64_t)b * mv.vstride + (int64_t)c * g.nd;
     C<T>* yc = y + (int64_t)b * mv.vstride + (int64_t)c * g.nd;
     const int64_t s0 = (int64_t)kz * g.J * g.K + i;
-    // the scatter in rounds of independent loads: occupancy and rank words,
-    // then the entries of p (and alpha^-1), then the stores of y
-    uint32_t word[8], rbase[8];
+    constexpr int nh = p15_sites<N>();
+    uint32_t word[nh], rbase[nh];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
+    for (int m = 0; m < nh; ++m) {
         const int n = t + m * TL;
-        const bool in = m < nv && n < g.J;
+        const bool in = ok && n < g.J;
         const int64_t q = (s0 + (int64_t)n * g.K) >> 5;
         word[m] = in ? __ldg(mv.tv.occ + q) : 0u;
         rbase[m] = in ? __ldg(mv.tv.rank + q) : 0u;
     }
-    C<T> pv[8];
+    C<T> pv[nh];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
+    for (int m = 0; m < nh; ++m) {
         const int n = t + m * TL;
         const uint32_t bit = (uint32_t)((s0 + (int64_t)n * g.K) & 31);
         rbase[m] += __popc(word[m] & ((1u << bit) - 1u));   // the site's rank
         word[m] = (word[m] >> bit) & 1u;                    // occupied?
         if (word[m]) pv[m] = pc[rbase[m]];
     }
+    fft_regs<T, true, N, false, true>(v, sm, ColLayoutT<LOGW>{}, w, t, mv.tw);
+    if (!ok) return;
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
+    for (int m = 0; m < nh; ++m) {
         if (!word[m]) continue;
         const int64_t s = s0 + (int64_t)(t + m * TL) * g.K;
         const int mat = material(mv.tv, s, c);
@@ -619,21 +517,10 @@ int launch_p3(const MatvecView<T>& mv, cudaStream_t st) {
         DDA_LAUNCH_CHECK("P3 z-forward, spectrum product, z-inverse (persistent)");
         return 0;
     }
-    dim3 grid(mv.nb, (g.Lx + W - 1) / W, g.Ly);
-    if constexpr (p3_staged_compiled<T, N>()) {
-        if (mv.p3_sched == 2) {
-            constexpr size_t sm = p3_staged_smem<T, N, LOGW>();
-            if (sm > kMaxSmem) return fail(DDA_ERR_ARG, "P3 staged schedule: shared memory exceeded");
-            static std::atomic<size_t> smem_set{0};
-            if (int rc = set_smem((const void*)k_p3b<T, N, LOGW>, sm, smem_set)) return rc;
-            k_p3b<T, N, LOGW><<<grid, threads, sm, st>>>(mv);
-            DDA_LAUNCH_CHECK("P3 z-forward, spectrum product, z-inverse (staged spectrum)");
-            return 0;
-        }
-    }
     const size_t sm = 3 * (size_t)col_elems(N, W) * sizeof(C<T>);
     static std::atomic<size_t> smem_set{0};
     if (int rc = set_smem((const void*)k_p3<T, N, LOGW>, sm, smem_set)) return rc;
+    dim3 grid(mv.nb, (g.Lx + W - 1) / W, g.Ly);
     k_p3<T, N, LOGW><<<grid, threads, sm, st>>>(mv);
     DDA_LAUNCH_CHECK("P3 z-forward, spectrum product, z-inverse");
     return 0;
