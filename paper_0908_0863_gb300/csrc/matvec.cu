@@ -13,7 +13,7 @@ bool tiles_ok(const Geometry& g, int logW_y, int logW_z, int logW_x, int p3_sche
     const int ty = threads_of(g.Ly), tz = threads_of(g.Lz), tx = threads_of(g.Lx);
     if (logW_y < 0 || logW_z < 0 || logW_x < 0) return false;
     if (logW_y > kMaxLogW || logW_z > kMaxLogW || logW_x > 10) return false;   // compiled widths
-    if ((1 << logW_y) * ty > kYThreads || (1ull << logW_y) * col_elems(g.Ly, 1) * elt > 200 * 1024) return false;
+    if ((1 << logW_y) * ty > kYThreads || 3ull * (1ull << logW_y) * col_elems(g.Ly, 1) * elt > 200 * 1024) return false;
     if ((1 << logW_z) * tz > p3_max_threads<T>() || 3ull * col_elems(g.Lz, 1 << logW_z) * elt > 220 * 1024)
         return false;
     if ((1 << logW_x) * tx > 512 || (1ull << logW_x) * row_ld(g.Lx) * elt > 200 * 1024) return false;
@@ -28,6 +28,7 @@ void configure_matvec(MatvecView<T>& mv) {
     // strided passes: W adjacent columns (64-byte rows)
     int wy = floor_log2(64 / elt);
     while (wy > 0 && (1 << wy) * ty > kYThreads) --wy;
+    while (wy > 0 && 3ull * (1ull << wy) * col_elems(g.Ly, 1) * elt > 200 * 1024) --wy;   // P1's three regions
     while (wy > 0 && (1 << (wy - 1)) >= g.K) --wy;          // no wider than the lattice
     int wz = floor_log2(64 / elt);
     while (wz > 0 && (1 << wz) * tz > p3_max_threads<T>()) --wz;

@@ -1,11 +1,12 @@
 // Kernels and per-length launchers of the pruned FFT matrix-vector product
 // y = A p of the DDA (OpenDDA Sec. 3).  Each of the translation units
-// mv_p1.cu, mv_p3_*.cu, mv_p5.cu and mv_rows.cu instantiates one pass for
+// mv_p1_*.cu, mv_p3_*.cu, mv_p5_*.cu and mv_rows.cu instantiates one pass for
 // every line length (and tile width) and exposes its dispatcher; matvec.cu
 // sequences the passes.
 //
 // Five stream-ordered passes over device arrays (x fastest everywhere):
-//   P1  expand + y-forward   compressed p -> Ay[3][P][Ly][K]   (K*P lines per component)
+//   P1  expand + y-forward   compressed p -> Ay[3][P][Ly][K]   (K*P lines per component;
+//                            a thread gathers a site's three components together)
 //   P2  x-forward            Ay -> Bxy[3][P][Ly][Lx]           (Ly*P lines, K nonzero inputs)
 //   P3  z conv               per (ix, jy): z-forward of the 3 components (P nonzero
 //                            inputs), the 3x3 spectrum product of Eqs. 6-8 with the
@@ -35,11 +36,12 @@
 // time, W adjacent columns so that each load and store touches W
 // contiguous elements.  In P3 each thread carries the same column of all
 // three components, so the spectrum product happens in registers between
-// the forward and the inverse transforms.  Each kernel is compiled for every
-// line length N (2^a up to 1024, 3 * 2^a from 24 to 768, 5 * 2^a from 40
-// to 640) and, for the
-// strided passes, every tile width (LOGW = 0..4 lines per CTA, log2), and
-// picked at launch, so all shared-memory addresses are compile-time offsets.
+// the forward and the inverse transforms; in P1 it gathers a site's three
+// components with one occupancy and rank lookup.  Each kernel is compiled
+// for every line length N (2^a up to 1024, 3 * 2^a from 24 to 768, 5 * 2^a
+// from 40 to 640) and, for the strided passes, every tile width (LOGW =
+// 0..4 lines per CTA, log2), and picked at launch, so all shared-memory
+// addresses are compile-time offsets.
 #pragma once
 
 #include <algorithm>
@@ -76,21 +78,24 @@ __host__ __device__ constexpr int p15_sites() {
 // ---------------------------------------------------------------- P1
 template <typename T, int N, int LOGW>
 __global__ void __launch_bounds__(kYThreads) k_p1(MatvecView<T> mv, const C<T>* __restrict__ p) {
-    const int c = blockIdx.z % 3, j = blockIdx.z / 3;      // component, batch slot
+    // the three components of a site share its occupancy and rank lookup:
+    // each thread gathers all three and transforms them as three lines
+    const int j = blockIdx.z;                                  // batch slot
     const int b = mv.b0 + j;
     if (rhs_done(mv, b)) return;
     extern __shared__ unsigned char smem_raw[];
     C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
     constexpr int TL = Line<N>::T, nv = Line<N>::NV;
     const Geometry& g = mv.g;
-    constexpr int logW = LOGW, W = 1 << LOGW;
-    const int w = threadIdx.x & (W - 1), t = threadIdx.x >> logW;
+    constexpr int W = 1 << LOGW, region = col_elems(N, W);
+    const int w = threadIdx.x & (W - 1), t = threadIdx.x >> LOGW;
     const int i = blockIdx.x * W + w, kz = blockIdx.y;
-    const C<T>* pc = p + (int64_t)b * mv.vstride + (int64_t)c * g.nd;
+    const C<T>* pb = p + (int64_t)b * mv.vstride;
     const int64_t s0 = (int64_t)kz * g.J * g.K + i;
     // the gather as two rounds of independent loads: first the occupancy and
-    // rank words of the thread's sites, then their occupied entries of p.
-    // Only the first half of the points can hold sites (J <= N/2).
+    // rank words of the thread's sites, then their entries of p (three
+    // components each).  Only the first half of the points can hold sites
+    // (J <= N/2).
     constexpr int nh = p15_sites<N>();
     uint32_t word[nh], rbase[nh];
     const bool inx = i < g.K;
@@ -102,16 +107,22 @@ __global__ void __launch_bounds__(kYThreads) k_p1(MatvecView<T> mv, const C<T>* 
         word[m] = in ? __ldg(mv.tv.occ + q) : 0u;
         rbase[m] = in ? __ldg(mv.tv.rank + q) : 0u;
     }
-    C<T> v[8];
+    C<T> v[3][8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = mk<T>(0, 0);
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int m = 0; m < 8; ++m) v[c][m] = mk<T>(0, 0);
 #pragma unroll
     for (int m = 0; m < nh; ++m) {
         const int n = t + m * TL;
         const uint32_t bit = (uint32_t)((s0 + (int64_t)n * g.K) & 31);
         if ((word[m] >> bit) & 1u) {
-            v[m] = pc[rbase[m] + __popc(word[m] & ((1u << bit) - 1u))];
-            if (mv.conj) v[m].y = -v[m].y;
+            const int64_t r = rbase[m] + __popc(word[m] & ((1u << bit) - 1u));
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                v[c][m] = pb[c * g.nd + r];
+                if (mv.conj) v[c][m].y = -v[c][m].y;
+            }
         }
     }
     if (mv.jac) {   // point-Jacobi: the product starts from S p
@@ -119,14 +130,19 @@ __global__ void __launch_bounds__(kYThreads) k_p1(MatvecView<T> mv, const C<T>* 
         for (int m = 0; m < nh; ++m) {
             const int n = t + m * TL;
             if (inx && n < g.J)
-                v[m] = cmul<T>(v[m], mv.jac[material(mv.tv, s0 + (int64_t)n * g.K, c) * 3 + c]);
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    v[c][m] = cmul<T>(v[c][m], mv.jac[material(mv.tv, s0 + (int64_t)n * g.K, c) * 3 + c]);
         }
     }
-    fft_regs<T, false, N, true, false>(v, sm, ColLayoutT<LOGW>{}, w, t, mv.tw);
-    if (i < g.K) {
-        C<T>* out = mv.Ay + j * ay_elems(g) + ((int64_t)c * g.P + kz) * ((int64_t)g.K * N) + i;
+    fft_lines<T, false, N, 3, true, false>(v, sm, region, ColLayoutT<LOGW>{}, w, t, mv.tw);
+    if (inx) {
 #pragma unroll
-        for (int m = 0; m < nv; ++m) out[(int64_t)(t + m * TL) * g.K] = v[m];
+        for (int c = 0; c < 3; ++c) {
+            C<T>* out = mv.Ay + j * ay_elems(g) + ((int64_t)c * g.P + kz) * ((int64_t)g.K * N) + i;
+#pragma unroll
+            for (int m = 0; m < nv; ++m) out[(int64_t)(t + m * TL) * g.K] = v[c][m];
+        }
     }
 }
 
@@ -448,10 +464,10 @@ template <typename T, int N, int LOGW>
 int launch_p1(const MatvecView<T>& mv, const C<T>* p, cudaStream_t st) {
     const Geometry& g = mv.g;
     constexpr int W = 1 << LOGW;
-    const size_t sm = (size_t)col_elems(N, W) * sizeof(C<T>);
+    const size_t sm = 3 * (size_t)col_elems(N, W) * sizeof(C<T>);
     static std::atomic<size_t> smem_set{0};
     if (int rc = set_smem((const void*)k_p1<T, N, LOGW>, sm, smem_set)) return rc;
-    dim3 grid((g.K + W - 1) / W, g.P, 3 * mv.nb);
+    dim3 grid((g.K + W - 1) / W, g.P, mv.nb);
     k_p1<T, N, LOGW><<<grid, W * Line<N>::T, sm, st>>>(mv, p);
     DDA_LAUNCH_CHECK("P1 expand + y-forward");
     return 0;
