@@ -292,6 +292,34 @@ def algorithmic_bytes(n, nd, esize):
             "matvec_min": 3 * V + 4 * A + T}
 
 
+def matvec_flops(n):
+    """Algorithmic flops of one product at lattice edge n (padded L = 2n per
+    axis): 5 L log2 L per transformed line over the pruned line counts of the
+    five passes, plus 84 per point of the padded grid for the spectrum
+    product (Eqs. 6-8)."""
+    K = J = P = n
+    L = 2 * n
+    lines = 3 * K * P + 3 * L * P + 2 * 3 * L * L + 3 * L * P + 3 * K * P
+    return lines * 5 * L * math.log2(L) + 84 * L ** 3
+
+
+def fp64_peak_tflops(torch, dev, size=8192, reps=3):
+    """Dense FP64 rate of this GPU: cuBLAS DGEMM (torch.matmul, float64)."""
+    a = torch.randn((size, size), dtype=torch.float64, device=dev)
+    b = torch.randn_like(a)
+    torch.matmul(a, b)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        torch.matmul(a, b)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    del a, b
+    return 2.0 * size ** 3 / (ms / 1e3) / 1e12
+
+
 # what the P3 traffic figure depends on: the P3 section of the kernel header
 # (from its P3 banner to the P5 banner) and the headers it includes
 KERNEL_SOURCES = ("fft_reg.cuh", "fft.cuh", "matvec.cuh", "common.cuh")
@@ -391,6 +419,14 @@ def extras(args, dda, torch, dev, shape, bits, alpha, nd, pass_ms, khat, pols, m
                            "pass_ms": [t / c if c else None for c, t in prof]}
             del p, y
         out["fft_matvecs"] = rates
+        # the complex128 product is FP64-ALU-bound: its algorithmic flops
+        # against the DGEMM rate measured here
+        peak64 = fp64_peak_tflops(torch, dev)
+        fl = matvec_flops(args.edge)
+        ach = fl / (rates["c128"]["ms"] / 1e3) / 1e12
+        out["fp64_roofline"] = {"bound": "alu", "kernel": "c128 matvec (P1-P5)", "achieved": ach, "peak": peak64,
+                                "unit": "TFLOP/s", "frac": ach / peak64, "flops_per_matvec": fl,
+                                "peak_source": "cuBLAS DGEMM 8192^3 (torch.matmul, float64) measured in this run"}
         if args.fp64_solve:
             E = torch.empty((3, nd), dtype=torch.complex128, device=dev)
             P = torch.empty_like(E)
