@@ -63,6 +63,9 @@ struct Line {
     static constexpr int LOGM = log2c(M);
     static constexpr int T = N >= 8 ? N / 8 : 1;      // threads per line
     static constexpr int NV = N >= 8 ? 8 : N;         // points per thread
+    // points per thread that can hold lattice sites (t + T m with m < NH):
+    // an edge of n sites pads to N >= 2n - 1 (N even), so n <= N/2
+    static constexpr int NH = N >= 8 ? 4 : (N / 2 > 0 ? N / 2 : 1);
     static_assert(!ODD || M >= 8, "3 * 2^a and 5 * 2^a lengths need a >= 3");
 };
 

@@ -67,14 +67,6 @@ constexpr int kYThreads = 512;
 __host__ __device__ __forceinline__ int64_t ay_elems(const Geometry& g) { return 3LL * g.P * g.Ly * g.K; }
 __host__ __device__ __forceinline__ int64_t bxy_elems(const Geometry& g) { return 3LL * g.P * g.Ly * g.Lx; }
 
-// points t + T m of a y line (T = N/8 threads, m < 8) that can hold
-// lattice sites: m < 4, since J <= N/2 (N >= 2J - 1 and N even); lines of
-// fewer than 8 points have all their points in one thread
-template <int N>
-__host__ __device__ constexpr int p15_sites() {
-    return N >= 8 ? 4 : (N / 2 > 0 ? N / 2 : 1);
-}
-
 // ---------------------------------------------------------------- P1
 template <typename T, int N, int LOGW>
 __global__ void __launch_bounds__(kYThreads) k_p1(MatvecView<T> mv, const C<T>* __restrict__ p) {
@@ -96,7 +88,7 @@ __global__ void __launch_bounds__(kYThreads) k_p1(MatvecView<T> mv, const C<T>* 
     // rank words of the thread's sites, then their entries of p (three
     // components each).  Only the first half of the points can hold sites
     // (J <= N/2).
-    constexpr int nh = p15_sites<N>();
+    constexpr int nh = Line<N>::NH;
     uint32_t word[nh], rbase[nh];
     const bool inx = i < g.K;
 #pragma unroll
@@ -273,7 +265,7 @@ __device__ __forceinline__ void p3_tile(const MatvecView<T>& mv, C<T>* sm, int j
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
-            for (int m = 0; m < nv; ++m) {
+            for (int m = 0; m < Line<N>::NH; ++m) {   // z < P <= N/2: first half only
                 const int n = t + m * TL;
                 if (n < g.P) col[c * comp + n * plane] = v[c][m];
             }
@@ -302,7 +294,7 @@ __global__ void __launch_bounds__(p3_max_threads<T>(), 1) k_p3(MatvecView<T> mv)
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
             const int n = t + m * TL;
-            v[c][m] = (ok && m < nv && n < g.P) ? col[c * comp + n * plane] : mk<T>(0, 0);
+            v[c][m] = (ok && m < Line<N>::NH && n < g.P) ? col[c * comp + n * plane] : mk<T>(0, 0);
         }
     p3_tile<T, N, LOGW>(mv, sm, j, xt, jy, v);
 }
@@ -400,7 +392,7 @@ __global__ void __launch_bounds__(kYThreads, sizeof(T) == 4 ? 2 : 1) k_p5(Matvec
     const C<T>* pc = p + (int64_t)b * mv.vstride + (int64_t)c * g.nd;
     C<T>* yc = y + (int64_t)b * mv.vstride + (int64_t)c * g.nd;
     const int64_t s0 = (int64_t)kz * g.J * g.K + i;
-    constexpr int nh = p15_sites<N>();
+    constexpr int nh = Line<N>::NH;
     uint32_t word[nh], rbase[nh];
 #pragma unroll
     for (int m = 0; m < nh; ++m) {
