@@ -751,9 +751,13 @@ def oracle_rows_sample(nd, mask, rows_count, threads):
 def cpu_baseline(args, nd, mask):
     threads = os.cpu_count() or 1
     rate, dt = oracle_rows_sample(nd, mask, args.cpu_rows, threads)
+    rows1 = max(1, args.cpu_rows // 10)
+    rate1, dt1 = oracle_rows_sample(nd, mask, rows1, 1)
     return {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{args.cpu_rows} rows of A p by direct FP64 summation over all {nd} dipoles "
-                      f"({dt:.1f} s), scaled to whole products"}
+                      f"({dt:.1f} s), scaled to whole products",
+            "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
+                              "sample": f"{rows1} rows on one thread ({dt1:.1f} s), scaled to whole products"}}
 
 
 def run_reference(args):
