@@ -1,0 +1,72 @@
+"""bench.py keeps its one-line JSON contract: the reference arm (the FP64
+oracle on the host cores) on CPU, and our arm on a small sphere on the GPU.
+The keys and their types are checked, not the numbers."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _run(args, timeout):
+    env = dict(os.environ, PYTHONPATH=ROOT)
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], capture_output=True, text=True,
+                       timeout=timeout, cwd=ROOT, env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.strip().startswith("{")]
+    assert len(lines) == 1, r.stdout
+    return json.loads(lines[0])
+
+
+def _common(d):
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "e2e", "cpu_baseline"):
+        assert key in d, key
+    assert d["higher_is_better"] is True and d["scaling"] == "weak" and d["vs_baseline"] is None
+    assert d["data"] == "synthetic" and "workload" in d["config"]
+    assert d["warmup"] >= 3 and d["value"] > 0
+    for key in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"):
+        assert key in d["e2e"], key
+    for key in ("value", "unit", "cores", "kind", "sample"):
+        assert key in d["cpu_baseline"], key
+    assert d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_reference_arm_contract():
+    d = _run(["--impl", "reference", "--edge", "16", "--diameter", "16", "--steps", "1", "--warmup", "3",
+              "--cpu-rows", "20"], timeout=600)
+    _common(d)
+    assert d["impl"] == "reference" and d["dtype"] == "f64"
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["cpu_baseline"]["value"] == d["value"]
+
+
+def test_warmup_below_three_is_refused():
+    env = dict(os.environ, PYTHONPATH=ROOT)
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--warmup", "2"],
+                       capture_output=True, text=True, timeout=120, cwd=ROOT, env=env)
+    assert r.returncode != 0 and "warmup" in r.stderr
+
+
+@pytest.mark.gpu
+def test_our_arm_contract():
+    d = _run(["--edge", "32", "--diameter", "30", "--steps", "3", "--warmup", "3", "--batch", "2",
+              "--cpu-rows", "20"], timeout=900)
+    _common(d)
+    assert "impl" not in d and d["n_gpus"] == 1
+    assert d["gpu_launches"] > 0
+    for key in ("sm_mhz", "sm_max_mhz", "reasons"):
+        assert key in d["clocks"], key
+    rl = d["roofline"]
+    for key in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
+        assert key in rl, key
+    assert rl["bound"] == "hbm" and rl["unit"] == "GB/s" and abs(rl["frac"] - rl["achieved"] / rl["peak"]) < 1e-9
+    assert d["e2e"]["h2d_bytes_per_step"] > 0 and d["e2e"]["d2h_bytes_per_step"] > 0
+    f64 = d["fp64_roofline"]
+    assert f64["bound"] == "alu" and 0 < f64["frac"]
+    assert d["unpruned_cufft"]["c128"]["rel_diff_vs_library"] < 1e-12
+    assert d["unpruned_cufft"]["c64"]["rel_diff_vs_library"] < 2e-5
+    assert d["job"]["status"] == [0]
