@@ -102,7 +102,7 @@ def test_table3_iteration_counts(dda, golden):
 
 
 def test_sphere_converges_to_mie_at_scale(dda):
-    """The benchmark spec's convergence check at GPU scale: a sphere of fixed size
+    """Convergence to Mie theory at GPU scale: a sphere of fixed size
     parameter x = 3 (m = 1.33 + 0.05i) discretised with D = 16, 32, 64 and
     128 dipoles across (|m| k d from 0.5 down to 0.06, up to 1.1 M dipoles),
     solved in FP64 and compared with the oracle's Mie series.  With LDR the

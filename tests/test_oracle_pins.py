@@ -465,7 +465,7 @@ def test_mie_textbook_example():
 
 
 def test_dda_sphere_approaches_mie():
-    # the benchmark spec invariant: |Q_DDA - Q_Mie| decreases as the dipole count grows
+    # convergence invariant: |Q_DDA - Q_Mie| decreases as the dipole count grows
     # (x = 2: at x = 1 the CM+RR error changes sign near D = 8, so the
     # decrease is only monotone from there on)
     m = 1.33 + 0.01j
