@@ -53,7 +53,7 @@ def random_case(shape, seed, fill=1.0, two_materials=True, k=0.45):
     return Case(mask, refr, k, mats)
 
 
-def config1_case():
+def sphere16_case():
     """16^3 sphere of diameter 16, m = 1.33 + 0.01i, |m| k d = 0.5, CM + RR."""
     m = 1.33 + 0.01j
     return Case(synth.sphere(16), [m], 0.5 / abs(m))

@@ -16,7 +16,7 @@ from oracle import adjoint as oadj
 from oracle import dda as odda
 from oracle import solvers as osolvers
 
-from _cases import Case, config1_case, random_case
+from _cases import Case, sphere16_case, random_case
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -51,7 +51,7 @@ def _solve_P(lat, case, method="bicgstab", precision="fp64", tol=1e-13):
 # ---------------------------------------------------------------- BiCG_sym
 
 def test_bicg_sym_iterates_match_oracle(dda):
-    case = config1_case()
+    case = sphere16_case()
     A = odda.dense_matrix(case.coords, case.ainv, case.k)
     E = odda.incident_field(case.coords, case.k, [0, 0, 1], [1, 0, 0])
     x, oinfo = osolvers.bicg_sym(lambda v: A @ v, E.reshape(-1), tol=1e-8, max_iter=2000)
@@ -66,7 +66,7 @@ def test_bicg_sym_iterates_match_oracle(dda):
 
 
 def test_bicg_sym_tight_cross_sections(dda):
-    case = config1_case()
+    case = sphere16_case()
     A = odda.dense_matrix(case.coords, case.ainv, case.k)
     E = odda.incident_field(case.coords, case.k, [0, 0, 1], [1, 0, 0])
     Pref = np.linalg.solve(A, E.reshape(-1)).reshape(3, -1)
@@ -91,7 +91,7 @@ def test_csca_pair_sum_matches_oracle(dda):
 
 
 def test_optical_theorem_with_gpu_csca(dda):
-    case = config1_case()
+    case = sphere16_case()
     with case.lattice() as lat:
         E, P = _solve_P(lat, case, "bicgstab", "fp64", 1e-13)
         cext, cabs, _ = lat.cross_sections(E, P)

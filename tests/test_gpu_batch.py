@@ -14,7 +14,7 @@ import pytest
 import synth
 from oracle import dda as odda
 
-from _cases import Case, config1_case, random_case
+from _cases import Case, sphere16_case, random_case
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -59,7 +59,7 @@ def _oracle_lu(case, pairs):
 
 @pytest.fixture(scope="module")
 def c1_batch():
-    case = config1_case()
+    case = sphere16_case()
     pairs = _pairs(20260051, 3)
     return case, pairs, _oracle_lu(case, pairs)
 

@@ -7,7 +7,7 @@ import synth
 from oracle import circulant
 from oracle import dda as odda
 
-from _cases import Case, config1_case, random_case
+from _cases import Case, sphere16_case, random_case
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -140,8 +140,8 @@ def test_matvec_c64_matches_direct_sum(dda, shape, fill):
     assert np.abs(y - y_ref).max() <= 2e-6 * np.abs(y_ref).max()
 
 
-def test_matvec_config1_sphere(dda):
-    case = config1_case()
+def test_matvec_sphere16(dda):
+    case = sphere16_case()
     p = synth.complex_normal(1, (3, case.nd))
     y_ref = odda.direct_matvec(case.coords, case.ainv, case.k, p)
     y = _matvec(dda, case, p, np.complex128)

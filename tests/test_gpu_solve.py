@@ -10,7 +10,7 @@ import synth
 from oracle import dda as odda
 from oracle import solvers as osolvers
 
-from _cases import Case, config1_case, random_case
+from _cases import Case, sphere16_case, random_case
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -26,8 +26,8 @@ def dda():
 
 
 @pytest.fixture(scope="module")
-def c1():
-    case = config1_case()
+def sphere16():
+    case = sphere16_case()
     A = odda.dense_matrix(case.coords, case.ainv, case.k)
     E = odda.incident_field(case.coords, case.k, [0, 0, 1], [1, 0, 0])
     P = np.linalg.solve(A, E.reshape(-1)).reshape(3, case.nd)
@@ -70,9 +70,9 @@ def test_cross_sections_match_oracle(dda):
 
 
 @pytest.mark.parametrize("method", ["bicg", "bicgstab", "qmr"])
-def test_fp64_solve_config1_tight(dda, c1, method):
+def test_fp64_solve_sphere16_tight(dda, sphere16, method):
     # same method, x0 = 0, tol 1e-12 -> cross sections within 1e-10 of the LU solution
-    case, A, E, P, C = c1
+    case, A, E, P, C = sphere16
     status, info, Eg, Pg, cx = _solve(dda, case, method, "fp64", 1e-12)
     assert status == dda.DDA_OK, info
     assert np.abs(Eg - E).max() < 1e-14
@@ -83,9 +83,9 @@ def test_fp64_solve_config1_tight(dda, c1, method):
 
 
 @pytest.mark.parametrize("method", ["bicg", "bicgstab", "qmr"])
-def test_fp64_iterates_match_oracle_solver(dda, c1, method):
+def test_fp64_iterates_match_oracle_solver(dda, sphere16, method):
     # the device recurrences are the oracle's: same iteration count at tol 1e-8
-    case, A, E, P, C = c1
+    case, A, E, P, C = sphere16
     status, info, Eg, Pg, cx = _solve(dda, case, method, "fp64", 1e-8)
     x, oinfo = osolvers.SOLVERS[method](lambda v: A @ v, E.reshape(-1), tol=1e-8, max_iter=2000)
     assert status == dda.DDA_OK
@@ -94,8 +94,8 @@ def test_fp64_iterates_match_oracle_solver(dda, c1, method):
 
 
 @pytest.mark.parametrize("method", ["bicg", "bicgstab", "qmr"])
-def test_mixed_solve_config1(dda, c1, method):
-    case, A, E, P, C = c1
+def test_mixed_solve_sphere16(dda, sphere16, method):
+    case, A, E, P, C = sphere16
     status, info, Eg, Pg, cx = _solve(dda, case, method, "mixed", 1e-6)
     assert status == dda.DDA_OK, info
     assert info["refinements"] >= 1 and info["rel_residual_true"] <= 1e-6
@@ -111,8 +111,8 @@ def test_optical_theorem_on_gpu_solution(dda):
     assert abs(cx[2] / cs - 1) < 1e-9
 
 
-def test_non_convergence_reported(dda, c1):
-    case = c1[0]
+def test_non_convergence_reported(dda, sphere16):
+    case = sphere16[0]
     for method in ("bicg", "bicgstab", "qmr"):
         status, info, *_ = _solve(dda, case, method, "fp64", 1e-14, max_iter=3)
         assert status == dda.DDA_ERR_NOT_CONVERGED

@@ -1,7 +1,7 @@
 """GPU parity of CG, CGS, TFQMR, QMR_sym and BiCGSTAB(l) and of point-Jacobi
 preconditioning against the FP64 oracle, through the C ABI.
 
-Targets: the 16^3 sphere of the single-solve tests (config 1, one
+Targets: the 16^3 sphere of the single-solve tests (one
 material: Jacobi is a scalar scaling there) and a 12^3 crop of the 48^3
 inclusion cube (host m = 1.33 + 0.001i, inclusions 2.0 + 0.5i), whose two
 materials make diag(A) vary from site to site.
@@ -13,7 +13,7 @@ import synth
 from oracle import dda as odda
 from oracle import solvers as osolvers
 
-from _cases import Case, config1_case
+from _cases import Case, sphere16_case
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -30,8 +30,8 @@ def dda():
 
 
 @pytest.fixture(scope="module")
-def c1():
-    case = config1_case()
+def sphere16():
+    case = sphere16_case()
     A = odda.dense_matrix(case.coords, case.ainv, case.k)
     E = odda.incident_field(case.coords, case.k, [0, 0, 1], [1, 0, 0])
     P = np.linalg.solve(A, E.reshape(-1)).reshape(3, -1)
@@ -59,8 +59,8 @@ def _gpu_solve(case, E, method, precision, tol, max_iter=3000):
 
 
 @pytest.mark.parametrize("method", NEW)
-def test_new_solvers_fp64_tight(dda, c1, method):
-    case, A, E, P = c1
+def test_new_solvers_fp64_tight(dda, sphere16, method):
+    case, A, E, P = sphere16
     status, info, Pg, cx = _gpu_solve(case, E, method, "fp64", 1e-12)
     assert status == dda.DDA_OK, info
     assert info["rel_residual_true"] < 5e-12
@@ -69,8 +69,8 @@ def test_new_solvers_fp64_tight(dda, c1, method):
 
 
 @pytest.mark.parametrize("method", NEW)
-def test_new_solvers_follow_oracle_iterates(dda, c1, method):
-    case, A, E, P = c1
+def test_new_solvers_follow_oracle_iterates(dda, sphere16, method):
+    case, A, E, P = sphere16
     x, oinfo = osolvers.SOLVERS[method](lambda v: A @ v, E.reshape(-1), tol=1e-8, max_iter=3000)
     status, info, Pg, _ = _gpu_solve(case, E, method, "fp64", 1e-8)
     assert status == dda.DDA_OK
@@ -80,8 +80,8 @@ def test_new_solvers_follow_oracle_iterates(dda, c1, method):
 
 
 @pytest.mark.parametrize("method", ["bicgstab", "qmr_sym", "tfqmr", "rbicgstab2"])
-def test_new_solvers_mixed(dda, c1, method):
-    case, A, E, P = c1
+def test_new_solvers_mixed(dda, sphere16, method):
+    case, A, E, P = sphere16
     status, info, Pg, cx = _gpu_solve(case, E, method, "mixed", 1e-6)
     assert status == dda.DDA_OK, info
     assert info["rel_residual_true"] <= 1e-6
@@ -113,10 +113,10 @@ def test_jacobi_mixed_two_materials(dda, incl):
     assert abs(cx[0] / ce - 1) < 1e-5
 
 
-def test_jacobi_single_material_is_a_scaling(dda, c1):
+def test_jacobi_single_material_is_a_scaling(dda, sphere16):
     # one material: S A S y = S b has the Krylov spaces of A x = b, so the same
     # iteration count and solution
-    case, A, E, P = c1
+    case, A, E, P = sphere16
     s0, i0, P0, _ = _gpu_solve(case, E, "qmr_sym", "fp64", 1e-10)
     s1, i1, P1, _ = _gpu_solve(case, E, "qmr_sym+jacobi", "fp64", 1e-10)
     assert s0 == s1 == dda.DDA_OK
@@ -125,8 +125,8 @@ def test_jacobi_single_material_is_a_scaling(dda, c1):
 
 
 @pytest.mark.parametrize("method", ["cg", "cgs", "tfqmr", "qmr_sym", "rbicgstab2"])
-def test_new_solvers_batched(dda, c1, method):
-    case, A, E, P = c1
+def test_new_solvers_batched(dda, sphere16, method):
+    case, A, E, P = sphere16
     pairs = []
     for kh in synth.random_direction(20260061, 2):
         e1, e2 = synth.orthogonal_polarisations(kh)
