@@ -217,11 +217,13 @@ def run_ours(args):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     barrier()
+    torch.cuda.profiler.start()   # profiler range = the timed steps (no-op without a profiler)
     ev0.record(stream)
     for _ in range(args.steps):
         job(True)
     ev1.record(stream)
     barrier()
+    torch.cuda.profiler.stop()
     clocks = sampler.stop()
     launches = dda.dda_launch_count() - l0
     ms = ev0.elapsed_time(ev1)
@@ -693,6 +695,7 @@ def run_aggregates(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     detail = []
     mv = solves = 0
+    torch.cuda.profiler.start()   # profiler range = the timed steps (no-op without a profiler)
     e0.record(stream)
     for _ in range(args.steps):
         for nm, mask, pairs in targets:
@@ -701,6 +704,7 @@ def run_aggregates(args):
             solves += b
     e1.record(stream)
     torch.cuda.synchronize(dev)
+    torch.cuda.profiler.stop()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
     launches = dda.dda_launch_count() - l0
