@@ -41,8 +41,8 @@
 // one thread each in registers.  Twiddles come from the FP64 table
 // tw[m] = exp(-2 pi i m / 3072), m < 3072, followed by
 // tw[3072 + m] = exp(-2 pi i m / 5120), m < 5120 (rounded once for FP32),
-// conjugated for the inverse; FP32 radix-8 stages load one twiddle and form
-// the other six as its powers.  Transforms are unnormalised.
+// conjugated for the inverse; FP32 stages load one twiddle per butterfly
+// and form the others as its powers.  Transforms are unnormalised.
 #pragma once
 
 #include "fft.cuh"
@@ -223,18 +223,32 @@ __device__ __forceinline__ void odd_finish(C<T> (&v)[NL][8], C<T>* __restrict__ 
     constexpr int R = Line<N>::R, M = N / R, Tn = N / 8;
     constexpr int off = R == 3 ? 0 : kTwLen, step = (R == 3 ? kTwLen : kTw5Len) / N;
     constexpr int nq = (M + Tn - 1) / Tn;   // butterflies per thread (3 for R = 3, 2 for R = 5)
+    // the twiddles depend on j only: loaded before the barrier, so their
+    // latency overlaps the wait (FP32: one load per butterfly and its powers,
+    // as in the radix-8 stages; FP64: every power from the table)
+    C<T> wq[nq][R];
+#pragma unroll
+    for (int q = 0; q < nq; ++q) {
+        const int j = t + q * Tn, jj = j < M ? j : 0;
+        wq[q][0] = mk<T>(1, 0);
+        if (sizeof(T) == 4) {
+            wq[q][1] = twiddle<T, INV>(tw, off + jj * step);
+#pragma unroll
+            for (int r = 2; r < R; ++r) wq[q][r] = cmul<T>(wq[q][r - 1], wq[q][1]);
+        } else {
+#pragma unroll
+            for (int r = 1; r < R; ++r) wq[q][r] = twiddle<T, INV>(tw, off + jj * r * step);
+        }
+    }
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < nq; ++q) {
         const int j = t + q * Tn;
         if (j < M) {
-            C<T> wr[R];
+            const C<T>(&wr)[R] = wq[q];
             int o[R];
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                wr[r] = twiddle<T, INV>(tw, off + j * r * step);
-                o[r] = L(w, j + r * M);
-            }
+            for (int r = 0; r < R; ++r) o[r] = L(w, j + r * M);
 #pragma unroll
             for (int l = 0; l < NL; ++l) {
                 C<T>* S = sm + l * region;
