@@ -217,7 +217,7 @@ __device__ __forceinline__ void dft5(C<T> (&x)[5]) {
 // place in shared memory -- butterfly j < M twiddles x[j + M r] by
 // exp(-+ 2 pi i j r / N) -- then the canonical read that ends the transform
 // in registers.  Thread t takes the butterflies j = t, t + T, ... below M.
-template <typename T, bool INV, int N, int NL, class Layout>
+template <typename T, bool INV, int N, int NL, bool TAIL = true, class Layout>
 __device__ __forceinline__ void odd_finish(C<T> (&v)[NL][8], C<T>* __restrict__ sm, int region,
                                            const Layout& L, int w, int t, const C<T>* __restrict__ tw) {
     constexpr int R = Line<N>::R, M = N / R, Tn = N / 8;
@@ -268,13 +268,13 @@ __device__ __forceinline__ void odd_finish(C<T> (&v)[NL][8], C<T>* __restrict__ 
     }
     __syncthreads();
     read_canonical<T, N, NL>(v, sm, region, L, w, t);
-    __syncthreads();
+    if constexpr (TAIL) __syncthreads();
 }
 
 // radix-8 stages from Ns = 2^LOGNS on.  The last one of a 2^a line leaves
 // the outputs on the canonical points; that of a 3 * 2^a or 5 * 2^a line
 // writes them to shared memory for the closing radix-3 or radix-5 stage.
-template <typename T, bool INV, int N, int LOGNS, int NL, bool HALF_OUT, class Layout>
+template <typename T, bool INV, int N, int LOGNS, int NL, bool HALF_OUT, class Layout, bool TAIL = true>
 struct Radix8Stages {
     __device__ __forceinline__ static void run(C<T> (&v)[NL][8], C<T>* __restrict__ sm, int region,
                                                const Layout& L, int w, int t, const C<T>* __restrict__ tw) {
@@ -294,10 +294,13 @@ struct Radix8Stages {
             if constexpr (LOGNS + 3 < LOGM) {
                 __syncthreads();
                 read_canonical<T, N, NL>(v, sm, region, L, w, t);
-                __syncthreads();
-                Radix8Stages<T, INV, N, LOGNS + 3, NL, HALF_OUT, Layout>::run(v, sm, region, L, w, t, tw);
+                // the next stage writes shared memory again, unless it is
+                // the last one of a 2^a line (registers only); then only a
+                // caller that reuses the buffer (TAIL) needs the barrier
+                if constexpr (TAIL || LOGNS + 6 < LOGM || Line<N>::ODD) __syncthreads();
+                Radix8Stages<T, INV, N, LOGNS + 3, NL, HALF_OUT, Layout, TAIL>::run(v, sm, region, L, w, t, tw);
             } else {
-                odd_finish<T, INV, N, NL>(v, sm, region, L, w, t, tw);
+                odd_finish<T, INV, N, NL, TAIL>(v, sm, region, L, w, t, tw);
             }
         } else {
 #pragma unroll
@@ -312,7 +315,10 @@ struct Radix8Stages {
 // In-place DFT of NL lines held as v[l][m] = x_l[t + T m].  All threads of
 // the CTA must call it together (it synchronises when it exchanges).
 // HALF_IN: inputs m >= 4 are zero.  HALF_OUT: only outputs m < 4 are needed.
-template <typename T, bool INV, int N, int NL, bool HALF_IN, bool HALF_OUT, class Layout>
+// TAIL: the caller reuses the shared buffer afterwards, so the transform
+// ends with a barrier after its last shared-memory read (false when nothing
+// touches the buffer again, e.g. the kernel's last transform).
+template <typename T, bool INV, int N, int NL, bool HALF_IN, bool HALF_OUT, bool TAIL = true, class Layout>
 __device__ __forceinline__ void fft_lines(C<T> (&v)[NL][8], C<T>* __restrict__ sm, int region, const Layout& L,
                                           int w, int t, const C<T>* __restrict__ tw) {
     if constexpr (N <= 8 && !Line<N>::ODD) {  // a single stage: one thread holds the whole line
@@ -359,22 +365,22 @@ __device__ __forceinline__ void fft_lines(C<T> (&v)[NL][8], C<T>* __restrict__ s
         }
         if constexpr (L1 == LOGM) {
             // the first stage was the only power-of-two stage (N = 3 * 8, 5 * 8)
-            odd_finish<T, INV, N, NL>(v, sm, region, L, w, t, tw);
+            odd_finish<T, INV, N, NL, TAIL>(v, sm, region, L, w, t, tw);
         } else {
             __syncthreads();
             read_canonical<T, N, NL>(v, sm, region, L, w, t);
-            __syncthreads();
-            Radix8Stages<T, INV, N, L1, NL, HALF_OUT, Layout>::run(v, sm, region, L, w, t, tw);
+            if constexpr (TAIL || L1 + 3 < LOGM || Line<N>::ODD) __syncthreads();
+            Radix8Stages<T, INV, N, L1, NL, HALF_OUT, Layout, TAIL>::run(v, sm, region, L, w, t, tw);
         }
     }
 }
 
 // one line: v[m] = x[t + T m]
-template <typename T, bool INV, int N, bool HALF_IN, bool HALF_OUT, class Layout>
+template <typename T, bool INV, int N, bool HALF_IN, bool HALF_OUT, bool TAIL = true, class Layout>
 __device__ __forceinline__ void fft_regs(C<T> (&v)[8], C<T>* __restrict__ sm, const Layout& L, int w, int t,
                                          const C<T>* __restrict__ tw) {
     C<T>(&vv)[1][8] = *reinterpret_cast<C<T>(*)[1][8]>(&v);
-    fft_lines<T, INV, N, 1, HALF_IN, HALF_OUT>(vv, sm, 0, L, w, t, tw);
+    fft_lines<T, INV, N, 1, HALF_IN, HALF_OUT, TAIL>(vv, sm, 0, L, w, t, tw);
 }
 
 }  // namespace dda

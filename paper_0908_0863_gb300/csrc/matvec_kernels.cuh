@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kYThreads) k_p1(MatvecView<T> mv, const C<T>* 
                     v[c][m] = cmul<T>(v[c][m], mv.jac[material(mv.tv, s0 + (int64_t)n * g.K, c) * 3 + c]);
         }
     }
-    fft_lines<T, false, N, 3, true, false>(v, sm, region, ColLayoutT<LOGW>{}, w, t, mv.tw);
+    fft_lines<T, false, N, 3, true, false, false>(v, sm, region, ColLayoutT<LOGW>{}, w, t, mv.tw);
     if (inx) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(512) k_rows(MatvecView<T> mv) {
         const int n = t + m * TL;
         v[m] = (ok && m < nv && n < nin) ? src[n] : mk<T>(0, 0);
     }
-    fft_regs<T, INV, N, !INV, INV>(v, sm, RowLayout<N>{}, wl, t, mv.tw);
+    fft_regs<T, INV, N, !INV, INV, false>(v, sm, RowLayout<N>{}, wl, t, mv.tw);
     if (ok) {
 #pragma unroll
         for (int m = 0; m < nv; ++m) {
@@ -260,7 +260,9 @@ __device__ __forceinline__ void p3_tile(const MatvecView<T>& mv, C<T>* sm, int j
         for (int m = 0; m < nv; ++m)
             p3_product<T, N>(spec, zstep, ok, fx, fy, t + m * TL, v[0][m], v[1][m], v[2][m]);
     }
-    fft_lines<T, true, N, 3, false, true>(v, sm, region, L, w, t, mv.tw);
+    // nothing reuses the exchange buffers after the inverse (the persistent
+    // schedule synchronises twice before its next tile)
+    fft_lines<T, true, N, 3, false, true, false>(v, sm, region, L, w, t, mv.tw);
     if (ok) {
 #pragma unroll
         for (int c = 0; c < 3; ++c)
@@ -411,7 +413,7 @@ __global__ void __launch_bounds__(kYThreads, sizeof(T) == 4 ? 2 : 1) k_p5(Matvec
         word[m] = (word[m] >> bit) & 1u;                    // occupied?
         if (word[m]) pv[m] = pc[rbase[m]];
     }
-    fft_regs<T, true, N, false, true>(v, sm, ColLayoutT<LOGW>{}, w, t, mv.tw);
+    fft_regs<T, true, N, false, true, false>(v, sm, ColLayoutT<LOGW>{}, w, t, mv.tw);
     if (!ok) return;
 #pragma unroll
     for (int m = 0; m < nh; ++m) {
