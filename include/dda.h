@@ -235,10 +235,12 @@ int dda_tiles(dda_ctx* ctx, int dtype, int* tiles_out, const int* tiles_in);
  * Autotune the tile settings of dtype on this context: starting from the
  * current ones, try every z pass schedule with P3 widths up to two steps
  * either way of the current one, then up to two width steps for P1/P5 and
- * for P2/P4, timing
- * `reps` batched products of nb right-hand sides per
+ * for P2/P4, timing `reps` batched products of nb right-hand sides per
  * candidate with CUDA events (after one untimed product), and keep the
- * fastest.  The choice is set on the context and remembered for the
+ * fastest.  Last, the chosen settings and the starting ones are timed once
+ * more, back to back, and the faster whole product wins (a guard against
+ * timing noise between the steps).  The choice is set on the context and
+ * remembered for the
  * process: contexts created later with the same lattice shape start with
  * it.  pass_ms (host double[5], may be NULL) receives the per-pass
  * milliseconds of the chosen widths.  Allocates (and frees) two scratch
