@@ -15,9 +15,10 @@ the tests can pin the readings the GPU path relies on:
   x, then y, then z.
 * ``mirror_signs``: Table 1 of the paper.
 
-The padded lengths L are passed in; the GPU path uses the next power of
-two >= 2n - 1 (the paper's K'' = 2K - 1 + kf with kf chosen for a fast
-transform, Sec. 3 and App. A).
+The padded lengths L are passed in.  ``padded_length`` gives the length
+the library pads each axis to: the smallest L >= 2n - 1 of the form 2^a,
+3 * 2^a or 5 * 2^a (the paper's K'' = 2K - 1 + kf with kf chosen for a fast
+transform, Sec. 3 and App. A).  Any L >= 2n - 1 gives the same product.
 """
 from __future__ import annotations
 

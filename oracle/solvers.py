@@ -7,6 +7,10 @@ the paper cites for it, written for complex vectors:
   TFQMR: Freund (1993); BiCG_sym and QMR_sym: Freund (1992), the
   complex-symmetric forms; CG: Hestenes & Stiefel (1952); RBiCGSTAB as
   BiCGSTAB(ell): Sleijpen & Fokkema (1993).
+* ML(n)BiCGSTAB (Yeung & Chan 1999): written from its definition, the
+  residual at the end of each cycle (see ``mlbicgstab``), not from a
+  recurrence; its n - 1 random shadow vectors come from the counter-based
+  SplitMix64 generator (``splitmix64``, ``shadow_vectors``).
 * Hermitian inner products x^H y where the real template has x^T y (BiCG,
   BiCGSTAB, CGS, TFQMR, all with the shadow vector r0 or conj(r0)),
   bilinear products x^T y where the method relies on A = A^T (BiCG_sym,
@@ -496,6 +500,156 @@ def bicgstab_l(A, b, tol=1e-8, max_iter=1000, x0=None, ell=2):
     return x, _info(max_iter, mv, False, False, rel)
 
 
+# ------------------------------------------------------------ ML(n)BiCGSTAB
+_M64 = (1 << 64) - 1
+_GOLDEN = 0x9E3779B97F4A7C15
+
+
+def _mix64(z: int) -> int:
+    """SplitMix64 output function (Steele, Lea & Flood 2014)."""
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def splitmix64(seed: int, count: int) -> list:
+    """The first `count` outputs of SplitMix64 started from state `seed`:
+    the state advances by the golden-ratio constant 0x9E3779B97F4A7C15 and
+    each output is the mix of the new state."""
+    out, st = [], seed & _M64
+    for _ in range(count):
+        st = (st + _GOLDEN) & _M64
+        out.append(_mix64(st))
+    return out
+
+
+def shadow_vectors(r0: np.ndarray, nvec: int) -> np.ndarray:
+    """The nvec left starting vectors of ML(n)BiCGSTAB as columns of an
+    (N, nvec) array: q_1 = r0 (so that ML(1)BiCGSTAB is BiCGSTAB with the
+    shadow residual r0), and for i = 1 .. nvec - 1 the vector q_(i+1) whose
+    entry e (flat index into the [3][N_d] vector) is u1 + i u2, where u1 and
+    u2 are the first two SplitMix64 outputs started from the state
+    i * 2^40 + e, each mapped to [-1, 1) as (u >> 11) * 2^-52 - 1."""
+    N = r0.size
+    Q = np.zeros((N, nvec), dtype=np.complex128)
+    Q[:, 0] = r0.reshape(-1)
+    for i in range(1, nvec):
+        for e in range(N):
+            u1, u2 = splitmix64((i << 40) + e, 2)
+            Q[e, i] = complex((u1 >> 11) * 2.0 ** -52 - 1.0, (u2 >> 11) * 2.0 ** -52 - 1.0)
+    return Q
+
+
+def _orth(v, basis):
+    """v orthogonalised against the orthonormal columns in `basis` (twice)."""
+    for _ in range(2):
+        for q in basis:
+            v = v - np.vdot(q, v) * q
+    return v
+
+
+def mlbicgstab(A, b, tol=1e-8, max_iter=1000, x0=None, nvec=2):
+    """ML(n)BiCGSTAB (Yeung & Chan 1999), n = nvec left starting vectors
+    Q = shadow_vectors(r0, n), evaluated from its definition at the end of
+    every cycle (one iteration = one cycle of n + 1 products, the unit of
+    the paper's Table 3):
+
+    * phi_j, the ML(n)BiCG residual polynomial of degree j n (phi_j(0) = 1),
+      is fixed by phi_j(A) r0 orthogonal to the block Krylov space
+      K_j(A^H, Q) = span{(A^H)^l q_i : l < j, i <= n}: with V an orthonormal
+      basis of K_(jn)(A, r0), phi_j(A) r0 = r0 - A V y where
+      (W^H A V) y = W^H r0 for an orthonormal basis W of K_j(A^H, Q);
+    * v_j = Omega_(j-1)(A) phi_j(A) r0, Omega_j(t) = prod_(l<=j)(1 - omega_l t);
+    * omega_j minimises ||(I - omega A) v_j||: omega_j = (t^H v_j)/(t^H t),
+      t = A v_j, and the cycle's residual is r_j = v_j - omega_j t;
+    * x_j = x0 + S_j r0 + Omega_j(A) V y, with 1 - Omega_j(t) = t S_j(t)
+      (S_j r0 = (I - omega_j A) S_(j-1) r0 + omega_j r0), so b - A x_j = r_j.
+
+    Plain and slow (dense bases, every Omega applied factor by factor): for
+    small test systems only.  Stops when ||r_j|| <= tol ||b||; matvecs
+    reports the method's count j (n + 1).  info also carries `history`, the
+    relative residual after each cycle."""
+    x0v = np.zeros_like(b) if x0 is None else x0.copy()
+    r0 = b - A(x0v) if x0 is not None else b.copy()
+    nb = _norm(b)
+    rel = _norm(r0) / nb
+    hist = []
+    if rel <= tol:
+        info = _info(0, 0, True, False, rel)
+        info["history"] = hist
+        return x0v, info
+
+    def AH(v):
+        return np.conj(A(np.conj(v)))
+
+    Q = shadow_vectors(r0, nvec)
+    V, AV = [], []                    # orthonormal basis of K(A, r0) and A applied to it
+    W, last = [], None                # orthonormal basis of K_j(A^H, Q), last block
+    omegas = []
+    s = np.zeros_like(r0)             # S_j r0
+    x = x0v
+    for j in range(1, max_iter + 1):
+        # right space: K_(jn)(A, r0) by Arnoldi
+        while len(V) < j * nvec:
+            w = r0.copy() if not V else AV[-1].copy()
+            w = _orth(w, V)
+            nw = _norm(w)
+            if nw == 0:
+                break
+            V.append(w / nw)
+            AV.append(A(V[-1]))
+        # left space: one more block (A^H)^(j-1) Q, orthonormalised
+        block = [Q[:, i].reshape(r0.shape) for i in range(nvec)] if last is None else [AH(q) for q in last]
+        last = []
+        for w in block:
+            w = _orth(w, W)
+            nw = _norm(w)
+            if nw == 0:
+                continue
+            W.append(w / nw)
+            last.append(W[-1])
+        Vm = np.stack([v.reshape(-1) for v in V], axis=1)
+        AVm = np.stack([v.reshape(-1) for v in AV], axis=1)
+        Wm = np.stack([v.reshape(-1) for v in W], axis=1)
+        G = Wm.conj().T @ AVm
+        if G.shape[0] != G.shape[1]:
+            info = _info(j, j * (nvec + 1), False, True, rel)
+            info["history"] = hist
+            return x, info
+        y = np.linalg.solve(G, Wm.conj().T @ r0.reshape(-1))
+        u = r0 - (AVm @ y).reshape(r0.shape)
+        v = u
+        for om in omegas:
+            v = v - om * A(v)
+        t = A(v)
+        tt = np.vdot(t, t)
+        if tt == 0:
+            info = _info(j, j * (nvec + 1), _norm(v) == 0, _norm(v) != 0, _norm(v) / nb)
+            info["history"] = hist
+            return x, info
+        om = np.vdot(t, v) / tt
+        omegas.append(om)
+        r = v - om * t
+        s = s - om * A(s) + om * r0
+        z = (Vm @ y).reshape(r0.shape)
+        for w_ in omegas:
+            z = z - w_ * A(z)
+        x = x0v + s + z
+        rel = _norm(r) / nb
+        hist.append(rel)
+        if rel <= tol:
+            info = _info(j, j * (nvec + 1), True, False, rel)
+            info["history"] = hist
+            return x, info
+        if om == 0:
+            info = _info(j, j * (nvec + 1), False, True, rel)
+            info["history"] = hist
+            return x, info
+    info = _info(max_iter, max_iter * (nvec + 1), False, False, rel)
+    info["history"] = hist
+    return x, info
+
+
 def jacobi(solver, diag):
     """Point-Jacobi (diagonal) preconditioning of `solver`, applied as the
     symmetric scaling S A S y = S b, x = S y, S = diag^(-1/2) (principal
@@ -513,4 +667,7 @@ SOLVERS = {"bicg": bicg, "bicgstab": bicgstab, "qmr": qmr, "bicg_sym": bicg_sym,
            "tfqmr": tfqmr, "qmr_sym": qmr_sym,
            "rbicgstab1": lambda *a, **k: bicgstab_l(*a, ell=1, **k),
            "rbicgstab2": lambda *a, **k: bicgstab_l(*a, ell=2, **k),
-           "rbicgstab3": lambda *a, **k: bicgstab_l(*a, ell=3, **k)}
+           "rbicgstab3": lambda *a, **k: bicgstab_l(*a, ell=3, **k),
+           "mlbicgstab1": lambda *a, **k: mlbicgstab(*a, nvec=1, **k),
+           "mlbicgstab2": lambda *a, **k: mlbicgstab(*a, nvec=2, **k),
+           "mlbicgstab3": lambda *a, **k: mlbicgstab(*a, nvec=3, **k)}
