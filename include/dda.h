@@ -76,14 +76,21 @@ typedef enum { DDA_C128 = 0, DDA_C64 = 1 } dda_dtype;
  * complex-symmetric systems "QMR_sym" [1] and the restarted, stabilised BiCG
  * "RBiCGSTAB" as BiCGSTAB(l), l = 1, 2, 3 [2 l; one iteration = one cycle of
  * l BiCG steps and a degree-l minimal-residual polynomial, with the stopping
- * test at the end of a cycle].  OR DDA_PRECOND_JACOBI into
+ * test at the end of a cycle], and ML(n)BiCGSTAB (Yeung & Chan 1999), the
+ * BiCGSTAB variant with n left Lanczos starting vectors, n = 1, 2, 3 [n + 1;
+ * one iteration = one cycle, with the stopping test at its end; n = 1 is
+ * BiCGSTAB].  Its starting vectors are r0 and n - 1 pseudo-random vectors
+ * whose entry e of vector i is u1 + i u2, u1 and u2 being the first two
+ * SplitMix64 outputs from the state i * 2^40 + e mapped to [-1, 1) as
+ * (u >> 11) * 2^-52 - 1.  OR DDA_PRECOND_JACOBI into
  * the method for point-Jacobi preconditioning (Sec. 6), applied as the
  * symmetric scaling (S A S) y = S E_inc, P = S y, S = diag(alpha)^(1/2),
  * which keeps the matrix complex symmetric; the stopping test then applies
  * to the scaled residual. */
 typedef enum {
     DDA_BICG = 0, DDA_BICGSTAB = 1, DDA_QMR = 2, DDA_BICG_SYM = 3, DDA_CG = 4, DDA_CGS = 5, DDA_TFQMR = 6,
-    DDA_QMR_SYM = 7, DDA_RBICGSTAB1 = 8, DDA_RBICGSTAB2 = 9, DDA_RBICGSTAB3 = 10
+    DDA_QMR_SYM = 7, DDA_RBICGSTAB1 = 8, DDA_RBICGSTAB2 = 9, DDA_RBICGSTAB3 = 10,
+    DDA_MLBICGSTAB1 = 11, DDA_MLBICGSTAB2 = 12, DDA_MLBICGSTAB3 = 13
 } dda_method;
 #define DDA_PRECOND_JACOBI 0x100
 typedef enum { DDA_FP64 = 0, DDA_MIXED = 1 } dda_precision;
@@ -185,9 +192,9 @@ int dda_site_ranks(const dda_ctx* ctx, uint32_t* rank, void* stream);
 
 /*
  * Copy the stored half spectrum of the six tensor components, scaled by
- * 1 / (Lx Ly Lz): device complex [Lz/2+1][Ly/2+1][Lx/2+1][6] of the given
- * dtype (components xx, xy, xz, yy, yz, zz innermost).  Diagnostic entry
- * point (parity of the init step).
+ * 1 / (Lx Ly Lz): device complex [Ly/2+1][Lx/2+1][Lz/2+1][6] of the given
+ * dtype (the storage order: z lines contiguous, components xx, xy, xz, yy,
+ * yz, zz innermost).  Diagnostic entry point (parity of the init step).
  */
 int dda_tensor_spectrum(const dda_ctx* ctx, void* out, int dtype, void* stream);
 
@@ -218,13 +225,12 @@ int dda_matvec_batch(dda_ctx* ctx, int nb, const void* p, void* y, int dtype, vo
 
 /*
  * Tile settings of the matvec passes for dtype DDA_C128 or DDA_C64, as host
- * int[4]: tiles[0], [1], [2] = log2 of the lines one CTA transforms in
- * P1/P5 (y lines), P3 (z columns) and P2/P4 (x rows); tiles[3] = the z
- * pass schedule, 0 = one CTA per tile of columns, 1 = persistent CTAs that
- * stage the next tile's input columns in shared memory (cp.async) while
- * transforming the current one (whole tiles and 16-byte stage rows only).
- * tiles_in (may be NULL) sets them after checking the launch limits
- * (threads per block, shared memory; DDA_ERR_ARG when exceeded);
+ * int[4]: tiles[0] = log2 of the y lines (adjacent x columns) one CTA
+ * transforms in P1/P5, tiles[1] = log2 of the whole z columns one CTA
+ * transforms in P3, tiles[2] = log2 of the x lines (consecutive z planes)
+ * one CTA transforms and transposes in P2/P4; tiles[3] is reserved and
+ * must be 0.  tiles_in (may be NULL) sets them after checking the launch
+ * limits (threads per block, shared memory; DDA_ERR_ARG when exceeded);
  * tiles_out (may be NULL) receives the current ones.  The settings only
  * regroup lines between CTAs: every line's arithmetic, and so every result
  * bit, is the same for all valid settings.
@@ -233,19 +239,18 @@ int dda_tiles(dda_ctx* ctx, int dtype, int* tiles_out, const int* tiles_in);
 
 /*
  * Autotune the tile settings of dtype on this context: starting from the
- * current ones, try every z pass schedule with P3 widths up to two steps
- * either way of the current one, then up to two width steps for P1/P5 and
- * for P2/P4, timing `reps` batched products of nb right-hand sides per
- * candidate with CUDA events (after one untimed product), and keep the
- * fastest.  Last, the chosen settings and the starting ones are timed once
- * more, back to back, and the faster whole product wins (a guard against
- * timing noise between the steps).  The choice is set on the context and
- * remembered for the
- * process: contexts created later with the same lattice shape start with
- * it.  pass_ms (host double[5], may be NULL) receives the per-pass
- * milliseconds of the chosen widths.  Allocates (and frees) two scratch
- * vectors of nb right-hand sides; may grow the workspace to nb slots.
- * Synchronises the stream.
+ * current ones, try P3 widths up to two steps either way of the current
+ * one, then the same for P1/P5 and for P2/P4, timing `reps` batched
+ * products of nb right-hand sides per candidate with CUDA events (after
+ * one untimed product), and keep the fastest.  Last, against timing noise
+ * between those steps, the chosen and the starting settings are timed
+ * alternately three times each; the chosen ones stay unless the median
+ * whole product of the starting ones is more than 1% faster.  The choice
+ * is set on the context and remembered for the process: contexts created
+ * later with the same lattice shape start with it.  pass_ms (host
+ * double[5], may be NULL) receives the per-pass milliseconds of the chosen
+ * widths.  Allocates (and frees) two scratch vectors of nb right-hand
+ * sides; may grow the workspace to nb slots.  Synchronises the stream.
  */
 int dda_autotune(dda_ctx* ctx, int dtype, int nb, int reps, double* pass_ms, void* stream);
 
@@ -254,7 +259,7 @@ int dda_autotune(dda_ctx* ctx, int dtype, int nb, int reps, double* pass_ms, voi
  * for solves of the given precision, so that later calls with up to nb
  * right-hand sides allocate nothing.  Per right-hand side it holds 3
  * complex128 vectors of 3 N_d, one complex64 matvec work slot (2 for the
- * first) and 10 complex128 (DDA_FP64) or 12 complex64 (DDA_MIXED) Krylov
+ * first) and 12 complex128 (DDA_FP64) or 14 complex64 (DDA_MIXED) Krylov
  * vectors; dda_query reports the total.  DDA_ERR_OOM when it does not fit.
  */
 int dda_reserve(dda_ctx* ctx, int nb, int precision);
@@ -337,6 +342,8 @@ int dda_cross_sections_batch(dda_ctx* ctx, int nb, const void* einc, const void*
  *                   only (padding bits past n_sites are ignored).
  *   word_rank:      device uint32[ceil(n_sites/32)], written.
  *   n_occupied:     device uint32[1], written.
+ * A NULL pointer, or one that is not device (or managed) memory, returns
+ * DDA_ERR_ARG before any work is queued.
  * The scan keeps its per-block totals in a 16 KB array inside the library
  * (a file-scope __device__ array, one per GPU, held until the process
  * exits), which limits n_sites to 536,870,912 (4096 x 4096 x 32); larger

@@ -27,13 +27,15 @@ DDA_C64 = 1
 DDA_BICG, DDA_BICGSTAB, DDA_QMR, DDA_BICG_SYM = 0, 1, 2, 3
 DDA_CG, DDA_CGS, DDA_TFQMR, DDA_QMR_SYM = 4, 5, 6, 7
 DDA_RBICGSTAB1, DDA_RBICGSTAB2, DDA_RBICGSTAB3 = 8, 9, 10
+DDA_MLBICGSTAB1, DDA_MLBICGSTAB2, DDA_MLBICGSTAB3 = 11, 12, 13
 DDA_PRECOND_JACOBI = 0x100
 DDA_FP64, DDA_MIXED = 0, 1
 DDA_POL_CM, DDA_POL_CMRR, DDA_POL_LDR = 0, 1, 2
 
 METHODS = {"bicg": DDA_BICG, "bicgstab": DDA_BICGSTAB, "qmr": DDA_QMR, "bicg_sym": DDA_BICG_SYM, "cg": DDA_CG,
            "cgs": DDA_CGS, "tfqmr": DDA_TFQMR, "qmr_sym": DDA_QMR_SYM, "rbicgstab1": DDA_RBICGSTAB1,
-           "rbicgstab2": DDA_RBICGSTAB2, "rbicgstab3": DDA_RBICGSTAB3}
+           "rbicgstab2": DDA_RBICGSTAB2, "rbicgstab3": DDA_RBICGSTAB3, "mlbicgstab1": DDA_MLBICGSTAB1,
+           "mlbicgstab2": DDA_MLBICGSTAB2, "mlbicgstab3": DDA_MLBICGSTAB3}
 
 
 def method_code(method) -> int:
@@ -258,15 +260,14 @@ def _dtype_name(dtype):
 
 
 def dda_tiles(ctx, dtype="c64", tiles=None):
-    """Current tile settings (log2 lines per CTA of P1/P5, P3, P2/P4, and the
-    z pass schedule 0/1); sets them first when given (3 widths keep the
-    schedule)."""
+    """Current tile settings (log2 lines per CTA of P1/P5, P3 and P2/P4, and a
+    reserved 0); sets them first when given (with 3 widths the fourth is 0)."""
     out = np.zeros(4, dtype=np.int32)
     tin = None
     if tiles is not None:
         tiles = list(tiles)
         if len(tiles) == 3:
-            tiles.append(dda_tiles(ctx, dtype)[3])
+            tiles.append(0)
         tin = np.ascontiguousarray(np.asarray(tiles, dtype=np.int32).reshape(4))
     _check(load().dda_tiles(ctypes.c_void_p(ctx), _dtype_name(dtype), _ptr(out), _ptr(tin)))
     return tuple(int(v) for v in out)

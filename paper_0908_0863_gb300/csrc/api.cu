@@ -44,7 +44,7 @@ int cuda_fail(cudaError_t e, const char* what) {
     return e == cudaErrorMemoryAllocation ? DDA_ERR_OOM : DDA_ERR_CUDA;
 }
 
-static bool is_device_ptr(const void* p) {
+bool is_device_ptr(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
@@ -100,8 +100,8 @@ struct Space {
     // Krylov vectors
     int cap64 = 0, cap32 = 0;
     void *mem64 = nullptr, *mem32 = nullptr;
-    double2* v64[10] = {};
-    float2* v32[10] = {};
+    double2* v64[12] = {};
+    float2* v32[12] = {};
     float2 *b32 = nullptr, *d32 = nullptr;   // inner right-hand side and solution
     size_t bytes64 = 0, bytes32 = 0;
     cudaStream_t capture = nullptr;   // graph capture stream
@@ -159,7 +159,7 @@ int check_dev(const void* p, const char* what) {
 constexpr int kMaxBatch = 4096;
 
 // elements of one matvec work slot (Ay + Bxy)
-size_t work_elems(const Geometry& g) { return 3ull * g.P * g.Ly * ((size_t)g.K + g.Lx); }
+size_t work_elems(const Geometry& g) { return 3ull * g.Ly * ((size_t)g.P * g.K + (size_t)g.Pb * g.Lx); }
 
 int ensure_core(Space& sp, int nb) {
     if (sp.cap_core >= nb) return 0;
@@ -231,13 +231,13 @@ int ensure_v64(Space& sp, int nb) {
     sp.bytes64 = 0;
     const size_t n = (size_t)sp.n;
     Arena probe;
-    for (int i = 0; i < 10; ++i) probe.take<double2>(nb * n);
+    for (int i = 0; i < 12; ++i) probe.take<double2>(nb * n);
     Arena a;
     a.cap = probe.used + 256;
     cudaError_t e = cudaMalloc(&sp.mem64, a.cap);
     if (e != cudaSuccess) { sp.mem64 = nullptr; return cuda_fail(e, "FP64 Krylov vectors"); }
     a.base = static_cast<char*>(sp.mem64);
-    for (int i = 0; i < 10; ++i) sp.v64[i] = a.take<double2>(nb * n);
+    for (int i = 0; i < 12; ++i) sp.v64[i] = a.take<double2>(nb * n);
     sp.cap64 = nb;
     sp.bytes64 = a.cap;
     return 0;
@@ -250,13 +250,13 @@ int ensure_v32(Space& sp, int nb) {
     sp.bytes32 = 0;
     const size_t n = (size_t)sp.n;
     Arena probe;
-    for (int i = 0; i < 12; ++i) probe.take<float2>(nb * n);
+    for (int i = 0; i < 14; ++i) probe.take<float2>(nb * n);
     Arena a;
     a.cap = probe.used + 256;
     cudaError_t e = cudaMalloc(&sp.mem32, a.cap);
     if (e != cudaSuccess) { sp.mem32 = nullptr; return cuda_fail(e, "complex64 Krylov vectors"); }
     a.base = static_cast<char*>(sp.mem32);
-    for (int i = 0; i < 10; ++i) sp.v32[i] = a.take<float2>(nb * n);
+    for (int i = 0; i < 12; ++i) sp.v32[i] = a.take<float2>(nb * n);
     sp.b32 = a.take<float2>(nb * n);
     sp.d32 = a.take<float2>(nb * n);
     sp.cap32 = nb;
@@ -309,7 +309,7 @@ KrylovWork<double> work64(const dda_ctx* c, int nb) {
     KrylovWork<double> w;
     w.n = c->sp.n;
     w.nb = nb;
-    for (int i = 0; i < 10; ++i) w.v[i] = c->sp.v64[i];
+    for (int i = 0; i < 12; ++i) w.v[i] = c->sp.v64[i];
     w.part = c->sp.part64;
     w.st = c->sp.st64;
     w.host = c->sp.host;
@@ -321,7 +321,7 @@ KrylovWork<float> work32(const dda_ctx* c, int nb) {
     KrylovWork<float> w;
     w.n = c->sp.n;
     w.nb = nb;
-    for (int i = 0; i < 10; ++i) w.v[i] = c->sp.v32[i];
+    for (int i = 0; i < 12; ++i) w.v[i] = c->sp.v32[i];
     w.part = c->sp.part32;
     w.st = c->sp.st32;
     w.host = c->sp.host;
@@ -342,7 +342,6 @@ void apply_tiles(MatvecView<T>& m, const std::array<int, 4>& t) {
     m.logW_y = t[0];
     m.logW_z = t[1];
     m.logW_x = t[2];
-    m.p3_sched = t[3];
 }
 
 int64_t context_bytes(const dda_ctx* c) {
@@ -459,6 +458,7 @@ int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occu
     g.K = shape[0]; g.J = shape[1]; g.P = shape[2];
     g.Lx = padded_length(g.K); g.Ly = padded_length(g.J); g.Lz = padded_length(g.P);
     g.Hx = g.Lx / 2 + 1; g.Hy = g.Ly / 2 + 1; g.Hz = g.Lz / 2 + 1;
+    g.Pb = column_pitch(g.P);
     g.nsites = (int64_t)g.K * g.J * g.P;
     g.nwords = (g.nsites + 31) / 32;
     g.nmat = n_materials;
@@ -685,22 +685,21 @@ int dda_tiles(dda_ctx* c, int dtype, int* tiles_out, const int* tiles_in) {
     if (int rc = check_ctx(c)) return rc;
     if (dtype != DDA_C128 && dtype != DDA_C64) return fail(DDA_ERR_ARG, "dda_tiles: unknown dtype");
     if (tiles_in) {
-        const bool ok =
-            dtype == DDA_C128 ? tiles_ok<double>(c->g, tiles_in[0], tiles_in[1], tiles_in[2], tiles_in[3])
-                              : tiles_ok<float>(c->g, tiles_in[0], tiles_in[1], tiles_in[2], tiles_in[3]);
-        if (!ok) return fail(DDA_ERR_ARG, "dda_tiles: tile widths or schedule not launchable for this lattice");
-        const std::array<int, 4> t{tiles_in[0], tiles_in[1], tiles_in[2], tiles_in[3]};
+        const bool ok = tiles_in[3] == 0 &&
+                        (dtype == DDA_C128 ? tiles_ok<double>(c->g, tiles_in[0], tiles_in[1], tiles_in[2])
+                                           : tiles_ok<float>(c->g, tiles_in[0], tiles_in[1], tiles_in[2]));
+        if (!ok) return fail(DDA_ERR_ARG, "dda_tiles: tile widths not launchable for this lattice");
+        const std::array<int, 4> t{tiles_in[0], tiles_in[1], tiles_in[2], 0};
         if (dtype == DDA_C128) apply_tiles(c->mv64, t);
         else apply_tiles(c->mv32, t);
     }
     if (tiles_out) {
         if (dtype == DDA_C128) {
             tiles_out[0] = c->mv64.logW_y; tiles_out[1] = c->mv64.logW_z; tiles_out[2] = c->mv64.logW_x;
-            tiles_out[3] = c->mv64.p3_sched;
         } else {
             tiles_out[0] = c->mv32.logW_y; tiles_out[1] = c->mv32.logW_z; tiles_out[2] = c->mv32.logW_x;
-            tiles_out[3] = c->mv32.p3_sched;
         }
+        tiles_out[3] = 0;
     }
     return DDA_OK;
 }
@@ -726,16 +725,16 @@ int dda_autotune(dda_ctx* c, int dtype, int nb, int reps, double* pass_ms, void*
     const int d = dtype == DDA_C128 ? 0 : 1;
     auto current = [&]() {
         return dtype == DDA_C128
-                   ? std::array<int, 4>{c->mv64.logW_y, c->mv64.logW_z, c->mv64.logW_x, c->mv64.p3_sched}
-                   : std::array<int, 4>{c->mv32.logW_y, c->mv32.logW_z, c->mv32.logW_x, c->mv32.p3_sched};
+                   ? std::array<int, 4>{c->mv64.logW_y, c->mv64.logW_z, c->mv64.logW_x, 0}
+                   : std::array<int, 4>{c->mv32.logW_y, c->mv32.logW_z, c->mv32.logW_x, 0};
     };
     auto set = [&](const std::array<int, 4>& t) {
         if (dtype == DDA_C128) apply_tiles(c->mv64, t);
         else apply_tiles(c->mv32, t);
     };
     auto valid = [&](const std::array<int, 4>& t) {
-        return dtype == DDA_C128 ? tiles_ok<double>(c->g, t[0], t[1], t[2], t[3])
-                                 : tiles_ok<float>(c->g, t[0], t[1], t[2], t[3]);
+        return dtype == DDA_C128 ? tiles_ok<double>(c->g, t[0], t[1], t[2])
+                                 : tiles_ok<float>(c->g, t[0], t[1], t[2]);
     };
     // one warm product, then reps timed ones; per-pass average milliseconds
     auto time_tiles = [&](double (&out)[5]) -> int {
@@ -756,8 +755,8 @@ int dda_autotune(dda_ctx* c, int dtype, int nb, int reps, double* pass_ms, void*
     double best_ms[5] = {};
     if (!rc) rc = time_tiles(best_ms);
     const std::array<int, 4> initial = current();
-    // P3's width (index 1) and schedule (3) together, then P1/P5's width
-    // (0), then P2/P4's (2)
+    // P3's width (index 1), then P1/P5's (0), then P2/P4's (2), each over
+    // two steps either side of the current one
     for (int a : {1, 0, 2}) {
         if (rc) break;
         std::array<int, 4> best = current();
@@ -765,11 +764,9 @@ int dda_autotune(dda_ctx* c, int dtype, int nb, int reps, double* pass_ms, void*
         double best_cost = cost(best_ms);
         const std::array<int, 4> start = best;
         const int center = start[a];
-        for (int cand = 0; cand < 5 * kP3Schedules && !rc; ++cand) {
+        for (int cand = 0; cand < 5 && !rc; ++cand) {
             std::array<int, 4> t = start;
-            t[a] = center - 2 + cand % 5;
-            if (a == 1) t[3] = cand / 5;
-            else if (cand >= 5) break;
+            t[a] = center - 2 + cand;
             if (t == start || t[a] < 0 || !valid(t)) continue;
             set(t);
             double m[5];
@@ -782,25 +779,32 @@ int dda_autotune(dda_ctx* c, int dtype, int nb, int reps, double* pass_ms, void*
         }
         set(best);
     }
-    // each step compared timings of separate runs; against that noise, the
-    // chosen settings and the initial ones are timed once more, one after
-    // the other, and the faster whole product is kept
+    // Each step compared timings of separate runs.  Against that noise the
+    // chosen and the initial settings are then timed alternately, three
+    // rounds each, and the chosen ones are kept unless the median of the
+    // initial ones is faster by more than 1%.
     if (!rc && current() != initial) {
         const std::array<int, 4> chosen = current();
-        double mc[5], mi[5];
-        rc = time_tiles(mc);
-        if (!rc) {
+        double tc[3], ti[3], mc[5] = {};
+        for (int r = 0; r < 3 && !rc; ++r) {
+            double m[5];
+            set(chosen);
+            rc = time_tiles(m);
+            tc[r] = m[0] + m[1] + m[2] + m[3] + m[4];
+            if (r == 0) std::copy(m, m + 5, mc);
+            if (rc) break;
             set(initial);
-            rc = time_tiles(mi);
+            rc = time_tiles(m);
+            ti[r] = m[0] + m[1] + m[2] + m[3] + m[4];
         }
         if (!rc) {
-            double tc = 0.0, ti = 0.0;
-            for (int q = 0; q < 5; ++q) { tc += mc[q]; ti += mi[q]; }
-            if (tc <= ti) {
+            std::sort(tc, tc + 3);
+            std::sort(ti, ti + 3);
+            if (ti[1] < 0.99 * tc[1]) {
+                set(initial);
+            } else {
                 set(chosen);
                 std::copy(mc, mc + 5, best_ms);
-            } else {
-                std::copy(mi, mi + 5, best_ms);
             }
         }
     }
@@ -1014,7 +1018,7 @@ static int check_solve_args(const dda_ctx* c, int nb, const void* einc, const vo
     if (int rc = check_ctx(c)) return rc;
     if (nb < 1 || nb > kMaxBatch) return fail(DDA_ERR_ARG, "dda_solve: nb must be in [1, 4096]");
     if (!einc || !p) return fail(DDA_ERR_ARG, "dda_solve: NULL einc or p");
-    if ((method & ~(0xff | DDA_PRECOND_JACOBI)) || (method & 0xff) > DDA_RBICGSTAB3)
+    if ((method & ~(0xff | DDA_PRECOND_JACOBI)) || (method & 0xff) > DDA_MLBICGSTAB3)
         return fail(DDA_ERR_ARG, "dda_solve: unknown method");
     if (precision != DDA_FP64 && precision != DDA_MIXED) return fail(DDA_ERR_ARG, "dda_solve: unknown precision");
     if (!(tol > 0.0) || !std::isfinite(tol)) return fail(DDA_ERR_ARG, "dda_solve: tol must be finite and > 0");

@@ -49,6 +49,10 @@ int cuda_fail(cudaError_t e, const char* what);
 
 void note_launches(int64_t n);
 
+// true for device or managed memory of any device; false for host memory,
+// stale or foreign pointers (checked on the host before any launch)
+bool is_device_ptr(const void* p);
+
 // after every kernel launch: count it and turn a launch error into a status
 #define DDA_LAUNCH_CHECK(what)                                           \
     do {                                                                 \
@@ -62,8 +66,9 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 // -------------------------------------------------------- lattice geometry
 struct Geometry {
     int K, J, P;          // lattice edges (x, y, z)
-    int Lx, Ly, Lz;       // padded DFT lengths, powers of two >= 2n - 1
+    int Lx, Ly, Lz;       // padded DFT lengths (padded_length)
     int Hx, Hy, Hz;       // stored half-spectrum extents L/2 + 1
+    int Pb;               // pitch of the z columns of the xy-transformed volume (>= P)
     int64_t nsites;       // K J P
     int64_t nwords;       // occupancy words
     int64_t nd;           // occupied sites
@@ -84,6 +89,15 @@ inline int padded_length(int n) {
         if (!best || L < best) best = L;
     }
     return best;
+}
+// Column pitch of the xy-transformed volume: P rounded up to a multiple of
+// 8 elements, and to an odd multiple of 8 (so that the columns, read and
+// written 64 or 128 bytes at a time across x by the x passes, do not start
+// at a power-of-two stride)
+inline int column_pitch(int P) {
+    int p = (P + 7) / 8 * 8;
+    if ((p / 8) % 2 == 0) p += 8;
+    return p;
 }
 inline int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
 

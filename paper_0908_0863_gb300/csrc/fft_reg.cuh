@@ -31,11 +31,12 @@
 // stage of a power-of-two length (a 3 * 2^a or 5 * 2^a length computes all
 // outputs).
 //
-// Shared-memory addresses come from a layout functor (line w, point p):
-// RowLayout keeps each line contiguous (lines of the lattice that are
-// contiguous in memory, threads t-fastest); ColLayoutT keeps point-major
-// tiles of 2^logW lines side by side (strided lines of the lattice, threads
-// w-fastest).
+// Shared-memory addresses come from a layout functor (line w, point p),
+// which also provides the barrier of the exchanges: RowLayout keeps each
+// line contiguous (lines of the lattice that are contiguous in memory,
+// threads t-fastest) and RowGroupLayout does the same with a barrier per
+// group of lines; ColLayoutT keeps point-major tiles of 2^logW lines side
+// by side (strided lines of the lattice, threads w-fastest).
 //
 // Lines shorter than 8 points (lattice edges of 1 or 2 sites) are done by
 // one thread each in registers.  Twiddles come from the FP64 table
@@ -73,13 +74,35 @@ template <int N>
 struct RowLayout {
     static constexpr int ld = N + N / 16 + 1;
     __device__ __forceinline__ int operator()(int w, int p) const { return w * ld + p + (p >> 4); }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
 };
+// RowLayout whose exchanges synchronise only a group of whole warps holding
+// whole lines (named barrier `id` > 0 over `count` threads), so that the
+// groups of a CTA progress independently; id 0 synchronises the CTA
+template <int N>
+struct RowGroupLayout {
+    static constexpr int ld = N + N / 16 + 1;
+    int id, count;
+    __device__ __forceinline__ int operator()(int w, int p) const { return w * ld + p + (p >> 4); }
+    __device__ __forceinline__ void sync() const {
+        if (id == 0) __syncthreads();
+        else asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(count) : "memory");
+    }
+};
+// lines of N points per barrier group of RowGroupLayout: the fewest whole
+// lines that fill whole warps
+__host__ __device__ constexpr int row_group_lines(int N) {
+    int g = 1;
+    while (((N >= 8 ? N / 8 : 1) * g) % 32 != 0) g *= 2;
+    return g;
+}
 // 2^LOGW lines per tile, one pad row after every 8 points; the width is a
 // compile-time constant, so every exchange address folds into a constant
 // offset from the thread's base
 template <int LOGW>
 struct ColLayoutT {
     __device__ __forceinline__ int operator()(int w, int p) const { return ((p + (p >> 3)) << LOGW) + w; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
 };
 
 __host__ __device__ constexpr int row_ld(int N) { return N + N / 16 + 1; }
@@ -240,7 +263,7 @@ __device__ __forceinline__ void odd_finish(C<T> (&v)[NL][8], C<T>* __restrict__ 
             for (int r = 1; r < R; ++r) wq[q][r] = twiddle<T, INV>(tw, off + jj * r * step);
         }
     }
-    __syncthreads();
+    L.sync();
 #pragma unroll
     for (int q = 0; q < nq; ++q) {
         const int j = t + q * Tn;
@@ -266,9 +289,9 @@ __device__ __forceinline__ void odd_finish(C<T> (&v)[NL][8], C<T>* __restrict__ 
             }
         }
     }
-    __syncthreads();
+    L.sync();
     read_canonical<T, N, NL>(v, sm, region, L, w, t);
-    if constexpr (TAIL) __syncthreads();
+    if constexpr (TAIL) L.sync();
 }
 
 // radix-8 stages from Ns = 2^LOGNS on.  The last one of a 2^a line leaves
@@ -292,12 +315,12 @@ struct Radix8Stages {
                 for (int l = 0; l < NL; ++l) sm[l * region + o] = v[l][r];
             }
             if constexpr (LOGNS + 3 < LOGM) {
-                __syncthreads();
+                L.sync();
                 read_canonical<T, N, NL>(v, sm, region, L, w, t);
                 // the next stage writes shared memory again, unless it is
                 // the last one of a 2^a line (registers only); then only a
                 // caller that reuses the buffer (TAIL) needs the barrier
-                if constexpr (TAIL || LOGNS + 6 < LOGM || Line<N>::ODD) __syncthreads();
+                if constexpr (TAIL || LOGNS + 6 < LOGM || Line<N>::ODD) L.sync();
                 Radix8Stages<T, INV, N, LOGNS + 3, NL, HALF_OUT, Layout, TAIL>::run(v, sm, region, L, w, t, tw);
             } else {
                 odd_finish<T, INV, N, NL, TAIL>(v, sm, region, L, w, t, tw);
@@ -367,9 +390,9 @@ __device__ __forceinline__ void fft_lines(C<T> (&v)[NL][8], C<T>* __restrict__ s
             // the first stage was the only power-of-two stage (N = 3 * 8, 5 * 8)
             odd_finish<T, INV, N, NL, TAIL>(v, sm, region, L, w, t, tw);
         } else {
-            __syncthreads();
+            L.sync();
             read_canonical<T, N, NL>(v, sm, region, L, w, t);
-            if constexpr (TAIL || L1 + 3 < LOGM || Line<N>::ODD) __syncthreads();
+            if constexpr (TAIL || L1 + 3 < LOGM || Line<N>::ODD) L.sync();
             Radix8Stages<T, INV, N, L1, NL, HALF_OUT, Layout, TAIL>::run(v, sm, region, L, w, t, tw);
         }
     }

@@ -15,7 +15,10 @@ enum Slot {
     S_RHO_NEW, S_XI_NEW, S_TMP,
     S_TAU, S_THETA, S_CD,                            // TFQMR: tau, theta, theta^2 eta / alpha
     S_G1, S_G2, S_G3,                                // BiCGSTAB(ell): minimal-residual coefficients
-    S_NSLOTS
+    S_ML,                                            // ML(n)BiCGSTAB: M = Q^H dR (n x n, column j at
+                                                     // S_ML + 3 j), then f = Q^H r (S_ML + 9), c
+                                                     // (S_ML + 12), omega (S_ML + 15), oldest column (S_ML + 16)
+    S_NSLOTS = S_ML + 17
 };
 
 // ST_RUN must stay 0: the matvec passes skip a right-hand side whose status

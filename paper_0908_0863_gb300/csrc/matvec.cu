@@ -6,17 +6,15 @@
 namespace dda {
 
 template <typename T>
-bool tiles_ok(const Geometry& g, int logW_y, int logW_z, int logW_x, int p3_sched) {
-    if (p3_sched < 0 || p3_sched >= kP3Schedules) return false;
-    if (p3_sched == 1 && (logW_z < 0 || logW_z > kMaxLogW || !p3_persistent_ok<T>(g, logW_z))) return false;
+bool tiles_ok(const Geometry& g, int logW_y, int logW_z, int logW_x) {
     const int elt = sizeof(C<T>);
     const int ty = threads_of(g.Ly), tz = threads_of(g.Lz), tx = threads_of(g.Lx);
     if (logW_y < 0 || logW_z < 0 || logW_x < 0) return false;
-    if (logW_y > kMaxLogW || logW_z > kMaxLogW || logW_x > 10) return false;   // compiled widths
+    if (logW_y > kMaxLogW || logW_z > kMaxLogR || logW_x > kMaxLogZ) return false;
     if ((1 << logW_y) * ty > kYThreads || 3ull * (1ull << logW_y) * col_elems(g.Ly, 1) * elt > 200 * 1024) return false;
-    if ((1 << logW_z) * tz > p3_max_threads<T>() || 3ull * col_elems(g.Lz, 1 << logW_z) * elt > 220 * 1024)
+    if ((1 << logW_z) * tz > p3_max_threads<T>() || 3ull * (1ull << logW_z) * row_ld(g.Lz) * elt > 200 * 1024)
         return false;
-    if ((1 << logW_x) * tx > 512 || (1ull << logW_x) * row_ld(g.Lx) * elt > 200 * 1024) return false;
+    if ((1 << logW_x) * tx > kRowThreads || rows_smem_elems(g.Lx, 1 << logW_x) * elt > 200 * 1024) return false;
     return true;
 }
 
@@ -25,17 +23,23 @@ void configure_matvec(MatvecView<T>& mv) {
     const Geometry& g = mv.g;
     const int elt = sizeof(C<T>);
     const int ty = threads_of(g.Ly), tz = threads_of(g.Lz), tx = threads_of(g.Lx);
-    // strided passes: W adjacent columns (64-byte rows)
+    // P1/P5: W adjacent columns (64-byte rows)
     int wy = floor_log2(64 / elt);
     while (wy > 0 && (1 << wy) * ty > kYThreads) --wy;
     while (wy > 0 && 3ull * (1ull << wy) * col_elems(g.Ly, 1) * elt > 200 * 1024) --wy;   // P1's three regions
     while (wy > 0 && (1 << (wy - 1)) >= g.K) --wy;          // no wider than the lattice
-    int wz = floor_log2(64 / elt);
-    while (wz > 0 && (1 << wz) * tz > p3_max_threads<T>()) --wz;
-    while (wz > 0 && 3ull * col_elems(g.Lz, 1 << wz) * elt > 200 * 1024) --wz;
-    while (wz > 0 && (1 << (wz - 1)) >= g.Lx) --wz;
-    int wx = 0;                                             // rows per CTA: about 128 threads
-    while ((2 << wx) * tx <= 128) ++wx;
+    // P3: the fewest whole columns per CTA that fill at least two warps
+    // exactly (small independent CTAs, many per SM)
+    int wz = 0;
+    while (wz < kMaxLogR && (((1 << wz) * tz) < 64 || (((1 << wz) * tz) & 31)) &&
+           (2 << wz) * tz <= p3_max_threads<T>() && (1 << wz) < g.Lx)
+        ++wz;
+    // P2/P4: 32 bytes of each column of Bxy per CTA (4 complex64 or 2
+    // complex128 consecutive z lines): whole sectors with small CTAs, which
+    // measured faster than 64- or 128-byte tiles with larger CTAs
+    int wx = floor_log2(32 / elt);
+    while (wx > 0 && !tiles_ok<T>(g, wy, wz, wx)) --wx;
+    while (wx > 0 && (1 << (wx - 1)) >= g.P) --wx;
     mv.logW_y = wy;
     mv.logW_z = wz;
     mv.logW_x = wx;
@@ -79,8 +83,8 @@ template int pass3<float>(const MatvecView<float>&, cudaStream_t);
 
 template void configure_matvec<double>(MatvecView<double>&);
 template void configure_matvec<float>(MatvecView<float>&);
-template bool tiles_ok<double>(const Geometry&, int, int, int, int);
-template bool tiles_ok<float>(const Geometry&, int, int, int, int);
+template bool tiles_ok<double>(const Geometry&, int, int, int);
+template bool tiles_ok<float>(const Geometry&, int, int, int);
 template int launch_matvec<double>(const MatvecView<double>&, const C<double>*, C<double>*, cudaStream_t);
 template int launch_matvec<float>(const MatvecView<float>&, const C<float>*, C<float>*, cudaStream_t);
 

@@ -6,19 +6,18 @@
 
 namespace dda {
 
-constexpr int kP3Schedules = 2;   // z pass schedules (MatvecView::p3_sched)
-
 template <typename T>
 struct MatvecView {
     Geometry g;
     TargetView tv;
     const C<T>* ainv;   // [nmat][3] alpha^-1
-    const C<T>* spec;   // [Hz][Hy][Hx][6], scaled by 1/(Lx Ly Lz)
+    const C<T>* spec;   // [Hy][Hx][Hz][6], scaled by 1/(Lx Ly Lz)
     const C<T>* tw;     // twiddle tables exp(-2 pi i m / 3072) then exp(-2 pi i m / 5120)
-    C<T>* Ay;           // [slots][3][P][Ly][K]
-    C<T>* Bxy;          // [slots][3][P][Ly][Lx]
-    int logW_y, logW_x, logW_z;  // tile widths (lines per CTA) of the passes
-    int p3_sched = 0;   // z pass: 0 = one CTA per tile, 1 = persistent CTAs with staged inputs
+    C<T>* Ay;           // [slots][3][P][Ly][K] (x fastest)
+    C<T>* Bxy;          // [slots][3][Ly][Lx][Pb] (z fastest, P of Pb used)
+    int logW_y;         // log2 of the y lines (adjacent x columns) per CTA of P1 and P5
+    int logW_z;         // log2 of the whole z columns per CTA of P3
+    int logW_x;         // log2 of the x lines (consecutive z planes) per CTA of P2 and P4
     const int* status;  // optional: right-hand side b is skipped while
                         // status[b * status_stride] != 0
     int status_stride;  // ints between the status words of consecutive RHS
@@ -45,7 +44,7 @@ __device__ __forceinline__ bool rhs_done(const MatvecView<T>& mv, int b) {
 template <typename T> void configure_matvec(MatvecView<T>& mv);
 // whether tile widths (log2 of lines per CTA of P1/P5, P3 and P2/P4) fit the
 // launch limits (threads per block, shared memory) for this geometry
-template <typename T> bool tiles_ok(const Geometry& g, int logW_y, int logW_z, int logW_x, int p3_sched = 0);
+template <typename T> bool tiles_ok(const Geometry& g, int logW_y, int logW_z, int logW_x);
 template <typename T> int launch_matvec(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t st);
 
 }  // namespace dda

@@ -4,10 +4,10 @@
 // every line length (and tile width) and exposes its dispatcher; matvec.cu
 // sequences the passes.
 //
-// Five stream-ordered passes over device arrays (x fastest everywhere):
-//   P1  expand + y-forward   compressed p -> Ay[3][P][Ly][K]   (K*P lines per component;
+// Five stream-ordered passes over device arrays:
+//   P1  expand + y-forward   compressed p -> Ay[3][P][Ly][K] (x fastest;  K*P lines per component;
 //                            a thread gathers a site's three components together)
-//   P2  x-forward            Ay -> Bxy[3][P][Ly][Lx]           (Ly*P lines, K nonzero inputs)
+//   P2  x-forward            Ay -> Bxy[3][Ly][Lx][Pb] (z fastest)      (Ly*P lines, K nonzero inputs)
 //   P3  z conv               per (ix, jy): z-forward of the 3 components (P nonzero
 //                            inputs), the 3x3 spectrum product of Eqs. 6-8 with the
 //                            signed mirror lookup, z-inverse keeping k < P, in place
@@ -21,27 +21,34 @@
 // zero half of their input and inverse transforms compute only the half of
 // the output that is kept.
 //
+// Layout of the xy-transformed volume: every z line of Bxy is contiguous,
+// and so is every z line of the half spectrum ([Hy][Hx][Hz][6]).  The z
+// pass, which does most of the work (a forward and an inverse transform of
+// every line, and the product), therefore runs small independent CTAs of a
+// few whole columns each, so that while some wait for memory others
+// compute.  The transpose between x-fastest Ay and z-fastest Bxy is done by
+// P2 and P4 through shared memory, on tiles of Wz x lines of consecutive z.
+//
 // Batches: one launch of each pass covers up to `slots` right-hand sides
 // that share the context's spectrum (vectors [nb][3][N_d], work arrays one
 // per slot); a right-hand side whose solver status is no longer "running"
 // is skipped block by block.  The slot is a grid coordinate of its own (no
 // index division in the kernels); in P3 it is the fastest-varying one, so
-// the CTAs of all right-hand sides that read one spectrum tile run back to
-// back and the tile is fetched from HBM once.
+// the CTAs of all right-hand sides that read one spectrum line run back to
+// back and the line is fetched from HBM once.
 //
 // Every pass keeps its lines in registers (fft_reg.cuh): points are loaded
 // from global memory straight into the registers of the first DFT stage and
 // stored from the registers of the last, and only the exchanges between
-// stages use shared memory.  Strided lines (y, z) are processed W at a
+// stages use shared memory.  Strided y lines (P1, P5) are processed W at a
 // time, W adjacent columns so that each load and store touches W
 // contiguous elements.  In P3 each thread carries the same column of all
 // three components, so the spectrum product happens in registers between
 // the forward and the inverse transforms; in P1 it gathers a site's three
 // components with one occupancy and rank lookup.  Each kernel is compiled
 // for every line length N (2^a up to 1024, 3 * 2^a from 24 to 768, 5 * 2^a
-// from 40 to 640) and, for the strided passes, every tile width (LOGW =
-// 0..4 lines per CTA, log2), and picked at launch, so all shared-memory
-// addresses are compile-time offsets.
+// from 40 to 640) and, for P1 and P5, every tile width (LOGW = 0..4 lines
+// per CTA, log2), and picked at launch.
 #pragma once
 
 #include <algorithm>
@@ -53,9 +60,15 @@
 namespace dda {
 
 
-// P3 keeps 3 x 8 complex values per thread: 512 threads fit the register
-// file for complex64, 256 for complex128
+// P3 keeps 3 x 8 complex values per thread: at most 512 threads per CTA for
+// complex64, 256 for complex128
 template <typename T> __host__ __device__ constexpr int p3_max_threads() { return sizeof(T) == 4 ? 512 : 256; }
+// widest tiles the runtime widths of P3 (columns per CTA) and P2/P4 (z lines
+// per CTA) may take, as log2
+constexpr int kMaxLogR = 6;
+constexpr int kMaxLogZ = 4;
+// P2/P4 keep eight points of one row per thread: up to 1024 threads per CTA
+constexpr int kRowThreads = 1024;
 
 // P1 and P5 keep the eight points, their gather indices and (P5) the
 // gathered entries of p in registers: at most 512 threads per CTA leave
@@ -65,7 +78,11 @@ constexpr int kYThreads = 512;
 
 // elements of one slot of the work arrays
 __host__ __device__ __forceinline__ int64_t ay_elems(const Geometry& g) { return 3LL * g.P * g.Ly * g.K; }
-__host__ __device__ __forceinline__ int64_t bxy_elems(const Geometry& g) { return 3LL * g.P * g.Ly * g.Lx; }
+__host__ __device__ __forceinline__ int64_t bxy_elems(const Geometry& g) { return 3LL * g.Pb * g.Ly * g.Lx; }
+// Element offsets inside one work slot of Bxy ([3][Ly][Lx][Pb], columns of
+// P values at pitch Pb) and inside the half spectrum fit in 32 bits for
+// every lattice the library accepts (edges <= 512: 3 Ly Lx Pb < 2^31,
+// 6 Hy Hx Hz < 2^31).
 
 // ---------------------------------------------------------------- P1
 template <typename T, int N, int LOGW>
@@ -139,35 +156,49 @@ __global__ void __launch_bounds__(kYThreads) k_p1(MatvecView<T> mv, const C<T>* 
 }
 
 // ------------------------------------------------------- P2 / P4 (rows)
-// Forward: rows of K inputs (Ay) -> Lx outputs (Bxy).  Inverse: rows of Lx
-// inputs (Bxy) -> first K outputs (Ay).  2^logW_x rows per CTA.
-template <typename T, bool INV, int N>
-__global__ void __launch_bounds__(512) k_rows(MatvecView<T> mv) {
-    const int j = blockIdx.y;                               // batch slot
+// One CTA takes the x lines of Wz = 2^LOGZ consecutive z planes at one
+// (component, y row): rows of K inputs in Ay (x fastest) and the same x
+// positions of Wz consecutive z in the columns of Bxy (z fastest).  Threads
+// run w-fastest (w = z offset, t = point slot), so each load or store of
+// the column side touches Wz consecutive z values of one x (64 bytes and
+// more), and the row side whole 32-byte sectors of Wz rows.
+// Forward (P2): Ay rows -> transform -> Bxy.  Inverse (P4): Bxy ->
+// transform -> the first K outputs into Ay.  Grid: (z tiles, Ly, 3 nb).
+template <typename T, bool INV, int N, int LOGZ>
+__global__ void __launch_bounds__(kRowThreads) k_rows(MatvecView<T> mv) {
+    const int c = blockIdx.z % 3, j = blockIdx.z / 3;      // component, batch slot
     if (rhs_done(mv, mv.b0 + j)) return;
     extern __shared__ unsigned char smem_raw[];
     C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
-    constexpr int TL = Line<N>::T, nv = Line<N>::NV;
+    constexpr int TL = Line<N>::T, nv = Line<N>::NV, Wz = 1 << LOGZ;
     const Geometry& g = mv.g;
-    const int t = threadIdx.x % TL, wl = threadIdx.x / TL;
-    const int64_t nrows = 3LL * g.P * g.Ly;
-    const int64_t row = ((int64_t)blockIdx.x << mv.logW_x) + wl;
-    const bool ok = row < nrows;
-    const int nin = INV ? N : g.K, nout = INV ? g.K : N;
-    const C<T>* src = (INV ? mv.Bxy + j * bxy_elems(g) : mv.Ay + j * ay_elems(g)) + (ok ? row * (INV ? N : g.K) : 0);
-    C<T>* dst = (INV ? mv.Ay + j * ay_elems(g) : mv.Bxy + j * bxy_elems(g)) + (ok ? row * (INV ? g.K : N) : 0);
+    const int w = threadIdx.x & (Wz - 1), t = threadIdx.x >> LOGZ;
+    const int y = blockIdx.y, z = blockIdx.x * Wz + w;
+    const bool ok = z < g.P;
+    C<T>* row = mv.Ay + j * ay_elems(g) + ((c * g.P + (ok ? z : 0)) * g.Ly + y) * g.K;
+    C<T>* col = mv.Bxy + j * bxy_elems(g) + (c * g.Ly + y) * g.Lx * g.Pb + (ok ? z : 0);
     C<T> v[8];
+    if (!INV) {
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
-        const int n = t + m * TL;
-        v[m] = (ok && m < nv && n < nin) ? src[n] : mk<T>(0, 0);
-    }
-    fft_regs<T, INV, N, !INV, INV, false>(v, sm, RowLayout<N>{}, wl, t, mv.tw);
-    if (ok) {
-#pragma unroll
-        for (int m = 0; m < nv; ++m) {
+        for (int m = 0; m < 8; ++m) {
             const int n = t + m * TL;
-            if (n < nout) dst[n] = v[m];
+            v[m] = (ok && m < Line<N>::NH && n < g.K) ? row[n] : mk<T>(0, 0);
+        }
+        fft_regs<T, false, N, true, false, false>(v, sm, ColLayoutT<LOGZ>{}, w, t, mv.tw);
+        if (ok) {
+#pragma unroll
+            for (int m = 0; m < nv; ++m) col[(t + m * TL) * g.Pb] = v[m];
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) v[m] = (ok && m < nv) ? col[(t + m * TL) * g.Pb] : mk<T>(0, 0);
+        fft_regs<T, true, N, false, true, false>(v, sm, ColLayoutT<LOGZ>{}, w, t, mv.tw);
+        if (ok) {
+#pragma unroll
+            for (int m = 0; m < Line<N>::NH; ++m) {   // i < K <= N/2: first half only
+                const int n = t + m * TL;
+                if (n < g.K) row[n] = v[m];
+            }
         }
     }
 }
@@ -201,25 +232,25 @@ __device__ __forceinline__ void load6(const C<T>* __restrict__ p, C<T> (&Y)[6]) 
     }
 }
 
-// row jy of the b-th tile row: rows jy and Ly - jy read the same spectrum
-// rows (mirror lookup), so they are visited back to back (0, 1, Ly-1, 2,
+// row jy of the b-th row of CTAs: rows jy and Ly - jy read the same spectrum
+// lines (mirror lookup), so they are visited back to back (0, 1, Ly-1, 2,
 // Ly-2, ...) and the second read hits L2
 __device__ __forceinline__ int p3_row(int b, int Ly) {
     const int q2 = (b + 1) >> 1;
     return b == 0 ? 0 : ((b & 1) ? q2 : Ly - q2);
 }
 
-// the spectrum product of Eqs. 6-8 at z point n of the column whose mirrored
-// spectrum row starts at spec (flips fx, fy of the x and y mirrors): one
-// 48-byte load of the six components, the Table-1 signs, then
-// (X0, X1, X2) <- Y (X0, X1, X2)
+// the spectrum product of Eqs. 6-8 at z point n of a column whose mirrored
+// spectrum line (contiguous in z) starts at line (flips fx, fy of the x and
+// y mirrors): one 48-byte load of the six components, the Table-1 signs,
+// then (X0, X1, X2) <- Y (X0, X1, X2)
 template <typename T, int N>
-__device__ __forceinline__ void p3_product(const C<T>* __restrict__ spec, int64_t zstep, bool ok, int fx, int fy,
-                                           int n, C<T>& X0, C<T>& X1, C<T>& X2) {
+__device__ __forceinline__ void p3_product(const C<T>* __restrict__ line, bool ok, int fx, int fy, int n, C<T>& X0,
+                                           C<T>& X1, C<T>& X2) {
     const int mz = n <= N / 2 ? n : N - n, fz = n > N / 2;
     C<T> Y[6];
     if (ok) {
-        load6<T>(spec + mz * zstep, Y);
+        load6<T>(line + mz * 6, Y);
     } else {
 #pragma unroll
         for (int q = 0; q < 6; ++q) Y[q] = mk<T>(0, 0);
@@ -233,137 +264,52 @@ __device__ __forceinline__ void p3_product(const C<T>* __restrict__ spec, int64_
     X2 = cfma<T>(Y[5], c, cfma<T>(Y[4], b, cmul<T>(Y[2], a)));
 }
 
-// One tile of W columns (x = xt W + w, row jy, batch slot j) whose inputs v
-// (the P nonzero z points of the three components, canonical order) are
-// loaded: forward z DFTs, the spectrum product of Eqs. 6-8 with the signed
-// mirror lookup of Sec. 3, inverse z DFTs, and the store of k < P.
-template <typename T, int N, int LOGW>
-__device__ __forceinline__ void p3_tile(const MatvecView<T>& mv, C<T>* sm, int j, int xt, int jy, C<T> (&v)[3][8]) {
-    constexpr int TL = Line<N>::T, nv = Line<N>::NV;
-    const Geometry& g = mv.g;
-    constexpr int logW = LOGW, W = 1 << LOGW;
-    const int w = threadIdx.x & (W - 1), t = threadIdx.x >> logW;
-    const int ix = xt * W + w;
-    const bool ok = ix < g.Lx;
-    const ColLayoutT<LOGW> L{};
-    constexpr int region = col_elems(N, W);
-    const int64_t plane = (int64_t)g.Ly * g.Lx;   // stride between z planes of Bxy
-    const int64_t comp = (int64_t)g.P * plane;    // stride between components
-    C<T>* col = mv.Bxy + j * bxy_elems(g) + (int64_t)jy * g.Lx + (ok ? ix : 0);
-    fft_lines<T, false, N, 3, true, false>(v, sm, region, L, w, t, mv.tw);
-    {
-        const int my = jy <= g.Ly / 2 ? jy : g.Ly - jy, fy = jy > g.Ly / 2;
-        const int mx = ix <= g.Lx / 2 ? ix : g.Lx - ix, fx = ix > g.Lx / 2;
-        const C<T>* spec = mv.spec + ((int64_t)my * g.Hx + (ok ? mx : 0)) * 6;
-        const int64_t zstep = (int64_t)g.Hy * g.Hx * 6;
-#pragma unroll
-        for (int m = 0; m < nv; ++m)
-            p3_product<T, N>(spec, zstep, ok, fx, fy, t + m * TL, v[0][m], v[1][m], v[2][m]);
-    }
-    // nothing reuses the exchange buffers after the inverse (the persistent
-    // schedule synchronises twice before its next tile)
-    fft_lines<T, true, N, 3, false, true, false>(v, sm, region, L, w, t, mv.tw);
-    if (ok) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int m = 0; m < Line<N>::NH; ++m) {   // z < P <= N/2: first half only
-                const int n = t + m * TL;
-                if (n < g.P) col[c * comp + n * plane] = v[c][m];
-            }
-    }
-}
-
-// one CTA per tile, inputs loaded from global memory
-template <typename T, int N, int LOGW>
-__global__ void __launch_bounds__(p3_max_threads<T>(), 1) k_p3(MatvecView<T> mv) {
-    const int j = blockIdx.x, xt = blockIdx.y;                  // batch slot, column tile
+// R = 2^logW_z whole columns (x = xg R + w, row jy, batch slot j) per CTA,
+// T = N/8 threads per column (thread t holds the points t + T m of the
+// three components): z-forward DFTs of the P nonzero inputs, the spectrum
+// product of Eqs. 6-8 with the signed mirror lookup of Sec. 3, z-inverse
+// DFTs, and the store of k < P.  Grid: (nb, Lx / R, Ly).
+template <typename T, int N>
+__global__ void __launch_bounds__(p3_max_threads<T>()) k_p3(MatvecView<T> mv) {
+    const int j = blockIdx.x;                                   // batch slot
     if (rhs_done(mv, mv.b0 + j)) return;
     extern __shared__ unsigned char smem_raw[];
     C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
     constexpr int TL = Line<N>::T, nv = Line<N>::NV;
     const Geometry& g = mv.g;
-    constexpr int W = 1 << LOGW;
-    const int w = threadIdx.x & (W - 1), t = threadIdx.x >> LOGW;
-    const int jy = p3_row(blockIdx.z, g.Ly);
-    const int ix = xt * W + w;
+    const int t = threadIdx.x % TL, w = threadIdx.x / TL;
+    const int ix = (blockIdx.y << mv.logW_z) + w, jy = p3_row(blockIdx.z, g.Ly);
     const bool ok = ix < g.Lx;
-    const int64_t plane = (int64_t)g.Ly * g.Lx, comp = (int64_t)g.P * plane;
-    const C<T>* col = mv.Bxy + j * bxy_elems(g) + (int64_t)jy * g.Lx + (ok ? ix : 0);
+    const int comp = g.Ly * g.Lx * g.Pb;                        // stride between components
+    C<T>* col = mv.Bxy + j * bxy_elems(g) + (jy * g.Lx + (ok ? ix : 0)) * g.Pb;
     C<T> v[3][8];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
             const int n = t + m * TL;
-            v[c][m] = (ok && m < Line<N>::NH && n < g.P) ? col[c * comp + n * plane] : mk<T>(0, 0);
+            v[c][m] = (ok && m < Line<N>::NH && n < g.P) ? col[c * comp + n] : mk<T>(0, 0);
         }
-    p3_tile<T, N, LOGW>(mv, sm, j, xt, jy, v);
-}
-
-// Persistent schedule: each CTA walks the tiles q = blockIdx.x, + gridDim.x,
-// ... in the order of the per-tile grid (batch slot fastest, then column
-// tile, then row), and while it transforms tile q the next one's input
-// columns are already on their way into a shared-memory stage with cp.async
-// (16-byte copies, no registers held), so the column loads of a tile no
-// longer stall the SM.  Tiles must be whole (W <= Lx) and a stage row must
-// be whole 16-byte copies (W * sizeof(C<T>) a multiple of 16).
-__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-template <typename T, int N, int LOGW>
-__global__ void __launch_bounds__(p3_max_threads<T>(), 1) k_p3p(MatvecView<T> mv, int stage_off) {
-    extern __shared__ unsigned char smem_raw[];
-    C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
-    C<T>* stage = sm + stage_off;                                  // [3][P][W]
-    constexpr int TL = Line<N>::T, nv = Line<N>::NV;
-    const Geometry& g = mv.g;
-    constexpr int W = 1 << LOGW;
-    constexpr int per16 = 16 / (int)sizeof(C<T>), chunks = W / per16;   // 16-byte copies per stage row
-    if constexpr (chunks == 0) {
-        return;   // never launched: the host only picks this schedule for whole 16-byte stage rows
-    } else {
-    const int w = threadIdx.x & (W - 1), t = threadIdx.x >> LOGW;
-    const int ntx = g.Lx / W;
-    const int ntiles = mv.nb * ntx * g.Ly;
-    const int64_t plane = (int64_t)g.Ly * g.Lx, comp = (int64_t)g.P * plane;
-    const int rows = 3 * g.P;
-    auto issue = [&](int q) {
-        const int j = q % mv.nb, xt = (q / mv.nb) % ntx, jy = p3_row(q / (mv.nb * ntx), g.Ly);
-        if (rhs_done(mv, mv.b0 + j)) return;
-        const C<T>* base = mv.Bxy + j * bxy_elems(g) + (int64_t)jy * g.Lx + xt * W;
-        for (int e = threadIdx.x; e < rows * chunks; e += blockDim.x) {
-            const int row = e / chunks, ch = e - row * chunks;
-            const int c = row / g.P, n = row - c * g.P;
-            cp_async16(stage + row * W + ch * per16, base + c * comp + (int64_t)n * plane + ch * per16);
-        }
-    };
-    int q = blockIdx.x;
-    if (q < ntiles) issue(q);
-    cp_async_commit();
-    for (; q < ntiles; q += gridDim.x) {
-        const int j = q % mv.nb, xt = (q / mv.nb) % ntx, jy = p3_row(q / (mv.nb * ntx), g.Ly);
-        const bool skip = rhs_done(mv, mv.b0 + j);             // the same for the whole CTA
-        cp_async_wait_all();
-        __syncthreads();
-        C<T> v[3][8];
+    const int region = row_ld(N) << mv.logW_z;
+    fft_lines<T, false, N, 3, true, false>(v, sm, region, RowLayout<N>{}, w, t, mv.tw);
+    {
+        const int my = jy <= g.Ly / 2 ? jy : g.Ly - jy, fy = jy > g.Ly / 2;
+        const int mx = ix <= g.Lx / 2 ? ix : g.Lx - ix, fx = ix > g.Lx / 2;
+        const C<T>* line = mv.spec + ((my * g.Hx + (ok ? mx : 0)) * g.Hz) * 6;
+#pragma unroll
+        for (int m = 0; m < nv; ++m)
+            p3_product<T, N>(line, ok, fx, fy, t + m * TL, v[0][m], v[1][m], v[2][m]);
+    }
+    // nothing reuses the exchange buffers after the inverse
+    fft_lines<T, true, N, 3, false, true, false>(v, sm, region, RowLayout<N>{}, w, t, mv.tw);
+    if (ok) {
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
-            for (int m = 0; m < 8; ++m) {
+            for (int m = 0; m < Line<N>::NH; ++m) {   // z < P <= N/2: first half only
                 const int n = t + m * TL;
-                v[c][m] = (!skip && m < nv && n < g.P) ? stage[(c * g.P + n) * W + w] : mk<T>(0, 0);
+                if (n < g.P) col[c * comp + n] = v[c][m];
             }
-        __syncthreads();                                         // the stage is free again
-        if (q + (int)gridDim.x < ntiles) issue(q + gridDim.x);
-        cp_async_commit();
-        if (!skip) p3_tile<T, N, LOGW>(mv, sm, j, xt, jy, v);
-    }
-    cp_async_wait_all();
     }
 }
 
@@ -467,71 +413,47 @@ int launch_p1(const MatvecView<T>& mv, const C<T>* p, cudaStream_t st) {
     return 0;
 }
 
-template <typename T, bool INV, int N>
-int launch_rows(const MatvecView<T>& mv, cudaStream_t st) {
+// shared memory of a P2/P4 CTA of Wz rows
+inline size_t rows_smem_elems(int N, int Wz) { return (size_t)col_elems(N, Wz); }
+
+template <typename T, bool INV, int N, int LOGZ>
+int launch_rows_w(const MatvecView<T>& mv, cudaStream_t st) {
     const Geometry& g = mv.g;
-    const int64_t rows = 3LL * g.P * g.Ly;
-    const int R = 1 << mv.logW_x;
-    const size_t sm = (size_t)R * row_ld(N) * sizeof(C<T>);
-    static std::atomic<size_t> smem_set{0};
-    if (int rc = set_smem((const void*)k_rows<T, INV, N>, sm, smem_set)) return rc;
-    const dim3 grid((unsigned)((rows + R - 1) / R), mv.nb);
-    k_rows<T, INV, N><<<grid, R * Line<N>::T, sm, st>>>(mv);
-    DDA_LAUNCH_CHECK(INV ? "P4 x-inverse" : "P2 x-forward");
-    return 0;
-}
-
-// the persistent z pass applies: whole tiles, whole 16-byte stage copies,
-// stage and exchange buffers within the shared-memory budget
-template <typename T>
-inline bool p3_persistent_ok(const Geometry& g, int logW) {
-    const int W = 1 << logW;
-    if (W > g.Lx || g.Lx % W || (W * (int)sizeof(C<T>)) % 16) return false;
-    const size_t stage_off = (3 * (size_t)col_elems(g.Lz, W) + 1) & ~size_t(1);
-    return (stage_off + 3ull * g.P * W) * sizeof(C<T>) <= 220 * 1024;
-}
-
-inline int sm_count() {
-    static std::atomic<int> n{0};
-    int v = n.load(std::memory_order_relaxed);
-    if (!v) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) v = 1;
-        n.store(v, std::memory_order_relaxed);
-    }
-    return v;
-}
-
-template <typename T, int N, int LOGW>
-int launch_p3(const MatvecView<T>& mv, cudaStream_t st) {
-    const Geometry& g = mv.g;
-    constexpr int W = 1 << LOGW;
-    const int threads = W * Line<N>::T;
-    if (mv.p3_sched == 1 && p3_persistent_ok<T>(g, LOGW)) {
-        const int stage_off = (int)((3 * (size_t)col_elems(N, W) + 1) & ~size_t(1));
-        const size_t sm = ((size_t)stage_off + 3ull * g.P * W) * sizeof(C<T>);
+    constexpr int Wz = 1 << LOGZ;
+    if constexpr (Wz * Line<N>::T > kRowThreads) {
+        return fail(DDA_ERR_ARG, "x pass tile wider than a CTA");
+    } else {
+        const size_t sm = rows_smem_elems(N, Wz) * sizeof(C<T>);
         static std::atomic<size_t> smem_set{0};
-        if (int rc = set_smem((const void*)k_p3p<T, N, LOGW>, sm, smem_set)) return rc;
-        static std::atomic<int> per_sm{0};
-        int bps = per_sm.load(std::memory_order_relaxed);
-        if (!bps) {
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_p3p<T, N, LOGW>, threads, sm) != cudaSuccess ||
-                bps < 1)
-                bps = 1;
-            per_sm.store(bps, std::memory_order_relaxed);
-        }
-        const int64_t ntiles = (int64_t)mv.nb * (g.Lx / W) * g.Ly;
-        const int grid = (int)std::min<int64_t>(ntiles, (int64_t)sm_count() * bps);
-        k_p3p<T, N, LOGW><<<grid, threads, sm, st>>>(mv, stage_off);
-        DDA_LAUNCH_CHECK("P3 z-forward, spectrum product, z-inverse (persistent)");
+        if (int rc = set_smem((const void*)k_rows<T, INV, N, LOGZ>, sm, smem_set)) return rc;
+        const dim3 grid((unsigned)((g.P + Wz - 1) / Wz), g.Ly, 3 * mv.nb);
+        k_rows<T, INV, N, LOGZ><<<grid, Wz * Line<N>::T, sm, st>>>(mv);
+        DDA_LAUNCH_CHECK(INV ? "P4 x-inverse" : "P2 x-forward");
         return 0;
     }
-    const size_t sm = 3 * (size_t)col_elems(N, W) * sizeof(C<T>);
+}
+
+template <typename T, bool INV, int N>
+int launch_rows(const MatvecView<T>& mv, cudaStream_t st) {
+    switch (mv.logW_x) {
+        case 0: return launch_rows_w<T, INV, N, 0>(mv, st);
+        case 1: return launch_rows_w<T, INV, N, 1>(mv, st);
+        case 2: return launch_rows_w<T, INV, N, 2>(mv, st);
+        case 3: return launch_rows_w<T, INV, N, 3>(mv, st);
+        case 4: return launch_rows_w<T, INV, N, 4>(mv, st);
+        default: return fail(DDA_ERR_ARG, "x pass tile width out of range");
+    }
+}
+
+template <typename T, int N>
+int launch_p3(const MatvecView<T>& mv, cudaStream_t st) {
+    const Geometry& g = mv.g;
+    const int R = 1 << mv.logW_z;
+    const size_t sm = 3 * (size_t)R * row_ld(N) * sizeof(C<T>);
     static std::atomic<size_t> smem_set{0};
-    if (int rc = set_smem((const void*)k_p3<T, N, LOGW>, sm, smem_set)) return rc;
-    dim3 grid(mv.nb, (g.Lx + W - 1) / W, g.Ly);
-    k_p3<T, N, LOGW><<<grid, threads, sm, st>>>(mv);
+    if (int rc = set_smem((const void*)k_p3<T, N>, sm, smem_set)) return rc;
+    const dim3 grid(mv.nb, (g.Lx + R - 1) / R, g.Ly);
+    k_p3<T, N><<<grid, R * Line<N>::T, sm, st>>>(mv);
     DDA_LAUNCH_CHECK("P3 z-forward, spectrum product, z-inverse");
     return 0;
 }
@@ -581,8 +503,8 @@ constexpr int kMaxLogW = 4;
 template <typename T> int pass1(const MatvecView<T>& mv, const C<T>* p, cudaStream_t st);
 template <typename T, bool INV> int pass_rows(const MatvecView<T>& mv, cudaStream_t st);
 template <typename T> int pass3(const MatvecView<T>& mv, cudaStream_t st);
-// P3 for one line length (all tile widths); each length group is
-// instantiated in its own translation unit (mv_p3_*.cu)
+// P3 for one line length; each length group is instantiated in its own
+// translation unit (mv_p3_*.cu)
 template <typename T, int N> int p3_len(const MatvecView<T>& mv, cudaStream_t st);
 template <typename T> int pass5(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t st);
 

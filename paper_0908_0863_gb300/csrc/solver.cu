@@ -1,7 +1,9 @@
 // Device-resident Krylov solvers (OpenDDA Sec. 4): BiCG, BiCG_sym (and CG
 // with the bilinear form, the same recurrence), BiCGSTAB, CGS, TFQMR, QMR
 // with coupled two-term recurrences and QMR_sym, in the textbook forms the
-// paper cites (Barrett et al. 1994; Sonneveld 1989; Freund 1992, 1993)
+// paper cites (Barrett et al. 1994; Sonneveld 1989; Freund 1992, 1993),
+// BiCGSTAB(l) (Sleijpen & Fokkema 1993) and ML(n)BiCGSTAB (Yeung & Chan
+// 1999)
 // written for complex vectors: Hermitian products x^H y in BiCG, BiCGSTAB,
 // CGS and TFQMR, bilinear x^T y in BiCG_sym, CG and the QMR Lanczos
 // processes with A^T = A (the DDA matrix is complex symmetric, Sec. 3);
@@ -1234,6 +1236,343 @@ __global__ void __launch_bounds__(kVecThreads) k_bl_scalar(KState* st, const dou
     }
 }
 
+// --------------------------------------------------------- ML(n)BiCGSTAB
+// ML(n)BiCGSTAB (Yeung & Chan 1999) with n = NS left starting vectors
+// Q = [r0, q_2, .., q_n].  Its residual at the end of cycle j is the unique
+// vector r_j = (I - omega_j A) v_j with v_j = Omega_(j-1)(A) phi_j(A) r0,
+// where phi_j (degree j n, phi_j(0) = 1) makes phi_j(A) r0 orthogonal to
+// K_j(A^H, Q) and omega_j minimises ||r_j||.  It is computed here with the
+// recurrences of induced dimension reduction (Sonneveld & van Gijzen 2008)
+// on the same shadow space: n differences dR_i = -A dX_i of residuals, the
+// n x n matrix M = Q^H dR and f = Q^H r, kept up to date as columns are
+// replaced oldest first.  Per cycle, n steps with one product each build n
+// new differences, then the closing step takes v = r - dR c with
+// M c = f (so Q^H v = 0), t = A v, omega = t^H v / t^H t and
+// r = v - omega t, which is r_j above.  Before the first cycle n
+// minimal-residual steps provide the first differences.
+template <typename T>
+struct MLVecs {
+    C<T>* dR[3];
+    C<T>* dX[3];
+    const C<T>* q[3];    // q[0] = r0 (per right-hand side); q[1], q[2] shared by all
+};
+
+// entry e of shadow vector i >= 1 (see include/dda.h): two SplitMix64
+// outputs (Steele, Lea & Flood 2014) from the state i 2^40 + e
+__device__ __forceinline__ uint64_t splitmix_out(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) k_ml_shadow(C<T>* __restrict__ q, int i, int64_t n) {
+    const int64_t S = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += S) {
+        const uint64_t st = ((uint64_t)i << 40) + (uint64_t)e;
+        const uint64_t u1 = splitmix_out(st + 0x9E3779B97F4A7C15ull);
+        const uint64_t u2 = splitmix_out(st + 2 * 0x9E3779B97F4A7C15ull);
+        const double re = (double)(u1 >> 11) * 0x1p-52 - 1.0, im = (double)(u2 >> 11) * 0x1p-52 - 1.0;
+        q[e] = mk<T>((T)re, (T)im);
+    }
+}
+
+template <typename T, int NS>
+__device__ __forceinline__ void ml_rows(const MLVecs<T>& w, int64_t n, const C<T>* (&q)[NS]) {
+    q[0] = rhs_vec(w.q[0], n);
+#pragma unroll
+    for (int i = 1; i < NS; ++i) q[i] = w.q[i];
+}
+
+__device__ __forceinline__ int ml_oldest(const KState* st) { return (int)st->s[S_ML + 16].x; }
+
+// start-up step k (minimal residual): with t = A r and omega = t^H r / t^H t,
+// dX_k = omega r, dR_k = -omega t, x += dX_k, r += dR_k; partials Q^H dR_k,
+// then Q^H r
+template <typename T, int NS>
+__global__ void __launch_bounds__(kVecThreads) k_ml_mr(const KState* st, MLVecs<T> w, C<T>* __restrict__ x,
+                                                       C<T>* __restrict__ r, const C<T>* __restrict__ t, int k,
+                                                       int64_t n, double2* __restrict__ part) {
+    st += blockIdx.y;
+    if (st->status != ST_RUN) return;
+    const C<T>* q[NS];
+    ml_rows<T, NS>(w, n, q);
+    C<T>* dR = rhs_vec(w.dR[k], n);
+    C<T>* dX = rhs_vec(w.dX[k], n);
+    x = rhs_vec(x, n); r = rhs_vec(r, n); t = rhs_vec(t, n); part = rhs_part(part);
+    const C<T> om = to_t<T>(st->s[S_ML + 15]);
+    const C<T> nom = mk<T>(-om.x, -om.y);
+    DotAcc<T> acc[2 * NS];
+#pragma unroll
+    for (int i = 0; i < 2 * NS; ++i) acc[i].init();
+    vec_loop(n,
+             [&](int64_t e) {
+                 VN<T, NS + 3> a;
+                 a.v[0] = r[e]; a.v[1] = t[e]; a.v[2] = x[e];
+#pragma unroll
+                 for (int i = 0; i < NS; ++i) a.v[3 + i] = q[i][e];
+                 return a;
+             },
+             [&](int64_t e, const VN<T, NS + 3>& a) {
+                 const C<T> dx = cmul<T>(om, a.v[0]), dr = cmul<T>(nom, a.v[1]);
+                 const C<T> rn = cadd<T>(a.v[0], dr);
+                 dX[e] = dx;
+                 dR[e] = dr;
+                 x[e] = cadd<T>(a.v[2], dx);
+                 r[e] = rn;
+#pragma unroll
+                 for (int i = 0; i < NS; ++i) {
+                     acc[i].add(cmul<T>(conjg<T>(a.v[3 + i]), dr));
+                     acc[NS + i].add(cmul<T>(conjg<T>(a.v[3 + i]), rn));
+                 }
+             });
+    double2 out[2 * NS];
+#pragma unroll
+    for (int i = 0; i < 2 * NS; ++i) { acc[i].flush(); out[i] = acc[i].hi; }
+    block_partials<2 * NS>(out, part);
+}
+
+// inner step: dX_old = -sum_i c_i dX_i + omega (r - sum_i c_i dR_i), also
+// written to dx (the column the host hands to the product)
+template <typename T, int NS>
+__global__ void __launch_bounds__(kVecThreads) k_ml_dx(const KState* st, MLVecs<T> w, const C<T>* __restrict__ r,
+                                                       C<T>* __restrict__ dx, int64_t n) {
+    st += blockIdx.y;
+    if (st->status != ST_RUN) return;
+    const C<T>* dR[NS];
+    const C<T>* dX[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) { dR[i] = rhs_vec(w.dR[i], n); dX[i] = rhs_vec(w.dX[i], n); }
+    C<T>* out = rhs_vec(w.dX[ml_oldest(st)], n);
+    r = rhs_vec(r, n); dx = rhs_vec(dx, n);
+    C<T> c[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) c[i] = to_t<T>(st->s[S_ML + 12 + i]);
+    const C<T> om = to_t<T>(st->s[S_ML + 15]);
+    vec_loop(n,
+             [&](int64_t e) {
+                 VN<T, 2 * NS + 1> a;
+                 a.v[0] = r[e];
+#pragma unroll
+                 for (int i = 0; i < NS; ++i) { a.v[1 + i] = dR[i][e]; a.v[1 + NS + i] = dX[i][e]; }
+                 return a;
+             },
+             [&](int64_t e, const VN<T, 2 * NS + 1>& a) {
+                 C<T> v = a.v[0], d = mk<T>(0, 0);
+#pragma unroll
+                 for (int i = 0; i < NS; ++i) {
+                     v = csub<T>(v, cmul<T>(c[i], a.v[1 + i]));
+                     d = csub<T>(d, cmul<T>(c[i], a.v[1 + NS + i]));
+                 }
+                 const C<T> o = cfma<T>(om, v, d);
+                 out[e] = o;
+                 dx[e] = o;
+             });
+}
+
+// inner step after u = A dx (dx = dX_old): dR_old = -u, r -= u, x += dx;
+// partials Q^H dR_old
+template <typename T, int NS>
+__global__ void __launch_bounds__(kVecThreads) k_ml_dr(const KState* st, MLVecs<T> w, C<T>* __restrict__ x,
+                                                       C<T>* __restrict__ r, const C<T>* __restrict__ u,
+                                                       const C<T>* __restrict__ dX, int64_t n,
+                                                       double2* __restrict__ part) {
+    st += blockIdx.y;
+    if (st->status != ST_RUN) return;
+    const C<T>* q[NS];
+    ml_rows<T, NS>(w, n, q);
+    const int old = ml_oldest(st);
+    C<T>* dR = rhs_vec(w.dR[old], n);
+    dX = rhs_vec(dX, n);
+    x = rhs_vec(x, n); r = rhs_vec(r, n); u = rhs_vec(u, n); part = rhs_part(part);
+    DotAcc<T> acc[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) acc[i].init();
+    vec_loop(n,
+             [&](int64_t e) {
+                 VN<T, NS + 4> a;
+                 a.v[0] = u[e]; a.v[1] = r[e]; a.v[2] = x[e]; a.v[3] = dX[e];
+#pragma unroll
+                 for (int i = 0; i < NS; ++i) a.v[4 + i] = q[i][e];
+                 return a;
+             },
+             [&](int64_t e, const VN<T, NS + 4>& a) {
+                 const C<T> dr = mk<T>(-a.v[0].x, -a.v[0].y);
+                 dR[e] = dr;
+                 r[e] = cadd<T>(a.v[1], dr);
+                 x[e] = cadd<T>(a.v[2], a.v[3]);
+#pragma unroll
+                 for (int i = 0; i < NS; ++i) acc[i].add(cmul<T>(conjg<T>(a.v[4 + i]), dr));
+             });
+    double2 out[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) { acc[i].flush(); out[i] = acc[i].hi; }
+    block_partials<NS>(out, part);
+}
+
+// closing step: v = r - sum_i c_i dR_i
+template <typename T, int NS>
+__global__ void __launch_bounds__(kVecThreads) k_ml_v(const KState* st, MLVecs<T> w, const C<T>* __restrict__ r,
+                                                      C<T>* __restrict__ v, int64_t n) {
+    st += blockIdx.y;
+    if (st->status != ST_RUN) return;
+    const C<T>* dR[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) dR[i] = rhs_vec(w.dR[i], n);
+    r = rhs_vec(r, n); v = rhs_vec(v, n);
+    C<T> c[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) c[i] = to_t<T>(st->s[S_ML + 12 + i]);
+    vec_loop(n,
+             [&](int64_t e) {
+                 VN<T, NS + 1> a;
+                 a.v[0] = r[e];
+#pragma unroll
+                 for (int i = 0; i < NS; ++i) a.v[1 + i] = dR[i][e];
+                 return a;
+             },
+             [&](int64_t e, const VN<T, NS + 1>& a) {
+                 C<T> vv = a.v[0];
+#pragma unroll
+                 for (int i = 0; i < NS; ++i) vv = csub<T>(vv, cmul<T>(c[i], a.v[1 + i]));
+                 v[e] = vv;
+             });
+}
+
+// closing step after t = A v and omega: dR_old = v - r - omega t,
+// dX_old = -sum_i c_i dX_i + omega v, r = v - omega t, x += dX_old;
+// partials Q^H dR_old, ||r||^2
+template <typename T, int NS>
+__global__ void __launch_bounds__(kVecThreads) k_ml_fin(const KState* st, MLVecs<T> w, C<T>* __restrict__ x,
+                                                        C<T>* __restrict__ r, const C<T>* __restrict__ v,
+                                                        const C<T>* __restrict__ t, int64_t n,
+                                                        double2* __restrict__ part) {
+    st += blockIdx.y;
+    if (st->status != ST_RUN) return;
+    const C<T>* q[NS];
+    ml_rows<T, NS>(w, n, q);
+    const int old = ml_oldest(st);
+    const C<T>* dX[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) dX[i] = rhs_vec(w.dX[i], n);
+    C<T>* dRo = rhs_vec(w.dR[old], n);
+    C<T>* dXo = rhs_vec(w.dX[old], n);
+    x = rhs_vec(x, n); r = rhs_vec(r, n); v = rhs_vec(v, n); t = rhs_vec(t, n); part = rhs_part(part);
+    C<T> c[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) c[i] = to_t<T>(st->s[S_ML + 12 + i]);
+    const C<T> om = to_t<T>(st->s[S_ML + 15]);
+    const C<T> nom = mk<T>(-om.x, -om.y);
+    DotAcc<T> acc[NS + 1];
+#pragma unroll
+    for (int i = 0; i <= NS; ++i) acc[i].init();
+    vec_loop(n,
+             [&](int64_t e) {
+                 VN<T, 2 * NS + 4> a;
+                 a.v[0] = v[e]; a.v[1] = t[e]; a.v[2] = r[e]; a.v[3] = x[e];
+#pragma unroll
+                 for (int i = 0; i < NS; ++i) { a.v[4 + i] = dX[i][e]; a.v[4 + NS + i] = q[i][e]; }
+                 return a;
+             },
+             [&](int64_t e, const VN<T, 2 * NS + 4>& a) {
+                 const C<T> rn = cfma<T>(nom, a.v[1], a.v[0]);
+                 const C<T> dr = csub<T>(rn, a.v[2]);
+                 C<T> dx = cmul<T>(om, a.v[0]);
+#pragma unroll
+                 for (int i = 0; i < NS; ++i) dx = csub<T>(dx, cmul<T>(c[i], a.v[4 + i]));
+                 dRo[e] = dr;
+                 dXo[e] = dx;
+                 r[e] = rn;
+                 x[e] = cadd<T>(a.v[3], dx);
+#pragma unroll
+                 for (int i = 0; i < NS; ++i) acc[i].add(cmul<T>(conjg<T>(a.v[4 + NS + i]), dr));
+                 acc[NS].add(norm2c<T>(rn));
+             });
+    double2 out[NS + 1];
+#pragma unroll
+    for (int i = 0; i <= NS; ++i) { acc[i].flush(); out[i] = acc[i].hi; }
+    block_partials<NS + 1>(out, part);
+}
+
+// solves the general ns x ns system M c = f (M column-major at S_ML, f at
+// S_ML + 9) by Gaussian elimination with partial pivoting; false when singular
+__device__ bool ml_solve(const KState* st, int ns, double2* c) {
+    double2 A[3][4];
+    for (int i = 0; i < ns; ++i) {
+        for (int j = 0; j < ns; ++j) A[i][j] = st->s[S_ML + 3 * j + i];
+        A[i][ns] = st->s[S_ML + 9 + i];
+    }
+    for (int col = 0; col < ns; ++col) {
+        int piv = col;
+        for (int i = col + 1; i < ns; ++i)
+            if (hypot(A[i][col].x, A[i][col].y) > hypot(A[piv][col].x, A[piv][col].y)) piv = i;
+        if (is_zero(A[piv][col])) return false;
+        if (piv != col)
+            for (int j = 0; j <= ns; ++j) { const double2 tmp = A[col][j]; A[col][j] = A[piv][j]; A[piv][j] = tmp; }
+        for (int i = col + 1; i < ns; ++i) {
+            const double2 f = ddiv(A[i][col], A[col][col]);
+            for (int j = col; j <= ns; ++j) {
+                const double2 tmp = dmul(f, A[col][j]);
+                A[i][j] = make_double2(A[i][j].x - tmp.x, A[i][j].y - tmp.y);
+            }
+        }
+    }
+    for (int i = ns - 1; i >= 0; --i) {
+        double2 acc = A[i][ns];
+        for (int j = i + 1; j < ns; ++j) {
+            const double2 tmp = dmul(A[i][j], c[j]);
+            acc = make_double2(acc.x - tmp.x, acc.y - tmp.y);
+        }
+        c[i] = ddiv(acc, A[i][i]);
+        if (!finite2(c[i])) return false;
+    }
+    return true;
+}
+
+// step 0: omega of start-up step k from (t^H t, t^H r); 1: after start-up
+// step k, M column k = partials, f = the next ns partials; 2: c = M^-1 f;
+// 3: after an inner step, M column `oldest` = partials, f += them, the next
+// column becomes the oldest; 4: omega from (t^H t, t^H v); 5: like 3, then
+// the end of the cycle (ns + 1 products) with ||r||^2 from partial ns
+__global__ void __launch_bounds__(kVecThreads) k_ml_scalar(KState* st, const double2* __restrict__ part,
+                                                           int nparts, int step, int k, int ns) {
+    st += blockIdx.x;
+    part += (int64_t)blockIdx.x * nparts * kMaxRed;
+    if (st->status != ST_RUN) return;
+    double2 s[7];
+    final_sums<7>(part, nparts, s);
+    if (threadIdx.x != 0) return;
+    if (step == 0 || step == 4) {
+        const double2 tt = s[0], tv = s[1];
+        if (!finite2(tt) || !finite2(tv)) { st->status = ST_NAN; return; }
+        if (tt.x == 0.0) { st->status = ST_BREAKDOWN; return; }
+        const double2 om = make_double2(tv.x / tt.x, tv.y / tt.x);
+        if (is_zero(om)) { st->status = ST_BREAKDOWN; return; }
+        st->s[S_ML + 15] = om;
+    } else if (step == 1) {
+        for (int i = 0; i < ns; ++i) {
+            st->s[S_ML + 3 * k + i] = s[i];
+            st->s[S_ML + 9 + i] = s[ns + i];
+        }
+        st->s[S_ML + 16] = make_double2(0.0, 0.0);
+    } else if (step == 2) {
+        double2 c[3];
+        if (!ml_solve(st, ns, c)) { st->status = ST_BREAKDOWN; return; }
+        for (int i = 0; i < ns; ++i) st->s[S_ML + 12 + i] = c[i];
+    } else {
+        const int old = ml_oldest(st);
+        for (int i = 0; i < ns; ++i) {
+            st->s[S_ML + 3 * old + i] = s[i];
+            const double2 f = st->s[S_ML + 9 + i];
+            st->s[S_ML + 9 + i] = make_double2(f.x + s[i].x, f.y + s[i].y);
+        }
+        st->s[S_ML + 16] = make_double2((double)((old + 1) % ns), 0.0);
+        if (step == 5) {
+            st->matvecs += ns + 1;
+            end_of_iteration(st, s[ns].x / st->bnorm2);
+        }
+    }
+}
+
 // ------------------------------------------------------ refinement helpers
 __global__ void __launch_bounds__(kVecThreads) k_norm2_c128(const double2* __restrict__ a, int64_t n,
                                                             double2* __restrict__ part) {
@@ -1306,6 +1645,61 @@ template <typename T>
 static int run_matvec(MatvecView<T> mv, const C<T>* p, C<T>* y, int conj, cudaStream_t st) {
     mv.conj = conj;
     return launch_matvec<T>(mv, p, y, st);
+}
+
+// ML(n)BiCGSTAB vectors in the workspace: r = v[0], q_1 = r0 = v[1] (the
+// shadow residual written by k_init), v = v[2], t = v[3], dR_i = v[4 + i],
+// dX_i = v[7 + i], q_2 = v[10], q_3 = v[11] (first n elements, shared)
+template <typename T>
+static MLVecs<T> ml_vecs(KrylovWork<T>& ws) {
+    C<T>** v = ws.v;
+    return MLVecs<T>{{v[4], v[5], v[6]}, {v[7], v[8], v[9]}, {v[1], v[10], v[11]}};
+}
+
+// One cycle: the start-up steps (first cycle) or the ns inner steps, then
+// the closing step with the stopping test.  Returns the kernels launched
+// besides the matvec passes; rc receives a launch failure.
+template <typename T, int NS>
+static int64_t enqueue_ml(const MatvecView<T>& mv, KrylovWork<T>& ws, C<T>* x, int first, cudaStream_t st,
+                          int& rc) {
+    const int64_t n = ws.n;
+    const int nb = ws.nb, gx = vec_blocks(n, nb);
+    const dim3 G(gx, nb), B(kVecThreads);
+    double2* part = ws.part;
+    KState* ds = ws.st;
+    C<T>** v = ws.v;
+    C<T>*r = v[0], *vv = v[2], *t = v[3];
+    const MLVecs<T> w = ml_vecs(ws);
+    int64_t k = 0;
+    rc = 0;
+    if (first) {
+        for (int q = 0; q < NS; ++q) {
+            if ((rc = run_matvec<T>(mv, r, t, 0, st))) return k;
+            k_dot_ts<T><<<G, B, 0, st>>>(ds, t, r, n, part);
+            k_ml_scalar<<<nb, B, 0, st>>>(ds, part, gx, 0, q, NS);
+            k_ml_mr<T, NS><<<G, B, 0, st>>>(ds, w, x, r, t, q, n, part);
+            k_ml_scalar<<<nb, B, 0, st>>>(ds, part, gx, 1, q, NS);
+            k += 4;
+        }
+    } else {
+        for (int q = 0; q < NS; ++q) {
+            k_ml_scalar<<<nb, B, 0, st>>>(ds, part, gx, 2, 0, NS);
+            k_ml_dx<T, NS><<<G, B, 0, st>>>(ds, w, r, vv, n);
+            if ((rc = run_matvec<T>(mv, vv, t, 0, st))) return k;
+            k_ml_dr<T, NS><<<G, B, 0, st>>>(ds, w, x, r, t, vv, n, part);
+            k_ml_scalar<<<nb, B, 0, st>>>(ds, part, gx, 3, 0, NS);
+            k += 4;
+        }
+    }
+    k_ml_scalar<<<nb, B, 0, st>>>(ds, part, gx, 2, 0, NS);
+    k_ml_v<T, NS><<<G, B, 0, st>>>(ds, w, r, vv, n);
+    if ((rc = run_matvec<T>(mv, vv, t, 0, st))) return k;
+    k_dot_ts<T><<<G, B, 0, st>>>(ds, t, vv, n, part);
+    k_ml_scalar<<<nb, B, 0, st>>>(ds, part, gx, 4, 0, NS);
+    k_ml_fin<T, NS><<<G, B, 0, st>>>(ds, w, x, r, vv, t, n, part);
+    k_ml_scalar<<<nb, B, 0, st>>>(ds, part, gx, 5, 0, NS);
+    k += 6;
+    return k;
 }
 
 // the kernels of one iteration (first: the first iteration's variants)
@@ -1411,6 +1805,12 @@ static int enqueue_iteration(int method, const MatvecView<T>& mv, KrylovWork<T>&
         else k_bl_fin<T, 3><<<G, B, 0, st>>>(ds, w, x, rt, n, part);
         k_bl_scalar<<<nb, B, 0, st>>>(ds, part, gx, 3, 0, ell);
         k += 4;
+    } else if (method >= DDA_MLBICGSTAB1 && method <= DDA_MLBICGSTAB3) {
+        const int ns = method - DDA_MLBICGSTAB1 + 1;
+        if (ns == 1) k = enqueue_ml<T, 1>(mv, ws, x, first, st, rc);
+        else if (ns == 2) k = enqueue_ml<T, 2>(mv, ws, x, first, st, rc);
+        else k = enqueue_ml<T, 3>(mv, ws, x, first, st, rc);
+        if (rc) return rc;
     } else if (method == DDA_QMR_SYM) {
         C<T>*vt = v[1], *vv = v[3], *p = v[5], *pt = v[7], *d = v[8], *s = v[9];
         k_qs_v<T><<<G, B, 0, st>>>(ds, vt, vv, n, part);
@@ -1503,6 +1903,12 @@ int krylov_solve(int method, MatvecView<T> mv, KrylovWork<T>& ws, const C<T>* b,
     DDA_LAUNCH_CHECK("krylov init scalar");
     if (method == DDA_QMR) {  // vt = r (v[1]), wt = r (v[2])
         DDA_CUDA_TRY(cudaMemcpyAsync(v[2], r, nb * n * sizeof(C<T>), cudaMemcpyDeviceToDevice, st));
+    }
+    if (method >= DDA_MLBICGSTAB1 && method <= DDA_MLBICGSTAB3) {   // shadow vectors q_2 .. q_n
+        for (int i = 1; i <= method - DDA_MLBICGSTAB1; ++i) {
+            k_ml_shadow<T><<<kVecBlocks, kVecThreads, 0, st>>>(v[9 + i], i, n);
+            DDA_LAUNCH_CHECK("ML(n)BiCGSTAB shadow vectors");
+        }
     }
     if (bl) {  // u_0 = 0
         DDA_CUDA_TRY(cudaMemsetAsync(v[5], 0, nb * n * sizeof(C<T>), st));

@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(512) k_tensor_x(Geometry g, int logW, const do
 // strided lines along y (axis 1) or z (axis 2) on arrays whose rows are Hx
 // long.  in: [6][n_outer][n_line][Hx] slices -> out: [6][n_outer][H][Hx]
 // (y pass: outer = P, line = J -> Hy; z pass: the line is the outermost
-// index of [6][P][Hy][Hx] -> [Hz][Hy][Hx][6], components innermost).
+// index of [6][P][Hy][Hx] -> [Hy][Hx][Hz][6], components innermost).
 template <int AXIS>
 __global__ void __launch_bounds__(512) k_tensor_col(Geometry g, int logW, const double2* __restrict__ tw,
                                                     const double2* __restrict__ in, double2* __restrict__ out,
@@ -150,9 +150,10 @@ __global__ void __launch_bounds__(512) k_tensor_col(Geometry g, int logW, const 
         if (AXIS == 1) {
             out[out_base + n * out_step + x] = v;
         } else {
-            // final spectrum: the six components of a point side by side,
-            // [Hz][Hy][Hx][6], so the matvec reads them with vector loads
-            const int64_t o = (((int64_t)n * g.Hy + outer) * g.Hx + x) * 6 + m;
+            // final spectrum: every z line contiguous and the six
+            // components of a point side by side, [Hy][Hx][Hz][6], so the z
+            // pass reads a column's line in one stream with vector loads
+            const int64_t o = (((int64_t)outer * g.Hx + x) * g.Hz + n) * 6 + m;
             out[o] = v;
             if (out32) out32[o] = make_float2((float)v.x, (float)v.y);
         }

@@ -538,6 +538,9 @@ extern "C" int dda_occupancy_ranks_static(const uint32_t* occupancy_bits, int64_
                                  "536870912 sites (4096 blocks of 4096 words)");
     if (!occupancy_bits || !word_rank || !n_occupied)
         return fail(DDA_ERR_ARG, "dda_occupancy_ranks_static: NULL pointer");
+    if (!is_device_ptr(occupancy_bits) || !is_device_ptr(word_rank) || !is_device_ptr(n_occupied))
+        return fail(DDA_ERR_ARG, "dda_occupancy_ranks_static: occupancy_bits, word_rank and n_occupied must be "
+                                 "device pointers");
     uint32_t* scratch = nullptr;
     if (int rc = static_scan_address(&scratch)) return rc;
     const cudaStream_t st = as_stream(stream);

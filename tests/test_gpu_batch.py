@@ -293,8 +293,8 @@ def test_tile_widths_do_not_change_results(dda, dtype, shape):
         y0 = torch.empty_like(p)
         lat.matvec_batch(p, y0)
         tried = 0
-        for d in ((-1, 0, 0, 0), (1, 0, 0, 0), (0, -1, 0, 0), (0, 1, 0, 0), (0, 0, -1, 0), (0, 0, 1, 0),
-                  (1, 1, 1, 0), (0, 0, 0, 1), (0, -1, 0, 1)):
+        for d in ((-1, 0, 0, 0), (1, 0, 0, 0), (0, -1, 0, 0), (0, 1, 0, 0), (0, 2, 0, 0), (0, 0, -1, 0),
+                  (0, 0, 1, 0), (0, 0, -2, 0), (1, 1, 1, 0)):
             t = tuple(b + e for b, e in zip(base, d))
             try:
                 lat.tiles(dtype, t)
@@ -311,8 +311,8 @@ def test_tile_widths_do_not_change_results(dda, dtype, shape):
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
-def test_persistent_z_pass_in_batched_solves(dda, dtype):
-    # the staged persistent z pass gives the same bits as the per-tile grid,
+def test_z_pass_widths_in_batched_solves(dda, dtype):
+    # one and two whole z columns per CTA of the z pass give the same bits,
     # also while right-hand sides drop out of a batched solve one by one
     case = Case(synth.sphere(24), [1.33 + 0.05j], 0.5 / abs(1.33 + 0.05j))
     pairs = _pairs(20260071, 3)
@@ -321,8 +321,8 @@ def test_persistent_z_pass_in_batched_solves(dda, dtype):
     with case.lattice() as lat:
         E = _einc(lat, case.nd, pairs)
         base = lat.tiles(dtype)
-        for sched in (0, 1):
-            lat.tiles(dtype, (base[0], base[1], base[2], sched))
+        for wz in (base[1], base[1] + 1):
+            lat.tiles(dtype, (base[0], wz, base[2], 0))
             P = torch.zeros_like(E)
             status, stats, infos = lat.solve_batch(E, P, "bicgstab", precision, tol=1e-9, max_iter=2000)
             assert status == dda.DDA_OK, stats
@@ -341,7 +341,7 @@ def test_tile_limits_rejected(dda):
             lat.tiles("c64", (base[0], 12, base[2], 0))     # 4096 columns x 4 threads per CTA
         assert e.value.code == dda.DDA_ERR_ARG
         assert lat.tiles("c64") == base
-        for sched in (-1, 2):                                  # no such schedule
+        for sched in (-1, 1, 2):                               # the reserved entry must be 0
             with pytest.raises(dda.DDAError) as e:
                 lat.tiles("c64", (base[0], base[1], base[2], sched))
             assert e.value.code == dda.DDA_ERR_ARG

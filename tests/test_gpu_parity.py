@@ -94,7 +94,7 @@ def test_tensor_spectrum_matches_oracle(dda, shape):
     case = Case(np.ones((P, J, K), dtype=np.uint8), [1.5 + 0.1j], k)
     L = tuple(circulant.padded_length(v) for v in shape)
     half = circulant.half_spectrum(circulant.tensor_section1(k, K, J, P), L) / (L[0] * L[1] * L[2])
-    half = np.ascontiguousarray(half.transpose(1, 2, 3, 0))   # stored as [Hz][Hy][Hx][6]
+    half = np.ascontiguousarray(half.transpose(2, 3, 1, 0))   # stored as [Hy][Hx][Hz][6]
     with case.lattice() as lat:
         assert lat.padded == L
         out = torch.empty(half.shape, dtype=torch.complex128, device=DEV)
