@@ -15,7 +15,19 @@ One step = one whole job on that target through the C ABI:
   Sec. 4), cross sections; then free the context.
 value = products with A (FFT matvecs, any precision) per second over the
 whole job, max over ranks; solves/s and the per-precision matvec rates are
-reported beside it.
+reported beside it.  e2e repeats the job through the public API with host
+buffers: the occupancy bits, each incident field E and each solution P
+cross the host boundary inside dda_init_lattice, dda_solve and
+dda_cross_sections.
+
+Extras of the default line (rank 0, after the timed region): the roofline
+of the dominant pass; complex64 and complex128 product rates; mixed against
+FP64 solves of the same right-hand side with BiCGSTAB and QMR to 1e-5
+(seconds, products, true residuals, the relative differences of the cross
+sections); the two-material LDR ellipsoid in 128^3 with 1,000 timed products
+in each precision; the context set-up (spectrum build) time; the batch of 16
+directions sharing the spectrum; the ballistic-aggregate batching workload;
+the unpruned cuFFT comparison.
 
 --impl reference times the oracle (plain FP64 direct sum, O(N_d^2)) on the
 host cores on a bounded sample of the same product: a few hundred rows of
@@ -160,6 +172,13 @@ def run_ours(args):
     # this shape starts with them
     tuned = {dt: {"pass_ms": probe.autotune(dt, nb=1, reps=3), "tiles": probe.tiles(dt)}
              for dt in ("c64", "c128")} if args.autotune else None
+    if args.autotune:
+        # the mixed-precision inner target, tuned on the first right-hand side
+        E0 = torch.empty((3, probe.n_dipoles), dtype=torch.complex128, device=dev)
+        dda.dda_incident_field(probe.ctx, khat, pols[0], E0)
+        rho, rho_ms = dda.dda_autotune_inner(probe.ctx, E0, args.method, args.tol, args.max_iter)
+        tuned["inner"] = {"rho": rho, "solve_ms": {str(k): v for k, v in rho_ms.items()}}
+        del E0
     probe.close()
     E = torch.empty((3, nd), dtype=torch.complex128, device=dev)
     P = torch.empty_like(E)
@@ -167,22 +186,26 @@ def run_ours(args):
              "status": [], "cx": None}
     pass_ms = {"c128": [[0, 0.0] for _ in range(5)], "c64": [[0, 0.0] for _ in range(5)]}
 
-    def job(record, host_bits=None, host_P=None):
-        if host_bits is None:
+    def job(record, host=None):
+        if host is None:
             dda.dda_pack_occupancy(mask_dev, bits)
             src = bits
         else:
-            src = host_bits
+            src = host["bits"]
         ctx = dda.dda_init_lattice(shape, src, None, 1, alpha, K_WAVE)
         try:
             if record:
                 dda.dda_profile(ctx, True)
-            for e in pols:
-                dda.dda_incident_field(ctx, khat, e, E)
-                status, info = dda.dda_solve(ctx, E, P, args.method, "mixed", args.tol, args.max_iter)
-                cx = dda.dda_cross_sections(ctx, E, P)
-                if host_P is not None:
-                    host_P.copy_(P, non_blocking=True)
+            for q, e in enumerate(pols):
+                if host is None:
+                    dda.dda_incident_field(ctx, khat, e, E)
+                    status, info = dda.dda_solve(ctx, E, P, args.method, "mixed", args.tol, args.max_iter)
+                    cx = dda.dda_cross_sections(ctx, E, P)
+                else:
+                    # the caller's host arrays, as a user of the library passes them
+                    Eh, Ph = host["E"][q], host["P"][q]
+                    status, info = dda.dda_solve(ctx, Eh, Ph, args.method, "mixed", args.tol, args.max_iter)
+                    cx = dda.dda_cross_sections(ctx, Eh, Ph)
                 if record:
                     stats["matvecs"] += info["matvecs"] + info["matvecs_fp64"]
                     stats["matvecs_fp64"] += info["matvecs_fp64"]
@@ -200,8 +223,6 @@ def run_ours(args):
                         pass_ms[dt][q][1] += ms
         finally:
             dda.dda_free(ctx)
-        if host_P is not None:
-            torch.cuda.current_stream(dev).synchronize()
 
     def barrier():
         if dist is not None:
@@ -231,21 +252,33 @@ def run_ours(args):
     value = totals[0] / (ms_max / 1e3)
     solves_per_s = totals[1] / (ms_max / 1e3)
 
-    # ---- end to end through the public API with host buffers (pinned)
-    host_bits = torch.empty(bits.numel(), dtype=torch.int32).pin_memory()
-    host_bits.copy_(bits.cpu())
-    host_P = torch.empty(P.shape, dtype=P.dtype).pin_memory()
+    # ---- end to end through the public API with host buffers (pinned): the
+    # occupancy bits and both incident fields go in, both solutions come
+    # out, every step, inside the library calls
+    host = {"bits": torch.empty(bits.numel(), dtype=torch.int32).pin_memory(),
+            "E": [torch.empty(E.shape, dtype=E.dtype).pin_memory() for _ in pols],
+            "P": [torch.empty(P.shape, dtype=P.dtype).pin_memory() for _ in pols]}
+    host["bits"].copy_(bits.cpu())
+    ctx0 = dda.dda_init_lattice(shape, bits, None, 1, alpha, K_WAVE)
+    for q, e in enumerate(pols):
+        dda.dda_incident_field(ctx0, khat, e, E)
+        host["E"][q].copy_(E.cpu())
+    dda.dda_free(ctx0)
+    hostnp = {"bits": host["bits"].numpy(), "E": [t.numpy() for t in host["E"]], "P": [t.numpy() for t in host["P"]]}
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
     barrier()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        job(False, host_bits=host_bits.numpy(), host_P=host_P)
+    for _ in range(e2e_steps):
+        job(False, host=hostnp)
     barrier()
     e2e_s = time.perf_counter() - t0
     # a job makes the same products as in the timed loop; ranks run replicas
     per_job_mv = stats["matvecs"] / max(1, args.steps)
-    e2e_value = per_job_mv * args.steps / e2e_s * world
-    h2d = host_bits.numel() * 4
-    d2h = 2 * P.numel() * 16 + 2 * 3 * 8
+    e2e_value = per_job_mv * e2e_steps / e2e_s * world
+    # per step: bits, then per polarisation E into dda_solve and E, P into
+    # dda_cross_sections; P out of dda_solve and the three cross sections
+    h2d = host["bits"].numel() * 4 + len(pols) * (2 * E.numel() * 16 + P.numel() * 16)
+    d2h = len(pols) * (P.numel() * 16 + 3 * 8)
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -259,7 +292,9 @@ def run_ours(args):
         "solves_per_s": solves_per_s,
         "clocks": clocks,
         "gpu_launches": int(launches),
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": e2e_steps, "how": "the same job through dda_init_lattice, dda_solve and "
+                                          "dda_cross_sections with pinned host buffers (bits, E in, P out)"},
         "job": {"matvecs_per_solve": stats["matvecs"] / max(1, stats["solves"]),
                 "fp64_matvecs_per_solve": stats["matvecs_fp64"] / max(1, stats["solves"]),
                 "iterations_per_solve": stats["iters"] / max(1, stats["solves"]),
@@ -430,20 +465,7 @@ def extras(args, dda, torch, dev, shape, bits, alpha, nd, pass_ms, khat, pols, m
                                 "unit": "TFLOP/s", "frac": ach / peak64, "flops_per_matvec": fl,
                                 "peak_source": "cuBLAS DGEMM 8192^3 (torch.matmul, float64) measured in this run"}
         if args.fp64_solve:
-            E = torch.empty((3, nd), dtype=torch.complex128, device=dev)
-            P = torch.empty_like(E)
-            dda.dda_incident_field(ctx, khat, pols[0], E)
-            torch.cuda.synchronize(dev)
-            t0 = time.perf_counter()
-            status, info = dda.dda_solve(ctx, E, P, args.method, "fp64", args.tol, args.max_iter)
-            dt = time.perf_counter() - t0
-            out["fp64_solve"] = {"seconds": dt, "solves_per_s": 1.0 / dt, "status": status,
-                                 "iterations": info["iterations"], "matvecs": info["matvecs"],
-                                 "rel_residual_true": info["rel_residual_true"],
-                                 "cross_sections": dda.dda_cross_sections(ctx, E, P)}
-            del E, P
-        if args.qmr_solve:
-            out["qmr_mixed_solve"] = timed_single_solve(dda, torch, dev, ctx, nd, khat, pols[0], "qmr", args)
+            out["mixed_vs_fp64"] = mixed_vs_fp64(dda, torch, dev, ctx, nd, khat, pols[0], args)
         for meth in [m for m in args.also_methods.split(",") if m]:
             out.setdefault("other_methods", {})[meth] = timed_single_solve(dda, torch, dev, ctx, nd, khat, pols[0],
                                                                            meth, args)
@@ -451,6 +473,123 @@ def extras(args, dda, torch, dev, shape, bits, alpha, nd, pass_ms, khat, pols, m
             out["batch"] = timed_batch(dda, torch, dev, ctx, nd, args)
         if args.unpruned:
             out["unpruned_cufft"] = timed_unpruned(dda, torch, dev, ctx, mask, alpha, nd)
+    finally:
+        dda.dda_free(ctx)
+    out["context_setup"] = timed_setup(dda, torch, dev, shape, bits, alpha)
+    if args.ellipsoid_matvecs > 0:
+        out["ellipsoid_128"] = ellipsoid_matvecs(dda, torch, dev, args.ellipsoid_matvecs, hbm)
+    if args.aggregates:
+        out["aggregates"] = aggregates_workload(dda, torch, dev, args, extra=True)
+    return out
+
+
+def timed_solve(dda, torch, dev, ctx, E, method, precision, args):
+    """One solve of A P = E (device) from zero; seconds by host wall clock
+    around the synchronising call."""
+    P = torch.empty_like(E)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    status, info = dda.dda_solve(ctx, E, P, method, precision, args.tol, args.max_iter)
+    dt = time.perf_counter() - t0
+    cx = dda.dda_cross_sections(ctx, E, P)
+    rec = {"method": method, "precision": precision, "seconds": dt, "solves_per_s": 1.0 / dt, "status": status,
+           "iterations": info["iterations"], "matvecs": info["matvecs"], "matvecs_fp64": info["matvecs_fp64"],
+           "refinements": info["refinements"], "rel_residual_true": info["rel_residual_true"],
+           "cross_sections": cx}
+    return rec, P
+
+
+def mixed_vs_fp64(dda, torch, dev, ctx, nd, khat, e0, args):
+    """The bench target's first right-hand side solved to the bench tolerance
+    with BiCGSTAB and QMR, each in mixed precision (complex64 products in
+    FP64 refinement) and in FP64: time, products, true residual (one FP64
+    product), and the mixed result's relative difference from the FP64 one
+    in C_ext, C_abs, C_sca and in P."""
+    E = torch.empty((3, nd), dtype=torch.complex128, device=dev)
+    dda.dda_incident_field(ctx, khat, e0, E)
+    res = {"tol": args.tol, "what": "same right-hand side, BiCGSTAB and QMR, mixed and FP64"}
+    for method in ("bicgstab", "qmr"):
+        mixed, Pm = timed_solve(dda, torch, dev, ctx, E, method, "mixed", args)
+        fp64, Pf = timed_solve(dda, torch, dev, ctx, E, method, "fp64", args)
+        diff = [abs(a / b - 1.0) for a, b in zip(mixed["cross_sections"], fp64["cross_sections"])]
+        pdiff = float((Pm - Pf).norm() / Pf.norm())
+        res[method] = {"mixed": mixed, "fp64": fp64, "speedup_mixed_over_fp64": fp64["seconds"] / mixed["seconds"],
+                       "rel_diff_cext_cabs_csca": diff, "rel_diff_P": pdiff}
+        del Pm, Pf
+    del E
+    return res
+
+
+def timed_setup(dda, torch, dev, shape, bits, alpha, reps=3):
+    """Context set-up of the bench target (ranks, alpha^-1 table, the FP64
+    Green's-tensor spectrum build with its complex64 copy, workspace), the
+    step the paper times as tensor creation + DFT (Table 4)."""
+    ms = []
+    for r in range(reps + 1):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        ctx = dda.dda_init_lattice(shape, bits, None, 1, alpha, K_WAVE)
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        dda.dda_free(ctx)
+        if r:
+            ms.append(dt * 1e3)
+    return {"ms": statistics.median(ms), "samples_ms": ms,
+            "what": "dda_init_lattice at 256^3 (padded 512^3): device allocations, ranks, alpha^-1, spectrum "
+                    "(section 1 + x/y/z line DFTs in FP64, complex64 copy)"}
+
+
+ELL_SEED = 20260002
+ELL_M = (1.5 + 0.01j, 1.7 + 0.1j)
+
+
+def ellipsoid_matvecs(dda, torch, dev, reps, hbm):
+    """The matvec-throughput workload: a seeded random ellipsoid (semi-axes
+    uniform in 0.6-1.0 x 64) in a 128^3 lattice, two materials (m1 = 1.5 +
+    0.01i, m2 = 1.7 + 0.1i by a Bernoulli(0.3) draw, one composition bit),
+    LDR with |m2| k d = 0.8, p complex normal; `reps` timed products in
+    complex64 and in complex128 after 10 untimed ones (CUDA events)."""
+    import numpy as np
+
+    import synth
+    mask, axes = synth.random_ellipsoid(ELL_SEED, 128)
+    mats = synth.bernoulli_materials(ELL_SEED + 1, mask, 0.3)
+    k = 0.8 / abs(ELL_M[1])
+    alpha = dda.dda_polarizability(list(ELL_M), k, "ldr", [0, 0, 1], [1, 0, 0])
+    n = mask.size
+    md = torch.from_numpy(mask.reshape(-1)).to(dev)
+    bits = torch.empty((n + 31) // 32, dtype=torch.int32, device=dev)
+    dda.dda_pack_occupancy(md, bits)
+    matd = torch.from_numpy(np.ascontiguousarray(mats.reshape(-1))).to(dev)
+    cbits = torch.empty((3 * n + 31) // 32, dtype=torch.int32, device=dev)
+    dda.dda_pack_composition(matd, n, 2, cbits)
+    ctx = dda.dda_init_lattice((128, 128, 128), bits, cbits, 2, alpha, k)
+    out = {"what": f"ellipsoid semi-axes {tuple(round(a, 2) for a in axes)} in 128^3, two materials "
+                   "(Bernoulli 0.3), LDR, |m2|kd = 0.8", "reps": reps}
+    try:
+        nd = dda.dda_query(ctx)["n_dipoles"]
+        out["n_dipoles"] = nd
+        g = torch.Generator(device="cpu").manual_seed(ELL_SEED)
+        for name, dtype in (("c64", torch.complex64), ("c128", torch.complex128)):
+            p = torch.randn((3, nd), dtype=dtype, generator=g).to(dev)
+            y = torch.empty_like(p)
+            for _ in range(10):
+                dda.dda_matvec(ctx, p, y)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                dda.dda_matvec(ctx, p, y)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1) / reps
+            es = 16 if name == "c128" else 8
+            ab = algorithmic_bytes(128, nd, es)
+            out[name] = {"matvecs_per_s": 1e3 / ms, "ms": ms,
+                         "algorithmic_GBps": ab["matvec_min"] / (ms / 1e3) / 1e9,
+                         "five_pass_GBps": sum(ab[f"P{i}"] for i in range(1, 6)) / (ms / 1e3) / 1e9,
+                         "five_pass_frac_of_hbm": sum(ab[f"P{i}"] for i in range(1, 6)) / (ms / 1e3) / 1e9 / hbm}
+            del p, y
     finally:
         dda.dda_free(ctx)
     return out
@@ -614,20 +753,19 @@ AGG_REFR = 1.6 + 0.05j
 AGG_SEED = 20260003
 
 
-def run_aggregates(args):
+def aggregates_workload(dda, torch, dev, args, extra=False):
     """Batching workload: 8 seeded ballistic aggregates of touching spheres
     (monomer diameter 8, 20-200 monomers, uneven lattices), each solved for
     64 seeded incidence directions x 2 polarisations in one batched
     mixed-precision call sharing that aggregate's spectrum; per-orientation
-    C_ext and C_abs.  value = solves per second over the whole job."""
+    C_ext and C_abs.  Returns the timed figures (CUDA events around the
+    solves of all aggregates, context set-up included); extra=True (inside
+    the default bench line) times one pass after one warm-up and skips the
+    single-call comparison."""
     import numpy as np
-    import torch
 
     import synth
-    import paper_0908_0863_gb300 as dda
 
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
     k = 0.5 / abs(AGG_REFR)
     alpha = dda.dda_polarizability([AGG_REFR], k, "cmrr")
     ndir = args.agg_directions
@@ -654,7 +792,7 @@ def run_aggregates(args):
             for b, (kh, e) in enumerate(pairs):
                 dda.dda_incident_field(ctx, kh, e, E[b])
             P = torch.zeros_like(E)
-            status, stats, infos = dda.dda_solve_batch(ctx, E, P, args.method, "mixed", args.tol, args.max_iter)
+            status, stats, infos = dda.dda_solve_batch(ctx, E, P, args.agg_method, "mixed", args.tol, args.max_iter)
             cx = dda.dda_cross_sections_batch(ctx, E, P)
             if detail is not None:
                 q = dda.dda_query(ctx)
@@ -670,7 +808,6 @@ def run_aggregates(args):
         finally:
             dda.dda_free(ctx)
 
-    tiles = {}
     if args.autotune:
         # tile widths per aggregate shape, tuned once before the timed region
         for nm, mask, _ in targets:
@@ -681,55 +818,73 @@ def run_aggregates(args):
             ctx = dda.dda_init_lattice((K_, J_, P_), bits, None, 1, alpha, k)
             try:
                 dda.dda_autotune(ctx, "c64", nb=8, reps=2)
-                tiles[nm] = dda.dda_tiles(ctx, "c64")
             finally:
                 dda.dda_free(ctx)
-    # warm-up: the smallest aggregate with a few right-hand sides
-    for _ in range(args.warmup):
+    warm = 1 if extra else args.warmup
+    steps = 1 if extra else args.steps
+    for _ in range(warm):
         solve_target(targets[0][0], targets[0][1], targets[0][2][:4], None)
     torch.cuda.synchronize(dev)
-    sampler = ClockSampler(0)
-    sampler.start()
+    sampler = None
+    if not extra:
+        sampler = ClockSampler(0)
+        sampler.start()
     l0 = dda.dda_launch_count()
     stream = torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     detail = []
     mv = solves = 0
-    torch.cuda.profiler.start()   # profiler range = the timed steps (no-op without a profiler)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         for nm, mask, pairs in targets:
             a, b = solve_target(nm, mask, pairs, detail if len(detail) < len(targets) else None)
             mv += a
             solves += b
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    torch.cuda.profiler.stop()
-    clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
-    launches = dda.dda_launch_count() - l0
-    # the same solves one right-hand side per call, on a sample of 8
-    nm, mask, pairs = targets[-1]
-    t0 = time.perf_counter()
-    solve_target(nm, mask, pairs[:8], None)
-    t_batched8 = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    for pr in pairs[:8]:
-        solve_target(nm, mask, [pr], None)
-    t_single8 = time.perf_counter() - t0
+    out = {"value": solves / (ms / 1e3), "unit": "solves/s", "ms_per_step": ms / steps, "steps": steps,
+           "solves": solves, "matvecs_per_s": mv / (ms / 1e3), "gpu_launches": int(dda.dda_launch_count() - l0),
+           "method": args.agg_method, "precision": "mixed", "tol": args.tol,
+           "workload": f"{len(targets)} ballistic aggregates ({', '.join(str(t[0]) for t in targets)} monomers of "
+                       f"diameter 8), m=1.6+0.05i, |m|kd=0.5, CM+RR, {ndir} directions x 2 polarisations each, "
+                       f"one dda_solve_batch per aggregate",
+           "aggregates": detail}
+    if sampler is not None:
+        out["clocks"] = sampler.stop()
+    if not extra:
+        # the same solves one right-hand side per call, on a sample of 8
+        nm, mask, pairs = targets[-1]
+        t0 = time.perf_counter()
+        solve_target(nm, mask, pairs[:8], None)
+        t_batched8 = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for pr in pairs[:8]:
+            solve_target(nm, mask, [pr], None)
+        t_single8 = time.perf_counter() - t0
+        out["batched_vs_single_8rhs_largest"] = {"batched_s": t_batched8, "single_calls_s": t_single8,
+                                                 "speedup": t_single8 / t_batched8}
+    return out
+
+
+def run_aggregates(args):
+    """--workload aggregates: the batching workload as its own JSON line."""
+    import torch
+
+    import paper_0908_0863_gb300 as dda
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    r = aggregates_workload(dda, torch, dev, args, extra=False)
     print(json.dumps({
         "metric": "batched mixed-precision solves/s: 8 ballistic aggregates x 64 orientations x 2 polarisations",
-        "value": solves / (ms / 1e3), "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "value": r["value"], "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c64+f64 (complex64 FFT products, FP64 refinement)", "data": "synthetic",
-        "config": {"workload": f"{len(targets)} ballistic aggregates ({', '.join(str(t[0]) for t in targets)} "
-                               f"monomers of diameter 8), m=1.6+0.05i, |m|kd=0.5, CM+RR, {ndir} directions x 2 "
-                               f"polarisations each, mixed {args.method} {args.tol:g}",
-                   "parallelism": "single", "batch": "one dda_solve_batch per aggregate (all its orientations)"},
-        "matvecs_per_s": mv / (ms / 1e3), "clocks": clocks, "gpu_launches": int(launches),
-        "aggregates": detail,
-        "batched_vs_single_8rhs_largest": {"batched_s": t_batched8, "single_calls_s": t_single8,
-                                           "speedup": t_single8 / t_batched8},
+        "config": {"workload": r["workload"], "parallelism": "single",
+                   "batch": "one dda_solve_batch per aggregate (all its orientations)"},
+        "matvecs_per_s": r["matvecs_per_s"], "clocks": r.get("clocks"), "gpu_launches": r["gpu_launches"],
+        "aggregates": r["aggregates"], "batched_vs_single_8rhs_largest": r["batched_vs_single_8rhs_largest"],
     }), flush=True)
 
 
@@ -808,8 +963,15 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=200)
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--fp64-solve", action="store_true")
-    ap.add_argument("--qmr-solve", action="store_true", help="also time one mixed QMR solve")
+    ap.add_argument("--no-fp64-solve", dest="fp64_solve", action="store_false",
+                    help="skip the mixed-vs-FP64 BiCGSTAB and QMR solves of the extras")
+    ap.add_argument("--ellipsoid-matvecs", type=int, default=1000,
+                    help="timed products per precision on the 128^3 two-material ellipsoid (0: skip)")
+    ap.add_argument("--no-aggregates", dest="aggregates", action="store_false",
+                    help="skip the ballistic-aggregate batching workload of the extras")
+    ap.add_argument("--agg-method", default="bicgstab")
+    ap.add_argument("--e2e-steps", type=int, default=3,
+                    help="jobs timed end to end through host buffers (at most --steps)")
     ap.add_argument("--also-methods", default="", help="comma-separated methods to time one mixed solve each")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the default tile widths instead of tuning them before the warm-up")

@@ -95,6 +95,10 @@ typedef enum {
 #define DDA_PRECOND_JACOBI 0x100
 typedef enum { DDA_FP64 = 0, DDA_MIXED = 1 } dda_precision;
 typedef enum { DDA_POL_CM = 0, DDA_POL_CMRR = 1, DDA_POL_LDR = 2 } dda_polarizability_rule;
+/* OR into the rule of dda_polarizability and dda_polarizability_derivative:
+ * the input array holds the complex permittivities eps = m^2 instead of the
+ * refractive indices m. */
+#define DDA_POL_EPS 0x10
 
 typedef struct {
     int iterations;           /* Krylov iterations (inner ones summed, mixed)   */
@@ -116,10 +120,10 @@ typedef struct {
  *   LDR  : a_CM / (1 + a_CM [(b1 + m^2 b2 + m^2 b3 S) k^2 - (2/3) i k^3]),
  *          b1 = -1.8915316, b2 = 0.1648469, b3 = -1.7700004,
  *          S = sum_a (khat_a e0_a)^2                      (Draine & Goodman 1993)
- * m: [n][2] (re, im); khat: unit propagation (LDR only, may be NULL
- * otherwise); e0: [3][2] polarisation (LDR only); alpha_out: [n][3][2], the
- * same value on all three axes.  Returns DDA_ERR_ARG for n < 1 or an
- * unknown rule.
+ * m: [n][2] (re, im), or eps itself when DDA_POL_EPS is OR'd into rule;
+ * khat: unit propagation (LDR only, may be NULL otherwise); e0: [3][2]
+ * polarisation (LDR only); alpha_out: [n][3][2], the same value on all
+ * three axes.  Returns DDA_ERR_ARG for n < 1 or an unknown rule.
  */
 int dda_polarizability(int n, const double* m, double k, int rule, const double* khat,
                        const double* e0, double* alpha_out);
@@ -253,6 +257,33 @@ int dda_tiles(dda_ctx* ctx, int dtype, int* tiles_out, const int* tiles_in);
  * sides; may grow the workspace to nb slots.  Synchronises the stream.
  */
 int dda_autotune(dda_ctx* ctx, int dtype, int nb, int reps, double* pass_ms, void* stream);
+
+/*
+ * Mixed precision (DDA_MIXED): every inner complex64 solve aims at the
+ * relative residual max(0.3 tol / rho_now, 1e-6, rho), rho_now being the
+ * refinement's current relative residual: by default (rho = 0) one inner
+ * solve reaches the final tolerance, a larger rho (in (0, 1)) stops each
+ * inner solve after that reduction and lets the FP64 refinement take more
+ * steps.  rho_in (may be NULL) sets rho, rho_out (may be NULL) receives it.
+ * This is a choice of this library (the paper runs one precision only).
+ */
+int dda_inner_tolerance(dda_ctx* ctx, const double* rho_in, double* rho_out);
+
+/*
+ * Tune rho of dda_inner_tolerance on this context: solve A P = einc (host
+ * or device [3][N_d] complex128) in mixed precision to tol with the given
+ * method for rho = 0, 1e-4, 1e-3 and 1e-2, timing each solve with CUDA
+ * events, and keep the fastest that converged; rho = 0 stays unless another
+ * candidate is faster by more than 2% (the noise of one timing is about
+ * 1%).  The choice is set on the
+ * context and remembered for the process: contexts created later with the
+ * same lattice shape start with it.  rho_out (host, may be NULL) receives
+ * it, ms_out (host double[4], may be NULL) the solve times (-1: not
+ * converged).  Allocates and frees one scratch solution; synchronises.
+ * DDA_ERR_NOT_CONVERGED when no candidate converged.
+ */
+int dda_autotune_inner(dda_ctx* ctx, const void* einc, int method, double tol, int max_iter, double* rho_out,
+                       double* ms_out, void* stream);
 
 /*
  * Grow the solve workspace to hold nb right-hand sides (1 <= nb <= 4096)
@@ -401,6 +432,21 @@ int dda_scattering_cross_section(dda_ctx* ctx, const void* p, double* out, void*
  */
 int dda_polarizability_derivative(int n, const double* m, double k, int rule, const double* khat,
                                   const double* e0, double* dalpha_inv_out);
+
+/*
+ * Per-material sums of a per-dipole complex field: out[q] = sum of v_j over
+ * the occupied sites j whose composition field of axis x holds material q
+ * (all dipoles are material 0 without composition bits).  With v =
+ * dda_gradient's g this is the chain rule from per-dipole permittivities
+ * to one permittivity per material, dC/deps_q (all dipoles of a material
+ * share its eps).  The paper has no gradient; this is the last step of the
+ * adjoint gradient of dda_gradient.
+ *   v:   host or device [N_d] complex128, compressed order.
+ *   out: host double[n_materials][2] (re, im).
+ * At most 32 materials (DDA_ERR_ARG beyond).  Fixed summation order (the
+ * same bits on every call).  Synchronises the stream.
+ */
+int dda_material_sums(dda_ctx* ctx, const void* v, double* out, void* stream);
 
 /*
  * Gradient of C_ext (which = 0) or C_abs (which = 1) with respect to the

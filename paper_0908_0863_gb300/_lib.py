@@ -31,6 +31,7 @@ DDA_MLBICGSTAB1, DDA_MLBICGSTAB2, DDA_MLBICGSTAB3 = 11, 12, 13
 DDA_PRECOND_JACOBI = 0x100
 DDA_FP64, DDA_MIXED = 0, 1
 DDA_POL_CM, DDA_POL_CMRR, DDA_POL_LDR = 0, 1, 2
+DDA_POL_EPS = 0x10
 
 METHODS = {"bicg": DDA_BICG, "bicgstab": DDA_BICGSTAB, "qmr": DDA_QMR, "bicg_sym": DDA_BICG_SYM, "cg": DDA_CG,
            "cgs": DDA_CGS, "tfqmr": DDA_TFQMR, "qmr_sym": DDA_QMR_SYM, "rbicgstab1": DDA_RBICGSTAB1,
@@ -58,6 +59,7 @@ EXPORTS = (
     "dda_unpack_composition", "dda_init_lattice", "dda_free", "dda_query", "dda_site_ranks",
     "dda_tensor_spectrum", "dda_matvec", "dda_incident_field", "dda_solve", "dda_cross_sections",
     "dda_profile", "dda_profile_read", "dda_launch_count", "dda_last_error", "dda_occupancy_ranks_static",
+    "dda_material_sums", "dda_inner_tolerance", "dda_autotune_inner",
     "dda_scattering_cross_section", "dda_polarizability_derivative", "dda_gradient",
     "dda_matvec_batch", "dda_reserve", "dda_solve_batch", "dda_cross_sections_batch", "dda_tiles",
     "dda_autotune",
@@ -118,6 +120,9 @@ def load(path: str | None = None):
     L.dda_solve_batch.argtypes = [vp, i32, vp, vp, i32, i32, d, i32, i32, vp, vp, vp]
     L.dda_cross_sections_batch.argtypes = [vp, i32, vp, vp, vp, vp]
     L.dda_occupancy_ranks_static.argtypes = [vp, i64, vp, vp, vp]
+    L.dda_material_sums.argtypes = [vp, vp, vp, vp]
+    L.dda_inner_tolerance.argtypes = [vp, vp, vp]
+    L.dda_autotune_inner.argtypes = [vp, vp, i32, ctypes.c_double, i32, vp, vp, vp]
     L.dda_scattering_cross_section.argtypes = [vp, vp, vp, vp]
     L.dda_polarizability_derivative.argtypes = [i32, vp, d, i32, vp, vp, vp]
     L.dda_gradient.argtypes = [vp, i32, vp, vp, vp, i32, i32, d, i32, vp, ctypes.POINTER(SolveInfo), vp]
@@ -180,15 +185,16 @@ def _c2(v, n):
 
 # ------------------------------------------------------------ entry points
 
-def dda_polarizability(m, k, rule="cmrr", khat=None, e0=None) -> np.ndarray:
-    """alpha per material and axis, shape (n_materials, 3) complex128."""
+def dda_polarizability(m, k, rule="cmrr", khat=None, e0=None, given="m") -> np.ndarray:
+    """alpha per material and axis, shape (n_materials, 3) complex128; m holds
+    refractive indices (given="m") or permittivities (given="eps")."""
     m = np.atleast_1d(np.asarray(m, dtype=np.complex128))
     n = m.size
     out = np.zeros(n * 6)
     kh = None if khat is None else np.ascontiguousarray(np.asarray(khat, dtype=np.float64))
     ee = None if e0 is None else _c2(e0, 3)
-    _check(load().dda_polarizability(n, _ptr(_c2(m, n)), float(k), RULES.get(rule, rule),
-                                     _ptr(kh), _ptr(ee), _ptr(out)))
+    code = RULES.get(rule, rule) | (DDA_POL_EPS if given == "eps" else 0)
+    _check(load().dda_polarizability(n, _ptr(_c2(m, n)), float(k), code, _ptr(kh), _ptr(ee), _ptr(out)))
     return (out[0::2] + 1j * out[1::2]).reshape(n, 3)
 
 
@@ -341,16 +347,43 @@ def dda_scattering_cross_section(ctx, p, stream=None) -> float:
     return float(out[0])
 
 
-def dda_polarizability_derivative(m, k, rule="cmrr", khat=None, e0=None) -> np.ndarray:
-    """d(1/alpha)/d eps per material and axis, shape (n_materials, 3) complex128."""
+def dda_polarizability_derivative(m, k, rule="cmrr", khat=None, e0=None, given="m") -> np.ndarray:
+    """d(1/alpha)/d eps per material and axis, shape (n_materials, 3) complex128;
+    m holds refractive indices (given="m") or permittivities (given="eps")."""
     m = np.atleast_1d(np.asarray(m, dtype=np.complex128))
     n = m.size
     out = np.zeros(n * 6)
     kh = None if khat is None else np.ascontiguousarray(np.asarray(khat, dtype=np.float64))
     ee = None if e0 is None else _c2(e0, 3)
-    _check(load().dda_polarizability_derivative(n, _ptr(_c2(m, n)), float(k), RULES.get(rule, rule),
-                                                _ptr(kh), _ptr(ee), _ptr(out)))
+    code = RULES.get(rule, rule) | (DDA_POL_EPS if given == "eps" else 0)
+    _check(load().dda_polarizability_derivative(n, _ptr(_c2(m, n)), float(k), code, _ptr(kh), _ptr(ee),
+                                                _ptr(out)))
     return (out[0::2] + 1j * out[1::2]).reshape(n, 3)
+
+
+def dda_inner_tolerance(ctx, rho=None) -> float:
+    """The mixed-precision inner reduction rho of the context (set first when given)."""
+    rin = None if rho is None else np.array([float(rho)])
+    out = np.zeros(1)
+    _check(load().dda_inner_tolerance(ctypes.c_void_p(ctx), _ptr(rin), _ptr(out)))
+    return float(out[0])
+
+
+def dda_autotune_inner(ctx, einc, method="bicgstab", tol=1e-5, max_iter=4000, stream=None):
+    """Tunes rho on einc; returns (rho, {rho candidate: solve ms or -1})."""
+    rho = np.zeros(1)
+    ms = np.zeros(4)
+    _check(load().dda_autotune_inner(ctypes.c_void_p(ctx), _ptr(einc), method_code(method), float(tol),
+                                     int(max_iter), _ptr(rho), _ptr(ms), _stream(stream)))
+    return float(rho[0]), dict(zip((0.0, 1e-4, 1e-3, 1e-2), (float(v) for v in ms)))
+
+
+def dda_material_sums(ctx, v, n_materials, stream=None) -> np.ndarray:
+    """Per-material sums of a per-dipole complex128 field v ([N_d], host or
+    device), shape (n_materials,) complex128."""
+    out = np.zeros(2 * int(n_materials))
+    _check(load().dda_material_sums(ctypes.c_void_p(ctx), _ptr(v), _ptr(out), _stream(stream)))
+    return out[0::2] + 1j * out[1::2]
 
 
 def dda_gradient(ctx, which, einc, p, dalpha_inv, grad, method="bicgstab", precision="fp64", tol=1e-8,

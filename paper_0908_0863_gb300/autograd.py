@@ -4,10 +4,12 @@
 materials have the complex permittivities ``eps`` (one per material, a
 complex128 tensor).  The forward pass builds a context, solves A P = E_inc
 and sums the cross section; the backward pass runs the adjoint entry point
-``dda_gradient`` (one extra solve with the same matrix, A^T = A) and adds
-the per-dipole gradients of each material.  The gradient follows PyTorch's
-convention for real outputs of complex inputs: dC/dRe(eps) + i dC/dIm(eps).
-All arithmetic runs in the CUDA library.
+``dda_gradient`` (one extra solve with the same matrix, A^T = A) and
+``dda_material_sums``, which adds the per-dipole gradients of each material
+(the material of a dipole is its composition field, axis x).  The gradient
+follows PyTorch's convention for real outputs of complex inputs:
+dC/dRe(eps) + i dC/dIm(eps).  The permittivities go to the library as they
+are (DDA_POL_EPS); all arithmetic runs in the CUDA library.
 """
 from __future__ import annotations
 
@@ -28,7 +30,6 @@ class Target:
     khat: tuple = (0.0, 0.0, 1.0)
     e0: tuple = (1.0, 0.0, 0.0)
     composition_bits: np.ndarray | None = None
-    material_of_dipole: np.ndarray | None = None   # (N_d,) material index (3 axes alike), for the backward sum
     method: str = "bicgstab"
     precision: str = "fp64"
     tol: float = 1e-10
@@ -38,8 +39,8 @@ class Target:
 
 def _solve(eps, tgt: Target):
     import torch
-    m = np.sqrt(eps.detach().cpu().numpy().astype(np.complex128))
-    alpha = _lib.dda_polarizability(m, tgt.k, tgt.rule, tgt.khat, tgt.e0)
+    m = np.ascontiguousarray(eps.detach().cpu().numpy().astype(np.complex128))   # permittivities
+    alpha = _lib.dda_polarizability(m, tgt.k, tgt.rule, tgt.khat, tgt.e0, given="eps")
     ctx = _lib.dda_init_lattice(tgt.shape, tgt.occupancy_bits, tgt.composition_bits, m.size, alpha, tgt.k)
     nd = _lib.dda_query(ctx)["n_dipoles"]
     E = torch.empty((3, nd), dtype=torch.complex128, device="cuda")
@@ -85,8 +86,8 @@ def _make_function():
         def backward(fctx, grad_out):
             tgt = fctx.tgt
             E, P, m = fctx.state
-            alpha = _lib.dda_polarizability(m, tgt.k, tgt.rule, tgt.khat, tgt.e0)
-            dainv = _lib.dda_polarizability_derivative(m, tgt.k, tgt.rule, tgt.khat, tgt.e0)
+            alpha = _lib.dda_polarizability(m, tgt.k, tgt.rule, tgt.khat, tgt.e0, given="eps")
+            dainv = _lib.dda_polarizability_derivative(m, tgt.k, tgt.rule, tgt.khat, tgt.e0, given="eps")
             ctx = _lib.dda_init_lattice(tgt.shape, tgt.occupancy_bits, tgt.composition_bits, m.size, alpha, tgt.k)
             try:
                 g = torch.empty(P.shape[1], dtype=torch.complex128, device="cuda")
@@ -94,14 +95,9 @@ def _make_function():
                                                  tgt.tol, tgt.max_iter)
                 if status != _lib.DDA_OK:
                     raise _lib.DDAError(status, f"adjoint solve failed: {info}")
+                per_mat = torch.from_numpy(_lib.dda_material_sums(ctx, g, m.size))
             finally:
                 _lib.dda_free(ctx)
-            mats = tgt.material_of_dipole
-            if mats is None:
-                per_mat = g.sum().reshape(1)
-            else:
-                idx = torch.as_tensor(np.asarray(mats, dtype=np.int64), device=g.device)
-                per_mat = torch.zeros(m.size, dtype=torch.complex128, device=g.device).index_add_(0, idx, g)
-            return (grad_out.to(per_mat.device) * per_mat).to(fctx.eps_device), None
+            return (grad_out.cpu() * per_mat).to(fctx.eps_device), None
 
     return _CrossSection

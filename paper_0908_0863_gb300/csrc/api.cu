@@ -124,9 +124,11 @@ struct dda_ctx {
     double2* tw64 = nullptr;
     float2* tw32 = nullptr;
     double2* xsec = nullptr;
+    double2* msum = nullptr;  // per-material sums: block partials, then the sums
     double2* aux[3] = {};     // adjoint / C_sca work vectors (P, right-hand side, mu)
     double2* dainv64 = nullptr;  // d(alpha^-1)/d eps table of the last gradient call
     Space sp;
+    double inner_rho = 0.0;      // mixed precision: smallest residual reduction an inner solve aims at (0: none)
     MatvecView<double> mv64{};   // geometry, tables and tiles; work set per call
     MatvecView<float> mv32{};
     PassProfiler prof;
@@ -337,6 +339,11 @@ std::map<std::array<int, 4>, std::array<int, 4>> g_tiles;
 
 std::array<int, 4> tile_key(const Geometry& g, int dtype) { return {g.K, g.J, g.P, dtype}; }
 
+// The inner-solve target of the mixed precision chosen by
+// dda_autotune_inner, per lattice shape, likewise.
+std::map<std::array<int, 4>, double> g_inner;
+constexpr int kInnerCandidates = 4;
+
 template <typename T>
 void apply_tiles(MatvecView<T>& m, const std::array<int, 4>& t) {
     m.logW_y = t[0];
@@ -358,6 +365,8 @@ const char* dda_last_error(void) { return g_last_error.c_str(); }
 int dda_polarizability(int n, const double* m, double k, int rule, const double* khat, const double* e0,
                        double* alpha_out) {
     if (n < 1 || !m || !alpha_out) return fail(DDA_ERR_ARG, "dda_polarizability: bad arguments");
+    const bool given_eps = (rule & DDA_POL_EPS) != 0;
+    rule &= ~DDA_POL_EPS;
     if (rule < DDA_POL_CM || rule > DDA_POL_LDR) return fail(DDA_ERR_ARG, "dda_polarizability: unknown rule");
     if (rule == DDA_POL_LDR && (!khat || !e0)) return fail(DDA_ERR_ARG, "dda_polarizability: LDR needs khat and e0");
     if (!(k >= 0.0) || !std::isfinite(k)) return fail(DDA_ERR_ARG, "dda_polarizability: bad k");
@@ -375,7 +384,7 @@ int dda_polarizability(int n, const double* m, double k, int rule, const double*
     }
     for (int q = 0; q < n; ++q) {
         const cd mm(m[2 * q], m[2 * q + 1]);
-        const cd eps = mm * mm;
+        const cd eps = given_eps ? mm : mm * mm;
         const cd acm = 3.0 / (4.0 * M_PI) * (eps - 1.0) / (eps + 2.0);
         cd a = acm;
         if (rule == DDA_POL_CMRR) {
@@ -485,6 +494,7 @@ int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occu
         probe.take<double2>(kTwEntries);
         probe.take<float2>(kTwEntries);
         probe.take<double2>(xsec_scratch_elems());
+        probe.take<double2>(material_sums_scratch_elems(g));
         probe.take<int>(4);
         a0.cap = probe.used + 256;
     }
@@ -505,6 +515,7 @@ int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occu
     c->tw64 = a0.take<double2>(kTwEntries);
     c->tw32 = a0.take<float2>(kTwEntries);
     c->xsec = a0.take<double2>(xsec_scratch_elems());
+    c->msum = a0.take<double2>(material_sums_scratch_elems(g));
     int* flags = a0.take<int>(4);
     c->bytes_fixed = (int64_t)a0.cap;
     int rc = 0;
@@ -607,6 +618,8 @@ int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occu
         if (it != g_tiles.end()) apply_tiles(m, it->second);
         it = g_tiles.find(tile_key(g, DDA_C64));
         if (it != g_tiles.end()) apply_tiles(f, it->second);
+        auto ir = g_inner.find(tile_key(g, -1));
+        if (ir != g_inner.end()) c->inner_rho = ir->second;
     }
     *out = c;
     return DDA_OK;
@@ -944,8 +957,11 @@ static int solve_batch(dda_ctx* c, int nb, const void* einc, void* p, int method
             for (int b = 0; b < nb; ++b) {
                 if (active[b]) {
                     const double rel = std::sqrt(rn2[b] / bn2[b]);
-                    // inner target: enough to reach tol from here, not below what FP32 sustains
-                    hc[b].tol = std::min(0.5, std::max(0.3 * tol / rel, 1e-6));
+                    // inner target: enough to reach tol from here, not below what FP32
+                    // sustains, and no finer than the context's per-solve reduction
+                    double ti = std::max(0.3 * tol / rel, 1e-6);
+                    if (c->inner_rho > 0.0) ti = std::max(ti, c->inner_rho);
+                    hc[b].tol = std::min(0.5, ti);
                     hc[b].scale = 1.0 / std::sqrt(rn2[b]);
                     hc[b].mult = std::sqrt(rn2[b]);
                     hc[b].maxit = max_iter - inf[b].iterations;
@@ -1057,8 +1073,70 @@ int dda_solve(dda_ctx* c, const void* einc, void* p, int method, int precision, 
     return dda_solve_batch(c, 1, einc, p, method, precision, tol, max_iter, use_x0, info, nullptr, stream);
 }
 
+int dda_inner_tolerance(dda_ctx* c, const double* rho_in, double* rho_out) {
+    if (int rc = check_ctx(c)) return rc;
+    if (rho_in) {
+        if (!(*rho_in >= 0.0 && *rho_in < 1.0)) return fail(DDA_ERR_ARG, "dda_inner_tolerance: rho must be in [0, 1)");
+        c->inner_rho = *rho_in;
+    }
+    if (rho_out) *rho_out = c->inner_rho;
+    return DDA_OK;
+}
+
+int dda_autotune_inner(dda_ctx* c, const void* einc, int method, double tol, int max_iter, double* rho_out,
+                       double* ms_out, void* stream) {
+    if (int rc = check_solve_args(c, 1, einc, einc, method, DDA_MIXED, tol, max_iter)) return rc;
+    cudaStream_t st = as_stream(stream);
+    const double cand[kInnerCandidates] = {0.0, 1e-4, 1e-3, 1e-2};
+    const size_t bytes = 3 * c->g.nd * sizeof(double2);
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "dda_autotune_inner: scratch solution");
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const double keep = c->inner_rho;
+    double best = -1.0, best_ms = 0.0;
+    int rc = 0;
+    for (int q = 0; q < kInnerCandidates && !rc; ++q) {
+        c->inner_rho = cand[q];
+        dda_solve_info info{};
+        cudaEventRecord(e0, st);
+        int status = dda_solve_batch(c, 1, einc, p, method, DDA_MIXED, tol, max_iter, 0, &info, nullptr, stream);
+        cudaEventRecord(e1, st);
+        if (status == DDA_ERR_ARG || status == DDA_ERR_CUDA || status == DDA_ERR_OOM) { rc = status; break; }
+        float ms = 0.0f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            rc = fail(DDA_ERR_CUDA, "dda_autotune_inner: event timing failed");
+            break;
+        }
+        const double t = status == DDA_OK ? ms : -1.0;
+        if (ms_out) ms_out[q] = t;
+        // the first candidate (rho = 0, the default) is kept unless another
+        // one is faster by more than 2% (single timings differ by about 1%)
+        if (t > 0.0 && (best < 0.0 || t < (q > 0 && best == cand[0] ? 0.98 : 1.0) * best_ms)) {
+            best = cand[q];
+            best_ms = t;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(p);
+    if (rc) { c->inner_rho = keep; return rc; }
+    if (best < 0.0) { c->inner_rho = keep; return fail(DDA_ERR_NOT_CONVERGED, "dda_autotune_inner: no candidate converged"); }
+    c->inner_rho = best;
+    {
+        std::lock_guard<std::mutex> lock(g_tiles_mu);
+        g_inner[tile_key(c->g, -1)] = best;
+    }
+    if (rho_out) *rho_out = best;
+    return DDA_OK;
+}
+
 int dda_polarizability_derivative(int n, const double* m, double k, int rule, const double* khat, const double* e0,
                                   double* out) {
+    const bool given_eps = (rule & DDA_POL_EPS) != 0;
+    rule &= ~DDA_POL_EPS;
     if (n < 1 || !m || !out) return fail(DDA_ERR_ARG, "dda_polarizability_derivative: bad arguments");
     if (rule < DDA_POL_CM || rule > DDA_POL_LDR)
         return fail(DDA_ERR_ARG, "dda_polarizability_derivative: unknown rule");
@@ -1077,7 +1155,7 @@ int dda_polarizability_derivative(int n, const double* m, double k, int rule, co
     const double b2 = 0.1648469, b3 = -1.7700004;
     for (int q = 0; q < n; ++q) {
         const cd mm(m[2 * q], m[2 * q + 1]);
-        const cd eps = mm * mm;
+        const cd eps = given_eps ? mm : mm * mm;
         if (eps == cd(1.0, 0.0)) return fail(DDA_ERR_ARG, "dda_polarizability_derivative: m = 1 (no polarisability)");
         // 1/alpha_CM = (4 pi/3)(eps + 2)/(eps - 1): derivative -4 pi/(eps - 1)^2;
         // radiative reaction adds a constant; LDR adds (b1 + eps b2 + eps b3 S) k^2
@@ -1088,6 +1166,24 @@ int dda_polarizability_derivative(int n, const double* m, double k, int rule, co
             out[(q * 3 + c) * 2 + 1] = d.imag();
         }
     }
+    return DDA_OK;
+}
+
+int dda_material_sums(dda_ctx* c, const void* v, double* out, void* stream) {
+    if (int rc = check_ctx(c)) return rc;
+    if (!v || !out) return fail(DDA_ERR_ARG, "dda_material_sums: NULL argument");
+    if (c->g.nmat > kMaxSumMaterials) return fail(DDA_ERR_ARG, "dda_material_sums: more than 32 materials");
+    cudaStream_t st = as_stream(stream);
+    const double2* vd = static_cast<const double2*>(v);
+    if (!is_device_ptr(v)) {
+        DDA_CUDA_TRY(cudaMemcpyAsync(c->aux[0], v, c->g.nd * sizeof(double2), cudaMemcpyHostToDevice, st));
+        vd = c->aux[0];
+    }
+    if (int rc = launch_material_sums(target_view(c), c->g, vd, c->msum, st)) return rc;
+    std::vector<double2> h(c->g.nmat);
+    DDA_CUDA_TRY(cudaMemcpyAsync(h.data(), c->msum, c->g.nmat * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    DDA_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int q = 0; q < c->g.nmat; ++q) { out[2 * q] = h[q].x; out[2 * q + 1] = h[q].y; }
     return DDA_OK;
 }
 

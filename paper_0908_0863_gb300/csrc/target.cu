@@ -468,6 +468,57 @@ int launch_gradient(const TargetView& tv, const Geometry& g, double k, int which
     return 0;
 }
 
+// ------------------------------------------------------ per-material sums
+// Each thread sums the values of its sites into its own row of a shared
+// [threads][nmat] table (no atomics), the block adds the rows in a fixed
+// order and writes one partial per material, and one block adds the
+// partials in block order: the same bits on every call.
+constexpr int kSumThreads = 64;   // the [threads][32] table of double2 fits 32 KB
+constexpr int kSumBlocks = 256;
+
+size_t material_sums_scratch_elems(const Geometry&) { return (size_t)(kSumBlocks + 1) * kMaxSumMaterials; }
+
+__global__ void __launch_bounds__(kSumThreads) k_material_partial(TargetView tv, Geometry g,
+                                                                   const double2* __restrict__ v,
+                                                                   double2* __restrict__ part) {
+    __shared__ double2 acc[kSumThreads][kMaxSumMaterials];
+    const int nm = g.nmat;
+    for (int q = 0; q < nm; ++q) acc[threadIdx.x][q] = make_double2(0.0, 0.0);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < g.nsites; s += stride) {
+        if (!occupied(tv, s)) continue;
+        const double2 x = v[site_rank(tv, s)];
+        double2& a = acc[threadIdx.x][material(tv, s, 0)];
+        a.x += x.x;
+        a.y += x.y;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < nm; q += blockDim.x) {
+        double2 t = make_double2(0.0, 0.0);
+        for (int i = 0; i < kSumThreads; ++i) { t.x += acc[i][q].x; t.y += acc[i][q].y; }
+        part[blockIdx.x * kMaxSumMaterials + q] = t;
+    }
+}
+
+__global__ void k_material_final(const double2* __restrict__ part, int nblocks, int nm, double2* __restrict__ out) {
+    for (int q = threadIdx.x; q < nm; q += blockDim.x) {
+        double2 t = make_double2(0.0, 0.0);
+        for (int b = 0; b < nblocks; ++b) { t.x += part[b * kMaxSumMaterials + q].x; t.y += part[b * kMaxSumMaterials + q].y; }
+        out[q] = t;
+    }
+}
+
+int launch_material_sums(const TargetView& tv, const Geometry& g, const double2* v, double2* scratch,
+                         cudaStream_t st) {
+    if (g.nmat > kMaxSumMaterials) return fail(DDA_ERR_ARG, "material sums: more than 32 materials");
+    const int nblocks = (int)std::max<int64_t>(1, std::min<int64_t>(kSumBlocks, (g.nsites + kSumThreads - 1) / kSumThreads));
+    k_material_partial<<<nblocks, kSumThreads, 0, st>>>(tv, g, v, scratch + kMaxSumMaterials);
+    DDA_LAUNCH_CHECK("material sums");
+    k_material_final<<<1, kMaxSumMaterials, 0, st>>>(scratch + kMaxSumMaterials, nblocks, g.nmat, scratch);
+    DDA_LAUNCH_CHECK("material sums final");
+    return 0;
+}
+
 // ------------------------------------- rank scan without device allocation
 // dda_occupancy_ranks_static runs the rank scan above with its per-block
 // totals in this file-scope array instead of caller or context memory, so

@@ -46,6 +46,13 @@ int launch_adjoint_rhs(const TargetView& tv, const Geometry& g, double k, int wh
 int launch_gradient(const TargetView& tv, const Geometry& g, double k, int which, const double2* dainv,
                     const double2* P, const double2* mu, double2* grad, cudaStream_t st);
 
+// out[q] = sum of v[rank(s)] over the occupied sites s of material q (axis
+// x field), q < g.nmat <= kMaxSumMaterials; scratch: at least
+// material_sums_scratch_elems(g) elements; out may alias scratch
+constexpr int kMaxSumMaterials = 32;
+size_t material_sums_scratch_elems(const Geometry& g);
+int launch_material_sums(const TargetView& tv, const Geometry& g, const double2* v, double2* out, cudaStream_t st);
+
 // Point-Jacobi scaling (Sec. 6): vec[b][c][rank(s)] *= tab[material(s, c)][c]
 // (or /= with inverse) for every occupied site s and right-hand side b < nb
 // (vectors of stride elements); tab = diag(A)^(-1/2) per material and axis

@@ -54,7 +54,8 @@ def test_warmup_below_three_is_refused():
 @pytest.mark.gpu
 def test_our_arm_contract():
     d = _run(["--edge", "32", "--diameter", "30", "--steps", "3", "--warmup", "3", "--batch", "2",
-              "--cpu-rows", "20"], timeout=900)
+              "--cpu-rows", "20", "--ellipsoid-matvecs", "20", "--agg-count", "1", "--agg-directions", "2"],
+             timeout=900)
     _common(d)
     assert "impl" not in d and d["n_gpus"] == 1
     assert d["gpu_launches"] > 0
@@ -70,3 +71,18 @@ def test_our_arm_contract():
     assert d["unpruned_cufft"]["c128"]["rel_diff_vs_library"] < 1e-12
     assert d["unpruned_cufft"]["c64"]["rel_diff_vs_library"] < 2e-5
     assert d["job"]["status"] == [0]
+    # the extras of the default line: mixed against FP64 on the same right-hand
+    # side (BiCGSTAB and QMR), the set-up time, the two-material ellipsoid
+    # and the aggregate workload
+    mv = d["mixed_vs_fp64"]
+    for method in ("bicgstab", "qmr"):
+        r = mv[method]
+        assert r["mixed"]["status"] == 0 and r["fp64"]["status"] == 0
+        assert r["mixed"]["rel_residual_true"] <= 1e-5 and r["fp64"]["rel_residual_true"] <= 1e-5
+        assert max(r["rel_diff_cext_cabs_csca"]) < 1e-4
+    assert d["context_setup"]["ms"] > 0
+    for name in ("c64", "c128"):
+        assert d["ellipsoid_128"][name]["matvecs_per_s"] > 0
+    agg = d["aggregates"]
+    assert agg["solves"] == 4 and agg["value"] > 0 and agg["aggregates"][0]["status"] == [0]
+    assert d["e2e"]["steps"] >= 1

@@ -171,8 +171,7 @@ def test_autograd_function_material_gradient(dda, crop_case):
     case = crop_case
     occ = odda.occupied_sites(case.mask)
     tgt = Target(shape=case.shape, occupancy_bits=case.occ_bits, k=case.k, which="abs", rule="cmrr",
-                 composition_bits=case.comp_bits, material_of_dipole=case.materials.reshape(-1, 3)[occ, 0],
-                 tol=1e-13)
+                 composition_bits=case.comp_bits, tol=1e-13)
     eps = torch.tensor([m * m for m in case.refr], dtype=torch.complex128, requires_grad=True)
     c = CrossSection.apply(eps, tgt)
     c.backward()
@@ -191,3 +190,28 @@ def test_autograd_function_material_gradient(dda, crop_case):
             fd.append((CrossSection.apply(e_p, tgt).item() - CrossSection.apply(e_m, tgt).item()) / (2 * h))
         fdq = fd[0] + 1j * fd[1]
         assert abs(fdq - eps.grad[q].item()) <= 1e-5 * abs(eps.grad).max().item()
+
+
+def test_material_sums_match_dense_adjoint(dda, crop_case):
+    """dda_material_sums of the per-dipole gradient equals the oracle's
+    dense-adjoint gradient summed over the dipoles of each material, and a
+    permittivity passed as eps (DDA_POL_EPS) gives the polarisability and
+    its derivative of the same material passed as m."""
+    case = crop_case
+    occ = odda.occupied_sites(case.mask)
+    mats = case.materials.reshape(-1, 3)[occ, 0]
+    eps = np.array([m * m for m in case.refr])
+    assert np.array_equal(dda.dda_polarizability(eps, case.k, "cmrr", given="eps"),
+                          dda.dda_polarizability(case.refr, case.k, "cmrr"))
+    d_eps = dda.dda_polarizability_derivative(eps, case.k, "cmrr", given="eps")
+    d_m = dda.dda_polarizability_derivative(case.refr, case.k, "cmrr")
+    assert np.abs(d_eps - d_m).max() <= 1e-15 * np.abs(d_m).max()
+    with case.lattice() as lat:
+        g = _gpu_gradient(dda, lat, case, "abs", "fp64", 1e-13)
+        sums = dda.dda_material_sums(lat.ctx, torch.from_numpy(g).to(DEV), case.nmat)
+        sums_host = dda.dda_material_sums(lat.ctx, np.ascontiguousarray(g), case.nmat)
+    assert np.array_equal(sums, sums_host)
+    E = odda.incident_field(case.coords, case.k, [0, 0, 1], [1, 0, 0])
+    ref, _ = oadj.abs_gradient_dense(case.coords, case.ainv, _oracle_dainv(case), case.k, E)
+    want = np.array([ref[mats == q].sum() for q in range(case.nmat)])
+    assert np.abs(sums - want).max() <= 1e-9 * np.abs(want).max()

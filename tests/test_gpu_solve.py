@@ -154,3 +154,31 @@ def test_polarizability_matches_oracle(dda):
     assert np.allclose(got[:, 1], [odda.alpha_ldr(m, k, kh, e) for m in ms], rtol=1e-15)
     got = dda.dda_polarizability(ms, k, "cm")
     assert np.allclose(got[:, 2], [odda.alpha_cm(m) for m in ms], rtol=1e-15)
+
+
+def test_inner_tolerance_control_and_autotune(dda):
+    """Mixed precision with a coarse inner target (rho = 1e-2) needs more FP64
+    refinements and reaches the same tolerance; dda_autotune_inner picks one
+    of its candidates, sets it and hands it to the next context of the shape
+    (a lattice shape of its own, so that no other test inherits the choice)."""
+    m = 1.33 + 0.01j
+    case = Case(synth.sphere(16, box=(16, 16, 17)), [m], 0.5 / abs(m))
+    with case.lattice() as lat:
+        E = torch.empty((3, case.nd), dtype=torch.complex128, device="cuda")
+        lat.incident_field([0, 0, 1], [1, 0, 0], E)
+        assert dda.dda_inner_tolerance(lat.ctx) == 0.0
+        P = torch.zeros_like(E)
+        s0, i0 = lat.solve(E, P, "bicgstab", "mixed", tol=1e-8, max_iter=2000)
+        assert dda.dda_inner_tolerance(lat.ctx, 1e-2) == 1e-2
+        P1 = torch.zeros_like(E)
+        s1, i1 = lat.solve(E, P1, "bicgstab", "mixed", tol=1e-8, max_iter=2000)
+        assert s0 == s1 == dda.DDA_OK
+        assert i1["rel_residual_true"] <= 1e-8 and i1["refinements"] > i0["refinements"]
+        assert float((P1 - P).norm() / P.norm()) < 1e-7
+        with pytest.raises(dda.DDAError):
+            dda.dda_inner_tolerance(lat.ctx, 1.5)
+        rho, ms = dda.dda_autotune_inner(lat.ctx, E, "bicgstab", 1e-8, 2000)
+        assert rho in ms and ms[rho] > 0 and all(v == -1 or v > 0 for v in ms.values())
+        assert dda.dda_inner_tolerance(lat.ctx) == rho
+    with case.lattice() as lat2:
+        assert dda.dda_inner_tolerance(lat2.ctx) == rho
