@@ -31,12 +31,17 @@
 // stage of a power-of-two length (a 3 * 2^a or 5 * 2^a length computes all
 // outputs).
 //
-// Shared-memory addresses come from a layout functor (line w, point p),
-// which also provides the barrier of the exchanges: RowLayout keeps each
-// line contiguous (lines of the lattice that are contiguous in memory,
-// threads t-fastest) and RowGroupLayout does the same with a barrier per
-// group of lines; ColLayoutT keeps point-major tiles of 2^logW lines side
-// by side (strided lines of the lattice, threads w-fastest).
+// Shared-memory addresses come from a layout object (line w, point p, and
+// the exchange), which also provides the barrier of the exchanges:
+// RowLayout keeps each line contiguous (lines of the lattice that are
+// contiguous in memory, threads t-fastest) with a bank-conflict pad per
+// exchange; ColLayoutT keeps point-major tiles of 2^logW lines side by side
+// (strided lines of the lattice, threads w-fastest).
+//
+// Lines of 3 * 2^a and 5 * 2^a points can also use the wide mapping below
+// (M/8 threads of 8R points per line; fft_wide), which needs one exchange
+// fewer and no shared-memory closing stage; fft_line picks the mapping
+// of Map<N>.
 //
 // Lines shorter than 8 points (lattice edges of 1 or 2 sites) are done by
 // one thread each in registers.  Twiddles come from the FP64 table
@@ -70,42 +75,108 @@ struct Line {
     static_assert(!ODD || M >= 8, "3 * 2^a and 5 * 2^a lengths need a >= 3");
 };
 
+// ------------------------------------------------------------------------
+// Wide mapping for N = R M (R = 3 or 5, M = 2^a >= 8).  The line is held
+// by T = M/8 threads, a power of two (warps hold whole lines), each with
+// the 8R points t + T m, m < 8R.  A radix-8 Stockham stage reads
+// x[j + (N/8) r] for butterfly j < N/8 = R T: thread t takes the R
+// butterflies j = t + T q (q < R), whose inputs are its own points
+// m = q + R r, and since Ns divides T they share one twiddle set.  The
+// power of two that radix 8 leaves over (2^B, B = log2 M mod 3) joins the
+// closing stage, of radix RC = 2^B R with Ns = M / 2^B: its butterfly
+// j < Ns reads and writes x[j + Ns r], and thread t takes j = t + T q
+// (q < 8 / 2^B), again its own points m = q + (8 / 2^B) r.  So every stage
+// works on registers, the radix-8 stages exchange through shared memory
+// once each, and the closing stage leaves the outputs in natural order on
+// the thread's points.  The closing DFT is the prime-factor (Good-Thomas)
+// form of 2^B R points: 2^B-point DFTs, then R-point DFTs, index maps
+// instead of twiddles (gcd(2^B, R) = 1).
+template <int N>
+struct Wide {
+    static constexpr int R = Line<N>::R, M = N / R, LOGM = log2c(M);
+    static constexpr int T = M / 8;                 // threads per line
+    static constexpr int V = 8 * R;                 // points per thread
+    static constexpr int B = LOGM % 3, RC = R << B; // closing radix 2^B R
+    static constexpr int S = (LOGM - B) / 3;        // radix-8 stages
+    static constexpr int NSC = M >> B;              // Ns of the closing stage
+    static constexpr int QC = 8 >> B;               // closing butterflies per thread
+};
+
+// thread mapping a pass uses for N-point lines: the wide one for
+// 3 * 2^a and 5 * 2^a, eight points per thread for 2^a
+template <int N>
+struct Map {
+    static constexpr bool WIDE = Line<N>::ODD;
+    static constexpr int T = WIDE ? Wide<N>::T : Line<N>::T;      // threads per line
+    static constexpr int V = WIDE ? Wide<N>::V : 8;               // register slots per thread
+    static constexpr int NV = WIDE ? Wide<N>::V : Line<N>::NV;    // points held (N < 8: N)
+    static constexpr int NH = WIDE ? Wide<N>::V / 2 : Line<N>::NH; // points of the first half
+};
+// threads per N-point line of that mapping, for host code
+__host__ __device__ constexpr int map_threads(int N) {
+    return (N % 3 == 0) ? N / 24 : (N % 5 == 0) ? N / 40 : (N >= 8 ? N / 8 : 1);
+}
+
+// Shared-memory layouts.  An address comes from at<KEY>(w, p) (line w,
+// point p), where KEY is log2 of Ns of the stage that writes the exchange;
+// the stage writes and the canonical read that follows use the same KEY,
+// so each exchange may have a layout of its own.  sync() is the barrier of
+// the exchanges.
+//
+// RowLayout keeps each line contiguous (lines of the lattice that are
+// contiguous in memory, threads t-fastest).  An 8-byte access of 16 lanes
+// (a half-warp) takes one shared-memory wavefront when its 16 words fall
+// in 16 different banks (word mod 16).  The canonical read (16 consecutive
+// points, or 8/T lines of T consecutive points) and the stage writes (points
+// 8j + r, or runs of Ns) need different pads; the pad of exchange KEY is
+//   word = p + c0 (p >> 3) + c1 (p >> 4) + c2 (p >> 6),
+// with (c0, c1, c2) = (1, 0, 0) after the first stage and 0 after the
+// others for lines of T <= 8 threads (line stride = T mod 2T, row_ld), and (0, 1, 0), (0, 2, 0)
+// for Ns = 2 or 4, (0, 0, 8) for Ns = 8, 0 beyond, for T >= 16.  These make
+// every exchange of every supported line (24 points and up) conflict-free
+// under that rule.  With T a power of two each shift term splits into a
+// per-thread part and a compile-time constant, so the pads cost no
+// per-access arithmetic.
+struct Pad { int c0, c1, c2; };
+__host__ __device__ constexpr Pad row_pad(int T, int KEY) {
+    return T <= 8 ? (KEY == 0 ? Pad{1, 0, 0} : Pad{0, 0, 0})
+                  : KEY == 0 ? Pad{0, 1, 0} : KEY <= 2 ? Pad{0, 2, 0} : KEY == 3 ? Pad{0, 0, 8} : Pad{0, 0, 0};
+}
+__host__ __device__ constexpr int pad_word(Pad c, int p) { return p + c.c0 * (p >> 3) + c.c1 * (p >> 4) + c.c2 * (p >> 6); }
+// elements per line of a RowLayout buffer, the line stride of every
+// exchange: the widest padded line of any key, and for lines of T <= 8
+// threads rounded up to T mod 2T, so that the 16/T lines a half-warp
+// touches fall in complementary banks
+__host__ __device__ constexpr int row_ld(int N) {
+    const int T = map_threads(N);
+    int ld = 0;
+    for (int k = 0; k <= 10; ++k) {
+        const int l = pad_word(row_pad(T, k), N - 1) + 1;
+        ld = l > ld ? l : ld;
+    }
+    return T >= 16 ? ld : ld + ((T - ld) % (2 * T) + 2 * T) % (2 * T);
+}
+
 template <int N>
 struct RowLayout {
-    static constexpr int ld = N + N / 16 + 1;
-    __device__ __forceinline__ int operator()(int w, int p) const { return w * ld + p + (p >> 4); }
+    static constexpr int T = Map<N>::T;
+    template <int KEY>
+    __device__ __forceinline__ int at(int w, int p) const {
+        return w * row_ld(N) + pad_word(row_pad(T, KEY), p);
+    }
     __device__ __forceinline__ void sync() const { __syncthreads(); }
 };
-// RowLayout whose exchanges synchronise only a group of whole warps holding
-// whole lines (named barrier `id` > 0 over `count` threads), so that the
-// groups of a CTA progress independently; id 0 synchronises the CTA
-template <int N>
-struct RowGroupLayout {
-    static constexpr int ld = N + N / 16 + 1;
-    int id, count;
-    __device__ __forceinline__ int operator()(int w, int p) const { return w * ld + p + (p >> 4); }
-    __device__ __forceinline__ void sync() const {
-        if (id == 0) __syncthreads();
-        else asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(count) : "memory");
-    }
-};
-// lines of N points per barrier group of RowGroupLayout: the fewest whole
-// lines that fill whole warps
-__host__ __device__ constexpr int row_group_lines(int N) {
-    int g = 1;
-    while (((N >= 8 ? N / 8 : 1) * g) % 32 != 0) g *= 2;
-    return g;
-}
-// 2^LOGW lines per tile, one pad row after every 8 points; the width is a
-// compile-time constant, so every exchange address folds into a constant
-// offset from the thread's base
+// 2^LOGW lines per tile, point-major (threads w-fastest, strided lines of
+// the lattice), one pad row after every 8 points, the same for every
+// exchange; the width is a compile-time constant, so every exchange
+// address folds into a constant offset from the thread's base
 template <int LOGW>
 struct ColLayoutT {
-    __device__ __forceinline__ int operator()(int w, int p) const { return ((p + (p >> 3)) << LOGW) + w; }
+    template <int KEY>
+    __device__ __forceinline__ int at(int w, int p) const { return ((p + (p >> 3)) << LOGW) + w; }
     __device__ __forceinline__ void sync() const { __syncthreads(); }
 };
 
-__host__ __device__ constexpr int row_ld(int N) { return N + N / 16 + 1; }
 // elements of a ColLayoutT tile of W lines of N points
 __host__ __device__ constexpr int col_elems(int N, int W) { return (N + N / 8) * W; }
 
@@ -192,14 +263,14 @@ __device__ __forceinline__ void twiddle8(C<T> (&v)[NL][8], int k, const C<T>* __
         for (int r = 1; r < 8; ++r) v[l][r] = cmul<T>(v[l][r], w[r]);
 }
 
-// read back the canonical points after an exchange
-template <typename T, int N, int NL, class Layout>
+// read back the canonical points after the exchange written with key KEY
+template <typename T, int N, int NL, int KEY, class Layout>
 __device__ __forceinline__ void read_canonical(C<T> (&v)[NL][8], const C<T>* __restrict__ sm, int region,
                                                const Layout& L, int w, int t) {
     constexpr int Tn = N / 8;
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
-        const int o = L(w, t + m * Tn);
+        const int o = L.template at<KEY>(w, t + m * Tn);
 #pragma unroll
         for (int l = 0; l < NL; ++l) v[l][m] = sm[l * region + o];
     }
@@ -240,7 +311,7 @@ __device__ __forceinline__ void dft5(C<T> (&x)[5]) {
 // place in shared memory -- butterfly j < M twiddles x[j + M r] by
 // exp(-+ 2 pi i j r / N) -- then the canonical read that ends the transform
 // in registers.  Thread t takes the butterflies j = t, t + T, ... below M.
-template <typename T, bool INV, int N, int NL, bool TAIL = true, class Layout>
+template <typename T, bool INV, int N, int NL, int KEY, bool TAIL = true, class Layout>
 __device__ __forceinline__ void odd_finish(C<T> (&v)[NL][8], C<T>* __restrict__ sm, int region,
                                            const Layout& L, int w, int t, const C<T>* __restrict__ tw) {
     constexpr int R = Line<N>::R, M = N / R, Tn = N / 8;
@@ -271,7 +342,7 @@ __device__ __forceinline__ void odd_finish(C<T> (&v)[NL][8], C<T>* __restrict__ 
             const C<T>(&wr)[R] = wq[q];
             int o[R];
 #pragma unroll
-            for (int r = 0; r < R; ++r) o[r] = L(w, j + r * M);
+            for (int r = 0; r < R; ++r) o[r] = L.template at<KEY>(w, j + r * M);
 #pragma unroll
             for (int l = 0; l < NL; ++l) {
                 C<T>* S = sm + l * region;
@@ -290,7 +361,7 @@ __device__ __forceinline__ void odd_finish(C<T> (&v)[NL][8], C<T>* __restrict__ 
         }
     }
     L.sync();
-    read_canonical<T, N, NL>(v, sm, region, L, w, t);
+    read_canonical<T, N, NL, KEY>(v, sm, region, L, w, t);
     if constexpr (TAIL) L.sync();
 }
 
@@ -310,20 +381,20 @@ struct Radix8Stages {
             const int base = ((t >> LOGNS) << (LOGNS + 3)) + k;
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
-                const int o = L(w, base + r * Ns);
+                const int o = L.template at<LOGNS>(w, base + r * Ns);
 #pragma unroll
                 for (int l = 0; l < NL; ++l) sm[l * region + o] = v[l][r];
             }
             if constexpr (LOGNS + 3 < LOGM) {
                 L.sync();
-                read_canonical<T, N, NL>(v, sm, region, L, w, t);
+                read_canonical<T, N, NL, LOGNS>(v, sm, region, L, w, t);
                 // the next stage writes shared memory again, unless it is
                 // the last one of a 2^a line (registers only); then only a
                 // caller that reuses the buffer (TAIL) needs the barrier
                 if constexpr (TAIL || LOGNS + 6 < LOGM || Line<N>::ODD) L.sync();
                 Radix8Stages<T, INV, N, LOGNS + 3, NL, HALF_OUT, Layout, TAIL>::run(v, sm, region, L, w, t, tw);
             } else {
-                odd_finish<T, INV, N, NL, TAIL>(v, sm, region, L, w, t, tw);
+                odd_finish<T, INV, N, NL, LOGNS, TAIL>(v, sm, region, L, w, t, tw);
             }
         } else {
 #pragma unroll
@@ -366,8 +437,8 @@ __device__ __forceinline__ void fft_lines(C<T> (&v)[NL][8], C<T>* __restrict__ s
                 for (int q = 0; q < 4; ++q) {
                     C<T> b[2] = {v[l][q], HALF_IN ? v[l][q] : v[l][q + 4]};
                     if (!HALF_IN) dft2<T, INV>(b);
-                    S[L(w, (t + q * Tn) * 2)] = b[0];
-                    S[L(w, (t + q * Tn) * 2 + 1)] = b[1];
+                    S[L.template at<0>(w, (t + q * Tn) * 2)] = b[0];
+                    S[L.template at<0>(w, (t + q * Tn) * 2 + 1)] = b[1];
                 }
             } else if constexpr (first == 2) {
                 // butterflies j = t + q T (q < 2) read x[j + 2T r] = v[q + 2r]
@@ -377,21 +448,21 @@ __device__ __forceinline__ void fft_lines(C<T> (&v)[NL][8], C<T>* __restrict__ s
                                  HALF_IN ? mk<T>(0, 0) : v[l][q + 6]};
                     dft4<T, INV>(b);
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) S[L(w, (t + q * Tn) * 4 + r)] = b[r];
+                    for (int r = 0; r < 4; ++r) S[L.template at<0>(w, (t + q * Tn) * 4 + r)] = b[r];
                 }
             } else {
                 if (HALF_IN) dft8_half_in<T, INV>(v[l]);
                 else dft8<T, INV>(v[l]);
 #pragma unroll
-                for (int r = 0; r < 8; ++r) S[L(w, t * 8 + r)] = v[l][r];
+                for (int r = 0; r < 8; ++r) S[L.template at<0>(w, t * 8 + r)] = v[l][r];
             }
         }
         if constexpr (L1 == LOGM) {
             // the first stage was the only power-of-two stage (N = 3 * 8, 5 * 8)
-            odd_finish<T, INV, N, NL, TAIL>(v, sm, region, L, w, t, tw);
+            odd_finish<T, INV, N, NL, 0, TAIL>(v, sm, region, L, w, t, tw);
         } else {
             L.sync();
-            read_canonical<T, N, NL>(v, sm, region, L, w, t);
+            read_canonical<T, N, NL, 0>(v, sm, region, L, w, t);
             if constexpr (TAIL || L1 + 3 < LOGM || Line<N>::ODD) L.sync();
             Radix8Stages<T, INV, N, L1, NL, HALF_OUT, Layout, TAIL>::run(v, sm, region, L, w, t, tw);
         }
@@ -404,6 +475,134 @@ __device__ __forceinline__ void fft_regs(C<T> (&v)[8], C<T>* __restrict__ sm, co
                                          const C<T>* __restrict__ tw) {
     C<T>(&vv)[1][8] = *reinterpret_cast<C<T>(*)[1][8]>(&v);
     fft_lines<T, INV, N, 1, HALF_IN, HALF_OUT, TAIL>(vv, sm, 0, L, w, t, tw);
+}
+
+__host__ __device__ constexpr int inv_mod(int a, int m) {
+    int r = 1;
+    while ((a * r) % m != 1 % m) ++r;
+    return r;
+}
+
+// DFT of RC = 2^B R points in place (prime-factor form: input n at
+// (R n1 + 2^B n2) mod RC, output k = e1 k1 + e2 k2 mod RC with
+// e1 = R (R^-1 mod 2^B), e2 = 2^B (2^-B mod R))
+template <typename T, bool INV, int R, int B>
+__device__ __forceinline__ void dft_pfa(C<T> (&x)[R << B]) {
+    if constexpr (B == 0) {
+        if constexpr (R == 3) dft3<T, INV>(x[0], x[1], x[2]);
+        else dft5<T, INV>(x);
+    } else {
+        constexpr int N1 = 1 << B, NC = R << B;
+        constexpr int e1 = R * inv_mod(R % N1, N1), e2 = N1 * inv_mod(N1 % R, R);
+        C<T> a[R][N1];
+#pragma unroll
+        for (int n2 = 0; n2 < R; ++n2) {
+#pragma unroll
+            for (int n1 = 0; n1 < N1; ++n1) a[n2][n1] = x[(R * n1 + N1 * n2) % NC];
+            if constexpr (B == 1) dft2<T, INV>(a[n2]);
+            else dft4<T, INV>(a[n2]);
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) {
+            C<T> b[R];
+#pragma unroll
+            for (int n2 = 0; n2 < R; ++n2) b[n2] = a[n2][k1];
+            if constexpr (R == 3) dft3<T, INV>(b[0], b[1], b[2]);
+            else dft5<T, INV>(b);
+#pragma unroll
+            for (int k2 = 0; k2 < R; ++k2) x[(e1 * k1 + e2 * k2) % NC] = b[k2];
+        }
+    }
+}
+
+// radix-8 stage S (Ns = 8^S) of the wide mapping and the ones after it
+template <typename T, bool INV, int N, int S, bool HALF_IN, bool TAIL, class Layout>
+__device__ __forceinline__ void wide_radix8(C<T> (&v)[Wide<N>::V], C<T>* __restrict__ sm, const Layout& L,
+                                            int w, int t, const C<T>* __restrict__ tw) {
+    constexpr int R = Wide<N>::R, Tn = Wide<N>::T, V = Wide<N>::V, LOGNS = 3 * S, Ns = 1 << LOGNS;
+    const int k = t & (Ns - 1);
+    C<T> u[R][8];
+#pragma unroll
+    for (int q = 0; q < R; ++q)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) u[q][r] = v[q + R * r];
+    if constexpr (S > 0) twiddle8<T, INV, LOGNS, R>(u, k, tw);
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        if (S == 0 && HALF_IN) dft8_half_in<T, INV>(u[q]);
+        else dft8<T, INV>(u[q]);
+        const int base = (((t + Tn * q) >> LOGNS) << (LOGNS + 3)) + k;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) sm[L.template at<LOGNS>(w, base + r * Ns)] = u[q][r];
+    }
+    L.sync();
+#pragma unroll
+    for (int m = 0; m < V; ++m) v[m] = sm[L.template at<LOGNS>(w, t + Tn * m)];
+    // the next radix-8 stage writes the buffer again; after the last one
+    // only a caller that reuses it (TAIL) needs the barrier
+    if constexpr (TAIL || S + 1 < Wide<N>::S) L.sync();
+    if constexpr (S + 1 < Wide<N>::S) wide_radix8<T, INV, N, S + 1, HALF_IN, TAIL>(v, sm, L, w, t, tw);
+}
+
+// In-place DFT of one N = R M line in the wide mapping: v[m] = x[t + T m],
+// m < 8R.  All threads of the CTA call it together.  HALF_IN: inputs
+// m >= 4R (n >= N/2) are zero.  Outputs the caller never reads are dead
+// code, so an inverse that keeps the first half needs no flag.  TAIL: see
+// fft_lines.
+template <typename T, bool INV, int N, bool HALF_IN, bool TAIL = true, class Layout>
+__device__ __forceinline__ void fft_wide(C<T> (&v)[Wide<N>::V], C<T>* __restrict__ sm, const Layout& L, int w,
+                                         int t, const C<T>* __restrict__ tw) {
+    using W = Wide<N>;
+    constexpr int R = W::R, B = W::B, RC = W::RC, QC = W::QC, Tn = W::T;
+    wide_radix8<T, INV, N, 0, HALF_IN, TAIL>(v, sm, L, w, t, tw);
+    // closing stage: butterfly j = t + T q twiddles x[j + Ns r] by
+    // exp(-+ 2 pi i j r / N), r < RC
+    constexpr int off = R == 3 ? 0 : kTwLen, step = (R == 3 ? kTwLen : kTw5Len) / N;
+#pragma unroll
+    for (int q = 0; q < QC; ++q) {
+        const int j = t + Tn * q;
+        C<T> wr[RC];
+        wr[0] = mk<T>(1, 0);
+        if (sizeof(T) == 4) {
+            // FP32: w^s (s < R) as powers of one table value, w^(g R + s) as
+            // w^(g R) (from the table) times w^s: at most three roundings
+            C<T> ws[R];
+            ws[0] = mk<T>(1, 0);
+            ws[1] = twiddle<T, INV>(tw, off + j * step);
+            ws[2] = cmul<T>(ws[1], ws[1]);
+            if constexpr (R == 5) {
+                ws[3] = cmul<T>(ws[2], ws[1]);
+                ws[4] = cmul<T>(ws[2], ws[2]);
+            }
+#pragma unroll
+            for (int s = 1; s < R; ++s) wr[s] = ws[s];
+#pragma unroll
+            for (int g = 1; g < (1 << B); ++g) {
+                const C<T> wg = twiddle<T, INV>(tw, off + j * g * R * step);
+                wr[g * R] = wg;
+#pragma unroll
+                for (int s = 1; s < R; ++s) wr[g * R + s] = cmul<T>(wg, ws[s]);
+            }
+        } else {
+#pragma unroll
+            for (int r = 1; r < RC; ++r) wr[r] = twiddle<T, INV>(tw, off + j * r * step);
+        }
+        C<T> x[RC];
+        x[0] = v[q];
+#pragma unroll
+        for (int r = 1; r < RC; ++r) x[r] = cmul<T>(v[q + QC * r], wr[r]);
+        dft_pfa<T, INV, R, B>(x);
+#pragma unroll
+        for (int r = 0; r < RC; ++r) v[q + QC * r] = x[r];
+    }
+}
+
+// one line in the mapping Map<N> chooses (v[m] = x[t + Map<N>::T m])
+template <typename T, bool INV, int N, bool HALF_IN, bool HALF_OUT, bool TAIL = true, class Layout>
+__device__ __forceinline__ void fft_line(C<T> (&v)[Map<N>::V], C<T>* __restrict__ sm, const Layout& L, int w,
+                                         int t, const C<T>* __restrict__ tw) {
+    if constexpr (Map<N>::WIDE) fft_wide<T, INV, N, HALF_IN, TAIL>(v, sm, L, w, t, tw);
+    else fft_regs<T, INV, N, HALF_IN, HALF_OUT, TAIL>(v, sm, L, w, t, tw);
 }
 
 }  // namespace dda

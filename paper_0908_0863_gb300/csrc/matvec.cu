@@ -8,13 +8,15 @@ namespace dda {
 template <typename T>
 bool tiles_ok(const Geometry& g, int logW_y, int logW_z, int logW_x) {
     const int elt = sizeof(C<T>);
-    const int ty = threads_of(g.Ly), tz = threads_of(g.Lz), tx = threads_of(g.Lx);
+    const int ty = threads_of(g.Ly), tz = threads_of(g.Lz);
     if (logW_y < 0 || logW_z < 0 || logW_x < 0) return false;
     if (logW_y > kMaxLogW || logW_z > kMaxLogR || logW_x > kMaxLogZ) return false;
     if ((1 << logW_y) * ty > kYThreads || 3ull * (1ull << logW_y) * col_elems(g.Ly, 1) * elt > 200 * 1024) return false;
     if ((1 << logW_z) * tz > p3_max_threads<T>() || 3ull * (1ull << logW_z) * row_ld(g.Lz) * elt > 200 * 1024)
         return false;
-    if ((1 << logW_x) * tx > kRowThreads || rows_smem_elems(g.Lx, 1 << logW_x) * elt > 200 * 1024) return false;
+    if (rows_groups(g.Lx, 1 << logW_x) * (1 << logW_x) * map_threads(g.Lx) > rows_max_threads(g.Lx) ||
+        rows_smem_elems(g.Lx, 1 << logW_x) * elt > 200 * 1024)
+        return false;
     return true;
 }
 
@@ -22,7 +24,7 @@ template <typename T>
 void configure_matvec(MatvecView<T>& mv) {
     const Geometry& g = mv.g;
     const int elt = sizeof(C<T>);
-    const int ty = threads_of(g.Ly), tz = threads_of(g.Lz), tx = threads_of(g.Lx);
+    const int ty = threads_of(g.Ly), tz = threads_of(g.Lz);
     // P1/P5: W adjacent columns (64-byte rows)
     int wy = floor_log2(64 / elt);
     while (wy > 0 && (1 << wy) * ty > kYThreads) --wy;

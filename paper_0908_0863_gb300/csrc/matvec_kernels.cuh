@@ -1,6 +1,6 @@
 // Kernels and per-length launchers of the pruned FFT matrix-vector product
 // y = A p of the DDA (OpenDDA Sec. 3).  Each of the translation units
-// mv_p1_*.cu, mv_p3_*.cu, mv_p5_*.cu and mv_rows.cu instantiates one pass for
+// mv_p1_*.cu, mv_p3_*.cu, mv_p5_*.cu and mv_rows_*.cu instantiates one pass for
 // every line length (and tile width) and exposes its dispatcher; matvec.cu
 // sequences the passes.
 //
@@ -67,8 +67,14 @@ template <typename T> __host__ __device__ constexpr int p3_max_threads() { retur
 // per CTA) may take, as log2
 constexpr int kMaxLogR = 6;
 constexpr int kMaxLogZ = 4;
-// P2/P4 keep eight points of one row per thread: up to 1024 threads per CTA
+// P2/P4 keep eight points of one row per thread: up to 1024 threads per CTA;
+// with the wide mapping of 3 * 2^a and 5 * 2^a rows (24 or 40 points per
+// thread) up to 256, which leaves the registers for them
 constexpr int kRowThreads = 1024;
+constexpr int kRowThreadsWide = 256;
+__host__ __device__ constexpr int rows_max_threads(int N) {
+    return (N % 3 == 0 || N % 5 == 0) ? kRowThreadsWide : kRowThreads;
+}
 
 // P1 and P5 keep the eight points, their gather indices and (P5) the
 // gathered entries of p in registers: at most 512 threads per CTA leave
@@ -156,46 +162,55 @@ __global__ void __launch_bounds__(kYThreads) k_p1(MatvecView<T> mv, const C<T>* 
 }
 
 // ------------------------------------------------------- P2 / P4 (rows)
-// One CTA takes the x lines of Wz = 2^LOGZ consecutive z planes at one
+// One tile takes the x lines of Wz = 2^LOGZ consecutive z planes at one
 // (component, y row): rows of K inputs in Ay (x fastest) and the same x
 // positions of Wz consecutive z in the columns of Bxy (z fastest).  Threads
 // run w-fastest (w = z offset, t = point slot), so each load or store of
-// the column side touches Wz consecutive z values of one x (64 bytes and
-// more), and the row side whole 32-byte sectors of Wz rows.
+// the column side touches Wz consecutive z values of one x (32 bytes and
+// more), and the row side whole 32-byte sectors of Wz rows.  A CTA holds
+// rows_groups(N, Wz) tiles of consecutive z (more than one only for the
+// wide mapping of 3 * 2^a and 5 * 2^a lines, whose few threads per line
+// would otherwise make CTAs of a warp or less), each with its own region
+// of shared memory.
 // Forward (P2): Ay rows -> transform -> Bxy.  Inverse (P4): Bxy ->
 // transform -> the first K outputs into Ay.  Grid: (z tiles, Ly, 3 nb).
+__host__ __device__ constexpr int rows_groups(int N, int Wz) {
+    return (N % 3 == 0 || N % 5 == 0) && Wz * map_threads(N) < 128 ? 128 / (Wz * map_threads(N)) : 1;
+}
+
 template <typename T, bool INV, int N, int LOGZ>
-__global__ void __launch_bounds__(kRowThreads) k_rows(MatvecView<T> mv) {
+__global__ void __launch_bounds__(rows_max_threads(N)) k_rows(MatvecView<T> mv) {
     const int c = blockIdx.z % 3, j = blockIdx.z / 3;      // component, batch slot
     if (rhs_done(mv, mv.b0 + j)) return;
     extern __shared__ unsigned char smem_raw[];
-    C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
-    constexpr int TL = Line<N>::T, nv = Line<N>::NV, Wz = 1 << LOGZ;
+    constexpr int TL = Map<N>::T, V = Map<N>::V, nv = Map<N>::NV, nh = Map<N>::NH, Wz = 1 << LOGZ;
+    constexpr int G = rows_groups(N, Wz);
     const Geometry& g = mv.g;
-    const int w = threadIdx.x & (Wz - 1), t = threadIdx.x >> LOGZ;
-    const int y = blockIdx.y, z = blockIdx.x * Wz + w;
+    const int w = threadIdx.x & (Wz - 1), t = (threadIdx.x >> LOGZ) % TL, gi = (threadIdx.x >> LOGZ) / TL;
+    C<T>* sm = reinterpret_cast<C<T>*>(smem_raw) + gi * col_elems(N, Wz);
+    const int y = blockIdx.y, z = (blockIdx.x * G + gi) * Wz + w;
     const bool ok = z < g.P;
     C<T>* row = mv.Ay + j * ay_elems(g) + ((c * g.P + (ok ? z : 0)) * g.Ly + y) * g.K;
     C<T>* col = mv.Bxy + j * bxy_elems(g) + (c * g.Ly + y) * g.Lx * g.Pb + (ok ? z : 0);
-    C<T> v[8];
+    C<T> v[V];
     if (!INV) {
 #pragma unroll
-        for (int m = 0; m < 8; ++m) {
+        for (int m = 0; m < V; ++m) {
             const int n = t + m * TL;
-            v[m] = (ok && m < Line<N>::NH && n < g.K) ? row[n] : mk<T>(0, 0);
+            v[m] = (ok && m < nh && n < g.K) ? row[n] : mk<T>(0, 0);
         }
-        fft_regs<T, false, N, true, false, false>(v, sm, ColLayoutT<LOGZ>{}, w, t, mv.tw);
+        fft_line<T, false, N, true, false, false>(v, sm, ColLayoutT<LOGZ>{}, w, t, mv.tw);
         if (ok) {
 #pragma unroll
             for (int m = 0; m < nv; ++m) col[(t + m * TL) * g.Pb] = v[m];
         }
     } else {
 #pragma unroll
-        for (int m = 0; m < 8; ++m) v[m] = (ok && m < nv) ? col[(t + m * TL) * g.Pb] : mk<T>(0, 0);
-        fft_regs<T, true, N, false, true, false>(v, sm, ColLayoutT<LOGZ>{}, w, t, mv.tw);
+        for (int m = 0; m < V; ++m) v[m] = (ok && m < nv) ? col[(t + m * TL) * g.Pb] : mk<T>(0, 0);
+        fft_line<T, true, N, false, true, false>(v, sm, ColLayoutT<LOGZ>{}, w, t, mv.tw);
         if (ok) {
 #pragma unroll
-            for (int m = 0; m < Line<N>::NH; ++m) {   // i < K <= N/2: first half only
+            for (int m = 0; m < nh; ++m) {   // i < K <= N/2: first half only
                 const int n = t + m * TL;
                 if (n < g.K) row[n] = v[m];
             }
@@ -414,20 +429,20 @@ int launch_p1(const MatvecView<T>& mv, const C<T>* p, cudaStream_t st) {
 }
 
 // shared memory of a P2/P4 CTA of Wz rows
-inline size_t rows_smem_elems(int N, int Wz) { return (size_t)col_elems(N, Wz); }
+inline size_t rows_smem_elems(int N, int Wz) { return (size_t)rows_groups(N, Wz) * col_elems(N, Wz); }
 
 template <typename T, bool INV, int N, int LOGZ>
 int launch_rows_w(const MatvecView<T>& mv, cudaStream_t st) {
     const Geometry& g = mv.g;
-    constexpr int Wz = 1 << LOGZ;
-    if constexpr (Wz * Line<N>::T > kRowThreads) {
+    constexpr int Wz = 1 << LOGZ, G = rows_groups(N, Wz), threads = G * Wz * Map<N>::T;
+    if constexpr (threads > rows_max_threads(N)) {
         return fail(DDA_ERR_ARG, "x pass tile wider than a CTA");
     } else {
         const size_t sm = rows_smem_elems(N, Wz) * sizeof(C<T>);
         static std::atomic<size_t> smem_set{0};
         if (int rc = set_smem((const void*)k_rows<T, INV, N, LOGZ>, sm, smem_set)) return rc;
-        const dim3 grid((unsigned)((g.P + Wz - 1) / Wz), g.Ly, 3 * mv.nb);
-        k_rows<T, INV, N, LOGZ><<<grid, Wz * Line<N>::T, sm, st>>>(mv);
+        const dim3 grid((unsigned)((g.P + G * Wz - 1) / (G * Wz)), g.Ly, 3 * mv.nb);
+        k_rows<T, INV, N, LOGZ><<<grid, threads, sm, st>>>(mv);
         DDA_LAUNCH_CHECK(INV ? "P4 x-inverse" : "P2 x-forward");
         return 0;
     }

@@ -1,0 +1,14 @@
+// Instantiations of the matvec passes P2 and P4 (x-forward, x-inverse) in
+// c128 for every line length and tile width, and their dispatcher.
+#include "matvec_kernels.cuh"
+
+namespace dda {
+
+template <typename T, bool INV> int pass_rows(const MatvecView<T>& mv, cudaStream_t st) {
+    DDA_LEN_SWITCH(mv.g.Lx, (launch_rows<T, INV, LN>(mv, st)))
+}
+
+template int pass_rows<double, false>(const MatvecView<double>&, cudaStream_t);
+template int pass_rows<double, true>(const MatvecView<double>&, cudaStream_t);
+
+}  // namespace dda

@@ -1,5 +1,5 @@
-// Instantiations of the matvec pass P2 and P4 (x-forward, x-inverse) for every line
-// length and tile width, and its dispatcher.
+// Instantiations of the matvec passes P2 and P4 (x-forward, x-inverse) in
+// c64 for every line length and tile width, and their dispatcher.
 #include "matvec_kernels.cuh"
 
 namespace dda {
@@ -8,8 +8,6 @@ template <typename T, bool INV> int pass_rows(const MatvecView<T>& mv, cudaStrea
     DDA_LEN_SWITCH(mv.g.Lx, (launch_rows<T, INV, LN>(mv, st)))
 }
 
-template int pass_rows<double, false>(const MatvecView<double>&, cudaStream_t);
-template int pass_rows<double, true>(const MatvecView<double>&, cudaStream_t);
 template int pass_rows<float, false>(const MatvecView<float>&, cudaStream_t);
 template int pass_rows<float, true>(const MatvecView<float>&, cudaStream_t);
 

@@ -205,6 +205,29 @@ def test_matvec_odd_radix_lengths_sampled_rows(dda, box, D):
     assert np.abs(y32 - ref).max() <= 5e-6 * scale
 
 
+ODD_LENGTHS = [24, 48, 96, 192, 384, 768, 40, 80, 160, 320, 640]
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+@pytest.mark.parametrize("L", ODD_LENGTHS)
+def test_matvec_every_odd_length(dda, L, axis):
+    # every 3 * 2^a and 5 * 2^a circulant length on each axis (an edge of L/2
+    # sites pads to L), the other two axes short and ragged: the wide thread
+    # mapping of those lines in each pass, every output against the direct sum
+    box = [3, 4, 5]
+    box[axis] = L // 2
+    case = random_case(tuple(box), seed=L + 7 * axis, fill=0.6)
+    with case.lattice() as lat:
+        assert lat.padded[axis] == L
+    p = synth.complex_normal(L + axis, (3, case.nd))
+    y_ref = odda.direct_matvec(case.coords, case.ainv, case.k, p)
+    y = _matvec(dda, case, p, np.complex128)
+    assert np.abs(y - y_ref).max() <= 1e-12 * np.abs(y_ref).max()
+    y_ref32 = odda.direct_matvec(case.coords, case.ainv, case.k, p.astype(np.complex64))
+    y32 = _matvec(dda, case, p, np.complex64)
+    assert np.abs(y32 - y_ref32).max() <= 2e-6 * np.abs(y_ref32).max()
+
+
 @pytest.mark.parametrize("box", [(512, 6, 5), (5, 512, 6), (6, 5, 512)])
 def test_matvec_longest_lines(dda, box):
     # a 512-site edge (the largest the library takes) gives 1024-point lines:
