@@ -662,14 +662,11 @@ int dda_site_ranks(const dda_ctx* c, uint32_t* rank, void* stream) {
 int dda_tensor_spectrum(const dda_ctx* c, void* out, int dtype, void* stream) {
     if (int rc = check_ctx(c)) return rc;
     if (int rc = check_dev(out, "dda_tensor_spectrum: out")) return rc;
-    const size_t ns = 6ull * c->g.Hz * c->g.Hy * c->g.Hx;
-    if (dtype == DDA_C128) {
-        DDA_CUDA_TRY(cudaMemcpyAsync(out, c->spec64, ns * sizeof(double2), cudaMemcpyDeviceToDevice, as_stream(stream)));
-    } else if (dtype == DDA_C64) {
-        DDA_CUDA_TRY(cudaMemcpyAsync(out, c->spec32, ns * sizeof(float2), cudaMemcpyDeviceToDevice, as_stream(stream)));
-    } else {
-        return fail(DDA_ERR_ARG, "dda_tensor_spectrum: unknown dtype");
-    }
+    if (dtype != DDA_C128 && dtype != DDA_C64) return fail(DDA_ERR_ARG, "dda_tensor_spectrum: unknown dtype");
+    const bool c128 = dtype == DDA_C128;
+    if (int rc = export_spectrum(c->g, c128 ? (const void*)c->spec64 : (const void*)c->spec32, out, c128,
+                                 as_stream(stream)))
+        return rc;
     return DDA_OK;
 }
 

@@ -77,6 +77,20 @@ struct Geometry {
     int cfields;          // fields per word
 };
 
+// lines of 3 * 2^a and 5 * 2^a points (the other supported lengths are 2^a)
+__host__ __device__ constexpr bool wide_len(int N) { return N % 3 == 0 || N % 5 == 0; }
+
+// Element of the half spectrum (my, mx, mz, component q): columns
+// [Hy][Hx], every z line contiguous.  For z lines of 2^a points the six
+// components of a point sit side by side ([Hz][6]: one 48-byte record per
+// point, read whole by the z-pass thread that holds all three components);
+// for 3 * 2^a and 5 * 2^a points, whose z pass gives each component its own
+// threads, each component's line is contiguous ([6][Hz]).
+__host__ __device__ __forceinline__ int64_t spec_index(const Geometry& g, int my, int mx, int mz, int q) {
+    const int64_t col = ((int64_t)my * g.Hx + mx) * 6 * g.Hz;
+    return col + (wide_len(g.Lz) ? (int64_t)q * g.Hz + mz : (int64_t)mz * 6 + q);
+}
+
 // circulant length of an n-point Toeplitz level: the smallest L >= 2n - 1
 // (and >= 2) of the form 2^a, 3 * 2^a or 5 * 2^a (a >= 3 for the last two;
 // Sec. 3: K'' = 2K - 1 + kf with kf chosen for a fast DFT)

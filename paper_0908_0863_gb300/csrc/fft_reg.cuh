@@ -112,7 +112,9 @@ struct Map {
     static constexpr int NV = WIDE ? Wide<N>::V : Line<N>::NV;    // points held (N < 8: N)
     static constexpr int NH = WIDE ? Wide<N>::V / 2 : Line<N>::NH; // points of the first half
 };
-// threads per N-point line of that mapping, for host code
+// threads per N-point line of the 8-point mapping, for host code
+__host__ __device__ constexpr int line_threads(int N) { return N >= 8 ? N / 8 : 1; }
+// threads per N-point line of the mapping Map<N>, for host code
 __host__ __device__ constexpr int map_threads(int N) {
     return (N % 3 == 0) ? N / 24 : (N % 5 == 0) ? N / 40 : (N >= 8 ? N / 8 : 1);
 }

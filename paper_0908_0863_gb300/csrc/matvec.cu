@@ -8,11 +8,11 @@ namespace dda {
 template <typename T>
 bool tiles_ok(const Geometry& g, int logW_y, int logW_z, int logW_x) {
     const int elt = sizeof(C<T>);
-    const int ty = threads_of(g.Ly), tz = threads_of(g.Lz);
+    const int ty = line_threads(g.Ly), tz = p3_col_threads(g.Lz);
     if (logW_y < 0 || logW_z < 0 || logW_x < 0) return false;
     if (logW_y > kMaxLogW || logW_z > kMaxLogR || logW_x > kMaxLogZ) return false;
     if ((1 << logW_y) * ty > kYThreads || 3ull * (1ull << logW_y) * col_elems(g.Ly, 1) * elt > 200 * 1024) return false;
-    if ((1 << logW_z) * tz > p3_max_threads<T>() || 3ull * (1ull << logW_z) * row_ld(g.Lz) * elt > 200 * 1024)
+    if ((1 << logW_z) * tz > p3_max_threads<T>(g.Lz) || 3ull * (1ull << logW_z) * row_ld(g.Lz) * elt > 200 * 1024)
         return false;
     if (rows_groups(g.Lx, 1 << logW_x) * (1 << logW_x) * map_threads(g.Lx) > rows_max_threads(g.Lx) ||
         rows_smem_elems(g.Lx, 1 << logW_x) * elt > 200 * 1024)
@@ -24,7 +24,7 @@ template <typename T>
 void configure_matvec(MatvecView<T>& mv) {
     const Geometry& g = mv.g;
     const int elt = sizeof(C<T>);
-    const int ty = threads_of(g.Ly), tz = threads_of(g.Lz);
+    const int ty = line_threads(g.Ly), tz = p3_col_threads(g.Lz);
     // P1/P5: W adjacent columns (64-byte rows)
     int wy = floor_log2(64 / elt);
     while (wy > 0 && (1 << wy) * ty > kYThreads) --wy;
@@ -34,7 +34,7 @@ void configure_matvec(MatvecView<T>& mv) {
     // exactly (small independent CTAs, many per SM)
     int wz = 0;
     while (wz < kMaxLogR && (((1 << wz) * tz) < 64 || (((1 << wz) * tz) & 31)) &&
-           (2 << wz) * tz <= p3_max_threads<T>() && (1 << wz) < g.Lx)
+           (2 << wz) * tz <= p3_max_threads<T>(g.Lz) && (1 << wz) < g.Lx)
         ++wz;
     // P2/P4: 32 bytes of each column of Bxy per CTA (4 complex64 or 2
     // complex128 consecutive z lines): whole sectors with small CTAs, which

@@ -11,7 +11,7 @@ struct MatvecView {
     Geometry g;
     TargetView tv;
     const C<T>* ainv;   // [nmat][3] alpha^-1
-    const C<T>* spec;   // [Hy][Hx][Hz][6], scaled by 1/(Lx Ly Lz)
+    const C<T>* spec;   // half spectrum (spec_index), scaled by 1/(Lx Ly Lz)
     const C<T>* tw;     // twiddle tables exp(-2 pi i m / 3072) then exp(-2 pi i m / 5120)
     C<T>* Ay;           // [slots][3][P][Ly][K] (x fastest)
     C<T>* Bxy;          // [slots][3][Ly][Lx][Pb] (z fastest, P of Pb used)

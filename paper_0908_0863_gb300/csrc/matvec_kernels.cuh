@@ -60,9 +60,16 @@
 namespace dda {
 
 
+
 // P3 keeps 3 x 8 complex values per thread: at most 512 threads per CTA for
-// complex64, 256 for complex128
-template <typename T> __host__ __device__ constexpr int p3_max_threads() { return sizeof(T) == 4 ? 512 : 256; }
+// complex64, 256 for complex128.  With the wide mapping (3 * 2^a, 5 * 2^a)
+// a thread keeps one component's 8R points (24 or 40): at most 256.
+template <typename T> __host__ __device__ constexpr int p3_max_threads(int N) {
+    return wide_len(N) ? 256 : (sizeof(T) == 4 ? 512 : 256);
+}
+// threads of one z column in P3: its three components share the T = N/8
+// threads of the 8-point mapping, or take 3 x M/8 in the wide one
+__host__ __device__ constexpr int p3_col_threads(int N) { return wide_len(N) ? 3 * map_threads(N) : map_threads(N); }
 // widest tiles the runtime widths of P3 (columns per CTA) and P2/P4 (z lines
 // per CTA) may take, as log2
 constexpr int kMaxLogR = 6;
@@ -72,14 +79,15 @@ constexpr int kMaxLogZ = 4;
 // thread) up to 256, which leaves the registers for them
 constexpr int kRowThreads = 1024;
 constexpr int kRowThreadsWide = 256;
-__host__ __device__ constexpr int rows_max_threads(int N) {
-    return (N % 3 == 0 || N % 5 == 0) ? kRowThreadsWide : kRowThreads;
-}
+__host__ __device__ constexpr int rows_max_threads(int N) { return wide_len(N) ? kRowThreadsWide : kRowThreads; }
 
 // P1 and P5 keep the eight points, their gather indices and (P5) the
 // gathered entries of p in registers: at most 512 threads per CTA leave
 // room for them (the complex64 P5 is held to two such CTAs per SM, which
-// measured faster than one with no register cap)
+// measured faster than one with no register cap).  They keep the 8-point
+// mapping for 3 * 2^a and 5 * 2^a lines too: with 8R points per thread the
+// gather's registers (P1 before, P5 beside the transform) cost more
+// occupancy than the wide mapping saves.
 constexpr int kYThreads = 512;
 
 // elements of one slot of the work arrays
@@ -175,7 +183,7 @@ __global__ void __launch_bounds__(kYThreads) k_p1(MatvecView<T> mv, const C<T>* 
 // Forward (P2): Ay rows -> transform -> Bxy.  Inverse (P4): Bxy ->
 // transform -> the first K outputs into Ay.  Grid: (z tiles, Ly, 3 nb).
 __host__ __device__ constexpr int rows_groups(int N, int Wz) {
-    return (N % 3 == 0 || N % 5 == 0) && Wz * map_threads(N) < 128 ? 128 / (Wz * map_threads(N)) : 1;
+    return wide_len(N) && Wz * map_threads(N) < 128 ? 128 / (Wz * map_threads(N)) : 1;
 }
 
 template <typename T, bool INV, int N, int LOGZ>
@@ -285,7 +293,7 @@ __device__ __forceinline__ void p3_product(const C<T>* __restrict__ line, bool o
 // product of Eqs. 6-8 with the signed mirror lookup of Sec. 3, z-inverse
 // DFTs, and the store of k < P.  Grid: (nb, Lx / R, Ly).
 template <typename T, int N>
-__global__ void __launch_bounds__(p3_max_threads<T>()) k_p3(MatvecView<T> mv) {
+__global__ void __launch_bounds__(p3_max_threads<T>(N)) k_p3(MatvecView<T> mv) {
     const int j = blockIdx.x;                                   // batch slot
     if (rhs_done(mv, mv.b0 + j)) return;
     extern __shared__ unsigned char smem_raw[];
@@ -325,6 +333,79 @@ __global__ void __launch_bounds__(p3_max_threads<T>()) k_p3(MatvecView<T> mv) {
                 const int n = t + m * TL;
                 if (n < g.P) col[c * comp + n] = v[c][m];
             }
+    }
+}
+
+// The wide mapping of P3 (N = 3 * 2^a, 5 * 2^a): each component of a column
+// is a line of T = M/8 threads of 8R points, so a CTA of R columns has
+// 3 T R threads (line l = c + 3 w, thread t).  After the forward DFTs every
+// line publishes its spectrum X_c at the canonical points; each thread then
+// reads X_0, X_1, X_2 at its own points and forms row c of the product,
+// y_c = f_c sum_d G_cd (f_d X_d): Table 1's sign of the (c, d) component
+// under the mirror flips is f_c f_d, with f = -1 on a mirrored axis.  Then
+// the inverse DFT and the store of k < P.  Grid: (nb, Lx / R, Ly).
+// (complex64: at most 128 registers, five 96-thread CTAs per SM, which
+// measured fastest among 128, 136 and no cap)
+template <typename T, int N>
+__global__ void __launch_bounds__(p3_max_threads<T>(N)) __maxnreg__(sizeof(T) == 4 ? 128 : 255) k_p3w(MatvecView<T> mv) {
+    const int j = blockIdx.x;                                   // batch slot
+    if (rhs_done(mv, mv.b0 + j)) return;
+    extern __shared__ unsigned char smem_raw[];
+    C<T>* sm = reinterpret_cast<C<T>*>(smem_raw);
+    constexpr int TL = Wide<N>::T, V = Wide<N>::V, nh = V / 2;
+    constexpr int KP = 10;                                      // key of the product exchange (no pad)
+    const Geometry& g = mv.g;
+    const int t = threadIdx.x % TL, l = threadIdx.x / TL;      // thread, line of the CTA
+    const int c = l % 3, w = l / 3;                             // component, column of the CTA
+    const int ix = (blockIdx.y << mv.logW_z) + w, jy = p3_row(blockIdx.z, g.Ly);
+    const bool ok = ix < g.Lx;
+    C<T>* col = mv.Bxy + j * bxy_elems(g) + c * (g.Ly * g.Lx * g.Pb) + (jy * g.Lx + (ok ? ix : 0)) * g.Pb;
+    C<T> v[V];
+#pragma unroll
+    for (int m = 0; m < V; ++m) {
+        const int n = t + m * TL;
+        v[m] = (ok && m < nh && n < g.P) ? col[n] : mk<T>(0, 0);
+    }
+    const RowLayout<N> L;
+    fft_wide<T, false, N, true>(v, sm, L, l, t, mv.tw);
+#pragma unroll
+    for (int m = 0; m < V; ++m) sm[L.template at<KP>(l, t + m * TL)] = v[m];
+    L.sync();
+    {
+        const int my = jy <= g.Ly / 2 ? jy : g.Ly - jy, fy = jy > g.Ly / 2;
+        const int mx = ix <= g.Lx / 2 ? ix : g.Lx - ix, fx = ix > g.Lx / 2;
+        // the column's six component lines ([6][Hz]); row c of the symmetric
+        // 3 x 3 block (xx, xy, xz, yy, yz, zz)
+        const int q0 = c == 0 ? 0 : (c == 1 ? 1 : 2), q1 = c == 0 ? 1 : (c == 1 ? 3 : 4),
+                  q2 = c == 0 ? 2 : (c == 1 ? 4 : 5);
+        const C<T>* line = mv.spec + ((my * g.Hx + (ok ? mx : 0)) * 6) * g.Hz;
+        const C<T>*G0l = line + q0 * g.Hz, *G1l = line + q1 * g.Hz, *G2l = line + q2 * g.Hz;
+        const int fc = c == 0 ? fx : (c == 1 ? fy : 0);   // z: per point below
+#pragma unroll
+        for (int m = 0; m < V; ++m) {
+            const int n = t + m * TL;
+            const int mz = n <= N / 2 ? n : N - n, fz = n > N / 2;
+            const C<T> G0 = ok ? __ldg(G0l + mz) : mk<T>(0, 0), G1 = ok ? __ldg(G1l + mz) : mk<T>(0, 0),
+                       G2 = ok ? __ldg(G2l + mz) : mk<T>(0, 0);
+            C<T> a = sm[L.template at<KP>(3 * w, n)], b = sm[L.template at<KP>(3 * w + 1, n)],
+                 d = sm[L.template at<KP>(3 * w + 2, n)];
+            if (fx) a = mk<T>(-a.x, -a.y);
+            if (fy) b = mk<T>(-b.x, -b.y);
+            if (fz) d = mk<T>(-d.x, -d.y);
+            C<T> y = cfma<T>(G2, d, cfma<T>(G1, b, cmul<T>(G0, a)));
+            if (fc ^ (c == 2 ? fz : 0)) y = mk<T>(-y.x, -y.y);
+            v[m] = y;
+        }
+    }
+    L.sync();   // the inverse's first stage writes the buffer
+    // nothing reuses the exchange buffers after the inverse
+    fft_wide<T, true, N, false, false>(v, sm, L, l, t, mv.tw);
+    if (ok) {
+#pragma unroll
+        for (int m = 0; m < nh; ++m) {   // z < P <= N/2: first half only
+            const int n = t + m * TL;
+            if (n < g.P) col[n] = v[m];
+        }
     }
 }
 
@@ -396,9 +477,6 @@ __global__ void __launch_bounds__(kYThreads, sizeof(T) == 4 ? 2 : 1) k_p5(Matvec
     }
 }
 
-// threads per line of N points
-inline int threads_of(int N) { return N >= 8 ? N / 8 : 1; }
-
 // largest power of two <= n (n >= 1), as its log
 inline int floor_log2(int n) { int l = 0; while ((2 << l) <= n) ++l; return l; }
 
@@ -466,9 +544,14 @@ int launch_p3(const MatvecView<T>& mv, cudaStream_t st) {
     const int R = 1 << mv.logW_z;
     const size_t sm = 3 * (size_t)R * row_ld(N) * sizeof(C<T>);
     static std::atomic<size_t> smem_set{0};
-    if (int rc = set_smem((const void*)k_p3<T, N>, sm, smem_set)) return rc;
     const dim3 grid(mv.nb, (g.Lx + R - 1) / R, g.Ly);
-    k_p3<T, N><<<grid, R * Line<N>::T, sm, st>>>(mv);
+    if constexpr (Map<N>::WIDE) {
+        if (int rc = set_smem((const void*)k_p3w<T, N>, sm, smem_set)) return rc;
+        k_p3w<T, N><<<grid, R * p3_col_threads(N), sm, st>>>(mv);
+    } else {
+        if (int rc = set_smem((const void*)k_p3<T, N>, sm, smem_set)) return rc;
+        k_p3<T, N><<<grid, R * p3_col_threads(N), sm, st>>>(mv);
+    }
     DDA_LAUNCH_CHECK("P3 z-forward, spectrum product, z-inverse");
     return 0;
 }

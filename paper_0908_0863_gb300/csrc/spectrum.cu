@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(512) k_tensor_x(Geometry g, int logW, const do
 // strided lines along y (axis 1) or z (axis 2) on arrays whose rows are Hx
 // long.  in: [6][n_outer][n_line][Hx] slices -> out: [6][n_outer][H][Hx]
 // (y pass: outer = P, line = J -> Hy; z pass: the line is the outermost
-// index of [6][P][Hy][Hx] -> [Hy][Hx][Hz][6], components innermost).
+// index of [6][P][Hy][Hx] -> the z-line layout of spec_index).
 template <int AXIS>
 __global__ void __launch_bounds__(512) k_tensor_col(Geometry g, int logW, const double2* __restrict__ tw,
                                                     const double2* __restrict__ in, double2* __restrict__ out,
@@ -150,10 +150,9 @@ __global__ void __launch_bounds__(512) k_tensor_col(Geometry g, int logW, const 
         if (AXIS == 1) {
             out[out_base + n * out_step + x] = v;
         } else {
-            // final spectrum: every z line contiguous and the six
-            // components of a point side by side, [Hy][Hx][Hz][6], so the z
-            // pass reads a column's line in one stream with vector loads
-            const int64_t o = (((int64_t)outer * g.Hx + x) * g.Hz + n) * 6 + m;
+            // final spectrum: every z line contiguous (spec_index), so the z
+            // pass reads a column's line in one stream
+            const int64_t o = spec_index(g, outer, x, n, m);
             out[o] = v;
             if (out32) out32[o] = make_float2((float)v.x, (float)v.y);
         }
@@ -228,6 +227,33 @@ int build_spectrum(const Geometry& g, double k, const double2* tw, double2* s0, 
         k_tensor_col<2><<<grid, W * g.Lz / kV, sm, st>>>(g, logW, tw, s0, spec64, scale, spec32);
         DDA_LAUNCH_CHECK("tensor z DFT");
     }
+    return 0;
+}
+
+// the spectrum in the exported order [Hy][Hx][Hz][6] from the stored one
+template <typename T>
+__global__ void __launch_bounds__(256) k_spec_export(Geometry g, const C<T>* __restrict__ in, C<T>* __restrict__ out) {
+    const int64_t n = 6LL * g.Hz * g.Hy * g.Hx;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int q = (int)(e % 6);
+        const int64_t r = e / 6;
+        const int mz = (int)(r % g.Hz);
+        const int64_t col = r / g.Hz;
+        out[e] = in[spec_index(g, (int)(col / g.Hx), (int)(col % g.Hx), mz, q)];
+    }
+}
+
+int export_spectrum(const Geometry& g, const void* in, void* out, bool c128, cudaStream_t st) {
+    const size_t ns = 6ull * g.Hz * g.Hy * g.Hx;
+    if (!wide_len(g.Lz)) {   // stored in the exported order
+        DDA_CUDA_TRY(cudaMemcpyAsync(out, in, ns * (c128 ? sizeof(double2) : sizeof(float2)),
+                                     cudaMemcpyDeviceToDevice, st));
+        return 0;
+    }
+    const unsigned blocks = (unsigned)std::min<size_t>((ns + 255) / 256, 152 * 16);
+    if (c128) k_spec_export<double><<<blocks, 256, 0, st>>>(g, static_cast<const double2*>(in), static_cast<double2*>(out));
+    else k_spec_export<float><<<blocks, 256, 0, st>>>(g, static_cast<const float2*>(in), static_cast<float2*>(out));
+    DDA_LAUNCH_CHECK("spectrum export");
     return 0;
 }
 
