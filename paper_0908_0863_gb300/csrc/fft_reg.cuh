@@ -78,28 +78,25 @@ struct Line {
 // ------------------------------------------------------------------------
 // Wide mapping for N = R M (R = 3 or 5, M = 2^a >= 8).  The line is held
 // by T = M/8 threads, a power of two (warps hold whole lines), each with
-// the 8R points t + T m, m < 8R.  A radix-8 Stockham stage reads
-// x[j + (N/8) r] for butterfly j < N/8 = R T: thread t takes the R
-// butterflies j = t + T q (q < R), whose inputs are its own points
-// m = q + R r, and since Ns divides T they share one twiddle set.  The
-// power of two that radix 8 leaves over (2^B, B = log2 M mod 3) joins the
-// closing stage, of radix RC = 2^B R with Ns = M / 2^B: its butterfly
-// j < Ns reads and writes x[j + Ns r], and thread t takes j = t + T q
-// (q < 8 / 2^B), again its own points m = q + (8 / 2^B) r.  So every stage
-// works on registers, the radix-8 stages exchange through shared memory
-// once each, and the closing stage leaves the outputs in natural order on
-// the thread's points.  The closing DFT is the prime-factor (Good-Thomas)
-// form of 2^B R points: 2^B-point DFTs, then R-point DFTs, index maps
-// instead of twiddles (gcd(2^B, R) = 1).
+// the V = 8R points t + T m, m < V.  A Stockham stage of radix r reads
+// x[j + (N/r) s] for butterfly j < N/r; when r divides V, N/r is a multiple
+// of T and thread t takes the V/r butterflies j = t + T q, whose inputs
+// are its own points m = q + (V/r) s.  So the transform is: one radix-V
+// stage (each thread one V-point DFT of its own points, the prime-factor
+// form 8 x R), then the power-of-two factor T in radix-8 stages and one
+// radix-2 or 4 stage, every stage on the thread's registers, with one
+// shared-memory exchange between two stages; the last stage leaves the
+// outputs in natural order on the thread's points.  Lines of 96, 160, 192
+// and 320 points need one exchange per transform, 384, 640 and 768 two.
 template <int N>
 struct Wide {
-    static constexpr int R = Line<N>::R, M = N / R, LOGM = log2c(M);
+    static constexpr int R = Line<N>::R, M = N / R;
     static constexpr int T = M / 8;                 // threads per line
-    static constexpr int V = 8 * R;                 // points per thread
-    static constexpr int B = LOGM % 3, RC = R << B; // closing radix 2^B R
-    static constexpr int S = (LOGM - B) / 3;        // radix-8 stages
-    static constexpr int NSC = M >> B;              // Ns of the closing stage
-    static constexpr int QC = 8 >> B;               // closing butterflies per thread
+    static constexpr int V = 8 * R;                 // points per thread, the first radix
+    static constexpr int LOGT = log2c(T);
+    static constexpr int NSTAGES = (LOGT + 2) / 3;  // power-of-two stages after the first
+    // radix of power-of-two stage i (radix 8, the remainder 2 or 4 last)
+    __host__ __device__ static constexpr int radix(int i) { return (i < LOGT / 3) ? 8 : 1 << (LOGT % 3); }
 };
 
 // thread mapping a pass uses for N-point lines: the wide one for
@@ -485,9 +482,10 @@ __host__ __device__ constexpr int inv_mod(int a, int m) {
     return r;
 }
 
-// DFT of RC = 2^B R points in place (prime-factor form: input n at
-// (R n1 + 2^B n2) mod RC, output k = e1 k1 + e2 k2 mod RC with
-// e1 = R (R^-1 mod 2^B), e2 = 2^B (2^-B mod R))
+// DFT of NC = 2^B R points in place (prime-factor form, gcd(2^B, R) = 1:
+// input n at (R n1 + 2^B n2) mod NC, output k = e1 k1 + e2 k2 mod NC with
+// e1 = R (R^-1 mod 2^B), e2 = 2^B (2^-B mod R); 2^B-point DFTs, then
+// R-point DFTs, no twiddles)
 template <typename T, bool INV, int R, int B>
 __device__ __forceinline__ void dft_pfa(C<T> (&x)[R << B]) {
     if constexpr (B == 0) {
@@ -502,7 +500,8 @@ __device__ __forceinline__ void dft_pfa(C<T> (&x)[R << B]) {
 #pragma unroll
             for (int n1 = 0; n1 < N1; ++n1) a[n2][n1] = x[(R * n1 + N1 * n2) % NC];
             if constexpr (B == 1) dft2<T, INV>(a[n2]);
-            else dft4<T, INV>(a[n2]);
+            else if constexpr (B == 2) dft4<T, INV>(a[n2]);
+            else dft8<T, INV>(a[n2]);
         }
 #pragma unroll
         for (int k1 = 0; k1 < N1; ++k1) {
@@ -517,85 +516,151 @@ __device__ __forceinline__ void dft_pfa(C<T> (&x)[R << B]) {
     }
 }
 
-// radix-8 stage S (Ns = 8^S) of the wide mapping and the ones after it
-template <typename T, bool INV, int N, int S, bool HALF_IN, bool TAIL, class Layout>
-__device__ __forceinline__ void wide_radix8(C<T> (&v)[Wide<N>::V], C<T>* __restrict__ sm, const Layout& L,
-                                            int w, int t, const C<T>* __restrict__ tw) {
-    constexpr int R = Wide<N>::R, Tn = Wide<N>::T, V = Wide<N>::V, LOGNS = 3 * S, Ns = 1 << LOGNS;
-    const int k = t & (Ns - 1);
-    C<T> u[R][8];
+// cos(2 pi n / V) for V = 24 or 40, from the first-quadrant values
+// cos(2 pi a / V), a <= V/4, and the symmetries of the cosine
+template <int V>
+__host__ __device__ constexpr double cos_v(int n) {
+    constexpr double q24[7] = {1.0, 0.96592582628906828675, 0.86602540378443864676, 0.70710678118654752440,
+                               0.5, 0.25881904510252076235, 0.0};
+    constexpr double q40[11] = {1.0, 0.98768834059513772620, 0.95105651629515357212, 0.89100652418836786236,
+                                0.80901699437494742410, 0.70710678118654752440, 0.58778525229247312917,
+                                0.45399049973954679156, 0.30901699437494742410, 0.15643446504023086901, 0.0};
+    n %= V;
+    if (n < 0) n += V;
+    if (n > V / 2) n = V - n;
+    const double sg = n > V / 4 ? -1.0 : 1.0;
+    const int a = n > V / 4 ? V / 2 - n : n;
+    return sg * (V == 24 ? q24[a] : q40[a]);
+}
+// exp(-+ 2 pi i n / V): forward -, inverse +
+template <typename T, bool INV, int V>
+__device__ __forceinline__ C<T> root_v(int n) {
+    const double c = cos_v<V>(n), s = cos_v<V>(n - V / 4);   // sin = cos(. - pi/2)
+    return mk<T>((T)c, INV ? (T)s : (T)-s);
+}
+
+// The first stage of the wide mapping: the V = 8R-point DFT of the
+// thread's own points.  With HALF_IN (inputs V/2.. zero): one radix-2
+// decimation-in-frequency layer, a = x and b = x W_V^n for n < 4R, then
+// 4R-point DFTs of a (even outputs) and b (odd outputs).
+template <typename T, bool INV, int R, bool HALF_IN>
+__device__ __forceinline__ void wide_first(C<T> (&v)[8 * R]) {
+    constexpr int V = 8 * R, H = 4 * R;
+    if constexpr (HALF_IN) {
+        C<T> a[H], b[H];
 #pragma unroll
-    for (int q = 0; q < R; ++q)
+        for (int n = 0; n < H; ++n) {
+            a[n] = v[n];
+            b[n] = n == 0 ? v[n] : cmul<T>(v[n], root_v<T, INV, V>(n));
+        }
+        dft_pfa<T, INV, R, 2>(a);
+        dft_pfa<T, INV, R, 2>(b);
 #pragma unroll
-        for (int r = 0; r < 8; ++r) u[q][r] = v[q + R * r];
-    if constexpr (S > 0) twiddle8<T, INV, LOGNS, R>(u, k, tw);
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-        if (S == 0 && HALF_IN) dft8_half_in<T, INV>(u[q]);
-        else dft8<T, INV>(u[q]);
-        const int base = (((t + Tn * q) >> LOGNS) << (LOGNS + 3)) + k;
-#pragma unroll
-        for (int r = 0; r < 8; ++r) sm[L.template at<LOGNS>(w, base + r * Ns)] = u[q][r];
+        for (int k = 0; k < H; ++k) {
+            v[2 * k] = a[k];
+            v[2 * k + 1] = b[k];
+        }
+    } else {
+        dft_pfa<T, INV, R, 3>(v);
     }
-    L.sync();
+}
+
+// power-of-two stage I (radix RDX = Wide<N>::radix(I), Ns = V RDX_0 ...) of
+// the wide mapping and the ones after it.  On entry the registers hold the
+// canonical points after the exchange; butterfly q (j = t + T q) reads
+// v[q + (V/RDX) r] and twiddles it by exp(-+ 2 pi i (j mod Ns) r / (RDX Ns)).
+template <typename T, bool INV, int N, int I, int NS, bool TAIL, class Layout>
+__device__ __forceinline__ void wide_stages(C<T> (&v)[Wide<N>::V], C<T>* __restrict__ sm, const Layout& L, int w,
+                                            int t, const C<T>* __restrict__ tw) {
+    using W = Wide<N>;
+    constexpr int R = W::R, Tn = W::T, V = W::V, RDX = W::radix(I), NQ = V / RDX;
+    constexpr int off = R == 3 ? 0 : kTwLen, TWN = R == 3 ? kTwLen : kTw5Len;
+    constexpr int step = TWN / (RDX * NS);   // table entries per unit of k r
+    constexpr bool LAST = I + 1 == W::NSTAGES;
+    // The last stage has Ns = N / RDX > j, so k = t + T q and its twiddles
+    // factor as exp(-+ 2 pi i t r / N) exp(-+ 2 pi i q r / V): the first
+    // from the table once per thread, the second a compile-time constant.
+    // The other stages take k = j mod Ns from the table per butterfly.
+    // FP32 forms powers of one table value (a few ulp, far below the FP32
+    // transform's own error); FP64 reads every power from the table.
+    C<T> wt[RDX];
+    if constexpr (LAST) {
+        wt[0] = mk<T>(1, 0);
+        if (sizeof(T) == 4) {
+            wt[1] = twiddle<T, INV>(tw, off + t * step);
 #pragma unroll
-    for (int m = 0; m < V; ++m) v[m] = sm[L.template at<LOGNS>(w, t + Tn * m)];
-    // the next radix-8 stage writes the buffer again; after the last one
-    // only a caller that reuses it (TAIL) needs the barrier
-    if constexpr (TAIL || S + 1 < Wide<N>::S) L.sync();
-    if constexpr (S + 1 < Wide<N>::S) wide_radix8<T, INV, N, S + 1, HALF_IN, TAIL>(v, sm, L, w, t, tw);
+            for (int r = 2; r < RDX; ++r) wt[r] = (r & 1) ? cmul<T>(wt[r - 1], wt[1]) : cmul<T>(wt[r / 2], wt[r / 2]);
+        } else {
+#pragma unroll
+            for (int r = 1; r < RDX; ++r) wt[r] = twiddle<T, INV>(tw, off + t * r * step);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        C<T> x[RDX], wr[RDX];
+        wr[0] = mk<T>(1, 0);
+        if constexpr (LAST) {
+#pragma unroll
+            for (int r = 1; r < RDX; ++r) wr[r] = q == 0 ? wt[r] : cmul<T>(wt[r], root_v<T, INV, V>(q * r));
+        } else {
+            const int k = (t + Tn * q) % NS;
+            if (sizeof(T) == 4) {
+                if constexpr (RDX > 1) wr[1] = twiddle<T, INV>(tw, off + k * step);
+#pragma unroll
+                for (int r = 2; r < RDX; ++r)
+                    wr[r] = (r & 1) ? cmul<T>(wr[r - 1], wr[1]) : cmul<T>(wr[r / 2], wr[r / 2]);
+            } else {
+#pragma unroll
+                for (int r = 1; r < RDX; ++r) wr[r] = twiddle<T, INV>(tw, off + k * r * step);
+            }
+        }
+        x[0] = v[q];
+#pragma unroll
+        for (int r = 1; r < RDX; ++r) x[r] = cmul<T>(v[q + NQ * r], wr[r]);
+        if constexpr (RDX == 2) dft2<T, INV>(x);
+        else if constexpr (RDX == 4) dft4<T, INV>(x);
+        else dft8<T, INV>(x);
+#pragma unroll
+        for (int r = 0; r < RDX; ++r) v[q + NQ * r] = x[r];
+    }
+    if constexpr (!LAST) {
+        // exchange: butterfly j's output r goes to (j / Ns) Ns RDX + j mod Ns + r Ns
+        constexpr int KEY = 3;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int j = t + Tn * q;
+            const int base = (j / NS) * NS * RDX + j % NS;
+#pragma unroll
+            for (int r = 0; r < RDX; ++r) sm[L.template at<KEY>(w, base + r * NS)] = v[q + NQ * r];
+        }
+        L.sync();
+#pragma unroll
+        for (int m = 0; m < V; ++m) v[m] = sm[L.template at<KEY>(w, t + Tn * m)];
+        if constexpr (TAIL || I + 2 < W::NSTAGES) L.sync();
+        wide_stages<T, INV, N, I + 1, NS * RDX, TAIL>(v, sm, L, w, t, tw);
+    }
 }
 
 // In-place DFT of one N = R M line in the wide mapping: v[m] = x[t + T m],
 // m < 8R.  All threads of the CTA call it together.  HALF_IN: inputs
 // m >= 4R (n >= N/2) are zero.  Outputs the caller never reads are dead
-// code, so an inverse that keeps the first half needs no flag.  TAIL: see
-// fft_lines.
+// code, so an inverse that keeps the first half needs no flag.  TAIL: the
+// caller reuses the shared buffer afterwards (see fft_lines).
 template <typename T, bool INV, int N, bool HALF_IN, bool TAIL = true, class Layout>
 __device__ __forceinline__ void fft_wide(C<T> (&v)[Wide<N>::V], C<T>* __restrict__ sm, const Layout& L, int w,
                                          int t, const C<T>* __restrict__ tw) {
     using W = Wide<N>;
-    constexpr int R = W::R, B = W::B, RC = W::RC, QC = W::QC, Tn = W::T;
-    wide_radix8<T, INV, N, 0, HALF_IN, TAIL>(v, sm, L, w, t, tw);
-    // closing stage: butterfly j = t + T q twiddles x[j + Ns r] by
-    // exp(-+ 2 pi i j r / N), r < RC
-    constexpr int off = R == 3 ? 0 : kTwLen, step = (R == 3 ? kTwLen : kTw5Len) / N;
+    constexpr int Tn = W::T, V = W::V;
+    wide_first<T, INV, W::R, HALF_IN>(v);
+    if constexpr (W::NSTAGES > 0) {
+        // exchange: the first stage's output r of thread t goes to t V + r
 #pragma unroll
-    for (int q = 0; q < QC; ++q) {
-        const int j = t + Tn * q;
-        C<T> wr[RC];
-        wr[0] = mk<T>(1, 0);
-        if (sizeof(T) == 4) {
-            // FP32: w^s (s < R) as powers of one table value, w^(g R + s) as
-            // w^(g R) (from the table) times w^s: at most three roundings
-            C<T> ws[R];
-            ws[0] = mk<T>(1, 0);
-            ws[1] = twiddle<T, INV>(tw, off + j * step);
-            ws[2] = cmul<T>(ws[1], ws[1]);
-            if constexpr (R == 5) {
-                ws[3] = cmul<T>(ws[2], ws[1]);
-                ws[4] = cmul<T>(ws[2], ws[2]);
-            }
+        for (int r = 0; r < V; ++r) sm[L.template at<0>(w, t * V + r)] = v[r];
+        L.sync();
 #pragma unroll
-            for (int s = 1; s < R; ++s) wr[s] = ws[s];
-#pragma unroll
-            for (int g = 1; g < (1 << B); ++g) {
-                const C<T> wg = twiddle<T, INV>(tw, off + j * g * R * step);
-                wr[g * R] = wg;
-#pragma unroll
-                for (int s = 1; s < R; ++s) wr[g * R + s] = cmul<T>(wg, ws[s]);
-            }
-        } else {
-#pragma unroll
-            for (int r = 1; r < RC; ++r) wr[r] = twiddle<T, INV>(tw, off + j * r * step);
-        }
-        C<T> x[RC];
-        x[0] = v[q];
-#pragma unroll
-        for (int r = 1; r < RC; ++r) x[r] = cmul<T>(v[q + QC * r], wr[r]);
-        dft_pfa<T, INV, R, B>(x);
-#pragma unroll
-        for (int r = 0; r < RC; ++r) v[q + QC * r] = x[r];
+        for (int m = 0; m < V; ++m) v[m] = sm[L.template at<0>(w, t + Tn * m)];
+        if constexpr (TAIL || W::NSTAGES > 1) L.sync();
+        wide_stages<T, INV, N, 0, V, TAIL>(v, sm, L, w, t, tw);
     }
 }
 

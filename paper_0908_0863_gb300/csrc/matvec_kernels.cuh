@@ -339,13 +339,17 @@ __global__ void __launch_bounds__(p3_max_threads<T>(N)) k_p3(MatvecView<T> mv) {
 // The wide mapping of P3 (N = 3 * 2^a, 5 * 2^a): each component of a column
 // is a line of T = M/8 threads of 8R points, so a CTA of R columns has
 // 3 T R threads (line l = c + 3 w, thread t).  After the forward DFTs every
-// line publishes its spectrum X_c at the canonical points; each thread then
-// reads X_0, X_1, X_2 at its own points and forms row c of the product,
-// y_c = f_c sum_d G_cd (f_d X_d): Table 1's sign of the (c, d) component
-// under the mirror flips is f_c f_d, with f = -1 on a mirrored axis.  Then
-// the inverse DFT and the store of k < P.  Grid: (nb, Lx / R, Ly).
+// line publishes its spectrum X_c in shared memory.  For the product the
+// 3 T threads of a column take the mirror pairs (mz, N - mz), mz <= N/2,
+// which share the spectrum entries of Eqs. 6-8: thread u reads the six
+// components at mz once (six coalesced loads from the column's [6][Hz]
+// lines), forms y = G X at both points and writes y back in place.  Table
+// 1's sign of the (c, d) component under the mirror flips is f_c f_d, with
+// f = -1 on a mirrored axis, so y_c = f_c sum_d G_cd (f_d X_d).  Then every
+// thread reads its own line back, does the inverse DFT and stores k < P.
+// Grid: (nb, Lx / R, Ly).
 // (complex64: at most 128 registers, five 96-thread CTAs per SM, which
-// measured fastest among 128, 136 and no cap)
+// measured fastest among 128, 136, 144, 160 and no cap)
 template <typename T, int N>
 __global__ void __launch_bounds__(p3_max_threads<T>(N)) __maxnreg__(sizeof(T) == 4 ? 128 : 255) k_p3w(MatvecView<T> mv) {
     const int j = blockIdx.x;                                   // batch slot
@@ -374,30 +378,44 @@ __global__ void __launch_bounds__(p3_max_threads<T>(N)) __maxnreg__(sizeof(T) ==
     {
         const int my = jy <= g.Ly / 2 ? jy : g.Ly - jy, fy = jy > g.Ly / 2;
         const int mx = ix <= g.Lx / 2 ? ix : g.Lx - ix, fx = ix > g.Lx / 2;
-        // the column's six component lines ([6][Hz]); row c of the symmetric
-        // 3 x 3 block (xx, xy, xz, yy, yz, zz)
-        const int q0 = c == 0 ? 0 : (c == 1 ? 1 : 2), q1 = c == 0 ? 1 : (c == 1 ? 3 : 4),
-                  q2 = c == 0 ? 2 : (c == 1 ? 4 : 5);
-        const C<T>* line = mv.spec + ((my * g.Hx + (ok ? mx : 0)) * 6) * g.Hz;
-        const C<T>*G0l = line + q0 * g.Hz, *G1l = line + q1 * g.Hz, *G2l = line + q2 * g.Hz;
-        const int fc = c == 0 ? fx : (c == 1 ? fy : 0);   // z: per point below
+        const C<T>* line = mv.spec + ((my * g.Hx + (ok ? mx : 0)) * 6) * g.Hz;   // [6][Hz]
+        const int u = c * TL + t;                               // thread of the column
+        constexpr int NU = 3 * TL, NMZ = (N / 2 + NU) / NU;     // mz per thread (at most)
 #pragma unroll
-        for (int m = 0; m < V; ++m) {
-            const int n = t + m * TL;
-            const int mz = n <= N / 2 ? n : N - n, fz = n > N / 2;
-            const C<T> G0 = ok ? __ldg(G0l + mz) : mk<T>(0, 0), G1 = ok ? __ldg(G1l + mz) : mk<T>(0, 0),
-                       G2 = ok ? __ldg(G2l + mz) : mk<T>(0, 0);
-            C<T> a = sm[L.template at<KP>(3 * w, n)], b = sm[L.template at<KP>(3 * w + 1, n)],
-                 d = sm[L.template at<KP>(3 * w + 2, n)];
-            if (fx) a = mk<T>(-a.x, -a.y);
-            if (fy) b = mk<T>(-b.x, -b.y);
-            if (fz) d = mk<T>(-d.x, -d.y);
-            C<T> y = cfma<T>(G2, d, cfma<T>(G1, b, cmul<T>(G0, a)));
-            if (fc ^ (c == 2 ? fz : 0)) y = mk<T>(-y.x, -y.y);
-            v[m] = y;
+        for (int i = 0; i < NMZ; ++i) {
+            const int mz = u + i * NU;
+            if (mz > N / 2) break;
+            C<T> G[6];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) G[q] = ok ? __ldg(line + q * g.Hz + mz) : mk<T>(0, 0);
+            // the point mz (z not mirrored) and, unless mz is 0 or N/2, its
+            // mirror N - mz (z mirrored)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (h == 1 && (mz == 0 || mz == N / 2)) break;
+                const int n = h ? N - mz : mz, fz = h;
+                const int o0 = L.template at<KP>(3 * w, n), o1 = L.template at<KP>(3 * w + 1, n),
+                          o2 = L.template at<KP>(3 * w + 2, n);
+                C<T> a = sm[o0], b = sm[o1], d = sm[o2];
+                if (fx) a = mk<T>(-a.x, -a.y);
+                if (fy) b = mk<T>(-b.x, -b.y);
+                if (fz) d = mk<T>(-d.x, -d.y);
+                C<T> y0 = cfma<T>(G[2], d, cfma<T>(G[1], b, cmul<T>(G[0], a)));
+                C<T> y1 = cfma<T>(G[4], d, cfma<T>(G[3], b, cmul<T>(G[1], a)));
+                C<T> y2 = cfma<T>(G[5], d, cfma<T>(G[4], b, cmul<T>(G[2], a)));
+                if (fx) y0 = mk<T>(-y0.x, -y0.y);
+                if (fy) y1 = mk<T>(-y1.x, -y1.y);
+                if (fz) y2 = mk<T>(-y2.x, -y2.y);
+                sm[o0] = y0;
+                sm[o1] = y1;
+                sm[o2] = y2;
+            }
         }
     }
-    L.sync();   // the inverse's first stage writes the buffer
+    L.sync();
+#pragma unroll
+    for (int m = 0; m < V; ++m) v[m] = sm[L.template at<KP>(l, t + m * TL)];
+    L.sync();   // the inverse's first exchange writes the buffer
     // nothing reuses the exchange buffers after the inverse
     fft_wide<T, true, N, false, false>(v, sm, L, l, t, mv.tw);
     if (ok) {
