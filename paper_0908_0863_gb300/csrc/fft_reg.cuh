@@ -76,34 +76,45 @@ struct Line {
 };
 
 // ------------------------------------------------------------------------
-// Wide mapping for N = R M (R = 3 or 5, M = 2^a >= 8).  The line is held
-// by T = M/8 threads, a power of two (warps hold whole lines), each with
-// the V = 8R points t + T m, m < V.  A Stockham stage of radix r reads
-// x[j + (N/r) s] for butterfly j < N/r; when r divides V, N/r is a multiple
-// of T and thread t takes the V/r butterflies j = t + T q, whose inputs
-// are its own points m = q + (V/r) s.  So the transform is: one radix-V
-// stage (each thread one V-point DFT of its own points, the prime-factor
-// form 8 x R), then the power-of-two factor T in radix-8 stages and one
-// radix-2 or 4 stage, every stage on the thread's registers, with one
-// shared-memory exchange between two stages; the last stage leaves the
-// outputs in natural order on the thread's points.  Lines of 96, 160, 192
-// and 320 points need one exchange per transform, 384, 640 and 768 two.
+// Wide mappings.  A line of N points is held by T threads (a power of two,
+// so warps hold whole lines) with V points each, t + T m, m < V.  A
+// Stockham stage of radix r reads x[j + (N/r) s] for butterfly j < N/r;
+// when r divides V, N/r is a multiple of T and thread t takes the V/r
+// butterflies j = t + T q, whose inputs are its own points m = q + (V/r) s.
+// So the transform is one radix-V stage (each thread one V-point DFT of its
+// own points), then stages of radices dividing V over the factor T, every
+// stage on the thread's registers, with one shared-memory exchange between
+// two stages; the last stage leaves the outputs in natural order on the
+// thread's points.
+//  * N = R M (R = 3 or 5, M = 2^a >= 8): V = 8R (a prime-factor 8 x R
+//    DFT), T = M/8, then radix-8 stages and one radix 2 or 4.  Lines of
+//    96, 160, 192 and 320 points need one exchange per transform, 384, 640
+//    and 768 two.
+//  * N = 2^a >= 128: V = 2^ceil(a/2), T = N/V <= V, then one radix-T stage:
+//    one exchange for every length (the 8-point mapping needs two from 128
+//    points on).
 template <int N>
 struct Wide {
-    static constexpr int R = Line<N>::R, M = N / R;
-    static constexpr int T = M / 8;                 // threads per line
-    static constexpr int V = 8 * R;                 // points per thread, the first radix
+    static constexpr bool ODD = Line<N>::ODD;
+    static constexpr int R = Line<N>::R;
+    static constexpr int V = ODD ? 8 * R : 1 << ((log2c(N) + 1) / 2);   // points per thread, first radix
+    static constexpr int T = N / V;                                      // threads per line
     static constexpr int LOGT = log2c(T);
-    static constexpr int NSTAGES = (LOGT + 2) / 3;  // power-of-two stages after the first
-    // radix of power-of-two stage i (radix 8, the remainder 2 or 4 last)
-    __host__ __device__ static constexpr int radix(int i) { return (i < LOGT / 3) ? 8 : 1 << (LOGT % 3); }
+    static constexpr int NSTAGES = ODD ? (LOGT + 2) / 3 : 1;             // stages after the first
+    // radix of stage i after the first
+    __host__ __device__ static constexpr int radix(int i) {
+        return ODD ? ((i < LOGT / 3) ? 8 : 1 << (LOGT % 3)) : T;
+    }
+    // exchange key of the first exchange: 0, or for a 2^k-point first stage
+    // (k >= 4) kPow2Key + k, whose column-tile pad is p >> k
+    static constexpr int KEY0 = (!ODD && V >= 16) ? 100 + log2c(V) : 0;
 };
 
-// thread mapping a pass uses for N-point lines: the wide one for
-// 3 * 2^a and 5 * 2^a, eight points per thread for 2^a
+// thread mapping the x pass uses for N-point lines: a wide one for
+// 3 * 2^a and 5 * 2^a and for 2^a >= 128, eight points per thread below
 template <int N>
 struct Map {
-    static constexpr bool WIDE = Line<N>::ODD;
+    static constexpr bool WIDE = Line<N>::ODD || N >= 128;
     static constexpr int T = WIDE ? Wide<N>::T : Line<N>::T;      // threads per line
     static constexpr int V = WIDE ? Wide<N>::V : 8;               // register slots per thread
     static constexpr int NV = WIDE ? Wide<N>::V : Line<N>::NV;    // points held (N < 8: N)
@@ -111,10 +122,12 @@ struct Map {
 };
 // threads per N-point line of the 8-point mapping, for host code
 __host__ __device__ constexpr int line_threads(int N) { return N >= 8 ? N / 8 : 1; }
-// threads per N-point line of the mapping Map<N>, for host code
-__host__ __device__ constexpr int map_threads(int N) {
-    return (N % 3 == 0) ? N / 24 : (N % 5 == 0) ? N / 40 : (N >= 8 ? N / 8 : 1);
+// whether Map<N> is a wide mapping, its points and threads per line
+__host__ __device__ constexpr bool map_wide(int N) { return N % 3 == 0 || N % 5 == 0 || N >= 128; }
+__host__ __device__ constexpr int wide_points(int N) {
+    return (N % 3 == 0) ? 24 : (N % 5 == 0) ? 40 : 1 << ((log2c(N) + 1) / 2);
 }
+__host__ __device__ constexpr int map_threads(int N) { return map_wide(N) ? N / wide_points(N) : line_threads(N); }
 
 // Shared-memory layouts.  An address comes from at<KEY>(w, p) (line w,
 // point p), where KEY is log2 of Ns of the stage that writes the exchange;
@@ -138,16 +151,16 @@ __host__ __device__ constexpr int map_threads(int N) {
 // per-access arithmetic.
 struct Pad { int c0, c1, c2; };
 __host__ __device__ constexpr Pad row_pad(int T, int KEY) {
-    return T <= 8 ? (KEY == 0 ? Pad{1, 0, 0} : Pad{0, 0, 0})
+    return KEY >= 100 ? row_pad(T, 0)
+         : T <= 8 ? (KEY == 0 ? Pad{1, 0, 0} : Pad{0, 0, 0})
                   : KEY == 0 ? Pad{0, 1, 0} : KEY <= 2 ? Pad{0, 2, 0} : KEY == 3 ? Pad{0, 0, 8} : Pad{0, 0, 0};
 }
 __host__ __device__ constexpr int pad_word(Pad c, int p) { return p + c.c0 * (p >> 3) + c.c1 * (p >> 4) + c.c2 * (p >> 6); }
-// elements per line of a RowLayout buffer, the line stride of every
-// exchange: the widest padded line of any key, and for lines of T <= 8
-// threads rounded up to T mod 2T, so that the 16/T lines a half-warp
-// touches fall in complementary banks
-__host__ __device__ constexpr int row_ld(int N) {
-    const int T = map_threads(N);
+// elements per line of a RowLayout buffer for lines of T threads, the
+// line stride of every exchange: the widest padded line of any key, and
+// for lines of T <= 8 threads rounded up to T mod 2T, so that the 16/T
+// lines a half-warp touches fall in complementary banks
+__host__ __device__ constexpr int row_ld(int N, int T) {
     int ld = 0;
     for (int k = 0; k <= 10; ++k) {
         const int l = pad_word(row_pad(T, k), N - 1) + 1;
@@ -156,27 +169,30 @@ __host__ __device__ constexpr int row_ld(int N) {
     return T >= 16 ? ld : ld + ((T - ld) % (2 * T) + 2 * T) % (2 * T);
 }
 
-template <int N>
+template <int N, int T>
 struct RowLayout {
-    static constexpr int T = Map<N>::T;
     template <int KEY>
     __device__ __forceinline__ int at(int w, int p) const {
-        return w * row_ld(N) + pad_word(row_pad(T, KEY), p);
+        return w * row_ld(N, T) + pad_word(row_pad(T, KEY), p);
     }
     __device__ __forceinline__ void sync() const { __syncthreads(); }
 };
 // 2^LOGW lines per tile, point-major (threads w-fastest, strided lines of
-// the lattice), one pad row after every 8 points, the same for every
-// exchange; the width is a compile-time constant, so every exchange
-// address folds into a constant offset from the thread's base
+// the lattice), one pad row after every 8 points, or, after a first stage
+// of 2^k points per thread (key 100 + k), after every 2^k (the stage writes
+// points 2^k t + r); the width is a compile-time constant, so every
+// exchange address folds into a constant offset from the thread's base
 template <int LOGW>
 struct ColLayoutT {
     template <int KEY>
-    __device__ __forceinline__ int at(int w, int p) const { return ((p + (p >> 3)) << LOGW) + w; }
+    __device__ __forceinline__ int at(int w, int p) const {
+        constexpr int SH = KEY >= 100 ? KEY - 100 : 3;
+        return ((p + (p >> SH)) << LOGW) + w;
+    }
     __device__ __forceinline__ void sync() const { __syncthreads(); }
 };
 
-// elements of a ColLayoutT tile of W lines of N points
+// elements of a ColLayoutT tile of W lines of N points (the pad of every key)
 __host__ __device__ constexpr int col_elems(int N, int W) { return (N + N / 8) * W; }
 
 template <typename T, bool INV>
@@ -516,12 +532,16 @@ __device__ __forceinline__ void dft_pfa(C<T> (&x)[R << B]) {
     }
 }
 
-// cos(2 pi n / V) for V = 24 or 40, from the first-quadrant values
-// cos(2 pi a / V), a <= V/4, and the symmetries of the cosine
+// cos(2 pi n / V) for V = 16, 24, 32 or 40, from the first-quadrant
+// values cos(2 pi a / V), a <= V/4, and the symmetries of the cosine
 template <int V>
 __host__ __device__ constexpr double cos_v(int n) {
+    constexpr double q16[5] = {1.0, 0.92387953251128675613, 0.70710678118654752440, 0.38268343236508977173, 0.0};
     constexpr double q24[7] = {1.0, 0.96592582628906828675, 0.86602540378443864676, 0.70710678118654752440,
                                0.5, 0.25881904510252076235, 0.0};
+    constexpr double q32[9] = {1.0, 0.98078528040323044913, 0.92387953251128675613, 0.83146961230254523708,
+                               0.70710678118654752440, 0.55557023301960222474, 0.38268343236508977173,
+                               0.19509032201612826785, 0.0};
     constexpr double q40[11] = {1.0, 0.98768834059513772620, 0.95105651629515357212, 0.89100652418836786236,
                                 0.80901699437494742410, 0.70710678118654752440, 0.58778525229247312917,
                                 0.45399049973954679156, 0.30901699437494742410, 0.15643446504023086901, 0.0};
@@ -530,7 +550,7 @@ __host__ __device__ constexpr double cos_v(int n) {
     if (n > V / 2) n = V - n;
     const double sg = n > V / 4 ? -1.0 : 1.0;
     const int a = n > V / 4 ? V / 2 - n : n;
-    return sg * (V == 24 ? q24[a] : q40[a]);
+    return sg * (V == 16 ? q16[a] : V == 24 ? q24[a] : V == 32 ? q32[a] : q40[a]);
 }
 // exp(-+ 2 pi i n / V): forward -, inverse +
 template <typename T, bool INV, int V>
@@ -538,35 +558,97 @@ __device__ __forceinline__ C<T> root_v(int n) {
     const double c = cos_v<V>(n), s = cos_v<V>(n - V / 4);   // sin = cos(. - pi/2)
     return mk<T>((T)c, INV ? (T)s : (T)-s);
 }
+// x exp(-+ 2 pi i e / V) for a compile-time e: quarter turns exactly, odd
+// eighths with one scale, the rest as a complex product
+template <typename T, bool INV, int V>
+__device__ __forceinline__ C<T> cmul_root(C<T> x, int e) {
+    e %= V;
+    if (e < 0) e += V;
+    if (e == 0) return x;
+    if (4 * e == V) return rot90<T, INV>(x);
+    if (2 * e == V) return mk<T>(-x.x, -x.y);
+    if (4 * e == 3 * V) return rot90<T, !INV>(x);
+    if ((8 * e) % V == 0) {   // (+-1 +- i) / sqrt(2)
+        const T h = (T)0.70710678118654752440;
+        const C<T> r = root_v<T, INV, V>(e);
+        const T c = r.x > 0 ? (T)1 : (T)-1, s = r.y > 0 ? (T)1 : (T)-1;
+        return mk<T>((c * x.x - s * x.y) * h, (c * x.y + s * x.x) * h);
+    }
+    return cmul<T>(x, root_v<T, INV, V>(e));
+}
 
-// The first stage of the wide mapping: the V = 8R-point DFT of the
-// thread's own points.  With HALF_IN (inputs V/2.. zero): one radix-2
-// decimation-in-frequency layer, a = x and b = x W_V^n for n < 4R, then
-// 4R-point DFTs of a (even outputs) and b (odd outputs).
-template <typename T, bool INV, int R, bool HALF_IN>
-__device__ __forceinline__ void wide_first(C<T> (&v)[8 * R]) {
-    constexpr int V = 8 * R, H = 4 * R;
+// DFT of n = 2^k <= 32 points in place, natural order.  n > 8: Cooley-Tukey
+// with n = n1 n2 (n1 = 4 for 16, 8 for 32), input index a + n1 b, output
+// n2 c + d: n1 DFTs of n2 points over b, the twiddles exp(-+ 2 pi i a d / n),
+// then n2 DFTs of n1 points over a.
+template <typename T, bool INV, int n>
+__device__ __forceinline__ void dft_p2(C<T> (&x)[n]) {
+    if constexpr (n == 1) {
+    } else if constexpr (n == 2) {
+        dft2<T, INV>(x);
+    } else if constexpr (n == 4) {
+        dft4<T, INV>(x);
+    } else if constexpr (n == 8) {
+        dft8<T, INV>(x);
+    } else {
+        constexpr int n1 = n == 16 ? 4 : 8, n2 = n / n1;
+        C<T> y[n1][n2];
+#pragma unroll
+        for (int a = 0; a < n1; ++a) {
+#pragma unroll
+            for (int b = 0; b < n2; ++b) y[a][b] = x[a + n1 * b];
+            dft_p2<T, INV, n2>(y[a]);
+#pragma unroll
+            for (int d = 1; d < n2; ++d) y[a][d] = cmul_root<T, INV, n>(y[a][d], a * d);
+        }
+#pragma unroll
+        for (int d = 0; d < n2; ++d) {
+            C<T> z[n1];
+#pragma unroll
+            for (int a = 0; a < n1; ++a) z[a] = y[a][d];
+            dft_p2<T, INV, n1>(z);
+#pragma unroll
+            for (int c = 0; c < n1; ++c) x[n2 * c + d] = z[c];
+        }
+    }
+}
+
+// The first stage of a wide mapping: the V-point DFT of the thread's own
+// points (prime-factor 8 x R for V = 8R, Cooley-Tukey for V = 2^k).  With
+// HALF_IN (inputs V/2.. zero): one radix-2 decimation-in-frequency layer,
+// a = x and b = x W_V^n for n < V/2, then V/2-point DFTs of a (even outputs)
+// and b (odd outputs).
+template <typename T, bool INV, int N, bool HALF_IN>
+__device__ __forceinline__ void wide_first(C<T> (&v)[Wide<N>::V]) {
+    using W = Wide<N>;
+    constexpr int V = W::V, H = V / 2, R = W::R;
     if constexpr (HALF_IN) {
         C<T> a[H], b[H];
 #pragma unroll
         for (int n = 0; n < H; ++n) {
             a[n] = v[n];
-            b[n] = n == 0 ? v[n] : cmul<T>(v[n], root_v<T, INV, V>(n));
+            b[n] = cmul_root<T, INV, V>(v[n], n);
         }
-        dft_pfa<T, INV, R, 2>(a);
-        dft_pfa<T, INV, R, 2>(b);
+        if constexpr (W::ODD) {
+            dft_pfa<T, INV, R, 2>(a);
+            dft_pfa<T, INV, R, 2>(b);
+        } else {
+            dft_p2<T, INV, H>(a);
+            dft_p2<T, INV, H>(b);
+        }
 #pragma unroll
         for (int k = 0; k < H; ++k) {
             v[2 * k] = a[k];
             v[2 * k + 1] = b[k];
         }
     } else {
-        dft_pfa<T, INV, R, 3>(v);
+        if constexpr (W::ODD) dft_pfa<T, INV, R, 3>(v);
+        else dft_p2<T, INV, V>(v);
     }
 }
 
-// power-of-two stage I (radix RDX = Wide<N>::radix(I), Ns = V RDX_0 ...) of
-// the wide mapping and the ones after it.  On entry the registers hold the
+// stage I after the first (radix RDX = Wide<N>::radix(I), Ns = V RDX_0 ...)
+// of a wide mapping and the ones after it.  On entry the registers hold the
 // canonical points after the exchange; butterfly q (j = t + T q) reads
 // v[q + (V/RDX) r] and twiddles it by exp(-+ 2 pi i (j mod Ns) r / (RDX Ns)).
 template <typename T, bool INV, int N, int I, int NS, bool TAIL, class Layout>
@@ -574,22 +656,30 @@ __device__ __forceinline__ void wide_stages(C<T> (&v)[Wide<N>::V], C<T>* __restr
                                             int t, const C<T>* __restrict__ tw) {
     using W = Wide<N>;
     constexpr int R = W::R, Tn = W::T, V = W::V, RDX = W::radix(I), NQ = V / RDX;
-    constexpr int off = R == 3 ? 0 : kTwLen, TWN = R == 3 ? kTwLen : kTw5Len;
+    constexpr int off = R == 5 ? kTwLen : 0, TWN = R == 5 ? kTw5Len : kTwLen;
     constexpr int step = TWN / (RDX * NS);   // table entries per unit of k r
     constexpr bool LAST = I + 1 == W::NSTAGES;
     // The last stage has Ns = N / RDX > j, so k = t + T q and its twiddles
     // factor as exp(-+ 2 pi i t r / N) exp(-+ 2 pi i q r / V): the first
     // from the table once per thread, the second a compile-time constant.
     // The other stages take k = j mod Ns from the table per butterfly.
-    // FP32 forms powers of one table value (a few ulp, far below the FP32
-    // transform's own error); FP64 reads every power from the table.
+    // FP32 forms powers of one table value for r < 8 and takes w^(8g) from
+    // the table for the radix-16 and -32 stages (at most four roundings, far
+    // below the FP32 transform's own error); FP64 reads every power.
     C<T> wt[RDX];
     if constexpr (LAST) {
         wt[0] = mk<T>(1, 0);
         if (sizeof(T) == 4) {
             wt[1] = twiddle<T, INV>(tw, off + t * step);
 #pragma unroll
-            for (int r = 2; r < RDX; ++r) wt[r] = (r & 1) ? cmul<T>(wt[r - 1], wt[1]) : cmul<T>(wt[r / 2], wt[r / 2]);
+            for (int r = 2; r < (RDX < 8 ? RDX : 8); ++r)
+                wt[r] = (r & 1) ? cmul<T>(wt[r - 1], wt[1]) : cmul<T>(wt[r / 2], wt[r / 2]);
+#pragma unroll
+            for (int g = 8; g < RDX; g += 8) {
+                wt[g] = twiddle<T, INV>(tw, off + t * g * step);
+#pragma unroll
+                for (int r = 1; r < 8; ++r) wt[g + r] = cmul<T>(wt[g], wt[r]);
+            }
         } else {
 #pragma unroll
             for (int r = 1; r < RDX; ++r) wt[r] = twiddle<T, INV>(tw, off + t * r * step);
@@ -601,7 +691,7 @@ __device__ __forceinline__ void wide_stages(C<T> (&v)[Wide<N>::V], C<T>* __restr
         wr[0] = mk<T>(1, 0);
         if constexpr (LAST) {
 #pragma unroll
-            for (int r = 1; r < RDX; ++r) wr[r] = q == 0 ? wt[r] : cmul<T>(wt[r], root_v<T, INV, V>(q * r));
+            for (int r = 1; r < RDX; ++r) wr[r] = cmul_root<T, INV, V>(wt[r], q * r);
         } else {
             const int k = (t + Tn * q) % NS;
             if (sizeof(T) == 4) {
@@ -617,9 +707,7 @@ __device__ __forceinline__ void wide_stages(C<T> (&v)[Wide<N>::V], C<T>* __restr
         x[0] = v[q];
 #pragma unroll
         for (int r = 1; r < RDX; ++r) x[r] = cmul<T>(v[q + NQ * r], wr[r]);
-        if constexpr (RDX == 2) dft2<T, INV>(x);
-        else if constexpr (RDX == 4) dft4<T, INV>(x);
-        else dft8<T, INV>(x);
+        dft_p2<T, INV, RDX>(x);
 #pragma unroll
         for (int r = 0; r < RDX; ++r) v[q + NQ * r] = x[r];
     }
@@ -641,24 +729,24 @@ __device__ __forceinline__ void wide_stages(C<T> (&v)[Wide<N>::V], C<T>* __restr
     }
 }
 
-// In-place DFT of one N = R M line in the wide mapping: v[m] = x[t + T m],
-// m < 8R.  All threads of the CTA call it together.  HALF_IN: inputs
-// m >= 4R (n >= N/2) are zero.  Outputs the caller never reads are dead
+// In-place DFT of one N-point line in its wide mapping: v[m] = x[t + T m],
+// m < V.  All threads of the CTA call it together.  HALF_IN: inputs
+// m >= V/2 (n >= N/2) are zero.  Outputs the caller never reads are dead
 // code, so an inverse that keeps the first half needs no flag.  TAIL: the
 // caller reuses the shared buffer afterwards (see fft_lines).
 template <typename T, bool INV, int N, bool HALF_IN, bool TAIL = true, class Layout>
 __device__ __forceinline__ void fft_wide(C<T> (&v)[Wide<N>::V], C<T>* __restrict__ sm, const Layout& L, int w,
                                          int t, const C<T>* __restrict__ tw) {
     using W = Wide<N>;
-    constexpr int Tn = W::T, V = W::V;
-    wide_first<T, INV, W::R, HALF_IN>(v);
-    if constexpr (W::NSTAGES > 0) {
+    constexpr int Tn = W::T, V = W::V, K0 = W::KEY0;
+    wide_first<T, INV, N, HALF_IN>(v);
+    if constexpr (W::NSTAGES > 0 && Tn > 1) {
         // exchange: the first stage's output r of thread t goes to t V + r
 #pragma unroll
-        for (int r = 0; r < V; ++r) sm[L.template at<0>(w, t * V + r)] = v[r];
+        for (int r = 0; r < V; ++r) sm[L.template at<K0>(w, t * V + r)] = v[r];
         L.sync();
 #pragma unroll
-        for (int m = 0; m < V; ++m) v[m] = sm[L.template at<0>(w, t + Tn * m)];
+        for (int m = 0; m < V; ++m) v[m] = sm[L.template at<K0>(w, t + Tn * m)];
         if constexpr (TAIL || W::NSTAGES > 1) L.sync();
         wide_stages<T, INV, N, 0, V, TAIL>(v, sm, L, w, t, tw);
     }

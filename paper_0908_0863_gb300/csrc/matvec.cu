@@ -12,7 +12,8 @@ bool tiles_ok(const Geometry& g, int logW_y, int logW_z, int logW_x) {
     if (logW_y < 0 || logW_z < 0 || logW_x < 0) return false;
     if (logW_y > kMaxLogW || logW_z > kMaxLogR || logW_x > kMaxLogZ) return false;
     if ((1 << logW_y) * ty > kYThreads || 3ull * (1ull << logW_y) * col_elems(g.Ly, 1) * elt > 200 * 1024) return false;
-    if ((1 << logW_z) * tz > p3_max_threads<T>(g.Lz) || 3ull * (1ull << logW_z) * row_ld(g.Lz) * elt > 200 * 1024)
+    if ((1 << logW_z) * tz > p3_max_threads<T>(g.Lz) ||
+        3ull * (1ull << logW_z) * row_ld(g.Lz, p3_line_threads(g.Lz)) * elt > 200 * 1024)
         return false;
     if (rows_groups(g.Lx, 1 << logW_x) * (1 << logW_x) * map_threads(g.Lx) > rows_max_threads(g.Lx) ||
         rows_smem_elems(g.Lx, 1 << logW_x) * elt > 200 * 1024)

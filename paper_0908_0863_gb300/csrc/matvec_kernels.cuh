@@ -69,17 +69,20 @@ template <typename T> __host__ __device__ constexpr int p3_max_threads(int N) {
 }
 // threads of one z column in P3: its three components share the T = N/8
 // threads of the 8-point mapping, or take 3 x M/8 in the wide one
-__host__ __device__ constexpr int p3_col_threads(int N) { return wide_len(N) ? 3 * map_threads(N) : map_threads(N); }
+__host__ __device__ constexpr int p3_col_threads(int N) { return wide_len(N) ? 3 * map_threads(N) : line_threads(N); }
+// threads of one z line in P3 (what its shared-memory pads are laid out for)
+__host__ __device__ constexpr int p3_line_threads(int N) { return wide_len(N) ? map_threads(N) : line_threads(N); }
 // widest tiles the runtime widths of P3 (columns per CTA) and P2/P4 (z lines
 // per CTA) may take, as log2
 constexpr int kMaxLogR = 6;
 constexpr int kMaxLogZ = 4;
 // P2/P4 keep eight points of one row per thread: up to 1024 threads per CTA;
-// with the wide mapping of 3 * 2^a and 5 * 2^a rows (24 or 40 points per
-// thread) up to 256, which leaves the registers for them
+// with a wide mapping (3 * 2^a and 5 * 2^a rows: 24 or 40 points per
+// thread; 2^a rows from 128 points: 16 or 32) up to 256, which leaves the
+// registers for them
 constexpr int kRowThreads = 1024;
 constexpr int kRowThreadsWide = 256;
-__host__ __device__ constexpr int rows_max_threads(int N) { return wide_len(N) ? kRowThreadsWide : kRowThreads; }
+__host__ __device__ constexpr int rows_max_threads(int N) { return map_wide(N) ? kRowThreadsWide : kRowThreads; }
 
 // P1 and P5 keep the eight points, their gather indices and (P5) the
 // gathered entries of p in registers: at most 512 threads per CTA leave
@@ -177,13 +180,12 @@ __global__ void __launch_bounds__(kYThreads) k_p1(MatvecView<T> mv, const C<T>* 
 // the column side touches Wz consecutive z values of one x (32 bytes and
 // more), and the row side whole 32-byte sectors of Wz rows.  A CTA holds
 // rows_groups(N, Wz) tiles of consecutive z (more than one only for the
-// wide mapping of 3 * 2^a and 5 * 2^a lines, whose few threads per line
-// would otherwise make CTAs of a warp or less), each with its own region
-// of shared memory.
+// wide mappings, whose few threads per line would otherwise make CTAs of a
+// warp or less), each with its own region of shared memory.
 // Forward (P2): Ay rows -> transform -> Bxy.  Inverse (P4): Bxy ->
 // transform -> the first K outputs into Ay.  Grid: (z tiles, Ly, 3 nb).
 __host__ __device__ constexpr int rows_groups(int N, int Wz) {
-    return wide_len(N) && Wz * map_threads(N) < 128 ? 128 / (Wz * map_threads(N)) : 1;
+    return map_wide(N) && Wz * map_threads(N) < 128 ? 128 / (Wz * map_threads(N)) : 1;
 }
 
 template <typename T, bool INV, int N, int LOGZ>
@@ -313,8 +315,8 @@ __global__ void __launch_bounds__(p3_max_threads<T>(N)) k_p3(MatvecView<T> mv) {
             const int n = t + m * TL;
             v[c][m] = (ok && m < Line<N>::NH && n < g.P) ? col[c * comp + n] : mk<T>(0, 0);
         }
-    const int region = row_ld(N) << mv.logW_z;
-    fft_lines<T, false, N, 3, true, false>(v, sm, region, RowLayout<N>{}, w, t, mv.tw);
+    const int region = row_ld(N, TL) << mv.logW_z;
+    fft_lines<T, false, N, 3, true, false>(v, sm, region, RowLayout<N, TL>{}, w, t, mv.tw);
     {
         const int my = jy <= g.Ly / 2 ? jy : g.Ly - jy, fy = jy > g.Ly / 2;
         const int mx = ix <= g.Lx / 2 ? ix : g.Lx - ix, fx = ix > g.Lx / 2;
@@ -324,7 +326,7 @@ __global__ void __launch_bounds__(p3_max_threads<T>(N)) k_p3(MatvecView<T> mv) {
             p3_product<T, N>(line, ok, fx, fy, t + m * TL, v[0][m], v[1][m], v[2][m]);
     }
     // nothing reuses the exchange buffers after the inverse
-    fft_lines<T, true, N, 3, false, true, false>(v, sm, region, RowLayout<N>{}, w, t, mv.tw);
+    fft_lines<T, true, N, 3, false, true, false>(v, sm, region, RowLayout<N, TL>{}, w, t, mv.tw);
     if (ok) {
 #pragma unroll
         for (int c = 0; c < 3; ++c)
@@ -352,6 +354,7 @@ __global__ void __launch_bounds__(p3_max_threads<T>(N)) k_p3(MatvecView<T> mv) {
 // measured fastest among 128, 136, 144, 160 and no cap)
 template <typename T, int N>
 __global__ void __launch_bounds__(p3_max_threads<T>(N)) __maxnreg__(sizeof(T) == 4 ? 128 : 255) k_p3w(MatvecView<T> mv) {
+    static_assert(Line<N>::ODD, "k_p3w takes 3 * 2^a and 5 * 2^a columns (their spectrum lines are [6][Hz])");
     const int j = blockIdx.x;                                   // batch slot
     if (rhs_done(mv, mv.b0 + j)) return;
     extern __shared__ unsigned char smem_raw[];
@@ -370,7 +373,7 @@ __global__ void __launch_bounds__(p3_max_threads<T>(N)) __maxnreg__(sizeof(T) ==
         const int n = t + m * TL;
         v[m] = (ok && m < nh && n < g.P) ? col[n] : mk<T>(0, 0);
     }
-    const RowLayout<N> L;
+    const RowLayout<N, TL> L;
     fft_wide<T, false, N, true>(v, sm, L, l, t, mv.tw);
 #pragma unroll
     for (int m = 0; m < V; ++m) sm[L.template at<KP>(l, t + m * TL)] = v[m];
@@ -560,10 +563,10 @@ template <typename T, int N>
 int launch_p3(const MatvecView<T>& mv, cudaStream_t st) {
     const Geometry& g = mv.g;
     const int R = 1 << mv.logW_z;
-    const size_t sm = 3 * (size_t)R * row_ld(N) * sizeof(C<T>);
+    const size_t sm = 3 * (size_t)R * row_ld(N, p3_line_threads(N)) * sizeof(C<T>);
     static std::atomic<size_t> smem_set{0};
     const dim3 grid(mv.nb, (g.Lx + R - 1) / R, g.Ly);
-    if constexpr (Map<N>::WIDE) {
+    if constexpr (Line<N>::ODD) {   // the wide z pass for 3 * 2^a and 5 * 2^a columns
         if (int rc = set_smem((const void*)k_p3w<T, N>, sm, smem_set)) return rc;
         k_p3w<T, N><<<grid, R * p3_col_threads(N), sm, st>>>(mv);
     } else {
