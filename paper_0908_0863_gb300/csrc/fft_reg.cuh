@@ -178,10 +178,15 @@ struct RowLayout {
     __device__ __forceinline__ void sync() const { __syncthreads(); }
 };
 // 2^LOGW lines per tile, point-major (threads w-fastest, strided lines of
-// the lattice), one pad row after every 8 points, or, after a first stage
-// of 2^k points per thread (key 100 + k), after every 2^k (the stage writes
-// points 2^k t + r); the width is a compile-time constant, so every
-// exchange address folds into a constant offset from the thread's base
+// the lattice), with a pad row after every 2^SH points: SH = 3, or after a
+// first stage of 2^k points per thread in a wide mapping (key 100 + k)
+// SH = k, since that stage writes points 2^k t + r.  (For the first
+// exchange of the 8-point mapping of 2^a lines, whose radix-2 or -4 first
+// stage writes at stride 2 or 4, a half-warp bank model finds shifts 1 or 2
+// conflict-free; in P1 at 256-point lines the larger tiles they need
+// measured slower, 0.0372 against 0.0340 ms, so SH stays 3.)  The width is
+// a compile-time constant, so every exchange address folds into a constant
+// offset from the thread's base.
 template <int LOGW>
 struct ColLayoutT {
     template <int KEY>
@@ -192,8 +197,10 @@ struct ColLayoutT {
     __device__ __forceinline__ void sync() const { __syncthreads(); }
 };
 
-// elements of a ColLayoutT tile of W lines of N points (the pad of every key)
-__host__ __device__ constexpr int col_elems(int N, int W) { return (N + N / 8) * W; }
+// elements of a ColLayoutT tile of W lines of N points with a pad row
+// after every 2^SH points (SH = 3: the 8-point and the odd wide mappings)
+__host__ __device__ constexpr int col_elems_sh(int N, int W, int SH) { return (N + (N >> SH)) * W; }
+__host__ __device__ constexpr int col_elems(int N, int W) { return col_elems_sh(N, W, 3); }
 
 template <typename T, bool INV>
 __device__ __forceinline__ C<T> twiddle(const C<T>* __restrict__ tw, int idx) {
@@ -441,6 +448,7 @@ __device__ __forceinline__ void fft_lines(C<T> (&v)[NL][8], C<T>* __restrict__ s
         constexpr int Tn = N / 8, LOGM = Line<N>::LOGM;
         constexpr int first = LOGM % 3;
         constexpr int L1 = first == 0 ? 3 : first;   // log2 of the first radix
+        constexpr int K1 = 0;                         // key of the first exchange
         // first stage (Ns = 1, no twiddles): outputs of butterfly j, point r
         // go to j R + r
 #pragma unroll
@@ -452,8 +460,8 @@ __device__ __forceinline__ void fft_lines(C<T> (&v)[NL][8], C<T>* __restrict__ s
                 for (int q = 0; q < 4; ++q) {
                     C<T> b[2] = {v[l][q], HALF_IN ? v[l][q] : v[l][q + 4]};
                     if (!HALF_IN) dft2<T, INV>(b);
-                    S[L.template at<0>(w, (t + q * Tn) * 2)] = b[0];
-                    S[L.template at<0>(w, (t + q * Tn) * 2 + 1)] = b[1];
+                    S[L.template at<K1>(w, (t + q * Tn) * 2)] = b[0];
+                    S[L.template at<K1>(w, (t + q * Tn) * 2 + 1)] = b[1];
                 }
             } else if constexpr (first == 2) {
                 // butterflies j = t + q T (q < 2) read x[j + 2T r] = v[q + 2r]
@@ -463,21 +471,21 @@ __device__ __forceinline__ void fft_lines(C<T> (&v)[NL][8], C<T>* __restrict__ s
                                  HALF_IN ? mk<T>(0, 0) : v[l][q + 6]};
                     dft4<T, INV>(b);
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) S[L.template at<0>(w, (t + q * Tn) * 4 + r)] = b[r];
+                    for (int r = 0; r < 4; ++r) S[L.template at<K1>(w, (t + q * Tn) * 4 + r)] = b[r];
                 }
             } else {
                 if (HALF_IN) dft8_half_in<T, INV>(v[l]);
                 else dft8<T, INV>(v[l]);
 #pragma unroll
-                for (int r = 0; r < 8; ++r) S[L.template at<0>(w, t * 8 + r)] = v[l][r];
+                for (int r = 0; r < 8; ++r) S[L.template at<K1>(w, t * 8 + r)] = v[l][r];
             }
         }
         if constexpr (L1 == LOGM) {
             // the first stage was the only power-of-two stage (N = 3 * 8, 5 * 8)
-            odd_finish<T, INV, N, NL, 0, TAIL>(v, sm, region, L, w, t, tw);
+            odd_finish<T, INV, N, NL, K1, TAIL>(v, sm, region, L, w, t, tw);
         } else {
             L.sync();
-            read_canonical<T, N, NL, 0>(v, sm, region, L, w, t);
+            read_canonical<T, N, NL, K1>(v, sm, region, L, w, t);
             if constexpr (TAIL || L1 + 3 < LOGM || Line<N>::ODD) L.sync();
             Radix8Stages<T, INV, N, L1, NL, HALF_OUT, Layout, TAIL>::run(v, sm, region, L, w, t, tw);
         }

@@ -11,7 +11,7 @@ bool tiles_ok(const Geometry& g, int logW_y, int logW_z, int logW_x) {
     const int ty = line_threads(g.Ly), tz = p3_col_threads(g.Lz);
     if (logW_y < 0 || logW_z < 0 || logW_x < 0) return false;
     if (logW_y > kMaxLogW || logW_z > kMaxLogR || logW_x > kMaxLogZ) return false;
-    if ((1 << logW_y) * ty > kYThreads || 3ull * (1ull << logW_y) * col_elems(g.Ly, 1) * elt > 200 * 1024) return false;
+    if ((1 << logW_y) * ty > kYThreads || 3ull * col_elems(g.Ly, 1 << logW_y) * elt > 200 * 1024) return false;
     if ((1 << logW_z) * tz > p3_max_threads<T>(g.Lz) ||
         3ull * (1ull << logW_z) * row_ld(g.Lz, p3_line_threads(g.Lz)) * elt > 200 * 1024)
         return false;
@@ -29,7 +29,7 @@ void configure_matvec(MatvecView<T>& mv) {
     // P1/P5: W adjacent columns (64-byte rows)
     int wy = floor_log2(64 / elt);
     while (wy > 0 && (1 << wy) * ty > kYThreads) --wy;
-    while (wy > 0 && 3ull * (1ull << wy) * col_elems(g.Ly, 1) * elt > 200 * 1024) --wy;   // P1's three regions
+    while (wy > 0 && 3ull * col_elems(g.Ly, 1 << wy) * elt > 200 * 1024) --wy;   // P1's three regions
     while (wy > 0 && (1 << (wy - 1)) >= g.K) --wy;          // no wider than the lattice
     // P3: the fewest whole columns per CTA that fill at least two warps
     // exactly (small independent CTAs, many per SM)

@@ -188,6 +188,13 @@ __host__ __device__ constexpr int rows_groups(int N, int Wz) {
     return map_wide(N) && Wz * map_threads(N) < 128 ? 128 / (Wz * map_threads(N)) : 1;
 }
 
+// elements of one P2/P4 tile of Wz rows: the 8-point mapping's tile, or for
+// a wide mapping one with the pad its exchanges use (after every V points
+// for 2^a rows, every 8 for 3 * 2^a and 5 * 2^a rows)
+__host__ __device__ constexpr int rows_tile_elems(int N, int Wz) {
+    return !map_wide(N) ? col_elems(N, Wz) : col_elems_sh(N, Wz, wide_len(N) ? 3 : log2c(wide_points(N)));
+}
+
 template <typename T, bool INV, int N, int LOGZ>
 __global__ void __launch_bounds__(rows_max_threads(N)) k_rows(MatvecView<T> mv) {
     const int c = blockIdx.z % 3, j = blockIdx.z / 3;      // component, batch slot
@@ -197,7 +204,7 @@ __global__ void __launch_bounds__(rows_max_threads(N)) k_rows(MatvecView<T> mv) 
     constexpr int G = rows_groups(N, Wz);
     const Geometry& g = mv.g;
     const int w = threadIdx.x & (Wz - 1), t = (threadIdx.x >> LOGZ) % TL, gi = (threadIdx.x >> LOGZ) / TL;
-    C<T>* sm = reinterpret_cast<C<T>*>(smem_raw) + gi * col_elems(N, Wz);
+    C<T>* sm = reinterpret_cast<C<T>*>(smem_raw) + gi * rows_tile_elems(N, Wz);
     const int y = blockIdx.y, z = (blockIdx.x * G + gi) * Wz + w;
     const bool ok = z < g.P;
     C<T>* row = mv.Ay + j * ay_elems(g) + ((c * g.P + (ok ? z : 0)) * g.Ly + y) * g.K;
@@ -528,7 +535,7 @@ int launch_p1(const MatvecView<T>& mv, const C<T>* p, cudaStream_t st) {
 }
 
 // shared memory of a P2/P4 CTA of Wz rows
-inline size_t rows_smem_elems(int N, int Wz) { return (size_t)rows_groups(N, Wz) * col_elems(N, Wz); }
+inline size_t rows_smem_elems(int N, int Wz) { return (size_t)rows_groups(N, Wz) * rows_tile_elems(N, Wz); }
 
 template <typename T, bool INV, int N, int LOGZ>
 int launch_rows_w(const MatvecView<T>& mv, cudaStream_t st) {
