@@ -41,7 +41,7 @@
 // Lines of 3 * 2^a and 5 * 2^a points can also use the wide mapping below
 // (M/8 threads of 8R points per line; fft_wide), which needs one exchange
 // fewer and no shared-memory closing stage; fft_line picks the mapping
-// of Map<N>.
+// of Map<T, N>.
 //
 // Lines shorter than 8 points (lattice edges of 1 or 2 sites) are done by
 // one thread each in registers.  Twiddles come from the FP64 table
@@ -110,24 +110,30 @@ struct Wide {
     static constexpr int KEY0 = (!ODD && V >= 16) ? 100 + log2c(V) : 0;
 };
 
-// thread mapping the x pass uses for N-point lines: a wide one for
-// 3 * 2^a and 5 * 2^a and for 2^a >= 128, eight points per thread below
-template <int N>
+// thread mapping the x pass uses for N-point lines of element type C<T>: a
+// wide one for 3 * 2^a and 5 * 2^a, and for complex64 2^a lines from 128
+// points; eight points per thread otherwise (the complex128 passes are
+// bound by the FP64 units, where the one-exchange 2^a form measured slower:
+// 10.0 against 9.5 ms for P2 at 256^3)
+template <typename T, int N>
 struct Map {
-    static constexpr bool WIDE = Line<N>::ODD || N >= 128;
-    static constexpr int T = WIDE ? Wide<N>::T : Line<N>::T;      // threads per line
+    static constexpr bool WIDE = Line<N>::ODD || (N >= 128 && sizeof(T) == 4);
+    static constexpr int T_ = WIDE ? Wide<N>::T : Line<N>::T;      // threads per line
     static constexpr int V = WIDE ? Wide<N>::V : 8;               // register slots per thread
     static constexpr int NV = WIDE ? Wide<N>::V : Line<N>::NV;    // points held (N < 8: N)
     static constexpr int NH = WIDE ? Wide<N>::V / 2 : Line<N>::NH; // points of the first half
 };
 // threads per N-point line of the 8-point mapping, for host code
 __host__ __device__ constexpr int line_threads(int N) { return N >= 8 ? N / 8 : 1; }
-// whether Map<N> is a wide mapping, its points and threads per line
-__host__ __device__ constexpr bool map_wide(int N) { return N % 3 == 0 || N % 5 == 0 || N >= 128; }
+// whether Map<T, N> (c128: complex128) is a wide mapping, its points and
+// threads per line
+__host__ __device__ constexpr bool map_wide(int N, bool c128) { return N % 3 == 0 || N % 5 == 0 || (N >= 128 && !c128); }
 __host__ __device__ constexpr int wide_points(int N) {
     return (N % 3 == 0) ? 24 : (N % 5 == 0) ? 40 : 1 << ((log2c(N) + 1) / 2);
 }
-__host__ __device__ constexpr int map_threads(int N) { return map_wide(N) ? N / wide_points(N) : line_threads(N); }
+__host__ __device__ constexpr int map_threads(int N, bool c128) {
+    return map_wide(N, c128) ? N / wide_points(N) : line_threads(N);
+}
 
 // Shared-memory layouts.  An address comes from at<KEY>(w, p) (line w,
 // point p), where KEY is log2 of Ns of the stage that writes the exchange;
@@ -769,11 +775,11 @@ __device__ __forceinline__ void fft_wide(C<T> (&v)[Wide<N>::V], C<T>* __restrict
     }
 }
 
-// one line in the mapping Map<N> chooses (v[m] = x[t + Map<N>::T m])
+// one line in the mapping Map<T, N> chooses (v[m] = x[t + Map<T, N>::T_ m])
 template <typename T, bool INV, int N, bool HALF_IN, bool HALF_OUT, bool TAIL = true, class Layout>
-__device__ __forceinline__ void fft_line(C<T> (&v)[Map<N>::V], C<T>* __restrict__ sm, const Layout& L, int w,
+__device__ __forceinline__ void fft_line(C<T> (&v)[Map<T, N>::V], C<T>* __restrict__ sm, const Layout& L, int w,
                                          int t, const C<T>* __restrict__ tw) {
-    if constexpr (Map<N>::WIDE) fft_wide<T, INV, N, HALF_IN, TAIL>(v, sm, L, w, t, tw);
+    if constexpr (Map<T, N>::WIDE) fft_wide<T, INV, N, HALF_IN, TAIL>(v, sm, L, w, t, tw);
     else fft_regs<T, INV, N, HALF_IN, HALF_OUT, TAIL>(v, sm, L, w, t, tw);
 }
 

@@ -15,8 +15,9 @@ bool tiles_ok(const Geometry& g, int logW_y, int logW_z, int logW_x) {
     if ((1 << logW_z) * tz > p3_max_threads<T>(g.Lz) ||
         3ull * (1ull << logW_z) * row_ld(g.Lz, p3_line_threads(g.Lz)) * elt > 200 * 1024)
         return false;
-    if (rows_groups(g.Lx, 1 << logW_x) * (1 << logW_x) * map_threads(g.Lx) > rows_max_threads(g.Lx) ||
-        rows_smem_elems(g.Lx, 1 << logW_x) * elt > 200 * 1024)
+    const bool c128 = sizeof(T) == 8;
+    if (rows_groups(g.Lx, 1 << logW_x, c128) * (1 << logW_x) * map_threads(g.Lx, c128) > rows_max_threads(g.Lx, c128) ||
+        rows_smem_elems(g.Lx, 1 << logW_x, c128) * elt > 200 * 1024)
         return false;
     return true;
 }

@@ -69,9 +69,9 @@ template <typename T> __host__ __device__ constexpr int p3_max_threads(int N) {
 }
 // threads of one z column in P3: its three components share the T = N/8
 // threads of the 8-point mapping, or take 3 x M/8 in the wide one
-__host__ __device__ constexpr int p3_col_threads(int N) { return wide_len(N) ? 3 * map_threads(N) : line_threads(N); }
+__host__ __device__ constexpr int p3_col_threads(int N) { return wide_len(N) ? 3 * map_threads(N, false) : line_threads(N); }
 // threads of one z line in P3 (what its shared-memory pads are laid out for)
-__host__ __device__ constexpr int p3_line_threads(int N) { return wide_len(N) ? map_threads(N) : line_threads(N); }
+__host__ __device__ constexpr int p3_line_threads(int N) { return wide_len(N) ? map_threads(N, false) : line_threads(N); }
 // widest tiles the runtime widths of P3 (columns per CTA) and P2/P4 (z lines
 // per CTA) may take, as log2
 constexpr int kMaxLogR = 6;
@@ -82,7 +82,7 @@ constexpr int kMaxLogZ = 4;
 // registers for them
 constexpr int kRowThreads = 1024;
 constexpr int kRowThreadsWide = 256;
-__host__ __device__ constexpr int rows_max_threads(int N) { return map_wide(N) ? kRowThreadsWide : kRowThreads; }
+__host__ __device__ constexpr int rows_max_threads(int N, bool c128) { return map_wide(N, c128) ? kRowThreadsWide : kRowThreads; }
 
 // P1 and P5 keep the eight points, their gather indices and (P5) the
 // gathered entries of p in registers: at most 512 threads per CTA leave
@@ -179,32 +179,33 @@ __global__ void __launch_bounds__(kYThreads) k_p1(MatvecView<T> mv, const C<T>* 
 // run w-fastest (w = z offset, t = point slot), so each load or store of
 // the column side touches Wz consecutive z values of one x (32 bytes and
 // more), and the row side whole 32-byte sectors of Wz rows.  A CTA holds
-// rows_groups(N, Wz) tiles of consecutive z (more than one only for the
+// rows_groups(N, Wz, c128) tiles of consecutive z (more than one only for the
 // wide mappings, whose few threads per line would otherwise make CTAs of a
 // warp or less), each with its own region of shared memory.
 // Forward (P2): Ay rows -> transform -> Bxy.  Inverse (P4): Bxy ->
 // transform -> the first K outputs into Ay.  Grid: (z tiles, Ly, 3 nb).
-__host__ __device__ constexpr int rows_groups(int N, int Wz) {
-    return map_wide(N) && Wz * map_threads(N) < 128 ? 128 / (Wz * map_threads(N)) : 1;
+__host__ __device__ constexpr int rows_groups(int N, int Wz, bool c128) {
+    return map_wide(N, c128) && Wz * map_threads(N, c128) < 128 ? 128 / (Wz * map_threads(N, c128)) : 1;
 }
 
 // elements of one P2/P4 tile of Wz rows: the 8-point mapping's tile, or for
 // a wide mapping one with the pad its exchanges use (after every V points
 // for 2^a rows, every 8 for 3 * 2^a and 5 * 2^a rows)
-__host__ __device__ constexpr int rows_tile_elems(int N, int Wz) {
-    return !map_wide(N) ? col_elems(N, Wz) : col_elems_sh(N, Wz, wide_len(N) ? 3 : log2c(wide_points(N)));
+__host__ __device__ constexpr int rows_tile_elems(int N, int Wz, bool c128) {
+    return !map_wide(N, c128) ? col_elems(N, Wz) : col_elems_sh(N, Wz, wide_len(N) ? 3 : log2c(wide_points(N)));
 }
 
 template <typename T, bool INV, int N, int LOGZ>
-__global__ void __launch_bounds__(rows_max_threads(N)) k_rows(MatvecView<T> mv) {
+__global__ void __launch_bounds__(rows_max_threads(N, sizeof(T) == 8)) k_rows(MatvecView<T> mv) {
     const int c = blockIdx.z % 3, j = blockIdx.z / 3;      // component, batch slot
     if (rhs_done(mv, mv.b0 + j)) return;
     extern __shared__ unsigned char smem_raw[];
-    constexpr int TL = Map<N>::T, V = Map<N>::V, nv = Map<N>::NV, nh = Map<N>::NH, Wz = 1 << LOGZ;
-    constexpr int G = rows_groups(N, Wz);
+    using MP = Map<T, N>;
+    constexpr int TL = MP::T_, V = MP::V, nv = MP::NV, nh = MP::NH, Wz = 1 << LOGZ;
+    constexpr int G = rows_groups(N, Wz, sizeof(T) == 8);
     const Geometry& g = mv.g;
     const int w = threadIdx.x & (Wz - 1), t = (threadIdx.x >> LOGZ) % TL, gi = (threadIdx.x >> LOGZ) / TL;
-    C<T>* sm = reinterpret_cast<C<T>*>(smem_raw) + gi * rows_tile_elems(N, Wz);
+    C<T>* sm = reinterpret_cast<C<T>*>(smem_raw) + gi * rows_tile_elems(N, Wz, sizeof(T) == 8);
     const int y = blockIdx.y, z = (blockIdx.x * G + gi) * Wz + w;
     const bool ok = z < g.P;
     C<T>* row = mv.Ay + j * ay_elems(g) + ((c * g.P + (ok ? z : 0)) * g.Ly + y) * g.K;
@@ -535,16 +536,17 @@ int launch_p1(const MatvecView<T>& mv, const C<T>* p, cudaStream_t st) {
 }
 
 // shared memory of a P2/P4 CTA of Wz rows
-inline size_t rows_smem_elems(int N, int Wz) { return (size_t)rows_groups(N, Wz) * rows_tile_elems(N, Wz); }
+inline size_t rows_smem_elems(int N, int Wz, bool c128) { return (size_t)rows_groups(N, Wz, c128) * rows_tile_elems(N, Wz, c128); }
 
 template <typename T, bool INV, int N, int LOGZ>
 int launch_rows_w(const MatvecView<T>& mv, cudaStream_t st) {
     const Geometry& g = mv.g;
-    constexpr int Wz = 1 << LOGZ, G = rows_groups(N, Wz), threads = G * Wz * Map<N>::T;
-    if constexpr (threads > rows_max_threads(N)) {
+    constexpr bool c128 = sizeof(T) == 8;
+    constexpr int Wz = 1 << LOGZ, G = rows_groups(N, Wz, c128), threads = G * Wz * Map<T, N>::T_;
+    if constexpr (threads > rows_max_threads(N, c128)) {
         return fail(DDA_ERR_ARG, "x pass tile wider than a CTA");
     } else {
-        const size_t sm = rows_smem_elems(N, Wz) * sizeof(C<T>);
+        const size_t sm = rows_smem_elems(N, Wz, c128) * sizeof(C<T>);
         static std::atomic<size_t> smem_set{0};
         if (int rc = set_smem((const void*)k_rows<T, INV, N, LOGZ>, sm, smem_set)) return rc;
         const dim3 grid((unsigned)((g.P + G * Wz - 1) / (G * Wz)), g.Ly, 3 * mv.nb);
