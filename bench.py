@@ -26,8 +26,9 @@ FP64 solves of the same right-hand side with BiCGSTAB and QMR to 1e-5
 (seconds, products, true residuals, the relative differences of the cross
 sections); the two-material LDR ellipsoid in 128^3 with 1,000 timed products
 in each precision; the context set-up (spectrum build) time; the batch of 16
-directions sharing the spectrum; the ballistic-aggregate batching workload;
-the unpruned cuFFT comparison.
+directions sharing the spectrum; the x passes on rows of 160, 192, 320 and
+384 points; the ballistic-aggregate batching workload; the unpruned cuFFT
+comparison.
 
 --impl reference times the oracle (plain FP64 direct sum, O(N_d^2)) on the
 host cores on a bounded sample of the same product: a few hundred rows of
@@ -478,6 +479,8 @@ def extras(args, dda, torch, dev, shape, bits, alpha, nd, pass_ms, khat, pols, m
     out["context_setup"] = timed_setup(dda, torch, dev, shape, bits, alpha)
     if args.ellipsoid_matvecs > 0:
         out["ellipsoid_128"] = ellipsoid_matvecs(dda, torch, dev, args.ellipsoid_matvecs, hbm)
+    if args.row_sweep:
+        out["x_rows"] = x_pass_rows(dda, torch, dev, hbm)
     if args.aggregates:
         out["aggregates"] = aggregates_workload(dda, torch, dev, args, extra=True)
     return out
@@ -592,6 +595,56 @@ def ellipsoid_matvecs(dda, torch, dev, reps, hbm):
             del p, y
     finally:
         dda.dda_free(ctx)
+    return out
+
+
+# x edges whose rows pad to 3 * 2^a and 5 * 2^a points (160, 192, 320, 384)
+ROW_EDGES = (80, 96, 160, 192)
+
+
+def x_pass_rows(dda, torch, dev, hbm, reps=20):
+    """The x passes (P2 forward, P4 inverse) on rows of 3 * 2^a and 5 * 2^a
+    points: full K x 128 x 128 boxes, K in ROW_EDGES, complex64, default
+    tiles, `reps` products after 3 untimed ones; device time per pass from
+    the library's CUDA events, GB/s of the algorithmic bytes A + B."""
+    import numpy as np
+    out = {"what": "P2/P4 on K x 128 x 128 full boxes (rows of 160, 192, 320, 384 points), complex64, "
+                   "algorithmic bytes A + B per pass", "rows": {}}
+    m = 1.33 + 0.05j
+    k = 0.5 / abs(m)
+    alpha = dda.dda_polarizability([m], k, "cmrr")
+    for K in ROW_EDGES:
+        J = P = 128
+        mask = np.ones((P, J, K), dtype=np.uint8)
+        md = torch.from_numpy(mask.reshape(-1)).to(dev)
+        bits = torch.empty((mask.size + 31) // 32, dtype=torch.int32, device=dev)
+        dda.dda_pack_occupancy(md, bits)
+        ctx = dda.dda_init_lattice((K, J, P), bits, None, 1, alpha, k)
+        try:
+            q = dda.dda_query(ctx)
+            nd = q["n_dipoles"]
+            Lx, Ly, _ = q["padded"]
+            g = torch.Generator(device="cpu").manual_seed(SEED + K)
+            p = torch.randn((3, nd), dtype=torch.complex64, generator=g).to(dev)
+            y = torch.empty_like(p)
+            for _ in range(3):
+                dda.dda_matvec(ctx, p, y)
+            torch.cuda.synchronize(dev)
+            dda.dda_profile(ctx, True)
+            for _ in range(reps):
+                dda.dda_matvec(ctx, p, y)
+            torch.cuda.synchronize(dev)
+            prof = dda.dda_profile_read(ctx)["c64"]
+            dda.dda_profile(ctx, False)
+            ms = [t / c for c, t in prof]
+            b = 3 * Ly * P * (K + Lx) * 8
+            out["rows"][str(Lx)] = {"lattice": [K, J, P], "P2_ms": ms[1], "P4_ms": ms[3],
+                                    "P2_GBps": b / (ms[1] / 1e3) / 1e9, "P4_GBps": b / (ms[3] / 1e3) / 1e9,
+                                    "P2_frac_of_hbm": b / (ms[1] / 1e3) / 1e9 / hbm,
+                                    "tiles": list(dda.dda_tiles(ctx, "c64"))}
+            del p, y
+        finally:
+            dda.dda_free(ctx)
     return out
 
 
@@ -967,6 +1020,8 @@ def main():
                     help="skip the mixed-vs-FP64 BiCGSTAB and QMR solves of the extras")
     ap.add_argument("--ellipsoid-matvecs", type=int, default=1000,
                     help="timed products per precision on the 128^3 two-material ellipsoid (0: skip)")
+    ap.add_argument("--no-row-sweep", dest="row_sweep", action="store_false",
+                    help="skip the x-pass sweep over rows of 160, 192, 320 and 384 points")
     ap.add_argument("--no-aggregates", dest="aggregates", action="store_false",
                     help="skip the ballistic-aggregate batching workload of the extras")
     ap.add_argument("--agg-method", default="bicgstab")

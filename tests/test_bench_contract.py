@@ -72,8 +72,9 @@ def test_our_arm_contract():
     assert d["unpruned_cufft"]["c64"]["rel_diff_vs_library"] < 2e-5
     assert d["job"]["status"] == [0]
     # the extras of the default line: mixed against FP64 on the same right-hand
-    # side (BiCGSTAB and QMR), the set-up time, the two-material ellipsoid
-    # and the aggregate workload
+    # side (BiCGSTAB and QMR), the set-up time, the two-material ellipsoid,
+    # the x passes on rows of 3 * 2^a and 5 * 2^a points and the aggregate
+    # workload
     mv = d["mixed_vs_fp64"]
     for method in ("bicgstab", "qmr"):
         r = mv[method]
@@ -85,4 +86,8 @@ def test_our_arm_contract():
         assert d["ellipsoid_128"][name]["matvecs_per_s"] > 0
     agg = d["aggregates"]
     assert agg["solves"] == 4 and agg["value"] > 0 and agg["aggregates"][0]["status"] == [0]
+    rows = d["x_rows"]["rows"]
+    assert sorted(rows, key=int) == ["160", "192", "320", "384"]
+    for r in rows.values():
+        assert r["P2_ms"] > 0 and r["P4_ms"] > 0 and r["P2_GBps"] > 0
     assert d["e2e"]["steps"] >= 1
