@@ -67,7 +67,13 @@ typedef enum {
     DDA_ERR_NAN = -6             /* non-finite value met                    */
 } dda_status;
 
-typedef enum { DDA_C128 = 0, DDA_C64 = 1 } dda_dtype;
+/* DDA_C128DF: complex128 vectors, the product computed in double-float
+ * arithmetic (each real the unevaluated sum of two floats, about 48
+ * significant bits, on the FP32 units; tables and spectrum split from the
+ * FP64 ones).  A choice of this library for the true residuals of the
+ * mixed-precision refinement (dda_residual_dtype); the paper computes in
+ * double precision throughout. */
+typedef enum { DDA_C128 = 0, DDA_C64 = 1, DDA_C128DF = 2 } dda_dtype;
 /* Krylov schemes of Sec. 4 (products with A per iteration in brackets):
  * BiCG [2], BiCGSTAB [2], QMR with coupled two-term recurrences [2],
  * BiCG for complex-symmetric systems "BiCG_sym" [1], CG with the bilinear
@@ -103,7 +109,7 @@ typedef enum { DDA_POL_CM = 0, DDA_POL_CMRR = 1, DDA_POL_LDR = 2 } dda_polarizab
 typedef struct {
     int iterations;           /* Krylov iterations (inner ones summed, mixed)   */
     int matvecs;              /* products with A in the working precision        */
-    int matvecs_fp64;         /* FP64 products (mixed: true-residual products)   */
+    int matvecs_fp64;         /* FP64 products (mixed: true-residual products, double-float by default) */
     int refinements;          /* outer refinement steps (mixed), 0 for FP64      */
     double rel_residual;      /* last recurrence residual / ||E_inc||            */
     double rel_residual_true; /* ||E_inc - A P|| / ||E_inc|| with an FP64 product */
@@ -213,7 +219,9 @@ int dda_tensor_spectrum(const dda_ctx* ctx, void* out, int dtype, void* stream);
  * along x keeping i < K, inverse along y keeping j < J, add alpha^-1 p and
  * compress.  p, y: device [3][N_d] complex of the given dtype; p and y may
  * not overlap.  DDA_C64 runs every step in complex FP32 with the complex64
- * spectrum.  Returns DDA_ERR_ARG for NULL or host pointers.
+ * spectrum; DDA_C128DF takes complex128 p and y and runs every step in
+ * double-float arithmetic (relative error about 1e-13 against 1e-15 for
+ * DDA_C128).  Returns DDA_ERR_ARG for NULL or host pointers.
  */
 int dda_matvec(dda_ctx* ctx, const void* p, void* y, int dtype, void* stream);
 
@@ -268,6 +276,20 @@ int dda_autotune(dda_ctx* ctx, int dtype, int nb, int reps, double* pass_ms, voi
  * This is a choice of this library (the paper runs one precision only).
  */
 int dda_inner_tolerance(dda_ctx* ctx, const double* rho_in, double* rho_out);
+
+/*
+ * Products of the true residuals r = einc - A x in the mixed-precision
+ * refinement (dda_solve, dda_solve_batch with DDA_MIXED): DDA_C128DF
+ * (default: double-float products, about 48 significant bits, a few times
+ * faster than FP64 on this GPU, whose FP64 rate is a small fraction of its
+ * FP32 rate) or DDA_C128 (FP64 products).  The double-float product is
+ * accurate to about 1e-13 relative to |A||x|, so residual tolerances down
+ * to about 1e-11 behave as with FP64 products.  dtype_in (host, may be
+ * NULL) sets the choice, dtype_out (host, may be NULL) receives it.  The
+ * FP64 solves always use FP64 products.  DDA_ERR_ARG for another dtype.
+ * This is a choice of this library (the paper runs one precision only).
+ */
+int dda_residual_dtype(dda_ctx* ctx, const int* dtype_in, int* dtype_out);
 
 /*
  * Tune rho of dda_inner_tolerance on this context: solve A P = einc (host

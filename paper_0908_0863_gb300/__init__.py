@@ -20,7 +20,7 @@ from ._lib import (  # noqa: F401
     dda_last_error, dda_matvec_batch, dda_reserve, dda_solve_batch, dda_tiles, dda_autotune,
     dda_launch_count, dda_polarizability_derivative, dda_scattering_cross_section,
     dda_matvec, dda_occupancy_ranks_static, dda_pack_composition, dda_pack_occupancy, dda_polarizability,
-    dda_profile, dda_profile_read, dda_material_sums, dda_inner_tolerance, dda_autotune_inner, DDA_POL_EPS, DDA_MLBICGSTAB1, DDA_MLBICGSTAB2,
+    dda_profile, dda_profile_read, dda_material_sums, dda_inner_tolerance, dda_autotune_inner, dda_residual_dtype, DDA_C128DF, DDA_POL_EPS, DDA_MLBICGSTAB1, DDA_MLBICGSTAB2,
     DDA_MLBICGSTAB3,
     dda_query, dda_site_ranks, dda_solve, dda_tensor_spectrum, dda_unpack_composition, dda_unpack_occupancy,
     library_path, load,

@@ -24,6 +24,7 @@ DDA_ERR_BREAKDOWN = -5
 DDA_ERR_NAN = -6
 DDA_C128 = 0
 DDA_C64 = 1
+DDA_C128DF = 2   # complex128 vectors, double-float products
 DDA_BICG, DDA_BICGSTAB, DDA_QMR, DDA_BICG_SYM = 0, 1, 2, 3
 DDA_CG, DDA_CGS, DDA_TFQMR, DDA_QMR_SYM = 4, 5, 6, 7
 DDA_RBICGSTAB1, DDA_RBICGSTAB2, DDA_RBICGSTAB3 = 8, 9, 10
@@ -59,7 +60,7 @@ EXPORTS = (
     "dda_unpack_composition", "dda_init_lattice", "dda_free", "dda_query", "dda_site_ranks",
     "dda_tensor_spectrum", "dda_matvec", "dda_incident_field", "dda_solve", "dda_cross_sections",
     "dda_profile", "dda_profile_read", "dda_launch_count", "dda_last_error", "dda_occupancy_ranks_static",
-    "dda_material_sums", "dda_inner_tolerance", "dda_autotune_inner",
+    "dda_material_sums", "dda_inner_tolerance", "dda_autotune_inner", "dda_residual_dtype",
     "dda_scattering_cross_section", "dda_polarizability_derivative", "dda_gradient",
     "dda_matvec_batch", "dda_reserve", "dda_solve_batch", "dda_cross_sections_batch", "dda_tiles",
     "dda_autotune",
@@ -122,6 +123,7 @@ def load(path: str | None = None):
     L.dda_occupancy_ranks_static.argtypes = [vp, i64, vp, vp, vp]
     L.dda_material_sums.argtypes = [vp, vp, vp, vp]
     L.dda_inner_tolerance.argtypes = [vp, vp, vp]
+    L.dda_residual_dtype.argtypes = [vp, vp, vp]
     L.dda_autotune_inner.argtypes = [vp, vp, i32, ctypes.c_double, i32, vp, vp, vp]
     L.dda_scattering_cross_section.argtypes = [vp, vp, vp, vp]
     L.dda_polarizability_derivative.argtypes = [i32, vp, d, i32, vp, vp, vp]
@@ -247,22 +249,33 @@ def dda_tensor_spectrum(ctx, out, stream=None):
     _check(load().dda_tensor_spectrum(ctypes.c_void_p(ctx), _ptr(out), _dtype_code(out), _stream(stream)))
 
 
-def dda_matvec(ctx, p, y, stream=None):
+def _product_code(p, dtype):
+    # dtype None: the tensors' precision; "c128df": double-float products of
+    # complex128 tensors
+    if dtype is None:
+        return _dtype_code(p)
+    code = _dtype_name(dtype)
+    if code == DDA_C128DF and _dtype_code(p) != DDA_C128:
+        raise TypeError("double-float products take complex128 vectors")
+    return code
+
+
+def dda_matvec(ctx, p, y, stream=None, dtype=None):
     if p.dtype != y.dtype:
         raise TypeError("p and y must have the same dtype")
-    _check(load().dda_matvec(ctypes.c_void_p(ctx), _ptr(p), _ptr(y), _dtype_code(p), _stream(stream)))
+    _check(load().dda_matvec(ctypes.c_void_p(ctx), _ptr(p), _ptr(y), _product_code(p, dtype), _stream(stream)))
 
 
-def dda_matvec_batch(ctx, p, y, stream=None):
+def dda_matvec_batch(ctx, p, y, stream=None, dtype=None):
     """y[b] = A p[b] for p, y of shape (nb, 3, N_d) (device, same complex dtype)."""
     if p.dtype != y.dtype or p.shape != y.shape:
         raise TypeError("p and y must have the same dtype and shape")
-    _check(load().dda_matvec_batch(ctypes.c_void_p(ctx), int(p.shape[0]), _ptr(p), _ptr(y), _dtype_code(p),
+    _check(load().dda_matvec_batch(ctypes.c_void_p(ctx), int(p.shape[0]), _ptr(p), _ptr(y), _product_code(p, dtype),
                                    _stream(stream)))
 
 
 def _dtype_name(dtype):
-    return {"c128": DDA_C128, "c64": DDA_C64}.get(dtype, dtype)
+    return {"c128": DDA_C128, "c64": DDA_C64, "c128df": DDA_C128DF}.get(dtype, dtype)
 
 
 def dda_tiles(ctx, dtype="c64", tiles=None):
@@ -367,6 +380,15 @@ def dda_inner_tolerance(ctx, rho=None) -> float:
     out = np.zeros(1)
     _check(load().dda_inner_tolerance(ctypes.c_void_p(ctx), _ptr(rin), _ptr(out)))
     return float(out[0])
+
+
+def dda_residual_dtype(ctx, dtype=None) -> str:
+    """Products of the mixed refinement's true residuals: "c128df" (double-float,
+    the default) or "c128" (FP64); set first when given."""
+    din = None if dtype is None else np.array([_dtype_name(dtype)], dtype=np.int32)
+    out = np.zeros(1, dtype=np.int32)
+    _check(load().dda_residual_dtype(ctypes.c_void_p(ctx), _ptr(din), _ptr(out)))
+    return {DDA_C128: "c128", DDA_C128DF: "c128df"}[int(out[0])]
 
 
 def dda_autotune_inner(ctx, einc, method="bicgstab", tol=1e-5, max_iter=4000, stream=None):

@@ -123,14 +123,18 @@ struct dda_ctx {
     float2* spec32 = nullptr;
     double2* tw64 = nullptr;
     float2* tw32 = nullptr;
+    // the same tables for the double-float product (df.cuh)
+    cdf *ainv_df = nullptr, *jac_df = nullptr, *spec_df = nullptr, *tw_df = nullptr;
     double2* xsec = nullptr;
     double2* msum = nullptr;  // per-material sums: block partials, then the sums
     double2* aux[3] = {};     // adjoint / C_sca work vectors (P, right-hand side, mu)
     double2* dainv64 = nullptr;  // d(alpha^-1)/d eps table of the last gradient call
     Space sp;
     double inner_rho = 0.0;      // mixed precision: smallest residual reduction an inner solve aims at (0: none)
+    int residual_dtype = DDA_C128DF;   // mixed precision: products of the true residuals
     MatvecView<double> mv64{};   // geometry, tables and tiles; work set per call
     MatvecView<float> mv32{};
+    MatvecView<DF> mvdf{};
     PassProfiler prof;
 };
 
@@ -288,6 +292,18 @@ MatvecView<double> view64(const dda_ctx* c, int nb) {
     MatvecView<double> m = c->mv64;
     m.slots = c->sp.slots64;
     m.Ay = static_cast<double2*>(c->sp.work);
+    m.Bxy = m.Ay + (size_t)m.slots * 3ull * c->g.P * c->g.Ly * c->g.K;
+    m.nb = nb;
+    m.vstride = 3 * c->g.nd;
+    m.status = nullptr;
+    m.conj = 0;
+    return m;
+}
+// the double-float product uses the complex128 work slots (16-byte elements)
+MatvecView<DF> viewdf(const dda_ctx* c, int nb) {
+    MatvecView<DF> m = c->mvdf;
+    m.slots = c->sp.slots64;
+    m.Ay = static_cast<cdf*>(c->sp.work);
     m.Bxy = m.Ay + (size_t)m.slots * 3ull * c->g.P * c->g.Ly * c->g.K;
     m.nb = nb;
     m.vstride = 3 * c->g.nd;
@@ -493,6 +509,10 @@ int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occu
         probe.take<float2>(nspec);
         probe.take<double2>(kTwEntries);
         probe.take<float2>(kTwEntries);
+        probe.take<cdf>(3 * (size_t)n_materials);
+        probe.take<cdf>(3 * (size_t)n_materials);
+        probe.take<cdf>(nspec);
+        probe.take<cdf>(kTwEntries);
         probe.take<double2>(xsec_scratch_elems());
         probe.take<double2>(material_sums_scratch_elems(g));
         probe.take<int>(4);
@@ -514,6 +534,10 @@ int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occu
     c->spec32 = a0.take<float2>(nspec);
     c->tw64 = a0.take<double2>(kTwEntries);
     c->tw32 = a0.take<float2>(kTwEntries);
+    c->ainv_df = a0.take<cdf>(3 * (size_t)n_materials);
+    c->jac_df = a0.take<cdf>(3 * (size_t)n_materials);
+    c->spec_df = a0.take<cdf>(nspec);
+    c->tw_df = a0.take<cdf>(kTwEntries);
     c->xsec = a0.take<double2>(xsec_scratch_elems());
     c->msum = a0.take<double2>(material_sums_scratch_elems(g));
     int* flags = a0.take<int>(4);
@@ -559,6 +583,17 @@ int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occu
             t64[m] = make_double2(std::cos(ang), std::sin(ang));
             t32[m] = make_float2((float)t64[m].x, (float)t64[m].y);
         }
+        // double-float copies (each double split into a float and the rounded remainder)
+        auto split = [](const std::vector<double2>& v) {
+            std::vector<cdf> out(v.size());
+            for (size_t i = 0; i < v.size(); ++i) { out[i].x = DF(v[i].x); out[i].y = DF(v[i].y); }
+            return out;
+        };
+        const std::vector<cdf> aidf = split(ai), sjdf = split(sj), twdf = split(t64);
+        if (cudaMemcpyAsync(c->ainv_df, aidf.data(), aidf.size() * sizeof(cdf), cudaMemcpyHostToDevice, st) ||
+            cudaMemcpyAsync(c->jac_df, sjdf.data(), sjdf.size() * sizeof(cdf), cudaMemcpyHostToDevice, st) ||
+            cudaMemcpyAsync(c->tw_df, twdf.data(), twdf.size() * sizeof(cdf), cudaMemcpyHostToDevice, st))
+            return bail(fail(DDA_ERR_CUDA, "dda_init_lattice: table upload"));
         if (cudaMemcpyAsync(c->ainv64, ai.data(), ai.size() * sizeof(double2), cudaMemcpyHostToDevice, st) ||
             cudaMemcpyAsync(c->ainv32, af.data(), af.size() * sizeof(float2), cudaMemcpyHostToDevice, st) ||
             cudaMemcpyAsync(c->jac64, sj.data(), sj.size() * sizeof(double2), cudaMemcpyHostToDevice, st) ||
@@ -576,6 +611,7 @@ int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occu
         if (e != cudaSuccess) return bail(cuda_fail(e, "dda_init_lattice: spectrum scratch"));
         double2* s0 = static_cast<double2*>(tmp);
         rc = build_spectrum(g, k, c->tw64, s0, s0 + ns, c->spec64, c->spec32, st);
+        if (!rc) rc = spectrum_to_df(c->spec64, c->spec_df, nspec, st);
         cudaError_t e2 = cudaStreamSynchronize(st);
         cudaFree(tmp);
         if (rc) return bail(rc);
@@ -613,6 +649,10 @@ int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occu
         f.g = g; f.tv = tv; f.ainv = c->ainv32; f.spec = c->spec32; f.tw = c->tw32;
         f.status = nullptr; f.conj = 0; f.prof = &c->prof;
         configure_matvec<float>(f);
+        MatvecView<DF>& d = c->mvdf;
+        d.g = g; d.tv = tv; d.ainv = c->ainv_df; d.spec = c->spec_df; d.tw = c->tw_df;
+        d.status = nullptr; d.conj = 0; d.prof = nullptr;
+        configure_matvec<DF>(d);
         std::lock_guard<std::mutex> lock(g_tiles_mu);
         auto it = g_tiles.find(tile_key(g, DDA_C128));
         if (it != g_tiles.end()) apply_tiles(m, it->second);
@@ -675,15 +715,17 @@ int dda_matvec_batch(dda_ctx* c, int nb, const void* p, void* y, int dtype, void
     if (nb < 1 || nb > kMaxBatch) return fail(DDA_ERR_ARG, "dda_matvec: nb must be in [1, 4096]");
     if (int rc = check_dev(p, "dda_matvec: p")) return rc;
     if (int rc = check_dev(y, "dda_matvec: y")) return rc;
-    const size_t esize = dtype == DDA_C128 ? sizeof(double2) : sizeof(float2);
+    if (dtype != DDA_C128 && dtype != DDA_C64 && dtype != DDA_C128DF) return fail(DDA_ERR_ARG, "dda_matvec: unknown dtype");
+    const size_t esize = dtype == DDA_C64 ? sizeof(float2) : sizeof(double2);
     const char *pb = static_cast<const char*>(p), *yb = static_cast<const char*>(y);
     const size_t span = (size_t)nb * 3 * c->g.nd * esize;
     if (pb < yb + span && yb < pb + span) return fail(DDA_ERR_ARG, "dda_matvec: p and y must not overlap");
-    if (dtype != DDA_C128 && dtype != DDA_C64) return fail(DDA_ERR_ARG, "dda_matvec: unknown dtype");
     if (int rc = ensure_work(c->sp, c->g, nb)) return rc;
     cudaStream_t st = as_stream(stream);
     if (dtype == DDA_C128)
         return launch_matvec<double>(view64(c, nb), static_cast<const double2*>(p), static_cast<double2*>(y), st);
+    if (dtype == DDA_C128DF)
+        return launch_matvec<DF>(viewdf(c, nb), static_cast<const double2*>(p), static_cast<double2*>(y), st);
     return launch_matvec<float>(view32(c, nb), static_cast<const float2*>(p), static_cast<float2*>(y), st);
 }
 
@@ -866,6 +908,23 @@ static int worst_status(const int* st, int nb) {
     return w;
 }
 
+// y = A x for the true residuals of the mixed refinement (x, y: the
+// workspace's complex128 x and r vectors): double-float products
+// (df.cuh, about 48 significant bits on the FP32 units) or FP64 ones, as
+// set by dda_residual_dtype; right-hand sides whose control word is set are
+// skipped when ctl is given
+static int residual_product(dda_ctx* c, int nb, const RhsCtl* ctl, cudaStream_t st) {
+    Space& sp = c->sp;
+    if (c->residual_dtype == DDA_C128DF) {
+        MatvecView<DF> m = viewdf(c, nb);
+        if (ctl) { m.status = &ctl[0].skip; m.status_stride = kCtlInts; }
+        return launch_matvec<DF>(m, sp.x64, sp.r64, st);
+    }
+    MatvecView<double> m = view64(c, nb);
+    if (ctl) { m.status = &ctl[0].skip; m.status_stride = kCtlInts; }
+    return launch_matvec<double>(m, sp.x64, sp.r64, st);
+}
+
 // Solves of nb right-hand sides in lock step (vectors [nb][3 N_d]); per-RHS
 // results into inf[] and stat[].  Returns a non-solver error (ARG, CUDA,
 // OOM) or 0.
@@ -919,7 +978,7 @@ static int solve_batch(dda_ctx* c, int nb, const void* einc, void* p, int method
         if (int rc = vec_norm2_c128(sp.b64, n, nb, sp.part64, sp.st64, st)) return rc;
         if (int rc = read_tmp_slots(sp.st64, nb, sp.host, bn2.data(), st)) return rc;
         if (use_x0) {
-            if (int rc = launch_matvec<double>(view64(c, nb), sp.x64, sp.r64, st)) return rc;
+            if (int rc = residual_product(c, nb, nullptr, st)) return rc;
             if (int rc = residual_from_product(sp.b64, sp.r64, n, nb, nullptr, sp.part64, sp.st64, st)) return rc;
             if (int rc = read_tmp_slots(sp.st64, nb, sp.host, rn2.data(), st)) return rc;
             for (int b = 0; b < nb; ++b) inf[b].matvecs_fp64 += 1;
@@ -937,9 +996,6 @@ static int solve_batch(dda_ctx* c, int nb, const void* einc, void* p, int method
         }
         RhsCtl* hc = sp.hctl;
         KrylovWork<float> w = work32(c, nb);
-        MatvecView<double> m64 = view64(c, nb);
-        m64.status = &sp.ctl[0].skip;   // the residual product skips finished right-hand sides
-        m64.status_stride = kCtlInts;
         while (true) {
             bool any = false;
             for (int b = 0; b < nb; ++b) {
@@ -994,7 +1050,8 @@ static int solve_batch(dda_ctx* c, int nb, const void* einc, void* p, int method
             if (changed)
                 DDA_CUDA_TRY(cudaMemcpyAsync(sp.ctl, hc, nb * sizeof(RhsCtl), cudaMemcpyHostToDevice, st));
             if (int rc = axpy_from_c64(sp.x64, sp.ctl, sp.d32, n, nb, st)) return rc;
-            if (int rc = launch_matvec<double>(m64, sp.x64, sp.r64, st)) return rc;
+            // the residual product skips finished right-hand sides
+            if (int rc = residual_product(c, nb, sp.ctl, st)) return rc;
             if (int rc = residual_from_product(sp.b64, sp.r64, n, nb, sp.ctl, sp.part64, sp.st64, st)) return rc;
             std::vector<double> rnew(nb);
             if (int rc = read_tmp_slots(sp.st64, nb, sp.host, rnew.data(), st)) return rc;
@@ -1077,6 +1134,17 @@ int dda_inner_tolerance(dda_ctx* c, const double* rho_in, double* rho_out) {
         c->inner_rho = *rho_in;
     }
     if (rho_out) *rho_out = c->inner_rho;
+    return DDA_OK;
+}
+
+int dda_residual_dtype(dda_ctx* c, const int* dtype_in, int* dtype_out) {
+    if (int rc = check_ctx(c)) return rc;
+    if (dtype_in) {
+        if (*dtype_in != DDA_C128 && *dtype_in != DDA_C128DF)
+            return fail(DDA_ERR_ARG, "dda_residual_dtype: DDA_C128 or DDA_C128DF");
+        c->residual_dtype = *dtype_in;
+    }
+    if (dtype_out) *dtype_out = c->residual_dtype;
     return DDA_OK;
 }
 

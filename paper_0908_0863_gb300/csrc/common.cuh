@@ -7,14 +7,42 @@
 #include <string>
 
 #include "../../include/dda.h"
+#include "df.cuh"
 
 namespace dda {
 
 // ------------------------------------------------------------ complex types
+// complex128, complex64 and complex double-float (df.cuh)
 template <typename T> struct cpx;
 template <> struct cpx<double> { using t = double2; };
 template <> struct cpx<float> { using t = float2; };
+template <> struct cpx<DF> { using t = cdf; };
 template <typename T> using C = typename cpx<T>::t;
+// element type of the vectors a product of element type T reads and writes
+// (the double-float product reads and writes complex128 vectors)
+template <typename T> struct io_of { using t = T; };
+template <> struct io_of<DF> { using t = double; };
+template <typename T> using IO = typename io_of<T>::t;
+template <typename T> __host__ __device__ __forceinline__ C<T> from_io(C<IO<T>> v) { return v; }
+template <> __host__ __device__ __forceinline__ cdf from_io<DF>(double2 v) {
+    cdf z;
+    z.x = DF(v.x);
+    z.y = DF(v.y);
+    return z;
+}
+template <typename T> __host__ __device__ __forceinline__ C<IO<T>> to_io(C<T> v) { return v; }
+template <> __host__ __device__ __forceinline__ double2 to_io<DF>(cdf v) {
+    return make_double2(to_double(v.x), to_double(v.y));
+}
+// read-only cached load of one complex value
+template <typename T> __device__ __forceinline__ C<T> ldg_c(const C<T>* p) { return __ldg(p); }
+template <> __device__ __forceinline__ cdf ldg_c<DF>(const cdf* p) {
+    const float4 f = __ldg(reinterpret_cast<const float4*>(p));
+    cdf z;
+    z.x = DF(f.x, f.y);
+    z.y = DF(f.z, f.w);
+    return z;
+}
 
 template <typename T> __host__ __device__ __forceinline__ C<T> mk(T re, T im) { C<T> z; z.x = re; z.y = im; return z; }
 template <typename T> __host__ __device__ __forceinline__ C<T> cadd(C<T> a, C<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }

@@ -210,7 +210,7 @@ __host__ __device__ constexpr int col_elems(int N, int W) { return col_elems_sh(
 
 template <typename T, bool INV>
 __device__ __forceinline__ C<T> twiddle(const C<T>* __restrict__ tw, int idx) {
-    C<T> t = __ldg(tw + idx);
+    C<T> t = ldg_c<T>(tw + idx);
     if (INV) t.y = -t.y;
     return t;
 }
@@ -584,8 +584,8 @@ __device__ __forceinline__ C<T> cmul_root(C<T> x, int e) {
     if (4 * e == 3 * V) return rot90<T, !INV>(x);
     if ((8 * e) % V == 0) {   // (+-1 +- i) / sqrt(2)
         const T h = (T)0.70710678118654752440;
-        const C<T> r = root_v<T, INV, V>(e);
-        const T c = r.x > 0 ? (T)1 : (T)-1, s = r.y > 0 ? (T)1 : (T)-1;
+        const double cr = cos_v<V>(e), sr = INV ? cos_v<V>(e - V / 4) : -cos_v<V>(e - V / 4);
+        const T c = (T)(cr > 0 ? 1.0 : -1.0), s = (T)(sr > 0 ? 1.0 : -1.0);
         return mk<T>((c * x.x - s * x.y) * h, (c * x.y + s * x.x) * h);
     }
     return cmul<T>(x, root_v<T, INV, V>(e));

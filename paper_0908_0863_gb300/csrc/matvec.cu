@@ -49,7 +49,7 @@ void configure_matvec(MatvecView<T>& mv) {
     mv.logW_x = wx;
 }
 template <typename T>
-static int launch_chunk(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t st) {
+static int launch_chunk(const MatvecView<T>& mv, const C<IO<T>>* p, C<IO<T>>* y, cudaStream_t st) {
     const int dt = sizeof(T) == 8 ? 0 : 1;
     PassProfiler* pf = (mv.prof && mv.prof->on) ? mv.prof : nullptr;
     int rc;
@@ -68,7 +68,7 @@ static int launch_chunk(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStr
 }
 
 template <typename T>
-int launch_matvec(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t st) {
+int launch_matvec(const MatvecView<T>& mv, const C<IO<T>>* p, C<IO<T>>* y, cudaStream_t st) {
     if (mv.nb < 1 || mv.slots < 1) return fail(DDA_ERR_ARG, "matvec: empty batch");
     for (int b0 = 0; b0 < mv.nb; b0 += mv.slots) {
         MatvecView<T> m = mv;
@@ -84,12 +84,16 @@ template <typename T> int pass3(const MatvecView<T>& mv, cudaStream_t st) {
 }
 template int pass3<double>(const MatvecView<double>&, cudaStream_t);
 template int pass3<float>(const MatvecView<float>&, cudaStream_t);
+template int pass3<DF>(const MatvecView<DF>&, cudaStream_t);
 
 template void configure_matvec<double>(MatvecView<double>&);
 template void configure_matvec<float>(MatvecView<float>&);
+template void configure_matvec<DF>(MatvecView<DF>&);
 template bool tiles_ok<double>(const Geometry&, int, int, int);
 template bool tiles_ok<float>(const Geometry&, int, int, int);
+template bool tiles_ok<DF>(const Geometry&, int, int, int);
 template int launch_matvec<double>(const MatvecView<double>&, const C<double>*, C<double>*, cudaStream_t);
 template int launch_matvec<float>(const MatvecView<float>&, const C<float>*, C<float>*, cudaStream_t);
+template int launch_matvec<DF>(const MatvecView<DF>&, const C<double>*, C<double>*, cudaStream_t);
 
 }  // namespace dda

@@ -45,6 +45,7 @@ template <typename T> void configure_matvec(MatvecView<T>& mv);
 // whether tile widths (log2 of lines per CTA of P1/P5, P3 and P2/P4) fit the
 // launch limits (threads per block, shared memory) for this geometry
 template <typename T> bool tiles_ok(const Geometry& g, int logW_y, int logW_z, int logW_x);
-template <typename T> int launch_matvec(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t st);
+// p and y: [nb][3][N_d] vectors of C<IO<T>> (complex128 for the double-float product)
+template <typename T> int launch_matvec(const MatvecView<T>& mv, const C<IO<T>>* p, C<IO<T>>* y, cudaStream_t st);
 
 }  // namespace dda

@@ -103,7 +103,7 @@ __host__ __device__ __forceinline__ int64_t bxy_elems(const Geometry& g) { retur
 
 // ---------------------------------------------------------------- P1
 template <typename T, int N, int LOGW>
-__global__ void __launch_bounds__(kYThreads) k_p1(MatvecView<T> mv, const C<T>* __restrict__ p) {
+__global__ void __launch_bounds__(kYThreads) k_p1(MatvecView<T> mv, const C<IO<T>>* __restrict__ p) {
     // the three components of a site share its occupancy and rank lookup:
     // each thread gathers all three and transforms them as three lines
     const int j = blockIdx.z;                                  // batch slot
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kYThreads) k_p1(MatvecView<T> mv, const C<T>* 
     constexpr int W = 1 << LOGW, region = col_elems(N, W);
     const int w = threadIdx.x & (W - 1), t = threadIdx.x >> LOGW;
     const int i = blockIdx.x * W + w, kz = blockIdx.y;
-    const C<T>* pb = p + (int64_t)b * mv.vstride;
+    const C<IO<T>>* pb = p + (int64_t)b * mv.vstride;
     const int64_t s0 = (int64_t)kz * g.J * g.K + i;
     // the gather as two rounds of independent loads: first the occupancy and
     // rank words of the thread's sites, then their entries of p (three
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(kYThreads) k_p1(MatvecView<T> mv, const C<T>* 
             const int64_t r = rbase[m] + __popc(word[m] & ((1u << bit) - 1u));
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                v[c][m] = pb[c * g.nd + r];
+                v[c][m] = from_io<T>(pb[c * g.nd + r]);
                 if (mv.conj) v[c][m].y = -v[c][m].y;
             }
         }
@@ -261,7 +261,7 @@ __device__ __forceinline__ void load6(const C<T>* __restrict__ p, C<T> (&Y)[6]) 
         }
     } else {
 #pragma unroll
-        for (int i = 0; i < 6; ++i) Y[i] = __ldg(p + i);
+        for (int i = 0; i < 6; ++i) Y[i] = ldg_c<T>(p + i);
     }
 }
 
@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(p3_max_threads<T>(N)) __maxnreg__(sizeof(T) ==
             if (mz > N / 2) break;
             C<T> G[6];
 #pragma unroll
-            for (int q = 0; q < 6; ++q) G[q] = ok ? __ldg(line + q * g.Hz + mz) : mk<T>(0, 0);
+            for (int q = 0; q < 6; ++q) G[q] = ok ? ldg_c<T>(line + q * g.Hz + mz) : mk<T>(0, 0);
             // the point mz (z not mirrored) and, unless mz is 0 or N/2, its
             // mirror N - mz (z mirrored)
 #pragma unroll
@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(p3_max_threads<T>(N)) __maxnreg__(sizeof(T) ==
 
 // ---------------------------------------------------------------- P5
 template <typename T, int N, int LOGW>
-__global__ void __launch_bounds__(kYThreads, sizeof(T) == 4 ? 2 : 1) k_p5(MatvecView<T> mv, const C<T>* __restrict__ p, C<T>* __restrict__ y) {
+__global__ void __launch_bounds__(kYThreads, sizeof(T) == 4 ? 2 : 1) k_p5(MatvecView<T> mv, const C<IO<T>>* __restrict__ p, C<IO<T>>* __restrict__ y) {
     const int c = blockIdx.z % 3, j = blockIdx.z / 3;      // component, batch slot
     const int b = mv.b0 + j;
     if (rhs_done(mv, b)) return;
@@ -462,8 +462,8 @@ __global__ void __launch_bounds__(kYThreads, sizeof(T) == 4 ? 2 : 1) k_p5(Matvec
     // the gather of the thread's sites (first half of the points, J <= N/2)
     // goes out before the transform, which does not depend on it: occupancy
     // and rank words, then the occupied entries of p
-    const C<T>* pc = p + (int64_t)b * mv.vstride + (int64_t)c * g.nd;
-    C<T>* yc = y + (int64_t)b * mv.vstride + (int64_t)c * g.nd;
+    const C<IO<T>>* pc = p + (int64_t)b * mv.vstride + (int64_t)c * g.nd;
+    C<IO<T>>* yc = y + (int64_t)b * mv.vstride + (int64_t)c * g.nd;
     const int64_t s0 = (int64_t)kz * g.J * g.K + i;
     constexpr int nh = Line<N>::NH;
     uint32_t word[nh], rbase[nh];
@@ -475,7 +475,7 @@ __global__ void __launch_bounds__(kYThreads, sizeof(T) == 4 ? 2 : 1) k_p5(Matvec
         word[m] = in ? __ldg(mv.tv.occ + q) : 0u;
         rbase[m] = in ? __ldg(mv.tv.rank + q) : 0u;
     }
-    C<T> pv[nh];
+    C<IO<T>> pv[nh];
 #pragma unroll
     for (int m = 0; m < nh; ++m) {
         const int n = t + m * TL;
@@ -492,7 +492,7 @@ __global__ void __launch_bounds__(kYThreads, sizeof(T) == 4 ? 2 : 1) k_p5(Matvec
         const int64_t s = s0 + (int64_t)(t + m * TL) * g.K;
         const int mat = material(mv.tv, s, c);
         const C<T> a = mv.ainv[mat * 3 + c];
-        C<T> q = pv[m];
+        C<T> q = from_io<T>(pv[m]);
         if (mv.conj) q.y = -q.y;
         C<T> out;
         if (mv.jac) {   // point-Jacobi: S (alpha^-1 S p + conv)
@@ -502,7 +502,7 @@ __global__ void __launch_bounds__(kYThreads, sizeof(T) == 4 ? 2 : 1) k_p5(Matvec
             out = cfma<T>(a, q, v[m]);
         }
         if (mv.conj) out.y = -out.y;
-        yc[rbase[m]] = out;
+        yc[rbase[m]] = to_io<T>(out);
     }
 }
 
@@ -523,7 +523,7 @@ inline int set_smem(const void* fn, size_t bytes, std::atomic<size_t>& done) {
 
 // ------------------------------------------------- per-length launchers
 template <typename T, int N, int LOGW>
-int launch_p1(const MatvecView<T>& mv, const C<T>* p, cudaStream_t st) {
+int launch_p1(const MatvecView<T>& mv, const C<IO<T>>* p, cudaStream_t st) {
     const Geometry& g = mv.g;
     constexpr int W = 1 << LOGW;
     const size_t sm = 3 * (size_t)col_elems(N, W) * sizeof(C<T>);
@@ -587,7 +587,7 @@ int launch_p3(const MatvecView<T>& mv, cudaStream_t st) {
 }
 
 template <typename T, int N, int LOGW>
-int launch_p5(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t st) {
+int launch_p5(const MatvecView<T>& mv, const C<IO<T>>* p, C<IO<T>>* y, cudaStream_t st) {
     const Geometry& g = mv.g;
     constexpr int W = 1 << LOGW;
     const size_t sm = (size_t)col_elems(N, W) * sizeof(C<T>);
@@ -628,12 +628,12 @@ int launch_p5(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t st) 
 constexpr int kMaxLogW = 4;
 
 // per-pass dispatchers (one translation unit each)
-template <typename T> int pass1(const MatvecView<T>& mv, const C<T>* p, cudaStream_t st);
+template <typename T> int pass1(const MatvecView<T>& mv, const C<IO<T>>* p, cudaStream_t st);
 template <typename T, bool INV> int pass_rows(const MatvecView<T>& mv, cudaStream_t st);
 template <typename T> int pass3(const MatvecView<T>& mv, cudaStream_t st);
 // P3 for one line length; each length group is instantiated in its own
 // translation unit (mv_p3_*.cu)
 template <typename T, int N> int p3_len(const MatvecView<T>& mv, cudaStream_t st);
-template <typename T> int pass5(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t st);
+template <typename T> int pass5(const MatvecView<T>& mv, const C<IO<T>>* p, C<IO<T>>* y, cudaStream_t st);
 
 }  // namespace dda

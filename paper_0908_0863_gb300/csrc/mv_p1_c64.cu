@@ -5,11 +5,11 @@
 namespace dda {
 
 template <typename T, int LN>
-static int p1_width(const MatvecView<T>& mv, const C<T>* p, cudaStream_t st) {
+static int p1_width(const MatvecView<T>& mv, const C<IO<T>>* p, cudaStream_t st) {
     DDA_LOGW_SWITCH(mv.logW_y, (launch_p1<T, LN, LW>(mv, p, st)))
 }
 
-template <typename T> int pass1(const MatvecView<T>& mv, const C<T>* p, cudaStream_t st) {
+template <typename T> int pass1(const MatvecView<T>& mv, const C<IO<T>>* p, cudaStream_t st) {
     DDA_LEN_SWITCH(mv.g.Ly, (p1_width<T, LN>(mv, p, st)))
 }
 

@@ -1,0 +1,18 @@
+// Instantiations of the matvec pass P3 (z-forward, spectrum product,
+// z-inverse) for the 3 * 2^a lengths, complex double-float (df.cuh).
+#include "matvec_kernels.cuh"
+
+namespace dda {
+
+template <typename T, int N> int p3_len(const MatvecView<T>& mv, cudaStream_t st) {
+    return launch_p3<T, N>(mv, st);
+}
+
+template int p3_len<DF, 24>(const MatvecView<DF>&, cudaStream_t);
+template int p3_len<DF, 48>(const MatvecView<DF>&, cudaStream_t);
+template int p3_len<DF, 96>(const MatvecView<DF>&, cudaStream_t);
+template int p3_len<DF, 192>(const MatvecView<DF>&, cudaStream_t);
+template int p3_len<DF, 384>(const MatvecView<DF>&, cudaStream_t);
+template int p3_len<DF, 768>(const MatvecView<DF>&, cudaStream_t);
+
+}  // namespace dda

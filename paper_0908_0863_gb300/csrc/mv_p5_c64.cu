@@ -5,11 +5,11 @@
 namespace dda {
 
 template <typename T, int LN>
-static int p5_width(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t st) {
+static int p5_width(const MatvecView<T>& mv, const C<IO<T>>* p, C<IO<T>>* y, cudaStream_t st) {
     DDA_LOGW_SWITCH(mv.logW_y, (launch_p5<T, LN, LW>(mv, p, y, st)))
 }
 
-template <typename T> int pass5(const MatvecView<T>& mv, const C<T>* p, C<T>* y, cudaStream_t st) {
+template <typename T> int pass5(const MatvecView<T>& mv, const C<IO<T>>* p, C<IO<T>>* y, cudaStream_t st) {
     DDA_LEN_SWITCH(mv.g.Ly, (p5_width<T, LN>(mv, p, y, st)))
 }
 

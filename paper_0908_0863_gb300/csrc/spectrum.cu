@@ -243,6 +243,25 @@ __global__ void __launch_bounds__(256) k_spec_export(Geometry g, const C<T>* __r
     }
 }
 
+// the double-float copy of the spectrum: each double split into the nearest
+// float and the rounded remainder
+__global__ void __launch_bounds__(256) k_spec_to_df(const double2* __restrict__ in, cdf* __restrict__ out, int64_t n) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = in[e];
+        cdf z;
+        z.x = DF(v.x);
+        z.y = DF(v.y);
+        out[e] = z;
+    }
+}
+
+int spectrum_to_df(const double2* in, cdf* out, size_t n, cudaStream_t st) {
+    const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
+    k_spec_to_df<<<blocks, 256, 0, st>>>(in, out, (int64_t)n);
+    DDA_LAUNCH_CHECK("spectrum double-float copy");
+    return 0;
+}
+
 int export_spectrum(const Geometry& g, const void* in, void* out, bool c128, cudaStream_t st) {
     const size_t ns = 6ull * g.Hz * g.Hy * g.Hx;
     if (!wide_len(g.Lz)) {   // stored in the exported order

@@ -182,3 +182,29 @@ def test_inner_tolerance_control_and_autotune(dda):
         assert dda.dda_inner_tolerance(lat.ctx) == rho
     with case.lattice() as lat2:
         assert dda.dda_inner_tolerance(lat2.ctx) == rho
+
+
+def test_mixed_refinement_residual_products(dda):
+    """The mixed refinement's true residuals from double-float products (the
+    default) and from FP64 products give the same solve to 1e-10 at tol 1e-10
+    (FP64 solve as the reference), both with a true residual within tol."""
+    m = 1.33 + 0.01j
+    case = Case(synth.sphere(18, box=(18, 17, 19)), [m], 0.5 / abs(m))
+    with case.lattice() as lat:
+        assert dda.dda_residual_dtype(lat.ctx) == "c128df"
+        E = torch.empty((3, case.nd), dtype=torch.complex128, device="cuda")
+        lat.incident_field([0.6, 0, 0.8], [0, 1, 0], E)
+        Pf = torch.zeros_like(E)
+        sf, _ = lat.solve(E, Pf, "bicgstab", "fp64", tol=1e-12, max_iter=4000)
+        out = {}
+        for rd in ("c128df", "c128"):
+            assert dda.dda_residual_dtype(lat.ctx, rd) == rd
+            P = torch.zeros_like(E)
+            st, info = lat.solve(E, P, "bicgstab", "mixed", tol=1e-10, max_iter=4000)
+            assert st == dda.DDA_OK and info["rel_residual_true"] <= 1e-10, (rd, info)
+            out[rd] = (P, info)
+        assert sf == dda.DDA_OK
+        for rd, (P, info) in out.items():
+            assert float((P - Pf).norm() / Pf.norm()) < 1e-9, rd
+        with pytest.raises(dda.DDAError):
+            dda.dda_residual_dtype(lat.ctx, "c64")
