@@ -456,6 +456,24 @@ def extras(args, dda, torch, dev, shape, bits, alpha, nd, pass_ms, khat, pols, m
                            "five_pass_GBps": sum(ab[f"P{i}"] for i in range(1, 6)) / (ms / 1e3) / 1e9,
                            "pass_ms": [t / c if c else None for c, t in prof]}
             del p, y
+        # the double-float product of the mixed refinement's residuals
+        # (complex128 in and out), against the FP64 product of the same vector
+        p = torch.randn((3, nd), dtype=torch.complex128, device=dev)
+        y, y64 = torch.empty_like(p), torch.empty_like(p)
+        dda.dda_matvec(ctx, p, y64)
+        dda.dda_matvec(ctx, p, y, dtype="c128df")
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            dda.dda_matvec(ctx, p, y, dtype="c128df")
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / 3
+        rates["c128df"] = {"matvecs_per_s": 1e3 / ms, "ms": ms,
+                           "rel_diff_vs_c128": float((y - y64).norm() / y64.norm()),
+                           "what": "double-float product (float pairs), complex128 in and out"}
+        del p, y, y64
         out["fft_matvecs"] = rates
         # the complex128 product is FP64-ALU-bound: its algorithmic flops
         # against the DGEMM rate measured here
@@ -505,14 +523,18 @@ def timed_solve(dda, torch, dev, ctx, E, method, precision, args):
 def mixed_vs_fp64(dda, torch, dev, ctx, nd, khat, e0, args):
     """The bench target's first right-hand side solved to the bench tolerance
     with BiCGSTAB and QMR, each in mixed precision (complex64 products in
-    FP64 refinement) and in FP64: time, products, true residual (one FP64
-    product), and the mixed result's relative difference from the FP64 one
-    in C_ext, C_abs, C_sca and in P."""
+    FP64 refinement, the method's own tuned inner target) and in FP64: time,
+    products, true residual (one FP64 product), and the mixed result's
+    relative difference from the FP64 one in C_ext, C_abs, C_sca and in P."""
     E = torch.empty((3, nd), dtype=torch.complex128, device=dev)
     dda.dda_incident_field(ctx, khat, e0, E)
     res = {"tol": args.tol, "what": "same right-hand side, BiCGSTAB and QMR, mixed and FP64"}
     for method in ("bicgstab", "qmr"):
+        if args.autotune and method != args.method:
+            # each method's own inner target (untimed), as the job's method has
+            dda.dda_autotune_inner(ctx, E, method, args.tol, args.max_iter)
         mixed, Pm = timed_solve(dda, torch, dev, ctx, E, method, "mixed", args)
+        mixed["inner_rho"] = dda.dda_inner_tolerance(ctx, method=method)
         fp64, Pf = timed_solve(dda, torch, dev, ctx, E, method, "fp64", args)
         diff = [abs(a / b - 1.0) for a, b in zip(mixed["cross_sections"], fp64["cross_sections"])]
         pdiff = float((Pm - Pf).norm() / Pf.norm())

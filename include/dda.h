@@ -272,10 +272,14 @@ int dda_autotune(dda_ctx* ctx, int dtype, int nb, int reps, double* pass_ms, voi
  * refinement's current relative residual: by default (rho = 0) one inner
  * solve reaches the final tolerance, a larger rho (in (0, 1)) stops each
  * inner solve after that reduction and lets the FP64 refinement take more
- * steps.  rho_in (may be NULL) sets rho, rho_out (may be NULL) receives it.
+ * steps.  Each Krylov method has its own rho (a method that restarts
+ * badly, such as QMR, loses by the extra refinements that suit BiCGSTAB);
+ * method is a dda_method value (the Jacobi flag is ignored).  rho_in (host,
+ * may be NULL) sets rho of that method, rho_out (host, may be NULL)
+ * receives it.  DDA_ERR_ARG for an unknown method or rho outside [0, 1).
  * This is a choice of this library (the paper runs one precision only).
  */
-int dda_inner_tolerance(dda_ctx* ctx, const double* rho_in, double* rho_out);
+int dda_inner_tolerance(dda_ctx* ctx, int method, const double* rho_in, double* rho_out);
 
 /*
  * Products of the true residuals r = einc - A x in the mixed-precision
@@ -292,17 +296,17 @@ int dda_inner_tolerance(dda_ctx* ctx, const double* rho_in, double* rho_out);
 int dda_residual_dtype(dda_ctx* ctx, const int* dtype_in, int* dtype_out);
 
 /*
- * Tune rho of dda_inner_tolerance on this context: solve A P = einc (host
- * or device [3][N_d] complex128) in mixed precision to tol with the given
- * method for rho = 0, 1e-4, 1e-3 and 1e-2, timing each solve with CUDA
- * events, and keep the fastest that converged; rho = 0 stays unless another
- * candidate is faster by more than 2% (the noise of one timing is about
- * 1%).  The choice is set on the
- * context and remembered for the process: contexts created later with the
- * same lattice shape start with it.  rho_out (host, may be NULL) receives
- * it, ms_out (host double[4], may be NULL) the solve times (-1: not
- * converged).  Allocates and frees one scratch solution; synchronises.
- * DDA_ERR_NOT_CONVERGED when no candidate converged.
+ * Tune rho of dda_inner_tolerance for one method on this context: solve
+ * A P = einc (host or device [3][N_d] complex128) in mixed precision to tol
+ * with the given method for rho = 0, 1e-4, 1e-3, 1e-2, 3e-2 and 1e-1,
+ * timing each solve with CUDA events, and keep the fastest that converged;
+ * rho = 0 stays unless another candidate is faster by more than 2% (the
+ * noise of one timing is about 1%).  The choice is set on the context for
+ * that method and remembered for the process: contexts created later with
+ * the same lattice shape start with it for that method.  rho_out (host, may
+ * be NULL) receives it, ms_out (host double[6], may be NULL) the solve times
+ * (-1: not converged).  Allocates and frees one scratch solution;
+ * synchronises.  DDA_ERR_NOT_CONVERGED when no candidate converged.
  */
 int dda_autotune_inner(dda_ctx* ctx, const void* einc, int method, double tol, int max_iter, double* rho_out,
                        double* ms_out, void* stream);

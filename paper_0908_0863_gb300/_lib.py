@@ -122,7 +122,7 @@ def load(path: str | None = None):
     L.dda_cross_sections_batch.argtypes = [vp, i32, vp, vp, vp, vp]
     L.dda_occupancy_ranks_static.argtypes = [vp, i64, vp, vp, vp]
     L.dda_material_sums.argtypes = [vp, vp, vp, vp]
-    L.dda_inner_tolerance.argtypes = [vp, vp, vp]
+    L.dda_inner_tolerance.argtypes = [vp, i32, vp, vp]
     L.dda_residual_dtype.argtypes = [vp, vp, vp]
     L.dda_autotune_inner.argtypes = [vp, vp, i32, ctypes.c_double, i32, vp, vp, vp]
     L.dda_scattering_cross_section.argtypes = [vp, vp, vp, vp]
@@ -374,11 +374,12 @@ def dda_polarizability_derivative(m, k, rule="cmrr", khat=None, e0=None, given="
     return (out[0::2] + 1j * out[1::2]).reshape(n, 3)
 
 
-def dda_inner_tolerance(ctx, rho=None) -> float:
-    """The mixed-precision inner reduction rho of the context (set first when given)."""
+def dda_inner_tolerance(ctx, rho=None, method="bicgstab") -> float:
+    """The mixed-precision inner reduction rho of the context for one Krylov
+    method (set first when given)."""
     rin = None if rho is None else np.array([float(rho)])
     out = np.zeros(1)
-    _check(load().dda_inner_tolerance(ctypes.c_void_p(ctx), _ptr(rin), _ptr(out)))
+    _check(load().dda_inner_tolerance(ctypes.c_void_p(ctx), method_code(method), _ptr(rin), _ptr(out)))
     return float(out[0])
 
 
@@ -394,10 +395,10 @@ def dda_residual_dtype(ctx, dtype=None) -> str:
 def dda_autotune_inner(ctx, einc, method="bicgstab", tol=1e-5, max_iter=4000, stream=None):
     """Tunes rho on einc; returns (rho, {rho candidate: solve ms or -1})."""
     rho = np.zeros(1)
-    ms = np.zeros(4)
+    ms = np.zeros(6)
     _check(load().dda_autotune_inner(ctypes.c_void_p(ctx), _ptr(einc), method_code(method), float(tol),
                                      int(max_iter), _ptr(rho), _ptr(ms), _stream(stream)))
-    return float(rho[0]), dict(zip((0.0, 1e-4, 1e-3, 1e-2), (float(v) for v in ms)))
+    return float(rho[0]), dict(zip((0.0, 1e-4, 1e-3, 1e-2, 3e-2, 1e-1), (float(v) for v in ms)))
 
 
 def dda_material_sums(ctx, v, n_materials, stream=None) -> np.ndarray:

@@ -130,7 +130,9 @@ struct dda_ctx {
     double2* aux[3] = {};     // adjoint / C_sca work vectors (P, right-hand side, mu)
     double2* dainv64 = nullptr;  // d(alpha^-1)/d eps table of the last gradient call
     Space sp;
-    double inner_rho = 0.0;      // mixed precision: smallest residual reduction an inner solve aims at (0: none)
+    // mixed precision, per Krylov method: smallest residual reduction an
+    // inner solve aims at (0: none)
+    std::array<double, DDA_MLBICGSTAB3 + 1> inner_rho{};
     int residual_dtype = DDA_C128DF;   // mixed precision: products of the true residuals
     MatvecView<double> mv64{};   // geometry, tables and tiles; work set per call
     MatvecView<float> mv32{};
@@ -356,9 +358,9 @@ std::map<std::array<int, 4>, std::array<int, 4>> g_tiles;
 std::array<int, 4> tile_key(const Geometry& g, int dtype) { return {g.K, g.J, g.P, dtype}; }
 
 // The inner-solve target of the mixed precision chosen by
-// dda_autotune_inner, per lattice shape, likewise.
+// dda_autotune_inner, per lattice shape and Krylov method, likewise.
 std::map<std::array<int, 4>, double> g_inner;
-constexpr int kInnerCandidates = 4;
+constexpr int kInnerCandidates = 6;
 
 template <typename T>
 void apply_tiles(MatvecView<T>& m, const std::array<int, 4>& t) {
@@ -658,8 +660,10 @@ int dda_init_lattice(dda_ctx** out, const int32_t shape[3], const uint32_t* occu
         if (it != g_tiles.end()) apply_tiles(m, it->second);
         it = g_tiles.find(tile_key(g, DDA_C64));
         if (it != g_tiles.end()) apply_tiles(f, it->second);
-        auto ir = g_inner.find(tile_key(g, -1));
-        if (ir != g_inner.end()) c->inner_rho = ir->second;
+        for (int mth = 0; mth <= DDA_MLBICGSTAB3; ++mth) {
+            auto ir = g_inner.find(tile_key(g, -1 - mth));
+            if (ir != g_inner.end()) c->inner_rho[mth] = ir->second;
+        }
     }
     *out = c;
     return DDA_OK;
@@ -1013,7 +1017,7 @@ static int solve_batch(dda_ctx* c, int nb, const void* einc, void* p, int method
                     // inner target: enough to reach tol from here, not below what FP32
                     // sustains, and no finer than the context's per-solve reduction
                     double ti = std::max(0.3 * tol / rel, 1e-6);
-                    if (c->inner_rho > 0.0) ti = std::max(ti, c->inner_rho);
+                    if (c->inner_rho[method] > 0.0) ti = std::max(ti, c->inner_rho[method]);
                     hc[b].tol = std::min(0.5, ti);
                     hc[b].scale = 1.0 / std::sqrt(rn2[b]);
                     hc[b].mult = std::sqrt(rn2[b]);
@@ -1127,13 +1131,16 @@ int dda_solve(dda_ctx* c, const void* einc, void* p, int method, int precision, 
     return dda_solve_batch(c, 1, einc, p, method, precision, tol, max_iter, use_x0, info, nullptr, stream);
 }
 
-int dda_inner_tolerance(dda_ctx* c, const double* rho_in, double* rho_out) {
+int dda_inner_tolerance(dda_ctx* c, int method, const double* rho_in, double* rho_out) {
     if (int rc = check_ctx(c)) return rc;
+    if ((method & ~(0xff | DDA_PRECOND_JACOBI)) || (method & 0xff) > DDA_MLBICGSTAB3)
+        return fail(DDA_ERR_ARG, "dda_inner_tolerance: unknown method");
+    method &= 0xff;
     if (rho_in) {
         if (!(*rho_in >= 0.0 && *rho_in < 1.0)) return fail(DDA_ERR_ARG, "dda_inner_tolerance: rho must be in [0, 1)");
-        c->inner_rho = *rho_in;
+        c->inner_rho[method] = *rho_in;
     }
-    if (rho_out) *rho_out = c->inner_rho;
+    if (rho_out) *rho_out = c->inner_rho[method];
     return DDA_OK;
 }
 
@@ -1152,7 +1159,7 @@ int dda_autotune_inner(dda_ctx* c, const void* einc, int method, double tol, int
                        double* ms_out, void* stream) {
     if (int rc = check_solve_args(c, 1, einc, einc, method, DDA_MIXED, tol, max_iter)) return rc;
     cudaStream_t st = as_stream(stream);
-    const double cand[kInnerCandidates] = {0.0, 1e-4, 1e-3, 1e-2};
+    const double cand[kInnerCandidates] = {0.0, 1e-4, 1e-3, 1e-2, 3e-2, 1e-1};
     const size_t bytes = 3 * c->g.nd * sizeof(double2);
     void* p = nullptr;
     cudaError_t e = cudaMalloc(&p, bytes);
@@ -1160,11 +1167,12 @@ int dda_autotune_inner(dda_ctx* c, const void* einc, int method, double tol, int
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const double keep = c->inner_rho;
+    const int mth = method & 0xff;
+    const double keep = c->inner_rho[mth];
     double best = -1.0, best_ms = 0.0;
     int rc = 0;
     for (int q = 0; q < kInnerCandidates && !rc; ++q) {
-        c->inner_rho = cand[q];
+        c->inner_rho[mth] = cand[q];
         dda_solve_info info{};
         cudaEventRecord(e0, st);
         int status = dda_solve_batch(c, 1, einc, p, method, DDA_MIXED, tol, max_iter, 0, &info, nullptr, stream);
@@ -1187,12 +1195,15 @@ int dda_autotune_inner(dda_ctx* c, const void* einc, int method, double tol, int
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(p);
-    if (rc) { c->inner_rho = keep; return rc; }
-    if (best < 0.0) { c->inner_rho = keep; return fail(DDA_ERR_NOT_CONVERGED, "dda_autotune_inner: no candidate converged"); }
-    c->inner_rho = best;
+    if (rc) { c->inner_rho[mth] = keep; return rc; }
+    if (best < 0.0) {
+        c->inner_rho[mth] = keep;
+        return fail(DDA_ERR_NOT_CONVERGED, "dda_autotune_inner: no candidate converged");
+    }
+    c->inner_rho[mth] = best;
     {
         std::lock_guard<std::mutex> lock(g_tiles_mu);
-        g_inner[tile_key(c->g, -1)] = best;
+        g_inner[tile_key(c->g, -1 - mth)] = best;
     }
     if (rho_out) *rho_out = best;
     return DDA_OK;

@@ -10,6 +10,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 
 namespace dda {
 
@@ -20,6 +21,17 @@ struct DF {
     __host__ __device__ __forceinline__ DF(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
     __host__ __device__ __forceinline__ DF(float h, float l) : hi(h), lo(l) {}
 };
+
+// The high product, rounded on its own: the device compiler never contracts
+// __fmul_rn into the sum that follows it, which would count the product's
+// rounding error twice.
+__host__ __device__ __forceinline__ float df_mul(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fmul_rn(a, b);
+#else
+    return a * b;
+#endif
+}
 
 __host__ __device__ __forceinline__ DF df_fast_two_sum(float a, float b) {   // |a| >= |b|
     const float s = a + b;
@@ -37,7 +49,7 @@ __host__ __device__ __forceinline__ DF operator+(DF a, DF b) {
 __host__ __device__ __forceinline__ DF operator-(DF a) { return DF(-a.hi, -a.lo); }
 __host__ __device__ __forceinline__ DF operator-(DF a, DF b) { return a + (-b); }
 __host__ __device__ __forceinline__ DF operator*(DF a, DF b) {
-    const float p = a.hi * b.hi;
+    const float p = df_mul(a.hi, b.hi);
     float e = fmaf(a.hi, b.hi, -p);   // the exact error of the high product
     e = fmaf(a.hi, b.lo, e);
     e = fmaf(a.lo, b.hi, e);

@@ -1,6 +1,6 @@
-// Instantiations of the matvec passes P2 and P4 (x-forward, x-inverse) in
-// complex double-float (df.cuh) for every line length and tile width, and
-// their dispatcher.
+// Instantiations of the matvec pass P2 (x-forward) in complex double-float
+// (df.cuh) for every line length and tile width, and its dispatcher (P4 is
+// a translation unit of its own, so that the two compile in parallel).
 #include "matvec_kernels.cuh"
 
 namespace dda {
@@ -10,6 +10,5 @@ template <typename T, bool INV> int pass_rows(const MatvecView<T>& mv, cudaStrea
 }
 
 template int pass_rows<DF, false>(const MatvecView<DF>&, cudaStream_t);
-template int pass_rows<DF, true>(const MatvecView<DF>&, cudaStream_t);
 
 }  // namespace dda

@@ -159,8 +159,9 @@ def test_polarizability_matches_oracle(dda):
 def test_inner_tolerance_control_and_autotune(dda):
     """Mixed precision with a coarse inner target (rho = 1e-2) needs more FP64
     refinements and reaches the same tolerance; dda_autotune_inner picks one
-    of its candidates, sets it and hands it to the next context of the shape
-    (a lattice shape of its own, so that no other test inherits the choice)."""
+    of its candidates, sets it for the tuned method only and hands it to the
+    next context of the shape (a lattice shape of its own, so that no other
+    test inherits the choice)."""
     m = 1.33 + 0.01j
     case = Case(synth.sphere(16, box=(16, 16, 17)), [m], 0.5 / abs(m))
     with case.lattice() as lat:
@@ -170,6 +171,7 @@ def test_inner_tolerance_control_and_autotune(dda):
         P = torch.zeros_like(E)
         s0, i0 = lat.solve(E, P, "bicgstab", "mixed", tol=1e-8, max_iter=2000)
         assert dda.dda_inner_tolerance(lat.ctx, 1e-2) == 1e-2
+        assert dda.dda_inner_tolerance(lat.ctx, method="qmr") == 0.0
         P1 = torch.zeros_like(E)
         s1, i1 = lat.solve(E, P1, "bicgstab", "mixed", tol=1e-8, max_iter=2000)
         assert s0 == s1 == dda.DDA_OK
@@ -177,11 +179,17 @@ def test_inner_tolerance_control_and_autotune(dda):
         assert float((P1 - P).norm() / P.norm()) < 1e-7
         with pytest.raises(dda.DDAError):
             dda.dda_inner_tolerance(lat.ctx, 1.5)
-        rho, ms = dda.dda_autotune_inner(lat.ctx, E, "bicgstab", 1e-8, 2000)
+        with pytest.raises(dda.DDAError):
+            dda.dda_inner_tolerance(lat.ctx, method=99)
+        dda.dda_inner_tolerance(lat.ctx, 0.0)
+        dda.dda_inner_tolerance(lat.ctx, 1e-3, method="qmr")
+        rho, ms = dda.dda_autotune_inner(lat.ctx, E, "bicgstab+jacobi", 1e-8, 2000)
         assert rho in ms and ms[rho] > 0 and all(v == -1 or v > 0 for v in ms.values())
         assert dda.dda_inner_tolerance(lat.ctx) == rho
+        assert dda.dda_inner_tolerance(lat.ctx, method="qmr") == 1e-3
     with case.lattice() as lat2:
         assert dda.dda_inner_tolerance(lat2.ctx) == rho
+        assert dda.dda_inner_tolerance(lat2.ctx, method="qmr") == 0.0
 
 
 def test_mixed_refinement_residual_products(dda):
