@@ -501,6 +501,8 @@ def extras(args, dda, torch, dev, shape, bits, alpha, nd, pass_ms, khat, pols, m
         out["x_rows"] = x_pass_rows(dda, torch, dev, hbm)
     if args.aggregates:
         out["aggregates"] = aggregates_workload(dda, torch, dev, args, extra=True)
+    if args.table4:
+        out["table4_sphere200"] = table4_sphere200(dda, torch, dev, args)
     return out
 
 
@@ -562,6 +564,88 @@ def timed_setup(dda, torch, dev, shape, bits, alpha, reps=3):
     return {"ms": statistics.median(ms), "samples_ms": ms,
             "what": "dda_init_lattice at 256^3 (padded 512^3): device allocations, ranks, alpha^-1, spectrum "
                     "(section 1 + x/y/z line DFTs in FP64, complex64 copy)"}
+
+
+# The paper's solver benchmark target (Sec. 6, Tables 3 and 4): SPHERE 200^3
+# (N_d = 4,188,896), size parameter x = 0.98948, m = 1.63631 + 0.372i,
+# point-Jacobi, tol 1e-10, x0 = 0; Table 4 prints, per scheme, the serial
+# (one NEMO core) and 4-thread times per iteration and per product, the
+# tensor set-up (creation + DFT) and the memory, all in FP64.
+T4_N = 200
+T4_X = 0.98948
+T4_M = 1.63631 + 0.372j
+T4_TOL = 1e-10
+T4_PAPER = {"bicgstab": {"iteration_s": 68.3, "product_s": 32.7, "memory_gb": 3.1},
+            "bicg_sym": {"iteration_s": 33.9, "product_s": 32.4, "memory_gb": 2.6},
+            "qmr_sym": {"iteration_s": 35.1, "product_s": 33.1, "memory_gb": 3.1},
+            "tensor_setup_s": 13.4, "omp4_tensor_setup_s": 3.8}
+
+
+def table4_sphere200(dda, torch, dev, args):
+    """Table 4's workload on the GPU: context set-up (the tensor creation +
+    DFT step), FP64 and complex64 products, and FP64 solves with point-Jacobi
+    to 1e-10 by BiCGSTAB, BiCG_sym and QMR_sym (time per iteration = solve
+    time / iterations; products per iteration from the solver's count), with
+    the device memory of the context, beside the paper's serial figures."""
+    import synth
+    mask = synth.sphere(T4_N)
+    nd = int(mask.sum())
+    a_eff = (3.0 * nd / (4.0 * math.pi)) ** (1.0 / 3.0)     # effective radius, lattice spacing 1
+    k = T4_X / a_eff
+    alpha = dda.dda_polarizability([T4_M], k, "ldr", [0, 0, 1], [1, 0, 0])
+    shape = (T4_N,) * 3
+    mask_dev = torch.from_numpy(mask.reshape(-1)).to(dev)
+    bits = torch.empty((mask.size + 31) // 32, dtype=torch.int32, device=dev)
+    dda.dda_pack_occupancy(mask_dev, bits)
+    del mask_dev
+    setup = []
+    for r in range(3):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        ctx = dda.dda_init_lattice(shape, bits, None, 1, alpha, k)
+        torch.cuda.synchronize(dev)
+        if r:
+            setup.append((time.perf_counter() - t0) * 1e3)
+        if r < 2:
+            dda.dda_free(ctx)
+    out = {"what": "SPHERE 200^3, x = 0.98948, m = 1.63631+0.372i, LDR, point-Jacobi, FP64 solves to 1e-10 from "
+                   "x0 = 0 (Sec. 6, Tables 3 and 4); paper: one NEMO core, FP64",
+           "n_dipoles": nd, "setup_ms": statistics.median(setup), "paper": T4_PAPER}
+    try:
+        E = torch.empty((3, nd), dtype=torch.complex128, device=dev)
+        dda.dda_incident_field(ctx, [0, 0, 1], [1, 0, 0], E)
+        for name, dtype, reps in (("c128", torch.complex128, 5), ("c64", torch.complex64, 20)):
+            p = E.to(dtype)
+            y = torch.empty_like(p)
+            dda.dda_matvec(ctx, p, y)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                dda.dda_matvec(ctx, p, y)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            out[f"product_ms_{name}"] = e0.elapsed_time(e1) / reps
+            del p, y
+        P = torch.empty_like(E)
+        for method in ("bicgstab", "bicg_sym", "qmr_sym"):
+            P.zero_()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            status, info = dda.dda_solve(ctx, E, P, method + "+jacobi", "fp64", T4_TOL, 10000)
+            dt = time.perf_counter() - t0
+            q = dda.dda_query(ctx)
+            out[method] = {"status": status, "seconds": dt, "iterations": info["iterations"],
+                           "matvecs": info["matvecs"], "iteration_ms": dt * 1e3 / max(1, info["iterations"]),
+                           "rel_residual_true": info["rel_residual_true"],
+                           "device_gb": q["device_bytes"] / 1e9,
+                           "speedup_per_iteration_vs_paper_serial":
+                               T4_PAPER[method]["iteration_s"] * 1e3 / (dt * 1e3 / max(1, info["iterations"]))}
+        out["speedup_product_vs_paper_serial"] = T4_PAPER["bicgstab"]["product_s"] * 1e3 / out["product_ms_c128"]
+        del E, P
+    finally:
+        dda.dda_free(ctx)
+    return out
 
 
 ELL_SEED = 20260002
@@ -1050,6 +1134,8 @@ def main():
                     help="skip the x-pass sweep over rows of 160, 192, 320 and 384 points")
     ap.add_argument("--no-aggregates", dest="aggregates", action="store_false",
                     help="skip the ballistic-aggregate batching workload of the extras")
+    ap.add_argument("--no-table4", dest="table4", action="store_false",
+                    help="skip the SPHERE 200^3 solver-benchmark timings (Table 4's workload) of the extras")
     ap.add_argument("--agg-method", default="bicgstab")
     ap.add_argument("--e2e-steps", type=int, default=3,
                     help="jobs timed end to end through host buffers (at most --steps)")

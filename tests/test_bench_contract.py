@@ -91,3 +91,12 @@ def test_our_arm_contract():
     for r in rows.values():
         assert r["P2_ms"] > 0 and r["P4_ms"] > 0 and r["P2_GBps"] > 0
     assert d["e2e"]["steps"] >= 1
+    df = d["fft_matvecs"]["c128df"]
+    assert df["ms"] > 0 and df["rel_diff_vs_c128"] < 1e-12
+    # Table 4's workload: SPHERE 200^3, FP64 solves with point-Jacobi to 1e-10
+    t4 = d["table4_sphere200"]
+    assert t4["n_dipoles"] == 4188896 and t4["setup_ms"] > 0 and t4["product_ms_c128"] > 0
+    for method, ni in (("bicgstab", 12), ("bicg_sym", 21), ("qmr_sym", 21)):
+        r = t4[method]
+        assert r["status"] == 0 and r["rel_residual_true"] <= 1e-10 and abs(r["iterations"] - ni) <= 2
+        assert r["iteration_ms"] > 0 and r["device_gb"] > 0
