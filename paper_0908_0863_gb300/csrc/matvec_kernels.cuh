@@ -53,6 +53,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <type_traits>
 
 #include "fft_reg.cuh"
 #include "matvec.cuh"
@@ -297,6 +298,24 @@ __device__ __forceinline__ void p3_product(const C<T>* __restrict__ line, bool o
     X2 = cfma<T>(Y[5], c, cfma<T>(Y[4], b, cmul<T>(Y[2], a)));
 }
 
+// Line c of three held in registers, copied out and back with selects on the
+// (CTA-uniform) index c, so that a loop over the lines needs no dynamically
+// indexed register array.
+template <typename T>
+__device__ __forceinline__ void take_line(const C<T> (&v)[3][8], int c, C<T> (&u)[1][8]) {
+#pragma unroll
+    for (int m = 0; m < 8; ++m) u[0][m] = c == 0 ? v[0][m] : (c == 1 ? v[1][m] : v[2][m]);
+}
+template <typename T>
+__device__ __forceinline__ void put_line(C<T> (&v)[3][8], int c, const C<T> (&u)[1][8]) {
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        if (c == 0) v[0][m] = u[0][m];
+        else if (c == 1) v[1][m] = u[0][m];
+        else v[2][m] = u[0][m];
+    }
+}
+
 // R = 2^logW_z whole columns (x = xg R + w, row jy, batch slot j) per CTA,
 // T = N/8 threads per column (thread t holds the points t + T m of the
 // three components): z-forward DFTs of the P nonzero inputs, the spectrum
@@ -324,7 +343,20 @@ __global__ void __launch_bounds__(p3_max_threads<T>(N)) k_p3(MatvecView<T> mv) {
             v[c][m] = (ok && m < Line<N>::NH && n < g.P) ? col[c * comp + n] : mk<T>(0, 0);
         }
     const int region = row_ld(N, TL) << mv.logW_z;
-    fft_lines<T, false, N, 3, true, false>(v, sm, region, RowLayout<N, TL>{}, w, t, mv.tw);
+    if constexpr (sizeof(T) == 8 && !std::is_same<T, double>::value) {
+        // double-float: one component at a time, in a loop that is not
+        // unrolled, so that the kernel holds one line's transform instead of
+        // three (unrolled, its instruction fetch limited it, not arithmetic)
+#pragma unroll 1
+        for (int c = 0; c < 3; ++c) {
+            C<T> u[1][8];
+            take_line<T>(v, c, u);
+            fft_lines<T, false, N, 1, true, false>(u, sm, region, RowLayout<N, TL>{}, w, t, mv.tw);
+            put_line<T>(v, c, u);
+        }
+    } else {
+        fft_lines<T, false, N, 3, true, false>(v, sm, region, RowLayout<N, TL>{}, w, t, mv.tw);
+    }
     {
         const int my = jy <= g.Ly / 2 ? jy : g.Ly - jy, fy = jy > g.Ly / 2;
         const int mx = ix <= g.Lx / 2 ? ix : g.Lx - ix, fx = ix > g.Lx / 2;
@@ -333,8 +365,20 @@ __global__ void __launch_bounds__(p3_max_threads<T>(N)) k_p3(MatvecView<T> mv) {
         for (int m = 0; m < nv; ++m)
             p3_product<T, N>(line, ok, fx, fy, t + m * TL, v[0][m], v[1][m], v[2][m]);
     }
-    // nothing reuses the exchange buffers after the inverse
-    fft_lines<T, true, N, 3, false, true, false>(v, sm, region, RowLayout<N, TL>{}, w, t, mv.tw);
+    if constexpr (sizeof(T) == 8 && !std::is_same<T, double>::value) {
+        // each transform but the last ends with a barrier after its last
+        // shared-memory read, before the next one writes the buffer
+#pragma unroll 1
+        for (int c = 0; c < 3; ++c) {
+            C<T> u[1][8];
+            take_line<T>(v, c, u);
+            fft_lines<T, true, N, 1, false, true, true>(u, sm, region, RowLayout<N, TL>{}, w, t, mv.tw);
+            put_line<T>(v, c, u);
+        }
+    } else {
+        // nothing reuses the exchange buffers after the inverse
+        fft_lines<T, true, N, 3, false, true, false>(v, sm, region, RowLayout<N, TL>{}, w, t, mv.tw);
+    }
     if (ok) {
 #pragma unroll
         for (int c = 0; c < 3; ++c)
