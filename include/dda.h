@@ -112,7 +112,8 @@ typedef struct {
     int matvecs_fp64;         /* FP64 products (mixed: true-residual products, double-float by default) */
     int refinements;          /* outer refinement steps (mixed), 0 for FP64      */
     double rel_residual;      /* last recurrence residual / ||E_inc||            */
-    double rel_residual_true; /* ||E_inc - A P|| / ||E_inc|| with an FP64 product */
+    double rel_residual_true; /* ||E_inc - A P|| / ||E_inc||: FP64 product (mixed: the
+                                 refinement's residual product, dda_residual_dtype) */
     double seconds;           /* wall time of the call                           */
 } dda_solve_info;
 
@@ -334,8 +335,9 @@ int dda_incident_field(dda_ctx* ctx, const double* khat, const double* e0, void*
  *            guess when use_x0 != 0, else the start is 0 (Sec. 6); on return
  *            it holds the last iterate.
  *   precision: DDA_FP64 runs everything in FP64.  DDA_MIXED runs an outer
- *            FP64 iterative refinement: r = E_inc - A P with the FP64
- *            product, an inner complex64 Krylov solve of A d = r / ||r||
+ *            FP64 iterative refinement: r = E_inc - A P with the
+ *            double-float (default) or FP64 product (dda_residual_dtype),
+ *            an inner complex64 Krylov solve of A d = r / ||r||
  *            (complex64 products and vectors, FP64 inner products and
  *            scalars), P += ||r|| d, until ||r|| <= tol ||E_inc||.
  *   tol:      relative residual target (> 0); max_iter: cap on Krylov
@@ -343,7 +345,8 @@ int dda_incident_field(dda_ctx* ctx, const double* khat, const double* e0, void*
  *   info:     host, may be NULL.
  * Stopping rule: ||r||_2 <= tol ||E_inc||_2 on the recurrence residual
  * (BiCGSTAB also stops half way on ||s||); info->rel_residual_true is then
- * recomputed with one FP64 product.  Returns DDA_OK, DDA_ERR_NOT_CONVERGED
+ * recomputed with one FP64 product (DDA_MIXED: it is the refinement's own
+ * true residual).  Returns DDA_OK, DDA_ERR_NOT_CONVERGED
  * (max_iter reached, p = last iterate), DDA_ERR_BREAKDOWN, DDA_ERR_NAN,
  * DDA_ERR_ARG.  Synchronises the stream.
  */
